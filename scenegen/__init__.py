@@ -1,0 +1,268 @@
+"""Seeded synthetic inputs for the particle-optimisation hot path.
+
+This module only draws random numbers and packs them into the scene / skeleton /
+particle layouts that the library's C ABI (``include/tamp.h``) documents.  It holds
+none of the method's arithmetic: no kinematics, no signed distances, no costs, no
+gradients, no optimiser.  Both the CUDA path (through its Python binding) and the
+FP64 oracle consume what it returns; neither is imported here.
+
+The paper's own scenes (Tetris blocks, bookshelf, stick button, Franka / UR5 /
+Kinova sphere models) are not available, so every workload is synthetic, with the
+shapes the paper's experiments use (7-DOF arms, box objects approximated by
+spheres, oriented-cuboid obstacles, rectangular placement regions, pick-place
+skeletons, batches of 256..65536 particles).
+
+Conventions (metres, radians, z up):
+  * the table top is the plane z = 0; the arm base frame is the world frame;
+  * a box rests on a surface with its centre at z_top + h_z;
+  * arm DH parameters follow the standard (distal) convention
+    A_i = Rz(q_i + offset_i) Tz(d_i) Tx(a_i) Rx(alpha_i);
+  * arm sphere k of link i sits on the segment between joint i's origin and joint
+    i+1's origin, written in frame i (the frame at the distal end of link i);
+    in frame i that segment runs from (-a_i, -d_i sin alpha_i, -d_i cos alpha_i)
+    to the origin;
+  * a box is modelled by 8 spheres of radius r = min(h) centred at
+    (+-(h_x - r), +-(h_y - r), +-(h_z - r)) in the box frame;
+  * an action is (kind, box, surface) with kind 0 = Pick, 1 = Place,
+    2 = MinimizeObjDist (goal cost over every box moved so far).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+PICK, PLACE, GOAL = 0, 1, 2
+
+
+@dataclass
+class Scene:
+    """A synthetic scene; field names mirror ``tamp_scene_desc`` in include/tamp.h."""
+
+    dh_a: np.ndarray
+    dh_d: np.ndarray
+    dh_alpha: np.ndarray
+    dh_offset: np.ndarray
+    q_lo: np.ndarray
+    q_hi: np.ndarray
+    base: np.ndarray          # [4,4]
+    tool: np.ndarray          # [4,4]
+    sphere_link: np.ndarray   # [S] int32, 1..n (frame index the sphere is fixed to)
+    sphere_xyzr: np.ndarray   # [S,4] centre in that frame + radius
+    box_half: np.ndarray      # [B,3]
+    box_init: np.ndarray      # [B,4] x, y, z, yaw of the box centre
+    box_spheres: np.ndarray   # [B,NBS,4] centre in the box frame + radius
+    obs_center: np.ndarray    # [O,3]
+    obs_rot: np.ndarray       # [O,3,3] columns = obstacle axes in world
+    obs_half: np.ndarray      # [O,3]
+    surf: np.ndarray          # [NS,6] cx, cy, yaw, hx, hy, z_top
+    name: str = ""
+    seed: int = 0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_joints(self) -> int:
+        return int(self.dh_a.shape[0])
+
+    @property
+    def n_boxes(self) -> int:
+        return int(self.box_half.shape[0])
+
+
+def _rz3(yaw: float) -> np.ndarray:
+    c, s = math.cos(yaw), math.sin(yaw)
+    return np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+
+
+def random_arm(rng: np.random.Generator, n_joints: int = 7, spheres_per_link=5,
+               r_range=(0.04, 0.08), q_limit: float = 2.8, min_twisted: int = 3):
+    """Random serial revolute arm: a_i, d_i ~ U[0, 0.4] m, alpha_i in {0, +-pi/2}.
+
+    Arms with fewer than ``min_twisted`` non-zero twists are redrawn: with almost
+    all axes parallel the end effector cannot point down, and no top-down grasp
+    could ever be reached.  ``spheres_per_link`` is an int or a per-link list.
+    """
+    while True:
+        alpha = rng.choice(np.array([0.0, math.pi / 2, -math.pi / 2]), size=n_joints)
+        if int(np.count_nonzero(alpha)) >= min_twisted:
+            break
+    a = rng.uniform(0.0, 0.4, n_joints)
+    d = rng.uniform(0.0, 0.4, n_joints)
+    if np.isscalar(spheres_per_link):
+        spl = [int(spheres_per_link)] * n_joints
+    else:
+        spl = [int(v) for v in spheres_per_link]
+    links, xyzr = [], []
+    for i in range(n_joints):
+        start = np.array([-a[i], -d[i] * math.sin(alpha[i]), -d[i] * math.cos(alpha[i])])
+        n = spl[i]
+        for k in range(n):
+            t = (k + 0.5) / n
+            links.append(i + 1)
+            xyzr.append([*(start * (1.0 - t)), rng.uniform(*r_range)])
+    return dict(
+        dh_a=a, dh_d=d, dh_alpha=alpha, dh_offset=np.zeros(n_joints),
+        q_lo=np.full(n_joints, -q_limit), q_hi=np.full(n_joints, q_limit),
+        base=np.eye(4), tool=np.eye(4),
+        sphere_link=np.array(links, dtype=np.int32), sphere_xyzr=np.array(xyzr),
+    )
+
+
+def box_sphere_model(half: np.ndarray) -> np.ndarray:
+    """8 corner spheres of radius min(h) inside a box of half extents ``half``."""
+    r = float(np.min(half))
+    out = []
+    for sx in (-1.0, 1.0):
+        for sy in (-1.0, 1.0):
+            for sz in (-1.0, 1.0):
+                out.append([sx * (half[0] - r), sy * (half[1] - r), sz * (half[2] - r), r])
+    return np.array(out)
+
+
+def _polar(rng, r_lo, r_hi, ang_c=None, ang_w=math.pi):
+    r = rng.uniform(r_lo, r_hi)
+    ang = rng.uniform(-ang_w, ang_w) + (0.0 if ang_c is None else ang_c)
+    return np.array([r * math.cos(ang), r * math.sin(ang)])
+
+
+def _scatter(rng, n, radius_of, placed, sampler, tries=2000):
+    """Rejection-sample n footprint centres whose bounding circles do not overlap."""
+    out = []
+    for i in range(n):
+        rad = radius_of(i)
+        for _ in range(tries):
+            c = sampler()
+            if all(np.hypot(*(c - pc)) > rad + pr for pc, pr in placed):
+                break
+        else:
+            raise RuntimeError("scene generator: could not place item without overlap")
+        placed.append((c, rad))
+        out.append(c)
+    return out
+
+
+def make_scene(seed: int, n_boxes: int, n_obs: int, region_size, spheres_per_link=5,
+               n_joints: int = 7, name: str = "", region_radius: float = 0.55,
+               box_radius=(0.40, 0.85), obs_radius=(0.30, 1.15), obs_edges=(0.05, 0.30)):
+    """Pick-and-place scene: arm, ``n_boxes`` boxes on the table, ``n_obs`` cuboids,
+    one rectangular target region (surface 0) on the table."""
+    rng = np.random.default_rng(seed)
+    arm = random_arm(rng, n_joints, spheres_per_link)
+    half = rng.uniform(0.04, 0.10, size=(n_boxes, 3)) / 2.0
+    reg_ang = rng.uniform(-math.pi, math.pi)
+    reg_c = region_radius * np.array([math.cos(reg_ang), math.sin(reg_ang)])
+    reg_yaw = rng.uniform(-math.pi, math.pi)
+    reg_h = np.array(region_size, dtype=float) / 2.0
+    placed = [(np.zeros(2), 0.22), (reg_c, float(np.hypot(*reg_h)) + 0.02)]
+    box_xy = _scatter(rng, n_boxes, lambda i: float(np.hypot(*half[i, :2])) + 0.01, placed,
+                      lambda: _polar(rng, *box_radius, ang_c=reg_ang + math.pi, ang_w=1.4))
+    box_init = np.array([[c[0], c[1], half[i, 2], rng.uniform(-math.pi, math.pi)]
+                         for i, c in enumerate(box_xy)]).reshape(n_boxes, 4)
+    obs_half = rng.uniform(*obs_edges, size=(n_obs, 3)) / 2.0
+    obs_xy = _scatter(rng, n_obs, lambda i: float(np.hypot(*obs_half[i, :2])) + 0.02, placed,
+                      lambda: _polar(rng, *obs_radius))
+    obs_center = np.array([[c[0], c[1], obs_half[i, 2]] for i, c in enumerate(obs_xy)]).reshape(n_obs, 3)
+    obs_rot = np.stack([_rz3(rng.uniform(-math.pi, math.pi)) for _ in range(n_obs)]) if n_obs else np.zeros((0, 3, 3))
+    surf = np.array([[reg_c[0], reg_c[1], reg_yaw, reg_h[0], reg_h[1], 0.0]])
+    box_spheres = np.stack([box_sphere_model(h) for h in half])
+    return Scene(**arm, box_half=half, box_init=box_init, box_spheres=box_spheres,
+                 obs_center=obs_center, obs_rot=obs_rot, obs_half=obs_half, surf=surf,
+                 name=name, seed=seed)
+
+
+def pick_place_skeleton(box_order, surface: int = 0, goal: bool = False):
+    """Pick(b) / Place(b, surface) for each box in order, optional goal action."""
+    acts = []
+    for b in box_order:
+        acts.append((PICK, int(b), -1))
+        acts.append((PLACE, int(b), int(surface)))
+    if goal:
+        acts.append((GOAL, -1, -1))
+    return acts
+
+
+# ---------------------------------------------------------------- named workloads
+
+def plain_problem(seed: int = 1001):
+    """One box, 4 cuboids, 0.6 x 0.4 m region, Pick-Place skeleton (D = 21)."""
+    sc = make_scene(seed, n_boxes=1, n_obs=4, region_size=(0.6, 0.4), name="plain-1box")
+    return sc, pick_place_skeleton([0])
+
+
+def packing_problem(seed: int = 2001):
+    """Six boxes packed into a 0.3 x 0.3 m region minimising the sum of pairwise
+    centre distances, 8 cuboids, 6 Pick-Place pairs + goal (D = 126)."""
+    sc = make_scene(seed, n_boxes=6, n_obs=8, region_size=(0.3, 0.3), name="packing-6box")
+    return sc, pick_place_skeleton(range(6), goal=True)
+
+
+def stress_problem(seed: int = 5001):
+    """12 boxes, 64 cuboids, 100-sphere arm, 12 Pick-Place pairs (D = 252)."""
+    spl = [15, 15, 14, 14, 14, 14, 14]
+    sc = make_scene(seed, n_boxes=12, n_obs=64, region_size=(0.5, 0.5), spheres_per_link=spl,
+                    name="stress-12box", box_radius=(0.45, 1.0), obs_radius=(0.3, 1.6))
+    return sc, pick_place_skeleton(range(12), goal=True)
+
+
+# ---------------------------------------------------------------- particle batches
+
+def layout(actions, n_joints: int):
+    """Variable blocks of one particle, in the order include/tamp.h documents:
+    Pick -> grasp (x, y, z, yaw) then q; Place -> placement (x, y, yaw) then q;
+    the goal action adds no variable.  Returns [(kind, box, offset, size)]."""
+    out, off = [], 0
+    for kind, box, _surf in actions:
+        if kind == PICK:
+            out.append(("grasp", box, off, 4)); off += 4
+            out.append(("q", box, off, n_joints)); off += n_joints
+        elif kind == PLACE:
+            out.append(("place", box, off, 3)); off += 3
+            out.append(("q", box, off, n_joints)); off += n_joints
+    return out, off
+
+
+def random_particles(scene: Scene, actions, n: int, seed: int, spread: float = 1.0):
+    """[n, D] float64 particles drawn around the variables' natural bounds.
+
+    Joint angles U[lo - 0.2, hi + 0.2]; grasp positions within the grasp box
+    widened by 2 cm, yaw U[-pi, pi]; placements in the target region widened by
+    5 cm (region frame, then rotated into the world), yaw U[-pi, pi].  ``spread``
+    scales the widening margins.
+    """
+    rng = np.random.default_rng(seed)
+    blocks, D = layout(actions, scene.n_joints)
+    X = np.zeros((n, D))
+    surf_of = {}
+    for kind, box, s in actions:
+        if kind == PLACE:
+            surf_of[box] = s
+    for kind, box, off, size in blocks:
+        if kind == "q":
+            m = 0.2 * spread
+            X[:, off:off + size] = rng.uniform(scene.q_lo - m, scene.q_hi + m, size=(n, size))
+        elif kind == "grasp":
+            h = scene.box_half[box]
+            m = 0.02 * spread
+            lo = np.array([-h[0], -h[1], h[2] - 0.02]) - m
+            hi = np.array([h[0], h[1], h[2]]) + m
+            X[:, off:off + 3] = rng.uniform(lo, hi, size=(n, 3))
+            X[:, off + 3] = rng.uniform(-math.pi, math.pi, n)
+        elif kind == "place":
+            cx, cy, yaw, hx, hy, _z = scene.surf[surf_of.get(box, 0)]
+            m = 0.05 * spread
+            u = rng.uniform(-hx - m, hx + m, n)
+            v = rng.uniform(-hy - m, hy + m, n)
+            c, s = math.cos(yaw), math.sin(yaw)
+            X[:, off] = cx + c * u - s * v
+            X[:, off + 1] = cy + s * u + c * v
+            X[:, off + 2] = rng.uniform(-math.pi, math.pi, n)
+    return X
+
+
+def random_adam_state(n: int, D: int, seed: int):
+    """First/second moment buffers and step counts for an Adam-step parity case."""
+    rng = np.random.default_rng(seed)
+    m = rng.normal(0.0, 1e-2, size=(n, D))
+    v = rng.uniform(1e-8, 1e-3, size=(n, D))
+    return m, v
