@@ -1,0 +1,293 @@
+"""Benchmark: particle-iterations/s of the fused cost + adjoint + Adam path.
+
+Workload: the packing problem -- synthetic 7-DOF arm, 6 boxes packed into a
+0.3 x 0.3 m region minimising the sum of pairwise centre distances, 8 static
+cuboids, 6 pick-place pairs (D = 126), P = 4096 particles, 500 Adam iterations.
+One step = sample a fresh uniform batch + 500 fused iterations (each with the
+Eq. 3 check) + the final check, all on the GPU.  value = P * 500 / step time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank optimises its own batch (weak scaling; particles are
+independent, so there is no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+P_PARTICLES = 4096
+N_ITERS = 500
+SCENE_SEED = 2001
+METRIC = "particle-iters/s (cost+grad+update)"
+L2_FLUSH_BYTES = 512 << 20
+
+# DRAM traffic of one optimize_kernel launch on this workload, from an ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the
+# kernel source whose hash is recorded with it.
+TRAFFIC = {"source_sha": None, "bytes_per_launch": None}
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("tamp_kernels.cu", "tamp_dev.cuh"):
+        with open(os.path.join(ROOT, "paper_2411_11833_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--particles", type=int, default=P_PARTICLES)
+    ap.add_argument("--iters", type=int, default=N_ITERS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.rows = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = sorted(float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def cpu_baseline(sample_particles=32, budget_s=12.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    import torch
+
+    import scenegen as sg
+    from oracle import philox
+    from oracle.problem import Problem
+    sc, acts = sg.packing_problem(SCENE_SEED)
+    pr = Problem(sc, acts)
+    x = torch.tensor(philox.sample_uniform(pr, sample_particles, 1))
+    m, v = torch.zeros_like(x), torch.zeros_like(x)
+    its = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        with torch.no_grad():
+            pr.satisfied(pr.term_values(x))
+        _, g = pr.gradient(x)
+        x, m, v = pr.adam_step(x, m, v, its + 1, g, sample_particles)
+        its += 1
+    dt = time.perf_counter() - t0
+    return {"value": sample_particles * its / dt, "unit": "particle-iters/s", "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": f"packing scene, {sample_particles} particles x {its} fused iterations (Eq. 3 check, "
+                      f"autodiff gradient, Adam) in FP64 on the host"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, same workload, metric
+    and unit, each step a bounded sample (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import torch
+
+    import scenegen as sg
+    from oracle import philox
+    from oracle.problem import Problem
+    sc, acts = sg.packing_problem(SCENE_SEED)
+    pr = Problem(sc, acts)
+    Ps, its_per_step = 32, 2
+    times = []
+    for step in range(args.warmup + args.steps):
+        x = torch.tensor(philox.sample_uniform(pr, Ps, 100 + step))
+        t0 = time.perf_counter()
+        pr.optimize(x, its_per_step)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    mean = sum(times) / len(times)
+    val = Ps * its_per_step / mean
+    cores = torch.get_num_threads()
+    sample = f"packing scene, {Ps} particles x {its_per_step} iterations per step, FP64 oracle on host cores"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "particle-iters/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "packing: 6 boxes, 8 cuboids, D=126, uniform init", "particles": Ps,
+                   "iters_per_step": its_per_step},
+        "cpu_baseline": {"value": val, "unit": "particle-iters/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "particle-iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2411_11833_b300.build import build_library
+    build_library()
+    import paper_2411_11833_b300 as pkg
+    import scenegen as sg
+    from paper_2411_11833_b300 import flops
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    P, T = args.particles, args.iters
+
+    sc, acts = sg.packing_problem(SCENE_SEED)
+    with torch.cuda.stream(stream):
+        scene = pkg.Scene(sc, device=local, stream=stream.cuda_stream)
+        pid = scene.set_skeleton(acts)
+    D, NT, _ = scene.problem_info(pid)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def one_step(seed):
+        scene.sample(pid, P, seed)
+        scene.optimize(pid, T)
+
+    for w in range(args.warmup):
+        one_step(1000 * rank + w)
+    torch.cuda.synchronize(dev)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()                      # evict L2 between timed steps
+                ev[k][0].record(stream)
+                scene.sample(pid, P, 7000 + 1000 * rank + k)
+                ev[k][1].record(stream)
+                scene.optimize(pid, T)
+                ev[k][2].record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    step_ms = [e0.elapsed_time(e2) for e0, _, e2 in ev]
+    kern_ms = [e1.elapsed_time(e2) for _, e1, e2 in ev]
+    total_ms = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(total_ms, op=dist.ReduceOp.MAX)
+    total_s = float(total_ms.item()) / 1e3
+    value = world * P * T * args.steps / total_s
+    q = scene.query(pid, P)
+
+    # end to end through the C ABI with host buffers: H2D of the batch, the
+    # optimisation, and the D2H read of the satisfied mask / costs / counts
+    x0 = torch.from_numpy(sg.random_particles(sc, acts, P, seed=11 + rank, spread=0.0).T.astype(np.float32).copy())
+    x0 = x0.pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    with torch.cuda.stream(stream):
+        scene.set_particles(pid, x0.numpy())
+        scene.optimize(pid, T)
+        scene.query(pid, P)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            scene.set_particles(pid, x0.numpy())
+            scene.optimize(pid, T)
+            qq = scene.query(pid, P)
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+    ncon = len(qq["counts"])
+    h2d = D * P * 4
+    d2h = P + 4 * P + 4 * ncon + 4
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    ev_flops = flops.eval_flops(sc, acts)
+    launch_flops = P * ((T + 1) * ev_flops + T * flops.adam_flops(D))
+    kern_s = sum(kern_ms) / len(kern_ms) / 1e3
+    props = torch.cuda.get_device_properties(dev)
+    peak = flops.fp32_peak_tflops(props.multi_processor_count, 2032.0)
+    achieved = launch_flops / kern_s / 1e12
+    sha = kernel_source_sha()
+    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["source_sha"] == sha else None
+    out = {
+        "metric": METRIC, "value": value, "unit": "particle-iters/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "packing: 7-DOF arm (35 spheres), 6 boxes, 8 cuboids, 0.3x0.3 m region, "
+                               "6 pick-place pairs + goal, D=126, uniform init",
+                   "particles_per_gpu": P, "iters_per_step": T, "l2": "flushed between steps (512 MiB write)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "optimize_kernel", "flop_per_launch": launch_flops,
+                     "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x 2032 MHz (max SM clock)"},
+        "e2e": {"value": P * T / e2e_s, "unit": "particle-iters/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+        "kernel_ms": sum(kern_ms) / len(kern_ms),
+        "satisfied_last_step": int(q["n_satisfied"]), "first_satisfying_iter_last_step": int(q["first_iter"]),
+    }
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(out))
+    scene.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * tamp.h -- C ABI of the B300 particle-optimisation library (libtamp.so).
+ *
+ * What it computes: the continuous half of a sequence-then-satisfy TAMP planner
+ * (arXiv 2411.11833, "cuTAMP").  A plan skeleton induces a constraint
+ * satisfaction problem over continuous parameters (Sec. V); a batch of
+ * "particles" -- candidate assignments -- is optimised in parallel by Adam on
+ * the batch-mean penalty objective (Eq. 2, Eq. 4, Sec. V-B) and a particle is a
+ * solution when every constraint is within its tolerance (Eq. 3).
+ *
+ * Conventions for every call:
+ *   - every function returns a tamp_status and never aborts; on failure the
+ *     outputs are left untouched and tamp_last_error() describes the cause;
+ *   - geometry is in metres and radians, z up; 4x4 poses are row-major;
+ *   - host pointers are owned by the caller and only read/written during the
+ *     call; the library owns all device memory it allocates (cudaMalloc on the
+ *     scene's device) and frees it in tamp_destroy_scene;
+ *   - all GPU work of a scene is issued on the stream given at creation, in call
+ *     order; calls on one scene must not be made from two threads at once;
+ *   - particle arrays are structure-of-arrays: component c of particle i is at
+ *     index c * stride + i (stride = number of particles unless stated).
+ *
+ * Particle layout of a skeleton (tamp_set_skeleton): the actions are walked in
+ * order; a Pick adds its grasp (x, y, z, yaw: end-effector pose in the object
+ * frame, top-down) and then its arm configuration (n_joints angles); a Place
+ * adds its placement (x, y, yaw of the box on the surface; z follows from the
+ * surface height) and then its configuration; the goal action adds nothing.
+ * This is the paper's stacking of each continuous variable across the batch
+ * (Sec. V-B, "Parallelizing on GPUs").
+ *
+ * Term layout of a skeleton: per action, in order, Pick -> [KIN_POS, KIN_ROT,
+ * GRASP, CFREE_HOLD, JOINT_LIMIT]; Place -> [KIN_POS, KIN_ROT, STABLE_PLACE,
+ * CFREE_HOLD, CFREE_PLACE, JOINT_LIMIT]; goal -> [OBJ_DIST].  OBJ_DIST is a
+ * cost (Eq. 1 objective), every other term a constraint with a tolerance.
+ */
+#ifndef TAMP_H
+#define TAMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TAMP_OK = 0,
+  TAMP_ERR_INVALID_ARG = 1,   /* a pointer, size or index is out of range        */
+  TAMP_ERR_STATE = 2,         /* call order violated (e.g. optimise before sample) */
+  TAMP_ERR_OOM = 3,           /* device allocation failed                         */
+  TAMP_ERR_CUDA = 4,          /* a CUDA runtime call failed                        */
+  TAMP_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up                */
+  TAMP_ERR_DEVICE_CHECK = 6   /* a device-side bounds check fired                  */
+} tamp_status;
+
+/* Action kinds (Listing 1; appendix "Actions"). */
+enum { TAMP_PICK = 0, TAMP_PLACE = 1, TAMP_GOAL_MIN_OBJ_DIST = 2 };
+
+/* Constraint / cost kinds (appendix "Constraints"; appendix cost listing). */
+enum {
+  TAMP_TERM_KIN_POS = 0,      /* Kin: ||t_EE - t_target||, m                          */
+  TAMP_TERM_KIN_ROT = 1,      /* Kin: geodesic angle between EE and target, rad       */
+  TAMP_TERM_GRASP = 2,        /* Grasp: bound distance of the grasp position          */
+  TAMP_TERM_STABLE_PLACE = 3, /* StablePlace: footprint corners outside the surface   */
+  TAMP_TERM_CFREE_HOLD = 4,   /* CFreeHold: arm + held box penetration depth, m       */
+  TAMP_TERM_CFREE_PLACE = 5,  /* CFreePlace: placed box penetration depth, m          */
+  TAMP_TERM_JOINT_LIMIT = 6,  /* Motion (limits part): bound distance of q            */
+  TAMP_TERM_OBJ_DIST = 7,     /* MinimizeObjDist goal cost: sum of pairwise distances */
+  TAMP_N_TERM_KINDS = 8
+};
+
+typedef struct tamp_scene tamp_scene;   /* opaque, library-owned */
+
+/* Scene Pi = (robot, movable boxes, static cuboids, surfaces) (Sec. III; the
+ * appendix's collision representation: spheres for robot and objects,
+ * oriented boxes for static obstacles).  All arrays are read during
+ * tamp_create_scene only. */
+typedef struct {
+  int n_joints;                 /* 1..8 revolute joints                                   */
+  const double *dh_a, *dh_d, *dh_alpha, *dh_offset;   /* [n_joints], standard DH:
+                                   A_i = Rz(q_i + offset_i) Tz(d_i) Tx(a_i) Rx(alpha_i)   */
+  const double *q_lo, *q_hi;    /* [n_joints] joint limits                                */
+  double base[16];              /* world <- frame 0                                       */
+  double tool[16];              /* frame n <- end effector                                */
+  int n_spheres;                /* arm collision spheres                                  */
+  const int *sphere_link;       /* [n_spheres] frame index 0..n_joints the sphere is on   */
+  const double *sphere_xyzr;    /* [n_spheres][4] centre in that frame, radius            */
+  int n_boxes;                  /* movable boxes, <= 32                                   */
+  const double *box_half;       /* [n_boxes][3] half extents                              */
+  const double *box_init;       /* [n_boxes][4] initial centre x, y, z and yaw            */
+  int spheres_per_box;          /* spheres per box model, 1..8                            */
+  const double *box_spheres;    /* [n_boxes][spheres_per_box][4] centre in box frame, r   */
+  int n_obs;                    /* static cuboids, 0..256                                 */
+  const double *obs_center;     /* [n_obs][3]                                             */
+  const double *obs_rot;        /* [n_obs][3][3] row-major, columns = cuboid axes         */
+  const double *obs_half;       /* [n_obs][3]                                             */
+  int n_surf;                   /* placement surfaces, >= 1 if the skeleton places        */
+  const double *surf;           /* [n_surf][6] centre x, y, yaw, half x, half y, top z    */
+} tamp_scene_desc;
+
+/* One skeleton action (Listing 1): Pick(box), Place(box, surface), or the goal
+ * MinimizeObjDist over every box the skeleton has placed so far. */
+typedef struct {
+  int kind;
+  int box;
+  int surface;
+} tamp_action;
+
+/* Weights lambda_c (Eq. 2), tolerances eps_c (Eq. 3) and Adam settings (Sec.
+ * V-B).  tamp_default_options fills the appendix's values: weights 1 except
+ * kinematic rotation 5 and stable placement 2, goal 0.25; tolerances 5 mm /
+ * 0.05 rad (Kin), 1 mm (collisions, containment, grasp bounds), 0 (joint
+ * limits); beta1 0.9, beta2 0.999, eps 1e-8; lr 1e-2 (joints, yaws), 3e-3 (m). */
+typedef struct {
+  float w[TAMP_N_TERM_KINDS];
+  float tol[TAMP_N_TERM_KINDS];
+  float lr_joint, lr_pos, lr_yaw;
+  float beta1, beta2, eps;
+  int optimize_grasp;           /* 0: grasps keep their sampled values (lr 0)            */
+  int scale_by_batch;           /* 1: gradient of the batch mean (Eq. 4), i.e. / N_b      */
+  int lanes;                    /* threads per (particle, configuration): 0 = tuned, 1,2,4,8 */
+  int reserved[3];
+} tamp_options;
+
+void tamp_default_options(tamp_options *opt);
+
+/* Copy a scene to the device.  device: CUDA ordinal; stream: a cudaStream_t
+ * (NULL = legacy default stream).  *out receives the handle. */
+tamp_status tamp_create_scene(const tamp_scene_desc *desc, int device, void *stream,
+                              tamp_scene **out);
+tamp_status tamp_destroy_scene(tamp_scene *scene);
+
+/* Compile a skeleton (Sec. V: con(pi), cost(pi), the particle layout above).
+ * Preconditions of the actions are checked (Pick needs an empty hand, Place
+ * the box in hand); a violation returns TAMP_ERR_INVALID_ARG.  opt may be NULL
+ * (defaults).  *problem_id receives an index valid for the scene's lifetime. */
+tamp_status tamp_set_skeleton(tamp_scene *scene, const tamp_action *actions, int n_actions,
+                              const tamp_options *opt, int *problem_id);
+
+/* Particle dimension D and number of terms of a compiled skeleton.  term_kinds
+ * (may be NULL) receives the kind of every term, in term order. */
+tamp_status tamp_problem_info(const tamp_scene *scene, int problem_id, int *D, int *n_terms,
+                              int *term_kinds);
+
+/* Initialise a batch of n_particles (InitializeParticles, Alg. 1).  sampler 0:
+ * uniform within bounds (the paper's "Optimization" initialisation, Sec. VIII):
+ * component c of particle i takes u = (w >> 8) * 2^-24 where w is the first
+ * output word of Philox4x32-10 (Salmon et al., SC'11) with counter (i, c, 0, 0)
+ * and key (seed & 0xffffffff, seed >> 32); joints map u onto [q_lo, q_hi],
+ * grasp positions onto [-h_x, h_x] x [-h_y, h_y] x [h_z - 0.02, h_z], yaws onto
+ * [-pi, pi), a placement's (x, y) onto the surface rectangle in the surface
+ * frame.  Adam state and the iteration counter are reset. */
+tamp_status tamp_sample_particles(tamp_scene *scene, int problem_id, int n_particles,
+                                  uint64_t seed, int sampler);
+
+/* Load a batch [D][n_particles] (host or device pointer, is_device says which)
+ * with optional Adam moments m, v (NULL = zeros) and step count t0. */
+tamp_status tamp_set_particles(tamp_scene *scene, int problem_id, int n_particles,
+                               const float *x, const float *m, const float *v, int t0,
+                               int is_device);
+
+/* Read back the batch state [D][n_particles] to host or device memory (any
+ * pointer may be NULL); *t receives the Adam step count.  Synchronises. */
+tamp_status tamp_get_particles(tamp_scene *scene, int problem_id, float *x, float *m, float *v,
+                               int *t, int is_device);
+
+/* OptimizeParticles (Alg. 1; Sec. V-B): n_steps Adam updates of each listed
+ * problem's batch.  At x_t before every update, and once more after the last
+ * update, every particle is checked against Eq. 3; the first check index with a
+ * satisfying particle is recorded per problem.  Asynchronous on the stream. */
+tamp_status tamp_optimize_steps(tamp_scene *scene, const int *problem_ids, int n_problems,
+                                int n_steps);
+
+/* Results of the last check of a problem (IsGoalSatisfied, Alg. 1; Eq. 3; the
+ * Eq. 5 per-constraint satisfied counts, in constraint order = term order with
+ * the OBJ_DIST term left out).  Host pointers, each may be NULL: mask[P],
+ * particles[D][P], cost[P] (Eq. 2 value), counts[n_constraints]; *first_iter is
+ * -1 if no check has found a satisfying particle.  Synchronises. */
+tamp_status tamp_query_satisfied(tamp_scene *scene, int problem_id, uint8_t *mask,
+                                 int *n_satisfied, int *first_iter, float *particles,
+                                 float *cost, int *counts);
+
+/* Evaluate a caller batch on the device without touching the problem's state:
+ * x_dev [D][n] (stride n), outputs (device, each may be NULL) cost[n] (Eq. 2),
+ * terms[n_terms][n] (unweighted J_c), flags[n] (Eq. 3) and grad[D][n]
+ * (dJ/dx of Eq. 2 for each particle, not divided by n). */
+tamp_status tamp_eval(tamp_scene *scene, int problem_id, int n, const float *x_dev,
+                      float *cost_dev, float *terms_dev, uint8_t *flags_dev, float *grad_dev);
+
+/* Text of the last error on this scene ("" if none); valid until the next call. */
+const char *tamp_last_error(const tamp_scene *scene);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TAMP_H */

@@ -1,0 +1,732 @@
+// C ABI of libtamp.so: scene and skeleton compilation on the host, device
+// buffers, and the launches of the sampler and the fused optimisation kernel.
+// The declarations, argument meanings and error behaviour are in include/tamp.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tamp.h"
+#include "tamp_dev.cuh"
+
+namespace tamp {
+cudaError_t launch_optimize(const OptArgs& a, int L, int K, size_t smem, cudaStream_t st);
+cudaError_t launch_sample(const uint32_t* pb, const uint32_t* sc, float* x, float* m, float* v, int stride, int P,
+                          int D, uint64_t seed, cudaStream_t st);
+size_t optimize_smem_bytes(int scene_words, int prob_words, int D, int NT, int L);
+}  // namespace tamp
+
+using namespace tamp;
+
+namespace {
+
+struct Problem {
+  int D = 0, K = 0, NT = 0, NCON = 0;
+  std::vector<uint32_t> blob;
+  uint32_t* d_blob = nullptr;
+  std::vector<int> term_kinds;
+  tamp_options opt{};
+  // batch state
+  int P = 0, cap = 0, t = 0;
+  float *d_x = nullptr, *d_m = nullptr, *d_v = nullptr, *d_cost = nullptr;
+  uint8_t* d_flags = nullptr;
+  int* d_counts = nullptr;
+  int* d_first = nullptr;
+  bool has_batch = false, checked = false;
+};
+
+}  // namespace
+
+struct tamp_scene {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int nj = 0, S = 0, B = 0, NBS = 0, O = 0, NS = 0;
+  std::vector<double> box_half, box_init, surf;
+  std::vector<uint32_t> blob;
+  uint32_t* d_blob = nullptr;
+  int* d_err = nullptr;
+  int* d_scratch_first = nullptr;
+  std::vector<Problem*> probs;
+  std::string err;
+};
+
+namespace {
+
+tamp_status fail(tamp_scene* s, tamp_status st, const char* fmt, ...) {
+  if (s) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    s->err = buf;
+  }
+  return st;
+}
+
+#define CUDA_TRY(s, call)                                                                 \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail((s), e_ == cudaErrorMemoryAllocation ? TAMP_ERR_OOM : TAMP_ERR_CUDA,    \
+                  "%s: %s", #call, cudaGetErrorString(e_));                               \
+  } while (0)
+
+inline uint32_t fbits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return u;
+}
+inline void align4(std::vector<uint32_t>& v) {
+  while (v.size() % 4) v.push_back(0);
+}
+inline void push_f(std::vector<uint32_t>& v, double x) { v.push_back(fbits(static_cast<float>(x))); }
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool finite_all(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+// Pack the scene blob (layout in tamp_dev.cuh).
+tamp_status build_scene_blob(tamp_scene* s, const tamp_scene_desc* d) {
+  const int nj = d->n_joints;
+  std::vector<uint32_t>& v = s->blob;
+  v.assign(SH_HDR_WORDS, 0);
+  // arm
+  v[SH_OFF_ARM] = static_cast<uint32_t>(v.size());
+  auto push_frame = [&](const double* T) {
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) push_f(v, T[4 * i + j]);
+    for (int i = 0; i < 3; ++i) push_f(v, T[4 * i + 3]);
+  };
+  push_frame(d->base);
+  push_frame(d->tool);
+  for (int j = 0; j < nj; ++j) {
+    push_f(v, d->dh_a[j]);
+    push_f(v, d->dh_d[j]);
+    push_f(v, std::cos(d->dh_alpha[j]));
+    push_f(v, std::sin(d->dh_alpha[j]));
+    push_f(v, d->dh_offset[j]);
+    push_f(v, d->q_lo[j]);
+    push_f(v, d->q_hi[j]);
+    v.push_back(0);
+  }
+  align4(v);
+  // spheres grouped by link, each group padded to a multiple of SB with far, zero-radius slots
+  v[SH_OFF_SPH] = static_cast<uint32_t>(v.size());
+  int slot = 0;
+  for (int l = 0; l <= nj; ++l) {
+    v[SH_LINK0 + l] = static_cast<uint32_t>(slot);
+    int cnt = 0;
+    for (int i = 0; i < d->n_spheres; ++i)
+      if (d->sphere_link[i] == l) {
+        for (int c = 0; c < 4; ++c) push_f(v, d->sphere_xyzr[4 * i + c]);
+        ++cnt;
+      }
+    while (cnt % SB) {
+      push_f(v, DUMMY_FAR); push_f(v, DUMMY_FAR); push_f(v, DUMMY_FAR); push_f(v, 0.0);
+      ++cnt;
+    }
+    slot += cnt;
+  }
+  for (int l = nj + 1; l <= MAXJ + 1; ++l) v[SH_LINK0 + l] = static_cast<uint32_t>(slot);
+  if (slot > MAX_SPH) return fail(s, TAMP_ERR_INVALID_ARG, "too many arm spheres after padding (%d > %d)", slot, MAX_SPH);
+  v[SH_NSPH] = static_cast<uint32_t>(slot);
+  align4(v);
+  // obstacles, structure of arrays
+  const int O = d->n_obs, Opad = std::max(4, (O + 3) & ~3);
+  v[SH_OFF_OBS] = static_cast<uint32_t>(v.size());
+  std::vector<float> rows(static_cast<size_t>(OBS_ROWS) * Opad, 0.f);
+  for (int o = 0; o < O; ++o) {
+    const double* Rm = d->obs_rot + 9 * o;
+    const double* c = d->obs_center + 3 * o;
+    for (int j = 0; j < 3; ++j)  // t' = R^T t
+      rows[j * Opad + o] = static_cast<float>(Rm[0 + j] * c[0] + Rm[3 + j] * c[1] + Rm[6 + j] * c[2]);
+    for (int k = 0; k < 9; ++k) rows[(3 + k) * Opad + o] = static_cast<float>(Rm[k]);
+    for (int j = 0; j < 3; ++j) rows[(12 + j) * Opad + o] = static_cast<float>(d->obs_half[3 * o + j]);
+  }
+  for (float f : rows) v.push_back(fbits(f));
+  v[SH_O] = static_cast<uint32_t>(O);
+  v[SH_OPAD] = static_cast<uint32_t>(Opad);
+  align4(v);
+  // boxes
+  const int B = d->n_boxes, NBS = d->spheres_per_box;
+  v[SH_OFF_BOX] = static_cast<uint32_t>(v.size());
+  for (int b = 0; b < B; ++b) {
+    const double* h = d->box_half + 3 * b;
+    const double* p = d->box_init + 4 * b;
+    push_f(v, h[0]); push_f(v, h[1]); push_f(v, h[2]); v.push_back(0);
+    push_f(v, p[0]); push_f(v, p[1]); push_f(v, p[2]); push_f(v, p[3]);
+    push_f(v, std::cos(p[3])); push_f(v, std::sin(p[3])); v.push_back(0); v.push_back(0);
+  }
+  align4(v);
+  v[SH_OFF_BLOC] = static_cast<uint32_t>(v.size());
+  for (int b = 0; b < B; ++b)
+    for (int e = 0; e < NBS; ++e)
+      for (int c = 0; c < 4; ++c) push_f(v, d->box_spheres[(b * NBS + e) * 4 + c]);
+  align4(v);
+  v[SH_OFF_BINIT] = static_cast<uint32_t>(v.size());
+  for (int b = 0; b < B; ++b) {
+    const double* p = d->box_init + 4 * b;
+    const double c = std::cos(p[3]), sn = std::sin(p[3]);
+    for (int e = 0; e < NBS; ++e) {
+      const double* l = d->box_spheres + (b * NBS + e) * 4;
+      push_f(v, p[0] + c * l[0] - sn * l[1]);
+      push_f(v, p[1] + sn * l[0] + c * l[1]);
+      push_f(v, p[2] + l[2]);
+      push_f(v, l[3]);
+    }
+  }
+  align4(v);
+  v[SH_OFF_SURF] = static_cast<uint32_t>(v.size());
+  for (int k = 0; k < d->n_surf; ++k) {
+    const double* f = d->surf + 6 * k;
+    for (int c = 0; c < 6; ++c) push_f(v, f[c]);
+    push_f(v, std::cos(f[2]));
+    push_f(v, std::sin(f[2]));
+  }
+  if (d->n_surf == 0)
+    for (int c = 0; c < SURF_W; ++c) v.push_back(0);
+  align4(v);
+  v[SH_NJ] = static_cast<uint32_t>(nj);
+  v[SH_B] = static_cast<uint32_t>(B);
+  v[SH_NBS] = static_cast<uint32_t>(NBS);
+  v[SH_NSURF] = static_cast<uint32_t>(d->n_surf);
+  v[SH_WORDS] = static_cast<uint32_t>(v.size());
+  return TAMP_OK;
+}
+
+struct PoseSrc {
+  int kind = 0;   // 0 = initial pose, 1 = placement variable, 2 = held
+  int off = -1;
+  int surf = -1;
+};
+
+// Walk the skeleton (Listing 1 preconditions / effects) and pack the problem blob.
+tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const tamp_options& opt, Problem& pr) {
+  const int nj = s->nj, B = s->B;
+  std::vector<PoseSrc> pose(B);
+  int held = -1, held_g = -1;
+  int off = 0;
+  struct Cfg {
+    int kind, box, qo, go, tsrc, surf;
+    std::vector<std::pair<int, PoseSrc>> env;
+    int t_kp, t_kr, t_x, t_cf, t_cp, t_jl;
+    float tx, ty, tz, tyaw, pz;
+  };
+  std::vector<Cfg> cfgs;
+  struct Term { int kind; };
+  std::vector<Term> terms;
+  std::vector<int> comp_kind;  // 0 q, 1 grasp pos, 2 grasp yaw, 3 place pos, 4 place yaw
+  struct Samp { int kind; float a, b; int surf; };
+  std::vector<Samp> samp;
+  int goal_t = -1;
+  std::vector<std::pair<int, PoseSrc>> goal;
+  auto add_term = [&](int kind) {
+    terms.push_back({kind});
+    return static_cast<int>(terms.size()) - 1;
+  };
+  for (int ai = 0; ai < n; ++ai) {
+    const int kind = acts[ai].kind, b = acts[ai].box, sf = acts[ai].surface;
+    if (kind == TAMP_PICK || kind == TAMP_PLACE) {
+      if (b < 0 || b >= B) return fail(s, TAMP_ERR_INVALID_ARG, "action %d: box %d out of range", ai, b);
+    }
+    if (kind == TAMP_PICK) {
+      if (held >= 0) return fail(s, TAMP_ERR_INVALID_ARG, "action %d: Pick while holding box %d", ai, held);
+      Cfg c{};
+      c.kind = 0; c.box = b; c.go = off;
+      const double* h = &s->box_half[3 * b];
+      samp.push_back({SK_LINEAR, static_cast<float>(-h[0]), static_cast<float>(h[0]), 0});
+      samp.push_back({SK_LINEAR, static_cast<float>(-h[1]), static_cast<float>(h[1]), 0});
+      samp.push_back({SK_LINEAR, static_cast<float>(h[2] - 0.02), static_cast<float>(h[2]), 0});
+      samp.push_back({SK_LINEAR, static_cast<float>(-M_PI), static_cast<float>(M_PI), 0});
+      comp_kind.insert(comp_kind.end(), {1, 1, 1, 2});
+      off += 4;
+      c.qo = off;
+      off += nj;
+      for (int j = 0; j < B; ++j)
+        if (j != b) c.env.push_back({j, pose[j]});
+      if (pose[b].kind == 1) {
+        c.tsrc = pose[b].off;
+        c.tz = static_cast<float>(s->surf[6 * pose[b].surf + 5] + s->box_half[3 * b + 2]);
+      } else {
+        c.tsrc = -1;
+        const double* p = &s->box_init[4 * b];
+        c.tx = static_cast<float>(p[0]); c.ty = static_cast<float>(p[1]);
+        c.tz = static_cast<float>(p[2]); c.tyaw = static_cast<float>(p[3]);
+      }
+      c.surf = -1;
+      c.t_kp = add_term(TK_KIN_POS); c.t_kr = add_term(TK_KIN_ROT); c.t_x = add_term(TK_GRASP);
+      c.t_cf = add_term(TK_CFREE_HOLD); c.t_cp = -1; c.t_jl = add_term(TK_JOINT_LIMIT);
+      cfgs.push_back(c);
+      held = b; held_g = c.go;
+      pose[b].kind = 2;
+    } else if (kind == TAMP_PLACE) {
+      if (held != b) return fail(s, TAMP_ERR_INVALID_ARG, "action %d: Place of box %d that is not held", ai, b);
+      if (sf < 0 || sf >= s->NS) return fail(s, TAMP_ERR_INVALID_ARG, "action %d: surface %d out of range", ai, sf);
+      Cfg c{};
+      c.kind = 1; c.box = b; c.go = held_g; c.surf = sf;
+      const int po = off;
+      samp.push_back({SK_PLACE_X, 0.f, 0.f, sf});
+      samp.push_back({SK_PLACE_Y, 0.f, 0.f, sf});
+      samp.push_back({SK_LINEAR, static_cast<float>(-M_PI), static_cast<float>(M_PI), 0});
+      comp_kind.insert(comp_kind.end(), {3, 3, 4});
+      off += 3;
+      c.qo = off;
+      off += nj;
+      for (int j = 0; j < B; ++j)
+        if (j != b) c.env.push_back({j, pose[j]});
+      c.tsrc = po;
+      c.tz = static_cast<float>(s->surf[6 * sf + 5] + s->box_half[3 * b + 2]);
+      c.pz = c.tz;
+      c.t_kp = add_term(TK_KIN_POS); c.t_kr = add_term(TK_KIN_ROT); c.t_x = add_term(TK_STABLE);
+      c.t_cf = add_term(TK_CFREE_HOLD); c.t_cp = add_term(TK_CFREE_PLACE); c.t_jl = add_term(TK_JOINT_LIMIT);
+      cfgs.push_back(c);
+      pose[b].kind = 1; pose[b].off = po; pose[b].surf = sf;
+      held = -1; held_g = -1;
+    } else if (kind == TAMP_GOAL_MIN_OBJ_DIST) {
+      goal.clear();
+      for (int j = 0; j < B; ++j)
+        if (pose[j].kind == 1) goal.push_back({j, pose[j]});
+      goal_t = add_term(TK_OBJ_DIST);
+    } else {
+      return fail(s, TAMP_ERR_INVALID_ARG, "action %d: unknown kind %d", ai, kind);
+    }
+    // q of the new configuration is sampled uniformly within the joint limits
+    if (kind == TAMP_PICK || kind == TAMP_PLACE) {
+      for (int j = 0; j < nj; ++j) {
+        samp.push_back({SK_LINEAR, 0.f, 0.f, 0});
+        comp_kind.push_back(0);
+      }
+    }
+  }
+  if (cfgs.empty()) return fail(s, TAMP_ERR_INVALID_ARG, "skeleton has no Pick/Place action");
+  if (static_cast<int>(cfgs.size()) > MAX_CFG) return fail(s, TAMP_ERR_INVALID_ARG, "too many configurations");
+  if (off > MAX_D) return fail(s, TAMP_ERR_INVALID_ARG, "particle dimension %d exceeds %d", off, MAX_D);
+  pr.D = off;
+  pr.K = static_cast<int>(cfgs.size());
+  pr.NT = static_cast<int>(terms.size());
+  // pack
+  std::vector<uint32_t>& v = pr.blob;
+  v.assign(PH_HDR_WORDS, 0);
+  v[PH_OFF_CFG] = static_cast<uint32_t>(v.size());
+  int env_count = 0;
+  for (const Cfg& c : cfgs) {
+    uint32_t rec[CFG_W] = {0};
+    rec[CF_KIND] = c.kind; rec[CF_BOX] = c.box; rec[CF_QOFF] = c.qo; rec[CF_GOFF] = c.go;
+    rec[CF_TSRC] = static_cast<uint32_t>(c.tsrc); rec[CF_SURF] = static_cast<uint32_t>(c.surf);
+    rec[CF_NENV] = static_cast<uint32_t>(c.env.size()); rec[CF_ENVOFF] = static_cast<uint32_t>(env_count);
+    rec[CF_T_KP] = c.t_kp; rec[CF_T_KR] = c.t_kr; rec[CF_T_X] = c.t_x; rec[CF_T_CF] = c.t_cf;
+    rec[CF_T_CP] = static_cast<uint32_t>(c.t_cp); rec[CF_T_JL] = c.t_jl;
+    rec[CF_PSRC] = static_cast<uint32_t>(c.tsrc);
+    rec[CF_TX] = fbits(c.tx); rec[CF_TY] = fbits(c.ty); rec[CF_TZ] = fbits(c.tz); rec[CF_TYAW] = fbits(c.tyaw);
+    rec[CF_PZ] = fbits(c.pz);
+    v.insert(v.end(), rec, rec + CFG_W);
+    env_count += static_cast<int>(c.env.size());
+  }
+  align4(v);
+  v[PH_OFF_ENV] = static_cast<uint32_t>(v.size());
+  for (const Cfg& c : cfgs)
+    for (const auto& e : c.env) {
+      const PoseSrc& ps = e.second;
+      v.push_back(static_cast<uint32_t>(e.first));
+      if (ps.kind == 1) {
+        v.push_back(static_cast<uint32_t>(ps.off));
+        v.push_back(fbits(static_cast<float>(s->surf[6 * ps.surf + 5] + s->box_half[3 * e.first + 2])));
+      } else {
+        v.push_back(static_cast<uint32_t>(-1));
+        v.push_back(0);
+      }
+      v.push_back(0);
+    }
+  if (env_count == 0)
+    for (int i = 0; i < ENV_W; ++i) v.push_back(0);
+  align4(v);
+  v[PH_OFF_TERMS] = static_cast<uint32_t>(v.size());
+  int ncon = 0;
+  pr.term_kinds.clear();
+  for (const Term& t : terms) {
+    v.push_back(static_cast<uint32_t>(t.kind));
+    v.push_back(fbits(opt.w[t.kind]));
+    v.push_back(fbits(opt.tol[t.kind]));
+    v.push_back(t.kind == TK_OBJ_DIST ? static_cast<uint32_t>(-1) : static_cast<uint32_t>(ncon++));
+    pr.term_kinds.push_back(t.kind);
+  }
+  pr.NCON = ncon;
+  align4(v);
+  v[PH_OFF_GOAL] = static_cast<uint32_t>(v.size());
+  for (const auto& g : goal) {
+    v.push_back(static_cast<uint32_t>(g.first));
+    v.push_back(static_cast<uint32_t>(g.second.off));
+    v.push_back(fbits(static_cast<float>(s->surf[6 * g.second.surf + 5] + s->box_half[3 * g.first + 2])));
+    v.push_back(0);
+  }
+  if (goal.empty())
+    for (int i = 0; i < GOAL_W; ++i) v.push_back(0);
+  align4(v);
+  v[PH_OFF_LR] = static_cast<uint32_t>(v.size());
+  for (int ck : comp_kind) {
+    float lr = 0.f;
+    switch (ck) {
+      case 0: lr = opt.lr_joint; break;
+      case 1: lr = opt.optimize_grasp ? opt.lr_pos : 0.f; break;
+      case 2: lr = opt.optimize_grasp ? opt.lr_yaw : 0.f; break;
+      case 3: lr = opt.lr_pos; break;
+      case 4: lr = opt.lr_yaw; break;
+    }
+    v.push_back(fbits(lr));
+  }
+  align4(v);
+  v[PH_OFF_SAMP] = static_cast<uint32_t>(v.size());
+  for (const Cfg& c : cfgs)
+    for (int j = 0; j < nj; ++j) {
+      // q ~ U[q_lo, q_hi]: bounds from the scene blob's joint records
+      const float* jr = reinterpret_cast<const float*>(&s->blob[s->blob[SH_OFF_ARM] + 24 + j * ARM_JW]);
+      samp[c.qo + j] = {SK_LINEAR, jr[5], jr[6], 0};
+    }
+  for (const Samp& sp : samp) {
+    v.push_back(static_cast<uint32_t>(sp.kind));
+    v.push_back(fbits(sp.a));
+    v.push_back(fbits(sp.b));
+    v.push_back(static_cast<uint32_t>(sp.surf));
+  }
+  align4(v);
+  v[PH_D] = pr.D; v[PH_K] = pr.K; v[PH_NT] = pr.NT; v[PH_NCON] = pr.NCON;
+  v[PH_GOAL_T] = static_cast<uint32_t>(goal_t); v[PH_NGOAL] = static_cast<uint32_t>(goal.size());
+  v[PH_WORDS] = static_cast<uint32_t>(v.size());
+  return TAMP_OK;
+}
+
+// dynamic shared memory of one CTA, below the 227 KB opt-in limit with room for
+// the kernel's static shared variables
+constexpr size_t kMaxDynSmem = 227 * 1024 - 256;
+
+int pick_lanes(const Problem& pr, int P) {
+  if (pr.opt.lanes == 1 || pr.opt.lanes == 2 || pr.opt.lanes == 4 || pr.opt.lanes == 8) return pr.opt.lanes;
+  // enough (particle, configuration) warps to fill 148 SMs several times over -> 1 lane each
+  const long units = static_cast<long>(P) * pr.K;
+  if (units >= 148L * 32 * 16) return 1;
+  if (units >= 148L * 32 * 4) return 2;
+  return 4;
+}
+
+void free_batch(Problem& pr) {
+  cudaFree(pr.d_x); cudaFree(pr.d_m); cudaFree(pr.d_v); cudaFree(pr.d_cost);
+  cudaFree(pr.d_flags); cudaFree(pr.d_counts); cudaFree(pr.d_first);
+  pr.d_x = pr.d_m = pr.d_v = pr.d_cost = nullptr;
+  pr.d_flags = nullptr; pr.d_counts = nullptr; pr.d_first = nullptr;
+  pr.cap = 0;
+}
+
+tamp_status ensure_batch(tamp_scene* s, Problem& pr, int P) {
+  if (P > pr.cap) {
+    free_batch(pr);
+    const size_t n = static_cast<size_t>(pr.D) * P;
+    CUDA_TRY(s, cudaMalloc(&pr.d_x, n * 4));
+    CUDA_TRY(s, cudaMalloc(&pr.d_m, n * 4));
+    CUDA_TRY(s, cudaMalloc(&pr.d_v, n * 4));
+    CUDA_TRY(s, cudaMalloc(&pr.d_cost, static_cast<size_t>(P) * 4));
+    CUDA_TRY(s, cudaMalloc(&pr.d_flags, static_cast<size_t>(P)));
+    CUDA_TRY(s, cudaMalloc(&pr.d_counts, static_cast<size_t>(std::max(pr.NCON, 1)) * 4));
+    CUDA_TRY(s, cudaMalloc(&pr.d_first, 4));
+    pr.cap = P;
+  }
+  pr.P = P;
+  const int big = INT_MAX;
+  CUDA_TRY(s, cudaMemcpyAsync(pr.d_first, &big, 4, cudaMemcpyHostToDevice, s->stream));
+  pr.t = 0;
+  pr.has_batch = true;
+  pr.checked = false;
+  return TAMP_OK;
+}
+
+OptArgs base_args(tamp_scene* s, Problem& pr) {
+  OptArgs a{};
+  a.scene = s->d_blob; a.scene_words = static_cast<int>(s->blob.size());
+  a.prob = pr.d_blob; a.prob_words = static_cast<int>(pr.blob.size());
+  a.gscale = 1.f;
+  a.beta1 = pr.opt.beta1; a.beta2 = pr.opt.beta2; a.eps = pr.opt.eps;
+  a.err = s->d_err;
+  return a;
+}
+
+tamp_status run_state(tamp_scene* s, Problem& pr, int n_steps) {
+  OptArgs a = base_args(s, pr);
+  a.x_in = pr.d_x; a.x_out = pr.d_x; a.m = pr.d_m; a.v = pr.d_v; a.load_mv = 1;
+  a.stride = pr.P; a.P = pr.P;
+  a.out_cost = pr.d_cost; a.out_flags = pr.d_flags; a.out_counts = pr.d_counts;
+  a.first_iter = pr.d_first;
+  a.n_steps = n_steps; a.t0 = pr.t;
+  a.gscale = pr.opt.scale_by_batch ? 1.f / static_cast<float>(pr.P) : 1.f;
+  const int L = pick_lanes(pr, pr.P);
+  CUDA_TRY(s, cudaMemsetAsync(pr.d_counts, 0, static_cast<size_t>(std::max(pr.NCON, 1)) * 4, s->stream));
+  const size_t smem = optimize_smem_bytes(a.scene_words, a.prob_words, pr.D, pr.NT, L);
+  if (smem > kMaxDynSmem) return fail(s, TAMP_ERR_INVALID_ARG, "problem needs %zu B of shared memory", smem);
+  CUDA_TRY(s, launch_optimize(a, L, pr.K, smem, s->stream));
+  pr.t += n_steps;
+  pr.checked = true;
+  return TAMP_OK;
+}
+
+Problem* get_problem(tamp_scene* s, int id) {
+  if (!s || id < 0 || id >= static_cast<int>(s->probs.size())) return nullptr;
+  return s->probs[id];
+}
+
+tamp_status check_device_error(tamp_scene* s) {
+  int e = 0;
+  CUDA_TRY(s, cudaMemcpyAsync(&e, s->d_err, 4, cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+  if (e & ERR_TMA_TIMEOUT) return fail(s, TAMP_ERR_TIMEOUT, "a shared-memory staging wait timed out on the device");
+  if (e) return fail(s, TAMP_ERR_DEVICE_CHECK, "device check word 0x%x", e);
+  return TAMP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void tamp_default_options(tamp_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  const float w[TAMP_N_TERM_KINDS] = {1.f, 5.f, 1.f, 2.f, 1.f, 1.f, 1.f, 0.25f};
+  const float tol[TAMP_N_TERM_KINDS] = {5e-3f, 0.05f, 1e-3f, 1e-3f, 1e-3f, 1e-3f, 0.f, INFINITY};
+  for (int i = 0; i < TAMP_N_TERM_KINDS; ++i) {
+    o->w[i] = w[i];
+    o->tol[i] = tol[i];
+  }
+  o->lr_joint = 1e-2f; o->lr_pos = 3e-3f; o->lr_yaw = 1e-2f;
+  o->beta1 = 0.9f; o->beta2 = 0.999f; o->eps = 1e-8f;
+  o->optimize_grasp = 1; o->scale_by_batch = 1; o->lanes = 0;
+}
+
+tamp_status tamp_create_scene(const tamp_scene_desc* d, int device, void* stream, tamp_scene** out) {
+  if (!d || !out) return TAMP_ERR_INVALID_ARG;
+  *out = nullptr;
+  tamp_scene* s = new tamp_scene();
+  auto bad = [&](const char*) {
+    delete s;
+    return TAMP_ERR_INVALID_ARG;
+  };
+  if (d->n_joints < 1 || d->n_joints > MAXJ) return bad("n_joints");
+  if (!d->dh_a || !d->dh_d || !d->dh_alpha || !d->dh_offset || !d->q_lo || !d->q_hi) return bad("arm arrays");
+  if (d->n_spheres < 0 || (d->n_spheres > 0 && (!d->sphere_link || !d->sphere_xyzr))) return bad("spheres");
+  for (int i = 0; i < d->n_spheres; ++i)
+    if (d->sphere_link[i] < 0 || d->sphere_link[i] > d->n_joints || d->sphere_xyzr[4 * i + 3] < 0) return bad("sphere");
+  if (d->n_boxes < 0 || d->n_boxes > MAX_BOX) return bad("n_boxes");
+  if (d->n_boxes > 0 && (!d->box_half || !d->box_init || !d->box_spheres)) return bad("box arrays");
+  if (d->spheres_per_box < 1 || d->spheres_per_box > MAX_NBS) return bad("spheres_per_box");
+  if (d->n_obs < 0 || d->n_obs > MAX_OBS) return bad("n_obs");
+  if (d->n_obs > 0 && (!d->obs_center || !d->obs_rot || !d->obs_half)) return bad("obstacle arrays");
+  if (d->n_surf < 0 || (d->n_surf > 0 && !d->surf)) return bad("surfaces");
+  if (!finite_all(d->dh_a, d->n_joints) || !finite_all(d->dh_d, d->n_joints) || !finite_all(d->base, 16) ||
+      !finite_all(d->tool, 16))
+    return bad("non-finite arm");
+  s->device = device;
+  s->stream = static_cast<cudaStream_t>(stream);
+  s->nj = d->n_joints; s->S = d->n_spheres; s->B = d->n_boxes; s->NBS = d->spheres_per_box;
+  s->O = d->n_obs; s->NS = d->n_surf;
+  s->box_half.assign(d->box_half, d->box_half + 3 * d->n_boxes);
+  s->box_init.assign(d->box_init, d->box_init + 4 * d->n_boxes);
+  if (d->n_surf) s->surf.assign(d->surf, d->surf + 6 * d->n_surf);
+  tamp_status st = build_scene_blob(s, d);
+  if (st != TAMP_OK) {
+    delete s;
+    return st;
+  }
+  DeviceGuard g(device);
+  cudaError_t e = cudaMalloc(&s->d_blob, s->blob.size() * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_err, 4);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_scratch_first, 4);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_blob, s->blob.data(), s->blob.size() * 4, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, 4, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    cudaFree(s->d_blob); cudaFree(s->d_err); cudaFree(s->d_scratch_first);
+    delete s;
+    return e == cudaErrorMemoryAllocation ? TAMP_ERR_OOM : TAMP_ERR_CUDA;
+  }
+  *out = s;
+  return TAMP_OK;
+}
+
+tamp_status tamp_destroy_scene(tamp_scene* s) {
+  if (!s) return TAMP_ERR_INVALID_ARG;
+  DeviceGuard g(s->device);
+  cudaStreamSynchronize(s->stream);
+  for (Problem* p : s->probs) {
+    free_batch(*p);
+    cudaFree(p->d_blob);
+    delete p;
+  }
+  cudaFree(s->d_blob); cudaFree(s->d_err); cudaFree(s->d_scratch_first);
+  delete s;
+  return TAMP_OK;
+}
+
+tamp_status tamp_set_skeleton(tamp_scene* s, const tamp_action* acts, int n, const tamp_options* opt, int* pid) {
+  if (!s) return TAMP_ERR_INVALID_ARG;
+  if (!acts || n <= 0 || !pid) return fail(s, TAMP_ERR_INVALID_ARG, "empty skeleton or null output");
+  Problem* pr = new Problem();
+  if (opt) pr->opt = *opt; else tamp_default_options(&pr->opt);
+  tamp_status st = compile_problem(s, acts, n, pr->opt, *pr);
+  if (st != TAMP_OK) {
+    delete pr;
+    return st;
+  }
+  DeviceGuard g(s->device);
+  cudaError_t e = cudaMalloc(&pr->d_blob, pr->blob.size() * 4);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pr->d_blob, pr->blob.data(), pr->blob.size() * 4, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    cudaFree(pr->d_blob);
+    delete pr;
+    return fail(s, TAMP_ERR_CUDA, "skeleton upload: %s", cudaGetErrorString(e));
+  }
+  s->probs.push_back(pr);
+  *pid = static_cast<int>(s->probs.size()) - 1;
+  s->err.clear();
+  return TAMP_OK;
+}
+
+tamp_status tamp_problem_info(const tamp_scene* sc, int id, int* D, int* n_terms, int* kinds) {
+  tamp_scene* s = const_cast<tamp_scene*>(sc);
+  Problem* pr = get_problem(s, id);
+  if (!pr) return fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", id);
+  if (D) *D = pr->D;
+  if (n_terms) *n_terms = pr->NT;
+  if (kinds) std::copy(pr->term_kinds.begin(), pr->term_kinds.end(), kinds);
+  return TAMP_OK;
+}
+
+tamp_status tamp_sample_particles(tamp_scene* s, int id, int P, uint64_t seed, int sampler) {
+  Problem* pr = get_problem(s, id);
+  if (!pr) return fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", id);
+  if (P <= 0 || P > (1 << 24)) return fail(s, TAMP_ERR_INVALID_ARG, "n_particles %d out of range", P);
+  if (sampler != 0) return fail(s, TAMP_ERR_INVALID_ARG, "sampler %d not available", sampler);
+  DeviceGuard g(s->device);
+  tamp_status st = ensure_batch(s, *pr, P);
+  if (st != TAMP_OK) return st;
+  CUDA_TRY(s, launch_sample(pr->d_blob, s->d_blob, pr->d_x, pr->d_m, pr->d_v, P, P, pr->D, seed, s->stream));
+  return TAMP_OK;
+}
+
+tamp_status tamp_set_particles(tamp_scene* s, int id, int P, const float* x, const float* m, const float* v, int t0,
+                               int is_device) {
+  Problem* pr = get_problem(s, id);
+  if (!pr) return fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", id);
+  if (P <= 0 || P > (1 << 24) || !x || t0 < 0) return fail(s, TAMP_ERR_INVALID_ARG, "bad batch arguments");
+  DeviceGuard g(s->device);
+  tamp_status st = ensure_batch(s, *pr, P);
+  if (st != TAMP_OK) return st;
+  const size_t n = static_cast<size_t>(pr->D) * P * 4;
+  const cudaMemcpyKind kd = is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CUDA_TRY(s, cudaMemcpyAsync(pr->d_x, x, n, kd, s->stream));
+  if (m) CUDA_TRY(s, cudaMemcpyAsync(pr->d_m, m, n, kd, s->stream));
+  else CUDA_TRY(s, cudaMemsetAsync(pr->d_m, 0, n, s->stream));
+  if (v) CUDA_TRY(s, cudaMemcpyAsync(pr->d_v, v, n, kd, s->stream));
+  else CUDA_TRY(s, cudaMemsetAsync(pr->d_v, 0, n, s->stream));
+  pr->t = t0;
+  if (!is_device) CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+  return TAMP_OK;
+}
+
+tamp_status tamp_get_particles(tamp_scene* s, int id, float* x, float* m, float* v, int* t, int is_device) {
+  Problem* pr = get_problem(s, id);
+  if (!pr) return fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", id);
+  if (!pr->has_batch) return fail(s, TAMP_ERR_STATE, "problem %d has no particles", id);
+  DeviceGuard g(s->device);
+  const size_t n = static_cast<size_t>(pr->D) * pr->P * 4;
+  const cudaMemcpyKind kd = is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (x) CUDA_TRY(s, cudaMemcpyAsync(x, pr->d_x, n, kd, s->stream));
+  if (m) CUDA_TRY(s, cudaMemcpyAsync(m, pr->d_m, n, kd, s->stream));
+  if (v) CUDA_TRY(s, cudaMemcpyAsync(v, pr->d_v, n, kd, s->stream));
+  if (t) *t = pr->t;
+  return check_device_error(s);
+}
+
+tamp_status tamp_optimize_steps(tamp_scene* s, const int* ids, int n, int n_steps) {
+  if (!s) return TAMP_ERR_INVALID_ARG;
+  if (!ids || n <= 0 || n_steps < 0) return fail(s, TAMP_ERR_INVALID_ARG, "bad optimize arguments");
+  DeviceGuard g(s->device);
+  for (int i = 0; i < n; ++i) {
+    Problem* pr = get_problem(s, ids[i]);
+    if (!pr) return fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", ids[i]);
+    if (!pr->has_batch) return fail(s, TAMP_ERR_STATE, "problem %d has no particles", ids[i]);
+  }
+  for (int i = 0; i < n; ++i) {
+    tamp_status st = run_state(s, *s->probs[ids[i]], n_steps);
+    if (st != TAMP_OK) return st;
+  }
+  return TAMP_OK;
+}
+
+tamp_status tamp_query_satisfied(tamp_scene* s, int id, uint8_t* mask, int* n_sat, int* first_iter, float* particles,
+                                 float* cost, int* counts) {
+  Problem* pr = get_problem(s, id);
+  if (!pr) return fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", id);
+  if (!pr->has_batch) return fail(s, TAMP_ERR_STATE, "problem %d has no particles", id);
+  DeviceGuard g(s->device);
+  if (!pr->checked) {
+    tamp_status st = run_state(s, *pr, 0);
+    if (st != TAMP_OK) return st;
+  }
+  std::vector<uint8_t> fl(pr->P);
+  int first = INT_MAX;
+  CUDA_TRY(s, cudaMemcpyAsync(fl.data(), pr->d_flags, pr->P, cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(s, cudaMemcpyAsync(&first, pr->d_first, 4, cudaMemcpyDeviceToHost, s->stream));
+  if (particles)
+    CUDA_TRY(s, cudaMemcpyAsync(particles, pr->d_x, static_cast<size_t>(pr->D) * pr->P * 4, cudaMemcpyDeviceToHost, s->stream));
+  if (cost) CUDA_TRY(s, cudaMemcpyAsync(cost, pr->d_cost, static_cast<size_t>(pr->P) * 4, cudaMemcpyDeviceToHost, s->stream));
+  if (counts && pr->NCON)
+    CUDA_TRY(s, cudaMemcpyAsync(counts, pr->d_counts, static_cast<size_t>(pr->NCON) * 4, cudaMemcpyDeviceToHost, s->stream));
+  tamp_status st = check_device_error(s);
+  if (st != TAMP_OK) return st;
+  int ns = 0;
+  for (int i = 0; i < pr->P; ++i) ns += fl[i] ? 1 : 0;
+  if (mask) std::copy(fl.begin(), fl.end(), mask);
+  if (n_sat) *n_sat = ns;
+  if (first_iter) *first_iter = first == INT_MAX ? -1 : first;
+  return TAMP_OK;
+}
+
+tamp_status tamp_eval(tamp_scene* s, int id, int n, const float* x, float* cost, float* terms, uint8_t* flags,
+                      float* grad) {
+  Problem* pr = get_problem(s, id);
+  if (!pr) return fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", id);
+  if (n <= 0 || !x) return fail(s, TAMP_ERR_INVALID_ARG, "bad eval arguments");
+  DeviceGuard g(s->device);
+  OptArgs a = base_args(s, *pr);
+  a.x_in = x; a.stride = n; a.P = n;
+  a.out_cost = cost; a.out_terms = terms; a.out_flags = flags; a.out_grad = grad;
+  a.first_iter = nullptr; a.n_steps = 0; a.t0 = 0;
+  const int L = pick_lanes(*pr, n);
+  const size_t smem = optimize_smem_bytes(a.scene_words, a.prob_words, pr->D, pr->NT, L);
+  if (smem > kMaxDynSmem) return fail(s, TAMP_ERR_INVALID_ARG, "problem needs %zu B of shared memory", smem);
+  CUDA_TRY(s, launch_optimize(a, L, pr->K, smem, s->stream));
+  return TAMP_OK;
+}
+
+const char* tamp_last_error(const tamp_scene* s) { return s ? s->err.c_str() : "null scene"; }
+
+}  // extern "C"

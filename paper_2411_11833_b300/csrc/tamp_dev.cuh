@@ -1,0 +1,82 @@
+// Device-side data layout shared by the host compiler (tamp_api.cu) and the
+// kernels (tamp_kernels.cu).  Everything a CTA needs is packed by the host into
+// two word arrays -- the scene blob and the problem blob -- that the kernel
+// stages into shared memory with one TMA bulk copy each.
+#pragma once
+#include <cstdint>
+
+namespace tamp {
+
+constexpr int MAXJ = 8;        // joints per arm
+constexpr int SB = 5;          // arm spheres per register batch (table padded per link)
+constexpr int HB = 4;          // box spheres per register batch
+constexpr int MAX_NBS = 8;     // spheres per box model
+constexpr int MAX_BOX = 32;
+constexpr int MAX_OBS = 256;
+constexpr int MAX_SPH = 512;   // padded arm sphere table
+constexpr int MAX_CFG = 32;    // arm configurations per skeleton
+constexpr int MAX_D = 1024;
+
+// ---- scene blob (32-bit words) ----------------------------------------------
+enum SceneHdr {
+  SH_NJ = 0, SH_NSPH, SH_O, SH_OPAD, SH_B, SH_NBS, SH_NSURF, SH_WORDS,
+  SH_LINK0 = 8,                 // link_start[0..MAXJ+1]: 10 entries (words 8..17)
+  SH_OFF_ARM = 18, SH_OFF_SPH, SH_OFF_OBS, SH_OFF_BOX, SH_OFF_BLOC, SH_OFF_BINIT, SH_OFF_SURF,
+  SH_HDR_WORDS = 32
+};
+// arm section: base frame (12), tool frame (12), then per joint ARM_JW words
+// frame = R row-major (9) + t (3)
+constexpr int ARM_JW = 8;       // a, d, cos(alpha), sin(alpha), offset, q_lo, q_hi, pad
+// sphere table: float4 (x, y, z, r) per padded slot; padding slots sit far away
+// with r = 0 so they never touch anything
+constexpr float DUMMY_FAR = 1.0e4f;
+// obstacles: OBS_ROWS rows of O_pad floats (structure of arrays):
+//   rows 0..2  t' = R^T t       rows 3..11 R row-major      rows 12..14 half
+constexpr int OBS_ROWS = 16;
+// box record: half x,y,z, pad, init x,y,z,yaw, cos(yaw), sin(yaw), pad, pad
+constexpr int BOX_W = 12;
+// surface record: cx, cy, yaw, hx, hy, z_top, cos(yaw), sin(yaw)
+constexpr int SURF_W = 8;
+
+// ---- problem blob ------------------------------------------------------------
+enum ProbHdr {
+  PH_D = 0, PH_K, PH_NT, PH_NCON, PH_GOAL_T, PH_NGOAL, PH_OFF_CFG, PH_OFF_ENV, PH_OFF_TERMS,
+  PH_OFF_GOAL, PH_OFF_LR, PH_OFF_SAMP, PH_WORDS, PH_HDR_WORDS = 16
+};
+constexpr int CFG_W = 24;
+enum CfgField {
+  CF_KIND = 0, CF_BOX, CF_QOFF, CF_GOFF, CF_TSRC, CF_SURF, CF_NENV, CF_ENVOFF,
+  CF_T_KP, CF_T_KR, CF_T_X, CF_T_CF, CF_T_CP, CF_T_JL, CF_PSRC, CF_PAD1,
+  CF_TX, CF_TY, CF_TZ, CF_TYAW,  // floats: target pose if CF_TSRC < 0, else CF_TZ = surface z + h_z
+  CF_PZ,                        // float: z of the placed box (place configurations)
+  CF_PAD2, CF_PAD3, CF_PAD4
+};
+constexpr int ENV_W = 4;        // box, src (-1 = initial pose, else placement offset), z (float), pad
+constexpr int TERM_W = 4;       // kind, weight (float), tol (float), is_constraint
+constexpr int GOAL_W = 4;       // box, src, z (float), pad
+constexpr int SAMP_W = 4;       // per component: kind, a (float), b (float), surface
+enum SampKind { SK_LINEAR = 0, SK_PLACE_X = 1, SK_PLACE_Y = 2 };
+
+enum TermKind {
+  TK_KIN_POS = 0, TK_KIN_ROT, TK_GRASP, TK_STABLE, TK_CFREE_HOLD, TK_CFREE_PLACE, TK_JOINT_LIMIT,
+  TK_OBJ_DIST, TK_N
+};
+
+// device error word bits
+enum ErrBits { ERR_TMA_TIMEOUT = 1, ERR_BAD_BLOB = 2 };
+
+struct OptArgs {
+  const uint32_t* scene; int scene_words;
+  const uint32_t* prob; int prob_words;
+  const float* x_in;            // [D][stride]
+  float* x_out; float* m; float* v;  // state (may be null in eval mode)
+  int stride; int P;
+  float* out_cost; float* out_terms; uint8_t* out_flags; float* out_grad; int* out_counts;
+  int* first_iter; int* err;
+  int n_steps; int t0;
+  float gscale;                 // 1/N_b (Eq. 4) or 1
+  float beta1, beta2, eps;
+  int load_mv;                  // read m, v from memory (else zeros)
+};
+
+}  // namespace tamp

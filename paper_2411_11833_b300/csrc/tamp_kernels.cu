@@ -1,0 +1,864 @@
+// Fused particle-optimisation kernels for sm_103a (B300).
+//
+// One CTA owns a tile of PT = 32 / L particles of one problem for the whole
+// optimisation: the particles' values, Adam moments and gradient live in
+// shared memory, every iteration (cost, hand-written adjoint, Adam, Eq. 3 flags)
+// runs inside the CTA, and HBM is touched only to load the tile and to write it
+// back.  Warp w evaluates arm configuration k = w, w + W, ... of the skeleton
+// for all PT particles; the L lanes of one (particle, configuration) pair split
+// the collision environment (obstacles and environment-box spheres) between
+// them and meet in a shuffle reduction.
+//
+// Per configuration (arXiv 2411.11833, Sec. V-A/V-B and the appendix):
+//   forward kinematics of the serial arm (standard DH) into registers;
+//   Kin: translation / geodesic rotation error between FK(q) and P(p) G(g);
+//   CFreeHold: arm spheres and the held box's spheres (at FK(q) G(g)^-1)
+//     against oriented cuboids (signed distance) and other boxes' spheres;
+//   CFreePlace: the placed box's spheres at P(p) against the same environment;
+//   joint limits, grasp bounds and footprint containment (bound distance);
+// the adjoint is a reverse sweep over the chain: the links' frames are
+// recovered from the tip (T_{l-1} = T_l A_l^-1) instead of being stored, and
+// the per-sphere gradients are folded into a world wrench (F, M) whose
+// projection on joint l's Plucker axis is dJ/dq_l = z.M + (o x z).F.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tamp_dev.cuh"
+
+namespace tamp {
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// 1-D TMA bulk copy global -> shared, completion counted on an mbarrier.
+__device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after `tries` polls (each poll may suspend briefly).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int tries) {
+  for (int i = 0; i < tries; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    __nanosleep(64);
+  }
+  return false;
+}
+
+// ------------------------------------------------------------------ frame helpers
+// A frame is R (row-major 3x3) and t.  Right-multiplications used by DH:
+__device__ __forceinline__ void rz_right(float* R, float c, float s) {  // T <- T Rz(theta)
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float a = R[3 * i], b = R[3 * i + 1];
+    R[3 * i] = fmaf(c, a, s * b);
+    R[3 * i + 1] = fmaf(c, b, -s * a);
+  }
+}
+__device__ __forceinline__ void rx_right(float* R, float c, float s) {  // T <- T Rx(alpha)
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float a = R[3 * i + 1], b = R[3 * i + 2];
+    R[3 * i + 1] = fmaf(c, a, s * b);
+    R[3 * i + 2] = fmaf(c, b, -s * a);
+  }
+}
+
+__device__ __forceinline__ float tw(const uint32_t* terms, int t) { return __uint_as_float(terms[t * TERM_W + 1]); }
+
+// ------------------------------------------------------------------ collision core
+// Penetration of a register batch of NB spheres into the environment of one
+// configuration: the static cuboids and the spheres of every other box at its
+// current pose.  Returns the summed penetration depth (unweighted) and adds
+// d(depth)/d(centre) into (gx, gy, gz).  Gradients towards boxes whose pose is a
+// placement variable are added (times wenv) straight into the tile's gradient.
+// Lane `sub` of the L lanes handles obstacles o = sub (mod L) and box spheres
+// e = sub (mod L).
+template <int L, int NB>
+__device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy)[NB], const float (&cz)[NB],
+                                         const float (&cr)[NB], float (&gx)[NB], float (&gy)[NB],
+                                         float (&gz)[NB], const float* __restrict__ obs, int O, int Opad,
+                                         const int* __restrict__ env, int n_env,
+                                         const float4* __restrict__ bloc, const float4* __restrict__ binit,
+                                         int NBS, const float* __restrict__ X, float* G, int pl, int sub,
+                                         float wenv) {
+  constexpr int PT = 32 / L;
+  float J = 0.f;
+  float r2[NB];
+#pragma unroll
+  for (int s = 0; s < NB; ++s) r2[s] = cr[s] * cr[s];
+
+  // sphere vs oriented cuboid: u = R^T c - R^T t, q = |u| - h,
+  // sdf = ||max(q, 0)|| + min(max_i q_i, 0); active iff ||max(q,0)||^2 < r^2.
+  for (int o = sub; o < O; o += L) {
+    const float tpx = obs[0 * Opad + o], tpy = obs[1 * Opad + o], tpz = obs[2 * Opad + o];
+    const float R00 = obs[3 * Opad + o], R01 = obs[4 * Opad + o], R02 = obs[5 * Opad + o];
+    const float R10 = obs[6 * Opad + o], R11 = obs[7 * Opad + o], R12 = obs[8 * Opad + o];
+    const float R20 = obs[9 * Opad + o], R21 = obs[10 * Opad + o], R22 = obs[11 * Opad + o];
+    const float hx = obs[12 * Opad + o], hy = obs[13 * Opad + o], hz = obs[14 * Opad + o];
+#pragma unroll
+    for (int s = 0; s < NB; ++s) {
+      const float ux = fmaf(R00, cx[s], fmaf(R10, cy[s], fmaf(R20, cz[s], -tpx)));
+      const float uy = fmaf(R01, cx[s], fmaf(R11, cy[s], fmaf(R21, cz[s], -tpy)));
+      const float uz = fmaf(R02, cx[s], fmaf(R12, cy[s], fmaf(R22, cz[s], -tpz)));
+      const float qx = fabsf(ux) - hx, qy = fabsf(uy) - hy, qz = fabsf(uz) - hz;
+      const float mx = fmaxf(qx, 0.f), my = fmaxf(qy, 0.f), mz = fmaxf(qz, 0.f);
+      const float o2 = fmaf(mx, mx, fmaf(my, my, mz * mz));
+      if (o2 < r2[s]) {
+        float dux, duy, duz;
+        float sdf;
+        if (o2 > 0.f) {
+          const float d = sqrtf(o2);
+          const float inv = 1.f / d;
+          sdf = d;
+          dux = copysignf(mx * inv, ux);
+          duy = copysignf(my * inv, uy);
+          duz = copysignf(mz * inv, uz);
+        } else {
+          dux = duy = duz = 0.f;
+          if (qx >= qy && qx >= qz) {
+            sdf = qx;
+            dux = copysignf(1.f, ux);
+          } else if (qy >= qz) {
+            sdf = qy;
+            duy = copysignf(1.f, uy);
+          } else {
+            sdf = qz;
+            duz = copysignf(1.f, uz);
+          }
+        }
+        J += cr[s] - sdf;
+        // d(pen)/dc = -R d(sdf)/du
+        gx[s] -= fmaf(R00, dux, fmaf(R01, duy, R02 * duz));
+        gy[s] -= fmaf(R10, dux, fmaf(R11, duy, R12 * duz));
+        gz[s] -= fmaf(R20, dux, fmaf(R21, duy, R22 * duz));
+      }
+    }
+  }
+
+  // sphere vs sphere of the other boxes: pen = max(0, r_a + r_b - ||c_a - c_b||)
+  for (int ei = 0; ei < n_env; ++ei) {
+    const int j = env[ei * ENV_W], src = env[ei * ENV_W + 1];
+    if (src < 0) {
+      for (int e = sub; e < NBS; e += L) {
+        const float4 c = binit[j * NBS + e];
+#pragma unroll
+        for (int s = 0; s < NB; ++s) {
+          const float dx = cx[s] - c.x, dy = cy[s] - c.y, dz = cz[s] - c.z;
+          const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          const float Rs = cr[s] + c.w;
+          if (d2 < Rs * Rs) {
+            const float d = sqrtf(d2);
+            J += Rs - d;
+            if (d > 0.f) {
+              const float inv = 1.f / d;
+              gx[s] -= dx * inv;
+              gy[s] -= dy * inv;
+              gz[s] -= dz * inv;
+            }
+          }
+        }
+      }
+    } else {
+      const float z = __int_as_float(env[ei * ENV_W + 2]);
+      const float px = X[src * PT + pl], py = X[(src + 1) * PT + pl];
+      float sn, cs;
+      sincosf(X[(src + 2) * PT + pl], &sn, &cs);
+      float fx = 0.f, fy = 0.f, tq = 0.f;
+      for (int e = sub; e < NBS; e += L) {
+        const float4 l = bloc[j * NBS + e];
+        const float rx = fmaf(cs, l.x, -sn * l.y), ry = fmaf(sn, l.x, cs * l.y);
+        const float ex = px + rx, ey = py + ry, ez = z + l.z;
+        float efx = 0.f, efy = 0.f;
+#pragma unroll
+        for (int s = 0; s < NB; ++s) {
+          const float dx = cx[s] - ex, dy = cy[s] - ey, dz = cz[s] - ez;
+          const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          const float Rs = cr[s] + l.w;
+          if (d2 < Rs * Rs) {
+            const float d = sqrtf(d2);
+            J += Rs - d;
+            if (d > 0.f) {
+              const float inv = 1.f / d;
+              const float vx = dx * inv, vy = dy * inv, vz = dz * inv;
+              gx[s] -= vx;
+              gy[s] -= vy;
+              gz[s] -= vz;
+              efx += vx;
+              efy += vy;
+            }
+          }
+        }
+        fx += efx;
+        fy += efy;
+        tq = fmaf(rx, efy, fmaf(-ry, efx, tq));
+      }
+      if (fx != 0.f || fy != 0.f || tq != 0.f) {
+        atomicAdd(&G[src * PT + pl], wenv * fx);
+        atomicAdd(&G[(src + 1) * PT + pl], wenv * fy);
+        atomicAdd(&G[(src + 2) * PT + pl], wenv * tq);
+      }
+    }
+  }
+  return J;
+}
+
+// Bound distance ||max(lo - v, v - hi, 0)|| and its gradient (appendix listing).
+template <int N>
+__device__ __forceinline__ float bound_dist(const float (&v)[N], const float (&lo)[N], const float (&hi)[N],
+                                            float (&grad)[N]) {
+  float e[N];
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    e[i] = fmaxf(fmaxf(lo[i] - v[i], v[i] - hi[i]), 0.f);
+    s = fmaf(e[i], e[i], s);
+  }
+  const float d = sqrtf(s);
+  const float inv = d > 0.f ? 1.f / d : 0.f;
+#pragma unroll
+  for (int i = 0; i < N; ++i) grad[i] = (v[i] > hi[i] ? e[i] : (v[i] < lo[i] ? -e[i] : 0.f)) * inv;
+  return d;
+}
+
+// ------------------------------------------------------------------ one configuration
+template <int L>
+__device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __restrict__ pb, int k,
+                            const float* __restrict__ X, float* G, float* Tm, int pl, int sub) {
+  constexpr int PT = 32 / L;
+  const int nj = sc[SH_NJ];
+  const float* arm = reinterpret_cast<const float*>(sc + sc[SH_OFF_ARM]);
+  const float4* sph = reinterpret_cast<const float4*>(sc + sc[SH_OFF_SPH]);
+  const int O = sc[SH_O], Opad = sc[SH_OPAD];
+  const float* obs = reinterpret_cast<const float*>(sc + sc[SH_OFF_OBS]);
+  const float* boxr = reinterpret_cast<const float*>(sc + sc[SH_OFF_BOX]);
+  const float4* bloc = reinterpret_cast<const float4*>(sc + sc[SH_OFF_BLOC]);
+  const float4* binit = reinterpret_cast<const float4*>(sc + sc[SH_OFF_BINIT]);
+  const float* surf = reinterpret_cast<const float*>(sc + sc[SH_OFF_SURF]);
+  const int NBS = sc[SH_NBS];
+
+  const int* cf = reinterpret_cast<const int*>(pb + pb[PH_OFF_CFG] + k * CFG_W);
+  const float* cff = reinterpret_cast<const float*>(cf);
+  const int kind = cf[CF_KIND], b = cf[CF_BOX], qo = cf[CF_QOFF], go = cf[CF_GOFF], tsrc = cf[CF_TSRC];
+  const int n_env = cf[CF_NENV];
+  const int* env = reinterpret_cast<const int*>(pb + pb[PH_OFF_ENV]) + cf[CF_ENVOFF] * ENV_W;
+  const uint32_t* terms = pb + pb[PH_OFF_TERMS];
+  const float w_kp = tw(terms, cf[CF_T_KP]), w_kr = tw(terms, cf[CF_T_KR]);
+  const float w_cf = tw(terms, cf[CF_T_CF]), w_jl = tw(terms, cf[CF_T_JL]), w_x = tw(terms, cf[CF_T_X]);
+  const float w_cp = kind == 1 ? tw(terms, cf[CF_T_CP]) : 0.f;
+  const float k0 = sub == 0 ? 1.f : 0.f;  // terms computed redundantly count on lane 0 only
+#define XV(c) X[(c) * PT + pl]
+
+  // ---------------- forward kinematics T_0 .. T_n
+  float R[9], t[3];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) R[i] = arm[i];
+  t[0] = arm[9]; t[1] = arm[10]; t[2] = arm[11];
+  float sn[MAXJ], cs[MAXJ];
+#pragma unroll
+  for (int j = 0; j < MAXJ; ++j) {
+    if (j < nj) {
+      const float* Jp = arm + 24 + j * ARM_JW;
+      sincosf(XV(qo + j) + Jp[4], &sn[j], &cs[j]);
+      rz_right(R, cs[j], sn[j]);
+      const float a = Jp[0], d = Jp[1];
+      t[0] = fmaf(d, R[2], fmaf(a, R[0], t[0]));
+      t[1] = fmaf(d, R[5], fmaf(a, R[3], t[1]));
+      t[2] = fmaf(d, R[8], fmaf(a, R[6], t[2]));
+      rx_right(R, Jp[2], Jp[3]);
+    }
+  }
+  // end effector = T_n * tool
+  float Re[9], te[3];
+  {
+    const float* tl = arm + 12;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        Re[3 * i + j] = fmaf(R[3 * i], tl[j], fmaf(R[3 * i + 1], tl[3 + j], R[3 * i + 2] * tl[6 + j]));
+      te[i] = fmaf(R[3 * i], tl[9], fmaf(R[3 * i + 1], tl[10], fmaf(R[3 * i + 2], tl[11], t[i])));
+    }
+  }
+
+  // ---------------- Kin: target P(p) G(g)
+  float px, py, pz, pyaw;
+  if (tsrc < 0) {
+    px = cff[CF_TX]; py = cff[CF_TY]; pz = cff[CF_TZ]; pyaw = cff[CF_TYAW];
+  } else {
+    px = XV(tsrc); py = XV(tsrc + 1); pz = cff[CF_TZ]; pyaw = XV(tsrc + 2);
+  }
+  const float gxv = XV(go), gyv = XV(go + 1), gzv = XV(go + 2), gyaw = XV(go + 3);
+  float sy, cy;
+  sincosf(pyaw, &sy, &cy);
+  const float rgx = fmaf(cy, gxv, -sy * gyv), rgy = fmaf(sy, gxv, cy * gyv);
+  const float ttx = px + rgx, tty = py + rgy, ttz = pz + gzv;
+  float s2, c2;
+  sincosf(pyaw + gyaw, &s2, &c2);
+  // M = Re^T R_tgt, R_tgt = [[c2, s2, 0], [s2, -c2, 0], [0, 0, -1]]
+  float Mr[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float e0 = Re[i], e1 = Re[3 + i], e2 = Re[6 + i];
+    Mr[3 * i] = fmaf(e0, c2, e1 * s2);
+    Mr[3 * i + 1] = fmaf(e0, s2, -e1 * c2);
+    Mr[3 * i + 2] = -e2;
+  }
+  const float wx = Mr[7] - Mr[5], wy = Mr[2] - Mr[6], wz = Mr[3] - Mr[1];
+  const float wn = sqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz)));
+  const float e_rot = atan2f(0.5f * wn, 0.5f * (Mr[0] + Mr[4] + Mr[8] - 1.f));
+  const float dlx = te[0] - ttx, dly = te[1] - tty, dlz = te[2] - ttz;
+  const float e_pos = sqrtf(fmaf(dlx, dlx, fmaf(dly, dly, dlz * dlz)));
+  // world wrench on the end effector from Kin (lane 0 only)
+  float fkx = 0.f, fky = 0.f, fkz = 0.f;
+  if (e_pos > 0.f) {
+    const float s = w_kp / e_pos;
+    fkx = s * dlx; fky = s * dly; fkz = s * dlz;
+  }
+  float ubx = 0.f, uby = 0.f, ubz = 0.f;  // R_EE * unit axis of M, times w_kr
+  if (wn > 0.f) {
+    const float s = w_kr / wn;
+    const float ux = s * wx, uy = s * wy, uz = s * wz;
+    ubx = fmaf(Re[0], ux, fmaf(Re[1], uy, Re[2] * uz));
+    uby = fmaf(Re[3], ux, fmaf(Re[4], uy, Re[5] * uz));
+    ubz = fmaf(Re[6], ux, fmaf(Re[7], uy, Re[8] * uz));
+  }
+  float F[3] = {k0 * fkx, k0 * fky, k0 * fkz};
+  float Mw[3] = {k0 * (te[1] * fkz - te[2] * fky - ubx), k0 * (te[2] * fkx - te[0] * fkz - uby),
+                 k0 * (te[0] * fky - te[1] * fkx - ubz)};
+  // gradients of the target: dJ/dt_tgt = -f, dJ/domega_tgt = ub
+  float gg[4];  // grasp x, y, z, yaw
+  gg[0] = k0 * (-(cy * fkx + sy * fky));
+  gg[1] = k0 * (-(-sy * fkx + cy * fky));
+  gg[2] = k0 * (-fkz);
+  gg[3] = k0 * ubz;
+  float gp[3];  // placement x, y, yaw of the target (if it is a variable)
+  gp[0] = k0 * (-fkx);
+  gp[1] = k0 * (-fky);
+  gp[2] = k0 * (fkx * rgy - fky * rgx + ubz);
+
+  float tau[MAXJ];
+#pragma unroll
+  for (int j = 0; j < MAXJ; ++j) tau[j] = 0.f;
+  float J_hold = 0.f, J_place = 0.f;
+
+  // ---------------- held box spheres at FK(q) G(g)^-1 (attached to the end effector)
+  {
+    float sg_, cg_;
+    sincosf(gyaw, &sg_, &cg_);
+    float Ro[9];  // R_obj = Re * [[cg, sg, 0], [sg, -cg, 0], [0, 0, -1]]
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Ro[3 * i] = fmaf(cg_, Re[3 * i], sg_ * Re[3 * i + 1]);
+      Ro[3 * i + 1] = fmaf(sg_, Re[3 * i], -cg_ * Re[3 * i + 1]);
+      Ro[3 * i + 2] = -Re[3 * i + 2];
+    }
+    for (int e0 = 0; e0 < NBS; e0 += HB) {
+      float cx[HB], cyy[HB], cz[HB], cr[HB], vx[HB], vy[HB], gx[HB], gyy[HB], gz[HB];
+#pragma unroll
+      for (int s = 0; s < HB; ++s) {
+        gx[s] = gyy[s] = gz[s] = 0.f;
+        if (e0 + s < NBS) {
+          const float4 l = bloc[b * NBS + e0 + s];
+          vx[s] = l.x - gxv; vy[s] = l.y - gyv;
+          const float vz = l.z - gzv;
+          cx[s] = fmaf(Ro[0], vx[s], fmaf(Ro[1], vy[s], fmaf(Ro[2], vz, te[0])));
+          cyy[s] = fmaf(Ro[3], vx[s], fmaf(Ro[4], vy[s], fmaf(Ro[5], vz, te[1])));
+          cz[s] = fmaf(Ro[6], vx[s], fmaf(Ro[7], vy[s], fmaf(Ro[8], vz, te[2])));
+          cr[s] = l.w;
+        } else {
+          cx[s] = cyy[s] = cz[s] = DUMMY_FAR;
+          cr[s] = 0.f; vx[s] = vy[s] = 0.f;
+        }
+      }
+      J_hold += collide<L, HB>(cx, cyy, cz, cr, gx, gyy, gz, obs, O, Opad, env, n_env, bloc, binit, NBS, X, G,
+                               pl, sub, w_cf);
+#pragma unroll
+      for (int s = 0; s < HB; ++s) {
+        const float fx = w_cf * gx[s], fy = w_cf * gyy[s], fz = w_cf * gz[s];
+        F[0] += fx; F[1] += fy; F[2] += fz;
+        Mw[0] += cyy[s] * fz - cz[s] * fy;
+        Mw[1] += cz[s] * fx - cx[s] * fz;
+        Mw[2] += cx[s] * fy - cyy[s] * fx;
+        // object-frame force G = R_obj^T f; c = t_EE + R_obj (l - g)
+        const float Gx = fmaf(Ro[0], fx, fmaf(Ro[3], fy, Ro[6] * fz));
+        const float Gy = fmaf(Ro[1], fx, fmaf(Ro[4], fy, Ro[7] * fz));
+        const float Gz = fmaf(Ro[2], fx, fmaf(Ro[5], fy, Ro[8] * fz));
+        gg[0] -= Gx; gg[1] -= Gy; gg[2] -= Gz;
+        gg[3] -= Gy * vx[s] - Gx * vy[s];
+      }
+    }
+  }
+
+  // ---------------- reverse sweep over the links (tip to base)
+  for (int l = nj; l >= 1; --l) {
+    const int ls = sc[SH_LINK0 + l], le = sc[SH_LINK0 + l + 1];
+    for (int s0 = ls; s0 < le; s0 += SB) {
+      float cx[SB], cyy[SB], cz[SB], cr[SB], gx[SB], gyy[SB], gz[SB];
+#pragma unroll
+      for (int s = 0; s < SB; ++s) {
+        const float4 p = sph[s0 + s];
+        cx[s] = fmaf(R[0], p.x, fmaf(R[1], p.y, fmaf(R[2], p.z, t[0])));
+        cyy[s] = fmaf(R[3], p.x, fmaf(R[4], p.y, fmaf(R[5], p.z, t[1])));
+        cz[s] = fmaf(R[6], p.x, fmaf(R[7], p.y, fmaf(R[8], p.z, t[2])));
+        cr[s] = p.w;
+        gx[s] = gyy[s] = gz[s] = 0.f;
+      }
+      J_hold += collide<L, SB>(cx, cyy, cz, cr, gx, gyy, gz, obs, O, Opad, env, n_env, bloc, binit, NBS, X, G,
+                               pl, sub, w_cf);
+#pragma unroll
+      for (int s = 0; s < SB; ++s) {
+        const float fx = w_cf * gx[s], fy = w_cf * gyy[s], fz = w_cf * gz[s];
+        F[0] += fx; F[1] += fy; F[2] += fz;
+        Mw[0] += cyy[s] * fz - cz[s] * fy;
+        Mw[1] += cz[s] * fx - cx[s] * fz;
+        Mw[2] += cx[s] * fy - cyy[s] * fx;
+      }
+    }
+    // T_{l-1} = T_l Rx(-alpha) Tx(-a) Tz(-d) Rz(-theta); joint l turns about z_{l-1} through o_{l-1}
+    const float* Jp = arm + 24 + (l - 1) * ARM_JW;
+    rx_right(R, Jp[2], -Jp[3]);
+    const float a = Jp[0], d = Jp[1];
+    t[0] -= fmaf(a, R[0], d * R[2]);
+    t[1] -= fmaf(a, R[3], d * R[5]);
+    t[2] -= fmaf(a, R[6], d * R[8]);
+    const float zx = R[2], zy = R[5], zz = R[8];
+    const float ox = t[1] * zz - t[2] * zy, oy = t[2] * zx - t[0] * zz, oz = t[0] * zy - t[1] * zx;
+    const float tq = fmaf(zx, Mw[0], fmaf(zy, Mw[1], fmaf(zz, Mw[2], fmaf(ox, F[0], fmaf(oy, F[1], oz * F[2])))));
+#pragma unroll
+    for (int j = 0; j < MAXJ; ++j)
+      if (j == l - 1) tau[j] = tq;
+    float snl = 0.f, csl = 1.f;
+#pragma unroll
+    for (int j = 0; j < MAXJ; ++j)
+      if (j == l - 1) { snl = sn[j]; csl = cs[j]; }
+    rz_right(R, csl, -snl);
+  }
+  // spheres fixed to the base frame (link 0): cost only
+  for (int s0 = sc[SH_LINK0]; s0 < sc[SH_LINK0 + 1]; s0 += SB) {
+    float cx[SB], cyy[SB], cz[SB], cr[SB], gx[SB], gyy[SB], gz[SB];
+#pragma unroll
+    for (int s = 0; s < SB; ++s) {
+      const float4 p = sph[s0 + s];
+      cx[s] = fmaf(R[0], p.x, fmaf(R[1], p.y, fmaf(R[2], p.z, t[0])));
+      cyy[s] = fmaf(R[3], p.x, fmaf(R[4], p.y, fmaf(R[5], p.z, t[1])));
+      cz[s] = fmaf(R[6], p.x, fmaf(R[7], p.y, fmaf(R[8], p.z, t[2])));
+      cr[s] = p.w;
+      gx[s] = gyy[s] = gz[s] = 0.f;
+    }
+    J_hold += collide<L, SB>(cx, cyy, cz, cr, gx, gyy, gz, obs, O, Opad, env, n_env, bloc, binit, NBS, X, G, pl,
+                             sub, w_cf);
+  }
+
+  // ---------------- CFreePlace: the placed box at P(p)
+  float gpc[3] = {0.f, 0.f, 0.f};
+  if (kind == 1) {
+    const float pzb = cff[CF_PZ];
+    for (int e0 = 0; e0 < NBS; e0 += HB) {
+      float cx[HB], cyy[HB], cz[HB], cr[HB], rx[HB], ry[HB], gx[HB], gyy[HB], gz[HB];
+#pragma unroll
+      for (int s = 0; s < HB; ++s) {
+        gx[s] = gyy[s] = gz[s] = 0.f;
+        if (e0 + s < NBS) {
+          const float4 l = bloc[b * NBS + e0 + s];
+          rx[s] = fmaf(cy, l.x, -sy * l.y);
+          ry[s] = fmaf(sy, l.x, cy * l.y);
+          cx[s] = px + rx[s]; cyy[s] = py + ry[s]; cz[s] = pzb + l.z;
+          cr[s] = l.w;
+        } else {
+          cx[s] = cyy[s] = cz[s] = DUMMY_FAR;
+          cr[s] = 0.f; rx[s] = ry[s] = 0.f;
+        }
+      }
+      J_place += collide<L, HB>(cx, cyy, cz, cr, gx, gyy, gz, obs, O, Opad, env, n_env, bloc, binit, NBS, X, G,
+                                pl, sub, w_cp);
+#pragma unroll
+      for (int s = 0; s < HB; ++s) {
+        gpc[0] += w_cp * gx[s];
+        gpc[1] += w_cp * gyy[s];
+        gpc[2] += w_cp * (rx[s] * gyy[s] - ry[s] * gx[s]);
+      }
+    }
+  }
+
+  // ---------------- reduce over the L lanes of this (particle, configuration)
+#pragma unroll
+  for (int m = 1; m < L; m <<= 1) {
+    J_hold += __shfl_xor_sync(0xffffffffu, J_hold, m);
+    J_place += __shfl_xor_sync(0xffffffffu, J_place, m);
+#pragma unroll
+    for (int j = 0; j < MAXJ; ++j) tau[j] += __shfl_xor_sync(0xffffffffu, tau[j], m);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) gg[i] += __shfl_xor_sync(0xffffffffu, gg[i], m);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) gpc[i] += __shfl_xor_sync(0xffffffffu, gpc[i], m);
+  }
+  if (sub != 0) return;
+
+  // ---------------- per-configuration scalar terms (lane 0)
+  // joint limits
+  float jl = 0.f;
+  {
+    float e2 = 0.f;
+    float ex[MAXJ];
+#pragma unroll
+    for (int j = 0; j < MAXJ; ++j) {
+      ex[j] = 0.f;
+      if (j < nj) {
+        const float* Jp = arm + 24 + j * ARM_JW;
+        const float q = XV(qo + j);
+        ex[j] = fmaxf(fmaxf(Jp[5] - q, q - Jp[6]), 0.f);
+        e2 = fmaf(ex[j], ex[j], e2);
+      }
+    }
+    jl = sqrtf(e2);
+    const float inv = jl > 0.f ? w_jl / jl : 0.f;
+#pragma unroll
+    for (int j = 0; j < MAXJ; ++j) {
+      if (j < nj) {
+        const float* Jp = arm + 24 + j * ARM_JW;
+        const float q = XV(qo + j);
+        const float gj = q > Jp[6] ? ex[j] * inv : (q < Jp[5] ? -ex[j] * inv : 0.f);
+        G[(qo + j) * PT + pl] = tau[j] + gj;
+      }
+    }
+  }
+  Tm[cf[CF_T_KP] * PT + pl] = e_pos;
+  Tm[cf[CF_T_KR] * PT + pl] = e_rot;
+  Tm[cf[CF_T_CF] * PT + pl] = J_hold;
+  Tm[cf[CF_T_JL] * PT + pl] = jl;
+  const float* br = boxr + b * BOX_W;
+  if (kind == 0) {
+    // Grasp(o, g): bound distance of g_xyz to [-hx, hx] x [-hy, hy] x [hz - 0.02, hz]
+    const float v[3] = {gxv, gyv, gzv};
+    const float lo[3] = {-br[0], -br[1], br[2] - 0.02f};
+    const float hi[3] = {br[0], br[1], br[2]};
+    float gr[3];
+    const float d = bound_dist<3>(v, lo, hi, gr);
+    Tm[cf[CF_T_X] * PT + pl] = d;
+    gg[0] += w_x * gr[0]; gg[1] += w_x * gr[1]; gg[2] += w_x * gr[2];
+  } else {
+    // StablePlace containment: 4 footprint corners in the surface frame
+    const float* sf = surf + cf[CF_SURF] * SURF_W;
+    const float scx = sf[0], scy = sf[1], shx = sf[3], shy = sf[4], scs = sf[6], ssn = sf[7];
+    float J = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float lx = (c & 1 ? 1.f : -1.f) * br[0], ly = (c & 2 ? 1.f : -1.f) * br[1];
+      const float rx = fmaf(cy, lx, -sy * ly), ry = fmaf(sy, lx, cy * ly);
+      const float wx_ = px + rx - scx, wy_ = py + ry - scy;
+      const float v[2] = {fmaf(scs, wx_, ssn * wy_), fmaf(-ssn, wx_, scs * wy_)};
+      const float lo[2] = {-shx, -shy}, hi[2] = {shx, shy};
+      float gu[2];
+      J += bound_dist<2>(v, lo, hi, gu);
+      // d/dw = Rz(-yaw_s)^T d/du ; w depends on (px, py) directly and on yaw through r
+      const float gwx = fmaf(scs, gu[0], -ssn * gu[1]), gwy = fmaf(ssn, gu[0], scs * gu[1]);
+      gpc[0] += w_x * gwx;
+      gpc[1] += w_x * gwy;
+      gpc[2] += w_x * (rx * gwy - ry * gwx);
+    }
+    Tm[cf[CF_T_X] * PT + pl] = J;
+    Tm[cf[CF_T_CP] * PT + pl] = J_place;
+  }
+  // grasp gradient (shared by the Pick and the Place that hold the same grasp)
+#pragma unroll
+  for (int i = 0; i < 4; ++i) atomicAdd(&G[(go + i) * PT + pl], gg[i]);
+  // placement gradient: Kin target if the target is a variable, plus CFreePlace/containment
+  const int psrc = cf[CF_PSRC];
+  if (tsrc >= 0) {
+    gpc[0] += gp[0]; gpc[1] += gp[1]; gpc[2] += gp[2];
+  }
+  if (psrc >= 0) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) atomicAdd(&G[(psrc + i) * PT + pl], gpc[i]);
+  }
+#undef XV
+}
+
+// Goal MinimizeObjDist: sum over pairs of moved boxes of ||pos_i - pos_j||.
+template <int L>
+__device__ void eval_goal(const uint32_t* __restrict__ sc, const uint32_t* __restrict__ pb,
+                          const float* __restrict__ X, float* G, float* Tm, int pl) {
+  constexpr int PT = 32 / L;
+  const int ng = pb[PH_NGOAL], gt = pb[PH_GOAL_T];
+  if (gt < 0) return;
+  const int* gl = reinterpret_cast<const int*>(pb + pb[PH_OFF_GOAL]);
+  const float* boxr = reinterpret_cast<const float*>(sc + sc[SH_OFF_BOX]);
+  const float w = tw(pb + pb[PH_OFF_TERMS], gt);
+  float J = 0.f;
+  for (int i = 0; i < ng; ++i) {
+    const int si = gl[i * GOAL_W + 1];
+    const float* bi = boxr + gl[i * GOAL_W] * BOX_W;
+    const float xi = si >= 0 ? X[si * PT + pl] : bi[4];
+    const float yi = si >= 0 ? X[(si + 1) * PT + pl] : bi[5];
+    const float zi = si >= 0 ? __int_as_float(gl[i * GOAL_W + 2]) : bi[6];
+    for (int j = i + 1; j < ng; ++j) {
+      const int sj = gl[j * GOAL_W + 1];
+      const float* bj = boxr + gl[j * GOAL_W] * BOX_W;
+      const float dx = xi - (sj >= 0 ? X[sj * PT + pl] : bj[4]);
+      const float dy = yi - (sj >= 0 ? X[(sj + 1) * PT + pl] : bj[5]);
+      const float dz = zi - (sj >= 0 ? __int_as_float(gl[j * GOAL_W + 2]) : bj[6]);
+      const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+      J += d;
+      if (d > 0.f) {
+        const float s = w / d;
+        if (si >= 0) {
+          atomicAdd(&G[si * PT + pl], s * dx);
+          atomicAdd(&G[(si + 1) * PT + pl], s * dy);
+        }
+        if (sj >= 0) {
+          atomicAdd(&G[sj * PT + pl], -s * dx);
+          atomicAdd(&G[(sj + 1) * PT + pl], -s * dy);
+        }
+      }
+    }
+  }
+  Tm[gt * PT + pl] = J;
+}
+
+// ------------------------------------------------------------------ fused optimisation kernel
+template <int L>
+__global__ void __launch_bounds__(512, 1) optimize_kernel(OptArgs a) {
+  constexpr int PT = 32 / L;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  const int sw = (a.scene_words + 3) & ~3, pw = (a.prob_words + 3) & ~3;
+  uint32_t* s_sc = reinterpret_cast<uint32_t*>(smem_raw);
+  uint32_t* s_pb = s_sc + sw;
+  const int D = a.prob[PH_D], K = a.prob[PH_K], NT = a.prob[PH_NT];
+  float* sx = reinterpret_cast<float*>(s_pb + pw);
+  float* sm = sx + D * PT;
+  float* sv = sm + D * PT;
+  float* sg = sv + D * PT;
+  float* st = sg + D * PT;
+  int* sflag = reinterpret_cast<int*>(st + NT * PT);
+
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tile0 = blockIdx.x * PT;
+  if (tid == 0) {
+    abort_flag = 0;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&bar, static_cast<uint32_t>((sw + pw) * 4));
+    tma_bulk_g2s(s_sc, a.scene, static_cast<uint32_t>(sw * 4), &bar);
+    tma_bulk_g2s(s_pb, a.prob, static_cast<uint32_t>(pw * 4), &bar);
+  }
+  // particle tile -> shared memory (overlaps the bulk copies)
+  for (int i = tid; i < D * PT; i += nthr) {
+    const int c = i / PT, p = i % PT, gp = tile0 + p;
+    float xv = 0.f, mv = 0.f, vv = 0.f;
+    if (gp < a.P) {
+      xv = a.x_in[c * a.stride + gp];
+      if (a.load_mv) {
+        mv = a.m[c * a.stride + gp];
+        vv = a.v[c * a.stride + gp];
+      }
+    }
+    sx[i] = xv; sm[i] = mv; sv[i] = vv; sg[i] = 0.f;
+  }
+  if (tid == 0) {
+    if (!mbar_wait_bounded(&bar, 0, 1 << 20)) {
+      atomicOr(a.err, ERR_TMA_TIMEOUT);
+      abort_flag = 1;
+      mbar_wait_bounded(&bar, 0, 1 << 16);  // give copies in flight a last chance to land
+    }
+  }
+  __syncthreads();
+  if (abort_flag) return;
+
+  const int w = tid >> 5, lane = tid & 31, W = nthr >> 5;
+  const int pl = lane / L, sub = lane % L;
+  const uint32_t* terms = s_pb + s_pb[PH_OFF_TERMS];
+  const float* lr = reinterpret_cast<const float*>(s_pb + s_pb[PH_OFF_LR]);
+  const int goal_warp = (K - 1) % W;
+
+  for (int it = 0;; ++it) {
+    for (int k = w; k < K; k += W) eval_config<L>(s_sc, s_pb, k, sx, sg, st, pl, sub);
+    if (w == goal_warp && sub == 0) eval_goal<L>(s_sc, s_pb, sx, sg, st, pl);
+    __syncthreads();
+    // Eq. 3 at x_t
+    if (w == 0) {
+      int sat = 0;
+      if (lane < PT) {
+        sat = 1;
+        for (int tt = 0; tt < NT; ++tt) {
+          const uint32_t* tr = terms + tt * TERM_W;
+          if (static_cast<int>(tr[3]) >= 0 && st[tt * PT + lane] > __uint_as_float(tr[2])) sat = 0;
+        }
+        sflag[lane] = sat;
+        if (tile0 + lane >= a.P) sat = 0;
+      }
+      if (__any_sync(0xffffffffu, sat) && lane == 0 && a.first_iter) atomicMin(a.first_iter, a.t0 + it);
+    }
+    if (it == a.n_steps) break;
+    // Adam (Kingma & Ba) on the Eq. 4 gradient; the gradient buffer is cleared for the next pass
+    const int step = a.t0 + it + 1;
+    const float bc1 = static_cast<float>(1.0 - pow(static_cast<double>(a.beta1), step));
+    const float bc2 = static_cast<float>(1.0 - pow(static_cast<double>(a.beta2), step));
+    const float ib1 = 1.f / bc1, ib2 = 1.f / bc2;
+    for (int i = tid; i < D * PT; i += nthr) {
+      const float g = sg[i] * a.gscale;
+      const float m = fmaf(a.beta1, sm[i], (1.f - a.beta1) * g);
+      const float v = fmaf(a.beta2, sv[i], (1.f - a.beta2) * g * g);
+      sm[i] = m;
+      sv[i] = v;
+      sx[i] -= lr[i / PT] * (m * ib1) / (sqrtf(v * ib2) + a.eps);
+      sg[i] = 0.f;
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+
+  // ---------------- outputs of the last check
+  if (tid < PT && tile0 + tid < a.P) {
+    const int gp = tile0 + tid;
+    if (a.out_cost) {
+      float c = 0.f;
+      for (int tt = 0; tt < NT; ++tt) c = fmaf(__uint_as_float(terms[tt * TERM_W + 1]), st[tt * PT + tid], c);
+      a.out_cost[gp] = c;
+    }
+    if (a.out_flags) a.out_flags[gp] = static_cast<uint8_t>(sflag[tid]);
+  }
+  if (a.out_terms)
+    for (int i = tid; i < NT * PT; i += nthr) {
+      const int tt = i / PT, p = i % PT;
+      if (tile0 + p < a.P) a.out_terms[tt * a.stride + tile0 + p] = st[i];
+    }
+  if (a.out_counts)
+    for (int tt = tid; tt < NT; tt += nthr) {
+      const uint32_t* tr = terms + tt * TERM_W;
+      const int ci = static_cast<int>(tr[3]);
+      if (ci < 0) continue;
+      const float tol = __uint_as_float(tr[2]);
+      int cnt = 0;
+      for (int p = 0; p < PT; ++p) cnt += (tile0 + p < a.P && st[tt * PT + p] <= tol) ? 1 : 0;
+      if (cnt) atomicAdd(&a.out_counts[ci], cnt);
+    }
+  for (int i = tid; i < D * PT; i += nthr) {
+    const int c = i / PT, p = i % PT, gp = tile0 + p;
+    if (gp >= a.P) continue;
+    if (a.out_grad) a.out_grad[c * a.stride + gp] = sg[i];
+    if (a.x_out) a.x_out[c * a.stride + gp] = sx[i];
+    if (a.m) a.m[c * a.stride + gp] = sm[i];
+    if (a.v) a.v[c * a.stride + gp] = sv[i];
+  }
+}
+
+// ------------------------------------------------------------------ uniform sampler
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k.x += W0;
+      k.y += W1;
+    }
+    const uint32_t lo0 = M0 * c.x, hi0 = __umulhi(M0, c.x);
+    const uint32_t lo1 = M1 * c.z, hi1 = __umulhi(M1, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+__device__ __forceinline__ float philox_u01(uint32_t i, uint32_t c, uint2 key) {
+  const uint4 w = philox4x32_10(make_uint4(i, c, 0u, 0u), key);
+  return static_cast<float>(w.x >> 8) * (1.0f / 16777216.0f);
+}
+
+__global__ void sample_uniform_kernel(const uint32_t* __restrict__ pb, const uint32_t* __restrict__ sc,
+                                      float* __restrict__ x, float* __restrict__ m, float* __restrict__ v,
+                                      int stride, int P, uint2 key) {
+  const int c = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  const uint32_t* rec = pb + pb[PH_OFF_SAMP] + c * SAMP_W;
+  const int kind = static_cast<int>(rec[0]);
+  const float lo = __uint_as_float(rec[1]), hi = __uint_as_float(rec[2]);
+  float val;
+  if (kind == SK_LINEAR) {
+    val = fmaf(hi - lo, philox_u01(i, c, key), lo);
+  } else {
+    const float* sf = reinterpret_cast<const float*>(sc + sc[SH_OFF_SURF]) + rec[3] * SURF_W;
+    const int cx = kind == SK_PLACE_X ? c : c - 1;
+    const float su = fmaf(2.f * sf[3], philox_u01(i, cx, key), -sf[3]);
+    const float sv = fmaf(2.f * sf[4], philox_u01(i, cx + 1, key), -sf[4]);
+    val = kind == SK_PLACE_X ? sf[0] + fmaf(sf[6], su, -sf[7] * sv) : sf[1] + fmaf(sf[7], su, sf[6] * sv);
+  }
+  x[c * stride + i] = val;
+  m[c * stride + i] = 0.f;
+  v[c * stride + i] = 0.f;
+}
+
+// ------------------------------------------------------------------ launchers
+template <int L>
+static cudaError_t launch_opt(const OptArgs& a, int K, size_t smem, cudaStream_t st) {
+  constexpr int PT = 32 / L;
+  static size_t attr_bytes = 0;  // largest dynamic shared-memory size enabled so far
+  if (smem > 48 * 1024 && smem > attr_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(optimize_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    attr_bytes = smem;
+  }
+  const int per = (K + 15) / 16;          // configurations per warp
+  const int W = (K + per - 1) / per;      // <= 16 warps
+  const int grid = (a.P + PT - 1) / PT;
+  if (grid == 0) return cudaSuccess;
+  optimize_kernel<L><<<grid, W * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_optimize(const OptArgs& a, int L, int K, size_t smem, cudaStream_t st) {
+  switch (L) {
+    case 1: return launch_opt<1>(a, K, smem, st);
+    case 2: return launch_opt<2>(a, K, smem, st);
+    case 4: return launch_opt<4>(a, K, smem, st);
+    case 8: return launch_opt<8>(a, K, smem, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_sample(const uint32_t* pb, const uint32_t* sc, float* x, float* m, float* v, int stride, int P,
+                          int D, uint64_t seed, cudaStream_t st) {
+  if (P == 0 || D == 0) return cudaSuccess;
+  dim3 grid((P + 255) / 256, D);
+  const uint2 key = make_uint2(static_cast<uint32_t>(seed & 0xffffffffu), static_cast<uint32_t>(seed >> 32));
+  sample_uniform_kernel<<<grid, 256, 0, st>>>(pb, sc, x, m, v, stride, P, key);
+  return cudaGetLastError();
+}
+
+size_t optimize_smem_bytes(int scene_words, int prob_words, int D, int NT, int L) {
+  const int PT = 32 / L;
+  const size_t sw = (scene_words + 3) & ~3, pw = (prob_words + 3) & ~3;
+  return 4 * (sw + pw) + 4 * (4 * static_cast<size_t>(D) * PT + static_cast<size_t>(NT) * PT + PT);
+}
+
+}  // namespace tamp

@@ -1,0 +1,214 @@
+"""CUDA path vs FP64 oracle, element by element, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import scenegen as sg
+from oracle import philox
+from oracle.problem import Options, Problem
+from tests.parity import compare_eval, cost_ok, grad_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2411_11833_b300.build import build_library
+    build_library()
+    import paper_2411_11833_b300 as p
+    torch.cuda.set_device(0)
+    return p
+
+
+def _dev(X):
+    return torch.tensor(np.ascontiguousarray(X.T), dtype=torch.float32, device="cuda")
+
+
+def _eval(pkg, sc, acts, X, lanes=0):
+    scene = pkg.Scene(sc)
+    pid = scene.set_skeleton(acts, pkg.default_options(lanes=lanes))
+    out = scene.eval(pid, _dev(X))
+    torch.cuda.synchronize()
+    scene.close()
+    return out
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
+def test_eval_parity_plain(pkg, lanes):
+    sc, acts = sg.plain_problem(1001)
+    X = sg.random_particles(sc, acts, 203, seed=31)          # several tiles + a ragged tail
+    res = compare_eval(Problem(sc, acts), X, *_eval(pkg, sc, acts, X, lanes), label=f"plain L={lanes}")
+    print(res)
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+def test_eval_parity_packing(pkg, lanes):
+    sc, acts = sg.packing_problem(2001)
+    X = sg.random_particles(sc, acts, 77, seed=32)
+    res = compare_eval(Problem(sc, acts), X, *_eval(pkg, sc, acts, X, lanes), label=f"packing L={lanes}")
+    print(res)
+
+
+@pytest.mark.parametrize("seed", [1002, 1003, 1004])
+def test_eval_parity_other_plain_scenes(pkg, seed):
+    sc, acts = sg.plain_problem(seed)
+    X = sg.random_particles(sc, acts, 64, seed=seed)
+    compare_eval(Problem(sc, acts), X, *_eval(pkg, sc, acts, X), label=f"plain seed {seed}")
+
+
+def test_eval_single_particle_and_full_warp(pkg):
+    sc, acts = sg.packing_problem(2002)
+    for n in (1, 32, 33):
+        X = sg.random_particles(sc, acts, n, seed=40 + n)
+        compare_eval(Problem(sc, acts), X, *_eval(pkg, sc, acts, X, 2), label=f"n={n}")
+
+
+def test_eval_stress_scene_sampled(pkg):
+    """100-sphere arm, 64 cuboids, 12 boxes, 24 configurations."""
+    sc, acts = sg.stress_problem(5001)
+    X = sg.random_particles(sc, acts, 12, seed=51)
+    compare_eval(Problem(sc, acts), X, *_eval(pkg, sc, acts, X, 1), label="stress")
+
+
+def test_eval_full_size_packing_sampled(pkg):
+    """4096 particles (the benchmark batch) evaluated in one launch; the oracle
+    checks a sample of them one by one."""
+    sc, acts = sg.packing_problem(2001)
+    X = sg.random_particles(sc, acts, 4096, seed=33)
+    cost, terms, flags, grad = _eval(pkg, sc, acts, X)
+    idx = np.random.default_rng(0).choice(4096, 48, replace=False)
+    compare_eval(Problem(sc, acts), X[idx], cost[idx], terms[:, idx], flags[idx], grad[:, idx], label="4096 sampled")
+
+
+def test_uniform_sampler_matches_oracle_philox(pkg):
+    sc, acts = sg.packing_problem(2001)
+    pr = Problem(sc, acts)
+    scene = pkg.Scene(sc)
+    pid = scene.set_skeleton(acts)
+    scene.sample(pid, 1000, seed=0x1234_5678_9ABC)
+    x, m, v, t = scene.get_particles(pid)
+    ref = philox.sample_uniform(pr, 1000, 0x1234_5678_9ABC)
+    assert np.abs(x.T - ref).max() < 2e-6
+    assert not m.any() and not v.any() and t == 0
+    scene.close()
+
+
+def test_adam_step_matches_oracle(pkg):
+    sc, acts = sg.plain_problem(1001)
+    pr = Problem(sc, acts)
+    P = 150
+    X = sg.random_particles(sc, acts, P, seed=61)
+    m0, v0 = sg.random_adam_state(P, pr.D, seed=62)
+    t0 = 7
+    scene = pkg.Scene(sc)
+    pid = scene.set_skeleton(acts)
+    scene.set_particles(pid, X.T.astype(np.float32), m0.T.astype(np.float32), v0.T.astype(np.float32), t0)
+    scene.optimize(pid, 1)
+    x1, m1, v1, t1 = scene.get_particles(pid)
+    scene.close()
+    assert t1 == t0 + 1
+    Xt = torch.tensor(X.astype(np.float32).astype(np.float64))
+    _, g = pr.gradient(Xt)
+    xr, mr, vr = pr.adam_step(Xt, torch.tensor(m0.astype(np.float32).astype(np.float64)),
+                              torch.tensor(v0.astype(np.float32).astype(np.float64)), t0 + 1, g, P)
+    margin = pr.kink_margin(Xt).numpy()
+    keep = margin > 1e-4
+    dm = np.abs(m1.T - mr.numpy())[keep]
+    assert dm.max() <= 1e-3 * np.abs(mr.numpy()[keep]).max() + 1e-9
+    # the update is lr * m_hat / (sqrt(v_hat) + eps): compare the step taken
+    step_g = (x1.T - X.astype(np.float32))[keep]
+    step_r = (xr.numpy() - Xt.numpy())[keep]
+    assert np.abs(step_g - step_r).max() <= 1e-3 * np.abs(step_r).max() + 2e-6
+
+
+def test_first_satisfying_iteration_of_witness(pkg):
+    from tests.test_oracle_pins import _scara_witness_scene
+    sc, acts, x = _scara_witness_scene()
+    scene = pkg.Scene(sc)
+    pid = scene.set_skeleton(acts)
+    X = np.repeat(x.numpy(), 5, axis=0)
+    scene.set_particles(pid, X.T.astype(np.float32))
+    scene.optimize(pid, 3)
+    q = scene.query(pid, 5)
+    scene.close()
+    assert q["first_iter"] == 0
+    assert q["n_satisfied"] == 5
+
+
+def test_optimize_trajectory_tracks_oracle(pkg):
+    """Ten fused Adam iterations from the same particles: FP32 vs FP64 paths
+    stay together except where a particle crosses a kink (counted)."""
+    sc, acts = sg.plain_problem(1001)
+    pr = Problem(sc, acts)
+    P = 64
+    X = philox.sample_uniform(pr, P, 77)
+    scene = pkg.Scene(sc)
+    pid = scene.set_skeleton(acts)
+    scene.set_particles(pid, X.T.astype(np.float32))
+    scene.optimize(pid, 10)
+    x10, _, _, t = scene.get_particles(pid)
+    q = scene.query(pid, P)
+    scene.close()
+    out = pr.optimize(torch.tensor(X.astype(np.float32).astype(np.float64)), 10)
+    d = np.abs(x10.T - out["x"].numpy()).max(axis=1)
+    close = d < 1e-3
+    assert t == 10
+    assert close.mean() >= 0.8, f"only {close.mean():.2f} of trajectories agree"
+    ok = cost_ok(q["cost"][close].astype(np.float64), out["cost"].numpy()[close]) | (np.abs(q["cost"][close] - out["cost"].numpy()[close]) < 1e-3)
+    assert ok.all()
+
+
+def test_counts_and_mask_match_oracle(pkg):
+    sc, acts = sg.packing_problem(2001)
+    pr = Problem(sc, acts)
+    P = 300
+    X = sg.random_particles(sc, acts, P, seed=71, spread=0.0)
+    scene = pkg.Scene(sc)
+    pid = scene.set_skeleton(acts)
+    scene.set_particles(pid, X.T.astype(np.float32))
+    q = scene.query(pid, P)
+    scene.close()
+    T = pr.term_values(torch.tensor(X.astype(np.float32).astype(np.float64)))
+    counts = pr.constraint_counts(T).numpy()
+    from tests.parity import near_threshold
+    band = near_threshold(pr, T.numpy())
+    assert np.abs(q["counts"] - counts).max() <= band.sum()
+    assert ((q["mask"] != pr.satisfied(T).numpy()) & ~band).sum() == 0
+
+
+def test_cost_autograd_function(pkg):
+    sc, acts = sg.plain_problem(1001)
+    pr = Problem(sc, acts)
+    scene = pkg.Scene(sc)
+    pid = scene.set_skeleton(acts)
+    X = sg.random_particles(sc, acts, 50, seed=81)
+    x = torch.tensor(X, dtype=torch.float32, device="cuda", requires_grad=True)
+    CostFn = pkg.cost_fn()
+    J = CostFn.apply(x, scene, pid)
+    (J * torch.linspace(0.5, 1.5, 50, device="cuda")).sum().backward()
+    scene.close()
+    Jr, gr = pr.gradient(torch.tensor(X.astype(np.float32).astype(np.float64)))
+    w = np.linspace(0.5, 1.5, 50)
+    margin = pr.kink_margin(torch.tensor(X)).numpy() > 1e-4
+    err, bound = grad_errors(x.grad.cpu().double().numpy()[margin], (gr.numpy() * w[:, None])[margin])
+    assert (err <= bound).all()
+
+
+def test_invalid_skeleton_rejected(pkg):
+    sc, acts = sg.plain_problem(1001)
+    scene = pkg.Scene(sc)
+    with pytest.raises(pkg.TampError):
+        scene.set_skeleton([(1, 0, 0)])
+    with pytest.raises(pkg.TampError):
+        scene.set_skeleton([(0, 5, -1)])
+    scene.close()
+
+
+def test_no_obstacles_no_other_boxes(pkg):
+    sc, acts = sg.plain_problem(1001)
+    import dataclasses
+    sc0 = dataclasses.replace(sc, obs_center=np.zeros((0, 3)), obs_rot=np.zeros((0, 3, 3)), obs_half=np.zeros((0, 3)))
+    X = sg.random_particles(sc0, acts, 40, seed=91)
+    compare_eval(Problem(sc0, acts), X, *_eval(pkg, sc0, acts, X), label="empty environment")
