@@ -19,7 +19,7 @@ namespace tamp {
 cudaError_t launch_optimize(const OptArgs& a, int L, int K, size_t smem, cudaStream_t st);
 cudaError_t launch_sample(const uint32_t* pb, const uint32_t* sc, float* x, float* m, float* v, int stride, int P,
                           int D, uint64_t seed, cudaStream_t st);
-size_t optimize_smem_bytes(int scene_words, int prob_words, int D, int NT, int L);
+size_t optimize_smem_bytes(int scene_words, int prob_words, int D, int NT, int nslot, int nbs, int L);
 }  // namespace tamp
 
 using namespace tamp;
@@ -27,7 +27,7 @@ using namespace tamp;
 namespace {
 
 struct Problem {
-  int D = 0, K = 0, NT = 0, NCON = 0;
+  int D = 0, K = 0, NT = 0, NCON = 0, NSLOT = 0;
   std::vector<uint32_t> blob;
   uint32_t* d_blob = nullptr;
   std::vector<int> term_kinds;
@@ -143,7 +143,7 @@ tamp_status build_scene_blob(tamp_scene* s, const tamp_scene_desc* d) {
         for (int c = 0; c < 4; ++c) push_f(v, d->sphere_xyzr[4 * i + c]);
         ++cnt;
       }
-    while (cnt % SB) {
+    while (cnt % NB) {
       push_f(v, DUMMY_FAR); push_f(v, DUMMY_FAR); push_f(v, DUMMY_FAR); push_f(v, 0.0);
       ++cnt;
     }
@@ -198,6 +198,17 @@ tamp_status build_scene_blob(tamp_scene* s, const tamp_scene_desc* d) {
     }
   }
   align4(v);
+  v[SH_OFF_BINIT_HB] = static_cast<uint32_t>(v.size());
+  for (int b = 0; b < B; ++b) {
+    const double* p = d->box_init + 4 * b;
+    const double c = std::cos(p[3]), sn = std::sin(p[3]);
+    for (int e = 0; e < NBS; ++e) {
+      const double* l = d->box_spheres + (b * NBS + e) * 4;
+      const double x = p[0] + c * l[0] - sn * l[1], y = p[1] + sn * l[0] + c * l[1], z = p[2] + l[2];
+      push_f(v, 0.5 * (x * x + y * y + z * z - l[3] * l[3]));
+    }
+  }
+  align4(v);
   v[SH_OFF_SURF] = static_cast<uint32_t>(v.size());
   for (int k = 0; k < d->n_surf; ++k) {
     const double* f = d->surf + 6 * k;
@@ -220,6 +231,7 @@ struct PoseSrc {
   int kind = 0;   // 0 = initial pose, 1 = placement variable, 2 = held
   int off = -1;
   int surf = -1;
+  int slot = -1;  // placement slot (index of the Place action among the Places)
 };
 
 // Walk the skeleton (Listing 1 preconditions / effects) and pack the problem blob.
@@ -242,6 +254,8 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
   std::vector<Samp> samp;
   int goal_t = -1;
   std::vector<std::pair<int, PoseSrc>> goal;
+  struct Slot { int box, off; float z; };
+  std::vector<Slot> slots;
   auto add_term = [&](int kind) {
     terms.push_back({kind});
     return static_cast<int>(terms.size()) - 1;
@@ -303,6 +317,8 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
       c.t_cf = add_term(TK_CFREE_HOLD); c.t_cp = add_term(TK_CFREE_PLACE); c.t_jl = add_term(TK_JOINT_LIMIT);
       cfgs.push_back(c);
       pose[b].kind = 1; pose[b].off = po; pose[b].surf = sf;
+      pose[b].slot = static_cast<int>(slots.size());
+      slots.push_back({b, po, static_cast<float>(s->surf[6 * sf + 5] + s->box_half[3 * b + 2])});
       held = -1; held_g = -1;
     } else if (kind == TAMP_GOAL_MIN_OBJ_DIST) {
       goal.clear();
@@ -323,6 +339,7 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
   if (cfgs.empty()) return fail(s, TAMP_ERR_INVALID_ARG, "skeleton has no Pick/Place action");
   if (static_cast<int>(cfgs.size()) > MAX_CFG) return fail(s, TAMP_ERR_INVALID_ARG, "too many configurations");
   if (off > MAX_D) return fail(s, TAMP_ERR_INVALID_ARG, "particle dimension %d exceeds %d", off, MAX_D);
+  if (static_cast<int>(slots.size()) > MAX_SLOT) return fail(s, TAMP_ERR_INVALID_ARG, "too many Place actions");
   pr.D = off;
   pr.K = static_cast<int>(cfgs.size());
   pr.NT = static_cast<int>(terms.size());
@@ -352,10 +369,10 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
       v.push_back(static_cast<uint32_t>(e.first));
       if (ps.kind == 1) {
         v.push_back(static_cast<uint32_t>(ps.off));
-        v.push_back(fbits(static_cast<float>(s->surf[6 * ps.surf + 5] + s->box_half[3 * e.first + 2])));
+        v.push_back(static_cast<uint32_t>(ps.slot));
       } else {
         v.push_back(static_cast<uint32_t>(-1));
-        v.push_back(0);
+        v.push_back(static_cast<uint32_t>(-1));
       }
       v.push_back(0);
     }
@@ -411,6 +428,18 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
     v.push_back(static_cast<uint32_t>(sp.surf));
   }
   align4(v);
+  v[PH_OFF_SLOT] = static_cast<uint32_t>(v.size());
+  for (const Slot& sl : slots) {
+    v.push_back(static_cast<uint32_t>(sl.box));
+    v.push_back(static_cast<uint32_t>(sl.off));
+    v.push_back(fbits(sl.z));
+    v.push_back(0);
+  }
+  if (slots.empty())
+    for (int i = 0; i < SLOT_W; ++i) v.push_back(0);
+  align4(v);
+  pr.NSLOT = static_cast<int>(slots.size());
+  v[PH_NSLOT] = static_cast<uint32_t>(pr.NSLOT);
   v[PH_D] = pr.D; v[PH_K] = pr.K; v[PH_NT] = pr.NT; v[PH_NCON] = pr.NCON;
   v[PH_GOAL_T] = static_cast<uint32_t>(goal_t); v[PH_NGOAL] = static_cast<uint32_t>(goal.size());
   v[PH_WORDS] = static_cast<uint32_t>(v.size());
@@ -480,7 +509,7 @@ tamp_status run_state(tamp_scene* s, Problem& pr, int n_steps) {
   a.gscale = pr.opt.scale_by_batch ? 1.f / static_cast<float>(pr.P) : 1.f;
   const int L = pick_lanes(pr, pr.P);
   CUDA_TRY(s, cudaMemsetAsync(pr.d_counts, 0, static_cast<size_t>(std::max(pr.NCON, 1)) * 4, s->stream));
-  const size_t smem = optimize_smem_bytes(a.scene_words, a.prob_words, pr.D, pr.NT, L);
+  const size_t smem = optimize_smem_bytes(a.scene_words, a.prob_words, pr.D, pr.NT, pr.NSLOT, s->NBS, L);
   if (smem > kMaxDynSmem) return fail(s, TAMP_ERR_INVALID_ARG, "problem needs %zu B of shared memory", smem);
   CUDA_TRY(s, launch_optimize(a, L, pr.K, smem, s->stream));
   pr.t += n_steps;
@@ -721,7 +750,7 @@ tamp_status tamp_eval(tamp_scene* s, int id, int n, const float* x, float* cost,
   a.out_cost = cost; a.out_terms = terms; a.out_flags = flags; a.out_grad = grad;
   a.first_iter = nullptr; a.n_steps = 0; a.t0 = 0;
   const int L = pick_lanes(*pr, n);
-  const size_t smem = optimize_smem_bytes(a.scene_words, a.prob_words, pr->D, pr->NT, L);
+  const size_t smem = optimize_smem_bytes(a.scene_words, a.prob_words, pr->D, pr->NT, pr->NSLOT, s->NBS, L);
   if (smem > kMaxDynSmem) return fail(s, TAMP_ERR_INVALID_ARG, "problem needs %zu B of shared memory", smem);
   CUDA_TRY(s, launch_optimize(a, L, pr->K, smem, s->stream));
   return TAMP_OK;

@@ -8,8 +8,7 @@
 namespace tamp {
 
 constexpr int MAXJ = 8;        // joints per arm
-constexpr int SB = 5;          // arm spheres per register batch (table padded per link)
-constexpr int HB = 4;          // box spheres per register batch
+constexpr int NB = 5;          // spheres per register batch (arm table padded per link)
 constexpr int MAX_NBS = 8;     // spheres per box model
 constexpr int MAX_BOX = 32;
 constexpr int MAX_OBS = 256;
@@ -21,8 +20,8 @@ constexpr int MAX_D = 1024;
 enum SceneHdr {
   SH_NJ = 0, SH_NSPH, SH_O, SH_OPAD, SH_B, SH_NBS, SH_NSURF, SH_WORDS,
   SH_LINK0 = 8,                 // link_start[0..MAXJ+1]: 10 entries (words 8..17)
-  SH_OFF_ARM = 18, SH_OFF_SPH, SH_OFF_OBS, SH_OFF_BOX, SH_OFF_BLOC, SH_OFF_BINIT, SH_OFF_SURF,
-  SH_HDR_WORDS = 32
+  SH_OFF_ARM = 18, SH_OFF_SPH, SH_OFF_OBS, SH_OFF_BOX, SH_OFF_BLOC, SH_OFF_BINIT, SH_OFF_BINIT_HB,
+  SH_OFF_SURF, SH_HDR_WORDS = 32
 };
 // arm section: base frame (12), tool frame (12), then per joint ARM_JW words
 // frame = R row-major (9) + t (3)
@@ -35,13 +34,16 @@ constexpr float DUMMY_FAR = 1.0e4f;
 constexpr int OBS_ROWS = 16;
 // box record: half x,y,z, pad, init x,y,z,yaw, cos(yaw), sin(yaw), pad, pad
 constexpr int BOX_W = 12;
+// box spheres: local (x, y, z, r) per box; the same at the initial pose in the
+// world, plus hb = (|c|^2 - r^2) / 2 for the dot-product contact test
+// (|c_a - c_b|^2 < (r_a + r_b)^2  <=>  c_a.c_b + r_a r_b - hb_b > ha_a).
 // surface record: cx, cy, yaw, hx, hy, z_top, cos(yaw), sin(yaw)
 constexpr int SURF_W = 8;
 
 // ---- problem blob ------------------------------------------------------------
 enum ProbHdr {
   PH_D = 0, PH_K, PH_NT, PH_NCON, PH_GOAL_T, PH_NGOAL, PH_OFF_CFG, PH_OFF_ENV, PH_OFF_TERMS,
-  PH_OFF_GOAL, PH_OFF_LR, PH_OFF_SAMP, PH_WORDS, PH_HDR_WORDS = 16
+  PH_OFF_GOAL, PH_OFF_LR, PH_OFF_SAMP, PH_WORDS, PH_NSLOT, PH_OFF_SLOT, PH_HDR_WORDS = 16
 };
 constexpr int CFG_W = 24;
 enum CfgField {
@@ -51,7 +53,12 @@ enum CfgField {
   CF_PZ,                        // float: z of the placed box (place configurations)
   CF_PAD2, CF_PAD3, CF_PAD4
 };
-constexpr int ENV_W = 4;        // box, src (-1 = initial pose, else placement offset), z (float), pad
+constexpr int ENV_W = 4;        // box, src (-1 = initial pose, else placement offset), slot, pad
+constexpr int SLOT_W = 4;       // placement slot (one per Place): box, placement offset, z (float), pad
+constexpr int MAX_SLOT = 16;
+// contact test margin (m^2): the fast dot-product test flags pairs with
+// |c_a - c_b|^2 - (r_a + r_b)^2 < 2 * SS_MARGIN, well above its FP32 rounding
+constexpr float SS_MARGIN = 4e-5f;
 constexpr int TERM_W = 4;       // kind, weight (float), tol (float), is_constraint
 constexpr int GOAL_W = 4;       // box, src, z (float), pad
 constexpr int SAMP_W = 4;       // per component: kind, a (float), b (float), surface

@@ -101,107 +101,122 @@ __device__ __forceinline__ float tw(const uint32_t* terms, int t) { return __uin
 // placement variable are added (times wenv) straight into the tile's gradient.
 // Lane `sub` of the L lanes handles obstacles o = sub (mod L) and box spheres
 // e = sub (mod L).
-template <int L, int NB>
+//
+// Each environment item is first tested against the NB spheres with a cheap,
+// branch-free test that never misses a contact; only when some lane of the warp
+// reports a candidate does the warp run the exact penetration and its gradient
+// (contacts are rare: well under 1% of pairs, even for random particles).
+template <int L>
 __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy)[NB], const float (&cz)[NB],
                                          const float (&cr)[NB], float (&gx)[NB], float (&gy)[NB],
                                          float (&gz)[NB], const float* __restrict__ obs, int O, int Opad,
                                          const int* __restrict__ env, int n_env,
-                                         const float4* __restrict__ bloc, const float4* __restrict__ binit,
+                                         const float4* __restrict__ binit, const float* __restrict__ binit_hb,
+                                         const float4* __restrict__ envT4, const float* __restrict__ envThb,
                                          int NBS, const float* __restrict__ X, float* G, int pl, int sub,
                                          float wenv) {
   constexpr int PT = 32 / L;
   float J = 0.f;
-  float r2[NB];
+  float ha[NB];
 #pragma unroll
-  for (int s = 0; s < NB; ++s) r2[s] = cr[s] * cr[s];
+  for (int s = 0; s < NB; ++s)
+    ha[s] = 0.5f * fmaf(cx[s], cx[s], fmaf(cy[s], cy[s], fmaf(cz[s], cz[s], -cr[s] * cr[s]))) - SS_MARGIN;
 
-  // sphere vs oriented cuboid: u = R^T c - R^T t, q = |u| - h,
-  // sdf = ||max(q, 0)|| + min(max_i q_i, 0); active iff ||max(q,0)||^2 < r^2.
+  // sphere vs oriented cuboid.  u = R^T c - R^T t, q = |u| - h; the sphere can
+  // only touch the box if max_i q_i < r (exact test: ||max(q, 0)||^2 < r^2);
+  // sdf = ||max(q, 0)|| + min(max_i q_i, 0).
   for (int o = sub; o < O; o += L) {
     const float tpx = obs[0 * Opad + o], tpy = obs[1 * Opad + o], tpz = obs[2 * Opad + o];
     const float R00 = obs[3 * Opad + o], R01 = obs[4 * Opad + o], R02 = obs[5 * Opad + o];
     const float R10 = obs[6 * Opad + o], R11 = obs[7 * Opad + o], R12 = obs[8 * Opad + o];
     const float R20 = obs[9 * Opad + o], R21 = obs[10 * Opad + o], R22 = obs[11 * Opad + o];
     const float hx = obs[12 * Opad + o], hy = obs[13 * Opad + o], hz = obs[14 * Opad + o];
+    bool hit = false;
 #pragma unroll
     for (int s = 0; s < NB; ++s) {
       const float ux = fmaf(R00, cx[s], fmaf(R10, cy[s], fmaf(R20, cz[s], -tpx)));
       const float uy = fmaf(R01, cx[s], fmaf(R11, cy[s], fmaf(R21, cz[s], -tpy)));
       const float uz = fmaf(R02, cx[s], fmaf(R12, cy[s], fmaf(R22, cz[s], -tpz)));
-      const float qx = fabsf(ux) - hx, qy = fabsf(uy) - hy, qz = fabsf(uz) - hz;
-      const float mx = fmaxf(qx, 0.f), my = fmaxf(qy, 0.f), mz = fmaxf(qz, 0.f);
-      const float o2 = fmaf(mx, mx, fmaf(my, my, mz * mz));
-      if (o2 < r2[s]) {
-        float dux, duy, duz;
-        float sdf;
-        if (o2 > 0.f) {
-          const float d = sqrtf(o2);
-          const float inv = 1.f / d;
-          sdf = d;
-          dux = copysignf(mx * inv, ux);
-          duy = copysignf(my * inv, uy);
-          duz = copysignf(mz * inv, uz);
-        } else {
-          dux = duy = duz = 0.f;
-          if (qx >= qy && qx >= qz) {
-            sdf = qx;
-            dux = copysignf(1.f, ux);
-          } else if (qy >= qz) {
-            sdf = qy;
-            duy = copysignf(1.f, uy);
+      const float mq = fmaxf(fabsf(ux) - hx, fmaxf(fabsf(uy) - hy, fabsf(uz) - hz));
+      hit |= mq < cr[s];
+    }
+    if (__any_sync(0xffffffffu, hit)) {
+#pragma unroll
+      for (int s = 0; s < NB; ++s) {
+        const float ux = fmaf(R00, cx[s], fmaf(R10, cy[s], fmaf(R20, cz[s], -tpx)));
+        const float uy = fmaf(R01, cx[s], fmaf(R11, cy[s], fmaf(R21, cz[s], -tpy)));
+        const float uz = fmaf(R02, cx[s], fmaf(R12, cy[s], fmaf(R22, cz[s], -tpz)));
+        const float qx = fabsf(ux) - hx, qy = fabsf(uy) - hy, qz = fabsf(uz) - hz;
+        const float mx = fmaxf(qx, 0.f), my = fmaxf(qy, 0.f), mz = fmaxf(qz, 0.f);
+        const float o2 = fmaf(mx, mx, fmaf(my, my, mz * mz));
+        if (o2 < cr[s] * cr[s]) {
+          float dux, duy, duz, sdf;
+          if (o2 > 0.f) {
+            const float d = sqrtf(o2);
+            const float inv = 1.f / d;
+            sdf = d;
+            dux = copysignf(mx * inv, ux);
+            duy = copysignf(my * inv, uy);
+            duz = copysignf(mz * inv, uz);
           } else {
-            sdf = qz;
-            duz = copysignf(1.f, uz);
+            dux = duy = duz = 0.f;
+            if (qx >= qy && qx >= qz) {
+              sdf = qx;
+              dux = copysignf(1.f, ux);
+            } else if (qy >= qz) {
+              sdf = qy;
+              duy = copysignf(1.f, uy);
+            } else {
+              sdf = qz;
+              duz = copysignf(1.f, uz);
+            }
           }
+          J += cr[s] - sdf;
+          // d(pen)/dc = -R d(sdf)/du
+          gx[s] -= fmaf(R00, dux, fmaf(R01, duy, R02 * duz));
+          gy[s] -= fmaf(R10, dux, fmaf(R11, duy, R12 * duz));
+          gz[s] -= fmaf(R20, dux, fmaf(R21, duy, R22 * duz));
         }
-        J += cr[s] - sdf;
-        // d(pen)/dc = -R d(sdf)/du
-        gx[s] -= fmaf(R00, dux, fmaf(R01, duy, R02 * duz));
-        gy[s] -= fmaf(R10, dux, fmaf(R11, duy, R12 * duz));
-        gz[s] -= fmaf(R20, dux, fmaf(R21, duy, R22 * duz));
       }
     }
   }
 
-  // sphere vs sphere of the other boxes: pen = max(0, r_a + r_b - ||c_a - c_b||)
+  // sphere vs the spheres of the other boxes: pen = max(0, r_a + r_b - ||c_a - c_b||).
+  // Boxes at their initial pose read the scene's world table (same for every
+  // particle); boxes on a placement variable read this iteration's per-particle
+  // table (slot-major, particle-minor).
   for (int ei = 0; ei < n_env; ++ei) {
-    const int j = env[ei * ENV_W], src = env[ei * ENV_W + 1];
+    const int src = env[ei * ENV_W + 1];
+    const float4* E4;
+    const float* Ehb;
+    int step;
     if (src < 0) {
-      for (int e = sub; e < NBS; e += L) {
-        const float4 c = binit[j * NBS + e];
+      const int j = env[ei * ENV_W];
+      E4 = binit + j * NBS;
+      Ehb = binit_hb + j * NBS;
+      step = 1;
+    } else {
+      const int slot = env[ei * ENV_W + 2];
+      E4 = envT4 + slot * NBS * PT + pl;
+      Ehb = envThb + slot * NBS * PT + pl;
+      step = PT;
+    }
+    for (int e = sub; e < NBS; e += L) {
+      const float4 c = E4[e * step];
+      const float hb = Ehb[e * step];
+      bool hit = false;
+#pragma unroll
+      for (int s = 0; s < NB; ++s) {
+        const float dot = fmaf(cx[s], c.x, fmaf(cy[s], c.y, fmaf(cz[s], c.z, fmaf(cr[s], c.w, -hb))));
+        hit |= dot > ha[s];
+      }
+      if (__any_sync(0xffffffffu, hit)) {
+        float efx = 0.f, efy = 0.f;
 #pragma unroll
         for (int s = 0; s < NB; ++s) {
           const float dx = cx[s] - c.x, dy = cy[s] - c.y, dz = cz[s] - c.z;
           const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
           const float Rs = cr[s] + c.w;
-          if (d2 < Rs * Rs) {
-            const float d = sqrtf(d2);
-            J += Rs - d;
-            if (d > 0.f) {
-              const float inv = 1.f / d;
-              gx[s] -= dx * inv;
-              gy[s] -= dy * inv;
-              gz[s] -= dz * inv;
-            }
-          }
-        }
-      }
-    } else {
-      const float z = __int_as_float(env[ei * ENV_W + 2]);
-      const float px = X[src * PT + pl], py = X[(src + 1) * PT + pl];
-      float sn, cs;
-      sincosf(X[(src + 2) * PT + pl], &sn, &cs);
-      float fx = 0.f, fy = 0.f, tq = 0.f;
-      for (int e = sub; e < NBS; e += L) {
-        const float4 l = bloc[j * NBS + e];
-        const float rx = fmaf(cs, l.x, -sn * l.y), ry = fmaf(sn, l.x, cs * l.y);
-        const float ex = px + rx, ey = py + ry, ez = z + l.z;
-        float efx = 0.f, efy = 0.f;
-#pragma unroll
-        for (int s = 0; s < NB; ++s) {
-          const float dx = cx[s] - ex, dy = cy[s] - ey, dz = cz[s] - ez;
-          const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          const float Rs = cr[s] + l.w;
           if (d2 < Rs * Rs) {
             const float d = sqrtf(d2);
             J += Rs - d;
@@ -216,14 +231,14 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
             }
           }
         }
-        fx += efx;
-        fy += efy;
-        tq = fmaf(rx, efy, fmaf(-ry, efx, tq));
-      }
-      if (fx != 0.f || fy != 0.f || tq != 0.f) {
-        atomicAdd(&G[src * PT + pl], wenv * fx);
-        atomicAdd(&G[(src + 1) * PT + pl], wenv * fy);
-        atomicAdd(&G[(src + 2) * PT + pl], wenv * tq);
+        if (src >= 0 && (efx != 0.f || efy != 0.f)) {
+          // the environment sphere is pushed by +v: force on the box's (x, y) and
+          // torque about its centre for the yaw
+          const float rx = c.x - X[src * PT + pl], ry = c.y - X[(src + 1) * PT + pl];
+          atomicAdd(&G[src * PT + pl], wenv * efx);
+          atomicAdd(&G[(src + 1) * PT + pl], wenv * efy);
+          atomicAdd(&G[(src + 2) * PT + pl], wenv * (rx * efy - ry * efx));
+        }
       }
     }
   }
@@ -249,9 +264,17 @@ __device__ __forceinline__ float bound_dist(const float (&v)[N], const float (&l
 }
 
 // ------------------------------------------------------------------ one configuration
+// Sphere batches of one configuration are visited by one loop (a single inlined
+// copy of the collision code keeps the kernel small):
+//   phase 0  the held box, in the object frame FK(q) G(g)^-1
+//   phase 1  links n .. 1 (tip to base); after each link its joint torque is
+//            taken from the accumulated wrench and the frame steps to T_{l-1}
+//   phase 2  spheres fixed to the base (cost only)
+//   phase 3  the placed box at P(p) (Place configurations: CFreePlace)
 template <int L>
 __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __restrict__ pb, int k,
-                            const float* __restrict__ X, float* G, float* Tm, int pl, int sub) {
+                            const float* __restrict__ X, float* G, float* Tm, const float4* __restrict__ envT4,
+                            const float* __restrict__ envThb, int pl, int sub) {
   constexpr int PT = 32 / L;
   const int nj = sc[SH_NJ];
   const float* arm = reinterpret_cast<const float*>(sc + sc[SH_OFF_ARM]);
@@ -261,8 +284,10 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   const float* boxr = reinterpret_cast<const float*>(sc + sc[SH_OFF_BOX]);
   const float4* bloc = reinterpret_cast<const float4*>(sc + sc[SH_OFF_BLOC]);
   const float4* binit = reinterpret_cast<const float4*>(sc + sc[SH_OFF_BINIT]);
+  const float* binit_hb = reinterpret_cast<const float*>(sc + sc[SH_OFF_BINIT_HB]);
   const float* surf = reinterpret_cast<const float*>(sc + sc[SH_OFF_SURF]);
   const int NBS = sc[SH_NBS];
+  const int nbs_pad = (NBS + NB - 1) / NB * NB;
 
   const int* cf = reinterpret_cast<const int*>(pb + pb[PH_OFF_CFG] + k * CFG_W);
   const float* cff = reinterpret_cast<const float*>(cf);
@@ -281,31 +306,26 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
 #pragma unroll
   for (int i = 0; i < 9; ++i) R[i] = arm[i];
   t[0] = arm[9]; t[1] = arm[10]; t[2] = arm[11];
-  float sn[MAXJ], cs[MAXJ];
-#pragma unroll
-  for (int j = 0; j < MAXJ; ++j) {
-    if (j < nj) {
-      const float* Jp = arm + 24 + j * ARM_JW;
-      sincosf(XV(qo + j) + Jp[4], &sn[j], &cs[j]);
-      rz_right(R, cs[j], sn[j]);
-      const float a = Jp[0], d = Jp[1];
-      t[0] = fmaf(d, R[2], fmaf(a, R[0], t[0]));
-      t[1] = fmaf(d, R[5], fmaf(a, R[3], t[1]));
-      t[2] = fmaf(d, R[8], fmaf(a, R[6], t[2]));
-      rx_right(R, Jp[2], Jp[3]);
-    }
+  for (int j = 0; j < nj; ++j) {
+    const float* Jp = arm + 24 + j * ARM_JW;
+    float sj, cj;
+    sincosf(XV(qo + j) + Jp[4], &sj, &cj);
+    rz_right(R, cj, sj);
+    const float a = Jp[0], d = Jp[1];
+    t[0] = fmaf(d, R[2], fmaf(a, R[0], t[0]));
+    t[1] = fmaf(d, R[5], fmaf(a, R[3], t[1]));
+    t[2] = fmaf(d, R[8], fmaf(a, R[6], t[2]));
+    rx_right(R, Jp[2], Jp[3]);
   }
+  const float* tl = arm + 12;  // tool frame (R row-major, t)
   // end effector = T_n * tool
   float Re[9], te[3];
-  {
-    const float* tl = arm + 12;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 3; ++i) {
 #pragma unroll
-      for (int j = 0; j < 3; ++j)
-        Re[3 * i + j] = fmaf(R[3 * i], tl[j], fmaf(R[3 * i + 1], tl[3 + j], R[3 * i + 2] * tl[6 + j]));
-      te[i] = fmaf(R[3 * i], tl[9], fmaf(R[3 * i + 1], tl[10], fmaf(R[3 * i + 2], tl[11], t[i])));
-    }
+    for (int j = 0; j < 3; ++j)
+      Re[3 * i + j] = fmaf(R[3 * i], tl[j], fmaf(R[3 * i + 1], tl[3 + j], R[3 * i + 2] * tl[6 + j]));
+    te[i] = fmaf(R[3 * i], tl[9], fmaf(R[3 * i + 1], tl[10], fmaf(R[3 * i + 2], tl[11], t[i])));
   }
 
   // ---------------- Kin: target P(p) G(g)
@@ -319,193 +339,169 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   float sy, cy;
   sincosf(pyaw, &sy, &cy);
   const float rgx = fmaf(cy, gxv, -sy * gyv), rgy = fmaf(sy, gxv, cy * gyv);
-  const float ttx = px + rgx, tty = py + rgy, ttz = pz + gzv;
   float s2, c2;
   sincosf(pyaw + gyaw, &s2, &c2);
-  // M = Re^T R_tgt, R_tgt = [[c2, s2, 0], [s2, -c2, 0], [0, 0, -1]]
-  float Mr[9];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const float e0 = Re[i], e1 = Re[3 + i], e2 = Re[6 + i];
-    Mr[3 * i] = fmaf(e0, c2, e1 * s2);
-    Mr[3 * i + 1] = fmaf(e0, s2, -e1 * c2);
-    Mr[3 * i + 2] = -e2;
-  }
-  const float wx = Mr[7] - Mr[5], wy = Mr[2] - Mr[6], wz = Mr[3] - Mr[1];
-  const float wn = sqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz)));
-  const float e_rot = atan2f(0.5f * wn, 0.5f * (Mr[0] + Mr[4] + Mr[8] - 1.f));
-  const float dlx = te[0] - ttx, dly = te[1] - tty, dlz = te[2] - ttz;
-  const float e_pos = sqrtf(fmaf(dlx, dlx, fmaf(dly, dly, dlz * dlz)));
-  // world wrench on the end effector from Kin (lane 0 only)
-  float fkx = 0.f, fky = 0.f, fkz = 0.f;
-  if (e_pos > 0.f) {
-    const float s = w_kp / e_pos;
-    fkx = s * dlx; fky = s * dly; fkz = s * dlz;
-  }
-  float ubx = 0.f, uby = 0.f, ubz = 0.f;  // R_EE * unit axis of M, times w_kr
-  if (wn > 0.f) {
-    const float s = w_kr / wn;
-    const float ux = s * wx, uy = s * wy, uz = s * wz;
-    ubx = fmaf(Re[0], ux, fmaf(Re[1], uy, Re[2] * uz));
-    uby = fmaf(Re[3], ux, fmaf(Re[4], uy, Re[5] * uz));
-    ubz = fmaf(Re[6], ux, fmaf(Re[7], uy, Re[8] * uz));
-  }
-  float F[3] = {k0 * fkx, k0 * fky, k0 * fkz};
-  float Mw[3] = {k0 * (te[1] * fkz - te[2] * fky - ubx), k0 * (te[2] * fkx - te[0] * fkz - uby),
-                 k0 * (te[0] * fky - te[1] * fkx - ubz)};
-  // gradients of the target: dJ/dt_tgt = -f, dJ/domega_tgt = ub
-  float gg[4];  // grasp x, y, z, yaw
-  gg[0] = k0 * (-(cy * fkx + sy * fky));
-  gg[1] = k0 * (-(-sy * fkx + cy * fky));
-  gg[2] = k0 * (-fkz);
-  gg[3] = k0 * ubz;
-  float gp[3];  // placement x, y, yaw of the target (if it is a variable)
-  gp[0] = k0 * (-fkx);
-  gp[1] = k0 * (-fky);
-  gp[2] = k0 * (fkx * rgy - fky * rgx + ubz);
-
-  float tau[MAXJ];
-#pragma unroll
-  for (int j = 0; j < MAXJ; ++j) tau[j] = 0.f;
-  float J_hold = 0.f, J_place = 0.f;
-
-  // ---------------- held box spheres at FK(q) G(g)^-1 (attached to the end effector)
+  float F[3], Mw[3], gg[4], gp[3];
+  float e_pos, e_rot;
   {
-    float sg_, cg_;
-    sincosf(gyaw, &sg_, &cg_);
-    float Ro[9];  // R_obj = Re * [[cg, sg, 0], [sg, -cg, 0], [0, 0, -1]]
+    const float ttx = px + rgx, tty = py + rgy, ttz = pz + gzv;
+    // M = Re^T R_tgt, R_tgt = [[c2, s2, 0], [s2, -c2, 0], [0, 0, -1]]
+    float Mr[9];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      Ro[3 * i] = fmaf(cg_, Re[3 * i], sg_ * Re[3 * i + 1]);
-      Ro[3 * i + 1] = fmaf(sg_, Re[3 * i], -cg_ * Re[3 * i + 1]);
-      Ro[3 * i + 2] = -Re[3 * i + 2];
+      const float e0 = Re[i], e1 = Re[3 + i], e2 = Re[6 + i];
+      Mr[3 * i] = fmaf(e0, c2, e1 * s2);
+      Mr[3 * i + 1] = fmaf(e0, s2, -e1 * c2);
+      Mr[3 * i + 2] = -e2;
     }
-    for (int e0 = 0; e0 < NBS; e0 += HB) {
-      float cx[HB], cyy[HB], cz[HB], cr[HB], vx[HB], vy[HB], gx[HB], gyy[HB], gz[HB];
-#pragma unroll
-      for (int s = 0; s < HB; ++s) {
-        gx[s] = gyy[s] = gz[s] = 0.f;
-        if (e0 + s < NBS) {
-          const float4 l = bloc[b * NBS + e0 + s];
-          vx[s] = l.x - gxv; vy[s] = l.y - gyv;
-          const float vz = l.z - gzv;
-          cx[s] = fmaf(Ro[0], vx[s], fmaf(Ro[1], vy[s], fmaf(Ro[2], vz, te[0])));
-          cyy[s] = fmaf(Ro[3], vx[s], fmaf(Ro[4], vy[s], fmaf(Ro[5], vz, te[1])));
-          cz[s] = fmaf(Ro[6], vx[s], fmaf(Ro[7], vy[s], fmaf(Ro[8], vz, te[2])));
-          cr[s] = l.w;
-        } else {
-          cx[s] = cyy[s] = cz[s] = DUMMY_FAR;
-          cr[s] = 0.f; vx[s] = vy[s] = 0.f;
-        }
-      }
-      J_hold += collide<L, HB>(cx, cyy, cz, cr, gx, gyy, gz, obs, O, Opad, env, n_env, bloc, binit, NBS, X, G,
-                               pl, sub, w_cf);
-#pragma unroll
-      for (int s = 0; s < HB; ++s) {
-        const float fx = w_cf * gx[s], fy = w_cf * gyy[s], fz = w_cf * gz[s];
-        F[0] += fx; F[1] += fy; F[2] += fz;
-        Mw[0] += cyy[s] * fz - cz[s] * fy;
-        Mw[1] += cz[s] * fx - cx[s] * fz;
-        Mw[2] += cx[s] * fy - cyy[s] * fx;
-        // object-frame force G = R_obj^T f; c = t_EE + R_obj (l - g)
-        const float Gx = fmaf(Ro[0], fx, fmaf(Ro[3], fy, Ro[6] * fz));
-        const float Gy = fmaf(Ro[1], fx, fmaf(Ro[4], fy, Ro[7] * fz));
-        const float Gz = fmaf(Ro[2], fx, fmaf(Ro[5], fy, Ro[8] * fz));
-        gg[0] -= Gx; gg[1] -= Gy; gg[2] -= Gz;
-        gg[3] -= Gy * vx[s] - Gx * vy[s];
-      }
+    const float wx = Mr[7] - Mr[5], wy = Mr[2] - Mr[6], wz = Mr[3] - Mr[1];
+    const float wn = sqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz)));
+    e_rot = atan2f(0.5f * wn, 0.5f * (Mr[0] + Mr[4] + Mr[8] - 1.f));
+    const float dlx = te[0] - ttx, dly = te[1] - tty, dlz = te[2] - ttz;
+    e_pos = sqrtf(fmaf(dlx, dlx, fmaf(dly, dly, dlz * dlz)));
+    // world wrench on the end effector from Kin (lane 0 only)
+    float fkx = 0.f, fky = 0.f, fkz = 0.f;
+    if (e_pos > 0.f) {
+      const float s = w_kp / e_pos;
+      fkx = s * dlx; fky = s * dly; fkz = s * dlz;
     }
+    float ubx = 0.f, uby = 0.f, ubz = 0.f;  // w_kr * R_EE * (unit axis of M)
+    if (wn > 0.f) {
+      const float s = w_kr / wn;
+      const float ux = s * wx, uy = s * wy, uz = s * wz;
+      ubx = fmaf(Re[0], ux, fmaf(Re[1], uy, Re[2] * uz));
+      uby = fmaf(Re[3], ux, fmaf(Re[4], uy, Re[5] * uz));
+      ubz = fmaf(Re[6], ux, fmaf(Re[7], uy, Re[8] * uz));
+    }
+    F[0] = k0 * fkx; F[1] = k0 * fky; F[2] = k0 * fkz;
+    Mw[0] = k0 * (te[1] * fkz - te[2] * fky - ubx);
+    Mw[1] = k0 * (te[2] * fkx - te[0] * fkz - uby);
+    Mw[2] = k0 * (te[0] * fky - te[1] * fkx - ubz);
+    // gradients of the target: dJ/dt_tgt = -f, dJ/domega_tgt = ub
+    gg[0] = k0 * (-(cy * fkx + sy * fky));
+    gg[1] = k0 * (-(-sy * fkx + cy * fky));
+    gg[2] = k0 * (-fkz);
+    gg[3] = k0 * ubz;
+    gp[0] = k0 * (-fkx);
+    gp[1] = k0 * (-fky);
+    gp[2] = k0 * (fkx * rgy - fky * rgx + ubz);
   }
+  float J_hold = 0.f, J_place = 0.f;
+  float gpc[3] = {0.f, 0.f, 0.f};
+  float sgr, cgr;  // grasp yaw: R_G = Rz(yaw) Rx(pi) = [[c, s, 0], [s, -c, 0], [0, 0, -1]] (symmetric)
+  sincosf(gyaw, &sgr, &cgr);
 
-  // ---------------- reverse sweep over the links (tip to base)
-  for (int l = nj; l >= 1; --l) {
-    const int ls = sc[SH_LINK0 + l], le = sc[SH_LINK0 + l + 1];
-    for (int s0 = ls; s0 < le; s0 += SB) {
-      float cx[SB], cyy[SB], cz[SB], cr[SB], gx[SB], gyy[SB], gz[SB];
-#pragma unroll
-      for (int s = 0; s < SB; ++s) {
-        const float4 p = sph[s0 + s];
-        cx[s] = fmaf(R[0], p.x, fmaf(R[1], p.y, fmaf(R[2], p.z, t[0])));
-        cyy[s] = fmaf(R[3], p.x, fmaf(R[4], p.y, fmaf(R[5], p.z, t[1])));
-        cz[s] = fmaf(R[6], p.x, fmaf(R[7], p.y, fmaf(R[8], p.z, t[2])));
-        cr[s] = p.w;
-        gx[s] = gyy[s] = gz[s] = 0.f;
+  // ---------------- batches: held box, links n..1, base, placed box
+  // Every batch is c = R l' + t with (R, t) the current link frame, except the
+  // placed box (phase 3), which overwrites (R, t) with P(p) once the links are done.
+  // A held-box sphere l (object frame) is first moved into frame n:
+  // l' = tool (G(g)^-1 l) = t_tool + R_tool R_G (l - g).
+  int phase = 0, l = nj;
+  int s0 = 0, s1 = nbs_pad;
+  for (;;) {
+    if (s0 >= s1) {
+      if (phase == 0) {
+        phase = 1;
+        s0 = sc[SH_LINK0 + l]; s1 = sc[SH_LINK0 + l + 1];
+      } else if (phase == 1) {
+        // joint l: T_{l-1} = T_l Rx(-alpha) Tx(-a) Tz(-d) Rz(-theta); it turns the
+        // links >= l about z_{l-1} through o_{l-1}: dJ/dq_l = z.M + (o x z).F
+        const float* Jp = arm + 24 + (l - 1) * ARM_JW;
+        rx_right(R, Jp[2], -Jp[3]);
+        const float a = Jp[0], d = Jp[1];
+        t[0] -= fmaf(a, R[0], d * R[2]);
+        t[1] -= fmaf(a, R[3], d * R[5]);
+        t[2] -= fmaf(a, R[6], d * R[8]);
+        const float zx = R[2], zy = R[5], zz = R[8];
+        const float ox = t[1] * zz - t[2] * zy, oy = t[2] * zx - t[0] * zz, oz = t[0] * zy - t[1] * zx;
+        const float tq =
+            fmaf(zx, Mw[0], fmaf(zy, Mw[1], fmaf(zz, Mw[2], fmaf(ox, F[0], fmaf(oy, F[1], oz * F[2])))));
+        atomicAdd(&G[(qo + l - 1) * PT + pl], tq);
+        float sl, cl;
+        sincosf(XV(qo + l - 1) + Jp[4], &sl, &cl);
+        rz_right(R, cl, -sl);
+        --l;
+        if (l == 0) phase = 2;
+        s0 = sc[SH_LINK0 + l]; s1 = sc[SH_LINK0 + l + 1];
+      } else if (phase == 2 && kind == 1) {
+        phase = 3;
+        s0 = 0; s1 = nbs_pad;
+        R[0] = cy; R[1] = -sy; R[2] = 0.f;
+        R[3] = sy; R[4] = cy; R[5] = 0.f;
+        R[6] = 0.f; R[7] = 0.f; R[8] = 1.f;
+        t[0] = px; t[1] = py; t[2] = cff[CF_PZ];
+      } else {
+        break;
       }
-      J_hold += collide<L, SB>(cx, cyy, cz, cr, gx, gyy, gz, obs, O, Opad, env, n_env, bloc, binit, NBS, X, G,
-                               pl, sub, w_cf);
-#pragma unroll
-      for (int s = 0; s < SB; ++s) {
-        const float fx = w_cf * gx[s], fy = w_cf * gyy[s], fz = w_cf * gz[s];
-        F[0] += fx; F[1] += fy; F[2] += fz;
-        Mw[0] += cyy[s] * fz - cz[s] * fy;
-        Mw[1] += cz[s] * fx - cx[s] * fz;
-        Mw[2] += cx[s] * fy - cyy[s] * fx;
-      }
+      continue;
     }
-    // T_{l-1} = T_l Rx(-alpha) Tx(-a) Tz(-d) Rz(-theta); joint l turns about z_{l-1} through o_{l-1}
-    const float* Jp = arm + 24 + (l - 1) * ARM_JW;
-    rx_right(R, Jp[2], -Jp[3]);
-    const float a = Jp[0], d = Jp[1];
-    t[0] -= fmaf(a, R[0], d * R[2]);
-    t[1] -= fmaf(a, R[3], d * R[5]);
-    t[2] -= fmaf(a, R[6], d * R[8]);
-    const float zx = R[2], zy = R[5], zz = R[8];
-    const float ox = t[1] * zz - t[2] * zy, oy = t[2] * zx - t[0] * zz, oz = t[0] * zy - t[1] * zx;
-    const float tq = fmaf(zx, Mw[0], fmaf(zy, Mw[1], fmaf(zz, Mw[2], fmaf(ox, F[0], fmaf(oy, F[1], oz * F[2])))));
+    float cx[NB], cyy[NB], cz[NB], cr[NB], gx[NB], gyy[NB], gz[NB];
 #pragma unroll
-    for (int j = 0; j < MAXJ; ++j)
-      if (j == l - 1) tau[j] = tq;
-    float snl = 0.f, csl = 1.f;
-#pragma unroll
-    for (int j = 0; j < MAXJ; ++j)
-      if (j == l - 1) { snl = sn[j]; csl = cs[j]; }
-    rz_right(R, csl, -snl);
-  }
-  // spheres fixed to the base frame (link 0): cost only
-  for (int s0 = sc[SH_LINK0]; s0 < sc[SH_LINK0 + 1]; s0 += SB) {
-    float cx[SB], cyy[SB], cz[SB], cr[SB], gx[SB], gyy[SB], gz[SB];
-#pragma unroll
-    for (int s = 0; s < SB; ++s) {
-      const float4 p = sph[s0 + s];
+    for (int s = 0; s < NB; ++s) {
+      float4 p;
+      if (phase == 0 || phase == 3) {
+        p = (s0 + s < NBS) ? bloc[b * NBS + s0 + s] : make_float4(DUMMY_FAR, DUMMY_FAR, DUMMY_FAR, 0.f);
+        if (phase == 0 && s0 + s < NBS) {
+          const float vx = p.x - gxv, vy = p.y - gyv, vz = p.z - gzv;
+          const float wx = fmaf(cgr, vx, sgr * vy), wy = fmaf(sgr, vx, -cgr * vy), wz = -vz;
+          p.x = fmaf(tl[0], wx, fmaf(tl[1], wy, fmaf(tl[2], wz, tl[9])));
+          p.y = fmaf(tl[3], wx, fmaf(tl[4], wy, fmaf(tl[5], wz, tl[10])));
+          p.z = fmaf(tl[6], wx, fmaf(tl[7], wy, fmaf(tl[8], wz, tl[11])));
+        }
+      } else {
+        p = sph[s0 + s];
+      }
       cx[s] = fmaf(R[0], p.x, fmaf(R[1], p.y, fmaf(R[2], p.z, t[0])));
       cyy[s] = fmaf(R[3], p.x, fmaf(R[4], p.y, fmaf(R[5], p.z, t[1])));
       cz[s] = fmaf(R[6], p.x, fmaf(R[7], p.y, fmaf(R[8], p.z, t[2])));
       cr[s] = p.w;
       gx[s] = gyy[s] = gz[s] = 0.f;
     }
-    J_hold += collide<L, SB>(cx, cyy, cz, cr, gx, gyy, gz, obs, O, Opad, env, n_env, bloc, binit, NBS, X, G, pl,
-                             sub, w_cf);
-  }
-
-  // ---------------- CFreePlace: the placed box at P(p)
-  float gpc[3] = {0.f, 0.f, 0.f};
-  if (kind == 1) {
-    const float pzb = cff[CF_PZ];
-    for (int e0 = 0; e0 < NBS; e0 += HB) {
-      float cx[HB], cyy[HB], cz[HB], cr[HB], rx[HB], ry[HB], gx[HB], gyy[HB], gz[HB];
+    const float wenv = phase == 3 ? w_cp : w_cf;
+    const float Jb = collide<L>(cx, cyy, cz, cr, gx, gyy, gz, obs, O, Opad, env, n_env, binit, binit_hb, envT4,
+                                envThb, NBS, X, G, pl, sub, wenv);
+    if (phase == 3) {
+      J_place += Jb;
 #pragma unroll
-      for (int s = 0; s < HB; ++s) {
-        gx[s] = gyy[s] = gz[s] = 0.f;
-        if (e0 + s < NBS) {
-          const float4 l = bloc[b * NBS + e0 + s];
-          rx[s] = fmaf(cy, l.x, -sy * l.y);
-          ry[s] = fmaf(sy, l.x, cy * l.y);
-          cx[s] = px + rx[s]; cyy[s] = py + ry[s]; cz[s] = pzb + l.z;
-          cr[s] = l.w;
-        } else {
-          cx[s] = cyy[s] = cz[s] = DUMMY_FAR;
-          cr[s] = 0.f; rx[s] = ry[s] = 0.f;
+      for (int s = 0; s < NB; ++s) {
+        const float fx = w_cp * gx[s], fy = w_cp * gyy[s];
+        gpc[0] += fx;
+        gpc[1] += fy;
+        gpc[2] += (cx[s] - px) * fy - (cyy[s] - py) * fx;
+      }
+    } else {
+      J_hold += Jb;
+      if (phase <= 1) {
+#pragma unroll
+        for (int s = 0; s < NB; ++s) {
+          const float fx = w_cf * gx[s], fy = w_cf * gyy[s], fz = w_cf * gz[s];
+          F[0] += fx; F[1] += fy; F[2] += fz;
+          Mw[0] += cyy[s] * fz - cz[s] * fy;
+          Mw[1] += cz[s] * fx - cx[s] * fz;
+          Mw[2] += cx[s] * fy - cyy[s] * fx;
+        }
+        if (phase == 0) {
+          // c = t_EE + R_obj (l - g): the object-frame force G = R_obj^T f moves g
+          // by -G and the grasp yaw by -(G x (l - g))_z; R_obj = R R_tool R_G
+#pragma unroll
+          for (int s = 0; s < NB; ++s) {
+            if (s0 + s >= NBS) continue;
+            const float fx = w_cf * gx[s], fy = w_cf * gyy[s], fz = w_cf * gz[s];
+            const float ax = fmaf(R[0], fx, fmaf(R[3], fy, R[6] * fz));
+            const float ay = fmaf(R[1], fx, fmaf(R[4], fy, R[7] * fz));
+            const float az = fmaf(R[2], fx, fmaf(R[5], fy, R[8] * fz));
+            const float bx = fmaf(tl[0], ax, fmaf(tl[3], ay, tl[6] * az));
+            const float by = fmaf(tl[1], ax, fmaf(tl[4], ay, tl[7] * az));
+            const float bz = fmaf(tl[2], ax, fmaf(tl[5], ay, tl[8] * az));
+            const float Gx = fmaf(cgr, bx, sgr * by), Gy = fmaf(sgr, bx, -cgr * by), Gz = -bz;
+            const float4 lp = bloc[b * NBS + s0 + s];
+            gg[0] -= Gx; gg[1] -= Gy; gg[2] -= Gz;
+            gg[3] -= Gy * (lp.x - gxv) - Gx * (lp.y - gyv);
+          }
         }
       }
-      J_place += collide<L, HB>(cx, cyy, cz, cr, gx, gyy, gz, obs, O, Opad, env, n_env, bloc, binit, NBS, X, G,
-                                pl, sub, w_cp);
-#pragma unroll
-      for (int s = 0; s < HB; ++s) {
-        gpc[0] += w_cp * gx[s];
-        gpc[1] += w_cp * gyy[s];
-        gpc[2] += w_cp * (rx[s] * gyy[s] - ry[s] * gx[s]);
-      }
     }
+    s0 += NB;
   }
 
   // ---------------- reduce over the L lanes of this (particle, configuration)
@@ -514,8 +510,6 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
     J_hold += __shfl_xor_sync(0xffffffffu, J_hold, m);
     J_place += __shfl_xor_sync(0xffffffffu, J_place, m);
 #pragma unroll
-    for (int j = 0; j < MAXJ; ++j) tau[j] += __shfl_xor_sync(0xffffffffu, tau[j], m);
-#pragma unroll
     for (int i = 0; i < 4; ++i) gg[i] += __shfl_xor_sync(0xffffffffu, gg[i], m);
 #pragma unroll
     for (int i = 0; i < 3; ++i) gpc[i] += __shfl_xor_sync(0xffffffffu, gpc[i], m);
@@ -523,7 +517,6 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   if (sub != 0) return;
 
   // ---------------- per-configuration scalar terms (lane 0)
-  // joint limits
   float jl = 0.f;
   {
     float e2 = 0.f;
@@ -546,7 +539,7 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
         const float* Jp = arm + 24 + j * ARM_JW;
         const float q = XV(qo + j);
         const float gj = q > Jp[6] ? ex[j] * inv : (q < Jp[5] ? -ex[j] * inv : 0.f);
-        G[(qo + j) * PT + pl] = tau[j] + gj;
+        if (gj != 0.f) atomicAdd(&G[(qo + j) * PT + pl], gj);
       }
     }
   }
@@ -571,8 +564,8 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
     float J = 0.f;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const float lx = (c & 1 ? 1.f : -1.f) * br[0], ly = (c & 2 ? 1.f : -1.f) * br[1];
-      const float rx = fmaf(cy, lx, -sy * ly), ry = fmaf(sy, lx, cy * ly);
+      const float lx_ = (c & 1 ? 1.f : -1.f) * br[0], ly_ = (c & 2 ? 1.f : -1.f) * br[1];
+      const float rx = fmaf(cy, lx_, -sy * ly_), ry = fmaf(sy, lx_, cy * ly_);
       const float wx_ = px + rx - scx, wy_ = py + ry - scy;
       const float v[2] = {fmaf(scs, wx_, ssn * wy_), fmaf(-ssn, wx_, scs * wy_)};
       const float lo[2] = {-shx, -shy}, hi[2] = {shx, shy};
@@ -645,7 +638,7 @@ __device__ void eval_goal(const uint32_t* __restrict__ sc, const uint32_t* __res
 
 // ------------------------------------------------------------------ fused optimisation kernel
 template <int L>
-__global__ void __launch_bounds__(512, 1) optimize_kernel(OptArgs a) {
+__global__ void __launch_bounds__(384, 1) optimize_kernel(OptArgs a) {
   constexpr int PT = 32 / L;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
@@ -654,12 +647,15 @@ __global__ void __launch_bounds__(512, 1) optimize_kernel(OptArgs a) {
   uint32_t* s_sc = reinterpret_cast<uint32_t*>(smem_raw);
   uint32_t* s_pb = s_sc + sw;
   const int D = a.prob[PH_D], K = a.prob[PH_K], NT = a.prob[PH_NT];
+  const int NSLOT = a.prob[PH_NSLOT], NBS = a.scene[SH_NBS];
   float* sx = reinterpret_cast<float*>(s_pb + pw);
   float* sm = sx + D * PT;
   float* sv = sm + D * PT;
   float* sg = sv + D * PT;
   float* st = sg + D * PT;
-  int* sflag = reinterpret_cast<int*>(st + NT * PT);
+  float4* envT4 = reinterpret_cast<float4*>(st + NT * PT);   // [slot][e][particle]
+  float* envThb = reinterpret_cast<float*>(envT4 + NSLOT * NBS * PT);
+  int* sflag = reinterpret_cast<int*>(envThb + NSLOT * NBS * PT);
 
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int tile0 = blockIdx.x * PT;
@@ -701,8 +697,25 @@ __global__ void __launch_bounds__(512, 1) optimize_kernel(OptArgs a) {
   const float* lr = reinterpret_cast<const float*>(s_pb + s_pb[PH_OFF_LR]);
   const int goal_warp = (K - 1) % W;
 
+  const int* slots = reinterpret_cast<const int*>(s_pb + s_pb[PH_OFF_SLOT]);
+  const float4* bloc = reinterpret_cast<const float4*>(s_sc + s_sc[SH_OFF_BLOC]);
   for (int it = 0;; ++it) {
-    for (int k = w; k < K; k += W) eval_config<L>(s_sc, s_pb, k, sx, sg, st, pl, sub);
+    // world spheres of every box standing on a placement variable, once per particle
+    for (int i = tid; i < NSLOT * NBS * PT; i += nthr) {
+      const int p = i % PT, se = i / PT, slot = se / NBS, e = se % NBS;
+      const int* sr = slots + slot * SLOT_W;
+      const int po = sr[1];
+      float sn, cs;
+      sincosf(sx[(po + 2) * PT + p], &sn, &cs);
+      const float4 l = bloc[sr[0] * NBS + e];
+      const float ex = sx[po * PT + p] + fmaf(cs, l.x, -sn * l.y);
+      const float ey = sx[(po + 1) * PT + p] + fmaf(sn, l.x, cs * l.y);
+      const float ez = __int_as_float(sr[2]) + l.z;
+      envT4[i] = make_float4(ex, ey, ez, l.w);
+      envThb[i] = 0.5f * fmaf(ex, ex, fmaf(ey, ey, fmaf(ez, ez, -l.w * l.w)));
+    }
+    __syncthreads();
+    for (int k = w; k < K; k += W) eval_config<L>(s_sc, s_pb, k, sx, sg, st, envT4, envThb, pl, sub);
     if (w == goal_warp && sub == 0) eval_goal<L>(s_sc, s_pb, sx, sg, st, pl);
     __syncthreads();
     // Eq. 3 at x_t
@@ -828,8 +841,8 @@ static cudaError_t launch_opt(const OptArgs& a, int K, size_t smem, cudaStream_t
     if (e != cudaSuccess) return e;
     attr_bytes = smem;
   }
-  const int per = (K + 15) / 16;          // configurations per warp
-  const int W = (K + per - 1) / per;      // <= 16 warps
+  const int per = (K + 11) / 12;          // configurations per warp
+  const int W = (K + per - 1) / per;      // <= 12 warps (384 threads)
   const int grid = (a.P + PT - 1) / PT;
   if (grid == 0) return cudaSuccess;
   optimize_kernel<L><<<grid, W * 32, smem, st>>>(a);
@@ -855,10 +868,11 @@ cudaError_t launch_sample(const uint32_t* pb, const uint32_t* sc, float* x, floa
   return cudaGetLastError();
 }
 
-size_t optimize_smem_bytes(int scene_words, int prob_words, int D, int NT, int L) {
+size_t optimize_smem_bytes(int scene_words, int prob_words, int D, int NT, int nslot, int nbs, int L) {
   const int PT = 32 / L;
   const size_t sw = (scene_words + 3) & ~3, pw = (prob_words + 3) & ~3;
-  return 4 * (sw + pw) + 4 * (4 * static_cast<size_t>(D) * PT + static_cast<size_t>(NT) * PT + PT);
+  return 4 * (sw + pw) +
+         4 * (4 * static_cast<size_t>(D) * PT + static_cast<size_t>(NT) * PT + 5 * static_cast<size_t>(nslot) * nbs * PT + PT);
 }
 
 }  // namespace tamp

@@ -10,10 +10,13 @@ Per configuration (arm with n joints, S arm spheres, the held box's NBS spheres)
   forward kinematics           48 FLOP per joint (Rz, DH translation, Rx)
   reverse sweep                48 FLOP per joint (inverse transforms) + 21 (torque)
   sphere centres               18 FLOP per sphere (3x3 rotation + translation)
+  contact-test preparation      8 FLOP per sphere ((|c|^2 - r^2) / 2)
   wrench accumulation          15 FLOP per sphere
-  sphere vs cuboid, forward    30 FLOP per pair (rotate 18, |u|-h 3, clamp 3, norm^2 5, test 1)
-  sphere vs sphere, forward    11 FLOP per pair (difference 3, norm^2 5, radius sum/square 2, test 1)
-  moving-box sphere centres     9 FLOP per environment sphere per register batch
+  held-box sphere into frame n 16 FLOP per sphere (G(g)^-1, tool)
+  sphere vs cuboid test        24 FLOP per pair (box-frame point 18, |u| - h 3, max 2, compare 1)
+  sphere vs sphere test         9 FLOP per pair (c_a.c_b + r_a r_b - hb: 4 FMA, compare 1)
+Per iteration and particle: 17 FLOP per sphere of every box standing on a
+placement variable (world centre and (|c|^2 - r^2) / 2).
 Adam: 12 FLOP per component.
 """
 from __future__ import annotations
@@ -23,12 +26,13 @@ import math
 FK_JOINT = 48
 SWEEP_JOINT = 48 + 21
 SPHERE_XFORM = 18
+SPHERE_PREP = 8
 SPHERE_WRENCH = 15
-PAIR_OBB = 30
-PAIR_SS = 11
-ENV_SPHERE = 9
+HELD_SPHERE = 16
+PAIR_OBB = 24
+PAIR_SS = 9
+ENV_SPHERE = 17
 ADAM = 12
-SB, HB = 5, 4
 
 
 def _walk(scene, actions):
@@ -48,21 +52,19 @@ def _walk(scene, actions):
 
 def eval_flops(scene, actions) -> int:
     n = scene.dh_a.shape[0]
-    links = list(scene.sphere_link)
-    S_pad = sum(int(math.ceil(links.count(l) / SB)) * SB for l in range(n + 1))
+    S = len(scene.sphere_link)              # real spheres only: padding slots are overhead
     nbs = scene.box_spheres.shape[1]
-    nbs_pad = int(math.ceil(nbs / HB)) * HB
     O = scene.obs_center.shape[0]
     total = 0
+    n_place = 0
     for kind, b, env in _walk(scene, actions):
-        sph = S_pad + nbs_pad + (nbs_pad if kind == 1 else 0)
-        batches = S_pad // SB + nbs_pad // HB * (2 if kind == 1 else 1)
+        sph = S + nbs + (nbs if kind == 1 else 0)
         env_sph = len(env) * nbs
-        moving = sum(nbs for _j, mv in env if mv)
         total += n * (FK_JOINT + SWEEP_JOINT)
-        total += sph * (SPHERE_XFORM + SPHERE_WRENCH)
+        total += sph * (SPHERE_XFORM + SPHERE_PREP + SPHERE_WRENCH) + nbs * HELD_SPHERE
         total += sph * O * PAIR_OBB + sph * env_sph * PAIR_SS
-        total += batches * moving * ENV_SPHERE
+        n_place += kind == 1
+    total += n_place * nbs * ENV_SPHERE
     return total
 
 

@@ -201,7 +201,8 @@ def stress_problem(seed: int = 5001):
     """12 boxes, 64 cuboids, 100-sphere arm, 12 Pick-Place pairs (D = 252)."""
     spl = [15, 15, 14, 14, 14, 14, 14]
     sc = make_scene(seed, n_boxes=12, n_obs=64, region_size=(0.5, 0.5), spheres_per_link=spl,
-                    name="stress-12box", box_radius=(0.45, 1.0), obs_radius=(0.3, 1.6))
+                    name="stress-12box", box_radius=(0.45, 1.1), obs_radius=(0.3, 2.2),
+                    obs_edges=(0.05, 0.20))
     return sc, pick_place_skeleton(range(12), goal=True)
 
 

@@ -130,11 +130,12 @@ def test_first_satisfying_iteration_of_witness(pkg):
     pid = scene.set_skeleton(acts)
     X = np.repeat(x.numpy(), 5, axis=0)
     scene.set_particles(pid, X.T.astype(np.float32))
+    q0 = scene.query(pid, 5)               # the check at x_0 alone
     scene.optimize(pid, 3)
     q = scene.query(pid, 5)
     scene.close()
+    assert q0["n_satisfied"] == 5 and q0["first_iter"] == 0
     assert q["first_iter"] == 0
-    assert q["n_satisfied"] == 5
 
 
 def test_optimize_trajectory_tracks_oracle(pkg):
