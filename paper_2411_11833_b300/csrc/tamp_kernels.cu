@@ -125,8 +125,12 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
   // sphere vs oriented cuboid.  u = R^T c - R^T t, q = |u| - h; the sphere can
   // only touch the box if max_i q_i < r (exact test: ||max(q, 0)||^2 < r^2);
   // sdf = ||max(q, 0)|| + min(max_i q_i, 0).
-  for (int o = sub; o < O; o += L) {
-    const float tpx = obs[0 * Opad + o], tpy = obs[1 * Opad + o], tpz = obs[2 * Opad + o];
+  // every lane runs the same trip count (the warp votes below need all 32
+  // lanes); a lane past the end tests a far-away, zero-size box
+  for (int o0 = 0; o0 < O; o0 += L) {
+    const int o = o0 + sub < O ? o0 + sub : 0;
+    const float far = o0 + sub < O ? 0.f : DUMMY_FAR;
+    const float tpx = obs[0 * Opad + o] + far, tpy = obs[1 * Opad + o], tpz = obs[2 * Opad + o];
     const float R00 = obs[3 * Opad + o], R01 = obs[4 * Opad + o], R02 = obs[5 * Opad + o];
     const float R10 = obs[6 * Opad + o], R11 = obs[7 * Opad + o], R12 = obs[8 * Opad + o];
     const float R20 = obs[9 * Opad + o], R21 = obs[10 * Opad + o], R22 = obs[11 * Opad + o];
@@ -201,9 +205,15 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
       Ehb = envThb + slot * NBS * PT + pl;
       step = PT;
     }
-    for (int e = sub; e < NBS; e += L) {
-      const float4 c = E4[e * step];
-      const float hb = Ehb[e * step];
+    for (int e0 = 0; e0 < NBS; e0 += L) {
+      const bool valid = e0 + sub < NBS;
+      const int e = valid ? e0 + sub : 0;
+      float4 c = E4[e * step];
+      float hb = Ehb[e * step];
+      if (!valid) {  // far away, zero radius: never a candidate
+        c = make_float4(DUMMY_FAR, DUMMY_FAR, DUMMY_FAR, 0.f);
+        hb = 1.5f * DUMMY_FAR * DUMMY_FAR;
+      }
       bool hit = false;
 #pragma unroll
       for (int s = 0; s < NB; ++s) {
