@@ -245,6 +245,8 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
     std::vector<std::pair<int, PoseSrc>> env;
     int t_kp, t_kr, t_x, t_cf, t_cp, t_jl;
     float tx, ty, tz, tyaw, pz;
+    int cp_src = -1, cp_first = 0, cp_count = 0, cp_t = -1;
+    float cp_z = 0.f;
   };
   std::vector<Cfg> cfgs;
   struct Term { int kind; };
@@ -337,6 +339,19 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
     }
   }
   if (cfgs.empty()) return fail(s, TAMP_ERR_INVALID_ARG, "skeleton has no Pick/Place action");
+  // CFreePlace of a Place: first half of the box's spheres on the preceding Pick
+  // (the hand holds one box, so that Pick is the configuration right before),
+  // second half on the Place itself
+  for (size_t i = 0; i < cfgs.size(); ++i) {
+    Cfg& c = cfgs[i];
+    if (c.kind != 1) continue;
+    const int half = (i > 0 && cfgs[i - 1].kind == 0 && cfgs[i - 1].box == c.box) ? s->NBS / 2 : 0;
+    c.cp_src = c.tsrc; c.cp_z = c.pz; c.cp_t = c.t_cp; c.cp_first = half; c.cp_count = s->NBS - half;
+    if (half > 0) {
+      Cfg& pk = cfgs[i - 1];
+      pk.cp_src = c.tsrc; pk.cp_z = c.pz; pk.cp_t = c.t_cp; pk.cp_first = 0; pk.cp_count = half;
+    }
+  }
   if (static_cast<int>(cfgs.size()) > MAX_CFG) return fail(s, TAMP_ERR_INVALID_ARG, "too many configurations");
   if (off > MAX_D) return fail(s, TAMP_ERR_INVALID_ARG, "particle dimension %d exceeds %d", off, MAX_D);
   if (static_cast<int>(slots.size()) > MAX_SLOT) return fail(s, TAMP_ERR_INVALID_ARG, "too many Place actions");
@@ -357,7 +372,11 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
     rec[CF_T_CP] = static_cast<uint32_t>(c.t_cp); rec[CF_T_JL] = c.t_jl;
     rec[CF_PSRC] = static_cast<uint32_t>(c.tsrc);
     rec[CF_TX] = fbits(c.tx); rec[CF_TY] = fbits(c.ty); rec[CF_TZ] = fbits(c.tz); rec[CF_TYAW] = fbits(c.tyaw);
-    rec[CF_PZ] = fbits(c.pz);
+    rec[CF_PZ] = fbits(c.cp_z);
+    rec[CF_CP_SRC] = static_cast<uint32_t>(c.cp_src);
+    rec[CF_CP_FIRST] = static_cast<uint32_t>(c.cp_first);
+    rec[CF_CP_COUNT] = static_cast<uint32_t>(c.cp_count);
+    rec[CF_CP_T] = static_cast<uint32_t>(c.cp_t);
     v.insert(v.end(), rec, rec + CFG_W);
     env_count += static_cast<int>(c.env.size());
   }

@@ -48,11 +48,15 @@ enum ProbHdr {
 constexpr int CFG_W = 24;
 enum CfgField {
   CF_KIND = 0, CF_BOX, CF_QOFF, CF_GOFF, CF_TSRC, CF_SURF, CF_NENV, CF_ENVOFF,
-  CF_T_KP, CF_T_KR, CF_T_X, CF_T_CF, CF_T_CP, CF_T_JL, CF_PSRC, CF_PAD1,
+  CF_T_KP, CF_T_KR, CF_T_X, CF_T_CF, CF_T_CP, CF_T_JL, CF_PSRC,
+  CF_CP_SRC,                    // placement offset of the CFreePlace spheres this configuration tests (-1: none)
   CF_TX, CF_TY, CF_TZ, CF_TYAW,  // floats: target pose if CF_TSRC < 0, else CF_TZ = surface z + h_z
-  CF_PZ,                        // float: z of the placed box (place configurations)
-  CF_PAD2, CF_PAD3, CF_PAD4
+  CF_PZ,                        // float: z of that placed box
+  CF_CP_FIRST, CF_CP_COUNT,     // its spheres [first, first + count)
+  CF_CP_T                       // CFreePlace term index
 };
+// A Place's CFreePlace spheres are split between the Place and the Pick right
+// before it (same box, same environment), which evens the work of their warps.
 constexpr int ENV_W = 4;        // box, src (-1 = initial pose, else placement offset), slot, pad
 constexpr int SLOT_W = 4;       // placement slot (one per Place): box, placement offset, z (float), pad
 constexpr int MAX_SLOT = 16;

@@ -94,18 +94,98 @@ __device__ __forceinline__ void rx_right(float* R, float c, float s) {  // T <- 
 __device__ __forceinline__ float tw(const uint32_t* terms, int t) { return __uint_as_float(terms[t * TERM_W + 1]); }
 
 // ------------------------------------------------------------------ collision core
+// Register-batch helpers: read or update element s (warp-uniform) of a small
+// register array with a select chain, which keeps the arrays in registers.
+template <int N>
+__device__ __forceinline__ float pick(const float (&a)[N], int s) {
+  float v = a[0];
+#pragma unroll
+  for (int i = 1; i < N; ++i) v = (s == i) ? a[i] : v;
+  return v;
+}
+template <int N>
+__device__ __forceinline__ void add_at(float (&a)[N], int s, float v) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) a[i] += (s == i) ? v : 0.f;
+}
+
+// An oriented cuboid: t' = R^T t, R row-major (columns = box axes), half extents.
+struct Obb {
+  float tx, ty, tz, r00, r01, r02, r10, r11, r12, r20, r21, r22, hx, hy, hz;
+};
+// Obstacle o of the structure-of-arrays table; past the end, a far-away box
+// that nothing touches (every lane of the warp runs the same trip count).
+__device__ __forceinline__ Obb load_obb(const float* __restrict__ obs, int Opad, int o, int O) {
+  const bool ok = o < O;
+  const int i = ok ? o : 0;
+  Obb b;
+  b.tx = obs[0 * Opad + i] + (ok ? 0.f : DUMMY_FAR);
+  b.ty = obs[1 * Opad + i]; b.tz = obs[2 * Opad + i];
+  b.r00 = obs[3 * Opad + i]; b.r01 = obs[4 * Opad + i]; b.r02 = obs[5 * Opad + i];
+  b.r10 = obs[6 * Opad + i]; b.r11 = obs[7 * Opad + i]; b.r12 = obs[8 * Opad + i];
+  b.r20 = obs[9 * Opad + i]; b.r21 = obs[10 * Opad + i]; b.r22 = obs[11 * Opad + i];
+  b.hx = obs[12 * Opad + i]; b.hy = obs[13 * Opad + i]; b.hz = obs[14 * Opad + i];
+  return b;
+}
+__device__ __forceinline__ Obb sel_obb(bool second, const Obb& a, const Obb& b) { return second ? b : a; }
+// Point in the box frame: u = R^T c - t'.
+__device__ __forceinline__ void obb_local(const Obb& b, float x, float y, float z, float& ux, float& uy, float& uz) {
+  ux = fmaf(b.r00, x, fmaf(b.r10, y, fmaf(b.r20, z, -b.tx)));
+  uy = fmaf(b.r01, x, fmaf(b.r11, y, fmaf(b.r21, z, -b.ty)));
+  uz = fmaf(b.r02, x, fmaf(b.r12, y, fmaf(b.r22, z, -b.tz)));
+}
+// max_i(|u_i| - h_i): a sphere of radius r can only touch the box if this is < r.
+__device__ __forceinline__ float obb_gap(const Obb& b, float x, float y, float z) {
+  float ux, uy, uz;
+  obb_local(b, x, y, z, ux, uy, uz);
+  return fmaxf(fabsf(ux) - b.hx, fmaxf(fabsf(uy) - b.hy, fabsf(uz) - b.hz));
+}
+// Exact penetration max(0, r - sdf), sdf = ||max(q, 0)|| + min(max_i q_i, 0) with
+// q = |u| - h, and its gradient with respect to the sphere centre (-R dsdf/du).
+__device__ __forceinline__ float obb_pen(const Obb& b, float x, float y, float z, float r, float& gx, float& gy,
+                                         float& gz) {
+  float ux, uy, uz;
+  obb_local(b, x, y, z, ux, uy, uz);
+  const float qx = fabsf(ux) - b.hx, qy = fabsf(uy) - b.hy, qz = fabsf(uz) - b.hz;
+  const float mx = fmaxf(qx, 0.f), my = fmaxf(qy, 0.f), mz = fmaxf(qz, 0.f);
+  const float o2 = fmaf(mx, mx, fmaf(my, my, mz * mz));
+  gx = gy = gz = 0.f;
+  if (!(o2 < r * r)) return 0.f;
+  float dux = 0.f, duy = 0.f, duz = 0.f, sdf;
+  if (o2 > 0.f) {
+    const float d = sqrtf(o2);
+    const float inv = 1.f / d;
+    sdf = d;
+    dux = copysignf(mx * inv, ux);
+    duy = copysignf(my * inv, uy);
+    duz = copysignf(mz * inv, uz);
+  } else if (qx >= qy && qx >= qz) {
+    sdf = qx;
+    dux = copysignf(1.f, ux);
+  } else if (qy >= qz) {
+    sdf = qy;
+    duy = copysignf(1.f, uy);
+  } else {
+    sdf = qz;
+    duz = copysignf(1.f, uz);
+  }
+  gx = -fmaf(b.r00, dux, fmaf(b.r01, duy, b.r02 * duz));
+  gy = -fmaf(b.r10, dux, fmaf(b.r11, duy, b.r12 * duz));
+  gz = -fmaf(b.r20, dux, fmaf(b.r21, duy, b.r22 * duz));
+  return r - sdf;
+}
+
 // Penetration of a register batch of NB spheres into the environment of one
 // configuration: the static cuboids and the spheres of every other box at its
 // current pose.  Returns the summed penetration depth (unweighted) and adds
 // d(depth)/d(centre) into (gx, gy, gz).  Gradients towards boxes whose pose is a
 // placement variable are added (times wenv) straight into the tile's gradient.
-// Lane `sub` of the L lanes handles obstacles o = sub (mod L) and box spheres
-// e = sub (mod L).
 //
-// Each environment item is first tested against the NB spheres with a cheap,
-// branch-free test that never misses a contact; only when some lane of the warp
-// reports a candidate does the warp run the exact penetration and its gradient
-// (contacts are rare: well under 1% of pairs, even for random particles).
+// Lane `sub` of the L lanes takes environment items sub, sub + L, ...; two
+// items at a time are tested against the NB spheres with a branch-free test
+// that never misses a contact, the warp ORs its candidate bits, and only the
+// (item, sphere) pairs some lane flagged get the exact penetration and gradient
+// (contacts are rare: well under 1% of pairs even for random particles).
 template <int L>
 __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy)[NB], const float (&cz)[NB],
                                          const float (&cr)[NB], float (&gx)[NB], float (&gy)[NB],
@@ -122,78 +202,40 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
   for (int s = 0; s < NB; ++s)
     ha[s] = 0.5f * fmaf(cx[s], cx[s], fmaf(cy[s], cy[s], fmaf(cz[s], cz[s], -cr[s] * cr[s]))) - SS_MARGIN;
 
-  // sphere vs oriented cuboid.  u = R^T c - R^T t, q = |u| - h; the sphere can
-  // only touch the box if max_i q_i < r (exact test: ||max(q, 0)||^2 < r^2);
-  // sdf = ||max(q, 0)|| + min(max_i q_i, 0).
-  // every lane runs the same trip count (the warp votes below need all 32
-  // lanes); a lane past the end tests a far-away, zero-size box
-  for (int o0 = 0; o0 < O; o0 += L) {
-    const int o = o0 + sub < O ? o0 + sub : 0;
-    const float far = o0 + sub < O ? 0.f : DUMMY_FAR;
-    const float tpx = obs[0 * Opad + o] + far, tpy = obs[1 * Opad + o], tpz = obs[2 * Opad + o];
-    const float R00 = obs[3 * Opad + o], R01 = obs[4 * Opad + o], R02 = obs[5 * Opad + o];
-    const float R10 = obs[6 * Opad + o], R11 = obs[7 * Opad + o], R12 = obs[8 * Opad + o];
-    const float R20 = obs[9 * Opad + o], R21 = obs[10 * Opad + o], R22 = obs[11 * Opad + o];
-    const float hx = obs[12 * Opad + o], hy = obs[13 * Opad + o], hz = obs[14 * Opad + o];
-    bool hit = false;
+  for (int o0 = 0; o0 < O; o0 += 2 * L) {
+    const Obb A = load_obb(obs, Opad, o0 + sub, O);
+    const Obb B = load_obb(obs, Opad, o0 + L + sub, O);
+    unsigned hm = 0;
 #pragma unroll
     for (int s = 0; s < NB; ++s) {
-      const float ux = fmaf(R00, cx[s], fmaf(R10, cy[s], fmaf(R20, cz[s], -tpx)));
-      const float uy = fmaf(R01, cx[s], fmaf(R11, cy[s], fmaf(R21, cz[s], -tpy)));
-      const float uz = fmaf(R02, cx[s], fmaf(R12, cy[s], fmaf(R22, cz[s], -tpz)));
-      const float mq = fmaxf(fabsf(ux) - hx, fmaxf(fabsf(uy) - hy, fabsf(uz) - hz));
-      hit |= mq < cr[s];
+      hm |= (obb_gap(A, cx[s], cy[s], cz[s]) < cr[s] ? 1u : 0u) << s;
+      hm |= (obb_gap(B, cx[s], cy[s], cz[s]) < cr[s] ? 1u : 0u) << (s + NB);
     }
-    if (__any_sync(0xffffffffu, hit)) {
-#pragma unroll
-      for (int s = 0; s < NB; ++s) {
-        const float ux = fmaf(R00, cx[s], fmaf(R10, cy[s], fmaf(R20, cz[s], -tpx)));
-        const float uy = fmaf(R01, cx[s], fmaf(R11, cy[s], fmaf(R21, cz[s], -tpy)));
-        const float uz = fmaf(R02, cx[s], fmaf(R12, cy[s], fmaf(R22, cz[s], -tpz)));
-        const float qx = fabsf(ux) - hx, qy = fabsf(uy) - hy, qz = fabsf(uz) - hz;
-        const float mx = fmaxf(qx, 0.f), my = fmaxf(qy, 0.f), mz = fmaxf(qz, 0.f);
-        const float o2 = fmaf(mx, mx, fmaf(my, my, mz * mz));
-        if (o2 < cr[s] * cr[s]) {
-          float dux, duy, duz, sdf;
-          if (o2 > 0.f) {
-            const float d = sqrtf(o2);
-            const float inv = 1.f / d;
-            sdf = d;
-            dux = copysignf(mx * inv, ux);
-            duy = copysignf(my * inv, uy);
-            duz = copysignf(mz * inv, uz);
-          } else {
-            dux = duy = duz = 0.f;
-            if (qx >= qy && qx >= qz) {
-              sdf = qx;
-              dux = copysignf(1.f, ux);
-            } else if (qy >= qz) {
-              sdf = qy;
-              duy = copysignf(1.f, uy);
-            } else {
-              sdf = qz;
-              duz = copysignf(1.f, uz);
-            }
-          }
-          J += cr[s] - sdf;
-          // d(pen)/dc = -R d(sdf)/du
-          gx[s] -= fmaf(R00, dux, fmaf(R01, duy, R02 * duz));
-          gy[s] -= fmaf(R10, dux, fmaf(R11, duy, R12 * duz));
-          gz[s] -= fmaf(R20, dux, fmaf(R21, duy, R22 * duz));
-        }
-      }
+    unsigned any = __reduce_or_sync(0xffffffffu, hm);
+    while (any) {
+      const int bit = __ffs(any) - 1;
+      any &= any - 1;
+      const int s = bit % NB;
+      const Obb o = sel_obb(bit >= NB, A, B);
+      float px_, py_, pz_;
+      J += obb_pen(o, pick(cx, s), pick(cy, s), pick(cz, s), pick(cr, s), px_, py_, pz_);
+      add_at(gx, s, px_);
+      add_at(gy, s, py_);
+      add_at(gz, s, pz_);
     }
   }
 
   // sphere vs the spheres of the other boxes: pen = max(0, r_a + r_b - ||c_a - c_b||).
   // Boxes at their initial pose read the scene's world table (same for every
   // particle); boxes on a placement variable read this iteration's per-particle
-  // table (slot-major, particle-minor).
+  // table (slot-major, particle-minor).  Candidate test:
+  // c_a.c_b + r_a r_b - hb_b > ha_a  (|c_a - c_b|^2 - (r_a + r_b)^2 < 2 SS_MARGIN).
   for (int ei = 0; ei < n_env; ++ei) {
     const int src = env[ei * ENV_W + 1];
     const float4* E4;
     const float* Ehb;
     int step;
+    float bx = 0.f, by = 0.f;
     if (src < 0) {
       const int j = env[ei * ENV_W];
       E4 = binit + j * NBS;
@@ -204,52 +246,58 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
       E4 = envT4 + slot * NBS * PT + pl;
       Ehb = envThb + slot * NBS * PT + pl;
       step = PT;
+      bx = X[src * PT + pl];
+      by = X[(src + 1) * PT + pl];
     }
-    for (int e0 = 0; e0 < NBS; e0 += L) {
-      const bool valid = e0 + sub < NBS;
-      const int e = valid ? e0 + sub : 0;
-      float4 c = E4[e * step];
-      float hb = Ehb[e * step];
-      if (!valid) {  // far away, zero radius: never a candidate
-        c = make_float4(DUMMY_FAR, DUMMY_FAR, DUMMY_FAR, 0.f);
-        hb = 1.5f * DUMMY_FAR * DUMMY_FAR;
+    float fx = 0.f, fy = 0.f, tq = 0.f;  // push on a moving box: force and torque about its centre
+    for (int e0 = 0; e0 < NBS; e0 += 2 * L) {
+      float4 cA = make_float4(DUMMY_FAR, DUMMY_FAR, DUMMY_FAR, 0.f), cB = cA;
+      float hA = 1.5f * DUMMY_FAR * DUMMY_FAR, hB = hA;  // far away, zero radius: never a candidate
+      if (e0 + sub < NBS) {
+        cA = E4[(e0 + sub) * step];
+        hA = Ehb[(e0 + sub) * step];
       }
-      bool hit = false;
+      if (e0 + L + sub < NBS) {
+        cB = E4[(e0 + L + sub) * step];
+        hB = Ehb[(e0 + L + sub) * step];
+      }
+      unsigned hm = 0;
 #pragma unroll
       for (int s = 0; s < NB; ++s) {
-        const float dot = fmaf(cx[s], c.x, fmaf(cy[s], c.y, fmaf(cz[s], c.z, fmaf(cr[s], c.w, -hb))));
-        hit |= dot > ha[s];
+        const float dA = fmaf(cx[s], cA.x, fmaf(cy[s], cA.y, fmaf(cz[s], cA.z, fmaf(cr[s], cA.w, -hA))));
+        const float dB = fmaf(cx[s], cB.x, fmaf(cy[s], cB.y, fmaf(cz[s], cB.z, fmaf(cr[s], cB.w, -hB))));
+        hm |= (dA > ha[s] ? 1u : 0u) << s;
+        hm |= (dB > ha[s] ? 1u : 0u) << (s + NB);
       }
-      if (__any_sync(0xffffffffu, hit)) {
-        float efx = 0.f, efy = 0.f;
-#pragma unroll
-        for (int s = 0; s < NB; ++s) {
-          const float dx = cx[s] - c.x, dy = cy[s] - c.y, dz = cz[s] - c.z;
-          const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          const float Rs = cr[s] + c.w;
-          if (d2 < Rs * Rs) {
-            const float d = sqrtf(d2);
-            J += Rs - d;
-            if (d > 0.f) {
-              const float inv = 1.f / d;
-              const float vx = dx * inv, vy = dy * inv, vz = dz * inv;
-              gx[s] -= vx;
-              gy[s] -= vy;
-              gz[s] -= vz;
-              efx += vx;
-              efy += vy;
-            }
+      unsigned any = __reduce_or_sync(0xffffffffu, hm);
+      while (any) {
+        const int bit = __ffs(any) - 1;
+        any &= any - 1;
+        const int s = bit % NB;
+        const float4 c = bit >= NB ? cB : cA;
+        const float dx = pick(cx, s) - c.x, dy = pick(cy, s) - c.y, dz = pick(cz, s) - c.z;
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float Rs = pick(cr, s) + c.w;
+        if (d2 < Rs * Rs) {
+          const float d = sqrtf(d2);
+          J += Rs - d;
+          if (d > 0.f) {
+            const float inv = 1.f / d;
+            const float vx = dx * inv, vy = dy * inv, vz = dz * inv;
+            add_at(gx, s, -vx);
+            add_at(gy, s, -vy);
+            add_at(gz, s, -vz);
+            fx += vx;
+            fy += vy;
+            tq = fmaf(c.x - bx, vy, fmaf(-(c.y - by), vx, tq));
           }
         }
-        if (src >= 0 && (efx != 0.f || efy != 0.f)) {
-          // the environment sphere is pushed by +v: force on the box's (x, y) and
-          // torque about its centre for the yaw
-          const float rx = c.x - X[src * PT + pl], ry = c.y - X[(src + 1) * PT + pl];
-          atomicAdd(&G[src * PT + pl], wenv * efx);
-          atomicAdd(&G[(src + 1) * PT + pl], wenv * efy);
-          atomicAdd(&G[(src + 2) * PT + pl], wenv * (rx * efy - ry * efx));
-        }
       }
+    }
+    if (src >= 0 && (fx != 0.f || fy != 0.f || tq != 0.f)) {
+      atomicAdd(&G[src * PT + pl], wenv * fx);
+      atomicAdd(&G[(src + 1) * PT + pl], wenv * fy);
+      atomicAdd(&G[(src + 2) * PT + pl], wenv * tq);
     }
   }
   return J;
@@ -307,7 +355,8 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   const uint32_t* terms = pb + pb[PH_OFF_TERMS];
   const float w_kp = tw(terms, cf[CF_T_KP]), w_kr = tw(terms, cf[CF_T_KR]);
   const float w_cf = tw(terms, cf[CF_T_CF]), w_jl = tw(terms, cf[CF_T_JL]), w_x = tw(terms, cf[CF_T_X]);
-  const float w_cp = kind == 1 ? tw(terms, cf[CF_T_CP]) : 0.f;
+  const int cp_src = cf[CF_CP_SRC], cp_first = cf[CF_CP_FIRST], cp_count = cp_src >= 0 ? cf[CF_CP_COUNT] : 0;
+  const float w_cp = cp_count > 0 ? tw(terms, cf[CF_CP_T]) : 0.f;
   const float k0 = sub == 0 ? 1.f : 0.f;  // terms computed redundantly count on lane 0 only
 #define XV(c) X[(c) * PT + pl]
 
@@ -397,7 +446,8 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
     gp[2] = k0 * (fkx * rgy - fky * rgx + ubz);
   }
   float J_hold = 0.f, J_place = 0.f;
-  float gpc[3] = {0.f, 0.f, 0.f};
+  float gpc[3] = {0.f, 0.f, 0.f};  // Kin target / containment -> this configuration's placement
+  float gcp[3] = {0.f, 0.f, 0.f};  // CFreePlace part -> placement cp_src
   float sgr, cgr;  // grasp yaw: R_G = Rz(yaw) Rx(pi) = [[c, s, 0], [s, -c, 0], [0, 0, -1]] (symmetric)
   sincosf(gyaw, &sgr, &cgr);
 
@@ -433,13 +483,15 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
         --l;
         if (l == 0) phase = 2;
         s0 = sc[SH_LINK0 + l]; s1 = sc[SH_LINK0 + l + 1];
-      } else if (phase == 2 && kind == 1) {
+      } else if (phase == 2 && cp_count > 0) {
         phase = 3;
-        s0 = 0; s1 = nbs_pad;
-        R[0] = cy; R[1] = -sy; R[2] = 0.f;
-        R[3] = sy; R[4] = cy; R[5] = 0.f;
+        s0 = cp_first; s1 = cp_first + (cp_count + NB - 1) / NB * NB;
+        float sp, cp;
+        sincosf(XV(cp_src + 2), &sp, &cp);
+        R[0] = cp; R[1] = -sp; R[2] = 0.f;
+        R[3] = sp; R[4] = cp; R[5] = 0.f;
         R[6] = 0.f; R[7] = 0.f; R[8] = 1.f;
-        t[0] = px; t[1] = py; t[2] = cff[CF_PZ];
+        t[0] = XV(cp_src); t[1] = XV(cp_src + 1); t[2] = cff[CF_PZ];
       } else {
         break;
       }
@@ -450,7 +502,8 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
     for (int s = 0; s < NB; ++s) {
       float4 p;
       if (phase == 0 || phase == 3) {
-        p = (s0 + s < NBS) ? bloc[b * NBS + s0 + s] : make_float4(DUMMY_FAR, DUMMY_FAR, DUMMY_FAR, 0.f);
+        const int lim = phase == 0 ? NBS : cp_first + cp_count;
+        p = (s0 + s < lim) ? bloc[b * NBS + s0 + s] : make_float4(DUMMY_FAR, DUMMY_FAR, DUMMY_FAR, 0.f);
         if (phase == 0 && s0 + s < NBS) {
           const float vx = p.x - gxv, vy = p.y - gyv, vz = p.z - gzv;
           const float wx = fmaf(cgr, vx, sgr * vy), wy = fmaf(sgr, vx, -cgr * vy), wz = -vz;
@@ -475,9 +528,9 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
 #pragma unroll
       for (int s = 0; s < NB; ++s) {
         const float fx = w_cp * gx[s], fy = w_cp * gyy[s];
-        gpc[0] += fx;
-        gpc[1] += fy;
-        gpc[2] += (cx[s] - px) * fy - (cyy[s] - py) * fx;
+        gcp[0] += fx;
+        gcp[1] += fy;
+        gcp[2] += (cx[s] - t[0]) * fy - (cyy[s] - t[1]) * fx;
       }
     } else {
       J_hold += Jb;
@@ -523,8 +576,15 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
     for (int i = 0; i < 4; ++i) gg[i] += __shfl_xor_sync(0xffffffffu, gg[i], m);
 #pragma unroll
     for (int i = 0; i < 3; ++i) gpc[i] += __shfl_xor_sync(0xffffffffu, gpc[i], m);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) gcp[i] += __shfl_xor_sync(0xffffffffu, gcp[i], m);
   }
   if (sub != 0) return;
+  if (cp_count > 0) {
+    atomicAdd(&Tm[cf[CF_CP_T] * PT + pl], J_place);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) atomicAdd(&G[(cp_src + i) * PT + pl], gcp[i]);
+  }
 
   // ---------------- per-configuration scalar terms (lane 0)
   float jl = 0.f;
@@ -588,7 +648,6 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
       gpc[2] += w_x * (rx * gwy - ry * gwx);
     }
     Tm[cf[CF_T_X] * PT + pl] = J;
-    Tm[cf[CF_T_CP] * PT + pl] = J_place;
   }
   // grasp gradient (shared by the Pick and the Place that hold the same grasp)
 #pragma unroll
@@ -724,6 +783,7 @@ __global__ void __launch_bounds__(384, 1) optimize_kernel(OptArgs a) {
       envT4[i] = make_float4(ex, ey, ez, l.w);
       envThb[i] = 0.5f * fmaf(ex, ex, fmaf(ey, ey, fmaf(ez, ez, -l.w * l.w)));
     }
+    for (int i = tid; i < NT * PT; i += nthr) st[i] = 0.f;  // CFreePlace terms are sums over two warps
     __syncthreads();
     for (int k = w; k < K; k += W) eval_config<L>(s_sc, s_pb, k, sx, sg, st, envT4, envThb, pl, sub);
     if (w == goal_warp && sub == 0) eval_goal<L>(s_sc, s_pb, sx, sg, st, pl);
