@@ -153,21 +153,20 @@ tamp_status build_scene_blob(tamp_scene* s, const tamp_scene_desc* d) {
   if (slot > MAX_SPH) return fail(s, TAMP_ERR_INVALID_ARG, "too many arm spheres after padding (%d > %d)", slot, MAX_SPH);
   v[SH_NSPH] = static_cast<uint32_t>(slot);
   align4(v);
-  // obstacles, structure of arrays
-  const int O = d->n_obs, Opad = std::max(4, (O + 3) & ~3);
+  // obstacles: t' = R^T t, R row-major, half extents, pad (16 words each)
+  const int O = d->n_obs;
   v[SH_OFF_OBS] = static_cast<uint32_t>(v.size());
-  std::vector<float> rows(static_cast<size_t>(OBS_ROWS) * Opad, 0.f);
   for (int o = 0; o < O; ++o) {
     const double* Rm = d->obs_rot + 9 * o;
     const double* c = d->obs_center + 3 * o;
-    for (int j = 0; j < 3; ++j)  // t' = R^T t
-      rows[j * Opad + o] = static_cast<float>(Rm[0 + j] * c[0] + Rm[3 + j] * c[1] + Rm[6 + j] * c[2]);
-    for (int k = 0; k < 9; ++k) rows[(3 + k) * Opad + o] = static_cast<float>(Rm[k]);
-    for (int j = 0; j < 3; ++j) rows[(12 + j) * Opad + o] = static_cast<float>(d->obs_half[3 * o + j]);
+    for (int j = 0; j < 3; ++j) push_f(v, Rm[0 + j] * c[0] + Rm[3 + j] * c[1] + Rm[6 + j] * c[2]);
+    for (int k = 0; k < 9; ++k) push_f(v, Rm[k]);
+    for (int j = 0; j < 3; ++j) push_f(v, d->obs_half[3 * o + j]);
+    v.push_back(0);
   }
-  for (float f : rows) v.push_back(fbits(f));
+  if (O == 0)
+    for (int k = 0; k < OBS_W; ++k) v.push_back(0);
   v[SH_O] = static_cast<uint32_t>(O);
-  v[SH_OPAD] = static_cast<uint32_t>(Opad);
   align4(v);
   // boxes
   const int B = d->n_boxes, NBS = d->spheres_per_box;

@@ -29,9 +29,8 @@ constexpr int ARM_JW = 8;       // a, d, cos(alpha), sin(alpha), offset, q_lo, q
 // sphere table: float4 (x, y, z, r) per padded slot; padding slots sit far away
 // with r = 0 so they never touch anything
 constexpr float DUMMY_FAR = 1.0e4f;
-// obstacles: OBS_ROWS rows of O_pad floats (structure of arrays):
-//   rows 0..2  t' = R^T t       rows 3..11 R row-major      rows 12..14 half
-constexpr int OBS_ROWS = 16;
+// obstacles: 16 floats each -- t' = R^T t (3), R row-major (9), half extents (3), pad
+constexpr int OBS_W = 16;
 // box record: half x,y,z, pad, init x,y,z,yaw, cos(yaw), sin(yaw), pad, pad
 constexpr int BOX_W = 12;
 // box spheres: local (x, y, z, r) per box; the same at the initial pose in the

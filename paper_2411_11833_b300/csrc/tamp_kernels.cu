@@ -115,16 +115,16 @@ struct Obb {
 };
 // Obstacle o of the structure-of-arrays table; past the end, a far-away box
 // that nothing touches (every lane of the warp runs the same trip count).
-__device__ __forceinline__ Obb load_obb(const float* __restrict__ obs, int Opad, int o, int O) {
+__device__ __forceinline__ Obb load_obb(const float4* __restrict__ obs, int o, int O) {
   const bool ok = o < O;
-  const int i = ok ? o : 0;
+  const float4* q = obs + 4 * (ok ? o : 0);
+  const float4 a = q[0], b4 = q[1], c = q[2], d = q[3];
   Obb b;
-  b.tx = obs[0 * Opad + i] + (ok ? 0.f : DUMMY_FAR);
-  b.ty = obs[1 * Opad + i]; b.tz = obs[2 * Opad + i];
-  b.r00 = obs[3 * Opad + i]; b.r01 = obs[4 * Opad + i]; b.r02 = obs[5 * Opad + i];
-  b.r10 = obs[6 * Opad + i]; b.r11 = obs[7 * Opad + i]; b.r12 = obs[8 * Opad + i];
-  b.r20 = obs[9 * Opad + i]; b.r21 = obs[10 * Opad + i]; b.r22 = obs[11 * Opad + i];
-  b.hx = obs[12 * Opad + i]; b.hy = obs[13 * Opad + i]; b.hz = obs[14 * Opad + i];
+  b.tx = a.x + (ok ? 0.f : DUMMY_FAR); b.ty = a.y; b.tz = a.z;
+  b.r00 = a.w; b.r01 = b4.x; b.r02 = b4.y;
+  b.r10 = b4.z; b.r11 = b4.w; b.r12 = c.x;
+  b.r20 = c.y; b.r21 = c.z; b.r22 = c.w;
+  b.hx = d.x; b.hy = d.y; b.hz = d.z;
   return b;
 }
 __device__ __forceinline__ Obb sel_obb(bool second, const Obb& a, const Obb& b) { return second ? b : a; }
@@ -189,7 +189,7 @@ __device__ __forceinline__ float obb_pen(const Obb& b, float x, float y, float z
 template <int L>
 __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy)[NB], const float (&cz)[NB],
                                          const float (&cr)[NB], float (&gx)[NB], float (&gy)[NB],
-                                         float (&gz)[NB], const float* __restrict__ obs, int O, int Opad,
+                                         float (&gz)[NB], const float4* __restrict__ obs, int O,
                                          const int* __restrict__ env, int n_env,
                                          const float4* __restrict__ binit, const float* __restrict__ binit_hb,
                                          const float4* __restrict__ envT4, const float* __restrict__ envThb,
@@ -203,8 +203,8 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
     ha[s] = 0.5f * fmaf(cx[s], cx[s], fmaf(cy[s], cy[s], fmaf(cz[s], cz[s], -cr[s] * cr[s]))) - SS_MARGIN;
 
   for (int o0 = 0; o0 < O; o0 += 2 * L) {
-    const Obb A = load_obb(obs, Opad, o0 + sub, O);
-    const Obb B = load_obb(obs, Opad, o0 + L + sub, O);
+    const Obb A = load_obb(obs, o0 + sub, O);
+    const Obb B = load_obb(obs, o0 + L + sub, O);
     unsigned hm = 0;
 #pragma unroll
     for (int s = 0; s < NB; ++s) {
@@ -337,8 +337,8 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   const int nj = sc[SH_NJ];
   const float* arm = reinterpret_cast<const float*>(sc + sc[SH_OFF_ARM]);
   const float4* sph = reinterpret_cast<const float4*>(sc + sc[SH_OFF_SPH]);
-  const int O = sc[SH_O], Opad = sc[SH_OPAD];
-  const float* obs = reinterpret_cast<const float*>(sc + sc[SH_OFF_OBS]);
+  const int O = sc[SH_O];
+  const float4* obs = reinterpret_cast<const float4*>(sc + sc[SH_OFF_OBS]);
   const float* boxr = reinterpret_cast<const float*>(sc + sc[SH_OFF_BOX]);
   const float4* bloc = reinterpret_cast<const float4*>(sc + sc[SH_OFF_BLOC]);
   const float4* binit = reinterpret_cast<const float4*>(sc + sc[SH_OFF_BINIT]);
@@ -521,7 +521,7 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
       gx[s] = gyy[s] = gz[s] = 0.f;
     }
     const float wenv = phase == 3 ? w_cp : w_cf;
-    const float Jb = collide<L>(cx, cyy, cz, cr, gx, gyy, gz, obs, O, Opad, env, n_env, binit, binit_hb, envT4,
+    const float Jb = collide<L>(cx, cyy, cz, cr, gx, gyy, gz, obs, O, env, n_env, binit, binit_hb, envT4,
                                 envThb, NBS, X, G, pl, sub, wenv);
     if (phase == 3) {
       J_place += Jb;
@@ -766,6 +766,7 @@ __global__ void __launch_bounds__(384, 1) optimize_kernel(OptArgs a) {
   const float* lr = reinterpret_cast<const float*>(s_pb + s_pb[PH_OFF_LR]);
   const int goal_warp = (K - 1) % W;
 
+  double b1t = pow(static_cast<double>(a.beta1), a.t0), b2t = pow(static_cast<double>(a.beta2), a.t0);
   const int* slots = reinterpret_cast<const int*>(s_pb + s_pb[PH_OFF_SLOT]);
   const float4* bloc = reinterpret_cast<const float4*>(s_sc + s_sc[SH_OFF_BLOC]);
   for (int it = 0;; ++it) {
@@ -804,10 +805,9 @@ __global__ void __launch_bounds__(384, 1) optimize_kernel(OptArgs a) {
     }
     if (it == a.n_steps) break;
     // Adam (Kingma & Ba) on the Eq. 4 gradient; the gradient buffer is cleared for the next pass
-    const int step = a.t0 + it + 1;
-    const float bc1 = static_cast<float>(1.0 - pow(static_cast<double>(a.beta1), step));
-    const float bc2 = static_cast<float>(1.0 - pow(static_cast<double>(a.beta2), step));
-    const float ib1 = 1.f / bc1, ib2 = 1.f / bc2;
+    b1t *= static_cast<double>(a.beta1);  // beta^(t0 + it + 1)
+    b2t *= static_cast<double>(a.beta2);
+    const float ib1 = static_cast<float>(1.0 / (1.0 - b1t)), ib2 = static_cast<float>(1.0 / (1.0 - b2t));
     for (int i = tid; i < D * PT; i += nthr) {
       const float g = sg[i] * a.gscale;
       const float m = fmaf(a.beta1, sm[i], (1.f - a.beta1) * g);
