@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--particles", type=int, default=P_PARTICLES)
     ap.add_argument("--iters", type=int, default=N_ITERS)
+    ap.add_argument("--lanes", type=int, default=0, help="threads per (particle, configuration); 0 = library choice")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -194,7 +195,7 @@ def main():
     sc, acts = sg.packing_problem(SCENE_SEED)
     with torch.cuda.stream(stream):
         scene = pkg.Scene(sc, device=local, stream=stream.cuda_stream)
-        pid = scene.set_skeleton(acts)
+        pid = scene.set_skeleton(acts, pkg.default_options(lanes=args.lanes))
     D, NT, _ = scene.problem_info(pid)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -223,6 +224,7 @@ def main():
         torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
+    work = scene.work_counters(pid)          # candidates of the last timed step
     step_ms = [e0.elapsed_time(e2) for e0, _, e2 in ev]
     kern_ms = [e1.elapsed_time(e2) for _, e1, e2 in ev]
     total_ms = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
@@ -256,7 +258,8 @@ def main():
             dist.destroy_process_group()
         return
     ev_flops = flops.eval_flops(sc, acts)
-    launch_flops = P * ((T + 1) * ev_flops + T * flops.adam_flops(D))
+    launch_flops = (P * ((T + 1) * ev_flops + T * flops.adam_flops(D))
+                    + flops.exact_flops(work[0], work[1], sc.box_spheres.shape[1]))
     kern_s = sum(kern_ms) / len(kern_ms) / 1e3
     props = torch.cuda.get_device_properties(dev)
     peak = flops.fp32_peak_tflops(props.multi_processor_count, 2032.0)
@@ -273,6 +276,7 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "optimize_kernel", "flop_per_launch": launch_flops,
+                     "exact_candidates": {"cuboid": work[0], "box": work[1]},
                      "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x 2032 MHz (max SM clock)"},
         "e2e": {"value": P * T / e2e_s, "unit": "particle-iters/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

@@ -187,6 +187,13 @@ tamp_status tamp_query_satisfied(tamp_scene *scene, int problem_id, uint8_t *mas
 tamp_status tamp_eval(tamp_scene *scene, int problem_id, int n, const float *x_dev,
                       float *cost_dev, float *terms_dev, uint8_t *flags_dev, float *grad_dev);
 
+/* Work counters of a problem since its batch was last sampled or set:
+ * out[0] = (sphere batch, cuboid) pairs and out[1] = (sphere batch, box) pairs
+ * that the collision broad phase passed on to the exact test (the exact work is
+ * data-dependent; everything else per iteration is fixed by the skeleton).
+ * Synchronises.  Not part of the paper's method: performance accounting only. */
+tamp_status tamp_work_counters(tamp_scene *scene, int problem_id, uint64_t out[2]);
+
 /* Text of the last error on this scene ("" if none); valid until the next call. */
 const char *tamp_last_error(const tamp_scene *scene);
 

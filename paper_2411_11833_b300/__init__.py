@@ -175,6 +175,12 @@ class Scene:
         return dict(mask=mask.astype(bool), n_satisfied=ns.value, first_iter=first.value, cost=cost,
                     counts=counts[:ncon], particles=parts)
 
+    def work_counters(self, pid: int):
+        """(cuboid, box) broad-phase candidates resolved exactly since the batch was set."""
+        out = (ctypes.c_uint64 * 2)()
+        self._check(self._lib.tamp_work_counters(self._h, pid, out))
+        return int(out[0]), int(out[1])
+
     def eval(self, pid: int, x, want_terms=True, want_grad=True):
         """Evaluate a device batch x [D][n] (float32 CUDA tensor).  Returns
         (cost [n], terms [n_terms][n], flags [n] uint8, grad [D][n])."""

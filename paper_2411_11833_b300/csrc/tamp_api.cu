@@ -19,7 +19,9 @@ namespace tamp {
 cudaError_t launch_optimize(const OptArgs& a, int L, int K, size_t smem, cudaStream_t st);
 cudaError_t launch_sample(const uint32_t* pb, const uint32_t* sc, float* x, float* m, float* v, int stride, int P,
                           int D, uint64_t seed, cudaStream_t st);
-size_t optimize_smem_bytes(int scene_words, int prob_words, int D, int NT, int nslot, int nbs, int L);
+size_t optimize_smem_bytes(int scene_words, int prob_words, int D, int NT, int nslot, int nbs, int n_obs,
+                           int n_boxes, int warps, int L);
+int optimize_warps(int K);
 }  // namespace tamp
 
 using namespace tamp;
@@ -38,6 +40,7 @@ struct Problem {
   uint8_t* d_flags = nullptr;
   int* d_counts = nullptr;
   int* d_first = nullptr;
+  unsigned long long* d_work = nullptr;  // [2] broad-phase candidates resolved exactly
   bool has_batch = false, checked = false;
 };
 
@@ -144,7 +147,7 @@ tamp_status build_scene_blob(tamp_scene* s, const tamp_scene_desc* d) {
         ++cnt;
       }
     while (cnt % NB) {
-      push_f(v, DUMMY_FAR); push_f(v, DUMMY_FAR); push_f(v, DUMMY_FAR); push_f(v, 0.0);
+      push_f(v, DUMMY_FAR); push_f(v, DUMMY_FAR); push_f(v, DUMMY_FAR); push_f(v, -1.0);
       ++cnt;
     }
     slot += cnt;
@@ -153,6 +156,38 @@ tamp_status build_scene_blob(tamp_scene* s, const tamp_scene_desc* d) {
   if (slot > MAX_SPH) return fail(s, TAMP_ERR_INVALID_ARG, "too many arm spheres after padding (%d > %d)", slot, MAX_SPH);
   v[SH_NSPH] = static_cast<uint32_t>(slot);
   align4(v);
+  // bounding sphere of every batch of NB slots (link frame), from its real spheres
+  {
+    const uint32_t base = v[SH_OFF_SPH];
+    std::vector<float> bounds;
+    for (int b0 = 0; b0 < slot; b0 += NB) {
+      double lo[3] = {1e30, 1e30, 1e30}, hi[3] = {-1e30, -1e30, -1e30};
+      auto rd = [&](int k, int c) { float f; std::memcpy(&f, &v[base + 4 * k + c], 4); return static_cast<double>(f); };
+      int nreal = 0;
+      for (int k = b0; k < b0 + NB; ++k)
+        if (rd(k, 3) >= 0.0) {
+          ++nreal;
+          for (int c = 0; c < 3; ++c) { lo[c] = std::min(lo[c], rd(k, c)); hi[c] = std::max(hi[c], rd(k, c)); }
+        }
+      double cen[3] = {0, 0, 0}, R = -1.0;
+      if (nreal) {
+        for (int c = 0; c < 3; ++c) cen[c] = 0.5 * (lo[c] + hi[c]);
+        for (int k = b0; k < b0 + NB; ++k)
+          if (rd(k, 3) >= 0.0) {
+            const double dx = rd(k, 0) - cen[0], dy = rd(k, 1) - cen[1], dz = rd(k, 2) - cen[2];
+            R = std::max(R, std::sqrt(dx * dx + dy * dy + dz * dz) + rd(k, 3));
+          }
+        R = R * (1.0 + 1e-5) + 1e-5;  // cover FP32 rounding of the transformed centre
+      }
+      for (int c = 0; c < 3; ++c) bounds.push_back(static_cast<float>(cen[c]));
+      bounds.push_back(static_cast<float>(R));
+    }
+    v[SH_OFF_SPHB] = static_cast<uint32_t>(v.size());
+    for (float f : bounds) v.push_back(fbits(f));
+    if (bounds.empty())
+      for (int c = 0; c < 4; ++c) v.push_back(0);
+    align4(v);
+  }
   // obstacles: t' = R^T t, R row-major, half extents, pad (16 words each)
   const int O = d->n_obs;
   v[SH_OFF_OBS] = static_cast<uint32_t>(v.size());
@@ -174,7 +209,12 @@ tamp_status build_scene_blob(tamp_scene* s, const tamp_scene_desc* d) {
   for (int b = 0; b < B; ++b) {
     const double* h = d->box_half + 3 * b;
     const double* p = d->box_init + 4 * b;
-    push_f(v, h[0]); push_f(v, h[1]); push_f(v, h[2]); v.push_back(0);
+    double rb = 0.0;  // radius about the centre that bounds every sphere of the box model
+    for (int e = 0; e < NBS; ++e) {
+      const double* l = d->box_spheres + (b * NBS + e) * 4;
+      rb = std::max(rb, std::sqrt(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]) + l[3]);
+    }
+    push_f(v, h[0]); push_f(v, h[1]); push_f(v, h[2]); push_f(v, rb * (1.0 + 1e-5) + 1e-5);
     push_f(v, p[0]); push_f(v, p[1]); push_f(v, p[2]); push_f(v, p[3]);
     push_f(v, std::cos(p[3])); push_f(v, std::sin(p[3])); v.push_back(0); v.push_back(0);
   }
@@ -194,17 +234,6 @@ tamp_status build_scene_blob(tamp_scene* s, const tamp_scene_desc* d) {
       push_f(v, p[1] + sn * l[0] + c * l[1]);
       push_f(v, p[2] + l[2]);
       push_f(v, l[3]);
-    }
-  }
-  align4(v);
-  v[SH_OFF_BINIT_HB] = static_cast<uint32_t>(v.size());
-  for (int b = 0; b < B; ++b) {
-    const double* p = d->box_init + 4 * b;
-    const double c = std::cos(p[3]), sn = std::sin(p[3]);
-    for (int e = 0; e < NBS; ++e) {
-      const double* l = d->box_spheres + (b * NBS + e) * 4;
-      const double x = p[0] + c * l[0] - sn * l[1], y = p[1] + sn * l[0] + c * l[1], z = p[2] + l[2];
-      push_f(v, 0.5 * (x * x + y * y + z * z - l[3] * l[3]));
     }
   }
   align4(v);
@@ -479,9 +508,9 @@ int pick_lanes(const Problem& pr, int P) {
 
 void free_batch(Problem& pr) {
   cudaFree(pr.d_x); cudaFree(pr.d_m); cudaFree(pr.d_v); cudaFree(pr.d_cost);
-  cudaFree(pr.d_flags); cudaFree(pr.d_counts); cudaFree(pr.d_first);
+  cudaFree(pr.d_flags); cudaFree(pr.d_counts); cudaFree(pr.d_first); cudaFree(pr.d_work);
   pr.d_x = pr.d_m = pr.d_v = pr.d_cost = nullptr;
-  pr.d_flags = nullptr; pr.d_counts = nullptr; pr.d_first = nullptr;
+  pr.d_flags = nullptr; pr.d_counts = nullptr; pr.d_first = nullptr; pr.d_work = nullptr;
   pr.cap = 0;
 }
 
@@ -496,8 +525,10 @@ tamp_status ensure_batch(tamp_scene* s, Problem& pr, int P) {
     CUDA_TRY(s, cudaMalloc(&pr.d_flags, static_cast<size_t>(P)));
     CUDA_TRY(s, cudaMalloc(&pr.d_counts, static_cast<size_t>(std::max(pr.NCON, 1)) * 4));
     CUDA_TRY(s, cudaMalloc(&pr.d_first, 4));
+    CUDA_TRY(s, cudaMalloc(&pr.d_work, 2 * sizeof(unsigned long long)));
     pr.cap = P;
   }
+  CUDA_TRY(s, cudaMemsetAsync(pr.d_work, 0, 2 * sizeof(unsigned long long), s->stream));
   pr.P = P;
   const int big = INT_MAX;
   CUDA_TRY(s, cudaMemcpyAsync(pr.d_first, &big, 4, cudaMemcpyHostToDevice, s->stream));
@@ -523,11 +554,13 @@ tamp_status run_state(tamp_scene* s, Problem& pr, int n_steps) {
   a.stride = pr.P; a.P = pr.P;
   a.out_cost = pr.d_cost; a.out_flags = pr.d_flags; a.out_counts = pr.d_counts;
   a.first_iter = pr.d_first;
+  a.work = pr.d_work;
   a.n_steps = n_steps; a.t0 = pr.t;
   a.gscale = pr.opt.scale_by_batch ? 1.f / static_cast<float>(pr.P) : 1.f;
   const int L = pick_lanes(pr, pr.P);
   CUDA_TRY(s, cudaMemsetAsync(pr.d_counts, 0, static_cast<size_t>(std::max(pr.NCON, 1)) * 4, s->stream));
-  const size_t smem = optimize_smem_bytes(a.scene_words, a.prob_words, pr.D, pr.NT, pr.NSLOT, s->NBS, L);
+  const size_t smem = optimize_smem_bytes(a.scene_words, a.prob_words, pr.D, pr.NT, pr.NSLOT, s->NBS, s->O, s->B,
+                                         optimize_warps(pr.K), L);
   if (smem > kMaxDynSmem) return fail(s, TAMP_ERR_INVALID_ARG, "problem needs %zu B of shared memory", smem);
   CUDA_TRY(s, launch_optimize(a, L, pr.K, smem, s->stream));
   pr.t += n_steps;
@@ -768,9 +801,25 @@ tamp_status tamp_eval(tamp_scene* s, int id, int n, const float* x, float* cost,
   a.out_cost = cost; a.out_terms = terms; a.out_flags = flags; a.out_grad = grad;
   a.first_iter = nullptr; a.n_steps = 0; a.t0 = 0;
   const int L = pick_lanes(*pr, n);
-  const size_t smem = optimize_smem_bytes(a.scene_words, a.prob_words, pr->D, pr->NT, pr->NSLOT, s->NBS, L);
+  const size_t smem = optimize_smem_bytes(a.scene_words, a.prob_words, pr->D, pr->NT, pr->NSLOT, s->NBS, s->O, s->B,
+                                         optimize_warps(pr->K), L);
   if (smem > kMaxDynSmem) return fail(s, TAMP_ERR_INVALID_ARG, "problem needs %zu B of shared memory", smem);
   CUDA_TRY(s, launch_optimize(a, L, pr->K, smem, s->stream));
+  return TAMP_OK;
+}
+
+tamp_status tamp_work_counters(tamp_scene* s, int id, uint64_t out[2]) {
+  Problem* pr = get_problem(s, id);
+  if (!pr) return fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", id);
+  if (!out) return fail(s, TAMP_ERR_INVALID_ARG, "null output");
+  if (!pr->has_batch) return fail(s, TAMP_ERR_STATE, "problem %d has no particles", id);
+  DeviceGuard g(s->device);
+  unsigned long long w[2] = {0, 0};
+  CUDA_TRY(s, cudaMemcpyAsync(w, pr->d_work, sizeof w, cudaMemcpyDeviceToHost, s->stream));
+  tamp_status st = check_device_error(s);
+  if (st != TAMP_OK) return st;
+  out[0] = w[0];
+  out[1] = w[1];
   return TAMP_OK;
 }
 

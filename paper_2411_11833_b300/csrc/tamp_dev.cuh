@@ -20,22 +20,22 @@ constexpr int MAX_D = 1024;
 enum SceneHdr {
   SH_NJ = 0, SH_NSPH, SH_O, SH_OPAD, SH_B, SH_NBS, SH_NSURF, SH_WORDS,
   SH_LINK0 = 8,                 // link_start[0..MAXJ+1]: 10 entries (words 8..17)
-  SH_OFF_ARM = 18, SH_OFF_SPH, SH_OFF_OBS, SH_OFF_BOX, SH_OFF_BLOC, SH_OFF_BINIT, SH_OFF_BINIT_HB,
+  SH_OFF_ARM = 18, SH_OFF_SPH, SH_OFF_OBS, SH_OFF_BOX, SH_OFF_BLOC, SH_OFF_BINIT, SH_OFF_SPHB,
   SH_OFF_SURF, SH_HDR_WORDS = 32
 };
 // arm section: base frame (12), tool frame (12), then per joint ARM_JW words
 // frame = R row-major (9) + t (3)
 constexpr int ARM_JW = 8;       // a, d, cos(alpha), sin(alpha), offset, q_lo, q_hi, pad
 // sphere table: float4 (x, y, z, r) per padded slot; padding slots sit far away
-// with r = 0 so they never touch anything
+// with r = -1 (unused).  Per batch of NB slots, a bounding sphere (centre in the
+// link frame, radius) for the broad phase.
 constexpr float DUMMY_FAR = 1.0e4f;
 // obstacles: 16 floats each -- t' = R^T t (3), R row-major (9), half extents (3), pad
 constexpr int OBS_W = 16;
-// box record: half x,y,z, pad, init x,y,z,yaw, cos(yaw), sin(yaw), pad, pad
+// box record: half x,y,z, bounding radius of its spheres about its centre,
+// init x,y,z,yaw, cos(yaw), sin(yaw), pad, pad
 constexpr int BOX_W = 12;
-// box spheres: local (x, y, z, r) per box; the same at the initial pose in the
-// world, plus hb = (|c|^2 - r^2) / 2 for the dot-product contact test
-// (|c_a - c_b|^2 < (r_a + r_b)^2  <=>  c_a.c_b + r_a r_b - hb_b > ha_a).
+// box spheres: local (x, y, z, r) per box, and the same at the initial pose in the world
 // surface record: cx, cy, yaw, hx, hy, z_top, cos(yaw), sin(yaw)
 constexpr int SURF_W = 8;
 
@@ -59,9 +59,6 @@ enum CfgField {
 constexpr int ENV_W = 4;        // box, src (-1 = initial pose, else placement offset), slot, pad
 constexpr int SLOT_W = 4;       // placement slot (one per Place): box, placement offset, z (float), pad
 constexpr int MAX_SLOT = 16;
-// contact test margin (m^2): the fast dot-product test flags pairs with
-// |c_a - c_b|^2 - (r_a + r_b)^2 < 2 * SS_MARGIN, well above its FP32 rounding
-constexpr float SS_MARGIN = 4e-5f;
 constexpr int TERM_W = 4;       // kind, weight (float), tol (float), is_constraint
 constexpr int GOAL_W = 4;       // box, src, z (float), pad
 constexpr int SAMP_W = 4;       // per component: kind, a (float), b (float), surface
@@ -87,6 +84,7 @@ struct OptArgs {
   float gscale;                 // 1/N_b (Eq. 4) or 1
   float beta1, beta2, eps;
   int load_mv;                  // read m, v from memory (else zeros)
+  unsigned long long* work;     // optional [2]: cuboid / box candidates of the broad phase resolved exactly
 };
 
 }  // namespace tamp

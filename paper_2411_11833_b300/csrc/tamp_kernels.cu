@@ -72,6 +72,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
+int optimize_warps(int K);
+
+// Broad-phase candidates one lane can collect for one sphere batch: its share of
+// the cuboids and of the other boxes.
+__host__ __device__ __forceinline__ int list_capacity(int n_obs, int n_boxes, int L) {
+  return (n_obs + L - 1) / L + (n_boxes + L - 1) / L + 1;
+}
+
 // ------------------------------------------------------------------ frame helpers
 // A frame is R (row-major 3x3) and t.  Right-multiplications used by DH:
 __device__ __forceinline__ void rz_right(float* R, float c, float s) {  // T <- T Rz(theta)
@@ -94,21 +102,6 @@ __device__ __forceinline__ void rx_right(float* R, float c, float s) {  // T <- 
 __device__ __forceinline__ float tw(const uint32_t* terms, int t) { return __uint_as_float(terms[t * TERM_W + 1]); }
 
 // ------------------------------------------------------------------ collision core
-// Register-batch helpers: read or update element s (warp-uniform) of a small
-// register array with a select chain, which keeps the arrays in registers.
-template <int N>
-__device__ __forceinline__ float pick(const float (&a)[N], int s) {
-  float v = a[0];
-#pragma unroll
-  for (int i = 1; i < N; ++i) v = (s == i) ? a[i] : v;
-  return v;
-}
-template <int N>
-__device__ __forceinline__ void add_at(float (&a)[N], int s, float v) {
-#pragma unroll
-  for (int i = 0; i < N; ++i) a[i] += (s == i) ? v : 0.f;
-}
-
 // An oriented cuboid: t' = R^T t, R row-major (columns = box axes), half extents.
 struct Obb {
   float tx, ty, tz, r00, r01, r02, r10, r11, r12, r20, r21, r22, hx, hy, hz;
@@ -127,7 +120,6 @@ __device__ __forceinline__ Obb load_obb(const float4* __restrict__ obs, int o, i
   b.hx = d.x; b.hy = d.y; b.hz = d.z;
   return b;
 }
-__device__ __forceinline__ Obb sel_obb(bool second, const Obb& a, const Obb& b) { return second ? b : a; }
 // Point in the box frame: u = R^T c - t'.
 __device__ __forceinline__ void obb_local(const Obb& b, float x, float y, float z, float& ux, float& uy, float& uz) {
   ux = fmaf(b.r00, x, fmaf(b.r10, y, fmaf(b.r20, z, -b.tx)));
@@ -150,7 +142,7 @@ __device__ __forceinline__ float obb_pen(const Obb& b, float x, float y, float z
   const float mx = fmaxf(qx, 0.f), my = fmaxf(qy, 0.f), mz = fmaxf(qz, 0.f);
   const float o2 = fmaf(mx, mx, fmaf(my, my, mz * mz));
   gx = gy = gz = 0.f;
-  if (!(o2 < r * r)) return 0.f;
+  if (!(r > 0.f && o2 < r * r)) return 0.f;
   float dux = 0.f, duy = 0.f, duz = 0.f, sdf;
   if (o2 > 0.f) {
     const float d = sqrtf(o2);
@@ -181,123 +173,103 @@ __device__ __forceinline__ float obb_pen(const Obb& b, float x, float y, float z
 // d(depth)/d(centre) into (gx, gy, gz).  Gradients towards boxes whose pose is a
 // placement variable are added (times wenv) straight into the tile's gradient.
 //
-// Lane `sub` of the L lanes takes environment items sub, sub + L, ...; two
-// items at a time are tested against the NB spheres with a branch-free test
-// that never misses a contact, the warp ORs its candidate bits, and only the
-// (item, sphere) pairs some lane flagged get the exact penetration and gradient
-// (contacts are rare: well under 1% of pairs even for random particles).
+// Broad phase: a sphere (cb, Rb) bounding the batch is tested once against
+// every cuboid (max_i(|u_i| - h_i) < Rb, implied by any contact) and against
+// the bounding sphere of every other box; these tests never miss a contact,
+// and the items they pass (a few percent) go into this lane's list in shared
+// memory.  Exact phase: the warp drains all lanes' lists together, each lane
+// testing its own candidates sphere by sphere.  Pairs the broad phase skips
+// have zero penetration and zero gradient, so the result equals the all-pairs
+// sum.  Lane `sub` of the L lanes of a (particle, configuration) takes items
+// sub, sub + L, ...
 template <int L>
 __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy)[NB], const float (&cz)[NB],
                                          const float (&cr)[NB], float (&gx)[NB], float (&gy)[NB],
-                                         float (&gz)[NB], const float4* __restrict__ obs, int O,
-                                         const int* __restrict__ env, int n_env,
-                                         const float4* __restrict__ binit, const float* __restrict__ binit_hb,
-                                         const float4* __restrict__ envT4, const float* __restrict__ envThb,
+                                         float (&gz)[NB], float cbx, float cby, float cbz, float Rb,
+                                         const float4* __restrict__ obs, int O, const int* __restrict__ env,
+                                         int n_env, const float* __restrict__ boxr, const int* __restrict__ slots,
+                                         const float4* __restrict__ binit, const float4* __restrict__ envT4,
                                          int NBS, const float* __restrict__ X, float* G, int pl, int sub,
-                                         float wenv) {
+                                         float wenv, uint16_t* list, unsigned& n_obb, unsigned& n_box) {
   constexpr int PT = 32 / L;
-  float J = 0.f;
-  float ha[NB];
-#pragma unroll
-  for (int s = 0; s < NB; ++s)
-    ha[s] = 0.5f * fmaf(cx[s], cx[s], fmaf(cy[s], cy[s], fmaf(cz[s], cz[s], -cr[s] * cr[s]))) - SS_MARGIN;
-
-  for (int o0 = 0; o0 < O; o0 += 2 * L) {
-    const Obb A = load_obb(obs, o0 + sub, O);
-    const Obb B = load_obb(obs, o0 + L + sub, O);
-    unsigned hm = 0;
-#pragma unroll
-    for (int s = 0; s < NB; ++s) {
-      hm |= (obb_gap(A, cx[s], cy[s], cz[s]) < cr[s] ? 1u : 0u) << s;
-      hm |= (obb_gap(B, cx[s], cy[s], cz[s]) < cr[s] ? 1u : 0u) << (s + NB);
-    }
-    unsigned any = __reduce_or_sync(0xffffffffu, hm);
-    while (any) {
-      const int bit = __ffs(any) - 1;
-      any &= any - 1;
-      const int s = bit % NB;
-      const Obb o = sel_obb(bit >= NB, A, B);
-      float px_, py_, pz_;
-      J += obb_pen(o, pick(cx, s), pick(cy, s), pick(cz, s), pick(cr, s), px_, py_, pz_);
-      add_at(gx, s, px_);
-      add_at(gy, s, py_);
-      add_at(gz, s, pz_);
-    }
+  int cnt = 0;
+  for (int o = sub; o < O; o += L) {
+    const Obb b = load_obb(obs, o, O);
+    list[cnt * 32] = static_cast<uint16_t>(o);
+    cnt += obb_gap(b, cbx, cby, cbz) < Rb ? 1 : 0;
   }
-
-  // sphere vs the spheres of the other boxes: pen = max(0, r_a + r_b - ||c_a - c_b||).
-  // Boxes at their initial pose read the scene's world table (same for every
-  // particle); boxes on a placement variable read this iteration's per-particle
-  // table (slot-major, particle-minor).  Candidate test:
-  // c_a.c_b + r_a r_b - hb_b > ha_a  (|c_a - c_b|^2 - (r_a + r_b)^2 < 2 SS_MARGIN).
-  for (int ei = 0; ei < n_env; ++ei) {
-    const int src = env[ei * ENV_W + 1];
-    const float4* E4;
-    const float* Ehb;
-    int step;
-    float bx = 0.f, by = 0.f;
+  for (int ei = sub; ei < n_env; ei += L) {
+    const int* er = env + ei * ENV_W;
+    const int j = er[0], src = er[1];
+    const float* br = boxr + j * BOX_W;
+    float x, y, z;
     if (src < 0) {
-      const int j = env[ei * ENV_W];
-      E4 = binit + j * NBS;
-      Ehb = binit_hb + j * NBS;
-      step = 1;
+      x = br[4]; y = br[5]; z = br[6];
     } else {
-      const int slot = env[ei * ENV_W + 2];
-      E4 = envT4 + slot * NBS * PT + pl;
-      Ehb = envThb + slot * NBS * PT + pl;
-      step = PT;
-      bx = X[src * PT + pl];
-      by = X[(src + 1) * PT + pl];
+      x = X[src * PT + pl]; y = X[(src + 1) * PT + pl]; z = __int_as_float(slots[er[2] * SLOT_W + 2]);
     }
-    float fx = 0.f, fy = 0.f, tq = 0.f;  // push on a moving box: force and torque about its centre
-    for (int e0 = 0; e0 < NBS; e0 += 2 * L) {
-      float4 cA = make_float4(DUMMY_FAR, DUMMY_FAR, DUMMY_FAR, 0.f), cB = cA;
-      float hA = 1.5f * DUMMY_FAR * DUMMY_FAR, hB = hA;  // far away, zero radius: never a candidate
-      if (e0 + sub < NBS) {
-        cA = E4[(e0 + sub) * step];
-        hA = Ehb[(e0 + sub) * step];
-      }
-      if (e0 + L + sub < NBS) {
-        cB = E4[(e0 + L + sub) * step];
-        hB = Ehb[(e0 + L + sub) * step];
-      }
-      unsigned hm = 0;
+    const float dx = cbx - x, dy = cby - y, dz = cbz - z, R = Rb + br[3];
+    list[cnt * 32] = static_cast<uint16_t>(0x8000 | ei);
+    cnt += fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R * R ? 1 : 0;
+  }
+  float J = 0.f;
+  while (__any_sync(0xffffffffu, cnt > 0)) {
+    if (cnt > 0) {
+      --cnt;
+      const int id = list[cnt * 32];
+      if (id & 0x8000) {
+        ++n_box;
+        // the other box's spheres: pen = max(0, r_a + r_b - ||c_a - c_b||)
+        const int* er = env + (id & 0x7fff) * ENV_W;
+        const int src = er[1];
+        const float4* E4 = src < 0 ? binit + er[0] * NBS : envT4 + er[2] * NBS * PT + pl;
+        const int step = src < 0 ? 1 : PT;
+        float bx = 0.f, by = 0.f;
+        if (src >= 0) {
+          bx = X[src * PT + pl];
+          by = X[(src + 1) * PT + pl];
+        }
+        float fx = 0.f, fy = 0.f, tq = 0.f;  // push on a moving box: force, torque about its centre
+        for (int e = 0; e < NBS; ++e) {
+          const float4 c = E4[e * step];
 #pragma unroll
-      for (int s = 0; s < NB; ++s) {
-        const float dA = fmaf(cx[s], cA.x, fmaf(cy[s], cA.y, fmaf(cz[s], cA.z, fmaf(cr[s], cA.w, -hA))));
-        const float dB = fmaf(cx[s], cB.x, fmaf(cy[s], cB.y, fmaf(cz[s], cB.z, fmaf(cr[s], cB.w, -hB))));
-        hm |= (dA > ha[s] ? 1u : 0u) << s;
-        hm |= (dB > ha[s] ? 1u : 0u) << (s + NB);
-      }
-      unsigned any = __reduce_or_sync(0xffffffffu, hm);
-      while (any) {
-        const int bit = __ffs(any) - 1;
-        any &= any - 1;
-        const int s = bit % NB;
-        const float4 c = bit >= NB ? cB : cA;
-        const float dx = pick(cx, s) - c.x, dy = pick(cy, s) - c.y, dz = pick(cz, s) - c.z;
-        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float Rs = pick(cr, s) + c.w;
-        if (d2 < Rs * Rs) {
-          const float d = sqrtf(d2);
-          J += Rs - d;
-          if (d > 0.f) {
-            const float inv = 1.f / d;
-            const float vx = dx * inv, vy = dy * inv, vz = dz * inv;
-            add_at(gx, s, -vx);
-            add_at(gy, s, -vy);
-            add_at(gz, s, -vz);
-            fx += vx;
-            fy += vy;
-            tq = fmaf(c.x - bx, vy, fmaf(-(c.y - by), vx, tq));
+          for (int s = 0; s < NB; ++s) {
+            const float dx = cx[s] - c.x, dy = cy[s] - c.y, dz = cz[s] - c.z;
+            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float Rs = cr[s] + c.w;
+            if (Rs > 0.f && d2 < Rs * Rs) {
+              const float d = sqrtf(d2);
+              J += Rs - d;
+              if (d > 0.f) {
+                const float inv = 1.f / d;
+                const float vx = dx * inv, vy = dy * inv, vz = dz * inv;
+                gx[s] -= vx;
+                gy[s] -= vy;
+                gz[s] -= vz;
+                fx += vx;
+                fy += vy;
+                tq = fmaf(c.x - bx, vy, fmaf(-(c.y - by), vx, tq));
+              }
+            }
           }
         }
+        if (src >= 0 && (fx != 0.f || fy != 0.f || tq != 0.f)) {
+          atomicAdd(&G[src * PT + pl], wenv * fx);
+          atomicAdd(&G[(src + 1) * PT + pl], wenv * fy);
+          atomicAdd(&G[(src + 2) * PT + pl], wenv * tq);
+        }
+      } else {
+        ++n_obb;
+        const Obb b = load_obb(obs, id, O);
+#pragma unroll
+        for (int s = 0; s < NB; ++s) {
+          float px_, py_, pz_;
+          J += obb_pen(b, cx[s], cy[s], cz[s], cr[s], px_, py_, pz_);
+          gx[s] += px_;
+          gy[s] += py_;
+          gz[s] += pz_;
+        }
       }
-    }
-    if (src >= 0 && (fx != 0.f || fy != 0.f || tq != 0.f)) {
-      atomicAdd(&G[src * PT + pl], wenv * fx);
-      atomicAdd(&G[(src + 1) * PT + pl], wenv * fy);
-      atomicAdd(&G[(src + 2) * PT + pl], wenv * tq);
     }
   }
   return J;
@@ -332,7 +304,8 @@ __device__ __forceinline__ float bound_dist(const float (&v)[N], const float (&l
 template <int L>
 __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __restrict__ pb, int k,
                             const float* __restrict__ X, float* G, float* Tm, const float4* __restrict__ envT4,
-                            const float* __restrict__ envThb, int pl, int sub) {
+                            const int* __restrict__ slots, uint16_t* list, unsigned& n_obb, unsigned& n_box, int pl,
+                            int sub) {
   constexpr int PT = 32 / L;
   const int nj = sc[SH_NJ];
   const float* arm = reinterpret_cast<const float*>(sc + sc[SH_OFF_ARM]);
@@ -342,7 +315,7 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   const float* boxr = reinterpret_cast<const float*>(sc + sc[SH_OFF_BOX]);
   const float4* bloc = reinterpret_cast<const float4*>(sc + sc[SH_OFF_BLOC]);
   const float4* binit = reinterpret_cast<const float4*>(sc + sc[SH_OFF_BINIT]);
-  const float* binit_hb = reinterpret_cast<const float*>(sc + sc[SH_OFF_BINIT_HB]);
+  const float4* sphb = reinterpret_cast<const float4*>(sc + sc[SH_OFF_SPHB]);
   const float* surf = reinterpret_cast<const float*>(sc + sc[SH_OFF_SURF]);
   const int NBS = sc[SH_NBS];
   const int nbs_pad = (NBS + NB - 1) / NB * NB;
@@ -503,7 +476,7 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
       float4 p;
       if (phase == 0 || phase == 3) {
         const int lim = phase == 0 ? NBS : cp_first + cp_count;
-        p = (s0 + s < lim) ? bloc[b * NBS + s0 + s] : make_float4(DUMMY_FAR, DUMMY_FAR, DUMMY_FAR, 0.f);
+        p = (s0 + s < lim) ? bloc[b * NBS + s0 + s] : make_float4(DUMMY_FAR, DUMMY_FAR, DUMMY_FAR, -1.f);
         if (phase == 0 && s0 + s < NBS) {
           const float vx = p.x - gxv, vy = p.y - gyv, vz = p.z - gzv;
           const float wx = fmaf(cgr, vx, sgr * vy), wy = fmaf(sgr, vx, -cgr * vy), wz = -vz;
@@ -520,9 +493,39 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
       cr[s] = p.w;
       gx[s] = gyy[s] = gz[s] = 0.f;
     }
+    // sphere bounding the batch: arm batches from the scene's per-batch table
+    // (link frame); box batches from their spheres (a negative radius marks an
+    // unused slot)
+    float cbx, cby, cbz, Rb;
+    if (phase == 1 || phase == 2) {
+      const float4 bb = sphb[s0 / NB];
+      cbx = fmaf(R[0], bb.x, fmaf(R[1], bb.y, fmaf(R[2], bb.z, t[0])));
+      cby = fmaf(R[3], bb.x, fmaf(R[4], bb.y, fmaf(R[5], bb.z, t[1])));
+      cbz = fmaf(R[6], bb.x, fmaf(R[7], bb.y, fmaf(R[8], bb.z, t[2])));
+      Rb = bb.w;
+    } else {
+      float lox = 3.0e38f, loy = 3.0e38f, loz = 3.0e38f, hix = -3.0e38f, hiy = -3.0e38f, hiz = -3.0e38f;
+#pragma unroll
+      for (int s = 0; s < NB; ++s) {
+        if (cr[s] >= 0.f) {
+          lox = fminf(lox, cx[s]); hix = fmaxf(hix, cx[s]);
+          loy = fminf(loy, cyy[s]); hiy = fmaxf(hiy, cyy[s]);
+          loz = fminf(loz, cz[s]); hiz = fmaxf(hiz, cz[s]);
+        }
+      }
+      cbx = 0.5f * (lox + hix); cby = 0.5f * (loy + hiy); cbz = 0.5f * (loz + hiz);
+      Rb = -1.f;
+#pragma unroll
+      for (int s = 0; s < NB; ++s) {
+        if (cr[s] >= 0.f) {
+          const float dx = cx[s] - cbx, dy = cyy[s] - cby, dz = cz[s] - cbz;
+          Rb = fmaxf(Rb, sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + cr[s] + 1e-5f);
+        }
+      }
+    }
     const float wenv = phase == 3 ? w_cp : w_cf;
-    const float Jb = collide<L>(cx, cyy, cz, cr, gx, gyy, gz, obs, O, env, n_env, binit, binit_hb, envT4,
-                                envThb, NBS, X, G, pl, sub, wenv);
+    const float Jb = collide<L>(cx, cyy, cz, cr, gx, gyy, gz, cbx, cby, cbz, Rb, obs, O, env, n_env, boxr, slots,
+                                binit, envT4, NBS, X, G, pl, sub, wenv, list, n_obb, n_box);
     if (phase == 3) {
       J_place += Jb;
 #pragma unroll
@@ -723,8 +726,10 @@ __global__ void __launch_bounds__(384, 1) optimize_kernel(OptArgs a) {
   float* sg = sv + D * PT;
   float* st = sg + D * PT;
   float4* envT4 = reinterpret_cast<float4*>(st + NT * PT);   // [slot][e][particle]
-  float* envThb = reinterpret_cast<float*>(envT4 + NSLOT * NBS * PT);
-  int* sflag = reinterpret_cast<int*>(envThb + NSLOT * NBS * PT);
+  int* sflag = reinterpret_cast<int*>(envT4 + NSLOT * NBS * PT);
+  // per-lane candidate lists of the broad phase: [warp][entry][lane]
+  const int cap = list_capacity(a.scene[SH_O], a.scene[SH_B], L);
+  uint16_t* lists = reinterpret_cast<uint16_t*>(sflag + PT);
 
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int tile0 = blockIdx.x * PT;
@@ -767,6 +772,7 @@ __global__ void __launch_bounds__(384, 1) optimize_kernel(OptArgs a) {
   const int goal_warp = (K - 1) % W;
 
   double b1t = pow(static_cast<double>(a.beta1), a.t0), b2t = pow(static_cast<double>(a.beta2), a.t0);
+  unsigned n_obb = 0, n_box = 0;  // broad-phase candidates resolved exactly (work accounting)
   const int* slots = reinterpret_cast<const int*>(s_pb + s_pb[PH_OFF_SLOT]);
   const float4* bloc = reinterpret_cast<const float4*>(s_sc + s_sc[SH_OFF_BLOC]);
   for (int it = 0;; ++it) {
@@ -782,11 +788,11 @@ __global__ void __launch_bounds__(384, 1) optimize_kernel(OptArgs a) {
       const float ey = sx[(po + 1) * PT + p] + fmaf(sn, l.x, cs * l.y);
       const float ez = __int_as_float(sr[2]) + l.z;
       envT4[i] = make_float4(ex, ey, ez, l.w);
-      envThb[i] = 0.5f * fmaf(ex, ex, fmaf(ey, ey, fmaf(ez, ez, -l.w * l.w)));
     }
     for (int i = tid; i < NT * PT; i += nthr) st[i] = 0.f;  // CFreePlace terms are sums over two warps
     __syncthreads();
-    for (int k = w; k < K; k += W) eval_config<L>(s_sc, s_pb, k, sx, sg, st, envT4, envThb, pl, sub);
+    for (int k = w; k < K; k += W)
+      eval_config<L>(s_sc, s_pb, k, sx, sg, st, envT4, slots, lists + w * cap * 32 + lane, n_obb, n_box, pl, sub);
     if (w == goal_warp && sub == 0) eval_goal<L>(s_sc, s_pb, sx, sg, st, pl);
     __syncthreads();
     // Eq. 3 at x_t
@@ -820,6 +826,19 @@ __global__ void __launch_bounds__(384, 1) optimize_kernel(OptArgs a) {
     __syncthreads();
   }
   __syncthreads();
+
+  if (a.work) {
+    unsigned long long no = n_obb, nb = n_box;
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+      no += __shfl_xor_sync(0xffffffffu, no, m);
+      nb += __shfl_xor_sync(0xffffffffu, nb, m);
+    }
+    if (lane == 0) {
+      atomicAdd(&a.work[0], no);
+      atomicAdd(&a.work[1], nb);
+    }
+  }
 
   // ---------------- outputs of the last check
   if (tid < PT && tile0 + tid < a.P) {
@@ -911,8 +930,7 @@ static cudaError_t launch_opt(const OptArgs& a, int K, size_t smem, cudaStream_t
     if (e != cudaSuccess) return e;
     attr_bytes = smem;
   }
-  const int per = (K + 11) / 12;          // configurations per warp
-  const int W = (K + per - 1) / per;      // <= 12 warps (384 threads)
+  const int W = optimize_warps(K);
   const int grid = (a.P + PT - 1) / PT;
   if (grid == 0) return cudaSuccess;
   optimize_kernel<L><<<grid, W * 32, smem, st>>>(a);
@@ -938,11 +956,18 @@ cudaError_t launch_sample(const uint32_t* pb, const uint32_t* sc, float* x, floa
   return cudaGetLastError();
 }
 
-size_t optimize_smem_bytes(int scene_words, int prob_words, int D, int NT, int nslot, int nbs, int L) {
+size_t optimize_smem_bytes(int scene_words, int prob_words, int D, int NT, int nslot, int nbs, int n_obs,
+                           int n_boxes, int warps, int L) {
   const int PT = 32 / L;
   const size_t sw = (scene_words + 3) & ~3, pw = (prob_words + 3) & ~3;
   return 4 * (sw + pw) +
-         4 * (4 * static_cast<size_t>(D) * PT + static_cast<size_t>(NT) * PT + 5 * static_cast<size_t>(nslot) * nbs * PT + PT);
+         4 * (4 * static_cast<size_t>(D) * PT + static_cast<size_t>(NT) * PT + 4 * static_cast<size_t>(nslot) * nbs * PT + PT) +
+         2 * static_cast<size_t>(list_capacity(n_obs, n_boxes, L)) * 32 * warps;
+}
+
+int optimize_warps(int K) {
+  const int per = (K + 11) / 12;  // configurations per warp
+  return (K + per - 1) / per;     // <= 12 warps (384 threads)
 }
 
 }  // namespace tamp

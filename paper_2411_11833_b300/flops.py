@@ -1,71 +1,90 @@
-"""Algorithmic FP32 work of one particle evaluation (cost + adjoint) and of one
-Adam update, counted from a scene and a skeleton.
+"""FP32 work of the fused evaluation (cost + adjoint) and the Adam update.
 
-The counts are the arithmetic the definitions need per unit, with an FMA
-counted as 2 FLOP and a compare/max as 1; square roots, divisions, sines and
-the backward work of active (penetrating) pairs are data-dependent and not
-counted, so the figure is a lower bound of the work done.
+FMA = 2 FLOP, add/mul/compare/max = 1; square roots, divisions and sines are
+not counted, so the figures are lower bounds of the arithmetic done.
 
-Per configuration (arm with n joints, S arm spheres, the held box's NBS spheres):
-  forward kinematics           48 FLOP per joint (Rz, DH translation, Rx)
-  reverse sweep                48 FLOP per joint (inverse transforms) + 21 (torque)
-  sphere centres               18 FLOP per sphere (3x3 rotation + translation)
-  contact-test preparation      8 FLOP per sphere ((|c|^2 - r^2) / 2)
-  wrench accumulation          15 FLOP per sphere
-  held-box sphere into frame n 16 FLOP per sphere (G(g)^-1, tool)
-  sphere vs cuboid test        24 FLOP per pair (box-frame point 18, |u| - h 3, max 2, compare 1)
-  sphere vs sphere test         9 FLOP per pair (c_a.c_b + r_a r_b - hb: 4 FMA, compare 1)
-Per iteration and particle: 17 FLOP per sphere of every box standing on a
-placement variable (world centre and (|c|^2 - r^2) / 2).
-Adam: 12 FLOP per component.
+Fixed work per (particle, configuration) -- set by the scene and skeleton:
+  forward kinematics            48 FLOP per joint (Rz, DH translation, Rx)
+  reverse sweep                 69 FLOP per joint (inverse transforms 48, torque 21)
+  sphere centres                18 FLOP per sphere (3x3 rotation + translation)
+  wrench accumulation           15 FLOP per sphere
+  held-box sphere into frame n  16 FLOP per sphere (G(g)^-1, tool)
+  batch bounding sphere         18 FLOP per arm batch (table centre into the world),
+                                80 FLOP per box batch (from its spheres)
+  broad phase                   24 FLOP per (batch, cuboid)  (box-frame point 18, |u|-h 3, max 2, test 1)
+                                10 FLOP per (batch, other box) (difference 3, norm^2 5, radius sum 1, test 1)
+Data-dependent work (counted by the kernel, tamp_work_counters):
+  exact cuboid test             40 FLOP per sphere of a candidate batch (point 18, q 3, clamp 3,
+                                norm^2 5, test 1, gradient 10)
+  exact sphere pair             11 FLOP per (batch sphere, box sphere) of a candidate
+Per iteration and particle: 12 FLOP per sphere of every box on a placement
+variable (its world centre), 12 FLOP per Adam component.
 """
 from __future__ import annotations
 
 import math
 
 FK_JOINT = 48
-SWEEP_JOINT = 48 + 21
+SWEEP_JOINT = 69
 SPHERE_XFORM = 18
-SPHERE_PREP = 8
 SPHERE_WRENCH = 15
 HELD_SPHERE = 16
-PAIR_OBB = 24
-PAIR_SS = 9
-ENV_SPHERE = 17
+ARM_BOUND = 18
+BOX_BOUND = 80
+BROAD_OBB = 24
+BROAD_BOX = 10
+EXACT_OBB_SPHERE = 40
+EXACT_PAIR = 11
+ENV_SPHERE = 12
 ADAM = 12
+NB = 5
 
 
 def _walk(scene, actions):
-    """(kind, box, env boxes with 'moving' flags) per configuration, following the
-    skeleton's effects (boxes placed earlier sit at placement variables)."""
+    """(kind, box, n_env) per configuration; a Place's CFreePlace spheres are
+    split with the Pick before it."""
     B = scene.box_half.shape[0]
-    placed = [False] * B
     out = []
     for kind, b, _s in actions:
         if kind in (0, 1):
-            env = [(j, placed[j]) for j in range(B) if j != b]
-            out.append((kind, b, env))
-            if kind == 1:
-                placed[b] = True
+            out.append((kind, b, B - 1))
     return out
 
 
 def eval_flops(scene, actions) -> int:
+    """Fixed FLOP of one evaluation (cost + gradient) of one particle."""
     n = scene.dh_a.shape[0]
-    S = len(scene.sphere_link)              # real spheres only: padding slots are overhead
+    links = list(scene.sphere_link)
+    S = len(links)
+    arm_batches = sum(int(math.ceil(links.count(l) / NB)) for l in range(n + 1))
     nbs = scene.box_spheres.shape[1]
     O = scene.obs_center.shape[0]
+    cfgs = _walk(scene, actions)
     total = 0
     n_place = 0
-    for kind, b, env in _walk(scene, actions):
-        sph = S + nbs + (nbs if kind == 1 else 0)
-        env_sph = len(env) * nbs
+    for i, (kind, b, n_env) in enumerate(cfgs):
+        held_batches = int(math.ceil(nbs / NB))
+        if kind == 1:
+            half = nbs // 2 if i > 0 and cfgs[i - 1][0] == 0 and cfgs[i - 1][1] == b else 0
+            cp = nbs - half
+            n_place += 1
+        else:
+            nxt = cfgs[i + 1] if i + 1 < len(cfgs) else None
+            cp = nbs // 2 if nxt is not None and nxt[0] == 1 and nxt[1] == b else 0
+        place_batches = int(math.ceil(cp / NB))
+        batches = arm_batches + held_batches + place_batches
+        sph = S + nbs + cp
         total += n * (FK_JOINT + SWEEP_JOINT)
-        total += sph * (SPHERE_XFORM + SPHERE_PREP + SPHERE_WRENCH) + nbs * HELD_SPHERE
-        total += sph * O * PAIR_OBB + sph * env_sph * PAIR_SS
-        n_place += kind == 1
+        total += sph * (SPHERE_XFORM + SPHERE_WRENCH) + nbs * HELD_SPHERE
+        total += arm_batches * ARM_BOUND + (held_batches + place_batches) * BOX_BOUND
+        total += batches * (O * BROAD_OBB + n_env * BROAD_BOX)
     total += n_place * nbs * ENV_SPHERE
     return total
+
+
+def exact_flops(n_obb: int, n_box: int, nbs: int) -> int:
+    """Data-dependent FLOP from the kernel's candidate counters."""
+    return n_obb * NB * EXACT_OBB_SPHERE + n_box * NB * nbs * EXACT_PAIR
 
 
 def adam_flops(D: int) -> int:
