@@ -19,8 +19,7 @@ namespace tamp {
 cudaError_t launch_optimize(const OptArgs& a, int L, int K, size_t smem, cudaStream_t st);
 cudaError_t launch_sample(const uint32_t* pb, const uint32_t* sc, float* x, float* m, float* v, int stride, int P,
                           int D, uint64_t seed, cudaStream_t st);
-size_t optimize_smem_bytes(int scene_words, int prob_words, int D, int NT, int nslot, int nbs, int n_obs,
-                           int n_boxes, int warps, int L);
+size_t optimize_smem_bytes(int scene_words, int prob_words, int D, int NT, int warps, int L);
 int optimize_warps(int K);
 }  // namespace tamp
 
@@ -497,13 +496,26 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
 // the kernel's static shared variables
 constexpr size_t kMaxDynSmem = 227 * 1024 - 256;
 
-int pick_lanes(const Problem& pr, int P) {
-  if (pr.opt.lanes == 1 || pr.opt.lanes == 2 || pr.opt.lanes == 4 || pr.opt.lanes == 8) return pr.opt.lanes;
-  // enough (particle, configuration) warps to fill 148 SMs several times over -> 1 lane each
-  const long units = static_cast<long>(P) * pr.K;
-  if (units >= 148L * 32 * 16) return 1;
-  if (units >= 148L * 32 * 4) return 2;
-  return 4;
+size_t smem_for(const tamp_scene* s, const Problem& pr, int L) {
+  return optimize_smem_bytes(static_cast<int>(s->blob.size()), static_cast<int>(pr.blob.size()), pr.D, pr.NT,
+                             optimize_warps(pr.K), L);
+}
+
+// Threads per (particle, configuration).  More lanes split each configuration's
+// environment (shorter critical path, more warps for small batches) but repeat
+// its kinematics; fewer lanes keep more particles per CTA.  The requested or
+// preferred value is lowered/raised until the CTA's shared memory fits.
+int pick_lanes(const tamp_scene* s, const Problem& pr, int P, size_t* smem) {
+  int L = pr.opt.lanes;
+  if (L != 1 && L != 2 && L != 4 && L != 8) {
+    const long units = static_cast<long>(P) * pr.K;  // (particle, configuration) pairs
+    L = units >= 148L * 32 * 24 ? 1 : (units >= 148L * 32 * 6 ? 2 : 4);
+  }
+  for (; L <= 8; L *= 2) {
+    *smem = smem_for(s, pr, L);
+    if (*smem <= kMaxDynSmem) return L;
+  }
+  return 0;
 }
 
 void free_batch(Problem& pr) {
@@ -557,11 +569,10 @@ tamp_status run_state(tamp_scene* s, Problem& pr, int n_steps) {
   a.work = pr.d_work;
   a.n_steps = n_steps; a.t0 = pr.t;
   a.gscale = pr.opt.scale_by_batch ? 1.f / static_cast<float>(pr.P) : 1.f;
-  const int L = pick_lanes(pr, pr.P);
   CUDA_TRY(s, cudaMemsetAsync(pr.d_counts, 0, static_cast<size_t>(std::max(pr.NCON, 1)) * 4, s->stream));
-  const size_t smem = optimize_smem_bytes(a.scene_words, a.prob_words, pr.D, pr.NT, pr.NSLOT, s->NBS, s->O, s->B,
-                                         optimize_warps(pr.K), L);
-  if (smem > kMaxDynSmem) return fail(s, TAMP_ERR_INVALID_ARG, "problem needs %zu B of shared memory", smem);
+  size_t smem = 0;
+  const int L = pick_lanes(s, pr, pr.P, &smem);
+  if (L == 0) return fail(s, TAMP_ERR_INVALID_ARG, "problem does not fit in shared memory (D=%d)", pr.D);
   CUDA_TRY(s, launch_optimize(a, L, pr.K, smem, s->stream));
   pr.t += n_steps;
   pr.checked = true;
@@ -800,10 +811,9 @@ tamp_status tamp_eval(tamp_scene* s, int id, int n, const float* x, float* cost,
   a.x_in = x; a.stride = n; a.P = n;
   a.out_cost = cost; a.out_terms = terms; a.out_flags = flags; a.out_grad = grad;
   a.first_iter = nullptr; a.n_steps = 0; a.t0 = 0;
-  const int L = pick_lanes(*pr, n);
-  const size_t smem = optimize_smem_bytes(a.scene_words, a.prob_words, pr->D, pr->NT, pr->NSLOT, s->NBS, s->O, s->B,
-                                         optimize_warps(pr->K), L);
-  if (smem > kMaxDynSmem) return fail(s, TAMP_ERR_INVALID_ARG, "problem needs %zu B of shared memory", smem);
+  size_t smem = 0;
+  const int L = pick_lanes(s, *pr, n, &smem);
+  if (L == 0) return fail(s, TAMP_ERR_INVALID_ARG, "problem does not fit in shared memory (D=%d)", pr->D);
   CUDA_TRY(s, launch_optimize(a, L, pr->K, smem, s->stream));
   return TAMP_OK;
 }

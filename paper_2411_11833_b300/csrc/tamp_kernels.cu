@@ -74,11 +74,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 int optimize_warps(int K);
 
-// Broad-phase candidates one lane can collect for one sphere batch: its share of
-// the cuboids and of the other boxes.
-__host__ __device__ __forceinline__ int list_capacity(int n_obs, int n_boxes, int L) {
-  return (n_obs + L - 1) / L + (n_boxes + L - 1) / L + 1;
-}
+// Broad-phase candidates are collected per chunk of LIST_CAP items per lane.
+constexpr int LIST_CAP = 16;
 
 // ------------------------------------------------------------------ frame helpers
 // A frame is R (row-major 3x3) and t.  Right-multiplications used by DH:
@@ -188,86 +185,100 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
                                          float (&gz)[NB], float cbx, float cby, float cbz, float Rb,
                                          const float4* __restrict__ obs, int O, const int* __restrict__ env,
                                          int n_env, const float* __restrict__ boxr, const int* __restrict__ slots,
-                                         const float4* __restrict__ binit, const float4* __restrict__ envT4,
+                                         const float4* __restrict__ bloc, const float4* __restrict__ binit,
                                          int NBS, const float* __restrict__ X, float* G, int pl, int sub,
                                          float wenv, uint16_t* list, unsigned& n_obb, unsigned& n_box) {
   constexpr int PT = 32 / L;
-  int cnt = 0;
-  for (int o = sub; o < O; o += L) {
-    const Obb b = load_obb(obs, o, O);
-    list[cnt * 32] = static_cast<uint16_t>(o);
-    cnt += obb_gap(b, cbx, cby, cbz) < Rb ? 1 : 0;
-  }
-  for (int ei = sub; ei < n_env; ei += L) {
-    const int* er = env + ei * ENV_W;
-    const int j = er[0], src = er[1];
-    const float* br = boxr + j * BOX_W;
-    float x, y, z;
-    if (src < 0) {
-      x = br[4]; y = br[5]; z = br[6];
-    } else {
-      x = X[src * PT + pl]; y = X[(src + 1) * PT + pl]; z = __int_as_float(slots[er[2] * SLOT_W + 2]);
-    }
-    const float dx = cbx - x, dy = cby - y, dz = cbz - z, R = Rb + br[3];
-    list[cnt * 32] = static_cast<uint16_t>(0x8000 | ei);
-    cnt += fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R * R ? 1 : 0;
-  }
   float J = 0.f;
-  while (__any_sync(0xffffffffu, cnt > 0)) {
-    if (cnt > 0) {
-      --cnt;
-      const int id = list[cnt * 32];
-      if (id & 0x8000) {
-        ++n_box;
-        // the other box's spheres: pen = max(0, r_a + r_b - ||c_a - c_b||)
-        const int* er = env + (id & 0x7fff) * ENV_W;
+  const int n_items = O + n_env;  // cuboids, then the other boxes
+  for (int base = 0; base < n_items; base += LIST_CAP * L) {
+    // broad phase over this chunk: candidates go to the lane's list
+    int cnt = 0;
+    const int end = min(base + LIST_CAP * L, n_items);
+    for (int i = base + sub; i < end; i += L) {
+      bool cand;
+      if (i < O) {
+        cand = obb_gap(load_obb(obs, i, O), cbx, cby, cbz) < Rb;
+      } else {
+        const int* er = env + (i - O) * ENV_W;
         const int src = er[1];
-        const float4* E4 = src < 0 ? binit + er[0] * NBS : envT4 + er[2] * NBS * PT + pl;
-        const int step = src < 0 ? 1 : PT;
-        float bx = 0.f, by = 0.f;
-        if (src >= 0) {
-          bx = X[src * PT + pl];
-          by = X[(src + 1) * PT + pl];
+        const float* br = boxr + er[0] * BOX_W;
+        float x, y, z;
+        if (src < 0) {
+          x = br[4]; y = br[5]; z = br[6];
+        } else {
+          x = X[src * PT + pl]; y = X[(src + 1) * PT + pl]; z = __int_as_float(slots[er[2] * SLOT_W + 2]);
         }
-        float fx = 0.f, fy = 0.f, tq = 0.f;  // push on a moving box: force, torque about its centre
-        for (int e = 0; e < NBS; ++e) {
-          const float4 c = E4[e * step];
+        const float dx = cbx - x, dy = cby - y, dz = cbz - z, R = Rb + br[3];
+        cand = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R * R;
+      }
+      list[cnt * 32] = static_cast<uint16_t>(i);
+      cnt += cand ? 1 : 0;
+    }
+    // exact phase: the warp drains all lanes' lists together
+    while (__any_sync(0xffffffffu, cnt > 0)) {
+      if (cnt > 0) {
+        --cnt;
+        const int i = list[cnt * 32];
+        if (i >= O) {
+          // the other box's spheres: pen = max(0, r_a + r_b - ||c_a - c_b||)
+          ++n_box;
+          const int* er = env + (i - O) * ENV_W;
+          const int j = er[0], src = er[1];
+          // a box on a placement variable: its spheres in the world from (x, y, yaw)
+          float bx = 0.f, by = 0.f, bz = 0.f, sn = 0.f, cs = 1.f;
+          if (src >= 0) {
+            bx = X[src * PT + pl];
+            by = X[(src + 1) * PT + pl];
+            bz = __int_as_float(slots[er[2] * SLOT_W + 2]);
+            sincosf(X[(src + 2) * PT + pl], &sn, &cs);
+          }
+          float fx = 0.f, fy = 0.f, tq = 0.f;  // push on a moving box: force, torque about its centre
+          for (int e = 0; e < NBS; ++e) {
+            float4 c;
+            if (src < 0) {
+              c = binit[j * NBS + e];
+            } else {
+              const float4 l = bloc[j * NBS + e];
+              c = make_float4(bx + fmaf(cs, l.x, -sn * l.y), by + fmaf(sn, l.x, cs * l.y), bz + l.z, l.w);
+            }
 #pragma unroll
-          for (int s = 0; s < NB; ++s) {
-            const float dx = cx[s] - c.x, dy = cy[s] - c.y, dz = cz[s] - c.z;
-            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float Rs = cr[s] + c.w;
-            if (Rs > 0.f && d2 < Rs * Rs) {
-              const float d = sqrtf(d2);
-              J += Rs - d;
-              if (d > 0.f) {
-                const float inv = 1.f / d;
-                const float vx = dx * inv, vy = dy * inv, vz = dz * inv;
-                gx[s] -= vx;
-                gy[s] -= vy;
-                gz[s] -= vz;
-                fx += vx;
-                fy += vy;
-                tq = fmaf(c.x - bx, vy, fmaf(-(c.y - by), vx, tq));
+            for (int s = 0; s < NB; ++s) {
+              const float dx = cx[s] - c.x, dy = cy[s] - c.y, dz = cz[s] - c.z;
+              const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+              const float Rs = cr[s] + c.w;
+              if (Rs > 0.f && d2 < Rs * Rs) {
+                const float d = sqrtf(d2);
+                J += Rs - d;
+                if (d > 0.f) {
+                  const float inv = 1.f / d;
+                  const float vx = dx * inv, vy = dy * inv, vz = dz * inv;
+                  gx[s] -= vx;
+                  gy[s] -= vy;
+                  gz[s] -= vz;
+                  fx += vx;
+                  fy += vy;
+                  tq = fmaf(c.x - bx, vy, fmaf(-(c.y - by), vx, tq));
+                }
               }
             }
           }
-        }
-        if (src >= 0 && (fx != 0.f || fy != 0.f || tq != 0.f)) {
-          atomicAdd(&G[src * PT + pl], wenv * fx);
-          atomicAdd(&G[(src + 1) * PT + pl], wenv * fy);
-          atomicAdd(&G[(src + 2) * PT + pl], wenv * tq);
-        }
-      } else {
-        ++n_obb;
-        const Obb b = load_obb(obs, id, O);
+          if (src >= 0 && (fx != 0.f || fy != 0.f || tq != 0.f)) {
+            atomicAdd(&G[src * PT + pl], wenv * fx);
+            atomicAdd(&G[(src + 1) * PT + pl], wenv * fy);
+            atomicAdd(&G[(src + 2) * PT + pl], wenv * tq);
+          }
+        } else {
+          ++n_obb;
+          const Obb b = load_obb(obs, i, O);
 #pragma unroll
-        for (int s = 0; s < NB; ++s) {
-          float px_, py_, pz_;
-          J += obb_pen(b, cx[s], cy[s], cz[s], cr[s], px_, py_, pz_);
-          gx[s] += px_;
-          gy[s] += py_;
-          gz[s] += pz_;
+          for (int s = 0; s < NB; ++s) {
+            float px_, py_, pz_;
+            J += obb_pen(b, cx[s], cy[s], cz[s], cr[s], px_, py_, pz_);
+            gx[s] += px_;
+            gy[s] += py_;
+            gz[s] += pz_;
+          }
         }
       }
     }
@@ -303,8 +314,7 @@ __device__ __forceinline__ float bound_dist(const float (&v)[N], const float (&l
 //   phase 3  the placed box at P(p) (Place configurations: CFreePlace)
 template <int L>
 __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __restrict__ pb, int k,
-                            const float* __restrict__ X, float* G, float* Tm, const float4* __restrict__ envT4,
-                            const int* __restrict__ slots, uint16_t* list, unsigned& n_obb, unsigned& n_box, int pl,
+                            const float* __restrict__ X, float* G, float* Tm, const int* __restrict__ slots, uint16_t* list, unsigned& n_obb, unsigned& n_box, int pl,
                             int sub) {
   constexpr int PT = 32 / L;
   const int nj = sc[SH_NJ];
@@ -525,7 +535,7 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
     }
     const float wenv = phase == 3 ? w_cp : w_cf;
     const float Jb = collide<L>(cx, cyy, cz, cr, gx, gyy, gz, cbx, cby, cbz, Rb, obs, O, env, n_env, boxr, slots,
-                                binit, envT4, NBS, X, G, pl, sub, wenv, list, n_obb, n_box);
+                                bloc, binit, NBS, X, G, pl, sub, wenv, list, n_obb, n_box);
     if (phase == 3) {
       J_place += Jb;
 #pragma unroll
@@ -719,16 +729,14 @@ __global__ void __launch_bounds__(384, 1) optimize_kernel(OptArgs a) {
   uint32_t* s_sc = reinterpret_cast<uint32_t*>(smem_raw);
   uint32_t* s_pb = s_sc + sw;
   const int D = a.prob[PH_D], K = a.prob[PH_K], NT = a.prob[PH_NT];
-  const int NSLOT = a.prob[PH_NSLOT], NBS = a.scene[SH_NBS];
   float* sx = reinterpret_cast<float*>(s_pb + pw);
   float* sm = sx + D * PT;
   float* sv = sm + D * PT;
   float* sg = sv + D * PT;
   float* st = sg + D * PT;
-  float4* envT4 = reinterpret_cast<float4*>(st + NT * PT);   // [slot][e][particle]
-  int* sflag = reinterpret_cast<int*>(envT4 + NSLOT * NBS * PT);
+  int* sflag = reinterpret_cast<int*>(st + NT * PT);
   // per-lane candidate lists of the broad phase: [warp][entry][lane]
-  const int cap = list_capacity(a.scene[SH_O], a.scene[SH_B], L);
+  const int cap = LIST_CAP;
   uint16_t* lists = reinterpret_cast<uint16_t*>(sflag + PT);
 
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -776,23 +784,10 @@ __global__ void __launch_bounds__(384, 1) optimize_kernel(OptArgs a) {
   const int* slots = reinterpret_cast<const int*>(s_pb + s_pb[PH_OFF_SLOT]);
   const float4* bloc = reinterpret_cast<const float4*>(s_sc + s_sc[SH_OFF_BLOC]);
   for (int it = 0;; ++it) {
-    // world spheres of every box standing on a placement variable, once per particle
-    for (int i = tid; i < NSLOT * NBS * PT; i += nthr) {
-      const int p = i % PT, se = i / PT, slot = se / NBS, e = se % NBS;
-      const int* sr = slots + slot * SLOT_W;
-      const int po = sr[1];
-      float sn, cs;
-      sincosf(sx[(po + 2) * PT + p], &sn, &cs);
-      const float4 l = bloc[sr[0] * NBS + e];
-      const float ex = sx[po * PT + p] + fmaf(cs, l.x, -sn * l.y);
-      const float ey = sx[(po + 1) * PT + p] + fmaf(sn, l.x, cs * l.y);
-      const float ez = __int_as_float(sr[2]) + l.z;
-      envT4[i] = make_float4(ex, ey, ez, l.w);
-    }
     for (int i = tid; i < NT * PT; i += nthr) st[i] = 0.f;  // CFreePlace terms are sums over two warps
     __syncthreads();
     for (int k = w; k < K; k += W)
-      eval_config<L>(s_sc, s_pb, k, sx, sg, st, envT4, slots, lists + w * cap * 32 + lane, n_obb, n_box, pl, sub);
+      eval_config<L>(s_sc, s_pb, k, sx, sg, st, slots, lists + w * cap * 32 + lane, n_obb, n_box, pl, sub);
     if (w == goal_warp && sub == 0) eval_goal<L>(s_sc, s_pb, sx, sg, st, pl);
     __syncthreads();
     // Eq. 3 at x_t
@@ -956,13 +951,11 @@ cudaError_t launch_sample(const uint32_t* pb, const uint32_t* sc, float* x, floa
   return cudaGetLastError();
 }
 
-size_t optimize_smem_bytes(int scene_words, int prob_words, int D, int NT, int nslot, int nbs, int n_obs,
-                           int n_boxes, int warps, int L) {
+size_t optimize_smem_bytes(int scene_words, int prob_words, int D, int NT, int warps, int L) {
   const int PT = 32 / L;
   const size_t sw = (scene_words + 3) & ~3, pw = (prob_words + 3) & ~3;
-  return 4 * (sw + pw) +
-         4 * (4 * static_cast<size_t>(D) * PT + static_cast<size_t>(NT) * PT + 4 * static_cast<size_t>(nslot) * nbs * PT + PT) +
-         2 * static_cast<size_t>(list_capacity(n_obs, n_boxes, L)) * 32 * warps;
+  return 4 * (sw + pw) + 4 * (4 * static_cast<size_t>(D) * PT + static_cast<size_t>(NT) * PT + PT) +
+         2 * static_cast<size_t>(LIST_CAP) * 32 * warps;
 }
 
 int optimize_warps(int K) {
