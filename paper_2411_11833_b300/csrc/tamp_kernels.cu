@@ -192,13 +192,14 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
   float J = 0.f;
   const int n_items = O + n_env;  // cuboids, then the other boxes
   for (int base = 0; base < n_items; base += LIST_CAP * L) {
-    // broad phase over this chunk: candidates go to the lane's list
-    int cnt = 0;
+    // broad phase over this chunk: cuboid candidates fill the lane's list from
+    // the front, box candidates from the back
+    int nc = 0, nbx = 0;
     const int end = min(base + LIST_CAP * L, n_items);
     for (int i = base + sub; i < end; i += L) {
-      bool cand;
       if (i < O) {
-        cand = obb_gap(load_obb(obs, i, O), cbx, cby, cbz) < Rb;
+        list[nc * 32] = static_cast<uint16_t>(i);
+        nc += obb_gap(load_obb(obs, i, O), cbx, cby, cbz) < Rb ? 1 : 0;
       } else {
         const int* er = env + (i - O) * ENV_W;
         const int src = er[1];
@@ -210,75 +211,78 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
           x = X[src * PT + pl]; y = X[(src + 1) * PT + pl]; z = __int_as_float(slots[er[2] * SLOT_W + 2]);
         }
         const float dx = cbx - x, dy = cby - y, dz = cbz - z, R = Rb + br[3];
-        cand = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R * R;
+        list[(LIST_CAP - 1 - nbx) * 32] = static_cast<uint16_t>(i);
+        nbx += fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R * R ? 1 : 0;
       }
-      list[cnt * 32] = static_cast<uint16_t>(i);
-      cnt += cand ? 1 : 0;
     }
-    // exact phase: the warp drains all lanes' lists together
-    while (__any_sync(0xffffffffu, cnt > 0)) {
-      if (cnt > 0) {
-        --cnt;
-        const int i = list[cnt * 32];
-        if (i >= O) {
-          // the other box's spheres: pen = max(0, r_a + r_b - ||c_a - c_b||)
-          ++n_box;
-          const int* er = env + (i - O) * ENV_W;
-          const int j = er[0], src = er[1];
-          // a box on a placement variable: its spheres in the world from (x, y, yaw)
-          float bx = 0.f, by = 0.f, bz = 0.f, sn = 0.f, cs = 1.f;
-          if (src >= 0) {
-            bx = X[src * PT + pl];
-            by = X[(src + 1) * PT + pl];
-            bz = __int_as_float(slots[er[2] * SLOT_W + 2]);
-            sincosf(X[(src + 2) * PT + pl], &sn, &cs);
-          }
-          float fx = 0.f, fy = 0.f, tq = 0.f;  // push on a moving box: force, torque about its centre
-          for (int e = 0; e < NBS; ++e) {
-            float4 c;
-            if (src < 0) {
-              c = binit[j * NBS + e];
-            } else {
-              const float4 l = bloc[j * NBS + e];
-              c = make_float4(bx + fmaf(cs, l.x, -sn * l.y), by + fmaf(sn, l.x, cs * l.y), bz + l.z, l.w);
-            }
+    // exact phase, cuboids: the warp drains all lanes' lists together
+    while (__any_sync(0xffffffffu, nc > 0)) {
+      if (nc > 0) {
+        --nc;
+        ++n_obb;
+        const Obb b = load_obb(obs, list[nc * 32], O);
 #pragma unroll
-            for (int s = 0; s < NB; ++s) {
-              const float dx = cx[s] - c.x, dy = cy[s] - c.y, dz = cz[s] - c.z;
-              const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-              const float Rs = cr[s] + c.w;
-              if (Rs > 0.f && d2 < Rs * Rs) {
-                const float d = sqrtf(d2);
-                J += Rs - d;
-                if (d > 0.f) {
-                  const float inv = 1.f / d;
-                  const float vx = dx * inv, vy = dy * inv, vz = dz * inv;
-                  gx[s] -= vx;
-                  gy[s] -= vy;
-                  gz[s] -= vz;
-                  fx += vx;
-                  fy += vy;
-                  tq = fmaf(c.x - bx, vy, fmaf(-(c.y - by), vx, tq));
-                }
+        for (int s = 0; s < NB; ++s) {
+          float px_, py_, pz_;
+          J += obb_pen(b, cx[s], cy[s], cz[s], cr[s], px_, py_, pz_);
+          gx[s] += px_;
+          gy[s] += py_;
+          gz[s] += pz_;
+        }
+      }
+    }
+    // exact phase, other boxes: pen = max(0, r_a + r_b - ||c_a - c_b||); each of
+    // the box's spheres is first checked against the batch's bounding sphere
+    while (__any_sync(0xffffffffu, nbx > 0)) {
+      if (nbx > 0) {
+        --nbx;
+        ++n_box;
+        const int* er = env + (list[(LIST_CAP - 1 - nbx) * 32] - O) * ENV_W;
+        const int j = er[0], src = er[1];
+        // a box on a placement variable: its spheres in the world from (x, y, yaw)
+        float bx = 0.f, by = 0.f, bz = 0.f, sn = 0.f, cs = 1.f;
+        if (src >= 0) {
+          bx = X[src * PT + pl];
+          by = X[(src + 1) * PT + pl];
+          bz = __int_as_float(slots[er[2] * SLOT_W + 2]);
+          sincosf(X[(src + 2) * PT + pl], &sn, &cs);
+        }
+        float fx = 0.f, fy = 0.f, tq = 0.f;  // push on a moving box: force, torque about its centre
+        for (int e = 0; e < NBS; ++e) {
+          float4 c;
+          if (src < 0) {
+            c = binit[j * NBS + e];
+          } else {
+            const float4 l = bloc[j * NBS + e];
+            c = make_float4(bx + fmaf(cs, l.x, -sn * l.y), by + fmaf(sn, l.x, cs * l.y), bz + l.z, l.w);
+          }
+          const float ex = cbx - c.x, ey = cby - c.y, ez = cbz - c.z, Re = Rb + c.w;
+          if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) >= Re * Re) continue;
+#pragma unroll
+          for (int s = 0; s < NB; ++s) {
+            const float dx = cx[s] - c.x, dy = cy[s] - c.y, dz = cz[s] - c.z;
+            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float Rs = cr[s] + c.w;
+            if (Rs > 0.f && d2 < Rs * Rs) {
+              const float d = sqrtf(d2);
+              J += Rs - d;
+              if (d > 0.f) {
+                const float inv = 1.f / d;
+                const float vx = dx * inv, vy = dy * inv, vz = dz * inv;
+                gx[s] -= vx;
+                gy[s] -= vy;
+                gz[s] -= vz;
+                fx += vx;
+                fy += vy;
+                tq = fmaf(c.x - bx, vy, fmaf(-(c.y - by), vx, tq));
               }
             }
           }
-          if (src >= 0 && (fx != 0.f || fy != 0.f || tq != 0.f)) {
-            atomicAdd(&G[src * PT + pl], wenv * fx);
-            atomicAdd(&G[(src + 1) * PT + pl], wenv * fy);
-            atomicAdd(&G[(src + 2) * PT + pl], wenv * tq);
-          }
-        } else {
-          ++n_obb;
-          const Obb b = load_obb(obs, i, O);
-#pragma unroll
-          for (int s = 0; s < NB; ++s) {
-            float px_, py_, pz_;
-            J += obb_pen(b, cx[s], cy[s], cz[s], cr[s], px_, py_, pz_);
-            gx[s] += px_;
-            gy[s] += py_;
-            gz[s] += pz_;
-          }
+        }
+        if (src >= 0 && (fx != 0.f || fy != 0.f || tq != 0.f)) {
+          atomicAdd(&G[src * PT + pl], wenv * fx);
+          atomicAdd(&G[(src + 1) * PT + pl], wenv * fy);
+          atomicAdd(&G[(src + 2) * PT + pl], wenv * tq);
         }
       }
     }
