@@ -74,8 +74,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 int optimize_warps(int K);
 
-// Broad-phase candidates are collected per chunk of LIST_CAP items per lane.
-constexpr int LIST_CAP = 16;
+// The broad phase runs over chunks of QUEUE_CHUNK items per lane, so a warp's
+// candidate queue never holds more than QUEUE_CAP entries.
+constexpr int QUEUE_CHUNK = 16;
+constexpr int QUEUE_CAP = 32 * QUEUE_CHUNK;
+// shared memory of one warp's WarpScratch: queue, counters (padded), accumulators
+constexpr int WARP_SCRATCH_BYTES = QUEUE_CAP * 4 + 16 + 32 * NB * 16;
 
 // ------------------------------------------------------------------ frame helpers
 // A frame is R (row-major 3x3) and t.  Right-multiplications used by DH:
@@ -164,21 +168,32 @@ __device__ __forceinline__ float obb_pen(const Obb& b, float x, float y, float z
   return r - sdf;
 }
 
-// Penetration of a register batch of NB spheres into the environment of one
-// configuration: the static cuboids and the spheres of every other box at its
-// current pose.  Returns the summed penetration depth (unweighted) and adds
-// d(depth)/d(centre) into (gx, gy, gz).  Gradients towards boxes whose pose is a
-// placement variable are added (times wenv) straight into the tile's gradient.
+// Per-warp scratch of the exact phase in shared memory: the candidate queue
+// (cuboid entries from the front, box entries from the back) and per-owner
+// accumulators (gradient and penetration of each of its NB spheres).
+struct WarpScratch {
+  uint32_t* queue;   // QUEUE_CAP entries: owner lane << 16 | item
+  int* count;        // [2]: cuboid entries, box entries
+  float4* acc;       // [32][NB]: (dpen/dc x, y, z; pen)
+};
+
+// Penetration of the register batches of NB spheres held by the 32 lanes of a
+// warp into the environment of their configurations: static cuboids and the
+// spheres of every other box at its current pose.  Returns this lane's summed
+// penetration depth (unweighted) and adds d(depth)/d(centre) into (gx, gy, gz);
+// gradients towards boxes whose pose is a placement variable are added (times
+// wenv) straight into the tile's gradient.
 //
-// Broad phase: a sphere (cb, Rb) bounding the batch is tested once against
-// every cuboid (max_i(|u_i| - h_i) < Rb, implied by any contact) and against
-// the bounding sphere of every other box; these tests never miss a contact,
-// and the items they pass (a few percent) go into this lane's list in shared
-// memory.  Exact phase: the warp drains all lanes' lists together, each lane
-// testing its own candidates sphere by sphere.  Pairs the broad phase skips
-// have zero penetration and zero gradient, so the result equals the all-pairs
-// sum.  Lane `sub` of the L lanes of a (particle, configuration) takes items
-// sub, sub + L, ...
+// Broad phase (per lane): a sphere (cb, Rb) bounding the lane's batch is tested
+// once against every cuboid (max_i(|u_i| - h_i) < Rb, implied by any contact)
+// and against the bounding sphere of every other box.  These tests never miss a
+// contact; the few percent of items that pass are appended to the warp's queue.
+// Exact phase (per warp): every lane takes one queued (owner, item) pair, pulls
+// the owner's spheres by shuffle, computes the exact penetrations and gradients
+// and adds them to the owner's accumulators -- all 32 lanes work whatever the
+// owners.  Pairs the broad phase skips have zero penetration and gradient, so
+// the result equals the all-pairs sum.  Lane `sub` of the L lanes of a
+// (particle, configuration) takes items sub, sub + L, ...
 template <int L>
 __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy)[NB], const float (&cz)[NB],
                                          const float (&cr)[NB], float (&gx)[NB], float (&gy)[NB],
@@ -187,19 +202,19 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
                                          int n_env, const float* __restrict__ boxr, const int* __restrict__ slots,
                                          const float4* __restrict__ bloc, const float4* __restrict__ binit,
                                          int NBS, const float* __restrict__ X, float* G, int pl, int sub,
-                                         float wenv, uint16_t* list, unsigned& n_obb, unsigned& n_box) {
+                                         int lane, float wenv, const WarpScratch& ws, unsigned& n_obb,
+                                         unsigned& n_box) {
   constexpr int PT = 32 / L;
-  float J = 0.f;
   const int n_items = O + n_env;  // cuboids, then the other boxes
-  for (int base = 0; base < n_items; base += LIST_CAP * L) {
-    // broad phase over this chunk: cuboid candidates fill the lane's list from
-    // the front, box candidates from the back
-    int nc = 0, nbx = 0;
-    const int end = min(base + LIST_CAP * L, n_items);
+  for (int base = 0; base < n_items; base += QUEUE_CHUNK * L) {
+    // ---- broad phase over this chunk of items
+    const int end = min(base + QUEUE_CHUNK * L, n_items);
     for (int i = base + sub; i < end; i += L) {
       if (i < O) {
-        list[nc * 32] = static_cast<uint16_t>(i);
-        nc += obb_gap(load_obb(obs, i, O), cbx, cby, cbz) < Rb ? 1 : 0;
+        if (obb_gap(load_obb(obs, i, O), cbx, cby, cbz) < Rb) {
+          const int q = atomicAdd(&ws.count[0], 1);
+          ws.queue[q] = static_cast<uint32_t>(lane) << 16 | static_cast<uint32_t>(i);
+        }
       } else {
         const int* er = env + (i - O) * ENV_W;
         const int src = er[1];
@@ -211,42 +226,78 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
           x = X[src * PT + pl]; y = X[(src + 1) * PT + pl]; z = __int_as_float(slots[er[2] * SLOT_W + 2]);
         }
         const float dx = cbx - x, dy = cby - y, dz = cbz - z, R = Rb + br[3];
-        list[(LIST_CAP - 1 - nbx) * 32] = static_cast<uint16_t>(i);
-        nbx += fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R * R ? 1 : 0;
-      }
-    }
-    // exact phase, cuboids: the warp drains all lanes' lists together
-    while (__any_sync(0xffffffffu, nc > 0)) {
-      if (nc > 0) {
-        --nc;
-        ++n_obb;
-        const Obb b = load_obb(obs, list[nc * 32], O);
-#pragma unroll
-        for (int s = 0; s < NB; ++s) {
-          float px_, py_, pz_;
-          J += obb_pen(b, cx[s], cy[s], cz[s], cr[s], px_, py_, pz_);
-          gx[s] += px_;
-          gy[s] += py_;
-          gz[s] += pz_;
+        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R * R) {
+          const int q = atomicAdd(&ws.count[1], 1);
+          ws.queue[QUEUE_CAP - 1 - q] = static_cast<uint32_t>(lane) << 16 | static_cast<uint32_t>(i);
         }
       }
     }
-    // exact phase, other boxes: pen = max(0, r_a + r_b - ||c_a - c_b||); each of
-    // the box's spheres is first checked against the batch's bounding sphere
-    while (__any_sync(0xffffffffu, nbx > 0)) {
-      if (nbx > 0) {
-        --nbx;
+    __syncwarp();
+    const int n_c = ws.count[0], n_b = ws.count[1];
+
+    // ---- exact phase, cuboids: one queued pair per lane per round
+    for (int r0 = 0; r0 < n_c; r0 += 32) {
+      const bool valid = r0 + lane < n_c;
+      const uint32_t ent = valid ? ws.queue[r0 + lane] : static_cast<uint32_t>(lane) << 16;
+      const int owner = static_cast<int>(ent >> 16);
+      float ox[NB], oy[NB], oz[NB], orr[NB];
+#pragma unroll
+      for (int s = 0; s < NB; ++s) {
+        ox[s] = __shfl_sync(0xffffffffu, cx[s], owner);
+        oy[s] = __shfl_sync(0xffffffffu, cy[s], owner);
+        oz[s] = __shfl_sync(0xffffffffu, cz[s], owner);
+        orr[s] = __shfl_sync(0xffffffffu, cr[s], owner);
+      }
+      if (valid) {
+        ++n_obb;
+        const Obb b = load_obb(obs, static_cast<int>(ent & 0xffffu), O);
+#pragma unroll
+        for (int s = 0; s < NB; ++s) {
+          float px_, py_, pz_;
+          const float pen = obb_pen(b, ox[s], oy[s], oz[s], orr[s], px_, py_, pz_);
+          if (pen > 0.f) {
+            float4* a = &ws.acc[owner * NB + s];
+            atomicAdd(&a->x, px_);
+            atomicAdd(&a->y, py_);
+            atomicAdd(&a->z, pz_);
+            atomicAdd(&a->w, pen);
+          }
+        }
+      }
+    }
+
+    // ---- exact phase, other boxes: pen = max(0, r_a + r_b - ||c_a - c_b||); each
+    // of the box's spheres is first checked against the owner's batch bound
+    for (int r0 = 0; r0 < n_b; r0 += 32) {
+      const bool valid = r0 + lane < n_b;
+      const uint32_t ent = valid ? ws.queue[QUEUE_CAP - 1 - (r0 + lane)] : static_cast<uint32_t>(lane) << 16;
+      const int owner = static_cast<int>(ent >> 16);
+      float ox[NB], oy[NB], oz[NB], orr[NB];
+#pragma unroll
+      for (int s = 0; s < NB; ++s) {
+        ox[s] = __shfl_sync(0xffffffffu, cx[s], owner);
+        oy[s] = __shfl_sync(0xffffffffu, cy[s], owner);
+        oz[s] = __shfl_sync(0xffffffffu, cz[s], owner);
+        orr[s] = __shfl_sync(0xffffffffu, cr[s], owner);
+      }
+      const float obx = __shfl_sync(0xffffffffu, cbx, owner), oby = __shfl_sync(0xffffffffu, cby, owner);
+      const float obz = __shfl_sync(0xffffffffu, cbz, owner), oR = __shfl_sync(0xffffffffu, Rb, owner);
+      if (valid) {
         ++n_box;
-        const int* er = env + (list[(LIST_CAP - 1 - nbx) * 32] - O) * ENV_W;
+        const int opl = owner / L;  // the owner's particle in the tile
+        const int* er = env + (static_cast<int>(ent & 0xffffu) - O) * ENV_W;
         const int j = er[0], src = er[1];
         // a box on a placement variable: its spheres in the world from (x, y, yaw)
         float bx = 0.f, by = 0.f, bz = 0.f, sn = 0.f, cs = 1.f;
         if (src >= 0) {
-          bx = X[src * PT + pl];
-          by = X[(src + 1) * PT + pl];
+          bx = X[src * PT + opl];
+          by = X[(src + 1) * PT + opl];
           bz = __int_as_float(slots[er[2] * SLOT_W + 2]);
-          sincosf(X[(src + 2) * PT + pl], &sn, &cs);
+          sincosf(X[(src + 2) * PT + opl], &sn, &cs);
         }
+        float ag[NB][4];
+#pragma unroll
+        for (int s = 0; s < NB; ++s) ag[s][0] = ag[s][1] = ag[s][2] = ag[s][3] = 0.f;
         float fx = 0.f, fy = 0.f, tq = 0.f;  // push on a moving box: force, torque about its centre
         for (int e = 0; e < NBS; ++e) {
           float4 c;
@@ -256,22 +307,22 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
             const float4 l = bloc[j * NBS + e];
             c = make_float4(bx + fmaf(cs, l.x, -sn * l.y), by + fmaf(sn, l.x, cs * l.y), bz + l.z, l.w);
           }
-          const float ex = cbx - c.x, ey = cby - c.y, ez = cbz - c.z, Re = Rb + c.w;
+          const float ex = obx - c.x, ey = oby - c.y, ez = obz - c.z, Re = oR + c.w;
           if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) >= Re * Re) continue;
 #pragma unroll
           for (int s = 0; s < NB; ++s) {
-            const float dx = cx[s] - c.x, dy = cy[s] - c.y, dz = cz[s] - c.z;
+            const float dx = ox[s] - c.x, dy = oy[s] - c.y, dz = oz[s] - c.z;
             const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float Rs = cr[s] + c.w;
+            const float Rs = orr[s] + c.w;
             if (Rs > 0.f && d2 < Rs * Rs) {
               const float d = sqrtf(d2);
-              J += Rs - d;
+              ag[s][3] += Rs - d;
               if (d > 0.f) {
                 const float inv = 1.f / d;
                 const float vx = dx * inv, vy = dy * inv, vz = dz * inv;
-                gx[s] -= vx;
-                gy[s] -= vy;
-                gz[s] -= vz;
+                ag[s][0] -= vx;
+                ag[s][1] -= vy;
+                ag[s][2] -= vz;
                 fx += vx;
                 fy += vy;
                 tq = fmaf(c.x - bx, vy, fmaf(-(c.y - by), vx, tq));
@@ -279,14 +330,43 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
             }
           }
         }
+#pragma unroll
+        for (int s = 0; s < NB; ++s) {
+          if (ag[s][3] > 0.f) {
+            float4* a = &ws.acc[owner * NB + s];
+            atomicAdd(&a->x, ag[s][0]);
+            atomicAdd(&a->y, ag[s][1]);
+            atomicAdd(&a->z, ag[s][2]);
+            atomicAdd(&a->w, ag[s][3]);
+          }
+        }
         if (src >= 0 && (fx != 0.f || fy != 0.f || tq != 0.f)) {
-          atomicAdd(&G[src * PT + pl], wenv * fx);
-          atomicAdd(&G[(src + 1) * PT + pl], wenv * fy);
-          atomicAdd(&G[(src + 2) * PT + pl], wenv * tq);
+          atomicAdd(&G[src * PT + opl], wenv * fx);
+          atomicAdd(&G[(src + 1) * PT + opl], wenv * fy);
+          atomicAdd(&G[(src + 2) * PT + opl], wenv * tq);
         }
       }
     }
+    __syncwarp();
+    if (lane == 0) {
+      ws.count[0] = 0;
+      ws.count[1] = 0;
+    }
+    __syncwarp();  // the reset lands before any lane appends to the next chunk
   }
+  // ---- each lane collects (and clears) its accumulators
+  __syncwarp();
+  float J = 0.f;
+#pragma unroll
+  for (int s = 0; s < NB; ++s) {
+    const float4 a = ws.acc[lane * NB + s];
+    gx[s] += a.x;
+    gy[s] += a.y;
+    gz[s] += a.z;
+    J += a.w;
+    ws.acc[lane * NB + s] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __syncwarp();
   return J;
 }
 
@@ -318,8 +398,8 @@ __device__ __forceinline__ float bound_dist(const float (&v)[N], const float (&l
 //   phase 3  the placed box at P(p) (Place configurations: CFreePlace)
 template <int L>
 __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __restrict__ pb, int k,
-                            const float* __restrict__ X, float* G, float* Tm, const int* __restrict__ slots, uint16_t* list, unsigned& n_obb, unsigned& n_box, int pl,
-                            int sub) {
+                            const float* __restrict__ X, float* G, float* Tm, const int* __restrict__ slots,
+                            const WarpScratch& ws, unsigned& n_obb, unsigned& n_box, int lane, int pl, int sub) {
   constexpr int PT = 32 / L;
   const int nj = sc[SH_NJ];
   const float* arm = reinterpret_cast<const float*>(sc + sc[SH_OFF_ARM]);
@@ -539,7 +619,7 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
     }
     const float wenv = phase == 3 ? w_cp : w_cf;
     const float Jb = collide<L>(cx, cyy, cz, cr, gx, gyy, gz, cbx, cby, cbz, Rb, obs, O, env, n_env, boxr, slots,
-                                bloc, binit, NBS, X, G, pl, sub, wenv, list, n_obb, n_box);
+                                bloc, binit, NBS, X, G, pl, sub, lane, wenv, ws, n_obb, n_box);
     if (phase == 3) {
       J_place += Jb;
 #pragma unroll
@@ -739,9 +819,8 @@ __global__ void __launch_bounds__(384, 1) optimize_kernel(OptArgs a) {
   float* sg = sv + D * PT;
   float* st = sg + D * PT;
   int* sflag = reinterpret_cast<int*>(st + NT * PT);
-  // per-lane candidate lists of the broad phase: [warp][entry][lane]
-  const int cap = LIST_CAP;
-  uint16_t* lists = reinterpret_cast<uint16_t*>(sflag + PT);
+  // exact-phase scratch of each warp (16-byte aligned after the flags)
+  unsigned char* scratch = reinterpret_cast<unsigned char*>(sflag) + ((PT * 4 + 15) & ~15);
 
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int tile0 = blockIdx.x * PT;
@@ -778,6 +857,15 @@ __global__ void __launch_bounds__(384, 1) optimize_kernel(OptArgs a) {
   if (abort_flag) return;
 
   const int w = tid >> 5, lane = tid & 31, W = nthr >> 5;
+  WarpScratch ws;
+  {
+    unsigned char* base = scratch + static_cast<size_t>(w) * WARP_SCRATCH_BYTES;
+    ws.acc = reinterpret_cast<float4*>(base);
+    ws.queue = reinterpret_cast<uint32_t*>(base + 32 * NB * 16);
+    ws.count = reinterpret_cast<int*>(base + 32 * NB * 16 + QUEUE_CAP * 4);
+    for (int i = lane; i < 32 * NB; i += 32) ws.acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane == 0) { ws.count[0] = 0; ws.count[1] = 0; }
+  }
   const int pl = lane / L, sub = lane % L;
   const uint32_t* terms = s_pb + s_pb[PH_OFF_TERMS];
   const float* lr = reinterpret_cast<const float*>(s_pb + s_pb[PH_OFF_LR]);
@@ -786,12 +874,11 @@ __global__ void __launch_bounds__(384, 1) optimize_kernel(OptArgs a) {
   double b1t = pow(static_cast<double>(a.beta1), a.t0), b2t = pow(static_cast<double>(a.beta2), a.t0);
   unsigned n_obb = 0, n_box = 0;  // broad-phase candidates resolved exactly (work accounting)
   const int* slots = reinterpret_cast<const int*>(s_pb + s_pb[PH_OFF_SLOT]);
-  const float4* bloc = reinterpret_cast<const float4*>(s_sc + s_sc[SH_OFF_BLOC]);
   for (int it = 0;; ++it) {
     for (int i = tid; i < NT * PT; i += nthr) st[i] = 0.f;  // CFreePlace terms are sums over two warps
     __syncthreads();
     for (int k = w; k < K; k += W)
-      eval_config<L>(s_sc, s_pb, k, sx, sg, st, slots, lists + w * cap * 32 + lane, n_obb, n_box, pl, sub);
+      eval_config<L>(s_sc, s_pb, k, sx, sg, st, slots, ws, n_obb, n_box, lane, pl, sub);
     if (w == goal_warp && sub == 0) eval_goal<L>(s_sc, s_pb, sx, sg, st, pl);
     __syncthreads();
     // Eq. 3 at x_t
@@ -958,8 +1045,8 @@ cudaError_t launch_sample(const uint32_t* pb, const uint32_t* sc, float* x, floa
 size_t optimize_smem_bytes(int scene_words, int prob_words, int D, int NT, int warps, int L) {
   const int PT = 32 / L;
   const size_t sw = (scene_words + 3) & ~3, pw = (prob_words + 3) & ~3;
-  return 4 * (sw + pw) + 4 * (4 * static_cast<size_t>(D) * PT + static_cast<size_t>(NT) * PT + PT) +
-         2 * static_cast<size_t>(LIST_CAP) * 32 * warps;
+  return 4 * (sw + pw) + 4 * (4 * static_cast<size_t>(D) * PT + static_cast<size_t>(NT) * PT) +
+         ((PT * 4 + 15) & ~15) + static_cast<size_t>(WARP_SCRATCH_BYTES) * warps;
 }
 
 int optimize_warps(int K) {
