@@ -257,9 +257,11 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return
-    ev_flops = flops.eval_flops(sc, acts)
-    launch_flops = (P * ((T + 1) * ev_flops + T * flops.adam_flops(D))
-                    + flops.exact_flops(work[0], work[1], sc.box_spheres.shape[1]))
+    # roofline numerator: the method's all-pairs work (SURVEY-style per-unit
+    # figures, flops.algorithmic_flops) x particle-iterations of one launch
+    launch_flops = P * T * flops.algorithmic_flops(sc, acts)
+    executed = (P * ((T + 1) * flops.eval_flops(sc, acts) + T * flops.adam_flops(D))
+                + flops.exact_flops(work[0], work[1], sc.box_spheres.shape[1]))
     kern_s = sum(kern_ms) / len(kern_ms) / 1e3
     props = torch.cuda.get_device_properties(dev)
     peak = flops.fp32_peak_tflops(props.multi_processor_count, 2032.0)
@@ -276,6 +278,7 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "optimize_kernel", "flop_per_launch": launch_flops,
+                     "executed_tflops": executed / kern_s / 1e12,
                      "exact_candidates": {"cuboid": work[0], "box": work[1]},
                      "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x 2032 MHz (max SM clock)"},
         "e2e": {"value": P * T / e2e_s, "unit": "particle-iters/s", "h2d_bytes_per_step": h2d,

@@ -1,5 +1,14 @@
 """FP32 work of the fused evaluation (cost + adjoint) and the Adam update.
 
+Two figures:
+  algorithmic_flops -- the method's work per particle-iteration, all sphere
+      pairs evaluated forward (the paper's cost functions have no broad phase):
+      forward kinematics 60 FLOP per joint, sphere transform 18 per sphere,
+      sphere vs cuboid 32 per pair, sphere vs sphere 10 per pair, reverse sweep
+      80 per joint, Adam 12 per component.  This is the roofline numerator.
+  eval_flops / exact_flops -- what this kernel executes: the broad phase skips
+      pairs that cannot touch, so it does a fraction of the algorithmic work.
+
 FMA = 2 FLOP, add/mul/compare/max = 1; square roots, divisions and sines are
 not counted, so the figures are lower bounds of the arithmetic done.
 
@@ -85,6 +94,25 @@ def eval_flops(scene, actions) -> int:
 def exact_flops(n_obb: int, n_box: int, nbs: int) -> int:
     """Data-dependent FLOP from the kernel's candidate counters."""
     return n_obb * NB * EXACT_OBB_SPHERE + n_box * NB * nbs * EXACT_PAIR
+
+
+def algorithmic_flops(scene, actions) -> int:
+    """All-pairs FLOP of one particle-iteration (evaluation, adjoint sweep, Adam)."""
+    n = scene.dh_a.shape[0]
+    S = len(scene.sphere_link)
+    nbs = scene.box_spheres.shape[1]
+    O = scene.obs_center.shape[0]
+    B = scene.box_half.shape[0]
+    total, D = 0, 0
+    for kind, _b, _s in actions:
+        if kind not in (0, 1):
+            continue
+        D += (4 if kind == 0 else 3) + n
+        own = S + nbs                                  # arm + held box
+        total += n * 60 + own * 18 + own * O * 32 + own * nbs * (B - 1) * 10 + n * 80
+        if kind == 1:                                  # CFreePlace: the placed box
+            total += nbs * 18 + nbs * O * 32 + nbs * nbs * (B - 1) * 10
+    return total + 12 * D
 
 
 def adam_flops(D: int) -> int:
