@@ -257,7 +257,7 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return
-    # roofline numerator: the method's all-pairs work (SURVEY-style per-unit
+    # roofline numerator: the method's all-pairs work (per-unit
     # figures, flops.algorithmic_flops) x particle-iterations of one launch
     launch_flops = P * T * flops.algorithmic_flops(sc, acts)
     executed = (P * ((T + 1) * flops.eval_flops(sc, acts) + T * flops.adam_flops(D))
