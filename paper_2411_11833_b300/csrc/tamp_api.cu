@@ -16,10 +16,12 @@
 #include "tamp_dev.cuh"
 
 namespace tamp {
-cudaError_t launch_optimize(const OptArgs& a, int L, int K, size_t smem, cudaStream_t st);
+cudaError_t launch_optimize(const LaunchArgs& a, int L, int warps, int grid, size_t smem, cudaStream_t st);
+size_t optimize_tile_bytes(int prob_words, int D, int NT, int L);
+size_t optimize_scratch_bytes(int warps);
+int optimize_blocks_per_sm(int L, int warps, size_t smem);
 cudaError_t launch_sample(const uint32_t* pb, const uint32_t* sc, float* x, float* m, float* v, int stride, int P,
                           int D, uint64_t seed, cudaStream_t st);
-size_t optimize_smem_bytes(int scene_words, int prob_words, int D, int NT, int warps, int L);
 int optimize_warps(int K);
 }  // namespace tamp
 
@@ -54,6 +56,13 @@ struct tamp_scene {
   uint32_t* d_blob = nullptr;
   int* d_err = nullptr;
   int* d_scratch_first = nullptr;
+  int sm_count = 148;
+  // launch tables of the persistent kernel (library-owned, grown on demand)
+  ProbDesc* d_descs = nullptr;
+  int descs_cap = 0;
+  uint32_t* d_items = nullptr;
+  int items_cap = 0;
+  int* d_item_counter = nullptr;
   std::vector<Problem*> probs;
   std::string err;
 };
@@ -496,28 +505,13 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
 // the kernel's static shared variables
 constexpr size_t kMaxDynSmem = 227 * 1024 - 256;
 
-size_t smem_for(const tamp_scene* s, const Problem& pr, int L) {
-  return optimize_smem_bytes(static_cast<int>(s->blob.size()), static_cast<int>(pr.blob.size()), pr.D, pr.NT,
-                             optimize_warps(pr.K), L);
-}
-
 // Threads per (particle, configuration).  More lanes split each configuration's
-// environment (shorter critical path, more warps for small batches) but repeat
-// its kinematics; fewer lanes keep more particles per CTA.  The requested or
-// preferred value is lowered/raised until the CTA's shared memory fits.
-int pick_lanes(const tamp_scene* s, const Problem& pr, int P, size_t* smem) {
-  int L = pr.opt.lanes;
-  if (L != 1 && L != 2 && L != 4 && L != 8) {
-    // one lane per (particle, configuration) unless the batch is too small to
-    // give every SM a CTA of 32-particle tiles; measured on the 4096-particle
-    // packing problem: 1 lane 41M, 2 lanes 25M particle-iterations/s
-    L = P >= 148 * 16 ? 1 : (P >= 148 * 8 ? 2 : 4);
-  }
-  for (; L <= 8; L *= 2) {
-    *smem = smem_for(s, pr, L);
-    if (*smem <= kMaxDynSmem) return L;
-  }
-  return 0;
+// environment (shorter critical path, more CTAs for small batches) but repeat
+// its kinematics; one lane keeps 32 particles per CTA.  Measured on the
+// 4096-particle packing problem: 1 lane 41M, 2 lanes 25M particle-iterations/s.
+int preferred_lanes(int requested, long total_particles) {
+  if (requested == 1 || requested == 2 || requested == 4 || requested == 8) return requested;
+  return total_particles >= 148L * 16 ? 1 : (total_particles >= 148L * 8 ? 2 : 4);
 }
 
 void free_batch(Problem& pr) {
@@ -552,32 +546,109 @@ tamp_status ensure_batch(tamp_scene* s, Problem& pr, int P) {
   return TAMP_OK;
 }
 
-OptArgs base_args(tamp_scene* s, Problem& pr) {
-  OptArgs a{};
-  a.scene = s->d_blob; a.scene_words = static_cast<int>(s->blob.size());
-  a.prob = pr.d_blob; a.prob_words = static_cast<int>(pr.blob.size());
-  a.gscale = 1.f;
-  a.beta1 = pr.opt.beta1; a.beta2 = pr.opt.beta2; a.eps = pr.opt.eps;
+struct Job {
+  Problem* pr;
+  ProbDesc d;
+};
+
+// One launch of the persistent kernel over several problems: descriptors and
+// the work-item list (longest skeletons first) go to the device, the lane split
+// and shared memory are sized for the largest problem, and the grid fills the
+// SMs (CTAs then pull items until the list is empty).
+tamp_status launch_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lanes) {
+  if (jobs.empty()) return TAMP_OK;
+  long total = 0;
+  int warps = 1;
+  for (const Job& j : jobs) {
+    total += j.d.P;
+    warps = std::max(warps, optimize_warps(j.pr->K));
+  }
+  int L = preferred_lanes(requested_lanes, total);
+  size_t smem = 0, tile = 0;
+  for (; L <= 8; L *= 2) {
+    tile = 0;
+    for (const Job& j : jobs)
+      tile = std::max(tile, optimize_tile_bytes(static_cast<int>(j.pr->blob.size()), j.pr->D, j.pr->NT, L));
+    smem = 4 * ((s->blob.size() + 3) & ~static_cast<size_t>(3)) + tile + optimize_scratch_bytes(warps);
+    if (smem <= kMaxDynSmem) break;
+  }
+  if (L > 8) return fail(s, TAMP_ERR_INVALID_ARG, "problem does not fit in shared memory");
+  const int PT = 32 / L;
+  // work items: problems by decreasing per-tile work (configurations), then tiles
+  std::vector<int> order(jobs.size());
+  for (size_t i = 0; i < jobs.size(); ++i) order[i] = static_cast<int>(i);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return jobs[a].pr->K > jobs[b].pr->K; });
+  std::vector<uint32_t> items;
+  for (int i : order) {
+    const int tiles = (jobs[i].d.P + PT - 1) / PT;
+    if (tiles >= (1 << ITEM_TILE_BITS)) return fail(s, TAMP_ERR_INVALID_ARG, "batch too large");
+    for (int t = 0; t < tiles; ++t) items.push_back(static_cast<uint32_t>(i) << ITEM_TILE_BITS | static_cast<uint32_t>(t));
+  }
+  if (static_cast<int>(jobs.size()) > s->descs_cap) {
+    cudaFree(s->d_descs);
+    s->d_descs = nullptr;
+    s->descs_cap = 0;
+    CUDA_TRY(s, cudaMalloc(&s->d_descs, jobs.size() * sizeof(ProbDesc)));
+    s->descs_cap = static_cast<int>(jobs.size());
+  }
+  if (static_cast<int>(items.size()) > s->items_cap) {
+    cudaFree(s->d_items);
+    s->d_items = nullptr;
+    s->items_cap = 0;
+    CUDA_TRY(s, cudaMalloc(&s->d_items, items.size() * 4));
+    s->items_cap = static_cast<int>(items.size());
+  }
+  std::vector<ProbDesc> descs;
+  for (const Job& j : jobs) descs.push_back(j.d);
+  CUDA_TRY(s, cudaMemcpyAsync(s->d_descs, descs.data(), descs.size() * sizeof(ProbDesc), cudaMemcpyHostToDevice,
+                              s->stream));
+  CUDA_TRY(s, cudaMemcpyAsync(s->d_items, items.data(), items.size() * 4, cudaMemcpyHostToDevice, s->stream));
+  CUDA_TRY(s, cudaMemsetAsync(s->d_item_counter, 0, 4, s->stream));
+  LaunchArgs a{};
+  a.scene = s->d_blob;
+  a.scene_words = static_cast<int>(s->blob.size());
+  a.probs = s->d_descs;
+  a.items = s->d_items;
+  a.n_items = static_cast<int>(items.size());
+  a.item_counter = s->d_item_counter;
   a.err = s->d_err;
-  return a;
+  a.scratch_offset = static_cast<int>(smem - optimize_scratch_bytes(warps));
+  const int per_sm = std::max(1, optimize_blocks_per_sm(L, warps, smem));
+  const int grid = std::min(a.n_items, s->sm_count * per_sm);
+  CUDA_TRY(s, launch_optimize(a, L, warps, grid, smem, s->stream));
+  return TAMP_OK;
 }
 
-tamp_status run_state(tamp_scene* s, Problem& pr, int n_steps) {
-  OptArgs a = base_args(s, pr);
-  a.x_in = pr.d_x; a.x_out = pr.d_x; a.m = pr.d_m; a.v = pr.d_v; a.load_mv = 1;
-  a.stride = pr.P; a.P = pr.P;
-  a.out_cost = pr.d_cost; a.out_flags = pr.d_flags; a.out_counts = pr.d_counts;
-  a.first_iter = pr.d_first;
-  a.work = pr.d_work;
-  a.n_steps = n_steps; a.t0 = pr.t;
-  a.gscale = pr.opt.scale_by_batch ? 1.f / static_cast<float>(pr.P) : 1.f;
-  CUDA_TRY(s, cudaMemsetAsync(pr.d_counts, 0, static_cast<size_t>(std::max(pr.NCON, 1)) * 4, s->stream));
-  size_t smem = 0;
-  const int L = pick_lanes(s, pr, pr.P, &smem);
-  if (L == 0) return fail(s, TAMP_ERR_INVALID_ARG, "problem does not fit in shared memory (D=%d)", pr.D);
-  CUDA_TRY(s, launch_optimize(a, L, pr.K, smem, s->stream));
-  pr.t += n_steps;
-  pr.checked = true;
+ProbDesc state_desc(Problem& pr, int n_steps) {
+  ProbDesc d{};
+  d.prob = pr.d_blob;
+  d.prob_words = static_cast<int>(pr.blob.size());
+  d.x_in = pr.d_x; d.x_out = pr.d_x; d.m = pr.d_m; d.v = pr.d_v; d.load_mv = 1;
+  d.stride = pr.P; d.P = pr.P;
+  d.out_cost = pr.d_cost; d.out_flags = pr.d_flags; d.out_counts = pr.d_counts;
+  d.first_iter = pr.d_first;
+  d.work = pr.d_work;
+  d.t0 = pr.t;
+  d.n_steps = n_steps;
+  d.gscale = pr.opt.scale_by_batch ? 1.f / static_cast<float>(pr.P) : 1.f;
+  d.beta1 = pr.opt.beta1; d.beta2 = pr.opt.beta2; d.eps = pr.opt.eps;
+  return d;
+}
+
+tamp_status run_state(tamp_scene* s, std::vector<Problem*> prs, int n_steps) {
+  std::vector<Job> jobs;
+  int lanes = 0;
+  for (Problem* pr : prs) {
+    CUDA_TRY(s, cudaMemsetAsync(pr->d_counts, 0, static_cast<size_t>(std::max(pr->NCON, 1)) * 4, s->stream));
+    jobs.push_back({pr, state_desc(*pr, n_steps)});
+    lanes = pr->opt.lanes;
+  }
+  tamp_status st = launch_jobs(s, jobs, lanes);
+  if (st != TAMP_OK) return st;
+  for (Problem* pr : prs) {
+    pr->t += n_steps;
+    pr->checked = true;
+  }
   return TAMP_OK;
 }
 
@@ -651,11 +722,13 @@ tamp_status tamp_create_scene(const tamp_scene_desc* d, int device, void* stream
   cudaError_t e = cudaMalloc(&s->d_blob, s->blob.size() * 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_err, 4);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_scratch_first, 4);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_item_counter, 4);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_blob, s->blob.data(), s->blob.size() * 4, cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, 4, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) {
-    cudaFree(s->d_blob); cudaFree(s->d_err); cudaFree(s->d_scratch_first);
+    cudaFree(s->d_blob); cudaFree(s->d_err); cudaFree(s->d_scratch_first); cudaFree(s->d_item_counter);
     delete s;
     return e == cudaErrorMemoryAllocation ? TAMP_ERR_OOM : TAMP_ERR_CUDA;
   }
@@ -672,7 +745,8 @@ tamp_status tamp_destroy_scene(tamp_scene* s) {
     cudaFree(p->d_blob);
     delete p;
   }
-  cudaFree(s->d_blob); cudaFree(s->d_err); cudaFree(s->d_scratch_first);
+  cudaFree(s->d_blob); cudaFree(s->d_err); cudaFree(s->d_scratch_first); cudaFree(s->d_item_counter);
+  cudaFree(s->d_descs); cudaFree(s->d_items);
   delete s;
   return TAMP_OK;
 }
@@ -767,11 +841,14 @@ tamp_status tamp_optimize_steps(tamp_scene* s, const int* ids, int n, int n_step
     if (!pr) return fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", ids[i]);
     if (!pr->has_batch) return fail(s, TAMP_ERR_STATE, "problem %d has no particles", ids[i]);
   }
+  std::vector<Problem*> prs;
   for (int i = 0; i < n; ++i) {
-    tamp_status st = run_state(s, *s->probs[ids[i]], n_steps);
-    if (st != TAMP_OK) return st;
+    Problem* pr = s->probs[ids[i]];
+    if (std::find(prs.begin(), prs.end(), pr) != prs.end())
+      return fail(s, TAMP_ERR_INVALID_ARG, "problem %d listed twice", ids[i]);
+    prs.push_back(pr);
   }
-  return TAMP_OK;
+  return run_state(s, prs, n_steps);
 }
 
 tamp_status tamp_query_satisfied(tamp_scene* s, int id, uint8_t* mask, int* n_sat, int* first_iter, float* particles,
@@ -781,7 +858,7 @@ tamp_status tamp_query_satisfied(tamp_scene* s, int id, uint8_t* mask, int* n_sa
   if (!pr->has_batch) return fail(s, TAMP_ERR_STATE, "problem %d has no particles", id);
   DeviceGuard g(s->device);
   if (!pr->checked) {
-    tamp_status st = run_state(s, *pr, 0);
+    tamp_status st = run_state(s, {pr}, 0);
     if (st != TAMP_OK) return st;
   }
   std::vector<uint8_t> fl(pr->P);
@@ -809,15 +886,15 @@ tamp_status tamp_eval(tamp_scene* s, int id, int n, const float* x, float* cost,
   if (!pr) return fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", id);
   if (n <= 0 || !x) return fail(s, TAMP_ERR_INVALID_ARG, "bad eval arguments");
   DeviceGuard g(s->device);
-  OptArgs a = base_args(s, *pr);
-  a.x_in = x; a.stride = n; a.P = n;
-  a.out_cost = cost; a.out_terms = terms; a.out_flags = flags; a.out_grad = grad;
-  a.first_iter = nullptr; a.n_steps = 0; a.t0 = 0;
-  size_t smem = 0;
-  const int L = pick_lanes(s, *pr, n, &smem);
-  if (L == 0) return fail(s, TAMP_ERR_INVALID_ARG, "problem does not fit in shared memory (D=%d)", pr->D);
-  CUDA_TRY(s, launch_optimize(a, L, pr->K, smem, s->stream));
-  return TAMP_OK;
+  ProbDesc d{};
+  d.prob = pr->d_blob;
+  d.prob_words = static_cast<int>(pr->blob.size());
+  d.x_in = x; d.stride = n; d.P = n;
+  d.out_cost = cost; d.out_terms = terms; d.out_flags = flags; d.out_grad = grad;
+  d.n_steps = 0;
+  d.gscale = 1.f; d.beta1 = pr->opt.beta1; d.beta2 = pr->opt.beta2; d.eps = pr->opt.eps;
+  std::vector<Job> jobs{{pr, d}};
+  return launch_jobs(s, jobs, pr->opt.lanes);
 }
 
 tamp_status tamp_work_counters(tamp_scene* s, int id, uint64_t out[2]) {

@@ -72,19 +72,34 @@ enum TermKind {
 // device error word bits
 enum ErrBits { ERR_TMA_TIMEOUT = 1, ERR_BAD_BLOB = 2 };
 
-struct OptArgs {
-  const uint32_t* scene; int scene_words;
+// One problem of a launch (an array of these lives in device memory).
+struct ProbDesc {
   const uint32_t* prob; int prob_words;
-  const float* x_in;            // [D][stride]
-  float* x_out; float* m; float* v;  // state (may be null in eval mode)
+  const float* x_in;                  // [D][stride]
+  float* x_out; float* m; float* v;   // state (may be null in evaluation mode)
   int stride; int P;
   float* out_cost; float* out_terms; uint8_t* out_flags; float* out_grad; int* out_counts;
-  int* first_iter; int* err;
-  int n_steps; int t0;
-  float gscale;                 // 1/N_b (Eq. 4) or 1
+  int* first_iter;
+  unsigned long long* work;           // optional [2]: cuboid / box candidates resolved exactly
+  const int* t_dev;                   // if set, the Adam step count before the launch is read here
+  int t0;                             // else this one
+  int n_steps;
+  float gscale;                       // 1/N_b (Eq. 4) or 1
   float beta1, beta2, eps;
-  int load_mv;                  // read m, v from memory (else zeros)
-  unsigned long long* work;     // optional [2]: cuboid / box candidates of the broad phase resolved exactly
+  int load_mv;                        // read m, v from memory (else zeros)
+  int pad;
 };
+
+// One launch of the persistent optimisation kernel: CTAs take work items
+// (problem << 20 | tile) from a shared counter until the list is exhausted.
+struct LaunchArgs {
+  const uint32_t* scene; int scene_words;
+  const ProbDesc* probs;
+  const uint32_t* items; int n_items;
+  int* item_counter;                  // zero before the launch
+  int* err;
+  int scratch_offset;                 // bytes from the start of dynamic shared memory to the warp scratch
+};
+constexpr int ITEM_TILE_BITS = 20;
 
 }  // namespace tamp

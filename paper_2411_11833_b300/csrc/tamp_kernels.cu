@@ -803,77 +803,45 @@ __device__ void eval_goal(const uint32_t* __restrict__ sc, const uint32_t* __res
 }
 
 // ------------------------------------------------------------------ fused optimisation kernel
+// One tile of PT particles of one problem: load it, run n_steps fused
+// iterations (evaluation + adjoint, Eq. 3 check, Adam) and one final check,
+// write it back.  All threads of the CTA call this together.
 template <int L>
-__global__ void __launch_bounds__(384, 1) optimize_kernel(OptArgs a) {
+__device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, const uint32_t* s_pb, float* tile_mem,
+                         const WarpScratch& ws) {
   constexpr int PT = 32 / L;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ int abort_flag;
-  const int sw = (a.scene_words + 3) & ~3, pw = (a.prob_words + 3) & ~3;
-  uint32_t* s_sc = reinterpret_cast<uint32_t*>(smem_raw);
-  uint32_t* s_pb = s_sc + sw;
-  const int D = a.prob[PH_D], K = a.prob[PH_K], NT = a.prob[PH_NT];
-  float* sx = reinterpret_cast<float*>(s_pb + pw);
+  const int D = s_pb[PH_D], K = s_pb[PH_K], NT = s_pb[PH_NT];
+  float* sx = tile_mem;
   float* sm = sx + D * PT;
   float* sv = sm + D * PT;
   float* sg = sv + D * PT;
   float* st = sg + D * PT;
   int* sflag = reinterpret_cast<int*>(st + NT * PT);
-  // exact-phase scratch of each warp (16-byte aligned after the flags)
-  unsigned char* scratch = reinterpret_cast<unsigned char*>(sflag) + ((PT * 4 + 15) & ~15);
-
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int tile0 = blockIdx.x * PT;
-  if (tid == 0) {
-    abort_flag = 0;
-    mbar_init(&bar, 1);
-    fence_mbar_init();
-    fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&bar, static_cast<uint32_t>((sw + pw) * 4));
-    tma_bulk_g2s(s_sc, a.scene, static_cast<uint32_t>(sw * 4), &bar);
-    tma_bulk_g2s(s_pb, a.prob, static_cast<uint32_t>(pw * 4), &bar);
-  }
-  // particle tile -> shared memory (overlaps the bulk copies)
+  const int w = tid >> 5, lane = tid & 31, W = nthr >> 5;
+  const int pl = lane / L, sub = lane % L;
+  const int tile0 = tile * PT;
+  const int t0 = d.t_dev ? *d.t_dev : d.t0;
+
   for (int i = tid; i < D * PT; i += nthr) {
     const int c = i / PT, p = i % PT, gp = tile0 + p;
     float xv = 0.f, mv = 0.f, vv = 0.f;
-    if (gp < a.P) {
-      xv = a.x_in[c * a.stride + gp];
-      if (a.load_mv) {
-        mv = a.m[c * a.stride + gp];
-        vv = a.v[c * a.stride + gp];
+    if (gp < d.P) {
+      xv = d.x_in[c * d.stride + gp];
+      if (d.load_mv) {
+        mv = d.m[c * d.stride + gp];
+        vv = d.v[c * d.stride + gp];
       }
     }
     sx[i] = xv; sm[i] = mv; sv[i] = vv; sg[i] = 0.f;
   }
-  if (tid == 0) {
-    if (!mbar_wait_bounded(&bar, 0, 1 << 20)) {
-      atomicOr(a.err, ERR_TMA_TIMEOUT);
-      abort_flag = 1;
-      mbar_wait_bounded(&bar, 0, 1 << 16);  // give copies in flight a last chance to land
-    }
-  }
-  __syncthreads();
-  if (abort_flag) return;
-
-  const int w = tid >> 5, lane = tid & 31, W = nthr >> 5;
-  WarpScratch ws;
-  {
-    unsigned char* base = scratch + static_cast<size_t>(w) * WARP_SCRATCH_BYTES;
-    ws.acc = reinterpret_cast<float4*>(base);
-    ws.queue = reinterpret_cast<uint32_t*>(base + 32 * NB * 16);
-    ws.count = reinterpret_cast<int*>(base + 32 * NB * 16 + QUEUE_CAP * 4);
-    for (int i = lane; i < 32 * NB; i += 32) ws.acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (lane == 0) { ws.count[0] = 0; ws.count[1] = 0; }
-  }
-  const int pl = lane / L, sub = lane % L;
   const uint32_t* terms = s_pb + s_pb[PH_OFF_TERMS];
   const float* lr = reinterpret_cast<const float*>(s_pb + s_pb[PH_OFF_LR]);
-  const int goal_warp = (K - 1) % W;
-
-  double b1t = pow(static_cast<double>(a.beta1), a.t0), b2t = pow(static_cast<double>(a.beta2), a.t0);
-  unsigned n_obb = 0, n_box = 0;  // broad-phase candidates resolved exactly (work accounting)
   const int* slots = reinterpret_cast<const int*>(s_pb + s_pb[PH_OFF_SLOT]);
+  const int goal_warp = (K - 1) % W;
+  double b1t = pow(static_cast<double>(d.beta1), t0), b2t = pow(static_cast<double>(d.beta2), t0);
+  unsigned n_obb = 0, n_box = 0;  // broad-phase candidates resolved exactly (work accounting)
+
   for (int it = 0;; ++it) {
     for (int i = tid; i < NT * PT; i += nthr) st[i] = 0.f;  // CFreePlace terms are sums over two warps
     __syncthreads();
@@ -891,73 +859,149 @@ __global__ void __launch_bounds__(384, 1) optimize_kernel(OptArgs a) {
           if (static_cast<int>(tr[3]) >= 0 && st[tt * PT + lane] > __uint_as_float(tr[2])) sat = 0;
         }
         sflag[lane] = sat;
-        if (tile0 + lane >= a.P) sat = 0;
+        if (tile0 + lane >= d.P) sat = 0;
       }
-      if (__any_sync(0xffffffffu, sat) && lane == 0 && a.first_iter) atomicMin(a.first_iter, a.t0 + it);
+      if (__any_sync(0xffffffffu, sat) && lane == 0 && d.first_iter) atomicMin(d.first_iter, t0 + it);
     }
-    if (it == a.n_steps) break;
+    if (it == d.n_steps) break;
     // Adam (Kingma & Ba) on the Eq. 4 gradient; the gradient buffer is cleared for the next pass
-    b1t *= static_cast<double>(a.beta1);  // beta^(t0 + it + 1)
-    b2t *= static_cast<double>(a.beta2);
+    b1t *= static_cast<double>(d.beta1);  // beta^(t0 + it + 1)
+    b2t *= static_cast<double>(d.beta2);
     const float ib1 = static_cast<float>(1.0 / (1.0 - b1t)), ib2 = static_cast<float>(1.0 / (1.0 - b2t));
     for (int i = tid; i < D * PT; i += nthr) {
-      const float g = sg[i] * a.gscale;
-      const float m = fmaf(a.beta1, sm[i], (1.f - a.beta1) * g);
-      const float v = fmaf(a.beta2, sv[i], (1.f - a.beta2) * g * g);
+      const float g = sg[i] * d.gscale;
+      const float m = fmaf(d.beta1, sm[i], (1.f - d.beta1) * g);
+      const float v = fmaf(d.beta2, sv[i], (1.f - d.beta2) * g * g);
       sm[i] = m;
       sv[i] = v;
-      sx[i] -= lr[i / PT] * (m * ib1) / (sqrtf(v * ib2) + a.eps);
+      sx[i] -= lr[i / PT] * (m * ib1) / (sqrtf(v * ib2) + d.eps);
       sg[i] = 0.f;
     }
     __syncthreads();
   }
   __syncthreads();
 
-  if (a.work) {
+  if (d.work) {
     unsigned long long no = n_obb, nb = n_box;
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) {
       no += __shfl_xor_sync(0xffffffffu, no, m);
       nb += __shfl_xor_sync(0xffffffffu, nb, m);
     }
-    if (lane == 0) {
-      atomicAdd(&a.work[0], no);
-      atomicAdd(&a.work[1], nb);
+    if (lane == 0 && (no | nb)) {
+      atomicAdd(&d.work[0], no);
+      atomicAdd(&d.work[1], nb);
     }
   }
 
   // ---------------- outputs of the last check
-  if (tid < PT && tile0 + tid < a.P) {
+  if (tid < PT && tile0 + tid < d.P) {
     const int gp = tile0 + tid;
-    if (a.out_cost) {
+    if (d.out_cost) {
       float c = 0.f;
       for (int tt = 0; tt < NT; ++tt) c = fmaf(__uint_as_float(terms[tt * TERM_W + 1]), st[tt * PT + tid], c);
-      a.out_cost[gp] = c;
+      d.out_cost[gp] = c;
     }
-    if (a.out_flags) a.out_flags[gp] = static_cast<uint8_t>(sflag[tid]);
+    if (d.out_flags) d.out_flags[gp] = static_cast<uint8_t>(sflag[tid]);
   }
-  if (a.out_terms)
+  if (d.out_terms)
     for (int i = tid; i < NT * PT; i += nthr) {
       const int tt = i / PT, p = i % PT;
-      if (tile0 + p < a.P) a.out_terms[tt * a.stride + tile0 + p] = st[i];
+      if (tile0 + p < d.P) d.out_terms[tt * d.stride + tile0 + p] = st[i];
     }
-  if (a.out_counts)
+  if (d.out_counts)
     for (int tt = tid; tt < NT; tt += nthr) {
       const uint32_t* tr = terms + tt * TERM_W;
       const int ci = static_cast<int>(tr[3]);
       if (ci < 0) continue;
       const float tol = __uint_as_float(tr[2]);
       int cnt = 0;
-      for (int p = 0; p < PT; ++p) cnt += (tile0 + p < a.P && st[tt * PT + p] <= tol) ? 1 : 0;
-      if (cnt) atomicAdd(&a.out_counts[ci], cnt);
+      for (int p = 0; p < PT; ++p) cnt += (tile0 + p < d.P && st[tt * PT + p] <= tol) ? 1 : 0;
+      if (cnt) atomicAdd(&d.out_counts[ci], cnt);
     }
   for (int i = tid; i < D * PT; i += nthr) {
     const int c = i / PT, p = i % PT, gp = tile0 + p;
-    if (gp >= a.P) continue;
-    if (a.out_grad) a.out_grad[c * a.stride + gp] = sg[i];
-    if (a.x_out) a.x_out[c * a.stride + gp] = sx[i];
-    if (a.m) a.m[c * a.stride + gp] = sm[i];
-    if (a.v) a.v[c * a.stride + gp] = sv[i];
+    if (gp >= d.P) continue;
+    if (d.out_grad) d.out_grad[c * d.stride + gp] = sg[i];
+    if (d.x_out) d.x_out[c * d.stride + gp] = sx[i];
+    if (d.m) d.m[c * d.stride + gp] = sm[i];
+    if (d.v) d.v[c * d.stride + gp] = sv[i];
+  }
+}
+
+// Persistent kernel: every CTA stages the scene tables once (TMA bulk copy),
+// then takes (problem, tile) work items from a global counter -- longest
+// skeletons first, as the host orders them -- staging a problem's tables
+// whenever it moves to a new problem.  Many skeletons of uneven length and
+// particle count thus share one launch and balance across the SMs.
+template <int L>
+__global__ void __launch_bounds__(384, 1) optimize_kernel(LaunchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag, s_item;
+  const int sw = (a.scene_words + 3) & ~3;
+  uint32_t* s_sc = reinterpret_cast<uint32_t*>(smem_raw);
+  uint32_t* s_pb = s_sc + sw;
+  const int tid = threadIdx.x;
+  uint32_t phase = 0;
+  if (tid == 0) {
+    abort_flag = 0;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&bar, static_cast<uint32_t>(sw * 4));
+    tma_bulk_g2s(s_sc, a.scene, static_cast<uint32_t>(sw * 4), &bar);
+    if (!mbar_wait_bounded(&bar, phase, 1 << 20)) {
+      atomicOr(a.err, ERR_TMA_TIMEOUT);
+      abort_flag = 1;
+      mbar_wait_bounded(&bar, phase, 1 << 16);  // give the copy in flight a last chance to land
+    }
+  }
+  phase ^= 1u;
+  __syncthreads();
+  if (abort_flag) return;
+
+  const int w = tid >> 5, lane = tid & 31, W = blockDim.x >> 5;
+  // exact-phase scratch of each warp at the end of the dynamic shared memory
+  WarpScratch ws;
+  {
+    unsigned char* base = smem_raw + a.scratch_offset + static_cast<size_t>(w) * WARP_SCRATCH_BYTES;
+    ws.acc = reinterpret_cast<float4*>(base);
+    ws.queue = reinterpret_cast<uint32_t*>(base + 32 * NB * 16);
+    ws.count = reinterpret_cast<int*>(base + 32 * NB * 16 + QUEUE_CAP * 4);
+    for (int i = lane; i < 32 * NB; i += 32) ws.acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane == 0) { ws.count[0] = 0; ws.count[1] = 0; }
+  }
+  (void)W;
+  int cur = -1;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(a.item_counter, 1);
+    __syncthreads();
+    const int idx = s_item;
+    if (idx >= a.n_items) break;
+    const uint32_t item = a.items[idx];
+    const int p = static_cast<int>(item >> ITEM_TILE_BITS);
+    const int tile = static_cast<int>(item & ((1u << ITEM_TILE_BITS) - 1));
+    const ProbDesc& d = a.probs[p];
+    const int pw = (d.prob_words + 3) & ~3;
+    if (p != cur) {
+      if (tid == 0) {
+        fence_proxy_async_smem();  // earlier generic reads of the old tables before the async overwrite
+        mbar_arrive_expect_tx(&bar, static_cast<uint32_t>(pw * 4));
+        tma_bulk_g2s(s_pb, d.prob, static_cast<uint32_t>(pw * 4), &bar);
+        if (!mbar_wait_bounded(&bar, phase, 1 << 20)) {
+          atomicOr(a.err, ERR_TMA_TIMEOUT);
+          abort_flag = 1;
+          mbar_wait_bounded(&bar, phase, 1 << 16);
+        }
+      }
+      phase ^= 1u;
+      cur = p;
+      __syncthreads();
+      if (abort_flag) return;
+    }
+    run_tile<L>(d, tile, s_sc, s_pb, reinterpret_cast<float*>(s_pb + pw), ws);
+    __syncthreads();  // everyone has read s_item and the tables before they change
   }
 }
 
@@ -1007,8 +1051,7 @@ __global__ void sample_uniform_kernel(const uint32_t* __restrict__ pb, const uin
 
 // ------------------------------------------------------------------ launchers
 template <int L>
-static cudaError_t launch_opt(const OptArgs& a, int K, size_t smem, cudaStream_t st) {
-  constexpr int PT = 32 / L;
+static cudaError_t launch_opt(const LaunchArgs& a, int warps, int grid, size_t smem, cudaStream_t st) {
   static size_t attr_bytes = 0;  // largest dynamic shared-memory size enabled so far
   if (smem > 48 * 1024 && smem > attr_bytes) {
     cudaError_t e = cudaFuncSetAttribute(optimize_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1016,19 +1059,29 @@ static cudaError_t launch_opt(const OptArgs& a, int K, size_t smem, cudaStream_t
     if (e != cudaSuccess) return e;
     attr_bytes = smem;
   }
-  const int W = optimize_warps(K);
-  const int grid = (a.P + PT - 1) / PT;
-  if (grid == 0) return cudaSuccess;
-  optimize_kernel<L><<<grid, W * 32, smem, st>>>(a);
+  if (grid <= 0) return cudaSuccess;
+  optimize_kernel<L><<<grid, warps * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_optimize(const OptArgs& a, int L, int K, size_t smem, cudaStream_t st) {
+int optimize_blocks_per_sm(int L, int warps, size_t smem) {
+  int n = 0;
+  cudaError_t e = cudaSuccess;
   switch (L) {
-    case 1: return launch_opt<1>(a, K, smem, st);
-    case 2: return launch_opt<2>(a, K, smem, st);
-    case 4: return launch_opt<4>(a, K, smem, st);
-    case 8: return launch_opt<8>(a, K, smem, st);
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<1>, warps * 32, smem); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<2>, warps * 32, smem); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<4>, warps * 32, smem); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<8>, warps * 32, smem); break;
+  }
+  return e == cudaSuccess ? n : 1;
+}
+
+cudaError_t launch_optimize(const LaunchArgs& a, int L, int warps, int grid, size_t smem, cudaStream_t st) {
+  switch (L) {
+    case 1: return launch_opt<1>(a, warps, grid, smem, st);
+    case 2: return launch_opt<2>(a, warps, grid, smem, st);
+    case 4: return launch_opt<4>(a, warps, grid, smem, st);
+    case 8: return launch_opt<8>(a, warps, grid, smem, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1042,12 +1095,14 @@ cudaError_t launch_sample(const uint32_t* pb, const uint32_t* sc, float* x, floa
   return cudaGetLastError();
 }
 
-size_t optimize_smem_bytes(int scene_words, int prob_words, int D, int NT, int warps, int L) {
+// Dynamic shared memory: scene tables, the largest problem's tables and tile
+// (x, m, v, gradient, terms, flags), then the warps' exact-phase scratch.
+size_t optimize_tile_bytes(int prob_words, int D, int NT, int L) {
   const int PT = 32 / L;
-  const size_t sw = (scene_words + 3) & ~3, pw = (prob_words + 3) & ~3;
-  return 4 * (sw + pw) + 4 * (4 * static_cast<size_t>(D) * PT + static_cast<size_t>(NT) * PT) +
-         ((PT * 4 + 15) & ~15) + static_cast<size_t>(WARP_SCRATCH_BYTES) * warps;
+  const size_t pw = (prob_words + 3) & ~3;
+  return 4 * pw + 4 * (4 * static_cast<size_t>(D) * PT + static_cast<size_t>(NT) * PT) + ((PT * 4 + 15) & ~15);
 }
+size_t optimize_scratch_bytes(int warps) { return static_cast<size_t>(WARP_SCRATCH_BYTES) * warps; }
 
 int optimize_warps(int K) {
   const int per = (K + 11) / 12;  // configurations per warp

@@ -213,3 +213,55 @@ def test_no_obstacles_no_other_boxes(pkg):
     sc0 = dataclasses.replace(sc, obs_center=np.zeros((0, 3)), obs_rot=np.zeros((0, 3, 3)), obs_half=np.zeros((0, 3)))
     X = sg.random_particles(sc0, acts, 40, seed=91)
     compare_eval(Problem(sc0, acts), X, *_eval(pkg, sc0, acts, X), label="empty environment")
+
+
+def test_batched_launch_matches_separate_launches(pkg):
+    """Skeletons of different lengths and batch sizes share one persistent
+    launch; every tile is independent, so the result equals separate launches
+    bit for bit."""
+    sc, _ = sg.packing_problem(2001)
+    skels = [sg.pick_place_skeleton([0]), sg.pick_place_skeleton([0, 1, 2]),
+             sg.pick_place_skeleton(range(6), goal=True)]
+    sizes = [100, 70, 45]
+    opts = pkg.default_options(lanes=1)
+
+    def run(batched):
+        scene = pkg.Scene(sc)
+        pids = [scene.set_skeleton(a, opts) for a in skels]
+        for pid, n, a in zip(pids, sizes, skels):
+            X = sg.random_particles(sc, a, n, seed=100 + n, spread=0.5)
+            scene.set_particles(pid, X.T.astype(np.float32))
+        if batched:
+            scene.optimize(pids, 6)
+        else:
+            for pid in pids:
+                scene.optimize(pid, 6)
+        out = [scene.get_particles(pid)[0] for pid in pids]
+        qs = [scene.query(pid, n) for pid, n in zip(pids, sizes)]
+        scene.close()
+        return out, qs
+
+    xb, qb = run(True)
+    xs, qs = run(False)
+    for a, b in zip(xb, xs):
+        assert np.array_equal(a, b)
+    for a, b in zip(qb, qs):
+        assert np.array_equal(a["cost"], b["cost"]) and a["first_iter"] == b["first_iter"]
+
+
+def test_batched_problem_matches_oracle(pkg):
+    """A short skeleton in a batched launch still matches the oracle."""
+    sc, _ = sg.packing_problem(2001)
+    acts = sg.pick_place_skeleton([0, 1])
+    pr = Problem(sc, acts)
+    scene = pkg.Scene(sc)
+    pid = scene.set_skeleton(acts)
+    other = scene.set_skeleton(sg.pick_place_skeleton(range(6), goal=True))
+    X = sg.random_particles(sc, acts, 64, seed=5)
+    scene.set_particles(pid, X.T.astype(np.float32))
+    scene.sample(other, 200, seed=3)
+    scene.optimize([other, pid], 0)              # evaluation only
+    q = scene.query(pid, 64)
+    scene.close()
+    J = pr.total_cost(torch.tensor(X.astype(np.float32).astype(np.float64))).numpy()
+    assert cost_ok(q["cost"].astype(np.float64), J).all()
