@@ -187,6 +187,29 @@ tamp_status tamp_query_satisfied(tamp_scene *scene, int problem_id, uint8_t *mas
 tamp_status tamp_eval(tamp_scene *scene, int problem_id, int n, const float *x_dev,
                       float *cost_dev, float *terms_dev, uint8_t *flags_dev, float *grad_dev);
 
+/* tamp_eval for callers that cannot allocate device memory while they run --
+ * for example a control loop whose device-memory budget is frozen after
+ * start-up, or a host framework that serves every device byte from its own
+ * pool and does not let libraries call cudaMalloc.  It evaluates exactly what
+ * tamp_eval does, with the same arguments, but never allocates: the launch's
+ * work-item list, problem descriptor and work counter live in one static
+ * device array of 16.5 KB compiled into the library (each GPU that loads the
+ * library keeps its copy until the process exits).
+ *   - The first call on a device sets the array up (resolves its address and
+ *     writes the work-item list); make that first call before any stream
+ *     capture.
+ *   - Batches are limited to 4096 tiles of 32/L particles (131072 particles at
+ *     one lane per particle-configuration); a larger n returns
+ *     TAMP_ERR_INVALID_ARG with the limit in tamp_last_error.
+ *   - Every call, on any scene, shares the array and leaves its contents in
+ *     place; the counter is cleared on the scene's stream at the start of each
+ *     call.  Calls whose work overlaps on the GPU (different streams, or
+ *     different scenes on one device without ordering) race on the array.
+ * The paper has no counterpart: this is an interface convenience. */
+tamp_status tamp_eval_static_scratch(tamp_scene *scene, int problem_id, int n, const float *x_dev,
+                                     float *cost_dev, float *terms_dev, uint8_t *flags_dev,
+                                     float *grad_dev);
+
 /* Work counters of a problem since its batch was last sampled or set:
  * out[0] = (sphere batch, cuboid) pairs and out[1] = (sphere batch, box) pairs
  * that the collision broad phase passed on to the exact test (the exact work is

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -915,3 +916,100 @@ tamp_status tamp_work_counters(tamp_scene* s, int id, uint64_t out[2]) {
 const char* tamp_last_error(const tamp_scene* s) { return s ? s->err.c_str() : "null scene"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- evaluation with static scratch
+// tamp_eval keeps its launch tables (work-item list, problem descriptor, work
+// counter) in device memory it allocates on demand.  Callers that may not
+// allocate device memory once they are running -- a control loop whose memory
+// budget is fixed after start-up, a host framework that hands every device
+// byte out of its own pool and forbids library allocations -- use
+// tamp_eval_static_scratch instead, which keeps those tables in the array below.
+// The array is a file-scope device variable: every GPU that loads the library
+// holds one copy until the process exits.  In host code its name only stands in
+// for the symbol; the device address comes from cudaGetSymbolAddress, resolved
+// once per device on that device's first call.
+namespace {
+
+constexpr int kStaticTiles = 4096;                 // largest batch: 4096 tiles of 32/L particles
+constexpr size_t kStaticCounterOff = 0;            // int work-item counter
+constexpr size_t kStaticDescOff = 256;             // one ProbDesc
+constexpr size_t kStaticItemsOff = 512;            // uint32 work items 0 .. kStaticTiles - 1
+constexpr size_t kStaticBytes = kStaticItemsOff + 4 * kStaticTiles;
+static_assert(sizeof(ProbDesc) <= kStaticItemsOff - kStaticDescOff, "descriptor slot too small");
+
+__device__ __align__(256) unsigned char g_eval_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+std::once_flag g_scratch_once[kMaxDevices];
+unsigned char* g_scratch_dev[kMaxDevices];
+cudaError_t g_scratch_err[kMaxDevices];
+
+// With `device` current: resolve the array's device address and write the
+// work-item list (tile i of problem 0), which never changes afterwards.
+cudaError_t static_scratch(int device, unsigned char** out) {
+  std::call_once(g_scratch_once[device], [device]() {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_eval_scratch);
+    if (e == cudaSuccess) {
+      uint32_t items[kStaticTiles];
+      for (int i = 0; i < kStaticTiles; ++i) items[i] = static_cast<uint32_t>(i);
+      e = cudaMemcpy(static_cast<unsigned char*>(p) + kStaticItemsOff, items, sizeof items, cudaMemcpyHostToDevice);
+    }
+    g_scratch_dev[device] = static_cast<unsigned char*>(p);
+    g_scratch_err[device] = e;
+  });
+  *out = g_scratch_dev[device];
+  return g_scratch_err[device];
+}
+
+}  // namespace
+
+extern "C" tamp_status tamp_eval_static_scratch(tamp_scene* s, int id, int n, const float* x, float* cost,
+                                                float* terms, uint8_t* flags, float* grad) {
+  Problem* pr = get_problem(s, id);
+  if (!pr) return fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", id);
+  if (n <= 0 || !x) return fail(s, TAMP_ERR_INVALID_ARG, "bad eval arguments");
+  if (s->device < 0 || s->device >= kMaxDevices) return fail(s, TAMP_ERR_INVALID_ARG, "device %d", s->device);
+  DeviceGuard g(s->device);
+  unsigned char* scratch = nullptr;
+  cudaError_t e = static_scratch(s->device, &scratch);
+  if (e != cudaSuccess)
+    return fail(s, TAMP_ERR_CUDA, "static scratch set-up: %s", cudaGetErrorString(e));
+  // lane split and shared memory as for tamp_eval
+  const int warps = optimize_warps(pr->K);
+  int L = preferred_lanes(pr->opt.lanes, n);
+  size_t smem = 0;
+  for (; L <= 8; L *= 2) {
+    smem = 4 * ((s->blob.size() + 3) & ~static_cast<size_t>(3)) +
+           optimize_tile_bytes(static_cast<int>(pr->blob.size()), pr->D, pr->NT, L) + optimize_scratch_bytes(warps);
+    if (smem <= kMaxDynSmem) break;
+  }
+  if (L > 8) return fail(s, TAMP_ERR_INVALID_ARG, "problem does not fit in shared memory");
+  const int PT = 32 / L;
+  const int tiles = (n + PT - 1) / PT;
+  if (tiles > kStaticTiles)
+    return fail(s, TAMP_ERR_INVALID_ARG,
+                "batch of %d particles exceeds the static scratch limit of %d tiles (%d particles at %d lanes)", n,
+                kStaticTiles, kStaticTiles * PT, L);
+  ProbDesc d{};
+  d.prob = pr->d_blob;
+  d.prob_words = static_cast<int>(pr->blob.size());
+  d.x_in = x; d.stride = n; d.P = n;
+  d.out_cost = cost; d.out_terms = terms; d.out_flags = flags; d.out_grad = grad;
+  d.n_steps = 0;
+  d.gscale = 1.f; d.beta1 = pr->opt.beta1; d.beta2 = pr->opt.beta2; d.eps = pr->opt.eps;
+  CUDA_TRY(s, cudaMemcpyAsync(scratch + kStaticDescOff, &d, sizeof d, cudaMemcpyHostToDevice, s->stream));
+  CUDA_TRY(s, cudaMemsetAsync(scratch + kStaticCounterOff, 0, sizeof(int), s->stream));  // starts at zero
+  LaunchArgs a{};
+  a.scene = s->d_blob;
+  a.scene_words = static_cast<int>(s->blob.size());
+  a.probs = reinterpret_cast<const ProbDesc*>(scratch + kStaticDescOff);
+  a.items = reinterpret_cast<const uint32_t*>(scratch + kStaticItemsOff);
+  a.n_items = tiles;
+  a.item_counter = reinterpret_cast<int*>(scratch + kStaticCounterOff);
+  a.err = s->d_err;
+  a.scratch_offset = static_cast<int>(smem - optimize_scratch_bytes(warps));
+  const int per_sm = std::max(1, optimize_blocks_per_sm(L, warps, smem));
+  CUDA_TRY(s, launch_optimize(a, L, warps, std::min(tiles, s->sm_count * per_sm), smem, s->stream));
+  return TAMP_OK;
+}
