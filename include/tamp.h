@@ -171,6 +171,22 @@ tamp_status tamp_get_particles(tamp_scene *scene, int problem_id, float *x, floa
 tamp_status tamp_optimize_steps(tamp_scene *scene, const int *problem_ids, int n_problems,
                                 int n_steps);
 
+/* A CUDA graph of the optimisation loop (OptimizeParticles, Alg. 1; Sec. V-B):
+ * n_chunks chunks of steps_per_chunk fused iterations of the listed problems,
+ * each chunk followed by a one-thread control kernel that advances the step
+ * counts and -- if stop_on_first -- raises a stop flag once any problem has a
+ * satisfying particle (Eq. 3, the stopping criterion of Sec. V-B), after which
+ * the remaining chunks return at once.  The graph records the problems' batch
+ * buffers: it is valid while each batch keeps its size.  Created on a private
+ * capture stream; run on the scene's stream. */
+typedef struct tamp_graph tamp_graph;
+tamp_status tamp_graph_create(tamp_scene *scene, const int *problem_ids, int n_problems, int steps_per_chunk,
+                              int n_chunks, int stop_on_first, tamp_graph **out);
+/* Replay a graph and wait for it; *steps_run (may be NULL) receives the number
+ * of iterations actually run (a multiple of steps_per_chunk). */
+tamp_status tamp_graph_run(tamp_graph *graph, int *steps_run);
+tamp_status tamp_graph_destroy(tamp_graph *graph);
+
 /* Results of the last check of a problem (IsGoalSatisfied, Alg. 1; Eq. 3; the
  * Eq. 5 per-constraint satisfied counts, in constraint order = term order with
  * the OBJ_DIST term left out).  Host pointers, each may be NULL: mask[P],

@@ -200,6 +200,38 @@ class Scene:
         return cost, terms, flags, grad
 
 
+class Graph:
+    """CUDA graph of chunked optimisation with an optional device-side stop on
+    the first satisfying particle (tamp_graph_*)."""
+
+    def __init__(self, scene: Scene, pids, steps_per_chunk: int, n_chunks: int, stop_on_first: bool = False):
+        if isinstance(pids, int):
+            pids = [pids]
+        self.scene = scene
+        arr = (ctypes.c_int * len(pids))(*pids)
+        h = ctypes.c_void_p()
+        scene._check(scene._lib.tamp_graph_create(scene._h, arr, len(pids), int(steps_per_chunk), int(n_chunks),
+                                                  int(bool(stop_on_first)), ctypes.byref(h)))
+        self._h = h
+
+    def run(self) -> int:
+        """Replay and wait; returns the number of iterations run."""
+        steps = ctypes.c_int()
+        self.scene._check(self.scene._lib.tamp_graph_run(self._h, ctypes.byref(steps)))
+        return steps.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.scene._lib.tamp_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def cost_fn():
     """torch.autograd.Function over the fused cost + adjoint kernel: forward
     returns the Eq. 2 cost of every particle; backward returns dJ/dx from the

@@ -64,6 +64,10 @@ SIGNATURES = {
     "tamp_eval_static_scratch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "tamp_work_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
+    "tamp_graph_create": (ctypes.c_int, [ctypes.c_void_p, c_int_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "tamp_graph_run": (ctypes.c_int, [ctypes.c_void_p, c_int_p]),
+    "tamp_graph_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "tamp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
 }
 

@@ -18,6 +18,9 @@
 
 namespace tamp {
 cudaError_t launch_optimize(const LaunchArgs& a, int L, int warps, int grid, size_t smem, cudaStream_t st);
+cudaError_t optimize_set_smem(int L, size_t smem);
+cudaError_t launch_chunk_control(int* t_dev, const int* const* first_iters, int n_problems, int steps,
+                                 int stop_on_first, int* stop, int* chunks_run, cudaStream_t st);
 size_t optimize_tile_bytes(int prob_words, int D, int NT, int L);
 size_t optimize_scratch_bytes(int warps);
 int optimize_blocks_per_sm(int L, int warps, size_t smem);
@@ -552,12 +555,18 @@ struct Job {
   ProbDesc d;
 };
 
-// One launch of the persistent kernel over several problems: descriptors and
-// the work-item list (longest skeletons first) go to the device, the lane split
-// and shared memory are sized for the largest problem, and the grid fills the
-// SMs (CTAs then pull items until the list is empty).
-tamp_status launch_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lanes) {
-  if (jobs.empty()) return TAMP_OK;
+// Launch plan of the persistent kernel over several problems: the lane split
+// and shared memory sized for the largest problem, the work-item list (longest
+// skeletons first) and the grid that fills the SMs (CTAs then pull items until
+// the list is empty).
+struct Plan {
+  int L = 1, warps = 1, grid = 0;
+  size_t smem = 0;
+  std::vector<ProbDesc> descs;
+  std::vector<uint32_t> items;
+};
+
+tamp_status plan_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lanes, Plan* plan) {
   long total = 0;
   int warps = 1;
   for (const Job& j : jobs) {
@@ -565,9 +574,9 @@ tamp_status launch_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lan
     warps = std::max(warps, optimize_warps(j.pr->K));
   }
   int L = preferred_lanes(requested_lanes, total);
-  size_t smem = 0, tile = 0;
+  size_t smem = 0;
   for (; L <= 8; L *= 2) {
-    tile = 0;
+    size_t tile = 0;
     for (const Job& j : jobs)
       tile = std::max(tile, optimize_tile_bytes(static_cast<int>(j.pr->blob.size()), j.pr->D, j.pr->NT, L));
     smem = 4 * ((s->blob.size() + 3) & ~static_cast<size_t>(3)) + tile + optimize_scratch_bytes(warps);
@@ -575,16 +584,44 @@ tamp_status launch_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lan
   }
   if (L > 8) return fail(s, TAMP_ERR_INVALID_ARG, "problem does not fit in shared memory");
   const int PT = 32 / L;
-  // work items: problems by decreasing per-tile work (configurations), then tiles
   std::vector<int> order(jobs.size());
   for (size_t i = 0; i < jobs.size(); ++i) order[i] = static_cast<int>(i);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return jobs[a].pr->K > jobs[b].pr->K; });
-  std::vector<uint32_t> items;
+  plan->items.clear();
   for (int i : order) {
     const int tiles = (jobs[i].d.P + PT - 1) / PT;
     if (tiles >= (1 << ITEM_TILE_BITS)) return fail(s, TAMP_ERR_INVALID_ARG, "batch too large");
-    for (int t = 0; t < tiles; ++t) items.push_back(static_cast<uint32_t>(i) << ITEM_TILE_BITS | static_cast<uint32_t>(t));
+    for (int t = 0; t < tiles; ++t)
+      plan->items.push_back(static_cast<uint32_t>(i) << ITEM_TILE_BITS | static_cast<uint32_t>(t));
   }
+  plan->descs.clear();
+  for (const Job& j : jobs) plan->descs.push_back(j.d);
+  plan->L = L;
+  plan->warps = warps;
+  plan->smem = smem;
+  const int per_sm = std::max(1, optimize_blocks_per_sm(L, warps, smem));
+  plan->grid = std::min(static_cast<int>(plan->items.size()), s->sm_count * per_sm);
+  return TAMP_OK;
+}
+
+LaunchArgs plan_args(const tamp_scene* s, const Plan& plan, ProbDesc* d_descs, uint32_t* d_items, int* d_counter) {
+  LaunchArgs a{};
+  a.scene = s->d_blob;
+  a.scene_words = static_cast<int>(s->blob.size());
+  a.probs = d_descs;
+  a.items = d_items;
+  a.n_items = static_cast<int>(plan.items.size());
+  a.item_counter = d_counter;
+  a.err = s->d_err;
+  a.scratch_offset = static_cast<int>(plan.smem - optimize_scratch_bytes(plan.warps));
+  return a;
+}
+
+tamp_status launch_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lanes) {
+  if (jobs.empty()) return TAMP_OK;
+  Plan plan;
+  tamp_status st = plan_jobs(s, jobs, requested_lanes, &plan);
+  if (st != TAMP_OK) return st;
   if (static_cast<int>(jobs.size()) > s->descs_cap) {
     cudaFree(s->d_descs);
     s->d_descs = nullptr;
@@ -592,31 +629,20 @@ tamp_status launch_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lan
     CUDA_TRY(s, cudaMalloc(&s->d_descs, jobs.size() * sizeof(ProbDesc)));
     s->descs_cap = static_cast<int>(jobs.size());
   }
-  if (static_cast<int>(items.size()) > s->items_cap) {
+  if (static_cast<int>(plan.items.size()) > s->items_cap) {
     cudaFree(s->d_items);
     s->d_items = nullptr;
     s->items_cap = 0;
-    CUDA_TRY(s, cudaMalloc(&s->d_items, items.size() * 4));
-    s->items_cap = static_cast<int>(items.size());
+    CUDA_TRY(s, cudaMalloc(&s->d_items, plan.items.size() * 4));
+    s->items_cap = static_cast<int>(plan.items.size());
   }
-  std::vector<ProbDesc> descs;
-  for (const Job& j : jobs) descs.push_back(j.d);
-  CUDA_TRY(s, cudaMemcpyAsync(s->d_descs, descs.data(), descs.size() * sizeof(ProbDesc), cudaMemcpyHostToDevice,
+  CUDA_TRY(s, cudaMemcpyAsync(s->d_descs, plan.descs.data(), plan.descs.size() * sizeof(ProbDesc),
+                              cudaMemcpyHostToDevice, s->stream));
+  CUDA_TRY(s, cudaMemcpyAsync(s->d_items, plan.items.data(), plan.items.size() * 4, cudaMemcpyHostToDevice,
                               s->stream));
-  CUDA_TRY(s, cudaMemcpyAsync(s->d_items, items.data(), items.size() * 4, cudaMemcpyHostToDevice, s->stream));
   CUDA_TRY(s, cudaMemsetAsync(s->d_item_counter, 0, 4, s->stream));
-  LaunchArgs a{};
-  a.scene = s->d_blob;
-  a.scene_words = static_cast<int>(s->blob.size());
-  a.probs = s->d_descs;
-  a.items = s->d_items;
-  a.n_items = static_cast<int>(items.size());
-  a.item_counter = s->d_item_counter;
-  a.err = s->d_err;
-  a.scratch_offset = static_cast<int>(smem - optimize_scratch_bytes(warps));
-  const int per_sm = std::max(1, optimize_blocks_per_sm(L, warps, smem));
-  const int grid = std::min(a.n_items, s->sm_count * per_sm);
-  CUDA_TRY(s, launch_optimize(a, L, warps, grid, smem, s->stream));
+  const LaunchArgs a = plan_args(s, plan, s->d_descs, s->d_items, s->d_item_counter);
+  CUDA_TRY(s, launch_optimize(a, plan.L, plan.warps, plan.grid, plan.smem, s->stream));
   return TAMP_OK;
 }
 
@@ -916,6 +942,129 @@ tamp_status tamp_work_counters(tamp_scene* s, int id, uint64_t out[2]) {
 const char* tamp_last_error(const tamp_scene* s) { return s ? s->err.c_str() : "null scene"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- CUDA graphs of the optimisation loop
+struct tamp_graph {
+  tamp_scene* s = nullptr;
+  std::vector<Problem*> prs;
+  std::vector<int> sizes;  // batch sizes the graph was built for
+  int steps = 0, chunks = 0;
+  ProbDesc* d_descs = nullptr;
+  uint32_t* d_items = nullptr;
+  int* d_ints = nullptr;  // [0] item counter, [1] stop, [2] chunks run, [3..] per-problem step counts
+  const int** d_first = nullptr;
+  cudaStream_t capture = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+void free_graph(tamp_graph* g) {
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->capture) cudaStreamDestroy(g->capture);
+  cudaFree(g->d_descs); cudaFree(g->d_items); cudaFree(g->d_ints); cudaFree(g->d_first);
+  delete g;
+}
+}  // namespace
+
+extern "C" tamp_status tamp_graph_create(tamp_scene* s, const int* ids, int n, int steps_per_chunk, int n_chunks,
+                                         int stop_on_first, tamp_graph** out) {
+  if (!s) return TAMP_ERR_INVALID_ARG;
+  if (!ids || n <= 0 || steps_per_chunk <= 0 || n_chunks <= 0 || !out)
+    return fail(s, TAMP_ERR_INVALID_ARG, "bad graph arguments");
+  DeviceGuard dg(s->device);
+  tamp_graph* g = new tamp_graph();
+  g->s = s;
+  g->steps = steps_per_chunk;
+  g->chunks = n_chunks;
+  std::vector<Job> jobs;
+  auto bail = [&](tamp_status st) {
+    free_graph(g);
+    return st;
+  };
+  cudaError_t e = cudaMalloc(&g->d_ints, (3 + n) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_first, n * sizeof(int*));
+  if (e != cudaSuccess) return bail(fail(s, TAMP_ERR_OOM, "graph buffers: %s", cudaGetErrorString(e)));
+  std::vector<const int*> firsts;
+  for (int i = 0; i < n; ++i) {
+    Problem* pr = get_problem(s, ids[i]);
+    if (!pr) return bail(fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", ids[i]));
+    if (!pr->has_batch) return bail(fail(s, TAMP_ERR_STATE, "problem %d has no particles", ids[i]));
+    if (std::find(g->prs.begin(), g->prs.end(), pr) != g->prs.end())
+      return bail(fail(s, TAMP_ERR_INVALID_ARG, "problem %d listed twice", ids[i]));
+    g->prs.push_back(pr);
+    g->sizes.push_back(pr->P);
+    ProbDesc d = state_desc(*pr, steps_per_chunk);
+    d.t_dev = g->d_ints + 3 + i;
+    jobs.push_back({pr, d});
+    firsts.push_back(pr->d_first);
+  }
+  Plan plan;
+  tamp_status st = plan_jobs(s, jobs, g->prs[0]->opt.lanes, &plan);
+  if (st != TAMP_OK) return bail(st);
+  e = cudaMalloc(&g->d_descs, plan.descs.size() * sizeof(ProbDesc));
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_items, plan.items.size() * 4);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(g->d_descs, plan.descs.data(), plan.descs.size() * sizeof(ProbDesc), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_items, plan.items.data(), plan.items.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_first, firsts.data(), n * sizeof(int*), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = optimize_set_smem(plan.L, plan.smem);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return bail(fail(s, TAMP_ERR_CUDA, "graph set-up: %s", cudaGetErrorString(e)));
+  LaunchArgs a = plan_args(s, plan, g->d_descs, g->d_items, g->d_ints);
+  a.stop = g->d_ints + 1;
+  // capture: per chunk, clear the counts and the item counter, optimise, control
+  e = cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal);
+  for (int c = 0; c < n_chunks && e == cudaSuccess; ++c) {
+    for (Problem* pr : g->prs)
+      if (e == cudaSuccess)
+        e = cudaMemsetAsync(pr->d_counts, 0, static_cast<size_t>(std::max(pr->NCON, 1)) * 4, g->capture);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_ints, 0, sizeof(int), g->capture);
+    if (e == cudaSuccess) e = launch_optimize(a, plan.L, plan.warps, plan.grid, plan.smem, g->capture);
+    if (e == cudaSuccess)
+      e = launch_chunk_control(g->d_ints + 3, g->d_first, n, steps_per_chunk, stop_on_first, g->d_ints + 1,
+                               g->d_ints + 2, g->capture);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(g->capture, &g->graph);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+  if (e != cudaSuccess) return bail(fail(s, TAMP_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e)));
+  *out = g;
+  return TAMP_OK;
+}
+
+extern "C" tamp_status tamp_graph_run(tamp_graph* g, int* steps_run) {
+  if (!g) return TAMP_ERR_INVALID_ARG;
+  tamp_scene* s = g->s;
+  DeviceGuard dg(s->device);
+  const int n = static_cast<int>(g->prs.size());
+  std::vector<int> host(3 + n, 0);
+  for (int i = 0; i < n; ++i) {
+    if (g->prs[i]->P != g->sizes[i] || !g->prs[i]->has_batch)
+      return fail(s, TAMP_ERR_STATE, "batch of a graph's problem changed size; rebuild the graph");
+    host[3 + i] = g->prs[i]->t;
+  }
+  CUDA_TRY(s, cudaMemcpyAsync(g->d_ints, host.data(), host.size() * sizeof(int), cudaMemcpyHostToDevice, s->stream));
+  CUDA_TRY(s, cudaGraphLaunch(g->exec, s->stream));
+  CUDA_TRY(s, cudaMemcpyAsync(host.data(), g->d_ints, host.size() * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  tamp_status st = check_device_error(s);  // synchronises
+  if (st != TAMP_OK) return st;
+  for (int i = 0; i < n; ++i) {
+    g->prs[i]->t = host[3 + i];
+    g->prs[i]->checked = true;
+  }
+  if (steps_run) *steps_run = host[2] * g->steps;
+  return TAMP_OK;
+}
+
+extern "C" tamp_status tamp_graph_destroy(tamp_graph* g) {
+  if (!g) return TAMP_ERR_INVALID_ARG;
+  DeviceGuard dg(g->s->device);
+  cudaStreamSynchronize(g->s->stream);
+  free_graph(g);
+  return TAMP_OK;
+}
 
 // ---------------------------------------------------------------- evaluation with static scratch
 // tamp_eval keeps its launch tables (work-item list, problem descriptor, work

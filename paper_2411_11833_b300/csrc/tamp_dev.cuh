@@ -99,6 +99,7 @@ struct LaunchArgs {
   int* item_counter;                  // zero before the launch
   int* err;
   int scratch_offset;                 // bytes from the start of dynamic shared memory to the warp scratch
+  const int* stop;                    // optional: a non-zero value makes the launch return at once
 };
 constexpr int ITEM_TILE_BITS = 20;
 

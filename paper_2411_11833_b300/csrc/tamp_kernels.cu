@@ -943,6 +943,7 @@ __global__ void __launch_bounds__(384, 1) optimize_kernel(LaunchArgs a) {
   uint32_t* s_sc = reinterpret_cast<uint32_t*>(smem_raw);
   uint32_t* s_pb = s_sc + sw;
   const int tid = threadIdx.x;
+  if (a.stop && *a.stop) return;  // a graph chunk after the stopping condition was met
   uint32_t phase = 0;
   if (tid == 0) {
     abort_flag = 0;
@@ -1049,15 +1050,41 @@ __global__ void sample_uniform_kernel(const uint32_t* __restrict__ pb, const uin
   v[c * stride + i] = 0.f;
 }
 
+// ------------------------------------------------------------------ graph chunk controller
+// After each chunk of a captured optimisation: advance every problem's step
+// count, and raise the stop flag when stopping on the first satisfying particle
+// and some problem has one (the Eq. 3 check records its iteration).
+__global__ void chunk_control_kernel(int* t_dev, const int* const* first_iters, int n_problems, int steps,
+                                     int stop_on_first, int* stop, int* chunks_run) {
+  if (threadIdx.x != 0 || blockIdx.x != 0 || *stop) return;
+  bool found = false;
+  for (int p = 0; p < n_problems; ++p) {
+    t_dev[p] += steps;
+    found = found || *first_iters[p] != 0x7fffffff;
+  }
+  *chunks_run += 1;
+  if (stop_on_first && found) *stop = 1;
+}
+
+cudaError_t launch_chunk_control(int* t_dev, const int* const* first_iters, int n_problems, int steps,
+                                 int stop_on_first, int* stop, int* chunks_run, cudaStream_t st) {
+  chunk_control_kernel<<<1, 32, 0, st>>>(t_dev, first_iters, n_problems, steps, stop_on_first, stop, chunks_run);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ launchers
+// largest dynamic shared-memory size enabled so far for optimize_kernel<1,2,4,8>
+static size_t g_smem_enabled[4] = {0, 0, 0, 0};
+static int lane_slot(int L) { return L == 1 ? 0 : (L == 2 ? 1 : (L == 4 ? 2 : 3)); }
+
 template <int L>
 static cudaError_t launch_opt(const LaunchArgs& a, int warps, int grid, size_t smem, cudaStream_t st) {
-  static size_t attr_bytes = 0;  // largest dynamic shared-memory size enabled so far
-  if (smem > 48 * 1024 && smem > attr_bytes) {
+  size_t& enabled = g_smem_enabled[lane_slot(L)];
+  if (smem > 48 * 1024 && smem > enabled) {
     cudaError_t e = cudaFuncSetAttribute(optimize_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    attr_bytes = smem;
+    enabled = smem;
   }
   if (grid <= 0) return cudaSuccess;
   optimize_kernel<L><<<grid, warps * 32, smem, st>>>(a);
@@ -1074,6 +1101,24 @@ int optimize_blocks_per_sm(int L, int warps, size_t smem) {
     default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<8>, warps * 32, smem); break;
   }
   return e == cudaSuccess ? n : 1;
+}
+
+// Allow `smem` bytes of dynamic shared memory for optimize_kernel<L> (outside
+// any stream capture).
+cudaError_t optimize_set_smem(int L, size_t smem) {
+  size_t& enabled = g_smem_enabled[lane_slot(L)];
+  if (smem <= 48 * 1024 || smem <= enabled) return cudaSuccess;
+  const int v = static_cast<int>(smem);
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (L) {
+    case 1: e = cudaFuncSetAttribute(optimize_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, v); break;
+    case 2: e = cudaFuncSetAttribute(optimize_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, v); break;
+    case 4: e = cudaFuncSetAttribute(optimize_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, v); break;
+    case 8: e = cudaFuncSetAttribute(optimize_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, v); break;
+    default: break;
+  }
+  if (e == cudaSuccess) enabled = smem;
+  return e;
 }
 
 cudaError_t launch_optimize(const LaunchArgs& a, int L, int warps, int grid, size_t smem, cudaStream_t st) {

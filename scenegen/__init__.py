@@ -206,6 +206,64 @@ def stress_problem(seed: int = 5001):
     return sc, pick_place_skeleton(range(12), goal=True)
 
 
+def stacking_problem(seed: int = 3001):
+    """Obstructed stacking: box A must go on box B, whose top face is fully
+    covered by 2-4 blockers.  Surface 0 is B's top face, surface 1 a table
+    region for the blockers; 16 static cuboids.  Returns (scene, skeletons,
+    batch sizes): 16 candidate skeletons -- move 0, 1, 2 or 3 blockers (in
+    every order, truncated to 16) to the table region, then Pick A / Place A on
+    B -- of 2 to 8 actions, each with a batch size from {1024, 2048, 4096, 8192}."""
+    import itertools
+    rng = np.random.default_rng(seed)
+    arm = random_arm(rng)
+    n_block = int(rng.integers(2, 5))
+    hB = np.array([0.07, 0.07, 0.03])                      # B: 14 x 14 x 6 cm
+    hA = rng.uniform(0.022, 0.03, 3)
+    ang = rng.uniform(-math.pi, math.pi)
+    Bxy = 0.6 * np.array([math.cos(ang), math.sin(ang)])
+    Byaw = rng.uniform(-math.pi, math.pi)
+    Axy = 0.6 * np.array([math.cos(ang + 0.8), math.sin(ang + 0.8)])
+    reg_xy = 0.6 * np.array([math.cos(ang - 0.9), math.sin(ang - 0.9)])
+    reg_h = np.array([0.15, 0.15])
+    topB = 2 * hB[2]
+    # blockers: strips across B's top (along B's x axis), each filling its strip
+    halves = [hA, hB]
+    init = [[Axy[0], Axy[1], hA[2], rng.uniform(-math.pi, math.pi)], [Bxy[0], Bxy[1], hB[2], Byaw]]
+    c, s_ = math.cos(Byaw), math.sin(Byaw)
+    w = 2 * hB[0] / n_block
+    for i in range(n_block):
+        hb = np.array([w / 2 - 0.001, hB[1] - 0.001, rng.uniform(0.02, 0.03)])
+        lx = -hB[0] + w * (i + 0.5)
+        halves.append(hb)
+        init.append([Bxy[0] + c * lx, Bxy[1] + s_ * lx, topB + hb[2], Byaw])
+    half = np.array(halves)
+    box_init = np.array(init)
+    placed = [(np.zeros(2), 0.22), (Bxy, 0.16), (Axy, 0.06), (reg_xy, float(np.hypot(*reg_h)) + 0.02)]
+    n_obs = 16
+    obs_half = rng.uniform(0.05, 0.25, size=(n_obs, 3)) / 2.0
+    obs_xy = _scatter(rng, n_obs, lambda i: float(np.hypot(*obs_half[i, :2])) + 0.02, placed,
+                      lambda: _polar(rng, 0.3, 1.4))
+    obs_center = np.array([[q[0], q[1], obs_half[i, 2]] for i, q in enumerate(obs_xy)])
+    obs_rot = np.stack([_rz3(rng.uniform(-math.pi, math.pi)) for _ in range(n_obs)])
+    surf = np.array([[Bxy[0], Bxy[1], Byaw, hB[0], hB[1], topB],
+                     [reg_xy[0], reg_xy[1], rng.uniform(-math.pi, math.pi), reg_h[0], reg_h[1], 0.0]])
+    sc = Scene(**arm, box_half=half, box_init=box_init, box_spheres=np.stack([box_sphere_model(h) for h in half]),
+               obs_center=obs_center, obs_rot=obs_rot, obs_half=obs_half, surf=surf,
+               name=f"stacking-{n_block}blockers", seed=seed, meta=dict(n_blockers=n_block))
+    blockers = list(range(2, 2 + n_block))
+    skels = []
+    for k in range(0, min(3, n_block) + 1):
+        for order in itertools.permutations(blockers, k):
+            acts = []
+            for b in order:
+                acts += [(PICK, b, -1), (PLACE, b, 1)]
+            acts += [(PICK, 0, -1), (PLACE, 0, 0)]
+            skels.append(acts)
+    skels = skels[:16]
+    sizes = [int(v) for v in rng.choice([1024, 2048, 4096, 8192], size=len(skels))]
+    return sc, skels, sizes
+
+
 # ---------------------------------------------------------------- particle batches
 
 def layout(actions, n_joints: int):

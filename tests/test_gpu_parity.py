@@ -269,3 +269,70 @@ def test_batched_problem_matches_oracle(pkg):
     scene.close()
     J = pr.total_cost(torch.tensor(X.astype(np.float32).astype(np.float64))).numpy()
     assert cost_ok(q["cost"].astype(np.float64), J).all()
+
+
+def test_graph_replays_the_optimisation_loop(pkg):
+    """4 captured chunks of 5 fused iterations == 20 iterations of tamp_optimize_steps
+    (up to float-atomic reordering); the step count advances on the device."""
+    sc, acts = sg.plain_problem(1001)
+    X = sg.random_particles(sc, acts, 150, seed=21, spread=0.5).T.astype(np.float32)
+
+    def run(graph):
+        scene = pkg.Scene(sc)
+        pid = scene.set_skeleton(acts)
+        scene.set_particles(pid, X)
+        if graph:
+            g = pkg.Graph(scene, pid, 5, 4)
+            steps = g.run()
+            g.close()
+        else:
+            scene.optimize(pid, 20)
+            steps = 20
+        x, _, _, t = scene.get_particles(pid)
+        q = scene.query(pid, 150)
+        scene.close()
+        return x, t, steps, q
+
+    xg, tg, sg_, qg = run(True)
+    xo, to, _, qo = run(False)
+    assert sg_ == 20 and tg == 20 and to == 20
+    d = np.abs(xg - xo)
+    assert (d < 1e-4).mean() > 0.99
+    assert qg["first_iter"] == qo["first_iter"]
+
+
+def test_graph_stops_on_first_satisfying_particle(pkg):
+    from tests.test_oracle_pins import _scara_witness_scene
+    sc, acts, x = _scara_witness_scene()
+    scene = pkg.Scene(sc)
+    pid = scene.set_skeleton(acts)
+    scene.set_particles(pid, np.repeat(x.numpy(), 3, axis=0).T.astype(np.float32))
+    g = pkg.Graph(scene, pid, 5, 10, stop_on_first=True)
+    steps = g.run()
+    q = scene.query(pid, 3)
+    g.close()
+    scene.close()
+    assert steps == 5 and q["first_iter"] == 0
+
+
+def test_stacking_skeleton_parity(pkg):
+    """Obstructed stacking: blockers standing on B, A placed on B's top face."""
+    sc, skels, _ = sg.stacking_problem(3002)
+    acts = max(skels, key=len)
+    X = sg.random_particles(sc, acts, 70, seed=8)
+    compare_eval(Problem(sc, acts), X, *_eval(pkg, sc, acts, X), label="stacking")
+
+
+def test_stacking_searches_run_end_to_end(pkg):
+    from paper_2411_11833_b300.search import batched_search, sequential_search
+    sc, skels, sizes = sg.stacking_problem(3001)
+    small = [max(64, n // 32) for n in sizes]
+    scene = pkg.Scene(sc)
+    out = batched_search(scene, skels, small, steps_per_chunk=10, max_iterations=30, seed=1)
+    assert out["iterations"] in (10, 20, 30)
+    scene.close()
+    scene = pkg.Scene(sc)
+    out = sequential_search(scene, skels[:4], small[:4], steps_per_chunk=10, chunks_per_visit=1,
+                            max_iterations=20, seed=1)
+    assert out["solved"] or out["iterations"] == 4 * 20
+    scene.close()
