@@ -236,6 +236,50 @@ tamp_status tamp_work_counters(tamp_scene *scene, int problem_id, uint64_t out[2
 /* Text of the last error on this scene ("" if none); valid until the next call. */
 const char *tamp_last_error(const tamp_scene *scene);
 
+/* ---------------------------------------------------------------------------
+ * Learned particle proposals (Sec. V-A and Sec. VIII: particles may be seeded
+ * from learned samplers instead of uniformly).  The paper leaves the sampler
+ * open; this library provides one small conditional density network that runs
+ * on the tensor cores:
+ *   4 dense layers 48 -> 256 -> 256 -> 256 -> 32, exact GELU between layers;
+ *   weights and inter-layer activations BF16, products accumulated in FP32;
+ *   output k < 16 is the predicted mean of target k, output 16 + k its log
+ *   standard deviation; trained by Adam (beta 0.9 / 0.999, eps 1e-8) on FP32
+ *   master weights with the Gaussian negative log-likelihood
+ *     L = mean over rows of sum_k mask_k ((y_k - mu_k)^2 exp(-2 s_k) / 2 + s_k).
+ * Parameter vector (FP32, tamp_mlp_param_count() entries), in order:
+ *   W1 [256][48], b1 [256], W2 [256][256], b2 [256], W3 [256][256], b3 [256],
+ *   W4 [32][256], b4 [32]   (row-major; W maps inputs to outputs: z = W a + b).
+ * All batch arrays are device pointers, row-major: x [B][48], y and mask
+ * [B][16], out [B][32].  Every call is asynchronous on the network's stream
+ * unless it says it synchronises.  A tensor-core completion wait that gives up
+ * on the device makes the next synchronising call return TAMP_ERR_TIMEOUT.
+ * --------------------------------------------------------------------------- */
+typedef struct tamp_mlp tamp_mlp;   /* opaque, library-owned */
+
+/* Create a network with zero parameters on `device`, issuing work on `stream`
+ * (a cudaStream_t, NULL = legacy default); max_batch bounds the batch of the
+ * training calls (activations for max_batch rows are kept on the device). */
+tamp_status tamp_mlp_create(int device, void *stream, int max_batch, tamp_mlp **out);
+tamp_status tamp_mlp_destroy(tamp_mlp *net);
+int tamp_mlp_param_count(void);
+/* Host parameter vector in the layout above; set also resets Adam's moments
+ * and step count.  Both synchronise. */
+tamp_status tamp_mlp_set_params(tamp_mlp *net, const float *host_params, int count);
+tamp_status tamp_mlp_get_params(tamp_mlp *net, float *host_params, int count);
+/* out = network(x) for B >= 1 rows (any B; no training state is touched). */
+tamp_status tamp_mlp_forward(tamp_mlp *net, const float *x_dev, int B, float *out_dev);
+/* Gradient of L at the current parameters (1 <= B <= max_batch): grad_dev
+ * (device, param_count floats, may be NULL) and *loss (host, may be NULL).
+ * Synchronises. */
+tamp_status tamp_mlp_gradient(tamp_mlp *net, const float *x_dev, const float *y_dev, const float *mask_dev,
+                              int B, float *grad_dev, float *loss);
+/* One Adam step on L with learning rate lr.  *loss (host, may be NULL) gets the
+ * loss before the step; asking for it synchronises. */
+tamp_status tamp_mlp_train_step(tamp_mlp *net, const float *x_dev, const float *y_dev, const float *mask_dev,
+                                int B, float lr, float *loss);
+const char *tamp_mlp_last_error(const tamp_mlp *net);
+
 #ifdef __cplusplus
 }
 #endif

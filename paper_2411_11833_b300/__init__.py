@@ -253,3 +253,75 @@ def cost_fn():
             return gout[:, None] * grad, None, None
 
     return CostFn
+
+
+class Mlp:
+    """Proposal network on the tensor cores (tamp_mlp_*): 48 -> 256 -> 256 ->
+    256 -> 32, BF16 weights and activations, FP32 accumulation, Adam on FP32
+    master weights, Gaussian NLL.  Batches are float32 CUDA tensors, row-major."""
+
+    IN, OUT, NTGT = 48, 32, 16
+
+    def __init__(self, max_batch: int, device: int = 0, stream=None):
+        lib = _native.load()
+        self._lib = lib
+        torch = _torch()
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        h = ctypes.c_void_p()
+        st = lib.tamp_mlp_create(int(device), ctypes.c_void_p(stream), int(max_batch), ctypes.byref(h))
+        if st != 0:
+            raise TampError(st, "tamp_mlp_create failed")
+        self._h = h
+        self.device = device
+        self.max_batch = int(max_batch)
+        self.n_params = int(lib.tamp_mlp_param_count())
+
+    def _check(self, st):
+        if st != 0:
+            raise TampError(st, self._lib.tamp_mlp_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.tamp_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        a = np.ascontiguousarray(np.asarray(theta, dtype=np.float32))
+        self._check(self._lib.tamp_mlp_set_params(self._h, ctypes.c_void_p(a.ctypes.data), int(a.size)))
+
+    def get_params(self) -> np.ndarray:
+        a = np.zeros(self.n_params, np.float32)
+        self._check(self._lib.tamp_mlp_get_params(self._h, ctypes.c_void_p(a.ctypes.data), int(a.size)))
+        return a
+
+    def forward(self, x):
+        torch = _torch()
+        x = x.contiguous()
+        out = torch.empty(x.shape[0], self.OUT, dtype=torch.float32, device=x.device)
+        self._check(self._lib.tamp_mlp_forward(self._h, ctypes.c_void_p(x.data_ptr()), int(x.shape[0]),
+                                               ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def gradient(self, x, y, mask):
+        torch = _torch()
+        x, y, mask = x.contiguous(), y.contiguous(), mask.contiguous()
+        g = torch.empty(self.n_params, dtype=torch.float32, device=x.device)
+        loss = ctypes.c_float()
+        self._check(self._lib.tamp_mlp_gradient(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                                ctypes.c_void_p(mask.data_ptr()), int(x.shape[0]),
+                                                ctypes.c_void_p(g.data_ptr()), ctypes.byref(loss)))
+        return loss.value, g
+
+    def train_step(self, x, y, mask, lr: float, want_loss: bool = True):
+        loss = ctypes.c_float()
+        self._check(self._lib.tamp_mlp_train_step(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                                  ctypes.c_void_p(mask.data_ptr()), int(x.shape[0]), float(lr),
+                                                  ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None

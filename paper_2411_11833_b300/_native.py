@@ -69,6 +69,17 @@ SIGNATURES = {
     "tamp_graph_run": (ctypes.c_int, [ctypes.c_void_p, c_int_p]),
     "tamp_graph_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "tamp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "tamp_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "tamp_mlp_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "tamp_mlp_param_count": (ctypes.c_int, []),
+    "tamp_mlp_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "tamp_mlp_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "tamp_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "tamp_mlp_gradient": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int, ctypes.c_void_p, c_float_p]),
+    "tamp_mlp_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int, ctypes.c_float, c_float_p]),
+    "tamp_mlp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
 }
 
 STATUS = {0: "TAMP_OK", 1: "TAMP_ERR_INVALID_ARG", 2: "TAMP_ERR_STATE", 3: "TAMP_ERR_OOM",

@@ -6,7 +6,7 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SOURCES = [os.path.join(HERE, "csrc", f) for f in ("tamp_kernels.cu", "tamp_api.cu")]
+SOURCES = [os.path.join(HERE, "csrc", f) for f in ("tamp_kernels.cu", "tamp_api.cu", "tamp_mlp.cu")]
 HEADERS = [os.path.join(HERE, "csrc", "tamp_dev.cuh"), os.path.join(ROOT, "include", "tamp.h")]
 OUT = os.path.join(HERE, "lib", "libtamp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

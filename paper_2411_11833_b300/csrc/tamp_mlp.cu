@@ -1,0 +1,609 @@
+// Proposal network kernels: BF16 tensor-core GEMMs on sm_103a (tcgen05 + TMEM)
+// with FP32 accumulation, for inference and training.
+//
+// The network: 4 dense layers IN -> H -> H -> H -> OUT (48, 256, 256, 256, 32),
+// exact GELU between layers, weights and inter-layer activations in BF16,
+// accumulation in FP32; output k < 16 is the mean of target k, output 16 + k its
+// log standard deviation, trained with the Gaussian negative log-likelihood.
+//
+// Every product is one tile GEMM D[128 x N] = A[128 x K] . B[N x K]^T: the CTA's
+// threads stage A and B into shared memory in the canonical K-major layout
+// without swizzle (8 x 16-byte core matrices: 128 B apart along K, 256 B apart
+// per group of 8 rows, K in chunks of 16), one thread issues K/16
+// tcgen05.mma instructions into a tensor-memory accumulator and commits them to
+// an mbarrier, and every thread reads back its own row with tcgen05.ld.  A
+// transposed operand is just staged transposed, so the backward pass (dA = dZ W,
+// dW = dZ^T A) uses the same instruction forms as the forward pass.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tamp.h"
+
+namespace mlpk {
+
+constexpr int IN = 48, H = 256, OUT = 32, NTGT = 16;
+constexpr int ROWS = 128;    // samples per CTA tile = MMA M
+constexpr int THREADS = 128; // one warpgroup: thread t owns tile row / TMEM lane t
+constexpr int TMEM_COLS = 256;
+constexpr size_t SMEM_A = 128 * 256 * 2;   // largest A operand (128 x 256 bf16)
+constexpr size_t SMEM_B = 256 * 256 * 2;   // largest B operand (256 x 256 bf16)
+constexpr size_t SMEM_BYTES = SMEM_A + SMEM_B;
+__host__ __device__ constexpr int kdim(int l) { return l == 0 ? IN : H; }  // inputs of layer l
+__host__ __device__ constexpr int ndim(int l) { return l == 3 ? OUT : H; } // outputs of layer l
+enum { ERR_WAIT = 1 };
+
+__host__ __device__ constexpr size_t w_off(int l) {
+  return l == 0 ? 0 : (l == 1 ? (size_t)H * IN + H : (l == 2 ? (size_t)H * IN + H + H * H + H : (size_t)H * IN + H + 2 * ((size_t)H * H + H)));
+}
+__host__ __device__ constexpr size_t b_off(int l) { return w_off(l) + (size_t)ndim(l) * kdim(l); }
+constexpr size_t N_PARAMS = w_off(3) + (size_t)OUT * H + OUT;
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (int i = 0; i < (1 << 22); ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    __nanosleep(32);
+  }
+  return false;
+}
+// tensor memory: allocated and freed by one whole warp
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(TMEM_COLS)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TMEM_COLS) : "memory");
+}
+// shared-memory matrix descriptor: K-major, no swizzle, LBO 128 B (next core
+// matrix along K), SBO 256 B (next group of 8 rows), descriptor version 1
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) | (static_cast<uint64_t>(128 >> 4) << 16) |
+         (static_cast<uint64_t>(256 >> 4) << 32) | (1ull << 46);
+}
+// instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t u[32];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+               : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]), "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]), "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
+               : "r"(taddr)
+               : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(u[i]);
+}
+
+// ------------------------------------------------------------------ tile GEMM
+// byte offset of element (r, k) of an R-row operand in the staged layout
+__device__ __forceinline__ uint32_t blk_off(int r, int k, int R) {
+  return static_cast<uint32_t>((k >> 4) * (R * 32) + (r >> 3) * 256 + ((k >> 3) & 1) * 128 + (r & 7) * 16 +
+                               (k & 7) * 2);
+}
+__device__ __forceinline__ float ld_f(const float* p) { return *p; }
+__device__ __forceinline__ float ld_f(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+// Stage an R x K operand (element (r, k) = src[r * rs + k * ks], zero outside
+// rows < Rv and columns < Kv) as BF16 in the K-major layout.
+template <typename T>
+__device__ void stage(unsigned char* dst, int R, int K, const T* src, long rs, long ks, int Rv, int Kv) {
+  for (int i = threadIdx.x; i < R * K; i += blockDim.x) {
+    const int r = i / K, k = i % K;
+    float v = 0.f;
+    if (r < Rv && k < Kv) v = ld_f(src + r * rs + k * ks);
+    *reinterpret_cast<__nv_bfloat16*>(dst + blk_off(r, k, R)) = __float2bfloat16_rn(v);
+  }
+}
+
+// D[128 x N] = A[128 x K] . B[N x K]^T into tensor memory; every thread calls
+// it; on return the accumulator is complete (or *err has ERR_WAIT set).
+__device__ bool gemm_tile(uint32_t tmem, const unsigned char* A, const unsigned char* B, int N, int K,
+                          uint64_t* bar, uint32_t& phase, int* err) {
+  fence_proxy_async();  // the staged operands, written by every thread, to the tensor core
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc_fence_after();
+    const uint32_t a0 = smem_u32(A), b0 = smem_u32(B), id = instr_desc(ROWS, N);
+    for (int c = 0; c < K / 16; ++c)
+      umma_bf16(tmem, smem_desc(a0 + c * ROWS * 32), smem_desc(b0 + c * N * 32), id, c > 0 ? 1u : 0u);
+    umma_commit(bar);
+  }
+  const bool ok = mbar_wait_bounded(bar, phase);
+  phase ^= 1u;
+  if (!ok) atomicOr(err, ERR_WAIT);
+  tc_fence_after();
+  return __syncthreads_and(ok) != 0;
+}
+
+__device__ __forceinline__ uint32_t lane_addr(uint32_t tmem, int col) {
+  return tmem + (static_cast<uint32_t>(threadIdx.x & ~31) << 16) + static_cast<uint32_t>(col);
+}
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+  return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+// ------------------------------------------------------------------ forward
+struct FwdArgs {
+  const float* x; int B;              // inputs [B][IN]
+  const __nv_bfloat16* W[4]; const float* b[4];
+  float* out;                         // [B][OUT]
+  float* Z[3]; __nv_bfloat16* A[3];   // training: pre-activations (FP32) and activations (BF16), [B][H]
+  int* err;
+};
+
+__global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* opA = smem;
+  unsigned char* opB = smem + SMEM_A;
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tslot;
+  const int t = threadIdx.x, row0 = blockIdx.x * ROWS, r = row0 + t;
+  const int Rv = min(ROWS, a.B - row0);
+  if (t == 0) mbar_init(&bar);
+  if (t < 32) tmem_alloc(&tslot);
+  stage(opA, ROWS, IN, a.x + static_cast<long>(row0) * IN, IN, 1, Rv, IN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tslot;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int l = 0; l < 4 && ok; ++l) {
+    const int K = kdim(l), N = ndim(l);
+    stage(opB, N, K, a.W[l], K, 1, N, K);
+    ok = gemm_tile(tmem, opA, opB, N, K, &bar, phase, a.err);
+    if (!ok) break;
+    for (int c0 = 0; c0 < N; c0 += 32) {
+      float v[32];
+      tmem_ld32(lane_addr(tmem, c0), v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int c = c0 + j;
+        const float z = v[j] + a.b[l][c];
+        if (l < 3) {
+          const __nv_bfloat16 h = __float2bfloat16_rn(gelu(z));
+          *reinterpret_cast<__nv_bfloat16*>(opA + blk_off(t, c, ROWS)) = h;
+          if (a.Z[l] && r < a.B) {
+            a.Z[l][static_cast<long>(r) * H + c] = z;
+            a.A[l][static_cast<long>(r) * H + c] = h;
+          }
+        } else if (r < a.B) {
+          a.out[static_cast<long>(r) * OUT + c] = z;
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();  // every row's activations staged; accumulator free for the next layer
+    tc_fence_after();
+  }
+  if (t < 32) tmem_dealloc(tmem);
+}
+
+// ------------------------------------------------------------------ loss
+// Gaussian NLL per row: sum over masked k of (y - mu)^2 exp(-2 s) / 2 + s,
+// mean over rows; dOut = d(mean)/d(out).
+__global__ void mlp_loss_kernel(const float* out, const float* y, const float* mask, int B, float* dout,
+                                float* loss_sum) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  float l = 0.f;
+  if (r < B) {
+    const float inv = 1.f / static_cast<float>(B);
+    for (int k = 0; k < NTGT; ++k) {
+      const float mu = out[static_cast<long>(r) * OUT + k], s = out[static_cast<long>(r) * OUT + NTGT + k];
+      const float m = mask[static_cast<long>(r) * NTGT + k], d = y[static_cast<long>(r) * NTGT + k] - mu;
+      const float e = expf(-2.f * s);
+      l += m * (0.5f * d * d * e + s);
+      dout[static_cast<long>(r) * OUT + k] = m * (-d * e) * inv;
+      dout[static_cast<long>(r) * OUT + NTGT + k] = m * (1.f - d * d * e) * inv;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if ((threadIdx.x & 31) == 0 && l != 0.f) atomicAdd(loss_sum, l / static_cast<float>(B));
+}
+
+// ------------------------------------------------------------------ backward
+struct BwdArgs {
+  const float* x; int B;
+  const __nv_bfloat16* W[4];
+  const float* Z[3]; const __nv_bfloat16* A[3];
+  const float* dout;                  // [B][OUT]
+  __nv_bfloat16* dz[2];               // [B][H] scratch, ping-pong between layers
+  float* grad;                        // [N_PARAMS] accumulated (weights then bias per layer)
+  int* err;
+};
+
+// Per 128-row tile, layer l = 3 .. 0:
+//   dW_l = dZ_l^T A_{l-1} (A_{-1} = x), reduced over the tile's rows by the
+//   tensor core (rows are the GEMM's K) and added to the global gradient;
+//   db_l = column sums of dZ_l;
+//   dZ_{l-1} = (dZ_l W_l) * gelu'(Z_{l-1}).
+__global__ void __launch_bounds__(THREADS, 1) mlp_backward_kernel(BwdArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* opA = smem;
+  unsigned char* opB = smem + SMEM_A;
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tslot;
+  const int t = threadIdx.x, row0 = blockIdx.x * ROWS, r = row0 + t;
+  const int Rv = min(ROWS, a.B - row0);
+  if (t == 0) mbar_init(&bar);
+  if (t < 32) tmem_alloc(&tslot);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tslot;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int l = 3; l >= 0 && ok; --l) {
+    const int K = kdim(l), N = ndim(l);
+    // dZ_l source: the loss gradient (FP32) for the output layer, else the
+    // previous layer's BF16 result
+    const float* dzf = l == 3 ? a.dout + static_cast<long>(row0) * OUT : nullptr;
+    const __nv_bfloat16* dzb = l == 3 ? nullptr : a.dz[l & 1] + static_cast<long>(row0) * H;
+    const long dzs = l == 3 ? OUT : H;
+    float* gW = a.grad + w_off(l);
+    float* gb = a.grad + b_off(l);
+    // ---- bias: column sums over the tile's rows
+    for (int n = t; n < N; n += THREADS) {
+      float s = 0.f;
+      for (int i = 0; i < Rv; ++i) s += dzf ? dzf[i * dzs + n] : __bfloat162float(dzb[i * dzs + n]);
+      atomicAdd(&gb[n], s);
+    }
+    // ---- weights: tiles of 128 along the wider of (outputs, inputs)
+    if (N >= ROWS) {
+      // dW[n][k]: M = outputs (128 per tile), N' = inputs, K' = rows
+      for (int n0 = 0; n0 < N && ok; n0 += ROWS) {
+        if (dzf) stage(opA, ROWS, ROWS, dzf + n0, 1, dzs, N - n0, Rv);
+        else stage(opA, ROWS, ROWS, dzb + n0, 1, dzs, N - n0, Rv);
+        if (l == 0) stage(opB, K, ROWS, a.x + static_cast<long>(row0) * IN, 1, IN, K, Rv);
+        else stage(opB, K, ROWS, a.A[l - 1] + static_cast<long>(row0) * H, 1, H, K, Rv);
+        ok = gemm_tile(tmem, opA, opB, K, ROWS, &bar, phase, a.err);
+        if (!ok) break;
+        for (int c0 = 0; c0 < K; c0 += 32) {
+          float v[32];
+          tmem_ld32(lane_addr(tmem, c0), v);
+#pragma unroll
+          for (int j = 0; j < 32; ++j)  // K = 48 for the first layer: the last group is half empty
+            if (n0 + t < N && c0 + j < K) atomicAdd(&gW[static_cast<long>(n0 + t) * K + c0 + j], v[j]);
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+      }
+    } else {
+      // dW^T[k][n]: M = inputs (128 per tile), N' = outputs, K' = rows
+      for (int k0 = 0; k0 < K && ok; k0 += ROWS) {
+        stage(opA, ROWS, ROWS, a.A[l - 1] + static_cast<long>(row0) * H + k0, 1, H, K - k0, Rv);
+        if (dzf) stage(opB, N, ROWS, dzf, 1, dzs, N, Rv);
+        else stage(opB, N, ROWS, dzb, 1, dzs, N, Rv);
+        ok = gemm_tile(tmem, opA, opB, N, ROWS, &bar, phase, a.err);
+        if (!ok) break;
+        for (int c0 = 0; c0 < N; c0 += 32) {
+          float v[32];
+          tmem_ld32(lane_addr(tmem, c0), v);
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (k0 + t < K) atomicAdd(&gW[static_cast<long>(c0 + j) * K + k0 + t], v[j]);
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+      }
+    }
+    if (l == 0 || !ok) break;
+    // ---- dA_{l-1} = dZ_l W_l: M = rows, N' = K (inputs of layer l), K' = N (outputs)
+    if (dzf) stage(opA, ROWS, N, dzf, dzs, 1, Rv, N);
+    else stage(opA, ROWS, N, dzb, dzs, 1, Rv, N);
+    stage(opB, K, N, a.W[l], 1, K, K, N);
+    ok = gemm_tile(tmem, opA, opB, K, N, &bar, phase, a.err);
+    if (!ok) break;
+    __nv_bfloat16* dzo = a.dz[(l - 1) & 1] + static_cast<long>(row0) * H;
+    for (int c0 = 0; c0 < K; c0 += 32) {
+      float v[32];
+      tmem_ld32(lane_addr(tmem, c0), v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (r < a.B) {
+          const int c = c0 + j;
+          dzo[t * H + c] = __float2bfloat16_rn(v[j] * gelu_grad(a.Z[l - 1][static_cast<long>(r) * H + c]));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();  // dZ_{l-1} written (global) before the next layer stages it
+    tc_fence_after();
+  }
+  if (t < 32) tmem_dealloc(tmem);
+}
+
+// ------------------------------------------------------------------ Adam on the FP32 master weights
+__global__ void mlp_adam_kernel(float* p, const float* g, float* m, float* v, __nv_bfloat16* wb, int n, float lr,
+                                float b1, float b2, float eps, float ib1, float ib2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = fmaf(b1, m[i], (1.f - b1) * gi), vi = fmaf(b2, v[i], (1.f - b2) * gi * gi);
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi * ib1) / (sqrtf(vi * ib2) + eps);
+  wb[i] = __float2bfloat16_rn(p[i]);
+}
+
+__global__ void to_bf16_kernel(const float* p, __nv_bfloat16* wb, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) wb[i] = __float2bfloat16_rn(p[i]);
+}
+
+}  // namespace mlpk
+
+using namespace mlpk;
+
+struct tamp_mlp {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int max_batch = 0;
+  float* params = nullptr;     // FP32 master
+  __nv_bfloat16* wb = nullptr; // BF16 copy (same layout; the kernels read the weight blocks)
+  float* grad = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  float* Z = nullptr;          // [3][max_batch][H]
+  __nv_bfloat16* A = nullptr;  // [3][max_batch][H]
+  __nv_bfloat16* dz = nullptr; // [2][max_batch][H]
+  float* out = nullptr;        // [max_batch][OUT]
+  float* dout = nullptr;       // [max_batch][OUT]
+  float* loss = nullptr;
+  int* err = nullptr;
+  long step = 0;
+  std::string last_error;
+};
+
+namespace {
+tamp_status mfail(tamp_mlp* n, tamp_status st, const std::string& msg) {
+  if (n) n->last_error = msg;
+  return st;
+}
+#define MLP_TRY(n, call)                                                                          \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess)                                                                        \
+      return mfail((n), e_ == cudaErrorMemoryAllocation ? TAMP_ERR_OOM : TAMP_ERR_CUDA,          \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));                          \
+  } while (0)
+
+struct Dev {
+  int prev = -1;
+  explicit Dev(int d) {
+    cudaGetDevice(&prev);
+    if (prev != d) cudaSetDevice(d);
+  }
+  ~Dev() {
+    int c;
+    cudaGetDevice(&c);
+    if (prev >= 0 && c != prev) cudaSetDevice(prev);
+  }
+};
+
+cudaError_t enable_smem(int device) {
+  static unsigned long long done = 0;  // one bit per device ordinal < 64
+  const unsigned long long bit = device < 64 ? 1ull << device : 0;
+  if (done & bit) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(SMEM_BYTES));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(SMEM_BYTES));
+  if (e == cudaSuccess) done |= bit;
+  return e;
+}
+
+FwdArgs fwd_args(tamp_mlp* n, const float* x, int B, float* out, bool train) {
+  FwdArgs a{};
+  a.x = x; a.B = B; a.out = out; a.err = n->err;
+  for (int l = 0; l < 4; ++l) {
+    a.W[l] = n->wb + w_off(l);
+    a.b[l] = n->params + b_off(l);
+  }
+  for (int l = 0; l < 3; ++l) {
+    a.Z[l] = train ? n->Z + static_cast<size_t>(l) * n->max_batch * H : nullptr;
+    a.A[l] = train ? n->A + static_cast<size_t>(l) * n->max_batch * H : nullptr;
+  }
+  return a;
+}
+
+tamp_status check_err(tamp_mlp* n) {
+  int e = 0;
+  MLP_TRY(n, cudaMemcpyAsync(&e, n->err, 4, cudaMemcpyDeviceToHost, n->stream));
+  MLP_TRY(n, cudaStreamSynchronize(n->stream));
+  if (e) return mfail(n, TAMP_ERR_TIMEOUT, "a tensor-core completion wait timed out on the device");
+  return TAMP_OK;
+}
+
+// forward (training form) + loss + backward into n->grad
+tamp_status gradient(tamp_mlp* n, const float* x, const float* y, const float* mask, int B) {
+  MLP_TRY(n, enable_smem(n->device));
+  const int tiles = (B + ROWS - 1) / ROWS;
+  MLP_TRY(n, cudaMemsetAsync(n->grad, 0, N_PARAMS * 4, n->stream));
+  MLP_TRY(n, cudaMemsetAsync(n->loss, 0, 4, n->stream));
+  mlp_forward_kernel<<<tiles, THREADS, SMEM_BYTES, n->stream>>>(fwd_args(n, x, B, n->out, true));
+  MLP_TRY(n, cudaGetLastError());
+  mlp_loss_kernel<<<(B + 255) / 256, 256, 0, n->stream>>>(n->out, y, mask, B, n->dout, n->loss);
+  MLP_TRY(n, cudaGetLastError());
+  BwdArgs b{};
+  b.x = x; b.B = B; b.dout = n->dout; b.grad = n->grad; b.err = n->err;
+  for (int l = 0; l < 4; ++l) b.W[l] = n->wb + w_off(l);
+  for (int l = 0; l < 3; ++l) {
+    b.Z[l] = n->Z + static_cast<size_t>(l) * n->max_batch * H;
+    b.A[l] = n->A + static_cast<size_t>(l) * n->max_batch * H;
+  }
+  b.dz[0] = n->dz;
+  b.dz[1] = n->dz + static_cast<size_t>(n->max_batch) * H;
+  mlp_backward_kernel<<<tiles, THREADS, SMEM_BYTES, n->stream>>>(b);
+  MLP_TRY(n, cudaGetLastError());
+  return TAMP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+tamp_status tamp_mlp_create(int device, void* stream, int max_batch, tamp_mlp** out) {
+  if (!out || max_batch <= 0 || max_batch > (1 << 22)) return TAMP_ERR_INVALID_ARG;
+  *out = nullptr;
+  tamp_mlp* n = new tamp_mlp();
+  n->device = device;
+  n->stream = static_cast<cudaStream_t>(stream);
+  n->max_batch = max_batch;
+  Dev g(device);
+  const size_t mb = static_cast<size_t>(max_batch);
+  cudaError_t e = cudaMalloc(&n->params, N_PARAMS * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&n->wb, N_PARAMS * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&n->grad, N_PARAMS * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&n->m, N_PARAMS * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&n->v, N_PARAMS * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&n->Z, 3 * mb * H * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&n->A, 3 * mb * H * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&n->dz, 2 * mb * H * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&n->out, mb * OUT * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&n->dout, mb * OUT * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&n->loss, 4);
+  if (e == cudaSuccess) e = cudaMalloc(&n->err, 4);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->params, 0, N_PARAMS * 4, n->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->wb, 0, N_PARAMS * 2, n->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->m, 0, N_PARAMS * 4, n->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->v, 0, N_PARAMS * 4, n->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->err, 0, 4, n->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+  if (e != cudaSuccess) {
+    tamp_mlp_destroy(n);
+    return e == cudaErrorMemoryAllocation ? TAMP_ERR_OOM : TAMP_ERR_CUDA;
+  }
+  *out = n;
+  return TAMP_OK;
+}
+
+tamp_status tamp_mlp_destroy(tamp_mlp* n) {
+  if (!n) return TAMP_ERR_INVALID_ARG;
+  Dev g(n->device);
+  cudaStreamSynchronize(n->stream);
+  cudaFree(n->params); cudaFree(n->wb); cudaFree(n->grad); cudaFree(n->m); cudaFree(n->v);
+  cudaFree(n->Z); cudaFree(n->A); cudaFree(n->dz); cudaFree(n->out); cudaFree(n->dout);
+  cudaFree(n->loss); cudaFree(n->err);
+  delete n;
+  return TAMP_OK;
+}
+
+int tamp_mlp_param_count(void) { return static_cast<int>(N_PARAMS); }
+
+tamp_status tamp_mlp_set_params(tamp_mlp* n, const float* host, int count) {
+  if (!n) return TAMP_ERR_INVALID_ARG;
+  if (!host || count != static_cast<int>(N_PARAMS)) return mfail(n, TAMP_ERR_INVALID_ARG, "parameter count");
+  Dev g(n->device);
+  MLP_TRY(n, cudaMemcpyAsync(n->params, host, N_PARAMS * 4, cudaMemcpyHostToDevice, n->stream));
+  to_bf16_kernel<<<static_cast<int>((N_PARAMS + 255) / 256), 256, 0, n->stream>>>(n->params, n->wb,
+                                                                                 static_cast<int>(N_PARAMS));
+  MLP_TRY(n, cudaGetLastError());
+  MLP_TRY(n, cudaMemsetAsync(n->m, 0, N_PARAMS * 4, n->stream));
+  MLP_TRY(n, cudaMemsetAsync(n->v, 0, N_PARAMS * 4, n->stream));
+  n->step = 0;
+  MLP_TRY(n, cudaStreamSynchronize(n->stream));
+  return TAMP_OK;
+}
+
+tamp_status tamp_mlp_get_params(tamp_mlp* n, float* host, int count) {
+  if (!n) return TAMP_ERR_INVALID_ARG;
+  if (!host || count != static_cast<int>(N_PARAMS)) return mfail(n, TAMP_ERR_INVALID_ARG, "parameter count");
+  Dev g(n->device);
+  MLP_TRY(n, cudaMemcpyAsync(host, n->params, N_PARAMS * 4, cudaMemcpyDeviceToHost, n->stream));
+  MLP_TRY(n, cudaStreamSynchronize(n->stream));
+  return TAMP_OK;
+}
+
+tamp_status tamp_mlp_forward(tamp_mlp* n, const float* x_dev, int B, float* out_dev) {
+  if (!n) return TAMP_ERR_INVALID_ARG;
+  if (!x_dev || !out_dev || B <= 0) return mfail(n, TAMP_ERR_INVALID_ARG, "bad forward arguments");
+  Dev g(n->device);
+  MLP_TRY(n, enable_smem(n->device));
+  mlp_forward_kernel<<<(B + ROWS - 1) / ROWS, THREADS, SMEM_BYTES, n->stream>>>(fwd_args(n, x_dev, B, out_dev, false));
+  MLP_TRY(n, cudaGetLastError());
+  return TAMP_OK;
+}
+
+tamp_status tamp_mlp_gradient(tamp_mlp* n, const float* x, const float* y, const float* mask, int B,
+                              float* grad_dev, float* loss) {
+  if (!n) return TAMP_ERR_INVALID_ARG;
+  if (!x || !y || !mask || B <= 0 || B > n->max_batch) return mfail(n, TAMP_ERR_INVALID_ARG, "bad batch");
+  Dev g(n->device);
+  tamp_status st = gradient(n, x, y, mask, B);
+  if (st != TAMP_OK) return st;
+  if (grad_dev) MLP_TRY(n, cudaMemcpyAsync(grad_dev, n->grad, N_PARAMS * 4, cudaMemcpyDeviceToDevice, n->stream));
+  if (loss) MLP_TRY(n, cudaMemcpyAsync(loss, n->loss, 4, cudaMemcpyDeviceToHost, n->stream));
+  return check_err(n);
+}
+
+tamp_status tamp_mlp_train_step(tamp_mlp* n, const float* x, const float* y, const float* mask, int B, float lr,
+                                float* loss) {
+  if (!n) return TAMP_ERR_INVALID_ARG;
+  if (!x || !y || !mask || B <= 0 || B > n->max_batch || !(lr >= 0.f)) return mfail(n, TAMP_ERR_INVALID_ARG, "bad batch");
+  Dev g(n->device);
+  tamp_status st = gradient(n, x, y, mask, B);
+  if (st != TAMP_OK) return st;
+  ++n->step;
+  const double b1 = 0.9, b2 = 0.999;
+  const float ib1 = static_cast<float>(1.0 / (1.0 - std::pow(b1, static_cast<double>(n->step))));
+  const float ib2 = static_cast<float>(1.0 / (1.0 - std::pow(b2, static_cast<double>(n->step))));
+  mlp_adam_kernel<<<static_cast<int>((N_PARAMS + 255) / 256), 256, 0, n->stream>>>(
+      n->params, n->grad, n->m, n->v, n->wb, static_cast<int>(N_PARAMS), lr, 0.9f, 0.999f, 1e-8f, ib1, ib2);
+  MLP_TRY(n, cudaGetLastError());
+  if (loss) {
+    MLP_TRY(n, cudaMemcpyAsync(loss, n->loss, 4, cudaMemcpyDeviceToHost, n->stream));
+    return check_err(n);
+  }
+  return TAMP_OK;
+}
+
+const char* tamp_mlp_last_error(const tamp_mlp* n) { return n ? n->last_error.c_str() : "null network"; }
+
+}  // extern "C"
