@@ -144,11 +144,16 @@ def _scatter(rng, n, radius_of, placed, sampler, tries=2000):
 
 def make_scene(seed: int, n_boxes: int, n_obs: int, region_size, spheres_per_link=5,
                n_joints: int = 7, name: str = "", region_radius: float = 0.55,
-               box_radius=(0.40, 0.85), obs_radius=(0.30, 1.15), obs_edges=(0.05, 0.30)):
+               box_radius=(0.40, 0.85), obs_radius=(0.30, 1.15), obs_edges=(0.05, 0.30),
+               arm_seed: int | None = None):
     """Pick-and-place scene: arm, ``n_boxes`` boxes on the table, ``n_obs`` cuboids,
-    one rectangular target region (surface 0) on the table."""
+    one rectangular target region (surface 0) on the table.  ``arm_seed`` fixes
+    the arm independently of the rest of the scene (one robot, many scenes)."""
     rng = np.random.default_rng(seed)
-    arm = random_arm(rng, n_joints, spheres_per_link)
+    if arm_seed is None:
+        arm = random_arm(rng, n_joints, spheres_per_link)
+    else:
+        arm = random_arm(np.random.default_rng(arm_seed), n_joints, spheres_per_link)
     half = rng.uniform(0.04, 0.10, size=(n_boxes, 3)) / 2.0
     reg_ang = rng.uniform(-math.pi, math.pi)
     reg_c = region_radius * np.array([math.cos(reg_ang), math.sin(reg_ang)])
@@ -190,6 +195,20 @@ def plain_problem(seed: int = 1001):
     return sc, pick_place_skeleton([0])
 
 
+def robot_plain_problem(seed: int, arm_seed: int = 4000):
+    """The plain Pick-Place problem with one fixed arm across seeds: the scenes
+    a learned proposal network for that robot trains and is tested on."""
+    sc = make_scene(seed, n_boxes=1, n_obs=4, region_size=(0.6, 0.4), name="plain-1box-robot", arm_seed=arm_seed)
+    return sc, pick_place_skeleton([0])
+
+
+def robot_packing_problem(seed: int, arm_seed: int = 4000, n_boxes: int = 6):
+    """The packing problem with the same fixed arm."""
+    sc = make_scene(seed, n_boxes=n_boxes, n_obs=8, region_size=(0.3, 0.3), name="packing-robot",
+                    arm_seed=arm_seed)
+    return sc, pick_place_skeleton(range(n_boxes), goal=True)
+
+
 def packing_problem(seed: int = 2001):
     """Six boxes packed into a 0.3 x 0.3 m region minimising the sum of pairwise
     centre distances, 8 cuboids, 6 Pick-Place pairs + goal (D = 126)."""
@@ -206,7 +225,7 @@ def stress_problem(seed: int = 5001):
     return sc, pick_place_skeleton(range(12), goal=True)
 
 
-def stacking_problem(seed: int = 3001):
+def stacking_problem(seed: int = 3001, arm_seed: int | None = None):
     """Obstructed stacking: box A must go on box B, whose top face is fully
     covered by 2-4 blockers.  Surface 0 is B's top face, surface 1 a table
     region for the blockers; 16 static cuboids.  Returns (scene, skeletons,
@@ -216,6 +235,8 @@ def stacking_problem(seed: int = 3001):
     import itertools
     rng = np.random.default_rng(seed)
     arm = random_arm(rng)
+    if arm_seed is not None:
+        arm = random_arm(np.random.default_rng(arm_seed))
     n_block = int(rng.integers(2, 5))
     hB = np.array([0.07, 0.07, 0.03])                      # B: 14 x 14 x 6 cm
     hA = rng.uniform(0.022, 0.03, 3)
