@@ -142,6 +142,18 @@ tamp_status tamp_set_skeleton(tamp_scene *scene, const tamp_action *actions, int
 tamp_status tamp_problem_info(const tamp_scene *scene, int problem_id, int *D, int *n_terms,
                               int *term_kinds);
 
+/* Sampler flags of tamp_sample_particles (combine with |). */
+enum {
+  TAMP_SAMPLE_UNIFORM = 0,   /* every component uniform within its bounds                 */
+  TAMP_SAMPLE_LEARNED = 1,   /* grasps and placements from the attached proposal network  */
+  TAMP_SAMPLE_IK = 2         /* joint configurations by parallel IK on the sampled targets */
+};
+/* Parameters of the IK configuration sampler: iterations, damping lambda, the
+ * largest entry of one step (rad). */
+#define TAMP_IK_ITERS 64
+#define TAMP_IK_DAMPING 0.05f
+#define TAMP_IK_MAX_STEP 0.4f
+
 /* Initialise a batch of n_particles (InitializeParticles, Alg. 1).  sampler 0:
  * uniform within bounds (the paper's "Optimization" initialisation, Sec. VIII):
  * component c of particle i takes u = (w >> 8) * 2^-24 where w is the first
@@ -149,7 +161,28 @@ tamp_status tamp_problem_info(const tamp_scene *scene, int problem_id, int *D, i
  * and key (seed & 0xffffffff, seed >> 32); joints map u onto [q_lo, q_hi],
  * grasp positions onto [-h_x, h_x] x [-h_y, h_y] x [h_z - 0.02, h_z], yaws onto
  * [-pi, pi), a placement's (x, y) onto the surface rectangle in the surface
- * frame.  Adam state and the iteration counter are reset. */
+ * frame.  sampler is a combination of the TAMP_SAMPLE_* flags, applied in
+ * this order:
+ * TAMP_SAMPLE_LEARNED (learned proposals, Sec. V-A; needs tamp_set_proposal):
+ * joint configurations as sampler 0; the attached network maps each Pick /
+ * Place row's features (tamp_proposal_rows) to means mu_k and log standard
+ * deviations s_k of the row's target slots, and slot k of row r of particle i
+ * takes t = mu_k + exp(clamp(s_k, -8, 3)) xi with xi = sqrt(-2 ln u1)
+ * cos(2 pi u2), u1 = ((w0 >> 8) + 1) 2^-24, u2 = (w1 >> 8) 2^-24 from the
+ * Philox4x32-10 words w0, w1 at counter (i, 16 r + k, 1, 0); positions are
+ * clamped to [-1, 1] and mapped back through the target normalisation, yaws
+ * are atan2(sin slot, cos slot); without a network the flag returns
+ * TAMP_ERR_STATE.
+ * TAMP_SAMPLE_IK (the conditional configuration sampler of Sec. VI): every
+ * configuration, in skeleton order, gets the joint positions that put the end
+ * effector on its Kin target P_box G(g) given the sampled grasp / placement,
+ * with one free yaw -- a Pick's grasp yaw, a Place's placement yaw -- solved
+ * along: TAMP_IK_ITERS damped-least-squares steps from the uniform q on
+ * r = [t* - t_EE ; log(R* R_EE^T)] over (q, yaw), A = [J_q | -d(t*, R*)/dyaw]
+ * (J_q the geometric Jacobian; d(t*, R*)/dyaw = [z x (t* - box centre) ; z] for a
+ * Place, [0 ; z] for a Pick), step = A^T (A A^T + lambda^2 I)^-1 r scaled to
+ * a largest entry <= TAMP_IK_MAX_STEP, q clamped to its limits.
+ * Adam state and the iteration counter are reset. */
 tamp_status tamp_sample_particles(tamp_scene *scene, int problem_id, int n_particles,
                                   uint64_t seed, int sampler);
 
@@ -279,6 +312,33 @@ tamp_status tamp_mlp_gradient(tamp_mlp *net, const float *x_dev, const float *y_
 tamp_status tamp_mlp_train_step(tamp_mlp *net, const float *x_dev, const float *y_dev, const float *mask_dev,
                                 int B, float lr, float *loss);
 const char *tamp_mlp_last_error(const tamp_mlp *net);
+
+/* Attach a proposal network to a scene (NULL detaches); tamp_sample_particles
+ * with sampler 1 then seeds grasps and placements from it.  The scene does not
+ * own the network: keep it alive while it is attached.  Both must be on the
+ * same device. */
+tamp_status tamp_set_proposal(tamp_scene *scene, tamp_mlp *net);
+
+/* Proposal rows of a skeleton: one per Pick or Place action, in action order
+ * (*n_rows receives R).  Features (48 floats per row):
+ *   [0:3] the box's half extents; [3:8] its initial pose x, y, z, cos yaw,
+ *   sin yaw; [8:15] the surface it is placed on -- a Place's own, for a Pick the
+ *   next Place of the same box (zeros if none) -- centre x, y, cos yaw, sin yaw,
+ *   half x, half y, top z; [15:17] one-hot Pick / Place; [17] action index /
+ *   number of actions; [18] 1 if the skeleton has a goal; [19:27] DH a,
+ *   [27:35] DH d, [35:43] DH alpha / (pi/2) of joints 1..8 (zero past the
+ *   arm); [43] joints / 8; [44:48] zero.
+ * Targets (16 slots, mask 1 where used), normalised so that the sampling
+ * bounds map to [-1, 1]:
+ *   Pick  slots 0..4: g_x / h_x, g_y / h_y, (g_z - h_z + 0.02) / 0.01 - 1,
+ *         cos g_yaw, sin g_yaw;
+ *   Place slots 5..8: u / H_x, v / H_y (placement centre in the surface frame
+ *         over the surface half sizes), cos p_yaw, sin p_yaw.
+ * For training data: x is a host batch [D][n] (stride n); feat [n*R][48],
+ * y [n*R][16] and mask [n*R][16] are host arrays (each may be NULL; all NULL
+ * only returns R); row i*R + r belongs to particle i, action row r. */
+tamp_status tamp_proposal_rows(tamp_scene *scene, int problem_id, int n, const float *x, float *feat,
+                               float *y, float *mask, int *n_rows);
 
 #ifdef __cplusplus
 }

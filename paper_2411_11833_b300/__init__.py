@@ -175,6 +175,29 @@ class Scene:
         return dict(mask=mask.astype(bool), n_satisfied=ns.value, first_iter=first.value, cost=cost,
                     counts=counts[:ncon], particles=parts)
 
+    def set_proposal(self, net):
+        """Attach a proposal network (``Mlp``) for ``sample(..., sampler=1)``; None detaches."""
+        self._proposal = net                      # keep it alive while attached
+        self._check(self._lib.tamp_set_proposal(self._h, None if net is None else net._h))
+
+    def proposal_rows(self, pid: int, X=None):
+        """Training rows of particles X [D][n] (host float32): (features
+        [n*R, 48], targets [n*R, 16], mask [n*R, 16]); with X None, R."""
+        R = ctypes.c_int()
+        if X is None:
+            self._check(self._lib.tamp_proposal_rows(self._h, pid, 0, None, None, None, None, ctypes.byref(R)))
+            return R.value
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        n = int(X.shape[1])
+        self._check(self._lib.tamp_proposal_rows(self._h, pid, 0, None, None, None, None, ctypes.byref(R)))
+        F = np.zeros((n * R.value, 48), np.float32)
+        Y = np.zeros((n * R.value, 16), np.float32)
+        M = np.zeros((n * R.value, 16), np.float32)
+        self._check(self._lib.tamp_proposal_rows(self._h, pid, n, ctypes.c_void_p(X.ctypes.data),
+                                                 ctypes.c_void_p(F.ctypes.data), ctypes.c_void_p(Y.ctypes.data),
+                                                 ctypes.c_void_p(M.ctypes.data), ctypes.byref(R)))
+        return F, Y, M
+
     def work_counters(self, pid: int):
         """(cuboid, box) broad-phase candidates resolved exactly since the batch was set."""
         out = (ctypes.c_uint64 * 2)()

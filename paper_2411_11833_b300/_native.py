@@ -80,6 +80,9 @@ SIGNATURES = {
     "tamp_mlp_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int, ctypes.c_float, c_float_p]),
     "tamp_mlp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "tamp_set_proposal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "tamp_proposal_rows": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_int_p]),
 }
 
 STATUS = {0: "TAMP_OK", 1: "TAMP_ERR_INVALID_ARG", 2: "TAMP_ERR_STATE", 3: "TAMP_ERR_OOM",

@@ -27,7 +27,14 @@ int optimize_blocks_per_sm(int L, int warps, size_t smem);
 cudaError_t launch_sample(const uint32_t* pb, const uint32_t* sc, float* x, float* m, float* v, int stride, int P,
                           int D, uint64_t seed, cudaStream_t st);
 int optimize_warps(int K);
+cudaError_t launch_sample_proposal(const uint32_t* rows, int R, const float* out, float* x, int stride, int P,
+                                   uint64_t seed, cudaStream_t st);
+cudaError_t launch_ik(const uint32_t* pb, const uint32_t* sc, float* x, int stride, int P, int iters, float lam,
+                      float dmax, cudaStream_t st);
 }  // namespace tamp
+
+tamp_status mlp_forward_on_stream(tamp_mlp* n, const float* x_dev, int B, float* out_dev, cudaStream_t st,
+                                  int device);
 
 using namespace tamp;
 
@@ -47,6 +54,14 @@ struct Problem {
   int* d_first = nullptr;
   unsigned long long* d_work = nullptr;  // [2] broad-phase candidates resolved exactly
   bool has_batch = false, checked = false;
+  // learned proposals: one row per Pick/Place action (features, decode record)
+  int R = 0;
+  std::vector<float> pfeat;               // [R][PROP_NF]
+  std::vector<uint32_t> prow;             // [R][PROW_W]
+  std::vector<int> prow_box, prow_kind, prow_off, prow_surf;
+  uint32_t* d_prow = nullptr;
+  float* d_pfeat = nullptr;
+  float* d_pout = nullptr;                // [R][2 * PROP_NT]
 };
 
 }  // namespace
@@ -56,6 +71,8 @@ struct tamp_scene {
   cudaStream_t stream = nullptr;
   int nj = 0, S = 0, B = 0, NBS = 0, O = 0, NS = 0;
   std::vector<double> box_half, box_init, surf;
+  std::vector<double> dh_a, dh_d, dh_alpha;
+  tamp_mlp* proposal = nullptr;           // attached proposal network (not owned)
   std::vector<uint32_t> blob;
   uint32_t* d_blob = nullptr;
   int* d_err = nullptr;
@@ -281,7 +298,7 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
   int held = -1, held_g = -1;
   int off = 0;
   struct Cfg {
-    int kind, box, qo, go, tsrc, surf;
+    int kind, box, qo, go, tsrc, surf, ai;
     std::vector<std::pair<int, PoseSrc>> env;
     int t_kp, t_kr, t_x, t_cf, t_cp, t_jl;
     float tx, ty, tz, tyaw, pz;
@@ -310,7 +327,7 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
     if (kind == TAMP_PICK) {
       if (held >= 0) return fail(s, TAMP_ERR_INVALID_ARG, "action %d: Pick while holding box %d", ai, held);
       Cfg c{};
-      c.kind = 0; c.box = b; c.go = off;
+      c.kind = 0; c.box = b; c.go = off; c.ai = ai;
       const double* h = &s->box_half[3 * b];
       samp.push_back({SK_LINEAR, static_cast<float>(-h[0]), static_cast<float>(h[0]), 0});
       samp.push_back({SK_LINEAR, static_cast<float>(-h[1]), static_cast<float>(h[1]), 0});
@@ -341,7 +358,7 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
       if (held != b) return fail(s, TAMP_ERR_INVALID_ARG, "action %d: Place of box %d that is not held", ai, b);
       if (sf < 0 || sf >= s->NS) return fail(s, TAMP_ERR_INVALID_ARG, "action %d: surface %d out of range", ai, sf);
       Cfg c{};
-      c.kind = 1; c.box = b; c.go = held_g; c.surf = sf;
+      c.kind = 1; c.box = b; c.go = held_g; c.surf = sf; c.ai = ai;
       const int po = off;
       samp.push_back({SK_PLACE_X, 0.f, 0.f, sf});
       samp.push_back({SK_PLACE_Y, 0.f, 0.f, sf});
@@ -397,6 +414,59 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
   if (static_cast<int>(slots.size()) > MAX_SLOT) return fail(s, TAMP_ERR_INVALID_ARG, "too many Place actions");
   pr.D = off;
   pr.K = static_cast<int>(cfgs.size());
+  // learned-proposal rows: features of what each Pick/Place acts on, and the
+  // record the sampler decodes with (Sec. V-A; the layouts are in tamp.h)
+  bool has_goal = false;
+  for (int ai = 0; ai < n; ++ai) has_goal = has_goal || acts[ai].kind == TAMP_GOAL_MIN_OBJ_DIST;
+  pr.R = static_cast<int>(cfgs.size());
+  pr.pfeat.assign(static_cast<size_t>(pr.R) * PROP_NF, 0.f);
+  pr.prow.assign(static_cast<size_t>(pr.R) * PROW_W, 0u);
+  pr.prow_box.clear(); pr.prow_kind.clear(); pr.prow_off.clear(); pr.prow_surf.clear();
+  for (int r = 0; r < pr.R; ++r) {
+    const Cfg& c = cfgs[r];
+    int sf = c.surf;
+    if (c.kind == 0) {
+      sf = -1;
+      for (int aj = c.ai + 1; aj < n && sf < 0; ++aj)
+        if (acts[aj].kind == TAMP_PLACE && acts[aj].box == c.box) sf = acts[aj].surface;
+    }
+    const int poff = c.kind == 0 ? c.go : c.tsrc;
+    pr.prow_box.push_back(c.box); pr.prow_kind.push_back(c.kind);
+    pr.prow_off.push_back(poff); pr.prow_surf.push_back(sf);
+    float* f = &pr.pfeat[static_cast<size_t>(r) * PROP_NF];
+    const double* h = &s->box_half[3 * c.box];
+    const double* p0 = &s->box_init[4 * c.box];
+    f[0] = static_cast<float>(h[0]); f[1] = static_cast<float>(h[1]); f[2] = static_cast<float>(h[2]);
+    f[3] = static_cast<float>(p0[0]); f[4] = static_cast<float>(p0[1]); f[5] = static_cast<float>(p0[2]);
+    f[6] = static_cast<float>(std::cos(p0[3])); f[7] = static_cast<float>(std::sin(p0[3]));
+    if (sf >= 0) {
+      const double* q = &s->surf[6 * sf];
+      f[8] = static_cast<float>(q[0]); f[9] = static_cast<float>(q[1]);
+      f[10] = static_cast<float>(std::cos(q[2])); f[11] = static_cast<float>(std::sin(q[2]));
+      f[12] = static_cast<float>(q[3]); f[13] = static_cast<float>(q[4]); f[14] = static_cast<float>(q[5]);
+    }
+    f[15 + c.kind] = 1.f;
+    f[17] = static_cast<float>(static_cast<double>(c.ai) / n);
+    f[18] = has_goal ? 1.f : 0.f;
+    for (int j = 0; j < nj; ++j) {
+      f[19 + j] = static_cast<float>(s->dh_a[j]);
+      f[27 + j] = static_cast<float>(s->dh_d[j]);
+      f[35 + j] = static_cast<float>(s->dh_alpha[j] / (M_PI / 2));
+    }
+    f[43] = static_cast<float>(nj / 8.0);
+    uint32_t* w = &pr.prow[static_cast<size_t>(r) * PROW_W];
+    w[0] = static_cast<uint32_t>(c.kind);
+    w[1] = static_cast<uint32_t>(poff);
+    float* wf = reinterpret_cast<float*>(w + 4);
+    if (c.kind == 0) {
+      wf[0] = f[0]; wf[1] = f[1]; wf[2] = f[2];
+    } else {
+      const double* q = &s->surf[6 * sf];
+      wf[0] = static_cast<float>(q[0]); wf[1] = static_cast<float>(q[1]);
+      wf[2] = static_cast<float>(std::cos(q[2])); wf[3] = static_cast<float>(std::sin(q[2]));
+      wf[4] = static_cast<float>(q[3]); wf[5] = static_cast<float>(q[4]);
+    }
+  }
   pr.NT = static_cast<int>(terms.size());
   // pack
   std::vector<uint32_t>& v = pr.blob;
@@ -738,6 +808,9 @@ tamp_status tamp_create_scene(const tamp_scene_desc* d, int device, void* stream
   s->nj = d->n_joints; s->S = d->n_spheres; s->B = d->n_boxes; s->NBS = d->spheres_per_box;
   s->O = d->n_obs; s->NS = d->n_surf;
   s->box_half.assign(d->box_half, d->box_half + 3 * d->n_boxes);
+  s->dh_a.assign(d->dh_a, d->dh_a + d->n_joints);
+  s->dh_d.assign(d->dh_d, d->dh_d + d->n_joints);
+  s->dh_alpha.assign(d->dh_alpha, d->dh_alpha + d->n_joints);
   s->box_init.assign(d->box_init, d->box_init + 4 * d->n_boxes);
   if (d->n_surf) s->surf.assign(d->surf, d->surf + 6 * d->n_surf);
   tamp_status st = build_scene_blob(s, d);
@@ -770,6 +843,7 @@ tamp_status tamp_destroy_scene(tamp_scene* s) {
   for (Problem* p : s->probs) {
     free_batch(*p);
     cudaFree(p->d_blob);
+    cudaFree(p->d_prow); cudaFree(p->d_pfeat); cudaFree(p->d_pout);
     delete p;
   }
   cudaFree(s->d_blob); cudaFree(s->d_err); cudaFree(s->d_scratch_first); cudaFree(s->d_item_counter);
@@ -817,11 +891,77 @@ tamp_status tamp_sample_particles(tamp_scene* s, int id, int P, uint64_t seed, i
   Problem* pr = get_problem(s, id);
   if (!pr) return fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", id);
   if (P <= 0 || P > (1 << 24)) return fail(s, TAMP_ERR_INVALID_ARG, "n_particles %d out of range", P);
-  if (sampler != 0) return fail(s, TAMP_ERR_INVALID_ARG, "sampler %d not available", sampler);
+  if (sampler < 0 || sampler > 3) return fail(s, TAMP_ERR_INVALID_ARG, "sampler %d not available", sampler);
+  if ((sampler & TAMP_SAMPLE_LEARNED) && !s->proposal)
+    return fail(s, TAMP_ERR_STATE, "the learned sampler needs a proposal network attached");
   DeviceGuard g(s->device);
   tamp_status st = ensure_batch(s, *pr, P);
   if (st != TAMP_OK) return st;
   CUDA_TRY(s, launch_sample(pr->d_blob, s->d_blob, pr->d_x, pr->d_m, pr->d_v, P, P, pr->D, seed, s->stream));
+  if (sampler & TAMP_SAMPLE_LEARNED) {
+    if (!pr->d_prow) {
+      CUDA_TRY(s, cudaMalloc(&pr->d_prow, pr->prow.size() * 4));
+      CUDA_TRY(s, cudaMalloc(&pr->d_pfeat, pr->pfeat.size() * 4));
+      CUDA_TRY(s, cudaMalloc(&pr->d_pout, static_cast<size_t>(pr->R) * 2 * PROP_NT * 4));
+      CUDA_TRY(s, cudaMemcpyAsync(pr->d_prow, pr->prow.data(), pr->prow.size() * 4, cudaMemcpyHostToDevice, s->stream));
+      CUDA_TRY(s, cudaMemcpyAsync(pr->d_pfeat, pr->pfeat.data(), pr->pfeat.size() * 4, cudaMemcpyHostToDevice,
+                                  s->stream));
+    }
+    st = mlp_forward_on_stream(s->proposal, pr->d_pfeat, pr->R, pr->d_pout, s->stream, s->device);
+    if (st != TAMP_OK) return fail(s, st, "proposal network forward: %s", tamp_mlp_last_error(s->proposal));
+    CUDA_TRY(s, launch_sample_proposal(pr->d_prow, pr->R, pr->d_pout, pr->d_x, P, P, seed, s->stream));
+  }
+  if (sampler & TAMP_SAMPLE_IK)
+    CUDA_TRY(s, launch_ik(pr->d_blob, s->d_blob, pr->d_x, P, P, TAMP_IK_ITERS, TAMP_IK_DAMPING, TAMP_IK_MAX_STEP,
+                          s->stream));
+  return TAMP_OK;
+}
+
+tamp_status tamp_set_proposal(tamp_scene* s, tamp_mlp* net) {
+  if (!s) return TAMP_ERR_INVALID_ARG;
+  s->proposal = net;
+  return TAMP_OK;
+}
+
+tamp_status tamp_proposal_rows(tamp_scene* s, int id, int n, const float* x, float* feat, float* y, float* mask,
+                               int* n_rows) {
+  Problem* pr = get_problem(s, id);
+  if (!pr) return fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", id);
+  if (n_rows) *n_rows = pr->R;
+  if (!feat && !y && !mask) return TAMP_OK;
+  if (n <= 0 || !x) return fail(s, TAMP_ERR_INVALID_ARG, "bad particle batch");
+  const int R = pr->R;
+  for (int i = 0; i < n; ++i) {
+    for (int r = 0; r < R; ++r) {
+      const size_t row = static_cast<size_t>(i) * R + r;
+      if (feat) std::copy(&pr->pfeat[static_cast<size_t>(r) * PROP_NF], &pr->pfeat[static_cast<size_t>(r + 1) * PROP_NF],
+                          feat + row * PROP_NF);
+      float* yy = y ? y + row * PROP_NT : nullptr;
+      float* mm = mask ? mask + row * PROP_NT : nullptr;
+      if (yy) std::fill(yy, yy + PROP_NT, 0.f);
+      if (mm) std::fill(mm, mm + PROP_NT, 0.f);
+      const int off = pr->prow_off[r], b = pr->prow_box[r];
+      auto X = [&](int c) { return static_cast<double>(x[static_cast<size_t>(off + c) * n + i]); };
+      if (pr->prow_kind[r] == 0) {
+        const double* h = &s->box_half[3 * b];
+        const double t[5] = {X(0) / h[0], X(1) / h[1], (X(2) - (h[2] - 0.02)) / 0.01 - 1.0, std::cos(X(3)),
+                             std::sin(X(3))};
+        for (int k = 0; k < 5; ++k) {
+          if (yy) yy[k] = static_cast<float>(t[k]);
+          if (mm) mm[k] = 1.f;
+        }
+      } else {
+        const double* q = &s->surf[6 * pr->prow_surf[r]];
+        const double dx = X(0) - q[0], dy = X(1) - q[1];
+        const double u = std::cos(q[2]) * dx + std::sin(q[2]) * dy, v = -std::sin(q[2]) * dx + std::cos(q[2]) * dy;
+        const double t[4] = {u / q[3], v / q[4], std::cos(X(2)), std::sin(X(2))};
+        for (int k = 0; k < 4; ++k) {
+          if (yy) yy[5 + k] = static_cast<float>(t[k]);
+          if (mm) mm[5 + k] = 1.f;
+        }
+      }
+    }
+  }
   return TAMP_OK;
 }
 

@@ -63,6 +63,12 @@ constexpr int TERM_W = 4;       // kind, weight (float), tol (float), is_constra
 constexpr int GOAL_W = 4;       // box, src, z (float), pad
 constexpr int SAMP_W = 4;       // per component: kind, a (float), b (float), surface
 enum SampKind { SK_LINEAR = 0, SK_PLACE_X = 1, SK_PLACE_Y = 2 };
+// Proposal-sampler row record (one per Pick/Place action, in action order):
+// word 0 kind (0 Pick, 1 Place), word 1 offset of the grasp / placement in the
+// particle, words 4.. floats: Pick h_x, h_y, h_z of the box; Place the surface's
+// centre x, y, cos yaw, sin yaw, half x, half y.
+constexpr int PROW_W = 12;
+constexpr int PROP_NF = 48, PROP_NT = 16;   // network inputs, target slots (outputs = 2 * PROP_NT)
 
 enum TermKind {
   TK_KIN_POS = 0, TK_KIN_ROT, TK_GRASP, TK_STABLE, TK_CFREE_HOLD, TK_CFREE_PLACE, TK_JOINT_LIMIT,

@@ -1050,6 +1050,230 @@ __global__ void sample_uniform_kernel(const uint32_t* __restrict__ pb, const uin
   v[c * stride + i] = 0.f;
 }
 
+// Learned proposals (Sec. V-A): overwrite the grasp / placement components of
+// a uniformly sampled batch with draws from the network's per-row Gaussians.
+// Slot k of row r draws t = mu + exp(clamp(s, -8, 3)) xi with xi a standard
+// normal by Box-Muller from Philox at counter (i, 16 r + k, 1, 0); positions
+// are clamped to the sampling bounds, yaws are atan2 of the (sin, cos) slots.
+__device__ __forceinline__ float philox_normal(uint32_t i, uint32_t c, uint2 key) {
+  const uint4 w = philox4x32_10(make_uint4(i, c, 1u, 0u), key);
+  const float u1 = static_cast<float>((w.x >> 8) + 1u) * (1.0f / 16777216.0f);  // (0, 1]
+  const float u2 = static_cast<float>(w.y >> 8) * (1.0f / 16777216.0f);         // [0, 1)
+  return sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
+}
+
+__global__ void sample_proposal_kernel(const uint32_t* __restrict__ rows, const float* __restrict__ out,
+                                       float* __restrict__ x, int stride, int P, uint2 key) {
+  const int r = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  const uint32_t* rec = rows + r * PROW_W;
+  const float* f = reinterpret_cast<const float*>(rec + 4);
+  const float* o = out + r * 2 * PROP_NT;
+  const int off = static_cast<int>(rec[1]);
+  auto draw = [&](int k) {
+    const float ls = fminf(fmaxf(o[PROP_NT + k], -8.f), 3.f);
+    return fmaf(expf(ls), philox_normal(i, 16u * r + k, key), o[k]);
+  };
+  auto clamp1 = [](float t) { return fminf(fmaxf(t, -1.f), 1.f); };
+  if (rec[0] == 0) {
+    const float t0 = draw(0), t1 = draw(1), t2 = draw(2), t3 = draw(3), t4 = draw(4);
+    x[off * stride + i] = f[0] * clamp1(t0);
+    x[(off + 1) * stride + i] = f[1] * clamp1(t1);
+    x[(off + 2) * stride + i] = f[2] - 0.02f + 0.01f * (clamp1(t2) + 1.f);
+    x[(off + 3) * stride + i] = atan2f(t4, t3);
+  } else {
+    const float t5 = draw(5), t6 = draw(6), t7 = draw(7), t8 = draw(8);
+    const float u = f[4] * clamp1(t5), v = f[5] * clamp1(t6);
+    x[off * stride + i] = f[0] + fmaf(f[2], u, -f[3] * v);
+    x[(off + 1) * stride + i] = f[1] + fmaf(f[3], u, f[2] * v);
+    x[(off + 2) * stride + i] = atan2f(t8, t7);
+  }
+}
+
+// Conditional configuration sampler (Sec. VI: joint positions solved by
+// parallel inverse kinematics for the target poses implied by the sampled
+// grasps and placements).  One thread per particle visits its configurations
+// in skeleton order; each has one free yaw (a Pick's grasp yaw, a Place's
+// placement yaw).  Damped least squares on r = [t* - t_EE ; log(R* R_EE^T)]
+// over (q, y) with A = [J_q | -dr*/dy], step = A^T (A A^T + lam^2 I)^-1 r
+// scaled to a largest entry <= dmax, q clamped to its limits.
+__device__ __forceinline__ void rot_log(const float (&E)[9], float (&w)[3]) {
+  const float vx = 0.5f * (E[7] - E[5]), vy = 0.5f * (E[2] - E[6]), vz = 0.5f * (E[3] - E[1]);
+  const float s = sqrtf(vx * vx + vy * vy + vz * vz);
+  const float c = 0.5f * (E[0] + E[4] + E[8] - 1.f);
+  if (s > 1e-6f || c > 0.f) {
+    const float f = s > 1e-6f ? atan2f(s, c) / s : 1.f;
+    w[0] = f * vx; w[1] = f * vy; w[2] = f * vz;
+    return;
+  }
+  // a half turn: (R + I) / 2 = axis axis^T
+  const float d0 = 0.5f * (E[0] + 1.f), d1 = 0.5f * (E[4] + 1.f), d2 = 0.5f * (E[8] + 1.f);
+  const int k = (d0 >= d1 && d0 >= d2) ? 0 : (d1 >= d2 ? 1 : 2);
+  const float dk = fmaxf(k == 0 ? d0 : (k == 1 ? d1 : d2), 1e-30f);
+  const float inv = 3.14159265358979f * rsqrtf(dk);
+  // column k of (R + I) / 2
+  w[0] = (k == 0 ? d0 : 0.5f * E[k]) * inv;
+  w[1] = (k == 1 ? d1 : 0.5f * E[3 + k]) * inv;
+  w[2] = (k == 2 ? d2 : 0.5f * E[6 + k]) * inv;
+}
+
+__global__ void __launch_bounds__(128) ik_configs_kernel(const uint32_t* __restrict__ pb,
+                                                         const uint32_t* __restrict__ sc, float* __restrict__ x,
+                                                         int stride, int P, int iters, float lam, float dmax) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  const int nj = sc[SH_NJ];
+  const float* arm = reinterpret_cast<const float*>(sc + sc[SH_OFF_ARM]);
+  const float* tl = arm + 12;
+  const int K = pb[PH_K];
+  const float lam2 = lam * lam;
+#define XG(c) x[(c) * stride + i]
+  for (int k = 0; k < K; ++k) {
+    const int* cf = reinterpret_cast<const int*>(pb + pb[PH_OFF_CFG] + k * CFG_W);
+    const float* cff = reinterpret_cast<const float*>(cf);
+    const int kind = cf[CF_KIND], qo = cf[CF_QOFF], go = cf[CF_GOFF], tsrc = cf[CF_TSRC];
+    const bool place = kind == 1;
+    float bx, by, bz, byaw;
+    if (tsrc < 0) {
+      bx = cff[CF_TX]; by = cff[CF_TY]; bz = cff[CF_TZ]; byaw = cff[CF_TYAW];
+    } else {
+      bx = XG(tsrc); by = XG(tsrc + 1); bz = cff[CF_TZ]; byaw = XG(tsrc + 2);
+    }
+    const float gx = XG(go), gy = XG(go + 1), gz = XG(go + 2);
+    const int yo = place ? tsrc + 2 : go + 3;
+    float y = XG(yo);
+    float q[MAXJ];
+#pragma unroll
+    for (int j = 0; j < MAXJ; ++j) q[j] = j < nj ? XG(qo + j) : 0.f;
+    for (int it = 0; it < iters; ++it) {
+      // target: position P_box g, orientation Rz(box yaw + grasp yaw) Rx(pi)
+      const float pyaw = place ? y : byaw;
+      const float phi = place ? y + XG(go + 3) : byaw + y;
+      float sp, cp, sf, cfv;
+      sincosf(pyaw, &sp, &cp);
+      sincosf(phi, &sf, &cfv);
+      const float tx = bx + fmaf(cp, gx, -sp * gy), ty = by + fmaf(sp, gx, cp * gy), tz = bz + gz;
+      const float Rt[9] = {cfv, sf, 0.f, sf, -cfv, 0.f, 0.f, 0.f, -1.f};
+      // forward kinematics, keeping each joint's axis and origin
+      float R[9], t[3], oz[MAXJ][6];
+#pragma unroll
+      for (int a = 0; a < 9; ++a) R[a] = arm[a];
+      t[0] = arm[9]; t[1] = arm[10]; t[2] = arm[11];
+#pragma unroll
+      for (int j = 0; j < MAXJ; ++j) {
+        if (j < nj) {
+          oz[j][0] = t[0]; oz[j][1] = t[1]; oz[j][2] = t[2];
+          oz[j][3] = R[2]; oz[j][4] = R[5]; oz[j][5] = R[8];
+          const float* Jp = arm + 24 + j * ARM_JW;
+          float sj, cj;
+          sincosf(q[j] + Jp[4], &sj, &cj);
+          rz_right(R, cj, sj);
+          t[0] = fmaf(Jp[1], R[2], fmaf(Jp[0], R[0], t[0]));
+          t[1] = fmaf(Jp[1], R[5], fmaf(Jp[0], R[3], t[1]));
+          t[2] = fmaf(Jp[1], R[8], fmaf(Jp[0], R[6], t[2]));
+          rx_right(R, Jp[2], Jp[3]);
+        }
+      }
+      float Re[9], pe[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+          Re[3 * a + b] = fmaf(R[3 * a], tl[b], fmaf(R[3 * a + 1], tl[3 + b], R[3 * a + 2] * tl[6 + b]));
+        pe[a] = fmaf(R[3 * a], tl[9], fmaf(R[3 * a + 1], tl[10], fmaf(R[3 * a + 2], tl[11], t[a])));
+      }
+      // residual
+      float E[9];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+          E[3 * a + b] = fmaf(Rt[3 * a], Re[3 * b], fmaf(Rt[3 * a + 1], Re[3 * b + 1], Rt[3 * a + 2] * Re[3 * b + 2]));
+      float w[3];
+      rot_log(E, w);
+      const float r[6] = {tx - pe[0], ty - pe[1], tz - pe[2], w[0], w[1], w[2]};
+      // A = [J_q | -dr*/dy]; the yaw column is [-(z x (t* - c_box)) ; -z] for a
+      // Place (c_box the box centre) and [0 ; -z] for a Pick
+      float A[6][MAXJ + 1];
+#pragma unroll
+      for (int j = 0; j < MAXJ; ++j) {
+        const float dx = pe[0] - oz[j][0], dy = pe[1] - oz[j][1], dz = pe[2] - oz[j][2];
+        const bool on = j < nj;
+        A[0][j] = on ? oz[j][4] * dz - oz[j][5] * dy : 0.f;
+        A[1][j] = on ? oz[j][5] * dx - oz[j][3] * dz : 0.f;
+        A[2][j] = on ? oz[j][3] * dy - oz[j][4] * dx : 0.f;
+        A[3][j] = on ? oz[j][3] : 0.f;
+        A[4][j] = on ? oz[j][4] : 0.f;
+        A[5][j] = on ? oz[j][5] : 0.f;
+      }
+      A[0][MAXJ] = place ? ty - by : 0.f;
+      A[1][MAXJ] = place ? -(tx - bx) : 0.f;
+      A[2][MAXJ] = 0.f;
+      A[3][MAXJ] = 0.f; A[4][MAXJ] = 0.f; A[5][MAXJ] = -1.f;
+      // M = A A^T + lam^2 I, Cholesky M = L L^T, solve M s = r
+      float L[6][6];
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+#pragma unroll
+        for (int b = 0; b <= a; ++b) {
+          float m = a == b ? lam2 : 0.f;
+#pragma unroll
+          for (int c = 0; c <= MAXJ; ++c) m = fmaf(A[a][c], A[b][c], m);
+#pragma unroll
+          for (int c = 0; c < b; ++c) m = fmaf(-L[a][c], L[b][c], m);
+          L[a][b] = a == b ? sqrtf(fmaxf(m, 1e-30f)) : m / L[b][b];
+        }
+      }
+      float s[6];
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        float m = r[a];
+#pragma unroll
+        for (int c = 0; c < a; ++c) m = fmaf(-L[a][c], s[c], m);
+        s[a] = m / L[a][a];
+      }
+#pragma unroll
+      for (int a = 5; a >= 0; --a) {
+        float m = s[a];
+#pragma unroll
+        for (int c = a + 1; c < 6; ++c) m = fmaf(-L[c][a], s[c], m);
+        s[a] = m / L[a][a];
+      }
+      float st[MAXJ + 1], mx = 0.f;
+#pragma unroll
+      for (int c = 0; c <= MAXJ; ++c) {
+        float m = 0.f;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) m = fmaf(A[a][c], s[a], m);
+        st[c] = m;
+        mx = fmaxf(mx, fabsf(m));
+      }
+      const float sc_ = mx > dmax ? dmax / mx : 1.f;
+#pragma unroll
+      for (int j = 0; j < MAXJ; ++j) {
+        if (j < nj) {
+          const float* Jp = arm + 24 + j * ARM_JW;
+          q[j] = fminf(fmaxf(fmaf(sc_, st[j], q[j]), Jp[5]), Jp[6]);
+        }
+      }
+      y = fmaf(sc_, st[MAXJ], y);
+    }
+#pragma unroll
+    for (int j = 0; j < MAXJ; ++j)
+      if (j < nj) XG(qo + j) = q[j];
+    XG(yo) = y;
+  }
+#undef XG
+}
+
+cudaError_t launch_ik(const uint32_t* pb, const uint32_t* sc, float* x, int stride, int P, int iters, float lam,
+                      float dmax, cudaStream_t st) {
+  if (P == 0 || iters <= 0) return cudaSuccess;
+  ik_configs_kernel<<<(P + 127) / 128, 128, 0, st>>>(pb, sc, x, stride, P, iters, lam, dmax);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ graph chunk controller
 // After each chunk of a captured optimisation: advance every problem's step
 // count, and raise the stop flag when stopping on the first satisfying particle
@@ -1137,6 +1361,15 @@ cudaError_t launch_sample(const uint32_t* pb, const uint32_t* sc, float* x, floa
   dim3 grid((P + 255) / 256, D);
   const uint2 key = make_uint2(static_cast<uint32_t>(seed & 0xffffffffu), static_cast<uint32_t>(seed >> 32));
   sample_uniform_kernel<<<grid, 256, 0, st>>>(pb, sc, x, m, v, stride, P, key);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample_proposal(const uint32_t* rows, int R, const float* out, float* x, int stride, int P,
+                                   uint64_t seed, cudaStream_t st) {
+  if (P == 0 || R == 0) return cudaSuccess;
+  dim3 grid((P + 255) / 256, R);
+  const uint2 key = make_uint2(static_cast<uint32_t>(seed & 0xffffffffu), static_cast<uint32_t>(seed >> 32));
+  sample_proposal_kernel<<<grid, 256, 0, st>>>(rows, out, x, stride, P, key);
   return cudaGetLastError();
 }
 

@@ -607,3 +607,16 @@ tamp_status tamp_mlp_train_step(tamp_mlp* n, const float* x, const float* y, con
 const char* tamp_mlp_last_error(const tamp_mlp* n) { return n ? n->last_error.c_str() : "null network"; }
 
 }  // extern "C"
+
+// The proposal sampler's forward pass, on the scene's stream after any work
+// queued on the network's own stream (training) has finished.
+tamp_status mlp_forward_on_stream(tamp_mlp* n, const float* x_dev, int B, float* out_dev, cudaStream_t st,
+                                  int device) {
+  if (!n || !x_dev || !out_dev || B <= 0) return TAMP_ERR_INVALID_ARG;
+  if (n->device != device) return mfail(n, TAMP_ERR_INVALID_ARG, "network and scene are on different devices");
+  MLP_TRY(n, cudaStreamSynchronize(n->stream));
+  MLP_TRY(n, enable_smem(n->device));
+  mlp_forward_kernel<<<(B + ROWS - 1) / ROWS, THREADS, SMEM_BYTES, st>>>(fwd_args(n, x_dev, B, out_dev, false));
+  MLP_TRY(n, cudaGetLastError());
+  return TAMP_OK;
+}
