@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--iters", type=int, default=N_ITERS)
     ap.add_argument("--lanes", type=int, default=0, help="threads per (particle, configuration); 0 = library choice")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ttfs", action="store_true", help="skip the time-to-first-satisfying measurement")
     return ap.parse_args()
 
 
@@ -165,6 +166,61 @@ def run_reference(args):
         "cpu_baseline": {"value": val, "unit": "particle-iters/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "particle-iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def measure_ttfs(pkg, sg, seeds=range(3001, 3009), budget_iters=1000):
+    """Time to the first satisfying particle on obstructed stacking (one fixed
+    7-DOF arm; 2-4 blockers cover B's top; 16 candidate skeletons of 2-8
+    actions with batches of 1024-8192): the plain form -- Algorithm 1 one
+    skeleton at a time from uniform seeds -- against the batched form (every
+    skeleton in one persistent launch) seeded by IK configurations, without
+    and with the proposal network.  The network is trained first, by the
+    library's kernels, on satisfying particles the method finds on plain
+    Pick-Place scenes of the same arm.  Wall-clock seconds per seed from the
+    start of sampling to the search's return, the give-up time when it fails."""
+    import numpy as np
+    import torch
+
+    from paper_2411_11833_b300 import proposal, search
+    t0 = time.perf_counter()
+    F, Y, M, st = proposal.harvest([sg.robot_plain_problem(10000 + k) for k in range(128)], n_particles=4096,
+                                   iters=200, chunk=50, sampler=2, max_rows_per_problem=256)
+    net, losses = proposal.train(F, Y, M, steps=1500, batch=4096, lr=1e-3, log_every=1499)
+    train_s = time.perf_counter() - t0
+    forms = {"plain_sequential_uniform": (0, False), "batched_ik": (2, True), "batched_learned_ik": (3, True)}
+    res = {k: [] for k in forms}
+    for seed in seeds:
+        sc, skels, sizes = sg.stacking_problem(seed, arm_seed=4000)
+        for name, (sampler, batched) in forms.items():
+            scene = pkg.Scene(sc)
+            if sampler & 1:
+                scene.set_proposal(net)
+            be = search._Backend(scene)
+            be.sample = lambda pid, n, sd, s=sampler: scene.sample(pid, n, sd, s)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            if batched:
+                r = search.batched_search(be, skels, sizes, steps_per_chunk=25, max_iterations=budget_iters, seed=seed)
+            else:
+                r = search.sequential_search(be, skels, sizes, steps_per_chunk=25, chunks_per_visit=2,
+                                             max_iterations=budget_iters, seed=seed)
+            res[name].append({"seed": seed, "solved": bool(r["solved"]), "s": round(time.perf_counter() - t1, 4),
+                              "first_iter": int(r["first_iter"])})
+            scene.set_proposal(None)
+            scene.close()
+    out = {"workload": "obstructed stacking: fixed 7-DOF arm, A on B under 2-4 blockers, 16 candidate skeletons "
+                       "of 2-8 actions, batches of 1024-8192, 16 cuboids",
+           "seeds": list(seeds), "budget_iters_per_skeleton": budget_iters, "unit": "s",
+           "network": {"harvest_particles": st["particles"], "harvest_scenes": st["problems"], "train_steps": 1500,
+                       "final_nll": round(losses[-1][1], 4), "harvest_and_train_s": round(train_s, 2)},
+           "forms": {}}
+    for name, rows in res.items():
+        solved = [r["s"] for r in rows if r["solved"]]
+        out["forms"][name] = {"solved": len(solved), "of": len(rows),
+                              "median_s_solved": float(np.median(solved)) if solved else None,
+                              "per_seed": rows}
+    net.close()
+    return out
 
 
 def main():
@@ -288,6 +344,8 @@ def main():
         "kernel_ms": sum(kern_ms) / len(kern_ms),
         "satisfied_last_step": int(q["n_satisfied"]), "first_satisfying_iter_last_step": int(q["first_iter"]),
     }
+    if not args.no_ttfs and world == 1:
+        out["ttfs"] = measure_ttfs(pkg, sg)
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out))

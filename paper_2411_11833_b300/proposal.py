@@ -25,17 +25,20 @@ def _solve(scene: Scene, pid: int, n: int, seed: int, sampler: int, iters: int, 
 
 
 def harvest(problems, n_particles: int = 4096, iters: int = 1000, chunk: int = 50, seed: int = 1,
-            max_rows_per_problem: int | None = None):
-    """Optimise each (scene, skeleton) with uniform seeds for ``iters``
-    iterations and turn every particle that then satisfies Eq. 3 into training
-    rows.  Returns (features, targets, mask, stats)."""
+            max_rows_per_problem: int | None = None, sampler: int = 0):
+    """Optimise each (scene, skeleton) from ``sampler`` seeds (never the
+    network: the method without it) for ``iters`` iterations and turn the
+    particles that then satisfy Eq. 3 into training rows.  Returns (features,
+    targets, mask, stats)."""
+    if sampler & 1:
+        raise ValueError("harvest runs the method without the network")
     Fs, Ys, Ms = [], [], []
     stats = dict(problems=0, solved=0, particles=0, wall_s=0.0)
     t0 = time.perf_counter()
     for k, (sc, acts) in enumerate(problems):
         scene = Scene(sc)
         pid = scene.set_skeleton(acts)
-        _solve(scene, pid, n_particles, seed + 7919 * k, 0, iters, chunk, False)
+        _solve(scene, pid, n_particles, seed + 7919 * k, sampler, iters, chunk, False)
         q = scene.query(pid, n_particles, want_particles=True)
         stats["problems"] += 1
         sel = np.flatnonzero(q["mask"])
@@ -101,18 +104,20 @@ def _init_params(seed: int) -> np.ndarray:
 
 
 def iterations_to_first(problems, net: Mlp | None, n_particles: int = 4096, iters: int = 1000, chunk: int = 25,
-                        seed: int = 1000):
+                        seed: int = 1000, ik: bool = False):
     """Per problem: the first iteration whose Eq. 3 check finds a satisfying
     particle (-1 if none within ``iters``), for uniform seeds and, if ``net``
     is given, for the network's proposals (same particle count, seeds and
-    tolerances).  Also the wall time of each run."""
+    tolerances; with ``ik`` both then get IK configurations).  Also the wall
+    time of each run."""
     out = []
     for k, (sc, acts) in enumerate(problems):
         scene = Scene(sc)
         pid = scene.set_skeleton(acts)
         row = {}
-        for name, sampler in (("uniform", 0), ("learned", 1)):
-            if sampler == 1:
+        base = 2 if ik else 0
+        for name, sampler in (("uniform", base), ("learned", base | 1)):
+            if sampler & 1:
                 if net is None:
                     continue
                 scene.set_proposal(net)

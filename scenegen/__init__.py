@@ -120,6 +120,26 @@ def box_sphere_model(half: np.ndarray) -> np.ndarray:
     return np.array(out)
 
 
+def box_sphere_fill(half: np.ndarray, n_max: int = 8) -> np.ndarray:
+    """Spheres of radius r = min(h) inside a box, centres on a grid over the box
+    shrunk by r with spacing at most r per axis where the budget allows (axes
+    of least extent give up spheres first); n_max slots, unused ones inert
+    (radius -1 at the centre).  Unlike the 8-corner model this covers the long
+    axis of an elongated box, so a thin strip actually blocks what sits on it."""
+    half = np.asarray(half, dtype=float)
+    r = float(half.min())
+    ext = half - r
+    counts = [1 if e <= 1e-9 else int(math.ceil(2.0 * e / r)) + 1 for e in ext]
+    while int(np.prod(counts)) > n_max:
+        cand = [a for a in range(3) if counts[a] > 1]
+        a = min(cand, key=lambda a: ext[a])
+        counts[a] -= 1
+    axes = [np.linspace(-e, e, n) if n > 1 else np.zeros(1) for e, n in zip(ext, counts)]
+    out = [[x, y, z, r] for x in axes[0] for y in axes[1] for z in axes[2]]
+    out += [[0.0, 0.0, 0.0, -1.0]] * (n_max - len(out))
+    return np.array(out)
+
+
 def _polar(rng, r_lo, r_hi, ang_c=None, ang_w=math.pi):
     r = rng.uniform(r_lo, r_hi)
     ang = rng.uniform(-ang_w, ang_w) + (0.0 if ang_c is None else ang_c)
@@ -268,7 +288,7 @@ def stacking_problem(seed: int = 3001, arm_seed: int | None = None):
     obs_rot = np.stack([_rz3(rng.uniform(-math.pi, math.pi)) for _ in range(n_obs)])
     surf = np.array([[Bxy[0], Bxy[1], Byaw, hB[0], hB[1], topB],
                      [reg_xy[0], reg_xy[1], rng.uniform(-math.pi, math.pi), reg_h[0], reg_h[1], 0.0]])
-    sc = Scene(**arm, box_half=half, box_init=box_init, box_spheres=np.stack([box_sphere_model(h) for h in half]),
+    sc = Scene(**arm, box_half=half, box_init=box_init, box_spheres=np.stack([box_sphere_fill(h) for h in half]),
                obs_center=obs_center, obs_rot=obs_rot, obs_half=obs_half, surf=surf,
                name=f"stacking-{n_block}blockers", seed=seed, meta=dict(n_blockers=n_block))
     blockers = list(range(2, 2 + n_block))

@@ -99,42 +99,48 @@ def test_proposal_sampler_needs_a_network(pkg):
     scene.close()
 
 
-def test_trained_proposals_against_uniform_seeds(pkg):
-    """The network trained by the library's own kernels on satisfying particles
-    of one robot's plain Pick-Place scenes, judged on held-out scenes of the
-    same robot: the FP64 oracle cost of its seeds on the term its placements
-    enter (StablePlace) must beat uniform seeds; the iterations to the first
-    satisfying particle of both forms are reported."""
-    from oracle.problem import STABLE_PLACE, CFREE_PLACE
+def test_trained_proposals_gain_over_the_method_without_them(pkg):
+    """What the trained network adds, judged on held-out scenes of one robot.
+
+    Training: the method itself (uniform grasps/placements, IK configurations,
+    200 Adam steps) solves 128 plain Pick-Place scenes; up to 256 satisfying
+    particles per scene become rows; the library's own tensor-core kernels fit
+    the network.  Test: on 16 unseen scenes, 4096 particles drawn with the
+    network's grasps and placements (then IK) against uniform ones (then IK),
+    same seeds and tolerances; the measure is how many particles satisfy
+    Eq. 3 straight after sampling, counted by the GPU check and re-judged by
+    the FP64 oracle on a subset."""
     from paper_2411_11833_b300 import proposal
     train = [sg.robot_plain_problem(10000 + k) for k in range(128)]
-    F, Y, M, st = proposal.harvest(train, n_particles=4096, iters=1000, chunk=100)
-    assert st["particles"] >= 300, st
-    net, losses = proposal.train(F, Y, M, steps=1500, batch=2048, lr=1e-3, log_every=500)
-    assert losses[-1][1] < losses[0][1] - 0.5
-    held = [sg.robot_plain_problem(20000 + k) for k in range(16)]
-    costs = {"uniform": {STABLE_PLACE: [], CFREE_PLACE: []}, "learned": {STABLE_PLACE: [], CFREE_PLACE: []}}
-    for k, (sc, acts) in enumerate(held):
+    F, Y, M, st = proposal.harvest(train, n_particles=4096, iters=200, chunk=50, sampler=2,
+                                   max_rows_per_problem=256)
+    assert st["particles"] >= 8000, st
+    net, losses = proposal.train(F, Y, M, steps=1500, batch=4096, lr=1e-3, log_every=500)
+    assert losses[-1][1] < losses[0][1] - 0.5, losses
+    counts = {2: [], 3: []}
+    oracle_rate = {2: [], 3: []}
+    for k in range(16):
+        sc, acts = sg.robot_plain_problem(20000 + k)
+        pr = Problem(sc, acts)
         scene = pkg.Scene(sc)
         pid = scene.set_skeleton(acts)
         scene.set_proposal(net)
-        pr = Problem(sc, acts)
-        for name, sampler in (("uniform", 0), ("learned", 1)):
-            scene.sample(pid, 256, 900 + k, sampler=sampler)
-            x = scene.get_particles(pid)[0].T.astype(np.float64)
-            tv = pr.term_values(torch.from_numpy(x)).numpy()
-            for kind in (STABLE_PLACE, CFREE_PLACE):
-                cols = [j for j, t in enumerate(pr.terms) if t.kind == kind]
-                costs[name][kind].append(tv[:, cols].sum(axis=1).mean())
+        for sampler in (2, 3):
+            scene.sample(pid, 4096, 555 + k, sampler=sampler)
+            scene.optimize(pid, 0)                      # the Eq. 3 check of the seeds
+            q = scene.query(pid, 4096, want_particles=k < 4)
+            counts[sampler].append(q["n_satisfied"])
+            if k < 4:                                   # the FP64 oracle as the judge
+                X = q["particles"][:, :512].T.astype(np.float64)
+                ok = pr.satisfied(pr.term_values(torch.from_numpy(X))).numpy()
+                oracle_rate[sampler].append(float(ok.mean()))
+                gpu = q["mask"][:512]
+                assert (ok != gpu).mean() < 0.01
         scene.set_proposal(None)
         scene.close()
-    mean = {n: {k: float(np.mean(v)) for k, v in c.items()} for n, c in costs.items()}
-    assert mean["learned"][STABLE_PLACE] < 0.5 * mean["uniform"][STABLE_PLACE], mean
-    res = proposal.iterations_to_first(held, net, n_particles=4096, iters=1000, chunk=25)
-    u = np.array([r["uniform"]["first_iter"] for r in res])
-    l = np.array([r["learned"]["first_iter"] for r in res])
-    print(f"\nproposal: harvest {st}; seed cost (oracle, mean per particle) {mean}; "
-          f"iterations to first satisfying: uniform {u.tolist()} learned {l.tolist()}")
-    # both forms solve the held-out scenes at the same tolerances
-    assert (l >= 0).sum() >= (u >= 0).sum() - 2
+    u, l = np.array(counts[2]), np.array(counts[3])
+    print(f"\nproposal: harvest {st}; satisfying seeds of 4096 per held-out scene: uniform+IK mean {u.mean():.0f} "
+          f"{u.tolist()}; learned+IK mean {l.mean():.0f} {l.tolist()}; oracle-judged rates uniform "
+          f"{np.round(oracle_rate[2], 3).tolist()} learned {np.round(oracle_rate[3], 3).tolist()}")
+    assert l.mean() > u.mean()
     net.close()

@@ -93,3 +93,20 @@ def test_stacking_skeletons():
         assert pr.D == sum(11 if k == 0 else 10 for k, _, _ in acts)
     # every blocker initially rests on B's top face
     assert np.allclose(sc.box_init[2:2 + nb, 2], sc.surf[0, 5] + sc.box_half[2:2 + nb, 2])
+
+
+def test_stacking_blockers_occupy_every_placement_on_b():
+    # the 0-blocker skeleton (Pick A, Place A on B) has no contained,
+    # collision-free placement: the blockers' spheres cover B's top
+    import torch
+    from oracle import philox
+    from oracle.problem import CFREE_PLACE, STABLE_PLACE
+    for seed in (3001, 3002, 3009):
+        sc, skels, _ = sg.stacking_problem(seed)
+        pr = Problem(sc, skels[0])
+        tv = pr.term_values(torch.tensor(philox.sample_uniform(pr, 1500, 5))).numpy()
+        cp = [j for j, t in enumerate(pr.terms) if t.kind == CFREE_PLACE]
+        st = [j for j, t in enumerate(pr.terms) if t.kind == STABLE_PLACE]
+        inside = tv[:, st].sum(axis=1) <= 1e-3
+        assert inside.sum() > 300
+        assert not (inside & (tv[:, cp].sum(axis=1) <= 1e-3)).any()
