@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--lanes", type=int, default=0, help="threads per (particle, configuration); 0 = library choice")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttfs", action="store_true", help="skip the time-to-first-satisfying measurement")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's heuristic launch shape")
+    ap.add_argument("--workload", default="packing", choices=["packing", "stress"],
+                    help="packing (the headline line) or the stress scene (12 boxes, 64 cuboids, 100 spheres)")
     return ap.parse_args()
 
 
@@ -248,12 +251,25 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     P, T = args.particles, args.iters
 
-    sc, acts = sg.packing_problem(SCENE_SEED)
+    if args.workload == "stress":
+        sc, acts = sg.stress_problem(5001)
+        workload = ("stress: 7-DOF arm (100 spheres), 12 boxes, 64 cuboids, 0.5x0.5 m region, "
+                    "12 pick-place pairs + goal, D=252, uniform init")
+    else:
+        sc, acts = sg.packing_problem(SCENE_SEED)
+        workload = ("packing: 7-DOF arm (35 spheres), 6 boxes, 8 cuboids, 0.3x0.3 m region, "
+                    "6 pick-place pairs + goal, D=126, uniform init")
     with torch.cuda.stream(stream):
         scene = pkg.Scene(sc, device=local, stream=stream.cuda_stream)
         pid = scene.set_skeleton(acts, pkg.default_options(lanes=args.lanes))
     D, NT, _ = scene.problem_info(pid)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    tuned = None
+    if not args.no_autotune and args.lanes == 0:
+        with torch.cuda.stream(stream):
+            scene.sample(pid, P, 999)
+            L, W, ms = scene.autotune(pid, trial_steps=10)
+        tuned = {"lanes": L, "warps": W, "trial_ms_10_iters": round(ms, 3)}
 
     def one_step(seed):
         scene.sample(pid, P, seed)
@@ -323,14 +339,13 @@ def main():
     peak = flops.fp32_peak_tflops(props.multi_processor_count, 2032.0)
     achieved = launch_flops / kern_s / 1e12
     sha = kernel_source_sha()
-    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["source_sha"] == sha else None
+    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["source_sha"] == sha and args.workload == "packing" else None
     out = {
         "metric": METRIC, "value": value, "unit": "particle-iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "packing: 7-DOF arm (35 spheres), 6 boxes, 8 cuboids, 0.3x0.3 m region, "
-                               "6 pick-place pairs + goal, D=126, uniform init",
-                   "particles_per_gpu": P, "iters_per_step": T, "l2": "flushed between steps (512 MiB write)"},
+        "config": {"workload": workload, "particles_per_gpu": P, "iters_per_step": T,
+                   "l2": "flushed between steps (512 MiB write)", "launch_shape": tuned or "library heuristic"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "optimize_kernel", "flop_per_launch": launch_flops,
@@ -344,9 +359,9 @@ def main():
         "kernel_ms": sum(kern_ms) / len(kern_ms),
         "satisfied_last_step": int(q["n_satisfied"]), "first_satisfying_iter_last_step": int(q["first_iter"]),
     }
-    if not args.no_ttfs and world == 1:
+    if not args.no_ttfs and world == 1 and args.workload == "packing":
         out["ttfs"] = measure_ttfs(pkg, sg)
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and args.workload == "packing":
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out))
     scene.close()

@@ -266,6 +266,22 @@ tamp_status tamp_eval_static_scratch(tamp_scene *scene, int problem_id, int n, c
  * Synchronises.  Not part of the paper's method: performance accounting only. */
 tamp_status tamp_work_counters(tamp_scene *scene, int problem_id, uint64_t out[2]);
 
+/* Autotuner of the persistent launch (not part of the paper's method: it only
+ * picks how the same work is laid out).  For the listed problems with their
+ * current batches, times every launch shape that fits -- lanes L in {1, 2, 4,
+ * 8} per (particle, configuration) (32 / L particles per CTA) and W warps per
+ * CTA (configurations per warp 1..4) -- with trial_steps fused iterations on
+ * scratch copies of the batches (the problems' state is left untouched), and
+ * keeps the fastest for later launches of exactly these problems at these batch
+ * sizes whose options have lanes = 0.  Outputs (host, each may be NULL): the
+ * chosen L, W and its trial time in ms.  Synchronises. */
+tamp_status tamp_autotune(tamp_scene *scene, const int *problem_ids, int n_problems, int trial_steps,
+                          int *lanes, int *warps, float *ms);
+/* Install a known launch shape for the listed problems at their current batch
+ * sizes (e.g. one tamp_autotune found earlier on the same GPU); lanes 0
+ * removes the entry.  A shape that does not fit returns TAMP_ERR_INVALID_ARG. */
+tamp_status tamp_set_tuning(tamp_scene *scene, const int *problem_ids, int n_problems, int lanes, int warps);
+
 /* Text of the last error on this scene ("" if none); valid until the next call. */
 const char *tamp_last_error(const tamp_scene *scene);
 

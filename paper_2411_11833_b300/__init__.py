@@ -82,6 +82,8 @@ class Scene:
         self._h = h
         self.device = device
         self._sizes = {}          # batch size per problem (host bookkeeping)
+        self.shape = dict(n_joints=d.n_joints, n_spheres=d.n_spheres, n_boxes=d.n_boxes,
+                          spheres_per_box=d.spheres_per_box, n_obs=d.n_obs, n_surf=d.n_surf)
 
     # -------------------------------------------------------------- helpers
     def _check(self, st):
@@ -197,6 +199,23 @@ class Scene:
                                                  ctypes.c_void_p(F.ctypes.data), ctypes.c_void_p(Y.ctypes.data),
                                                  ctypes.c_void_p(M.ctypes.data), ctypes.byref(R)))
         return F, Y, M
+
+    def autotune(self, pids, trial_steps: int = 10):
+        """Time the launch shapes for these problems' current batches and keep
+        the fastest (tamp_autotune).  Returns (lanes, warps, ms)."""
+        if isinstance(pids, int):
+            pids = [pids]
+        arr = (ctypes.c_int * len(pids))(*pids)
+        L, W, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        self._check(self._lib.tamp_autotune(self._h, arr, len(pids), int(trial_steps), ctypes.byref(L),
+                                            ctypes.byref(W), ctypes.byref(ms)))
+        return L.value, W.value, ms.value
+
+    def set_tuning(self, pids, lanes: int, warps: int):
+        if isinstance(pids, int):
+            pids = [pids]
+        arr = (ctypes.c_int * len(pids))(*pids)
+        self._check(self._lib.tamp_set_tuning(self._h, arr, len(pids), int(lanes), int(warps)))
 
     def work_counters(self, pid: int):
         """(cuboid, box) broad-phase candidates resolved exactly since the batch was set."""

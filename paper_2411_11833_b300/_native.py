@@ -81,6 +81,8 @@ SIGNATURES = {
                                            ctypes.c_int, ctypes.c_float, c_float_p]),
     "tamp_mlp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "tamp_set_proposal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "tamp_autotune": (ctypes.c_int, [ctypes.c_void_p, c_int_p, ctypes.c_int, ctypes.c_int, c_int_p, c_int_p, c_float_p]),
+    "tamp_set_tuning": (ctypes.c_int, [ctypes.c_void_p, c_int_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "tamp_proposal_rows": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_int_p]),
 }

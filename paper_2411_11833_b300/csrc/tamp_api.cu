@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "tamp.h"
@@ -41,6 +42,7 @@ using namespace tamp;
 namespace {
 
 struct Problem {
+  int id = -1;
   int D = 0, K = 0, NT = 0, NCON = 0, NSLOT = 0;
   std::vector<uint32_t> blob;
   uint32_t* d_blob = nullptr;
@@ -73,6 +75,9 @@ struct tamp_scene {
   std::vector<double> box_half, box_init, surf;
   std::vector<double> dh_a, dh_d, dh_alpha;
   tamp_mlp* proposal = nullptr;           // attached proposal network (not owned)
+  // launch shapes chosen by tamp_autotune / tamp_set_tuning, keyed by the
+  // sorted (problem id, batch size) list of a launch: lanes L and warps W
+  std::map<std::vector<long long>, std::pair<int, int>> tuning;
   std::vector<uint32_t> blob;
   uint32_t* d_blob = nullptr;
   int* d_err = nullptr;
@@ -636,7 +641,18 @@ struct Plan {
   std::vector<uint32_t> items;
 };
 
-tamp_status plan_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lanes, Plan* plan) {
+std::vector<long long> job_key(const std::vector<Job>& jobs) {
+  std::vector<long long> key;
+  for (const Job& j : jobs) key.push_back((static_cast<long long>(j.pr->id) << 32) | static_cast<long long>(j.d.P));
+  std::sort(key.begin(), key.end());
+  return key;
+}
+
+// forced_L / forced_W > 0 pin the launch shape (the autotuner's trials);
+// otherwise a tuned shape for this set of problems and batch sizes is used
+// when the options leave the lane count to the library.
+tamp_status plan_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lanes, Plan* plan, int forced_L = 0,
+                      int forced_W = 0) {
   long total = 0;
   int warps = 1;
   for (const Job& j : jobs) {
@@ -644,6 +660,16 @@ tamp_status plan_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lanes
     warps = std::max(warps, optimize_warps(j.pr->K));
   }
   int L = preferred_lanes(requested_lanes, total);
+  if (forced_L > 0) {
+    L = forced_L;
+    warps = std::max(1, std::min(forced_W, warps));
+  } else if (requested_lanes == 0) {
+    auto it = s->tuning.find(job_key(jobs));
+    if (it != s->tuning.end()) {
+      L = it->second.first;
+      warps = std::max(1, std::min(it->second.second, warps));
+    }
+  }
   size_t smem = 0;
   for (; L <= 8; L *= 2) {
     size_t tile = 0;
@@ -653,6 +679,7 @@ tamp_status plan_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lanes
     if (smem <= kMaxDynSmem) break;
   }
   if (L > 8) return fail(s, TAMP_ERR_INVALID_ARG, "problem does not fit in shared memory");
+  if (forced_L > 0 && L != forced_L) return fail(s, TAMP_ERR_INVALID_ARG, "lane split %d does not fit", forced_L);
   const int PT = 32 / L;
   std::vector<int> order(jobs.size());
   for (size_t i = 0; i < jobs.size(); ++i) order[i] = static_cast<int>(i);
@@ -687,10 +714,11 @@ LaunchArgs plan_args(const tamp_scene* s, const Plan& plan, ProbDesc* d_descs, u
   return a;
 }
 
-tamp_status launch_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lanes) {
+tamp_status launch_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lanes, int forced_L = 0,
+                        int forced_W = 0) {
   if (jobs.empty()) return TAMP_OK;
   Plan plan;
-  tamp_status st = plan_jobs(s, jobs, requested_lanes, &plan);
+  tamp_status st = plan_jobs(s, jobs, requested_lanes, &plan, forced_L, forced_W);
   if (st != TAMP_OK) return st;
   if (static_cast<int>(jobs.size()) > s->descs_cap) {
     cudaFree(s->d_descs);
@@ -873,6 +901,7 @@ tamp_status tamp_set_skeleton(tamp_scene* s, const tamp_action* acts, int n, con
   }
   s->probs.push_back(pr);
   *pid = static_cast<int>(s->probs.size()) - 1;
+  pr->id = *pid;
   s->err.clear();
   return TAMP_OK;
 }
@@ -1062,6 +1091,138 @@ tamp_status tamp_eval(tamp_scene* s, int id, int n, const float* x, float* cost,
   d.gscale = 1.f; d.beta1 = pr->opt.beta1; d.beta2 = pr->opt.beta2; d.eps = pr->opt.eps;
   std::vector<Job> jobs{{pr, d}};
   return launch_jobs(s, jobs, pr->opt.lanes);
+}
+
+tamp_status tamp_autotune(tamp_scene* s, const int* ids, int n, int trial_steps, int* lanes_out, int* warps_out,
+                          float* ms_out) {
+  if (!s) return TAMP_ERR_INVALID_ARG;
+  if (!ids || n <= 0 || trial_steps <= 0 || trial_steps > 100000) return fail(s, TAMP_ERR_INVALID_ARG, "bad arguments");
+  std::vector<Problem*> prs;
+  for (int i = 0; i < n; ++i) {
+    Problem* pr = get_problem(s, ids[i]);
+    if (!pr) return fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", ids[i]);
+    if (!pr->has_batch) return fail(s, TAMP_ERR_STATE, "problem %d has no particles", ids[i]);
+    for (Problem* q : prs)
+      if (q == pr) return fail(s, TAMP_ERR_INVALID_ARG, "problem %d listed twice", ids[i]);
+    prs.push_back(pr);
+  }
+  DeviceGuard g(s->device);
+  // scratch copies of every batch: the trials must leave the problems' state alone
+  struct Scratch { float *x = nullptr, *m = nullptr, *v = nullptr, *cost = nullptr; uint8_t* flags = nullptr;
+                   int *counts = nullptr, *first = nullptr; unsigned long long* work = nullptr; };
+  std::vector<Scratch> sc(prs.size());
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto release = [&]() {
+    for (Scratch& b : sc) {
+      cudaFree(b.x); cudaFree(b.m); cudaFree(b.v); cudaFree(b.cost); cudaFree(b.flags);
+      cudaFree(b.counts); cudaFree(b.first); cudaFree(b.work);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (size_t i = 0; i < prs.size() && e == cudaSuccess; ++i) {
+    const size_t nb = static_cast<size_t>(prs[i]->D) * prs[i]->P * 4;
+    e = cudaMalloc(&sc[i].x, nb);
+    if (e == cudaSuccess) e = cudaMalloc(&sc[i].m, nb);
+    if (e == cudaSuccess) e = cudaMalloc(&sc[i].v, nb);
+    if (e == cudaSuccess) e = cudaMalloc(&sc[i].cost, static_cast<size_t>(prs[i]->P) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&sc[i].flags, static_cast<size_t>(prs[i]->P));
+    if (e == cudaSuccess) e = cudaMalloc(&sc[i].counts, static_cast<size_t>(std::max(prs[i]->NCON, 1)) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&sc[i].first, 4);
+    if (e == cudaSuccess) e = cudaMalloc(&sc[i].work, 16);
+  }
+  if (e != cudaSuccess) {
+    release();
+    return fail(s, e == cudaErrorMemoryAllocation ? TAMP_ERR_OOM : TAMP_ERR_CUDA, "autotune scratch: %s",
+                cudaGetErrorString(e));
+  }
+  std::vector<Job> jobs;
+  for (size_t i = 0; i < prs.size(); ++i) {
+    ProbDesc d = state_desc(*prs[i], trial_steps);
+    d.x_in = d.x_out = sc[i].x; d.m = sc[i].m; d.v = sc[i].v;
+    d.out_cost = sc[i].cost; d.out_flags = sc[i].flags; d.out_counts = sc[i].counts;
+    d.first_iter = sc[i].first; d.work = sc[i].work;
+    jobs.push_back({prs[i], d});
+  }
+  auto restore = [&]() {
+    cudaError_t r = cudaSuccess;
+    for (size_t i = 0; i < prs.size() && r == cudaSuccess; ++i) {
+      const size_t nb = static_cast<size_t>(prs[i]->D) * prs[i]->P * 4;
+      r = cudaMemcpyAsync(sc[i].x, prs[i]->d_x, nb, cudaMemcpyDeviceToDevice, s->stream);
+      if (r == cudaSuccess) r = cudaMemcpyAsync(sc[i].m, prs[i]->d_m, nb, cudaMemcpyDeviceToDevice, s->stream);
+      if (r == cudaSuccess) r = cudaMemcpyAsync(sc[i].v, prs[i]->d_v, nb, cudaMemcpyDeviceToDevice, s->stream);
+    }
+    return r;
+  };
+  int max_w = 1;
+  for (Problem* pr : prs) max_w = std::max(max_w, optimize_warps(pr->K));
+  std::vector<int> wc;
+  for (int per = 1; per <= 4; ++per) {
+    int kmax = 0;
+    for (Problem* pr : prs) kmax = std::max(kmax, pr->K);
+    const int w = std::min(max_w, (kmax + per - 1) / per);
+    if (std::find(wc.begin(), wc.end(), w) == wc.end()) wc.push_back(w);
+  }
+  float best = -1.f;
+  int bL = 0, bW = 0;
+  const std::string saved = s->err;
+  for (int L = 1; L <= 8; L *= 2) {
+    for (int W : wc) {
+      Plan probe;
+      if (plan_jobs(s, jobs, 0, &probe, L, W) != TAMP_OK) continue;  // does not fit: not a candidate
+      e = restore();
+      if (e == cudaSuccess && launch_jobs(s, jobs, 0, L, W) != TAMP_OK) e = cudaErrorLaunchFailure;  // warm-up
+      if (e == cudaSuccess) e = restore();
+      if (e == cudaSuccess) e = cudaEventRecord(e0, s->stream);
+      if (e == cudaSuccess && launch_jobs(s, jobs, 0, L, W) != TAMP_OK) e = cudaErrorLaunchFailure;
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        release();
+        return fail(s, TAMP_ERR_CUDA, "autotune trial L=%d W=%d: %s", L, W, cudaGetErrorString(e));
+      }
+      if (best < 0.f || ms < best) {
+        best = ms; bL = L; bW = W;
+      }
+    }
+  }
+  s->err = saved;
+  release();
+  if (best < 0.f) return fail(s, TAMP_ERR_INVALID_ARG, "no launch shape fits these problems");
+  tamp_status st = check_device_error(s);
+  if (st != TAMP_OK) return st;
+  s->tuning[job_key(jobs)] = {bL, bW};
+  if (lanes_out) *lanes_out = bL;
+  if (warps_out) *warps_out = bW;
+  if (ms_out) *ms_out = best;
+  return TAMP_OK;
+}
+
+tamp_status tamp_set_tuning(tamp_scene* s, const int* ids, int n, int lanes, int warps) {
+  if (!s) return TAMP_ERR_INVALID_ARG;
+  if (!ids || n <= 0) return fail(s, TAMP_ERR_INVALID_ARG, "bad arguments");
+  std::vector<Job> jobs;
+  for (int i = 0; i < n; ++i) {
+    Problem* pr = get_problem(s, ids[i]);
+    if (!pr) return fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", ids[i]);
+    if (!pr->has_batch) return fail(s, TAMP_ERR_STATE, "problem %d has no particles", ids[i]);
+    jobs.push_back({pr, state_desc(*pr, 1)});
+  }
+  if (lanes == 0) {
+    s->tuning.erase(job_key(jobs));
+    return TAMP_OK;
+  }
+  if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) return fail(s, TAMP_ERR_INVALID_ARG, "lanes %d", lanes);
+  if (warps < 1 || warps > 12) return fail(s, TAMP_ERR_INVALID_ARG, "warps %d", warps);
+  Plan probe;
+  tamp_status st = plan_jobs(s, jobs, 0, &probe, lanes, warps);
+  if (st != TAMP_OK) return st;
+  s->tuning[job_key(jobs)] = {lanes, warps};
+  return TAMP_OK;
 }
 
 tamp_status tamp_work_counters(tamp_scene* s, int id, uint64_t out[2]) {
