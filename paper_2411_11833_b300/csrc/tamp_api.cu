@@ -22,7 +22,7 @@ cudaError_t launch_optimize(const LaunchArgs& a, int L, int warps, int grid, siz
 cudaError_t optimize_set_smem(int L, size_t smem);
 cudaError_t launch_chunk_control(int* t_dev, const int* const* first_iters, int n_problems, int steps,
                                  int stop_on_first, int* stop, int* chunks_run, cudaStream_t st);
-size_t optimize_tile_bytes(int prob_words, int D, int NT, int L);
+size_t optimize_tile_bytes(int prob_words, int D, int NT, int NSLOT, int L);
 size_t optimize_scratch_bytes(int warps);
 int optimize_blocks_per_sm(int L, int warps, size_t smem);
 cudaError_t launch_sample(const uint32_t* pb, const uint32_t* sc, float* x, float* m, float* v, int stride, int P,
@@ -674,7 +674,8 @@ tamp_status plan_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lanes
   for (; L <= 8; L *= 2) {
     size_t tile = 0;
     for (const Job& j : jobs)
-      tile = std::max(tile, optimize_tile_bytes(static_cast<int>(j.pr->blob.size()), j.pr->D, j.pr->NT, L));
+      tile = std::max(tile, optimize_tile_bytes(static_cast<int>(j.pr->blob.size()), j.pr->D, j.pr->NT,
+                                                j.pr->NSLOT, L));
     smem = 4 * ((s->blob.size() + 3) & ~static_cast<size_t>(3)) + tile + optimize_scratch_bytes(warps);
     if (smem <= kMaxDynSmem) break;
   }
@@ -1431,7 +1432,8 @@ extern "C" tamp_status tamp_eval_static_scratch(tamp_scene* s, int id, int n, co
   size_t smem = 0;
   for (; L <= 8; L *= 2) {
     smem = 4 * ((s->blob.size() + 3) & ~static_cast<size_t>(3)) +
-           optimize_tile_bytes(static_cast<int>(pr->blob.size()), pr->D, pr->NT, L) + optimize_scratch_bytes(warps);
+           optimize_tile_bytes(static_cast<int>(pr->blob.size()), pr->D, pr->NT, pr->NSLOT, L) +
+           optimize_scratch_bytes(warps);
     if (smem <= kMaxDynSmem) break;
   }
   if (L > 8) return fail(s, TAMP_ERR_INVALID_ARG, "problem does not fit in shared memory");

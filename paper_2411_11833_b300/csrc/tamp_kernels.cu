@@ -79,7 +79,9 @@ int optimize_warps(int K);
 constexpr int QUEUE_CHUNK = 16;
 constexpr int QUEUE_CAP = 32 * QUEUE_CHUNK;
 // shared memory of one warp's WarpScratch: queue, counters (padded), accumulators
-constexpr int WARP_SCRATCH_BYTES = QUEUE_CAP * 4 + 16 + 32 * NB * 16;
+// accumulators, queue, counters (padded), then every lane's published batch:
+// its NB spheres and their bounding sphere
+constexpr int WARP_SCRATCH_BYTES = 32 * NB * 16 + QUEUE_CAP * 4 + 16 + 32 * (NB + 1) * 16;
 
 // ------------------------------------------------------------------ frame helpers
 // A frame is R (row-major 3x3) and t.  Right-multiplications used by DH:
@@ -175,6 +177,7 @@ struct WarpScratch {
   uint32_t* queue;   // QUEUE_CAP entries: owner lane << 16 | item
   int* count;        // [2]: cuboid entries, box entries
   float4* acc;       // [32][NB]: (dpen/dc x, y, z; pen)
+  float4* sph;       // [32][NB + 1]: each lane's batch (x, y, z, r) and its bounding sphere
 };
 
 // Penetration of the register batches of NB spheres held by the 32 lanes of a
@@ -201,11 +204,12 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
                                          const float4* __restrict__ obs, int O, const int* __restrict__ env,
                                          int n_env, const float* __restrict__ boxr, const int* __restrict__ slots,
                                          const float4* __restrict__ bloc, const float4* __restrict__ binit,
-                                         int NBS, const float* __restrict__ X, float* G, int pl, int sub,
+                                         int NBS, const float4* __restrict__ place, float* G, int pl, int sub,
                                          int lane, float wenv, const WarpScratch& ws, unsigned& n_obb,
                                          unsigned& n_box) {
   constexpr int PT = 32 / L;
   const int n_items = O + n_env;  // cuboids, then the other boxes
+  bool published = false;
   for (int base = 0; base < n_items; base += QUEUE_CHUNK * L) {
     // ---- broad phase over this chunk of items
     const int end = min(base + QUEUE_CHUNK * L, n_items);
@@ -223,7 +227,8 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
         if (src < 0) {
           x = br[4]; y = br[5]; z = br[6];
         } else {
-          x = X[src * PT + pl]; y = X[(src + 1) * PT + pl]; z = __int_as_float(slots[er[2] * SLOT_W + 2]);
+          const float4 pp = place[er[2] * PT + pl];
+          x = pp.x; y = pp.y; z = __int_as_float(slots[er[2] * SLOT_W + 2]);
         }
         const float dx = cbx - x, dy = cby - y, dz = cbz - z, R = Rb + br[3];
         if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R * R) {
@@ -234,27 +239,31 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
     }
     __syncwarp();
     const int n_c = ws.count[0], n_b = ws.count[1];
+    if (n_c + n_b == 0) continue;  // warp-uniform: nothing to resolve in this chunk
+    if (!published) {
+      // every lane publishes its batch once; the exact tasks read it from here
+      float4* mine = ws.sph + lane * (NB + 1);
+#pragma unroll
+      for (int s = 0; s < NB; ++s) mine[s] = make_float4(cx[s], cy[s], cz[s], cr[s]);
+      mine[NB] = make_float4(cbx, cby, cbz, Rb);
+      published = true;
+      __syncwarp();
+    }
 
-    // ---- exact phase, cuboids: one queued pair per lane per round
-    for (int r0 = 0; r0 < n_c; r0 += 32) {
-      const bool valid = r0 + lane < n_c;
-      const uint32_t ent = valid ? ws.queue[r0 + lane] : static_cast<uint32_t>(lane) << 16;
-      const int owner = static_cast<int>(ent >> 16);
-      float ox[NB], oy[NB], oz[NB], orr[NB];
-#pragma unroll
-      for (int s = 0; s < NB; ++s) {
-        ox[s] = __shfl_sync(0xffffffffu, cx[s], owner);
-        oy[s] = __shfl_sync(0xffffffffu, cy[s], owner);
-        oz[s] = __shfl_sync(0xffffffffu, cz[s], owner);
-        orr[s] = __shfl_sync(0xffffffffu, cr[s], owner);
-      }
-      if (valid) {
-        ++n_obb;
-        const Obb b = load_obb(obs, static_cast<int>(ent & 0xffffu), O);
-#pragma unroll
-        for (int s = 0; s < NB; ++s) {
+    // ---- exact phase, cuboids: one (queued pair, sphere) task per lane
+    const int Tc = n_c * NB;
+    for (int t0 = 0; t0 < Tc; t0 += 32) {
+      const int t = t0 + lane;
+      if (t < Tc) {
+        const int ci = t / NB, s = t - ci * NB;
+        const uint32_t ent = ws.queue[ci];
+        const int owner = static_cast<int>(ent >> 16);
+        if (s == 0) ++n_obb;
+        const float4 sp = ws.sph[owner * (NB + 1) + s];
+        if (sp.w > 0.f) {
+          const Obb b = load_obb(obs, static_cast<int>(ent & 0xffffu), O);
           float px_, py_, pz_;
-          const float pen = obb_pen(b, ox[s], oy[s], oz[s], orr[s], px_, py_, pz_);
+          const float pen = obb_pen(b, sp.x, sp.y, sp.z, sp.w, px_, py_, pz_);
           if (pen > 0.f) {
             float4* a = &ws.acc[owner * NB + s];
             atomicAdd(&a->x, px_);
@@ -266,84 +275,65 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
       }
     }
 
-    // ---- exact phase, other boxes: pen = max(0, r_a + r_b - ||c_a - c_b||); each
-    // of the box's spheres is first checked against the owner's batch bound
-    for (int r0 = 0; r0 < n_b; r0 += 32) {
-      const bool valid = r0 + lane < n_b;
-      const uint32_t ent = valid ? ws.queue[QUEUE_CAP - 1 - (r0 + lane)] : static_cast<uint32_t>(lane) << 16;
-      const int owner = static_cast<int>(ent >> 16);
-      float ox[NB], oy[NB], oz[NB], orr[NB];
-#pragma unroll
-      for (int s = 0; s < NB; ++s) {
-        ox[s] = __shfl_sync(0xffffffffu, cx[s], owner);
-        oy[s] = __shfl_sync(0xffffffffu, cy[s], owner);
-        oz[s] = __shfl_sync(0xffffffffu, cz[s], owner);
-        orr[s] = __shfl_sync(0xffffffffu, cr[s], owner);
-      }
-      const float obx = __shfl_sync(0xffffffffu, cbx, owner), oby = __shfl_sync(0xffffffffu, cby, owner);
-      const float obz = __shfl_sync(0xffffffffu, cbz, owner), oR = __shfl_sync(0xffffffffu, Rb, owner);
-      if (valid) {
-        ++n_box;
+    // ---- exact phase, other boxes: one (queued pair, box sphere) task per lane;
+    // pen = max(0, r_a + r_b - ||c_a - c_b||) against the owner's NB spheres,
+    // after a check of the box sphere against the owner's batch bound
+    const int Tb = n_b * NBS;
+    for (int t0 = 0; t0 < Tb; t0 += 32) {
+      const int t = t0 + lane;
+      if (t < Tb) {
+        const int bi = t / NBS, e = t - bi * NBS;
+        const uint32_t ent = ws.queue[QUEUE_CAP - 1 - bi];
+        const int owner = static_cast<int>(ent >> 16);
+        if (e == 0) ++n_box;
         const int opl = owner / L;  // the owner's particle in the tile
         const int* er = env + (static_cast<int>(ent & 0xffffu) - O) * ENV_W;
         const int j = er[0], src = er[1];
-        // a box on a placement variable: its spheres in the world from (x, y, yaw)
-        float bx = 0.f, by = 0.f, bz = 0.f, sn = 0.f, cs = 1.f;
-        if (src >= 0) {
-          bx = X[src * PT + opl];
-          by = X[(src + 1) * PT + opl];
-          bz = __int_as_float(slots[er[2] * SLOT_W + 2]);
-          sincosf(X[(src + 2) * PT + opl], &sn, &cs);
+        float4 c;
+        float bx = 0.f, by = 0.f;
+        if (src < 0) {
+          c = binit[j * NBS + e];
+        } else {
+          // a box on a placement variable: its sphere in the world from (x, y, yaw)
+          const float4 pp = place[er[2] * PT + opl];
+          const float4 l = bloc[j * NBS + e];
+          bx = pp.x;
+          by = pp.y;
+          c = make_float4(bx + fmaf(pp.z, l.x, -pp.w * l.y), by + fmaf(pp.w, l.x, pp.z * l.y),
+                          __int_as_float(slots[er[2] * SLOT_W + 2]) + l.z, l.w);
         }
-        float ag[NB][4];
-#pragma unroll
-        for (int s = 0; s < NB; ++s) ag[s][0] = ag[s][1] = ag[s][2] = ag[s][3] = 0.f;
-        float fx = 0.f, fy = 0.f, tq = 0.f;  // push on a moving box: force, torque about its centre
-        for (int e = 0; e < NBS; ++e) {
-          float4 c;
-          if (src < 0) {
-            c = binit[j * NBS + e];
-          } else {
-            const float4 l = bloc[j * NBS + e];
-            c = make_float4(bx + fmaf(cs, l.x, -sn * l.y), by + fmaf(sn, l.x, cs * l.y), bz + l.z, l.w);
-          }
-          const float ex = obx - c.x, ey = oby - c.y, ez = obz - c.z, Re = oR + c.w;
-          if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) >= Re * Re) continue;
+        const float4 ob = ws.sph[owner * (NB + 1) + NB];
+        const float ex = ob.x - c.x, ey = ob.y - c.y, ez = ob.z - c.z, Re = ob.w + c.w;
+        if (c.w >= 0.f && fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < Re * Re) {
+          float fx = 0.f, fy = 0.f, tq = 0.f;  // push on a moving box: force, torque about its centre
 #pragma unroll
           for (int s = 0; s < NB; ++s) {
-            const float dx = ox[s] - c.x, dy = oy[s] - c.y, dz = oz[s] - c.z;
+            const float4 sp = ws.sph[owner * (NB + 1) + s];
+            const float dx = sp.x - c.x, dy = sp.y - c.y, dz = sp.z - c.z;
             const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float Rs = orr[s] + c.w;
-            if (Rs > 0.f && d2 < Rs * Rs) {
+            const float Rs = sp.w + c.w;
+            if (sp.w > 0.f && Rs > 0.f && d2 < Rs * Rs) {
               const float d = sqrtf(d2);
-              ag[s][3] += Rs - d;
+              float vx = 0.f, vy = 0.f, vz = 0.f;
               if (d > 0.f) {
                 const float inv = 1.f / d;
-                const float vx = dx * inv, vy = dy * inv, vz = dz * inv;
-                ag[s][0] -= vx;
-                ag[s][1] -= vy;
-                ag[s][2] -= vz;
+                vx = dx * inv; vy = dy * inv; vz = dz * inv;
                 fx += vx;
                 fy += vy;
                 tq = fmaf(c.x - bx, vy, fmaf(-(c.y - by), vx, tq));
               }
+              float4* a = &ws.acc[owner * NB + s];
+              atomicAdd(&a->x, -vx);
+              atomicAdd(&a->y, -vy);
+              atomicAdd(&a->z, -vz);
+              atomicAdd(&a->w, Rs - d);
             }
           }
-        }
-#pragma unroll
-        for (int s = 0; s < NB; ++s) {
-          if (ag[s][3] > 0.f) {
-            float4* a = &ws.acc[owner * NB + s];
-            atomicAdd(&a->x, ag[s][0]);
-            atomicAdd(&a->y, ag[s][1]);
-            atomicAdd(&a->z, ag[s][2]);
-            atomicAdd(&a->w, ag[s][3]);
+          if (src >= 0 && (fx != 0.f || fy != 0.f || tq != 0.f)) {
+            atomicAdd(&G[src * PT + opl], wenv * fx);
+            atomicAdd(&G[(src + 1) * PT + opl], wenv * fy);
+            atomicAdd(&G[(src + 2) * PT + opl], wenv * tq);
           }
-        }
-        if (src >= 0 && (fx != 0.f || fy != 0.f || tq != 0.f)) {
-          atomicAdd(&G[src * PT + opl], wenv * fx);
-          atomicAdd(&G[(src + 1) * PT + opl], wenv * fy);
-          atomicAdd(&G[(src + 2) * PT + opl], wenv * tq);
         }
       }
     }
@@ -357,16 +347,18 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
   // ---- each lane collects (and clears) its accumulators
   __syncwarp();
   float J = 0.f;
+  if (published) {
 #pragma unroll
-  for (int s = 0; s < NB; ++s) {
-    const float4 a = ws.acc[lane * NB + s];
-    gx[s] += a.x;
-    gy[s] += a.y;
-    gz[s] += a.z;
-    J += a.w;
-    ws.acc[lane * NB + s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int s = 0; s < NB; ++s) {
+      const float4 a = ws.acc[lane * NB + s];
+      gx[s] += a.x;
+      gy[s] += a.y;
+      gz[s] += a.z;
+      J += a.w;
+      ws.acc[lane * NB + s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncwarp();
   }
-  __syncwarp();
   return J;
 }
 
@@ -399,7 +391,8 @@ __device__ __forceinline__ float bound_dist(const float (&v)[N], const float (&l
 template <int L>
 __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __restrict__ pb, int k,
                             const float* __restrict__ X, float* G, float* Tm, const int* __restrict__ slots,
-                            const WarpScratch& ws, unsigned& n_obb, unsigned& n_box, int lane, int pl, int sub) {
+                            const float4* __restrict__ place, const WarpScratch& ws, unsigned& n_obb,
+                            unsigned& n_box, int lane, int pl, int sub) {
   constexpr int PT = 32 / L;
   const int nj = sc[SH_NJ];
   const float* arm = reinterpret_cast<const float*>(sc + sc[SH_OFF_ARM]);
@@ -619,7 +612,7 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
     }
     const float wenv = phase == 3 ? w_cp : w_cf;
     const float Jb = collide<L>(cx, cyy, cz, cr, gx, gyy, gz, cbx, cby, cbz, Rb, obs, O, env, n_env, boxr, slots,
-                                bloc, binit, NBS, X, G, pl, sub, lane, wenv, ws, n_obb, n_box);
+                                bloc, binit, NBS, place, G, pl, sub, lane, wenv, ws, n_obb, n_box);
     if (phase == 3) {
       J_place += Jb;
 #pragma unroll
@@ -817,6 +810,10 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
   float* sg = sv + D * PT;
   float* st = sg + D * PT;
   int* sflag = reinterpret_cast<int*>(st + NT * PT);
+  // pose of every placed box of every particle at the current iterate: (x, y,
+  // cos yaw, sin yaw), refreshed at the start of each iteration
+  float4* splace = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(sflag) + ((PT * 4 + 15) & ~15));
+  const int NSLOT = s_pb[PH_NSLOT];
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int w = tid >> 5, lane = tid & 31, W = nthr >> 5;
   const int pl = lane / L, sub = lane % L;
@@ -835,6 +832,7 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
     }
     sx[i] = xv; sm[i] = mv; sv[i] = vv; sg[i] = 0.f;
   }
+  __syncthreads();  // the tile is loaded before the placement poses are read from it
   const uint32_t* terms = s_pb + s_pb[PH_OFF_TERMS];
   const float* lr = reinterpret_cast<const float*>(s_pb + s_pb[PH_OFF_LR]);
   const int* slots = reinterpret_cast<const int*>(s_pb + s_pb[PH_OFF_SLOT]);
@@ -844,9 +842,16 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
 
   for (int it = 0;; ++it) {
     for (int i = tid; i < NT * PT; i += nthr) st[i] = 0.f;  // CFreePlace terms are sums over two warps
+    for (int i = tid; i < NSLOT * PT; i += nthr) {
+      const int si = i / PT, p = i - si * PT;
+      const int off = slots[si * SLOT_W + 1];
+      float sn, cs;
+      sincosf(sx[(off + 2) * PT + p], &sn, &cs);
+      splace[i] = make_float4(sx[off * PT + p], sx[(off + 1) * PT + p], cs, sn);
+    }
     __syncthreads();
     for (int k = w; k < K; k += W)
-      eval_config<L>(s_sc, s_pb, k, sx, sg, st, slots, ws, n_obb, n_box, lane, pl, sub);
+      eval_config<L>(s_sc, s_pb, k, sx, sg, st, slots, splace, ws, n_obb, n_box, lane, pl, sub);
     if (w == goal_warp && sub == 0) eval_goal<L>(s_sc, s_pb, sx, sg, st, pl);
     __syncthreads();
     // Eq. 3 at x_t
@@ -970,6 +975,7 @@ __global__ void __launch_bounds__(384, 1) optimize_kernel(LaunchArgs a) {
     ws.acc = reinterpret_cast<float4*>(base);
     ws.queue = reinterpret_cast<uint32_t*>(base + 32 * NB * 16);
     ws.count = reinterpret_cast<int*>(base + 32 * NB * 16 + QUEUE_CAP * 4);
+    ws.sph = reinterpret_cast<float4*>(base + 32 * NB * 16 + QUEUE_CAP * 4 + 16);
     for (int i = lane; i < 32 * NB; i += 32) ws.acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (lane == 0) { ws.count[0] = 0; ws.count[1] = 0; }
   }
@@ -1375,10 +1381,11 @@ cudaError_t launch_sample_proposal(const uint32_t* rows, int R, const float* out
 
 // Dynamic shared memory: scene tables, the largest problem's tables and tile
 // (x, m, v, gradient, terms, flags), then the warps' exact-phase scratch.
-size_t optimize_tile_bytes(int prob_words, int D, int NT, int L) {
+size_t optimize_tile_bytes(int prob_words, int D, int NT, int NSLOT, int L) {
   const int PT = 32 / L;
   const size_t pw = (prob_words + 3) & ~3;
-  return 4 * pw + 4 * (4 * static_cast<size_t>(D) * PT + static_cast<size_t>(NT) * PT) + ((PT * 4 + 15) & ~15);
+  return 4 * pw + 4 * (4 * static_cast<size_t>(D) * PT + static_cast<size_t>(NT) * PT) + ((PT * 4 + 15) & ~15) +
+         16 * static_cast<size_t>(NSLOT) * PT;
 }
 size_t optimize_scratch_bytes(int warps) { return static_cast<size_t>(WARP_SCRATCH_BYTES) * warps; }
 
