@@ -248,9 +248,17 @@ tamp_status build_scene_blob(tamp_scene* s, const tamp_scene_desc* d) {
       const double* l = d->box_spheres + (b * NBS + e) * 4;
       rb = std::max(rb, std::sqrt(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]) + l[3]);
     }
+    double hull[3] = {0.0, 0.0, 0.0};  // box-frame half extents holding every (real) sphere
+    for (int e = 0; e < NBS; ++e) {
+      const double* l = d->box_spheres + (b * NBS + e) * 4;
+      if (l[3] < 0.0) continue;
+      for (int a = 0; a < 3; ++a) hull[a] = std::max(hull[a], std::fabs(l[a]) + l[3]);
+    }
     push_f(v, h[0]); push_f(v, h[1]); push_f(v, h[2]); push_f(v, rb * (1.0 + 1e-5) + 1e-5);
     push_f(v, p[0]); push_f(v, p[1]); push_f(v, p[2]); push_f(v, p[3]);
-    push_f(v, std::cos(p[3])); push_f(v, std::sin(p[3])); v.push_back(0); v.push_back(0);
+    push_f(v, std::cos(p[3])); push_f(v, std::sin(p[3]));
+    for (int a = 0; a < 3; ++a) push_f(v, hull[a] * (1.0 + 1e-5) + 1e-5);
+    for (int k = 13; k < BOX_W; ++k) v.push_back(0);
   }
   align4(v);
   v[SH_OFF_BLOC] = static_cast<uint32_t>(v.size());

@@ -33,8 +33,9 @@ constexpr float DUMMY_FAR = 1.0e4f;
 // obstacles: 16 floats each -- t' = R^T t (3), R row-major (9), half extents (3), pad
 constexpr int OBS_W = 16;
 // box record: half x,y,z, bounding radius of its spheres about its centre,
-// init x,y,z,yaw, cos(yaw), sin(yaw), pad, pad
-constexpr int BOX_W = 12;
+// init x,y,z,yaw, cos(yaw), sin(yaw), then the half extents (box frame, about
+// the centre) of a box that holds every sphere of the model, pad
+constexpr int BOX_W = 16;
 // box spheres: local (x, y, z, r) per box, and the same at the initial pose in the world
 // surface record: cx, cy, yaw, hx, hy, z_top, cos(yaw), sin(yaw)
 constexpr int SURF_W = 8;

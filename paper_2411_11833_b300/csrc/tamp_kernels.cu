@@ -220,18 +220,24 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
           ws.queue[q] = static_cast<uint32_t>(lane) << 16 | static_cast<uint32_t>(i);
         }
       } else {
+        // the batch bound against the other box's bounding sphere and against the
+        // oriented box holding its spheres (centre, yaw, sphere hull); a contact
+        // needs both: |d| < Rb + r_box and ||max(|u| - hull, 0)|| < Rb
         const int* er = env + (i - O) * ENV_W;
         const int src = er[1];
         const float* br = boxr + er[0] * BOX_W;
-        float x, y, z;
+        float x, y, z, cy_, sy_;
         if (src < 0) {
-          x = br[4]; y = br[5]; z = br[6];
+          x = br[4]; y = br[5]; z = br[6]; cy_ = br[8]; sy_ = br[9];
         } else {
           const float4 pp = place[er[2] * PT + pl];
-          x = pp.x; y = pp.y; z = __int_as_float(slots[er[2] * SLOT_W + 2]);
+          x = pp.x; y = pp.y; z = __int_as_float(slots[er[2] * SLOT_W + 2]); cy_ = pp.z; sy_ = pp.w;
         }
         const float dx = cbx - x, dy = cby - y, dz = cbz - z, R = Rb + br[3];
-        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R * R) {
+        const float ux = fmaf(cy_, dx, sy_ * dy), uy = fmaf(-sy_, dx, cy_ * dy);
+        const float qx = fmaxf(fabsf(ux) - br[10], 0.f), qy = fmaxf(fabsf(uy) - br[11], 0.f);
+        const float qz = fmaxf(fabsf(dz) - br[12], 0.f);
+        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R * R && fmaf(qx, qx, fmaf(qy, qy, qz * qz)) < Rb * Rb) {
           const int q = atomicAdd(&ws.count[1], 1);
           ws.queue[QUEUE_CAP - 1 - q] = static_cast<uint32_t>(lane) << 16 | static_cast<uint32_t>(i);
         }
@@ -278,11 +284,11 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
     // ---- exact phase, other boxes: one (queued pair, box sphere) task per lane;
     // pen = max(0, r_a + r_b - ||c_a - c_b||) against the owner's NB spheres,
     // after a check of the box sphere against the owner's batch bound
-    const int Tb = n_b * NBS;
+    const int Tb = n_b * MAX_NBS;  // MAX_NBS = 8 task slots per box: the index splits by shift and mask
     for (int t0 = 0; t0 < Tb; t0 += 32) {
       const int t = t0 + lane;
-      if (t < Tb) {
-        const int bi = t / NBS, e = t - bi * NBS;
+      const int bi = t >> 3, e = t & (MAX_NBS - 1);
+      if (t < Tb && e < NBS) {
         const uint32_t ent = ws.queue[QUEUE_CAP - 1 - bi];
         const int owner = static_cast<int>(ent >> 16);
         if (e == 0) ++n_box;
