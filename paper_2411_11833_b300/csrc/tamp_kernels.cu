@@ -281,59 +281,70 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
       }
     }
 
-    // ---- exact phase, other boxes: one (queued pair, box sphere) task per lane;
-    // pen = max(0, r_a + r_b - ||c_a - c_b||) against the owner's NB spheres,
-    // after a check of the box sphere against the owner's batch bound
-    const int Tb = n_b * MAX_NBS;  // MAX_NBS = 8 task slots per box: the index splits by shift and mask
+    // ---- exact phase, other boxes: one (queued pair, owner sphere) task per lane.
+    // The sphere is first tested against the oriented box that holds every
+    // sphere of the other box's model (any contact needs it within r of that
+    // box); only then against the model's spheres:
+    // pen = max(0, r_a + r_b - ||c_a - c_b||)
+    const int Tb = n_b * NB;
     for (int t0 = 0; t0 < Tb; t0 += 32) {
       const int t = t0 + lane;
-      const int bi = t >> 3, e = t & (MAX_NBS - 1);
-      if (t < Tb && e < NBS) {
+      if (t < Tb) {
+        const int bi = t / NB, s = t - bi * NB;
         const uint32_t ent = ws.queue[QUEUE_CAP - 1 - bi];
         const int owner = static_cast<int>(ent >> 16);
-        if (e == 0) ++n_box;
+        if (s == 0) ++n_box;
+        const float4 sp = ws.sph[owner * (NB + 1) + s];
         const int opl = owner / L;  // the owner's particle in the tile
         const int* er = env + (static_cast<int>(ent & 0xffffu) - O) * ENV_W;
         const int j = er[0], src = er[1];
-        float4 c;
-        float bx = 0.f, by = 0.f;
+        const float* br = boxr + j * BOX_W;
+        float bx, by, bz, cy_, sy_;
         if (src < 0) {
-          c = binit[j * NBS + e];
+          bx = br[4]; by = br[5]; bz = br[6]; cy_ = br[8]; sy_ = br[9];
         } else {
-          // a box on a placement variable: its sphere in the world from (x, y, yaw)
           const float4 pp = place[er[2] * PT + opl];
-          const float4 l = bloc[j * NBS + e];
-          bx = pp.x;
-          by = pp.y;
-          c = make_float4(bx + fmaf(pp.z, l.x, -pp.w * l.y), by + fmaf(pp.w, l.x, pp.z * l.y),
-                          __int_as_float(slots[er[2] * SLOT_W + 2]) + l.z, l.w);
+          bx = pp.x; by = pp.y; bz = __int_as_float(slots[er[2] * SLOT_W + 2]); cy_ = pp.z; sy_ = pp.w;
         }
-        const float4 ob = ws.sph[owner * (NB + 1) + NB];
-        const float ex = ob.x - c.x, ey = ob.y - c.y, ez = ob.z - c.z, Re = ob.w + c.w;
-        if (c.w >= 0.f && fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < Re * Re) {
+        const float dx0 = sp.x - bx, dy0 = sp.y - by, dz0 = sp.z - bz;
+        const float ux = fmaf(cy_, dx0, sy_ * dy0), uy = fmaf(-sy_, dx0, cy_ * dy0);
+        const float qx = fmaxf(fabsf(ux) - br[10], 0.f), qy = fmaxf(fabsf(uy) - br[11], 0.f);
+        const float qz = fmaxf(fabsf(dz0) - br[12], 0.f);
+        if (sp.w > 0.f && fmaf(qx, qx, fmaf(qy, qy, qz * qz)) < sp.w * sp.w) {
+          float ax = 0.f, ay = 0.f, az = 0.f, pen = 0.f;
           float fx = 0.f, fy = 0.f, tq = 0.f;  // push on a moving box: force, torque about its centre
-#pragma unroll
-          for (int s = 0; s < NB; ++s) {
-            const float4 sp = ws.sph[owner * (NB + 1) + s];
+          for (int e = 0; e < NBS; ++e) {
+            float4 c;
+            if (src < 0) {
+              c = binit[j * NBS + e];
+            } else {
+              const float4 l = bloc[j * NBS + e];
+              c = make_float4(bx + fmaf(cy_, l.x, -sy_ * l.y), by + fmaf(sy_, l.x, cy_ * l.y), bz + l.z, l.w);
+            }
             const float dx = sp.x - c.x, dy = sp.y - c.y, dz = sp.z - c.z;
             const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const float Rs = sp.w + c.w;
-            if (sp.w > 0.f && Rs > 0.f && d2 < Rs * Rs) {
+            if (c.w >= 0.f && d2 < Rs * Rs) {
               const float d = sqrtf(d2);
-              float vx = 0.f, vy = 0.f, vz = 0.f;
+              pen += Rs - d;
               if (d > 0.f) {
                 const float inv = 1.f / d;
-                vx = dx * inv; vy = dy * inv; vz = dz * inv;
+                const float vx = dx * inv, vy = dy * inv, vz = dz * inv;
+                ax -= vx;
+                ay -= vy;
+                az -= vz;
                 fx += vx;
                 fy += vy;
                 tq = fmaf(c.x - bx, vy, fmaf(-(c.y - by), vx, tq));
               }
-              float4* a = &ws.acc[owner * NB + s];
-              atomicAdd(&a->x, -vx);
-              atomicAdd(&a->y, -vy);
-              atomicAdd(&a->z, -vz);
-              atomicAdd(&a->w, Rs - d);
             }
+          }
+          if (pen > 0.f) {
+            float4* a = &ws.acc[owner * NB + s];
+            atomicAdd(&a->x, ax);
+            atomicAdd(&a->y, ay);
+            atomicAdd(&a->z, az);
+            atomicAdd(&a->w, pen);
           }
           if (src >= 0 && (fx != 0.f || fy != 0.f || tq != 0.f)) {
             atomicAdd(&G[src * PT + opl], wenv * fx);
