@@ -853,7 +853,9 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
   const uint32_t* terms = s_pb + s_pb[PH_OFF_TERMS];
   const float* lr = reinterpret_cast<const float*>(s_pb + s_pb[PH_OFF_LR]);
   const int* slots = reinterpret_cast<const int*>(s_pb + s_pb[PH_OFF_SLOT]);
-  const int goal_warp = (K - 1) % W;
+  // the goal cost goes to a warp with fewer or lighter configurations: the last
+  // warp when the configurations do not divide evenly, else warp 0 (a Pick)
+  const int goal_warp = K % W != 0 ? W - 1 : 0;
   double b1t = pow(static_cast<double>(d.beta1), t0), b2t = pow(static_cast<double>(d.beta2), t0);
   unsigned n_obb = 0, n_box = 0;  // broad-phase candidates resolved exactly (work accounting)
 
