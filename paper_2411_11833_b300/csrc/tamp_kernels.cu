@@ -398,15 +398,22 @@ __device__ __forceinline__ float bound_dist(const float (&v)[N], const float (&l
 }
 
 // ------------------------------------------------------------------ one configuration
-// Sphere batches of one configuration are visited by one loop (a single inlined
+// A configuration is evaluated in two independent pieces so that warps can
+// balance them dynamically:
+//   head (piece 0)  Kin, the held box and links n .. m + 1, plus the scalar
+//                   terms (joint limits, grasp bounds or containment)
+//   tail (piece 1)  links m .. 1, the base spheres and the placed box
+// Each piece sweeps from its top link down to joint 1: after each link the
+// joint's torque dJ/dq_l = z.M + (o x z).F is taken from the wrench of the
+// piece's own spheres so far, so the two pieces' torques add up to the
+// configuration's.  Sphere batches are visited by one loop (a single inlined
 // copy of the collision code keeps the kernel small):
-//   phase 0  the held box, in the object frame FK(q) G(g)^-1
-//   phase 1  links n .. 1 (tip to base); after each link its joint torque is
-//            taken from the accumulated wrench and the frame steps to T_{l-1}
-//   phase 2  spheres fixed to the base (cost only)
-//   phase 3  the placed box at P(p) (Place configurations: CFreePlace)
+//   phase 0  the held box, in the object frame FK(q) G(g)^-1 (head)
+//   phase 1  links (tip to base); the frame steps back to T_{l-1} after each
+//   phase 2  spheres fixed to the base (tail, cost only)
+//   phase 3  the placed box at P(p) (tail of a Place: CFreePlace)
 template <int L>
-__device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __restrict__ pb, int k,
+__device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __restrict__ pb, int k, int piece,
                             const float* __restrict__ X, float* G, float* Tm, const int* __restrict__ slots,
                             const float4* __restrict__ place, const WarpScratch& ws, unsigned& n_obb,
                             unsigned& n_box, int lane, int pl, int sub) {
@@ -434,15 +441,19 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   const float w_cf = tw(terms, cf[CF_T_CF]), w_jl = tw(terms, cf[CF_T_JL]), w_x = tw(terms, cf[CF_T_X]);
   const int cp_src = cf[CF_CP_SRC], cp_first = cf[CF_CP_FIRST], cp_count = cp_src >= 0 ? cf[CF_CP_COUNT] : 0;
   const float w_cp = cp_count > 0 ? tw(terms, cf[CF_CP_T]) : 0.f;
-  const float k0 = sub == 0 ? 1.f : 0.f;  // terms computed redundantly count on lane 0 only
+  const bool head = piece == 0;
+  const int m = (nj + 1) / 2;  // the tail's top link
+  // terms computed redundantly count on lane 0 only; Kin belongs to the head
+  const float k0 = (sub == 0 && head) ? 1.f : 0.f;
 #define XV(c) X[(c) * PT + pl]
 
-  // ---------------- forward kinematics T_0 .. T_n
+  // ---------------- forward kinematics T_0 .. T_n (the tail stops at T_m)
   float R[9], t[3];
 #pragma unroll
   for (int i = 0; i < 9; ++i) R[i] = arm[i];
   t[0] = arm[9]; t[1] = arm[10]; t[2] = arm[11];
-  for (int j = 0; j < nj; ++j) {
+  const int jtop = head ? nj : m;
+  for (int j = 0; j < jtop; ++j) {
     const float* Jp = arm + 24 + j * ARM_JW;
     float sj, cj;
     sincosf(XV(qo + j) + Jp[4], &sj, &cj);
@@ -533,13 +544,14 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   // placed box (phase 3), which overwrites (R, t) with P(p) once the links are done.
   // A held-box sphere l (object frame) is first moved into frame n:
   // l' = tool (G(g)^-1 l) = t_tool + R_tool R_G (l - g).
-  int phase = 0, l = nj;
-  int s0 = 0, s1 = nbs_pad;
+  int phase = head ? 0 : 1, l = head ? nj : m;
+  int s0 = head ? 0 : sc[SH_LINK0 + m], s1 = head ? nbs_pad : sc[SH_LINK0 + m + 1];
   for (;;) {
     if (s0 >= s1) {
       if (phase == 0) {
         phase = 1;
         s0 = sc[SH_LINK0 + l]; s1 = sc[SH_LINK0 + l + 1];
+        if (l <= m) s0 = s1 = 0;  // an arm of at most one link: the tail has it
       } else if (phase == 1) {
         // joint l: T_{l-1} = T_l Rx(-alpha) Tx(-a) Tz(-d) Rz(-theta); it turns the
         // links >= l about z_{l-1} through o_{l-1}: dJ/dq_l = z.M + (o x z).F
@@ -560,7 +572,8 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
         --l;
         if (l == 0) phase = 2;
         s0 = sc[SH_LINK0 + l]; s1 = sc[SH_LINK0 + l + 1];
-      } else if (phase == 2 && cp_count > 0) {
+        if (head && l <= m) s0 = s1 = 0;  // the tail's links (and the base): torques only
+      } else if (phase == 2 && cp_count > 0 && !head) {
         phase = 3;
         s0 = cp_first; s1 = cp_first + (cp_count + NB - 1) / NB * NB;
         float sp, cp;
@@ -687,10 +700,14 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
     for (int i = 0; i < 3; ++i) gcp[i] += __shfl_xor_sync(0xffffffffu, gcp[i], m);
   }
   if (sub != 0) return;
-  if (cp_count > 0) {
-    atomicAdd(&Tm[cf[CF_CP_T] * PT + pl], J_place);
+  atomicAdd(&Tm[cf[CF_T_CF] * PT + pl], J_hold);
+  if (!head) {
+    if (cp_count > 0) {
+      atomicAdd(&Tm[cf[CF_CP_T] * PT + pl], J_place);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) atomicAdd(&G[(cp_src + i) * PT + pl], gcp[i]);
+      for (int i = 0; i < 3; ++i) atomicAdd(&G[(cp_src + i) * PT + pl], gcp[i]);
+    }
+    return;
   }
 
   // ---------------- per-configuration scalar terms (lane 0)
@@ -722,7 +739,6 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   }
   Tm[cf[CF_T_KP] * PT + pl] = e_pos;
   Tm[cf[CF_T_KR] * PT + pl] = e_rot;
-  Tm[cf[CF_T_CF] * PT + pl] = J_hold;
   Tm[cf[CF_T_JL] * PT + pl] = jl;
   const float* br = boxr + b * BOX_W;
   if (kind == 0) {
@@ -832,7 +848,7 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
   float4* splace = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(sflag) + ((PT * 4 + 15) & ~15));
   const int NSLOT = s_pb[PH_NSLOT];
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int w = tid >> 5, lane = tid & 31, W = nthr >> 5;
+  const int lane = tid & 31;
   const int pl = lane / L, sub = lane % L;
   const int tile0 = tile * PT;
   const int t0 = d.t_dev ? *d.t_dev : d.t0;
@@ -853,14 +869,17 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
   const uint32_t* terms = s_pb + s_pb[PH_OFF_TERMS];
   const float* lr = reinterpret_cast<const float*>(s_pb + s_pb[PH_OFF_LR]);
   const int* slots = reinterpret_cast<const int*>(s_pb + s_pb[PH_OFF_SLOT]);
-  // the goal cost goes to a warp with fewer or lighter configurations: the last
-  // warp when the configurations do not divide evenly, else warp 0 (a Pick)
-  const int goal_warp = K % W != 0 ? W - 1 : 0;
+  // work items of an evaluation pass: two pieces per configuration, later
+  // configurations first (their environments hold more placed boxes), then the
+  // goal cost; warps pull them from a counter so that they finish together
+  __shared__ int s_next;
+  const int n_work = 2 * K + (s_pb[PH_GOAL_T] != 0xffffffffu ? 1 : 0);
   double b1t = pow(static_cast<double>(d.beta1), t0), b2t = pow(static_cast<double>(d.beta2), t0);
   unsigned n_obb = 0, n_box = 0;  // broad-phase candidates resolved exactly (work accounting)
 
   for (int it = 0;; ++it) {
-    for (int i = tid; i < NT * PT; i += nthr) st[i] = 0.f;  // CFreePlace terms are sums over two warps
+    if (tid == 0) s_next = 0;
+    for (int i = tid; i < NT * PT; i += nthr) st[i] = 0.f;  // collision terms are sums over pieces
     for (int i = tid; i < NSLOT * PT; i += nthr) {
       const int si = i / PT, p = i - si * PT;
       const int off = slots[si * SLOT_W + 1];
@@ -869,9 +888,17 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
       splace[i] = make_float4(sx[off * PT + p], sx[(off + 1) * PT + p], cs, sn);
     }
     __syncthreads();
-    for (int k = w; k < K; k += W)
-      eval_config<L>(s_sc, s_pb, k, sx, sg, st, slots, splace, ws, n_obb, n_box, lane, pl, sub);
-    if (w == goal_warp && sub == 0) eval_goal<L>(s_sc, s_pb, sx, sg, st, pl);
+    for (;;) {
+      int item = 0;
+      if (lane == 0) item = atomicAdd(&s_next, 1);
+      item = __shfl_sync(0xffffffffu, item, 0);
+      if (item >= n_work) break;
+      if (item < 2 * K)
+        eval_config<L>(s_sc, s_pb, K - 1 - (item >> 1), item & 1, sx, sg, st, slots, splace, ws, n_obb, n_box,
+                       lane, pl, sub);
+      else if (sub == 0)
+        eval_goal<L>(s_sc, s_pb, sx, sg, st, pl);
+    }
     __syncthreads();
     // Eq. 3 at x_t
     if (w == 0) {
