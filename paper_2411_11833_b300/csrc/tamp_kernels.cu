@@ -848,7 +848,7 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
   float4* splace = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(sflag) + ((PT * 4 + 15) & ~15));
   const int NSLOT = s_pb[PH_NSLOT];
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int lane = tid & 31;
+  const int w = tid >> 5, lane = tid & 31;
   const int pl = lane / L, sub = lane % L;
   const int tile0 = tile * PT;
   const int t0 = d.t_dev ? *d.t_dev : d.t0;
