@@ -488,9 +488,9 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   const float rgx = fmaf(cy, gxv, -sy * gyv), rgy = fmaf(sy, gxv, cy * gyv);
   float s2, c2;
   sincosf(pyaw + gyaw, &s2, &c2);
-  float F[3], Mw[3], gg[4], gp[3];
-  float e_pos, e_rot;
-  {
+  float F[3] = {0.f, 0.f, 0.f}, Mw[3] = {0.f, 0.f, 0.f}, gg[4] = {0.f, 0.f, 0.f, 0.f}, gp[3] = {0.f, 0.f, 0.f};
+  float e_pos = 0.f, e_rot = 0.f;
+  if (head) {
     const float ttx = px + rgx, tty = py + rgy, ttz = pz + gzv;
     // M = Re^T R_tgt, R_tgt = [[c2, s2, 0], [s2, -c2, 0], [0, 0, -1]]
     float Mr[9];
