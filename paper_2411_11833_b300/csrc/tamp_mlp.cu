@@ -29,7 +29,10 @@ namespace mlpk {
 
 constexpr int IN = 48, H = 256, OUT = 32, NTGT = 16;
 constexpr int ROWS = 128;    // samples per CTA tile = MMA M
-constexpr int THREADS = 128; // one warpgroup: thread t owns tile row / TMEM lane t
+// 16 warps: warp w reads the TMEM lanes (tile rows) 32 (w % 4) .. + 31 and the
+// column group w / 4 of the accumulator in the epilogues
+constexpr int THREADS = 512;
+constexpr int NGRP = THREADS / 128;
 constexpr int TMEM_COLS = 256;
 constexpr size_t SMEM_A = 128 * 256 * 2;   // largest A operand (128 x 256 bf16)
 constexpr size_t SMEM_B = 256 * 256 * 2;   // largest B operand (256 x 256 bf16)
@@ -43,6 +46,15 @@ __host__ __device__ constexpr size_t w_off(int l) {
 }
 __host__ __device__ constexpr size_t b_off(int l) { return w_off(l) + (size_t)ndim(l) * kdim(l); }
 constexpr size_t N_PARAMS = w_off(3) + (size_t)OUT * H + OUT;
+// BF16 weights pre-packed in the canonical K-major layout of the GEMM operands:
+// per layer the forward operand W [N][K] and the transposed operand W^T [K][N]
+// (the backward pass's dA = dZ W), each one contiguous block that one bulk copy
+// moves into shared memory
+__host__ __device__ constexpr size_t pk_bytes(int l) { return (size_t)ndim(l) * kdim(l) * 2; }
+__host__ __device__ constexpr size_t pk_off(int l) {
+  return l == 0 ? 0 : pk_off(l - 1) + pk_bytes(l - 1);
+}
+constexpr size_t PK_BYTES = pk_off(4);
 
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -64,6 +76,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
   return ok != 0;
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// 1-D bulk copy global -> shared; completion counted on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
   for (int i = 0; i < (1 << 22); ++i) {
@@ -119,7 +141,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 
 // ------------------------------------------------------------------ tile GEMM
 // byte offset of element (r, k) of an R-row operand in the staged layout
-__device__ __forceinline__ uint32_t blk_off(int r, int k, int R) {
+__host__ __device__ __forceinline__ uint32_t blk_off(int r, int k, int R) {
   return static_cast<uint32_t>((k >> 4) * (R * 32) + (r >> 3) * 256 + ((k >> 3) & 1) * 128 + (r & 7) * 16 +
                                (k & 7) * 2);
 }
@@ -138,6 +160,21 @@ __device__ void stage(unsigned char* dst, int R, int K, const T* src, long rs, l
   }
 }
 
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Issue D[128 x N] = A[128 x K] . B[N x K]^T (one thread) and commit it.
+__device__ __forceinline__ void issue_gemm(uint32_t tmem, const unsigned char* A, const unsigned char* B, int N, int K,
+                                           uint64_t* bar) {
+  tc_fence_after();
+  const uint32_t a0 = smem_u32(A), b0 = smem_u32(B), id = instr_desc(ROWS, N);
+  for (int c = 0; c < K / 16; ++c)
+    umma_bf16(tmem, smem_desc(a0 + c * ROWS * 32), smem_desc(b0 + c * N * 32), id, c > 0 ? 1u : 0u);
+  umma_commit(bar);
+}
+
 // D[128 x N] = A[128 x K] . B[N x K]^T into tensor memory; every thread calls
 // it; on return the accumulator is complete (or *err has ERR_WAIT set).
 __device__ bool gemm_tile(uint32_t tmem, const unsigned char* A, const unsigned char* B, int N, int K,
@@ -145,13 +182,7 @@ __device__ bool gemm_tile(uint32_t tmem, const unsigned char* A, const unsigned 
   fence_proxy_async();  // the staged operands, written by every thread, to the tensor core
   tc_fence_before();
   __syncthreads();
-  if (threadIdx.x == 0) {
-    tc_fence_after();
-    const uint32_t a0 = smem_u32(A), b0 = smem_u32(B), id = instr_desc(ROWS, N);
-    for (int c = 0; c < K / 16; ++c)
-      umma_bf16(tmem, smem_desc(a0 + c * ROWS * 32), smem_desc(b0 + c * N * 32), id, c > 0 ? 1u : 0u);
-    umma_commit(bar);
-  }
+  if (threadIdx.x == 0) issue_gemm(tmem, A, B, N, K, bar);
   const bool ok = mbar_wait_bounded(bar, phase);
   phase ^= 1u;
   if (!ok) atomicOr(err, ERR_WAIT);
@@ -159,8 +190,9 @@ __device__ bool gemm_tile(uint32_t tmem, const unsigned char* A, const unsigned 
   return __syncthreads_and(ok) != 0;
 }
 
+// TMEM address of column `col` in this warp's quarter of the lanes
 __device__ __forceinline__ uint32_t lane_addr(uint32_t tmem, int col) {
-  return tmem + (static_cast<uint32_t>(threadIdx.x & ~31) << 16) + static_cast<uint32_t>(col);
+  return tmem + (static_cast<uint32_t>(32 * ((threadIdx.x >> 5) & 3)) << 16) + static_cast<uint32_t>(col);
 }
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float z) {
@@ -170,58 +202,118 @@ __device__ __forceinline__ float gelu_grad(float z) {
 // ------------------------------------------------------------------ forward
 struct FwdArgs {
   const float* x; int B;              // inputs [B][IN]
-  const __nv_bfloat16* W[4]; const float* b[4];
+  const unsigned char* Wp;            // packed BF16 forward operands (pk_off)
+  const float* b[4];
   float* out;                         // [B][OUT]
   float* Z[3]; __nv_bfloat16* A[3];   // training: pre-activations (FP32) and activations (BF16), [B][H]
   int* err;
 };
 
+// One CTA per 128 rows.  Each layer's packed weights arrive by one bulk copy,
+// issued as soon as the previous layer's MMAs have finished reading the operand
+// buffer, so it overlaps that layer's epilogue; activations stay in shared
+// memory as the next layer's A operand.
 __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* opA = smem;
   unsigned char* opB = smem + SMEM_A;
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar_mma, bar_w;
   __shared__ uint32_t tslot;
-  const int t = threadIdx.x, row0 = blockIdx.x * ROWS, r = row0 + t;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31, grp = warp >> 2;
+  const int row = 32 * (warp & 3) + lane, row0 = blockIdx.x * ROWS, r = row0 + row;
   const int Rv = min(ROWS, a.B - row0);
-  if (t == 0) mbar_init(&bar);
-  if (t < 32) tmem_alloc(&tslot);
-  stage(opA, ROWS, IN, a.x + static_cast<long>(row0) * IN, IN, 1, Rv, IN);
+  bool w_pending = false;  // thread 0: a weight copy is in flight
+  if (t == 0) {
+    mbar_init(&bar_mma);
+    mbar_init(&bar_w);
+    fence_proxy_async();
+    mbar_expect_tx(&bar_w, static_cast<uint32_t>(pk_bytes(0)));
+    bulk_g2s(opB, a.Wp + pk_off(0), static_cast<uint32_t>(pk_bytes(0)), &bar_w);
+    w_pending = true;
+  }
+  if (warp == 0) tmem_alloc(&tslot);
+  // inputs: 8 columns (one 16-byte chunk of the layout) per step
+  for (int c = t; c < ROWS * (IN / 8); c += THREADS) {
+    const int rr = c / (IN / 8), kk = (c % (IN / 8)) * 8;
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = rr < Rv ? a.x[static_cast<long>(row0 + rr) * IN + kk + e] : 0.f;
+    *reinterpret_cast<uint4*>(opA + blk_off(rr, kk, ROWS)) =
+        make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+  }
+  fence_proxy_async();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tslot;
-  uint32_t phase = 0;
+  uint32_t ph_mma = 0, ph_w = 0;
   bool ok = true;
-  for (int l = 0; l < 4 && ok; ++l) {
+  for (int l = 0; l < 4; ++l) {
     const int K = kdim(l), N = ndim(l);
-    stage(opB, N, K, a.W[l], K, 1, N, K);
-    ok = gemm_tile(tmem, opA, opB, N, K, &bar, phase, a.err);
+    if (t == 0) {
+      const bool okw = mbar_wait_bounded(&bar_w, ph_w);
+      w_pending = !okw;
+      if (okw) issue_gemm(tmem, opA, opB, N, K, &bar_mma);
+      else atomicOr(a.err, ERR_WAIT);
+    }
+    ph_w ^= 1u;
+    bool okm = mbar_wait_bounded(&bar_mma, ph_mma);
+    ph_mma ^= 1u;
+    if (!okm) atomicOr(a.err, ERR_WAIT);
+    tc_fence_after();
+    ok = __syncthreads_and(okm) != 0;
     if (!ok) break;
-    for (int c0 = 0; c0 < N; c0 += 32) {
-      float v[32];
-      tmem_ld32(lane_addr(tmem, c0), v);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int c = c0 + j;
-        const float z = v[j] + a.b[l][c];
+    if (t == 0 && l < 3) {  // the MMAs are done with opB: fetch the next layer's weights
+      mbar_expect_tx(&bar_w, static_cast<uint32_t>(pk_bytes(l + 1)));
+      bulk_g2s(opB, a.Wp + pk_off(l + 1), static_cast<uint32_t>(pk_bytes(l + 1)), &bar_w);
+      w_pending = true;
+    }
+    // epilogue: this warp's rows, its group's columns (the 32-wide last layer:
+    // group 0 only)
+    const int per = N >= 128 ? N / NGRP : N;
+    if (N >= 128 || grp == 0) {
+      for (int c0 = grp * per; c0 < grp * per + per; c0 += 32) {
+        float v[32];
+        tmem_ld32(lane_addr(tmem, c0), v);
+        const float* bias = a.b[l] + c0;
         if (l < 3) {
-          const __nv_bfloat16 h = __float2bfloat16_rn(gelu(z));
-          *reinterpret_cast<__nv_bfloat16*>(opA + blk_off(t, c, ROWS)) = h;
+          uint32_t hp[16];
+#pragma unroll
+          for (int j = 0; j < 32; j += 2) {
+            const float z0 = v[j] + bias[j], z1 = v[j + 1] + bias[j + 1];
+            v[j] = z0;
+            v[j + 1] = z1;
+            hp[j / 2] = pack_bf16x2(gelu(z0), gelu(z1));
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4*>(opA + blk_off(row, c0 + 8 * q, ROWS)) =
+                make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
           if (a.Z[l] && r < a.B) {
-            a.Z[l][static_cast<long>(r) * H + c] = z;
-            a.A[l][static_cast<long>(r) * H + c] = h;
+            float4* zd = reinterpret_cast<float4*>(a.Z[l] + static_cast<long>(r) * H + c0);
+            uint4* ad = reinterpret_cast<uint4*>(a.A[l] + static_cast<long>(r) * H + c0);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) zd[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) ad[q] = make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
           }
         } else if (r < a.B) {
-          a.out[static_cast<long>(r) * OUT + c] = z;
+          float4* od = reinterpret_cast<float4*>(a.out + static_cast<long>(r) * OUT + c0);
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            od[q] = make_float4(v[4 * q] + bias[4 * q], v[4 * q + 1] + bias[4 * q + 1], v[4 * q + 2] + bias[4 * q + 2],
+                                v[4 * q + 3] + bias[4 * q + 3]);
         }
       }
     }
+    fence_proxy_async();  // the activations, written by every thread, to the tensor core
     tc_fence_before();
-    __syncthreads();  // every row's activations staged; accumulator free for the next layer
+    __syncthreads();      // every row's activations staged; accumulator free for the next layer
     tc_fence_after();
   }
-  if (t < 32) tmem_dealloc(tmem);
+  if (t == 0 && w_pending) mbar_wait_bounded(&bar_w, ph_w);  // no copy may land after the CTA ends
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem);
 }
 
 // ------------------------------------------------------------------ loss
@@ -249,7 +341,7 @@ __global__ void mlp_loss_kernel(const float* out, const float* y, const float* m
 // ------------------------------------------------------------------ backward
 struct BwdArgs {
   const float* x; int B;
-  const __nv_bfloat16* W[4];
+  const unsigned char* WpT;           // packed BF16 transposed operands W^T (pk_off)
   const float* Z[3]; const __nv_bfloat16* A[3];
   const float* dout;                  // [B][OUT]
   __nv_bfloat16* dz[2];               // [B][H] scratch, ping-pong between layers
@@ -266,17 +358,22 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_backward_kernel(BwdArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* opA = smem;
   unsigned char* opB = smem + SMEM_A;
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar, bar_w;
   __shared__ uint32_t tslot;
-  const int t = threadIdx.x, row0 = blockIdx.x * ROWS, r = row0 + t;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31, grp = warp >> 2;
+  const int row = 32 * (warp & 3) + lane, row0 = blockIdx.x * ROWS, r = row0 + row;
   const int Rv = min(ROWS, a.B - row0);
-  if (t == 0) mbar_init(&bar);
-  if (t < 32) tmem_alloc(&tslot);
+  if (t == 0) {
+    mbar_init(&bar);
+    mbar_init(&bar_w);
+    fence_proxy_async();
+  }
+  if (warp == 0) tmem_alloc(&tslot);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tslot;
-  uint32_t phase = 0;
+  uint32_t phase = 0, ph_w = 0;
   bool ok = true;
   for (int l = 3; l >= 0 && ok; --l) {
     const int K = kdim(l), N = ndim(l);
@@ -303,12 +400,15 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_backward_kernel(BwdArgs a) {
         else stage(opB, K, ROWS, a.A[l - 1] + static_cast<long>(row0) * H, 1, H, K, Rv);
         ok = gemm_tile(tmem, opA, opB, K, ROWS, &bar, phase, a.err);
         if (!ok) break;
-        for (int c0 = 0; c0 < K; c0 += 32) {
-          float v[32];
-          tmem_ld32(lane_addr(tmem, c0), v);
+        const int per = K >= 128 ? K / NGRP : K;
+        if (K >= 128 || grp == 0) {
+          for (int c0 = grp * per; c0 < grp * per + per; c0 += 32) {
+            float v[32];
+            tmem_ld32(lane_addr(tmem, c0), v);
 #pragma unroll
-          for (int j = 0; j < 32; ++j)  // K = 48 for the first layer: the last group is half empty
-            if (n0 + t < N && c0 + j < K) atomicAdd(&gW[static_cast<long>(n0 + t) * K + c0 + j], v[j]);
+            for (int j = 0; j < 32; ++j)  // K = 48 for the first layer: the last group is half empty
+              if (n0 + row < N && c0 + j < K) atomicAdd(&gW[static_cast<long>(n0 + row) * K + c0 + j], v[j]);
+          }
         }
         tc_fence_before();
         __syncthreads();
@@ -322,12 +422,14 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_backward_kernel(BwdArgs a) {
         else stage(opB, N, ROWS, dzb, 1, dzs, N, Rv);
         ok = gemm_tile(tmem, opA, opB, N, ROWS, &bar, phase, a.err);
         if (!ok) break;
-        for (int c0 = 0; c0 < N; c0 += 32) {
-          float v[32];
-          tmem_ld32(lane_addr(tmem, c0), v);
+        if (grp == 0) {
+          for (int c0 = 0; c0 < N; c0 += 32) {
+            float v[32];
+            tmem_ld32(lane_addr(tmem, c0), v);
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (k0 + t < K) atomicAdd(&gW[static_cast<long>(c0 + j) * K + k0 + t], v[j]);
+            for (int j = 0; j < 32; ++j)
+              if (k0 + row < K) atomicAdd(&gW[static_cast<long>(c0 + j) * K + k0 + row], v[j]);
+          }
         }
         tc_fence_before();
         __syncthreads();
@@ -335,46 +437,76 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_backward_kernel(BwdArgs a) {
       }
     }
     if (l == 0 || !ok) break;
-    // ---- dA_{l-1} = dZ_l W_l: M = rows, N' = K (inputs of layer l), K' = N (outputs)
+    // ---- dA_{l-1} = dZ_l W_l: M = rows, N' = K (inputs of layer l), K' = N (outputs);
+    // W^T arrives packed by one bulk copy while the threads stage dZ
+    if (t == 0) {
+      mbar_expect_tx(&bar_w, static_cast<uint32_t>(pk_bytes(l)));
+      bulk_g2s(opB, a.WpT + pk_off(l), static_cast<uint32_t>(pk_bytes(l)), &bar_w);
+    }
     if (dzf) stage(opA, ROWS, N, dzf, dzs, 1, Rv, N);
     else stage(opA, ROWS, N, dzb, dzs, 1, Rv, N);
-    stage(opB, K, N, a.W[l], 1, K, K, N);
+    if (t == 0 && !mbar_wait_bounded(&bar_w, ph_w)) atomicOr(a.err, ERR_WAIT);
+    ph_w ^= 1u;
     ok = gemm_tile(tmem, opA, opB, K, N, &bar, phase, a.err);
     if (!ok) break;
     __nv_bfloat16* dzo = a.dz[(l - 1) & 1] + static_cast<long>(row0) * H;
-    for (int c0 = 0; c0 < K; c0 += 32) {
+    for (int c0 = grp * (K / NGRP); c0 < (grp + 1) * (K / NGRP); c0 += 32) {
       float v[32];
       tmem_ld32(lane_addr(tmem, c0), v);
+      if (r < a.B) {
+        const float4* zs = reinterpret_cast<const float4*>(a.Z[l - 1] + static_cast<long>(r) * H + c0);
+        uint4* dd = reinterpret_cast<uint4*>(dzo + static_cast<long>(row) * H + c0);
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (r < a.B) {
-          const int c = c0 + j;
-          dzo[t * H + c] = __float2bfloat16_rn(v[j] * gelu_grad(a.Z[l - 1][static_cast<long>(r) * H + c]));
+        for (int q = 0; q < 4; ++q) {
+          const float4 z0 = zs[2 * q], z1 = zs[2 * q + 1];
+          dd[q] = make_uint4(pack_bf16x2(v[8 * q] * gelu_grad(z0.x), v[8 * q + 1] * gelu_grad(z0.y)),
+                             pack_bf16x2(v[8 * q + 2] * gelu_grad(z0.z), v[8 * q + 3] * gelu_grad(z0.w)),
+                             pack_bf16x2(v[8 * q + 4] * gelu_grad(z1.x), v[8 * q + 5] * gelu_grad(z1.y)),
+                             pack_bf16x2(v[8 * q + 6] * gelu_grad(z1.z), v[8 * q + 7] * gelu_grad(z1.w)));
         }
+      }
     }
     tc_fence_before();
     __syncthreads();  // dZ_{l-1} written (global) before the next layer stages it
     tc_fence_after();
   }
-  if (t < 32) tmem_dealloc(tmem);
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem);
 }
 
 // ------------------------------------------------------------------ Adam on the FP32 master weights
-__global__ void mlp_adam_kernel(float* p, const float* g, float* m, float* v, __nv_bfloat16* wb, int n, float lr,
-                                float b1, float b2, float eps, float ib1, float ib2) {
+// Element i of the parameter vector: its layer and (row, column) if it is a
+// weight, so that the BF16 copy can be written straight into both packed
+// operand layouts.
+__device__ __forceinline__ void store_packed(int i, float w, unsigned char* Wp, unsigned char* WpT) {
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const int off = static_cast<int>(w_off(l)), K = kdim(l), N = ndim(l);
+    if (i >= off && i < off + N * K) {
+      const int n = (i - off) / K, k = (i - off) % K;
+      const __nv_bfloat16 h = __float2bfloat16_rn(w);
+      *reinterpret_cast<__nv_bfloat16*>(Wp + pk_off(l) + blk_off(n, k, N)) = h;
+      *reinterpret_cast<__nv_bfloat16*>(WpT + pk_off(l) + blk_off(k, n, K)) = h;
+    }
+  }
+}
+
+__global__ void mlp_adam_kernel(float* p, const float* g, float* m, float* v, unsigned char* Wp, unsigned char* WpT,
+                                int n, float lr, float b1, float b2, float eps, float ib1, float ib2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float gi = g[i];
   const float mi = fmaf(b1, m[i], (1.f - b1) * gi), vi = fmaf(b2, v[i], (1.f - b2) * gi * gi);
   m[i] = mi;
   v[i] = vi;
-  p[i] -= lr * (mi * ib1) / (sqrtf(vi * ib2) + eps);
-  wb[i] = __float2bfloat16_rn(p[i]);
+  const float w = p[i] - lr * (mi * ib1) / (sqrtf(vi * ib2) + eps);
+  p[i] = w;
+  store_packed(i, w, Wp, WpT);
 }
 
-__global__ void to_bf16_kernel(const float* p, __nv_bfloat16* wb, int n) {
+__global__ void pack_kernel(const float* p, unsigned char* Wp, unsigned char* WpT, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) wb[i] = __float2bfloat16_rn(p[i]);
+  if (i < n) store_packed(i, p[i], Wp, WpT);
 }
 
 }  // namespace mlpk
@@ -386,7 +518,8 @@ struct tamp_mlp {
   cudaStream_t stream = nullptr;
   int max_batch = 0;
   float* params = nullptr;     // FP32 master
-  __nv_bfloat16* wb = nullptr; // BF16 copy (same layout; the kernels read the weight blocks)
+  unsigned char* wp = nullptr;  // BF16 weights packed as forward GEMM operands (pk_off)
+  unsigned char* wpt = nullptr; // ... and as transposed operands for the backward pass
   float* grad = nullptr;
   float* m = nullptr;
   float* v = nullptr;
@@ -443,10 +576,8 @@ cudaError_t enable_smem(int device) {
 FwdArgs fwd_args(tamp_mlp* n, const float* x, int B, float* out, bool train) {
   FwdArgs a{};
   a.x = x; a.B = B; a.out = out; a.err = n->err;
-  for (int l = 0; l < 4; ++l) {
-    a.W[l] = n->wb + w_off(l);
-    a.b[l] = n->params + b_off(l);
-  }
+  a.Wp = n->wp;
+  for (int l = 0; l < 4; ++l) a.b[l] = n->params + b_off(l);
   for (int l = 0; l < 3; ++l) {
     a.Z[l] = train ? n->Z + static_cast<size_t>(l) * n->max_batch * H : nullptr;
     a.A[l] = train ? n->A + static_cast<size_t>(l) * n->max_batch * H : nullptr;
@@ -474,7 +605,7 @@ tamp_status gradient(tamp_mlp* n, const float* x, const float* y, const float* m
   MLP_TRY(n, cudaGetLastError());
   BwdArgs b{};
   b.x = x; b.B = B; b.dout = n->dout; b.grad = n->grad; b.err = n->err;
-  for (int l = 0; l < 4; ++l) b.W[l] = n->wb + w_off(l);
+  b.WpT = n->wpt;
   for (int l = 0; l < 3; ++l) {
     b.Z[l] = n->Z + static_cast<size_t>(l) * n->max_batch * H;
     b.A[l] = n->A + static_cast<size_t>(l) * n->max_batch * H;
@@ -499,7 +630,8 @@ tamp_status tamp_mlp_create(int device, void* stream, int max_batch, tamp_mlp** 
   Dev g(device);
   const size_t mb = static_cast<size_t>(max_batch);
   cudaError_t e = cudaMalloc(&n->params, N_PARAMS * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&n->wb, N_PARAMS * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&n->wp, PK_BYTES);
+  if (e == cudaSuccess) e = cudaMalloc(&n->wpt, PK_BYTES);
   if (e == cudaSuccess) e = cudaMalloc(&n->grad, N_PARAMS * 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->m, N_PARAMS * 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->v, N_PARAMS * 4);
@@ -511,7 +643,8 @@ tamp_status tamp_mlp_create(int device, void* stream, int max_batch, tamp_mlp** 
   if (e == cudaSuccess) e = cudaMalloc(&n->loss, 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->err, 4);
   if (e == cudaSuccess) e = cudaMemsetAsync(n->params, 0, N_PARAMS * 4, n->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(n->wb, 0, N_PARAMS * 2, n->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->wp, 0, PK_BYTES, n->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->wpt, 0, PK_BYTES, n->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(n->m, 0, N_PARAMS * 4, n->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(n->v, 0, N_PARAMS * 4, n->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(n->err, 0, 4, n->stream);
@@ -528,7 +661,7 @@ tamp_status tamp_mlp_destroy(tamp_mlp* n) {
   if (!n) return TAMP_ERR_INVALID_ARG;
   Dev g(n->device);
   cudaStreamSynchronize(n->stream);
-  cudaFree(n->params); cudaFree(n->wb); cudaFree(n->grad); cudaFree(n->m); cudaFree(n->v);
+  cudaFree(n->params); cudaFree(n->wp); cudaFree(n->wpt); cudaFree(n->grad); cudaFree(n->m); cudaFree(n->v);
   cudaFree(n->Z); cudaFree(n->A); cudaFree(n->dz); cudaFree(n->out); cudaFree(n->dout);
   cudaFree(n->loss); cudaFree(n->err);
   delete n;
@@ -542,8 +675,8 @@ tamp_status tamp_mlp_set_params(tamp_mlp* n, const float* host, int count) {
   if (!host || count != static_cast<int>(N_PARAMS)) return mfail(n, TAMP_ERR_INVALID_ARG, "parameter count");
   Dev g(n->device);
   MLP_TRY(n, cudaMemcpyAsync(n->params, host, N_PARAMS * 4, cudaMemcpyHostToDevice, n->stream));
-  to_bf16_kernel<<<static_cast<int>((N_PARAMS + 255) / 256), 256, 0, n->stream>>>(n->params, n->wb,
-                                                                                 static_cast<int>(N_PARAMS));
+  pack_kernel<<<static_cast<int>((N_PARAMS + 255) / 256), 256, 0, n->stream>>>(n->params, n->wp, n->wpt,
+                                                                              static_cast<int>(N_PARAMS));
   MLP_TRY(n, cudaGetLastError());
   MLP_TRY(n, cudaMemsetAsync(n->m, 0, N_PARAMS * 4, n->stream));
   MLP_TRY(n, cudaMemsetAsync(n->v, 0, N_PARAMS * 4, n->stream));
@@ -595,7 +728,8 @@ tamp_status tamp_mlp_train_step(tamp_mlp* n, const float* x, const float* y, con
   const float ib1 = static_cast<float>(1.0 / (1.0 - std::pow(b1, static_cast<double>(n->step))));
   const float ib2 = static_cast<float>(1.0 / (1.0 - std::pow(b2, static_cast<double>(n->step))));
   mlp_adam_kernel<<<static_cast<int>((N_PARAMS + 255) / 256), 256, 0, n->stream>>>(
-      n->params, n->grad, n->m, n->v, n->wb, static_cast<int>(N_PARAMS), lr, 0.9f, 0.999f, 1e-8f, ib1, ib2);
+      n->params, n->grad, n->m, n->v, n->wp, n->wpt, static_cast<int>(N_PARAMS), lr, 0.9f, 0.999f, 1e-8f, ib1,
+      ib2);
   MLP_TRY(n, cudaGetLastError());
   if (loss) {
     MLP_TRY(n, cudaMemcpyAsync(loss, n->loss, 4, cudaMemcpyDeviceToHost, n->stream));
