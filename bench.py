@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttfs", action="store_true", help="skip the time-to-first-satisfying measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's heuristic launch shape")
+    ap.add_argument("--mode", default="optimize", choices=["optimize", "mlp"],
+                    help="optimize: the headline line; mlp: the proposal network's tensor-core kernels alone")
     ap.add_argument("--workload", default="packing", choices=["packing", "stress"],
                     help="packing (the headline line) or the stress scene (12 boxes, 64 cuboids, 100 spheres)")
     return ap.parse_args()
@@ -226,10 +228,59 @@ def measure_ttfs(pkg, sg, seeds=range(3001, 3009), budget_iters=1000):
     return out
 
 
+def run_mlp(args):
+    """The proposal network's kernels alone: forward over 65536 rows and one
+    training step (forward, NLL, backward, Adam) over 16384 rows, CUDA events
+    on the network's stream, against the measured BF16 tensor-core peak."""
+    import numpy as np
+    import torch
+
+    from paper_2411_11833_b300.build import build_library
+    build_library()
+    import paper_2411_11833_b300 as pkg
+    from paper_2411_11833_b300 import proposal
+    torch.cuda.set_device(0)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    net = pkg.Mlp(max_batch=16384)
+    net.set_params(proposal._init_params(1))
+    x = torch.randn(65536, 48, device="cuda", generator=g)
+    xt = torch.randn(16384, 48, device="cuda", generator=g)
+    y = torch.randn(16384, 16, device="cuda", generator=g)
+    m = torch.ones(16384, 16, device="cuda")
+    flop_row = 2 * (48 * 256 + 2 * 256 * 256 + 256 * 32)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / args.steps
+    fwd_ms = timed(lambda: net.forward(x))
+    trn_ms = timed(lambda: net.train_step(xt, y, m, 1e-4, want_loss=False))
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1800.0
+    fwd = flop_row * 65536 / fwd_ms / 1e9
+    trn = 3 * flop_row * 16384 / trn_ms / 1e9
+    print(json.dumps({"metric": "proposal-network TFLOP/s", "unit": "TFLOP/s", "dtype": "bf16 (fp32 accumulate)",
+                      "forward": {"rows": 65536, "ms": fwd_ms, "tflops": fwd, "frac": fwd / peak},
+                      "train_step": {"rows": 16384, "ms": trn_ms, "tflops": trn, "frac": trn / peak},
+                      "peak": peak, "peak_basis": "MEASURED_PEAKS.json bf16 burst",
+                      "steps": args.steps, "warmup": args.warmup}))
+    net.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.mode == "mlp":
+        run_mlp(args)
         return
     import numpy as np
     import torch
