@@ -173,6 +173,20 @@ def run_reference(args):
     }))
 
 
+def job_throughput(step_ms, world: int, units_per_rank_step: int, device=None):
+    """Whole-job rate of a weak-scaling run: every rank processed
+    ``units_per_rank_step`` units per step; the job's time is the slowest
+    rank's (max over ranks, an all-reduce when the process group is up).
+    Returns (units per second, the job's seconds)."""
+    import torch
+    import torch.distributed as dist
+    total = torch.tensor([float(sum(step_ms))], dtype=torch.float64, device=device)
+    if world > 1 and dist.is_available() and dist.is_initialized():
+        dist.all_reduce(total, op=dist.ReduceOp.MAX)
+    total_s = float(total.item()) / 1e3
+    return world * units_per_rank_step * len(step_ms) / total_s, total_s
+
+
 def measure_ttfs(pkg, sg, seeds=range(3001, 3009), budget_iters=1000):
     """Time to the first satisfying particle on obstructed stacking (one fixed
     7-DOF arm; 2-4 blockers cover B's top; 16 candidate skeletons of 2-8
@@ -350,11 +364,7 @@ def main():
     work = scene.work_counters(pid)          # candidates of the last timed step
     step_ms = [e0.elapsed_time(e2) for e0, _, e2 in ev]
     kern_ms = [e1.elapsed_time(e2) for _, e1, e2 in ev]
-    total_ms = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(total_ms, op=dist.ReduceOp.MAX)
-    total_s = float(total_ms.item()) / 1e3
-    value = world * P * T * args.steps / total_s
+    value, total_s = job_throughput(step_ms, world, P * T, device=dev)
     q = scene.query(pid, P)
 
     # end to end through the C ABI with host buffers: H2D of the batch, the
