@@ -1168,10 +1168,10 @@ tamp_status tamp_autotune(tamp_scene* s, const int* ids, int n, int trial_steps,
   int max_w = 1;
   for (Problem* pr : prs) max_w = std::max(max_w, optimize_warps(pr->K));
   std::vector<int> wc;
-  for (int per = 1; per <= 4; ++per) {
+  for (int per = 1; per <= 4; ++per) {  // work items (two per configuration) per warp
     int kmax = 0;
     for (Problem* pr : prs) kmax = std::max(kmax, pr->K);
-    const int w = std::min(max_w, (kmax + per - 1) / per);
+    const int w = std::min(max_w, (2 * kmax + per - 1) / per);
     if (std::find(wc.begin(), wc.end(), w) == wc.end()) wc.push_back(w);
   }
   float best = -1.f;
@@ -1226,7 +1226,7 @@ tamp_status tamp_set_tuning(tamp_scene* s, const int* ids, int n, int lanes, int
     return TAMP_OK;
   }
   if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) return fail(s, TAMP_ERR_INVALID_ARG, "lanes %d", lanes);
-  if (warps < 1 || warps > 12) return fail(s, TAMP_ERR_INVALID_ARG, "warps %d", warps);
+  if (warps < 1 || warps > 16) return fail(s, TAMP_ERR_INVALID_ARG, "warps %d", warps);
   Plan probe;
   tamp_status st = plan_jobs(s, jobs, 0, &probe, lanes, warps);
   if (st != TAMP_OK) return st;

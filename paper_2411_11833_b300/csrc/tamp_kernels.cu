@@ -986,7 +986,7 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
 // whenever it moves to a new problem.  Many skeletons of uneven length and
 // particle count thus share one launch and balance across the SMs.
 template <int L>
-__global__ void __launch_bounds__(384, 1) optimize_kernel(LaunchArgs a) {
+__global__ void __launch_bounds__(512, 1) optimize_kernel(LaunchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int abort_flag, s_item;
@@ -1435,9 +1435,8 @@ size_t optimize_tile_bytes(int prob_words, int D, int NT, int NSLOT, int L) {
 }
 size_t optimize_scratch_bytes(int warps) { return static_cast<size_t>(WARP_SCRATCH_BYTES) * warps; }
 
-int optimize_warps(int K) {
-  const int per = (K + 11) / 12;  // configurations per warp
-  return (K + per - 1) / per;     // <= 12 warps (384 threads)
-}
+// Warps of the default launch shape: one per work item of an evaluation pass
+// (two pieces per configuration), at most 16 (512 threads, 128 registers each).
+int optimize_warps(int K) { return std::min(16, 2 * K); }
 
 }  // namespace tamp

@@ -30,7 +30,7 @@ def test_autotune_keeps_state_and_matches_other_shapes(pkg):
     scene.optimize(pid, 3)
     before = scene.get_particles(pid)
     L, W, ms = scene.autotune(pid, trial_steps=5)
-    assert L in (1, 2, 4, 8) and 1 <= W <= 12 and ms > 0
+    assert L in (1, 2, 4, 8) and 1 <= W <= 16 and ms > 0
     after = scene.get_particles(pid)
     for a, b in zip(before[:3], after[:3]):
         assert np.array_equal(a, b)
@@ -65,7 +65,7 @@ def test_set_tuning_validates_and_clears(pkg):
     with pytest.raises(TampError):
         scene.set_tuning(pid, 3, 2)
     with pytest.raises(TampError):
-        scene.set_tuning(pid, 1, 13)
+        scene.set_tuning(pid, 1, 17)
     scene.set_tuning(pid, 4, 1)
     scene.optimize(pid, 2)
     scene.set_tuning(pid, 0, 0)                  # back to the library's heuristic
