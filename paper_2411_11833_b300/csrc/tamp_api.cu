@@ -222,7 +222,7 @@ tamp_status build_scene_blob(tamp_scene* s, const tamp_scene_desc* d) {
       for (int c = 0; c < 4; ++c) v.push_back(0);
     align4(v);
   }
-  // obstacles: t' = R^T t, R row-major, half extents, pad (16 words each)
+  // obstacles: t' = R^T t, R row-major, half extents, pad (OBS_W words each)
   const int O = d->n_obs;
   v[SH_OFF_OBS] = static_cast<uint32_t>(v.size());
   for (int o = 0; o < O; ++o) {
@@ -231,7 +231,7 @@ tamp_status build_scene_blob(tamp_scene* s, const tamp_scene_desc* d) {
     for (int j = 0; j < 3; ++j) push_f(v, Rm[0 + j] * c[0] + Rm[3 + j] * c[1] + Rm[6 + j] * c[2]);
     for (int k = 0; k < 9; ++k) push_f(v, Rm[k]);
     for (int j = 0; j < 3; ++j) push_f(v, d->obs_half[3 * o + j]);
-    v.push_back(0);
+    for (int k = 15; k < OBS_W; ++k) v.push_back(0);
   }
   if (O == 0)
     for (int k = 0; k < OBS_W; ++k) v.push_back(0);

@@ -30,8 +30,10 @@ constexpr int ARM_JW = 8;       // a, d, cos(alpha), sin(alpha), offset, q_lo, q
 // with r = -1 (unused).  Per batch of NB slots, a bounding sphere (centre in the
 // link frame, radius) for the broad phase.
 constexpr float DUMMY_FAR = 1.0e4f;
-// obstacles: 16 floats each -- t' = R^T t (3), R row-major (9), half extents (3), pad
-constexpr int OBS_W = 16;
+// obstacles: 20 floats each -- t' = R^T t (3), R row-major (9), half extents (3),
+// pad; the 80-byte stride puts the records of 8 consecutive obstacles in
+// disjoint shared-memory banks when the lanes of a warp read different ones
+constexpr int OBS_W = 20;
 // box record: half x,y,z, bounding radius of its spheres about its centre,
 // init x,y,z,yaw, cos(yaw), sin(yaw), then the half extents (box frame, about
 // the centre) of a box that holds every sphere of the model, pad

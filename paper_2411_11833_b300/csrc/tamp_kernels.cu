@@ -113,7 +113,7 @@ struct Obb {
 // that nothing touches (every lane of the warp runs the same trip count).
 __device__ __forceinline__ Obb load_obb(const float4* __restrict__ obs, int o, int O) {
   const bool ok = o < O;
-  const float4* q = obs + 4 * (ok ? o : 0);
+  const float4* q = obs + (OBS_W / 4) * (ok ? o : 0);
   const float4 a = q[0], b4 = q[1], c = q[2], d = q[3];
   Obb b;
   b.tx = a.x + (ok ? 0.f : DUMMY_FAR); b.ty = a.y; b.tz = a.z;
