@@ -270,7 +270,7 @@ tamp_status tamp_work_counters(tamp_scene *scene, int problem_id, uint64_t out[2
  * picks how the same work is laid out).  For the listed problems with their
  * current batches, times every launch shape that fits -- lanes L in {1, 2, 4,
  * 8} per (particle, configuration) (32 / L particles per CTA) and W <= 16 warps
- * per CTA (1..4 work items per warp; a configuration is two items) -- with
+ * per CTA (1..8 work items per warp; a configuration is two items) -- with
  * trial_steps fused iterations on
  * scratch copies of the batches (the problems' state is left untouched), and
  * keeps the fastest for later launches of exactly these problems at these batch

@@ -1168,7 +1168,7 @@ tamp_status tamp_autotune(tamp_scene* s, const int* ids, int n, int trial_steps,
   int max_w = 1;
   for (Problem* pr : prs) max_w = std::max(max_w, optimize_warps(pr->K));
   std::vector<int> wc;
-  for (int per = 1; per <= 4; ++per) {  // work items (two per configuration) per warp
+  for (int per : {1, 2, 3, 4, 6, 8}) {  // work items (two per configuration) per warp
     int kmax = 0;
     for (Problem* pr : prs) kmax = std::max(kmax, pr->K);
     const int w = std::min(max_w, (2 * kmax + per - 1) / per);
