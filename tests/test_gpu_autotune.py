@@ -72,3 +72,36 @@ def test_set_tuning_validates_and_clears(pkg):
     scene.optimize(pid, 2)
     assert scene.get_particles(pid)[3] == 4
     scene.close()
+
+
+@pytest.mark.parametrize("lanes,warps", [(1, 16), (1, 5), (1, 1), (2, 7), (4, 16), (8, 3)])
+def test_every_launch_shape_takes_the_oracle_adam_step(pkg, lanes, warps):
+    """Whatever the lane split and however many warps share a configuration's
+    two pieces (the work items pulled from the per-pass counter), one fused
+    iteration equals the oracle's gradient + Adam step (packing problem, 12
+    configurations, a ragged last tile)."""
+    from oracle.problem import Problem
+    sc, acts = sg.packing_problem(2002)
+    pr = Problem(sc, acts)
+    P = 45
+    X = sg.random_particles(sc, acts, P, seed=71, spread=0.5)
+    m0, v0 = sg.random_adam_state(P, pr.D, seed=72)
+    scene = pkg.Scene(sc)
+    pid = scene.set_skeleton(acts)
+    scene.set_particles(pid, X.T.astype(np.float32), m0.T.astype(np.float32), v0.T.astype(np.float32), 3)
+    scene.set_tuning(pid, lanes, warps)
+    scene.optimize(pid, 1)
+    x1, m1, _, t1 = scene.get_particles(pid)
+    scene.close()
+    assert t1 == 4
+    Xt = torch.tensor(X.astype(np.float32).astype(np.float64))
+    _, g = pr.gradient(Xt)
+    xr, mr, _ = pr.adam_step(Xt, torch.tensor(m0.astype(np.float32).astype(np.float64)),
+                             torch.tensor(v0.astype(np.float32).astype(np.float64)), 4, g, P)
+    keep = pr.kink_margin(Xt).numpy() > 1e-4
+    assert keep.mean() > 0.5
+    dm = np.abs(m1.T - mr.numpy())[keep]
+    assert dm.max() <= 1e-3 * np.abs(mr.numpy()[keep]).max() + 1e-9
+    step_g = (x1.T - X.astype(np.float32))[keep]
+    step_r = (xr.numpy() - Xt.numpy())[keep]
+    assert np.abs(step_g - step_r).max() <= 1e-3 * np.abs(step_r).max() + 2e-6
