@@ -336,3 +336,35 @@ def test_stacking_searches_run_end_to_end(pkg):
                             max_iterations=20, seed=1)
     assert out["solved"] or out["iterations"] == 4 * 20
     scene.close()
+
+
+def test_stress_full_batch_adam_step_sampled(pkg):
+    """The stress workload at its full batch (65536 particles, D = 252, 24
+    configurations) in the launch shape the benchmark's tuner picks for it
+    (2 lanes, 16 warps): one fused iteration, then 32 sampled particles checked
+    against the oracle's gradient + Adam step one by one (those within 1e-4 of a
+    kink of the 64-cuboid scene are left out and counted)."""
+    sc, acts = sg.stress_problem(5001)
+    pr = Problem(sc, acts)
+    P = 65536
+    X = sg.random_particles(sc, acts, P, seed=81, spread=0.5).astype(np.float32)
+    scene = pkg.Scene(sc)
+    pid = scene.set_skeleton(acts)
+    scene.set_particles(pid, np.ascontiguousarray(X.T))
+    scene.set_tuning(pid, 2, 16)
+    scene.optimize(pid, 1)
+    x1, m1, _, t1 = scene.get_particles(pid)
+    scene.close()
+    assert t1 == 1
+    idx = np.random.default_rng(3).choice(P, 32, replace=False)
+    Xs = torch.tensor(X[idx].astype(np.float64))
+    _, g = pr.gradient(Xs)
+    xr, mr, _ = pr.adam_step(Xs, torch.zeros_like(Xs), torch.zeros_like(Xs), 1, g, P)
+    keep = pr.kink_margin(Xs).numpy() > 1e-4
+    assert keep.sum() >= 8, keep.sum()
+    dm = np.abs(m1.T[idx] - mr.numpy())[keep]
+    assert dm.max() <= 1e-3 * np.abs(mr.numpy()[keep]).max() + 1e-12
+    step_g = (x1.T[idx] - X[idx])[keep]
+    step_r = (xr.numpy() - Xs.numpy())[keep]
+    # first Adam step: -lr * g / (|g| + eps), so compare the steps' signs and sizes
+    assert np.abs(step_g - step_r).max() <= 1e-3 * np.abs(step_r).max() + 2e-6
