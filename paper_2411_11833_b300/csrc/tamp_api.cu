@@ -22,7 +22,7 @@ cudaError_t launch_optimize(const LaunchArgs& a, int L, int warps, int grid, siz
 cudaError_t optimize_set_smem(int L, size_t smem);
 cudaError_t launch_chunk_control(int* t_dev, const int* const* first_iters, int n_problems, int steps,
                                  int stop_on_first, int* stop, int* chunks_run, cudaStream_t st);
-size_t optimize_tile_bytes(int prob_words, int D, int NT, int NSLOT, int L);
+size_t optimize_tile_bytes(int prob_words, int D, int NT, int NSLOT, int L, bool mv_global);
 size_t optimize_scratch_bytes(int warps);
 int optimize_blocks_per_sm(int L, int warps, size_t smem);
 cudaError_t launch_sample(const uint32_t* pb, const uint32_t* sc, float* x, float* m, float* v, int stride, int P,
@@ -644,6 +644,7 @@ struct Job {
 // the list is empty).
 struct Plan {
   int L = 1, warps = 1, grid = 0;
+  bool mv_global = false;  // Adam moments in global memory: the tile fits shared memory only that way
   size_t smem = 0;
   std::vector<ProbDesc> descs;
   std::vector<uint32_t> items;
@@ -679,12 +680,19 @@ tamp_status plan_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lanes
     }
   }
   size_t smem = 0;
+  // the first lane split that fits, with the Adam moments staged in shared
+  // memory if possible, else used in place in global memory
+  bool mvg = false;
   for (; L <= 8; L *= 2) {
-    size_t tile = 0;
-    for (const Job& j : jobs)
-      tile = std::max(tile, optimize_tile_bytes(static_cast<int>(j.pr->blob.size()), j.pr->D, j.pr->NT,
-                                                j.pr->NSLOT, L));
-    smem = 4 * ((s->blob.size() + 3) & ~static_cast<size_t>(3)) + tile + optimize_scratch_bytes(warps);
+    for (int g = 0; g < 2; ++g) {
+      size_t tile = 0;
+      for (const Job& j : jobs)
+        tile = std::max(tile, optimize_tile_bytes(static_cast<int>(j.pr->blob.size()), j.pr->D, j.pr->NT,
+                                                  j.pr->NSLOT, L, g == 1));
+      smem = 4 * ((s->blob.size() + 3) & ~static_cast<size_t>(3)) + tile + optimize_scratch_bytes(warps);
+      mvg = g == 1;
+      if (smem <= kMaxDynSmem) break;
+    }
     if (smem <= kMaxDynSmem) break;
   }
   if (L > 8) return fail(s, TAMP_ERR_INVALID_ARG, "problem does not fit in shared memory");
@@ -705,6 +713,7 @@ tamp_status plan_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lanes
   plan->L = L;
   plan->warps = warps;
   plan->smem = smem;
+  plan->mv_global = mvg;
   const int per_sm = std::max(1, optimize_blocks_per_sm(L, warps, smem));
   plan->grid = std::min(static_cast<int>(plan->items.size()), s->sm_count * per_sm);
   return TAMP_OK;
@@ -720,6 +729,7 @@ LaunchArgs plan_args(const tamp_scene* s, const Plan& plan, ProbDesc* d_descs, u
   a.item_counter = d_counter;
   a.err = s->d_err;
   a.scratch_offset = static_cast<int>(plan.smem - optimize_scratch_bytes(plan.warps));
+  a.mv_global = plan.mv_global ? 1 : 0;
   return a;
 }
 
@@ -1440,7 +1450,7 @@ extern "C" tamp_status tamp_eval_static_scratch(tamp_scene* s, int id, int n, co
   size_t smem = 0;
   for (; L <= 8; L *= 2) {
     smem = 4 * ((s->blob.size() + 3) & ~static_cast<size_t>(3)) +
-           optimize_tile_bytes(static_cast<int>(pr->blob.size()), pr->D, pr->NT, pr->NSLOT, L) +
+           optimize_tile_bytes(static_cast<int>(pr->blob.size()), pr->D, pr->NT, pr->NSLOT, L, false) +
            optimize_scratch_bytes(warps);
     if (smem <= kMaxDynSmem) break;
   }

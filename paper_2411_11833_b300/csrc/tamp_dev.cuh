@@ -109,6 +109,7 @@ struct LaunchArgs {
   int* err;
   int scratch_offset;                 // bytes from the start of dynamic shared memory to the warp scratch
   const int* stop;                    // optional: a non-zero value makes the launch return at once
+  int mv_global;                      // 1: Adam moments used in place in global memory (not staged)
 };
 constexpr int ITEM_TILE_BITS = 20;
 

@@ -834,13 +834,16 @@ __device__ void eval_goal(const uint32_t* __restrict__ sc, const uint32_t* __res
 // write it back.  All threads of the CTA call this together.
 template <int L>
 __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, const uint32_t* s_pb, float* tile_mem,
-                         const WarpScratch& ws) {
+                         const WarpScratch& ws, bool mv_global) {
   constexpr int PT = 32 / L;
   const int D = s_pb[PH_D], K = s_pb[PH_K], NT = s_pb[PH_NT];
+  // the tile in shared memory: x, the Adam moments m and v (unless they are
+  // used in place in global memory, for problems whose tile would not fit
+  // otherwise), the gradient, the term values
   float* sx = tile_mem;
-  float* sm = sx + D * PT;
-  float* sv = sm + D * PT;
-  float* sg = sv + D * PT;
+  float* sm = mv_global ? nullptr : sx + D * PT;
+  float* sv = mv_global ? nullptr : sm + D * PT;
+  float* sg = mv_global ? sx + D * PT : sv + D * PT;
   float* st = sg + D * PT;
   int* sflag = reinterpret_cast<int*>(st + NT * PT);
   // pose of every placed box of every particle at the current iterate: (x, y,
@@ -858,12 +861,20 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
     float xv = 0.f, mv = 0.f, vv = 0.f;
     if (gp < d.P) {
       xv = d.x_in[c * d.stride + gp];
-      if (d.load_mv) {
+      if (d.load_mv && !mv_global) {
         mv = d.m[c * d.stride + gp];
         vv = d.v[c * d.stride + gp];
       }
+      if (mv_global && !d.load_mv && d.m) {  // moments start at zero, in place
+        d.m[c * d.stride + gp] = 0.f;
+        d.v[c * d.stride + gp] = 0.f;
+      }
     }
-    sx[i] = xv; sm[i] = mv; sv[i] = vv; sg[i] = 0.f;
+    sx[i] = xv; sg[i] = 0.f;
+    if (!mv_global) {
+      sm[i] = mv;
+      sv[i] = vv;
+    }
   }
   __syncthreads();  // the tile is loaded before the placement poses are read from it
   const uint32_t* terms = s_pb + s_pb[PH_OFF_TERMS];
@@ -921,10 +932,29 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
     const float ib1 = static_cast<float>(1.0 / (1.0 - b1t)), ib2 = static_cast<float>(1.0 / (1.0 - b2t));
     for (int i = tid; i < D * PT; i += nthr) {
       const float g = sg[i] * d.gscale;
-      const float m = fmaf(d.beta1, sm[i], (1.f - d.beta1) * g);
-      const float v = fmaf(d.beta2, sv[i], (1.f - d.beta2) * g * g);
-      sm[i] = m;
-      sv[i] = v;
+      float m0, v0;
+      long gi = 0;
+      if (mv_global) {
+        const int c = i / PT, gp = tile0 + (i - c * PT);
+        gi = static_cast<long>(c) * d.stride + gp;
+        const bool in = gp < d.P;
+        m0 = in ? d.m[gi] : 0.f;
+        v0 = in ? d.v[gi] : 0.f;
+      } else {
+        m0 = sm[i];
+        v0 = sv[i];
+      }
+      const float m = fmaf(d.beta1, m0, (1.f - d.beta1) * g);
+      const float v = fmaf(d.beta2, v0, (1.f - d.beta2) * g * g);
+      if (mv_global) {
+        if (tile0 + (i % PT) < d.P) {
+          d.m[gi] = m;
+          d.v[gi] = v;
+        }
+      } else {
+        sm[i] = m;
+        sv[i] = v;
+      }
       sx[i] -= lr[i / PT] * (m * ib1) / (sqrtf(v * ib2) + d.eps);
       sg[i] = 0.f;
     }
@@ -975,8 +1005,8 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
     if (gp >= d.P) continue;
     if (d.out_grad) d.out_grad[c * d.stride + gp] = sg[i];
     if (d.x_out) d.x_out[c * d.stride + gp] = sx[i];
-    if (d.m) d.m[c * d.stride + gp] = sm[i];
-    if (d.v) d.v[c * d.stride + gp] = sv[i];
+    if (d.m && !mv_global) d.m[c * d.stride + gp] = sm[i];
+    if (d.v && !mv_global) d.v[c * d.stride + gp] = sv[i];
   }
 }
 
@@ -1053,7 +1083,7 @@ __global__ void __launch_bounds__(512, 1) optimize_kernel(LaunchArgs a) {
       __syncthreads();
       if (abort_flag) return;
     }
-    run_tile<L>(d, tile, s_sc, s_pb, reinterpret_cast<float*>(s_pb + pw), ws);
+    run_tile<L>(d, tile, s_sc, s_pb, reinterpret_cast<float*>(s_pb + pw), ws, a.mv_global != 0);
     __syncthreads();  // everyone has read s_item and the tables before they change
   }
 }
@@ -1427,11 +1457,12 @@ cudaError_t launch_sample_proposal(const uint32_t* rows, int R, const float* out
 
 // Dynamic shared memory: scene tables, the largest problem's tables and tile
 // (x, m, v, gradient, terms, flags), then the warps' exact-phase scratch.
-size_t optimize_tile_bytes(int prob_words, int D, int NT, int NSLOT, int L) {
+size_t optimize_tile_bytes(int prob_words, int D, int NT, int NSLOT, int L, bool mv_global) {
   const int PT = 32 / L;
   const size_t pw = (prob_words + 3) & ~3;
-  return 4 * pw + 4 * (4 * static_cast<size_t>(D) * PT + static_cast<size_t>(NT) * PT) + ((PT * 4 + 15) & ~15) +
-         16 * static_cast<size_t>(NSLOT) * PT;
+  const size_t arrays = mv_global ? 2 : 4;  // x, g (and m, v unless they stay in global memory)
+  return 4 * pw + 4 * (arrays * static_cast<size_t>(D) * PT + static_cast<size_t>(NT) * PT) +
+         ((PT * 4 + 15) & ~15) + 16 * static_cast<size_t>(NSLOT) * PT;
 }
 size_t optimize_scratch_bytes(int warps) { return static_cast<size_t>(WARP_SCRATCH_BYTES) * warps; }
 

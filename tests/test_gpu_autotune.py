@@ -105,3 +105,35 @@ def test_every_launch_shape_takes_the_oracle_adam_step(pkg, lanes, warps):
     step_g = (x1.T - X.astype(np.float32))[keep]
     step_r = (xr.numpy() - Xt.numpy())[keep]
     assert np.abs(step_g - step_r).max() <= 1e-3 * np.abs(step_r).max() + 2e-6
+
+
+def test_adam_moments_in_global_memory_take_the_oracle_step(pkg):
+    """A tile too large for shared memory at one lane with its Adam moments
+    (the stress skeleton, D = 252, 12 warps) runs with the moments used in
+    place in global memory; one fused iteration from non-zero moments still
+    equals the oracle's step, and the moments it leaves are the oracle's."""
+    from oracle.problem import Problem
+    sc, acts = sg.stress_problem(5001)
+    pr = Problem(sc, acts)
+    P = 40
+    X = sg.random_particles(sc, acts, P, seed=91, spread=0.5)
+    m0, v0 = sg.random_adam_state(P, pr.D, seed=92)
+    scene = pkg.Scene(sc)
+    pid = scene.set_skeleton(acts)
+    scene.set_particles(pid, X.T.astype(np.float32), m0.T.astype(np.float32), v0.T.astype(np.float32), 5)
+    scene.set_tuning(pid, 1, 12)
+    scene.optimize(pid, 1)
+    x1, m1, v1, t1 = scene.get_particles(pid)
+    scene.close()
+    assert t1 == 6
+    Xt = torch.tensor(X.astype(np.float32).astype(np.float64))
+    _, g = pr.gradient(Xt)
+    xr, mr, vr = pr.adam_step(Xt, torch.tensor(m0.astype(np.float32).astype(np.float64)),
+                              torch.tensor(v0.astype(np.float32).astype(np.float64)), 6, g, P)
+    keep = pr.kink_margin(Xt).numpy() > 1e-4
+    assert keep.sum() >= 8
+    assert np.abs(m1.T - mr.numpy())[keep].max() <= 1e-3 * np.abs(mr.numpy()[keep]).max() + 1e-9
+    assert np.abs(v1.T - vr.numpy())[keep].max() <= 1e-3 * np.abs(vr.numpy()[keep]).max() + 1e-12
+    step_g = (x1.T - X.astype(np.float32))[keep]
+    step_r = (xr.numpy() - Xt.numpy())[keep]
+    assert np.abs(step_g - step_r).max() <= 1e-3 * np.abs(step_r).max() + 2e-6
