@@ -48,7 +48,7 @@ def kernel_source_sha() -> str:
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--particles", type=int, default=P_PARTICLES)
@@ -78,7 +78,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                                          "-lms", "50", "-i", str(self.idx)], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -369,8 +369,11 @@ def main():
 
     # end to end through the C ABI with host buffers: H2D of the batch, the
     # optimisation, and the D2H read of the satisfied mask / costs / counts
-    x0 = torch.from_numpy(sg.random_particles(sc, acts, P, seed=11 + rank, spread=0.0).T.astype(np.float32).copy())
-    x0 = x0.pin_memory()
+    # the same kind of batch as the timed steps: a uniform draw, held in pinned host memory
+    with torch.cuda.stream(stream):
+        scene.sample(pid, P, 11 + 1000 * rank)
+        x_host = scene.get_particles(pid)[0]
+    x0 = torch.from_numpy(np.ascontiguousarray(x_host)).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
     with torch.cuda.stream(stream):
         scene.set_particles(pid, x0.numpy())
