@@ -31,7 +31,7 @@ int optimize_warps(int K);
 cudaError_t launch_sample_proposal(const uint32_t* rows, int R, const float* out, float* x, int stride, int P,
                                    uint64_t seed, cudaStream_t st);
 cudaError_t launch_ik(const uint32_t* pb, const uint32_t* sc, float* x, int stride, int P, int iters, float lam,
-                      float dmax, cudaStream_t st);
+                      float dmax, const int* chains, int n_chains, int chain_w, cudaStream_t st);
 }  // namespace tamp
 
 tamp_status mlp_forward_on_stream(tamp_mlp* n, const float* x_dev, int B, float* out_dev, cudaStream_t st,
@@ -64,6 +64,10 @@ struct Problem {
   uint32_t* d_prow = nullptr;
   float* d_pfeat = nullptr;
   float* d_pout = nullptr;                // [R][2 * PROP_NT]
+  // IK sampler: per box its configurations in order ([n_chain][1 + K]: length, indices)
+  int n_chain = 0;
+  std::vector<int> chains;
+  int* d_chains = nullptr;
 };
 
 }  // namespace
@@ -431,6 +435,26 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
   // record the sampler decodes with (Sec. V-A; the layouts are in tamp.h)
   bool has_goal = false;
   for (int ai = 0; ai < n; ++ai) has_goal = has_goal || acts[ai].kind == TAMP_GOAL_MIN_OBJ_DIST;
+  // the IK sampler's chains: each box's configurations, in skeleton order
+  {
+    std::vector<int> box_chain(B, -1);
+    std::vector<std::vector<int>> ch;
+    for (int k = 0; k < static_cast<int>(cfgs.size()); ++k) {
+      const int b = cfgs[k].box;
+      if (box_chain[b] < 0) {
+        box_chain[b] = static_cast<int>(ch.size());
+        ch.emplace_back();
+      }
+      ch[box_chain[b]].push_back(k);
+    }
+    const int w = 1 + static_cast<int>(cfgs.size());
+    pr.n_chain = static_cast<int>(ch.size());
+    pr.chains.assign(static_cast<size_t>(pr.n_chain) * w, 0);
+    for (int c = 0; c < pr.n_chain; ++c) {
+      pr.chains[static_cast<size_t>(c) * w] = static_cast<int>(ch[c].size());
+      for (size_t e = 0; e < ch[c].size(); ++e) pr.chains[static_cast<size_t>(c) * w + 1 + e] = ch[c][e];
+    }
+  }
   pr.R = static_cast<int>(cfgs.size());
   pr.pfeat.assign(static_cast<size_t>(pr.R) * PROP_NF, 0.f);
   pr.prow.assign(static_cast<size_t>(pr.R) * PROW_W, 0u);
@@ -890,7 +914,7 @@ tamp_status tamp_destroy_scene(tamp_scene* s) {
   for (Problem* p : s->probs) {
     free_batch(*p);
     cudaFree(p->d_blob);
-    cudaFree(p->d_prow); cudaFree(p->d_pfeat); cudaFree(p->d_pout);
+    cudaFree(p->d_prow); cudaFree(p->d_pfeat); cudaFree(p->d_pout); cudaFree(p->d_chains);
     delete p;
   }
   cudaFree(s->d_blob); cudaFree(s->d_err); cudaFree(s->d_scratch_first); cudaFree(s->d_item_counter);
@@ -959,9 +983,15 @@ tamp_status tamp_sample_particles(tamp_scene* s, int id, int P, uint64_t seed, i
     if (st != TAMP_OK) return fail(s, st, "proposal network forward: %s", tamp_mlp_last_error(s->proposal));
     CUDA_TRY(s, launch_sample_proposal(pr->d_prow, pr->R, pr->d_pout, pr->d_x, P, P, seed, s->stream));
   }
-  if (sampler & TAMP_SAMPLE_IK)
+  if (sampler & TAMP_SAMPLE_IK) {
+    if (!pr->d_chains) {
+      CUDA_TRY(s, cudaMalloc(&pr->d_chains, pr->chains.size() * 4));
+      CUDA_TRY(s, cudaMemcpyAsync(pr->d_chains, pr->chains.data(), pr->chains.size() * 4, cudaMemcpyHostToDevice,
+                                  s->stream));
+    }
     CUDA_TRY(s, launch_ik(pr->d_blob, s->d_blob, pr->d_x, P, P, TAMP_IK_ITERS, TAMP_IK_DAMPING, TAMP_IK_MAX_STEP,
-                          s->stream));
+                          pr->d_chains, pr->n_chain, 1 + pr->K, s->stream));
+  }
   return TAMP_OK;
 }
 

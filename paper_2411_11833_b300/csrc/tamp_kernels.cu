@@ -1200,18 +1200,27 @@ __device__ __forceinline__ void rot_log(const float (&E)[9], float (&w)[3]) {
   w[2] = (k == 2 ? d2 : 0.5f * E[6 + k]) * inv;
 }
 
+// The configurations of one box (its Picks and Places, in skeleton order) form
+// a chain: a Place reads the grasp yaw its Pick chose, a later Pick the yaw its
+// Place chose, and nothing reads another box's variables.  One thread per
+// (particle, chain); chains[c * chain_w] is a chain's length, then its
+// configuration indices.
 __global__ void __launch_bounds__(128) ik_configs_kernel(const uint32_t* __restrict__ pb,
                                                          const uint32_t* __restrict__ sc, float* __restrict__ x,
-                                                         int stride, int P, int iters, float lam, float dmax) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P) return;
+                                                         int stride, int P, int iters, float lam, float dmax,
+                                                         const int* __restrict__ chains, int n_chains,
+                                                         int chain_w) {
+  const long g = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (g >= static_cast<long>(P) * n_chains) return;
+  const int i = static_cast<int>(g % P), chain = static_cast<int>(g / P);
+  const int* ch = chains + chain * chain_w;
   const int nj = sc[SH_NJ];
   const float* arm = reinterpret_cast<const float*>(sc + sc[SH_OFF_ARM]);
   const float* tl = arm + 12;
-  const int K = pb[PH_K];
   const float lam2 = lam * lam;
 #define XG(c) x[(c) * stride + i]
-  for (int k = 0; k < K; ++k) {
+  for (int ci = 0; ci < ch[0]; ++ci) {
+    const int k = ch[1 + ci];
     const int* cf = reinterpret_cast<const int*>(pb + pb[PH_OFF_CFG] + k * CFG_W);
     const float* cff = reinterpret_cast<const float*>(cf);
     const int kind = cf[CF_KIND], qo = cf[CF_QOFF], go = cf[CF_GOFF], tsrc = cf[CF_TSRC];
@@ -1350,9 +1359,11 @@ __global__ void __launch_bounds__(128) ik_configs_kernel(const uint32_t* __restr
 }
 
 cudaError_t launch_ik(const uint32_t* pb, const uint32_t* sc, float* x, int stride, int P, int iters, float lam,
-                      float dmax, cudaStream_t st) {
-  if (P == 0 || iters <= 0) return cudaSuccess;
-  ik_configs_kernel<<<(P + 127) / 128, 128, 0, st>>>(pb, sc, x, stride, P, iters, lam, dmax);
+                      float dmax, const int* chains, int n_chains, int chain_w, cudaStream_t st) {
+  if (P == 0 || iters <= 0 || n_chains == 0) return cudaSuccess;
+  const long threads = static_cast<long>(P) * n_chains;
+  ik_configs_kernel<<<static_cast<unsigned>((threads + 127) / 128), 128, 0, st>>>(pb, sc, x, stride, P, iters, lam,
+                                                                                dmax, chains, n_chains, chain_w);
   return cudaGetLastError();
 }
 
