@@ -401,6 +401,11 @@ def main():
     kern_s = sum(kern_ms) / len(kern_ms) / 1e3
     props = torch.cuda.get_device_properties(dev)
     peak = flops.fp32_peak_tflops(props.multi_processor_count, 2032.0)
+    import ctypes
+    probe_tf, probe_ms = ctypes.c_double(), ctypes.c_double()
+    probe = None
+    if pkg._native.load().tamp_measure_fp32_peak(local, ctypes.byref(probe_tf), ctypes.byref(probe_ms)) == 0:
+        probe = round(probe_tf.value, 2)
     achieved = launch_flops / kern_s / 1e12
     sha = kernel_source_sha()
     traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["source_sha"] == sha and args.workload == "packing" else None
@@ -415,7 +420,8 @@ def main():
                      "kernel": "optimize_kernel", "flop_per_launch": launch_flops,
                      "executed_tflops": executed / kern_s / 1e12,
                      "exact_candidates": {"cuboid": work[0], "box": work[1]},
-                     "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x 2032 MHz (max SM clock)"},
+                     "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x 2032 MHz (max SM clock)",
+                     "ffma_probe_tflops": probe},
         "e2e": {"value": P * T / e2e_s, "unit": "particle-iters/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": 2 * args.steps,

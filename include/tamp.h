@@ -286,6 +286,13 @@ tamp_status tamp_set_tuning(tamp_scene *scene, const int *problem_ids, int n_pro
 /* Text of the last error on this scene ("" if none); valid until the next call. */
 const char *tamp_last_error(const tamp_scene *scene);
 
+/* Measurement utility, not part of the method: times independent FFMA chains
+ * filling every SM of `device` on the legacy default stream and returns the
+ * achieved FP32 rate (2 FLOP per FFMA) in *tflops and the kernel time in *ms
+ * (may be NULL) -- the measured counterpart of the FP32 peak the roofline of
+ * the optimisation kernel is quoted against.  Synchronises. */
+tamp_status tamp_measure_fp32_peak(int device, double *tflops, double *ms);
+
 /* ---------------------------------------------------------------------------
  * Learned particle proposals (Sec. V-A and Sec. VIII: particles may be seeded
  * from learned samplers instead of uniformly).  The paper leaves the sampler

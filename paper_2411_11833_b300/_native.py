@@ -83,6 +83,8 @@ SIGNATURES = {
     "tamp_set_proposal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "tamp_autotune": (ctypes.c_int, [ctypes.c_void_p, c_int_p, ctypes.c_int, ctypes.c_int, c_int_p, c_int_p, c_float_p]),
     "tamp_set_tuning": (ctypes.c_int, [ctypes.c_void_p, c_int_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "tamp_measure_fp32_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double)]),
     "tamp_proposal_rows": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_int_p]),
 }

@@ -32,6 +32,7 @@ cudaError_t launch_sample_proposal(const uint32_t* rows, int R, const float* out
                                    uint64_t seed, cudaStream_t st);
 cudaError_t launch_ik(const uint32_t* pb, const uint32_t* sc, float* x, int stride, int P, int iters, float lam,
                       float dmax, const int* chains, int n_chains, int chain_w, cudaStream_t st);
+cudaError_t launch_ffma_probe(float* out, int blocks, int iters, cudaStream_t st);
 }  // namespace tamp
 
 tamp_status mlp_forward_on_stream(tamp_mlp* n, const float* x_dev, int B, float* out_dev, cudaStream_t st,
@@ -1271,6 +1272,34 @@ tamp_status tamp_set_tuning(tamp_scene* s, const int* ids, int n, int lanes, int
   tamp_status st = plan_jobs(s, jobs, 0, &probe, lanes, warps);
   if (st != TAMP_OK) return st;
   s->tuning[job_key(jobs)] = {lanes, warps};
+  return TAMP_OK;
+}
+
+tamp_status tamp_measure_fp32_peak(int device, double* tflops, double* ms) {
+  if (!tflops) return TAMP_ERR_INVALID_ARG;
+  DeviceGuard g(device);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return TAMP_ERR_CUDA;
+  const int blocks = sms * 8, iters = 4096;  // 8 x 256 threads per SM, 8 chains each
+  float* out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&out, static_cast<size_t>(blocks) * 256 * 4);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = launch_ffma_probe(out, blocks, iters, nullptr);  // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(e0, nullptr);
+  if (e == cudaSuccess) e = launch_ffma_probe(out, blocks, iters, nullptr);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, nullptr);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaFree(out);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return TAMP_ERR_CUDA;
+  const double flop = 2.0 * blocks * 256.0 * iters * 16.0 * 8.0;
+  *tflops = flop / (t * 1e-3) / 1e12;
+  if (ms) *ms = t;
   return TAMP_OK;
 }
 

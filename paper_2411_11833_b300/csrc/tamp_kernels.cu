@@ -1367,6 +1367,32 @@ cudaError_t launch_ik(const uint32_t* pb, const uint32_t* sc, float* x, int stri
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ FP32 peak probe
+// Measurement utility (not part of the method): independent FFMA chains, 8 per
+// thread, enough warps to fill every SM, so the FP32 pipes are the only limit.
+// 2 FLOP per FFMA; the result is written so that nothing is optimised away.
+__global__ void __launch_bounds__(256) ffma_probe_kernel(float* out, int iters, float a, float b) {
+  float v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = threadIdx.x * 1e-3f + k;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = fmaf(v[k], a, b);
+    }
+  }
+  float sum = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) sum += v[k];
+  if (sum == 1234.5f) out[blockIdx.x * blockDim.x + threadIdx.x] = sum;  // practically never
+}
+
+cudaError_t launch_ffma_probe(float* out, int blocks, int iters, cudaStream_t st) {
+  ffma_probe_kernel<<<blocks, 256, 0, st>>>(out, iters, 0.999999f, 1e-7f);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ graph chunk controller
 // After each chunk of a captured optimisation: advance every problem's step
 // count, and raise the stop flag when stopping on the first satisfying particle

@@ -137,3 +137,16 @@ def test_adam_moments_in_global_memory_take_the_oracle_step(pkg):
     step_g = (x1.T - X.astype(np.float32))[keep]
     step_r = (xr.numpy() - Xt.numpy())[keep]
     assert np.abs(step_g - step_r).max() <= 1e-3 * np.abs(step_r).max() + 2e-6
+
+
+def test_fp32_peak_probe_is_near_the_unit_count_peak(pkg):
+    """The FFMA-chain probe behind the roofline denominator: its rate is of
+    the order of SMs x 128 lanes x 2 FLOP x clock (it may run below the
+    maximum clock under the power cap, never far above)."""
+    import ctypes
+    from paper_2411_11833_b300 import _native, flops
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    assert _native.load().tamp_measure_fp32_peak(0, ctypes.byref(tf), ctypes.byref(ms)) == 0
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nominal = flops.fp32_peak_tflops(sms, 2032.0)
+    assert 0.4 * nominal < tf.value < 1.05 * nominal, (tf.value, nominal)
