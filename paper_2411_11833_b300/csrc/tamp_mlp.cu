@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -205,7 +206,10 @@ struct FwdArgs {
   const unsigned char* Wp;            // packed BF16 forward operands (pk_off)
   const float* b[4];
   float* out;                         // [B][OUT]
-  float* Z[3]; __nv_bfloat16* A[3];   // training: pre-activations (FP32) and activations (BF16), [B][H]
+  // training only (else null): pre-activations Z_l [B][H] (FP32), and the
+  // BF16 operands of the weight gradients, feature-major: x^T [IN][ldT],
+  // A_l^T [H][ldT]
+  float* Z[3]; __nv_bfloat16* XT; __nv_bfloat16* AT[3]; int ldT;
   int* err;
 };
 
@@ -240,6 +244,9 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
     for (int e = 0; e < 8; ++e) v[e] = rr < Rv ? a.x[static_cast<long>(row0 + rr) * IN + kk + e] : 0.f;
     *reinterpret_cast<uint4*>(opA + blk_off(rr, kk, ROWS)) =
         make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+    if (a.XT && rr < Rv)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) a.XT[static_cast<long>(kk + e) * a.ldT + row0 + rr] = __float2bfloat16_rn(v[e]);
   }
   fence_proxy_async();
   tc_fence_before();
@@ -291,11 +298,16 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
                 make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
           if (a.Z[l] && r < a.B) {
             float4* zd = reinterpret_cast<float4*>(a.Z[l] + static_cast<long>(r) * H + c0);
-            uint4* ad = reinterpret_cast<uint4*>(a.A[l] + static_cast<long>(r) * H + c0);
 #pragma unroll
             for (int q = 0; q < 8; ++q) zd[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            // feature-major: for each column the 32 rows of a warp are 64 contiguous bytes
+            __nv_bfloat16* at = a.AT[l] + static_cast<long>(c0) * a.ldT + r;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) ad[q] = make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
+            for (int j = 0; j < 16; ++j) {
+              const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&hp[j]);
+              at[static_cast<long>(2 * j) * a.ldT] = h2.x;
+              at[static_cast<long>(2 * j + 1) * a.ldT] = h2.y;
+            }
           }
         } else if (r < a.B) {
           float4* od = reinterpret_cast<float4*>(a.out + static_cast<long>(r) * OUT + c0);
@@ -321,157 +333,337 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
 // mean over rows; dOut = d(mean)/d(out).
 __global__ void mlp_loss_kernel(const float* out, const float* y, const float* mask, int B, float* dout,
                                 float* loss_sum) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  // one thread per (row, target): consecutive threads read consecutive targets
+  const long i = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
   float l = 0.f;
-  if (r < B) {
+  if (i < static_cast<long>(B) * NTGT) {
+    const long r = i / NTGT;
+    const int k = static_cast<int>(i - r * NTGT);
     const float inv = 1.f / static_cast<float>(B);
-    for (int k = 0; k < NTGT; ++k) {
-      const float mu = out[static_cast<long>(r) * OUT + k], s = out[static_cast<long>(r) * OUT + NTGT + k];
-      const float m = mask[static_cast<long>(r) * NTGT + k], d = y[static_cast<long>(r) * NTGT + k] - mu;
-      const float e = expf(-2.f * s);
-      l += m * (0.5f * d * d * e + s);
-      dout[static_cast<long>(r) * OUT + k] = m * (-d * e) * inv;
-      dout[static_cast<long>(r) * OUT + NTGT + k] = m * (1.f - d * d * e) * inv;
-    }
+    const float mu = out[r * OUT + k], s = out[r * OUT + NTGT + k];
+    const float m = mask[i], d = y[i] - mu;
+    const float e = expf(-2.f * s);
+    l = m * (0.5f * d * d * e + s);
+    dout[r * OUT + k] = m * (-d * e) * inv;
+    dout[r * OUT + NTGT + k] = m * (1.f - d * d * e) * inv;
   }
   for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-  if ((threadIdx.x & 31) == 0 && l != 0.f) atomicAdd(loss_sum, l / static_cast<float>(B));
+  __shared__ float part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = l;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float sum = 0.f;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) sum += part[w];
+    if (sum != 0.f) atomicAdd(loss_sum, sum / static_cast<float>(B));
+  }
 }
 
 // ------------------------------------------------------------------ backward
-struct BwdArgs {
-  const float* x; int B;
-  const unsigned char* WpT;           // packed BF16 transposed operands W^T (pk_off)
-  const float* Z[3]; const __nv_bfloat16* A[3];
-  const float* dout;                  // [B][OUT]
-  __nv_bfloat16* dz[2];               // [B][H] scratch, ping-pong between layers
-  float* grad;                        // [N_PARAMS] accumulated (weights then bias per layer)
+// Two kernels.  (1) Per 128-row tile: dZ_l for l = 3 .. 0 through the layers,
+// dA_{l-1} = dZ_l W_l on the tensor core (W_l^T packed, one bulk copy per
+// layer, prefetched during the previous epilogue), dZ_{l-1} = dA_{l-1} *
+// gelu'(Z_{l-1}) kept in shared memory as the next product's operand and
+// written feature-major for (2).  (2) Per (layer, 128 outputs, row split):
+// dW_l = dZ_l^T A_{l-1} accumulated over the split's rows in tensor memory
+// (rows are the GEMM's K), both operands read feature-major in 16-byte pieces
+// and double-buffered; each split adds its partial dW with one atomic per
+// weight, and db_l with one per output.
+struct DzArgs {
+  int B, ldT;
+  const float* dout;                  // [B][OUT]: dL/d(outputs) = dZ_3
+  const float* Z[3];                  // [B][H]
+  const unsigned char* WpT;           // packed W^T operands (pk_off)
+  __nv_bfloat16* dZT[4];              // feature-major dZ_l: [H][ldT] (l < 3), [OUT][ldT] (l = 3)
   int* err;
 };
 
-// Per 128-row tile, layer l = 3 .. 0:
-//   dW_l = dZ_l^T A_{l-1} (A_{-1} = x), reduced over the tile's rows by the
-//   tensor core (rows are the GEMM's K) and added to the global gradient;
-//   db_l = column sums of dZ_l;
-//   dZ_{l-1} = (dZ_l W_l) * gelu'(Z_{l-1}).
-__global__ void __launch_bounds__(THREADS, 1) mlp_backward_kernel(BwdArgs a) {
+__global__ void __launch_bounds__(THREADS, 1) mlp_backward_dz_kernel(DzArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* opA = smem;
   unsigned char* opB = smem + SMEM_A;
-  __shared__ __align__(8) uint64_t bar, bar_w;
+  __shared__ __align__(8) uint64_t bar_mma, bar_w;
   __shared__ uint32_t tslot;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31, grp = warp >> 2;
   const int row = 32 * (warp & 3) + lane, row0 = blockIdx.x * ROWS, r = row0 + row;
   const int Rv = min(ROWS, a.B - row0);
+  bool w_pending = false;
   if (t == 0) {
-    mbar_init(&bar);
+    mbar_init(&bar_mma);
     mbar_init(&bar_w);
     fence_proxy_async();
+    mbar_expect_tx(&bar_w, static_cast<uint32_t>(pk_bytes(3)));
+    bulk_g2s(opB, a.WpT + pk_off(3), static_cast<uint32_t>(pk_bytes(3)), &bar_w);
+    w_pending = true;
   }
+  if (warp == 0) tmem_alloc(&tslot);
+  // dZ_3 = dL/d(outputs): the A operand (K = 32) and its feature-major copy
+  for (int c = t; c < ROWS * (OUT / 8); c += THREADS) {
+    const int rr = c / (OUT / 8), kk = (c % (OUT / 8)) * 8;
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = rr < Rv ? a.dout[static_cast<long>(row0 + rr) * OUT + kk + e] : 0.f;
+    *reinterpret_cast<uint4*>(opA + blk_off(rr, kk, ROWS)) =
+        make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+    if (rr < Rv)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) a.dZT[3][static_cast<long>(kk + e) * a.ldT + row0 + rr] = __float2bfloat16_rn(v[e]);
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tslot;
+  uint32_t ph_mma = 0, ph_w = 0;
+  for (int l = 3; l >= 1; --l) {
+    const int K = kdim(l), N = ndim(l);
+    if (t == 0) {
+      const bool okw = mbar_wait_bounded(&bar_w, ph_w);
+      w_pending = !okw;
+      if (okw) issue_gemm(tmem, opA, opB, K, N, &bar_mma);  // dA_{l-1} [128 x K] = dZ_l [128 x N] . W_l
+      else atomicOr(a.err, ERR_WAIT);
+    }
+    ph_w ^= 1u;
+    const bool okm = mbar_wait_bounded(&bar_mma, ph_mma);
+    ph_mma ^= 1u;
+    if (!okm) atomicOr(a.err, ERR_WAIT);
+    tc_fence_after();
+    if (__syncthreads_and(okm) == 0) break;
+    if (t == 0 && l > 1) {
+      mbar_expect_tx(&bar_w, static_cast<uint32_t>(pk_bytes(l - 1)));
+      bulk_g2s(opB, a.WpT + pk_off(l - 1), static_cast<uint32_t>(pk_bytes(l - 1)), &bar_w);
+      w_pending = true;
+    }
+    __nv_bfloat16* dzt = a.dZT[l - 1];
+    for (int c0 = grp * (K / NGRP); c0 < (grp + 1) * (K / NGRP); c0 += 32) {
+      float v[32];
+      tmem_ld32(lane_addr(tmem, c0), v);
+      uint32_t hp[16];
+      if (r < a.B) {
+        const float4* zs = reinterpret_cast<const float4*>(a.Z[l - 1] + static_cast<long>(r) * H + c0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 z = zs[q];
+          hp[2 * q] = pack_bf16x2(v[4 * q] * gelu_grad(z.x), v[4 * q + 1] * gelu_grad(z.y));
+          hp[2 * q + 1] = pack_bf16x2(v[4 * q + 2] * gelu_grad(z.z), v[4 * q + 3] * gelu_grad(z.w));
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) hp[q] = 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(opA + blk_off(row, c0 + 8 * q, ROWS)) =
+            make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
+      if (r < a.B) {
+        __nv_bfloat16* dt = dzt + static_cast<long>(c0) * a.ldT + r;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&hp[j]);
+          dt[static_cast<long>(2 * j) * a.ldT] = h2.x;
+          dt[static_cast<long>(2 * j + 1) * a.ldT] = h2.y;
+        }
+      }
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  if (t == 0 && w_pending) mbar_wait_bounded(&bar_w, ph_w);
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem);
+}
+
+constexpr int DW_THREADS = 256;        // 8 warps: TMEM lane quarter (w % 4), column half (w / 4)
+constexpr int DW_CHUNK = 64;           // rows per staged chunk (4 MMAs of K = 16)
+constexpr size_t DW_BUF_A = 128 * DW_CHUNK * 2, DW_BUF_B = 256 * DW_CHUNK * 2;
+constexpr size_t DW_SMEM = 2 * (DW_BUF_A + DW_BUF_B);
+
+constexpr int DW_MAX_SPLITS = 32;
+
+struct DwArgs {
+  int B, ldT, rows_per_split;
+  const __nv_bfloat16* XT;            // [IN][ldT]
+  const __nv_bfloat16* AT[3];         // [H][ldT]
+  const __nv_bfloat16* dZT[4];        // [H][ldT] (l < 3), [OUT][ldT] (l = 3)
+  float* part;                        // [split][N_PARAMS]: this split's share of dW and db
+  int* err;
+};
+
+// 16 bytes (8 BF16) of a feature-major row starting at column r (zero past B)
+__device__ __forceinline__ uint4 load8(const __nv_bfloat16* p, int r, int B) {
+  if (r + 8 <= B) return *reinterpret_cast<const uint4*>(p);
+  uint32_t w[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const unsigned short lo = r + 2 * q < B ? __bfloat16_as_ushort(p[2 * q]) : 0;
+    const unsigned short hi = r + 2 * q + 1 < B ? __bfloat16_as_ushort(p[2 * q + 1]) : 0;
+    w[q] = static_cast<uint32_t>(lo) | static_cast<uint32_t>(hi) << 16;
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+__device__ __forceinline__ float sum8(const uint4& u) {
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+  float s = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) s += __low2float(h[q]) + __high2float(h[q]);
+  return s;
+}
+
+// One chunk of both operands: A = 128 rows, B = NBR rows, 64 columns each.
+template <int NBR>
+__device__ __forceinline__ void dw_stage(unsigned char* bufA, unsigned char* bufB, const __nv_bfloat16* srcA,
+                                         const __nv_bfloat16* srcB, int ldT, int r0, int r_end, int ra, int kc,
+                                         bool sum_a, bool sum_b, float (&csA)[4], float (&csB)[8]) {
+  constexpr int KB = (NBR + 31) / 32;
+  uint4 ua[4], ub[KB];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) ua[k] = load8(srcA + static_cast<long>(ra + 32 * k) * ldT + r0 + kc, r0 + kc, r_end);
+#pragma unroll
+  for (int k = 0; k < KB; ++k)
+    ub[k] = (NBR % 32 == 0 || ra + 32 * k < NBR)
+                ? load8(srcB + static_cast<long>(ra + 32 * k) * ldT + r0 + kc, r0 + kc, r_end)
+                : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    *reinterpret_cast<uint4*>(bufA + blk_off(ra + 32 * k, kc, 128)) = ua[k];
+    if (sum_a) csA[k] += sum8(ua[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < KB; ++k)
+    if (NBR % 32 == 0 || ra + 32 * k < NBR) {
+      *reinterpret_cast<uint4*>(bufB + blk_off(ra + 32 * k, kc, NBR)) = ub[k];
+      if (sum_b) csB[k] += sum8(ub[k]);
+    }
+}
+
+__global__ void __launch_bounds__(DW_THREADS, 2) mlp_backward_dw_kernel(DwArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  // two buffers, each an A and a B operand chunk; mbarrier phases and pending
+  // commits of the two kept as bit masks (no dynamically indexed arrays)
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ uint32_t tslot;
+  __shared__ float colsum[256];
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31, grp = warp >> 2;
+  const int l = blockIdx.x >> 1, half = blockIdx.x & 1;
+  const bool swapped = l == 3;  // 32 outputs: M runs over the inputs, D = dW^T
+  const int K = kdim(l), N = ndim(l);
+  // A operand: 128 rows of dZ_l^T (outputs), or of A_2^T (inputs) when swapped;
+  // B operand: the N' rows of the other factor
+  const __nv_bfloat16* srcA = swapped ? a.AT[2] + static_cast<long>(half * 128) * a.ldT
+                                      : a.dZT[l] + static_cast<long>(half * 128) * a.ldT;
+  const __nv_bfloat16* srcB = swapped ? a.dZT[3] : (l == 0 ? a.XT : a.AT[l - 1]);
+  const int NB_ = swapped ? N : K;  // the GEMM's N'
+  const bool sum_a = !swapped, sum_b = swapped && half == 0;  // db: each output's column once
+  const int r_begin = blockIdx.y * a.rows_per_split, r_end = min(a.B, r_begin + a.rows_per_split);
+  if (t == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+  }
+  for (int i = t; i < 256; i += DW_THREADS) colsum[i] = 0.f;
   if (warp == 0) tmem_alloc(&tslot);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tslot;
-  uint32_t phase = 0, ph_w = 0;
+  uint32_t ph = 0u, pend = 0u;
   bool ok = true;
-  for (int l = 3; l >= 0 && ok; --l) {
-    const int K = kdim(l), N = ndim(l);
-    // dZ_l source: the loss gradient (FP32) for the output layer, else the
-    // previous layer's BF16 result
-    const float* dzf = l == 3 ? a.dout + static_cast<long>(row0) * OUT : nullptr;
-    const __nv_bfloat16* dzb = l == 3 ? nullptr : a.dz[l & 1] + static_cast<long>(row0) * H;
-    const long dzs = l == 3 ? OUT : H;
-    float* gW = a.grad + w_off(l);
-    float* gb = a.grad + b_off(l);
-    // ---- bias: column sums over the tile's rows
-    for (int n = t; n < N; n += THREADS) {
-      float s = 0.f;
-      for (int i = 0; i < Rv; ++i) s += dzf ? dzf[i * dzs + n] : __bfloat162float(dzb[i * dzs + n]);
-      atomicAdd(&gb[n], s);
+  int ci = 0;
+  const int ra = t >> 3, kc = (t & 7) * 8;  // this thread's staging rows (ra + 32 k) and column piece
+  float csA[4] = {0.f, 0.f, 0.f, 0.f}, csB[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int r0 = r_begin; r0 < r_end; r0 += DW_CHUNK, ++ci) {
+    const int b = ci & 1;
+    unsigned char* bA = smem + b * DW_BUF_A;
+    unsigned char* bB = smem + 2 * DW_BUF_A + b * DW_BUF_B;
+    if (pend >> b & 1u) {  // the MMAs of two chunks ago read this buffer
+      const bool okb = mbar_wait_bounded(&bar[b], ph >> b & 1u);
+      ph ^= 1u << b;
+      pend &= ~(1u << b);
+      if (!okb) atomicOr(a.err, ERR_WAIT);
+      ok = __syncthreads_and(okb) != 0;
+      if (!ok) break;
     }
-    // ---- weights: tiles of 128 along the wider of (outputs, inputs)
-    if (N >= ROWS) {
-      // dW[n][k]: M = outputs (128 per tile), N' = inputs, K' = rows
-      for (int n0 = 0; n0 < N && ok; n0 += ROWS) {
-        if (dzf) stage(opA, ROWS, ROWS, dzf + n0, 1, dzs, N - n0, Rv);
-        else stage(opA, ROWS, ROWS, dzb + n0, 1, dzs, N - n0, Rv);
-        if (l == 0) stage(opB, K, ROWS, a.x + static_cast<long>(row0) * IN, 1, IN, K, Rv);
-        else stage(opB, K, ROWS, a.A[l - 1] + static_cast<long>(row0) * H, 1, H, K, Rv);
-        ok = gemm_tile(tmem, opA, opB, K, ROWS, &bar, phase, a.err);
-        if (!ok) break;
-        const int per = K >= 128 ? K / NGRP : K;
-        if (K >= 128 || grp == 0) {
-          for (int c0 = grp * per; c0 < grp * per + per; c0 += 32) {
-            float v[32];
-            tmem_ld32(lane_addr(tmem, c0), v);
-#pragma unroll
-            for (int j = 0; j < 32; ++j)  // K = 48 for the first layer: the last group is half empty
-              if (n0 + row < N && c0 + j < K) atomicAdd(&gW[static_cast<long>(n0 + row) * K + c0 + j], v[j]);
-          }
-        }
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-      }
-    } else {
-      // dW^T[k][n]: M = inputs (128 per tile), N' = outputs, K' = rows
-      for (int k0 = 0; k0 < K && ok; k0 += ROWS) {
-        stage(opA, ROWS, ROWS, a.A[l - 1] + static_cast<long>(row0) * H + k0, 1, H, K - k0, Rv);
-        if (dzf) stage(opB, N, ROWS, dzf, 1, dzs, N, Rv);
-        else stage(opB, N, ROWS, dzb, 1, dzs, N, Rv);
-        ok = gemm_tile(tmem, opA, opB, N, ROWS, &bar, phase, a.err);
-        if (!ok) break;
-        if (grp == 0) {
-          for (int c0 = 0; c0 < N; c0 += 32) {
-            float v[32];
-            tmem_ld32(lane_addr(tmem, c0), v);
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (k0 + row < K) atomicAdd(&gW[static_cast<long>(c0 + j) * K + k0 + row], v[j]);
-          }
-        }
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-      }
-    }
-    if (l == 0 || !ok) break;
-    // ---- dA_{l-1} = dZ_l W_l: M = rows, N' = K (inputs of layer l), K' = N (outputs);
-    // W^T arrives packed by one bulk copy while the threads stage dZ
-    if (t == 0) {
-      mbar_expect_tx(&bar_w, static_cast<uint32_t>(pk_bytes(l)));
-      bulk_g2s(opB, a.WpT + pk_off(l), static_cast<uint32_t>(pk_bytes(l)), &bar_w);
-    }
-    if (dzf) stage(opA, ROWS, N, dzf, dzs, 1, Rv, N);
-    else stage(opA, ROWS, N, dzb, dzs, 1, Rv, N);
-    if (t == 0 && !mbar_wait_bounded(&bar_w, ph_w)) atomicOr(a.err, ERR_WAIT);
-    ph_w ^= 1u;
-    ok = gemm_tile(tmem, opA, opB, K, N, &bar, phase, a.err);
-    if (!ok) break;
-    __nv_bfloat16* dzo = a.dz[(l - 1) & 1] + static_cast<long>(row0) * H;
-    for (int c0 = grp * (K / NGRP); c0 < (grp + 1) * (K / NGRP); c0 += 32) {
-      float v[32];
-      tmem_ld32(lane_addr(tmem, c0), v);
-      if (r < a.B) {
-        const float4* zs = reinterpret_cast<const float4*>(a.Z[l - 1] + static_cast<long>(r) * H + c0);
-        uint4* dd = reinterpret_cast<uint4*>(dzo + static_cast<long>(row) * H + c0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 z0 = zs[2 * q], z1 = zs[2 * q + 1];
-          dd[q] = make_uint4(pack_bf16x2(v[8 * q] * gelu_grad(z0.x), v[8 * q + 1] * gelu_grad(z0.y)),
-                             pack_bf16x2(v[8 * q + 2] * gelu_grad(z0.z), v[8 * q + 3] * gelu_grad(z0.w)),
-                             pack_bf16x2(v[8 * q + 4] * gelu_grad(z1.x), v[8 * q + 5] * gelu_grad(z1.y)),
-                             pack_bf16x2(v[8 * q + 6] * gelu_grad(z1.z), v[8 * q + 7] * gelu_grad(z1.w)));
-        }
-      }
-    }
+    // every piece of this thread's share first (independent 16-byte loads),
+    // then the stores: thread t stages rows t / 8 + 32 k, columns 8 (t % 8) ..
+    if (NB_ == 256)
+      dw_stage<256>(bA, bB, srcA, srcB, a.ldT, r0, r_end, ra, kc, sum_a, sum_b, csA, csB);
+    else if (NB_ == 48)
+      dw_stage<48>(bA, bB, srcA, srcB, a.ldT, r0, r_end, ra, kc, sum_a, sum_b, csA, csB);
+    else
+      dw_stage<32>(bA, bB, srcA, srcB, a.ldT, r0, r_end, ra, kc, sum_a, sum_b, csA, csB);
+    fence_proxy_async();
     tc_fence_before();
-    __syncthreads();  // dZ_{l-1} written (global) before the next layer stages it
-    tc_fence_after();
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(bA), b0 = smem_u32(bB), id = instr_desc(ROWS, NB_);
+      for (int c = 0; c < DW_CHUNK / 16; ++c)
+        umma_bf16(tmem, smem_desc(a0 + c * ROWS * 32), smem_desc(b0 + c * NB_ * 32), id, (ci > 0 || c > 0) ? 1u : 0u);
+      umma_commit(&bar[b]);
+    }
+    pend |= 1u << b;
   }
+  // drain: the last commit covers every MMA issued before it
+  for (int b = 0; b < 2; ++b)
+    if (pend >> b & 1u) {
+      if (!mbar_wait_bounded(&bar[b], ph >> b & 1u)) {
+        atomicOr(a.err, ERR_WAIT);
+        ok = false;
+      }
+      ph ^= 1u << b;
+    }
+  tc_fence_after();
+  ok = __syncthreads_and(ok) != 0;
+  // this split's partial dW, written whole (zeros for a split past the last row)
+  float* part = a.part + static_cast<long>(blockIdx.y) * N_PARAMS;
+  if (ok) {
+    float* gW = part + w_off(l);
+    const int row = 32 * (warp & 3) + lane;
+    const int per = NB_ >= 128 ? NB_ / 2 : NB_;
+    if (NB_ >= 128 || grp == 0) {
+      for (int c0 = grp * per; c0 < grp * per + per; c0 += 32) {
+        float v[32];
+        tmem_ld32(lane_addr(tmem, c0), v);
+        if (ci == 0)
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = 0.f;
+        if (swapped) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (c0 + j < NB_) gW[static_cast<long>(c0 + j) * K + half * 128 + row] = v[j];
+        } else {
+          float4* dst = reinterpret_cast<float4*>(gW + static_cast<long>(half * 128 + row) * K + c0);
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (c0 + 4 * q < NB_) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+      }
+    }
+  }
+  // the bias: each row's sum over the split, from the registers of its 8 threads
+  if (sum_a)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) atomicAdd(&colsum[ra + 32 * k], csA[k]);
+  if (sum_b)
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (ra + 32 * k < NB_) atomicAdd(&colsum[ra + 32 * k], csB[k]);
   __syncthreads();
+  if (sum_a || sum_b) {
+    float* gb = part + b_off(l);
+    const int nb = sum_a ? 128 : N;
+    for (int i = t; i < nb; i += DW_THREADS) gb[(sum_a ? half * 128 : 0) + i] = colsum[i];
+  }
   if (warp == 0) tmem_dealloc(tmem);
+}
+
+// grad = sum over the row splits of their partial gradients
+__global__ void mlp_reduce_kernel(const float* __restrict__ part, int splits, float* __restrict__ grad, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float sum = 0.f;
+  for (int s = 0; s < splits; ++s) sum += part[static_cast<long>(s) * n + i];
+  grad[i] = sum;
 }
 
 // ------------------------------------------------------------------ Adam on the FP32 master weights
@@ -523,11 +715,14 @@ struct tamp_mlp {
   float* grad = nullptr;
   float* m = nullptr;
   float* v = nullptr;
-  float* Z = nullptr;          // [3][max_batch][H]
-  __nv_bfloat16* A = nullptr;  // [3][max_batch][H]
-  __nv_bfloat16* dz = nullptr; // [2][max_batch][H]
+  int ldT = 0;                   // row length of the feature-major arrays: max_batch rounded up to 64
+  float* Z = nullptr;            // [3][max_batch][H]
+  __nv_bfloat16* XT = nullptr;   // [IN][ldT]
+  __nv_bfloat16* AT = nullptr;   // [3][H][ldT]
+  __nv_bfloat16* dZT = nullptr;  // [3][H][ldT] then [OUT][ldT]
   float* out = nullptr;        // [max_batch][OUT]
   float* dout = nullptr;       // [max_batch][OUT]
+  float* part = nullptr;       // [DW_MAX_SPLITS][N_PARAMS]: per row split partial gradients
   float* loss = nullptr;
   int* err = nullptr;
   long step = 0;
@@ -567,8 +762,11 @@ cudaError_t enable_smem(int device) {
   cudaError_t e = cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(SMEM_BYTES));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(mlp_backward_dz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(SMEM_BYTES));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mlp_backward_dw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(DW_SMEM));
   if (e == cudaSuccess) done |= bit;
   return e;
 }
@@ -578,9 +776,11 @@ FwdArgs fwd_args(tamp_mlp* n, const float* x, int B, float* out, bool train) {
   a.x = x; a.B = B; a.out = out; a.err = n->err;
   a.Wp = n->wp;
   for (int l = 0; l < 4; ++l) a.b[l] = n->params + b_off(l);
+  a.ldT = n->ldT;
+  a.XT = train ? n->XT : nullptr;
   for (int l = 0; l < 3; ++l) {
     a.Z[l] = train ? n->Z + static_cast<size_t>(l) * n->max_batch * H : nullptr;
-    a.A[l] = train ? n->A + static_cast<size_t>(l) * n->max_batch * H : nullptr;
+    a.AT[l] = train ? n->AT + static_cast<size_t>(l) * H * n->ldT : nullptr;
   }
   return a;
 }
@@ -597,22 +797,31 @@ tamp_status check_err(tamp_mlp* n) {
 tamp_status gradient(tamp_mlp* n, const float* x, const float* y, const float* mask, int B) {
   MLP_TRY(n, enable_smem(n->device));
   const int tiles = (B + ROWS - 1) / ROWS;
-  MLP_TRY(n, cudaMemsetAsync(n->grad, 0, N_PARAMS * 4, n->stream));
   MLP_TRY(n, cudaMemsetAsync(n->loss, 0, 4, n->stream));
   mlp_forward_kernel<<<tiles, THREADS, SMEM_BYTES, n->stream>>>(fwd_args(n, x, B, n->out, true));
   MLP_TRY(n, cudaGetLastError());
-  mlp_loss_kernel<<<(B + 255) / 256, 256, 0, n->stream>>>(n->out, y, mask, B, n->dout, n->loss);
+  mlp_loss_kernel<<<static_cast<int>((static_cast<long>(B) * NTGT + 255) / 256), 256, 0, n->stream>>>(
+      n->out, y, mask, B, n->dout, n->loss);
   MLP_TRY(n, cudaGetLastError());
-  BwdArgs b{};
-  b.x = x; b.B = B; b.dout = n->dout; b.grad = n->grad; b.err = n->err;
-  b.WpT = n->wpt;
+  DzArgs z{};
+  z.B = B; z.ldT = n->ldT; z.dout = n->dout; z.WpT = n->wpt; z.err = n->err;
   for (int l = 0; l < 3; ++l) {
-    b.Z[l] = n->Z + static_cast<size_t>(l) * n->max_batch * H;
-    b.A[l] = n->A + static_cast<size_t>(l) * n->max_batch * H;
+    z.Z[l] = n->Z + static_cast<size_t>(l) * n->max_batch * H;
+    z.dZT[l] = n->dZT + static_cast<size_t>(l) * H * n->ldT;
   }
-  b.dz[0] = n->dz;
-  b.dz[1] = n->dz + static_cast<size_t>(n->max_batch) * H;
-  mlp_backward_kernel<<<tiles, THREADS, SMEM_BYTES, n->stream>>>(b);
+  z.dZT[3] = n->dZT + static_cast<size_t>(3) * H * n->ldT;
+  mlp_backward_dz_kernel<<<tiles, THREADS, SMEM_BYTES, n->stream>>>(z);
+  MLP_TRY(n, cudaGetLastError());
+  DwArgs w{};
+  const int splits = std::max(1, std::min(DW_MAX_SPLITS, (B + 511) / 512));
+  w.B = B; w.ldT = n->ldT; w.part = n->part; w.err = n->err; w.XT = n->XT;
+  w.rows_per_split = ((B + splits - 1) / splits + DW_CHUNK - 1) / DW_CHUNK * DW_CHUNK;
+  for (int l = 0; l < 3; ++l) w.AT[l] = n->AT + static_cast<size_t>(l) * H * n->ldT;
+  for (int l = 0; l < 4; ++l) w.dZT[l] = z.dZT[l];
+  mlp_backward_dw_kernel<<<dim3(8, splits), DW_THREADS, DW_SMEM, n->stream>>>(w);
+  MLP_TRY(n, cudaGetLastError());
+  mlp_reduce_kernel<<<static_cast<int>((N_PARAMS + 255) / 256), 256, 0, n->stream>>>(n->part, splits, n->grad,
+                                                                                   static_cast<int>(N_PARAMS));
   MLP_TRY(n, cudaGetLastError());
   return TAMP_OK;
 }
@@ -635,11 +844,15 @@ tamp_status tamp_mlp_create(int device, void* stream, int max_batch, tamp_mlp** 
   if (e == cudaSuccess) e = cudaMalloc(&n->grad, N_PARAMS * 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->m, N_PARAMS * 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->v, N_PARAMS * 4);
+  n->ldT = static_cast<int>((mb + 63) / 64 * 64);
+  const size_t lt = static_cast<size_t>(n->ldT);
   if (e == cudaSuccess) e = cudaMalloc(&n->Z, 3 * mb * H * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&n->A, 3 * mb * H * 2);
-  if (e == cudaSuccess) e = cudaMalloc(&n->dz, 2 * mb * H * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&n->XT, IN * lt * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&n->AT, 3 * H * lt * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&n->dZT, (3 * H + OUT) * lt * 2);
   if (e == cudaSuccess) e = cudaMalloc(&n->out, mb * OUT * 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->dout, mb * OUT * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&n->part, static_cast<size_t>(DW_MAX_SPLITS) * N_PARAMS * 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->loss, 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->err, 4);
   if (e == cudaSuccess) e = cudaMemsetAsync(n->params, 0, N_PARAMS * 4, n->stream);
@@ -662,8 +875,8 @@ tamp_status tamp_mlp_destroy(tamp_mlp* n) {
   Dev g(n->device);
   cudaStreamSynchronize(n->stream);
   cudaFree(n->params); cudaFree(n->wp); cudaFree(n->wpt); cudaFree(n->grad); cudaFree(n->m); cudaFree(n->v);
-  cudaFree(n->Z); cudaFree(n->A); cudaFree(n->dz); cudaFree(n->out); cudaFree(n->dout);
-  cudaFree(n->loss); cudaFree(n->err);
+  cudaFree(n->Z); cudaFree(n->XT); cudaFree(n->AT); cudaFree(n->dZT); cudaFree(n->out); cudaFree(n->dout);
+  cudaFree(n->loss); cudaFree(n->err); cudaFree(n->part);
   delete n;
   return TAMP_OK;
 }
