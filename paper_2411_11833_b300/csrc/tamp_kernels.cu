@@ -77,6 +77,8 @@ int optimize_warps(int K);
 // The broad phase runs over chunks of QUEUE_CHUNK items per lane, so a warp's
 // candidate queue never holds more than QUEUE_CAP entries.
 constexpr int QUEUE_CHUNK = 16;
+// pieces a configuration's evaluation is split into (work items of a pass)
+constexpr int NPIECE = 2;
 constexpr int QUEUE_CAP = 32 * QUEUE_CHUNK;
 // shared memory of one warp's WarpScratch: queue, counters (padded), accumulators
 // accumulators, queue, counters (padded), then every lane's published batch:
@@ -441,8 +443,13 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   const float w_cf = tw(terms, cf[CF_T_CF]), w_jl = tw(terms, cf[CF_T_JL]), w_x = tw(terms, cf[CF_T_X]);
   const int cp_src = cf[CF_CP_SRC], cp_first = cf[CF_CP_FIRST], cp_count = cp_src >= 0 ? cf[CF_CP_COUNT] : 0;
   const float w_cp = cp_count > 0 ? tw(terms, cf[CF_CP_T]) : 0.f;
-  const bool head = piece == 0;
-  const int m = (nj + 1) / 2;  // the tail's top link
+  const bool head = piece == 0, last = piece == NPIECE - 1;
+  // links of each piece, so that sphere batches spread evenly: the head also
+  // has the held box (2 batches), the tail the placed box (1)
+  const int n_head = NPIECE == 2 ? nj / 2 : max(0, (nj + 3) / 3 - 2);       // links of the head
+  const int n_tail = NPIECE == 2 ? nj - n_head : max(0, (nj + 3) / 3 - 1);  // links of the tail
+  const int top = head ? nj : (last ? n_tail : nj - n_head);                  // this piece's top link
+  const int lo = head ? nj - n_head + 1 : (last ? 1 : n_tail + 1);            // ... and bottom link
   // terms computed redundantly count on lane 0 only; Kin belongs to the head
   const float k0 = (sub == 0 && head) ? 1.f : 0.f;
 #define XV(c) X[(c) * PT + pl]
@@ -452,7 +459,7 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
 #pragma unroll
   for (int i = 0; i < 9; ++i) R[i] = arm[i];
   t[0] = arm[9]; t[1] = arm[10]; t[2] = arm[11];
-  const int jtop = head ? nj : m;
+  const int jtop = top;
   for (int j = 0; j < jtop; ++j) {
     const float* Jp = arm + 24 + j * ARM_JW;
     float sj, cj;
@@ -544,14 +551,17 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   // placed box (phase 3), which overwrites (R, t) with P(p) once the links are done.
   // A held-box sphere l (object frame) is first moved into frame n:
   // l' = tool (G(g)^-1 l) = t_tool + R_tool R_G (l - g).
-  int phase = head ? 0 : 1, l = head ? nj : m;
-  int s0 = head ? 0 : sc[SH_LINK0 + m], s1 = head ? nbs_pad : sc[SH_LINK0 + m + 1];
+  // a piece without links of its own below the end effector (the tail of a
+  // very short arm) starts at the base spheres
+  int phase = head ? 0 : (top >= 1 ? 1 : 2), l = top;
+  int s0 = head ? 0 : sc[SH_LINK0 + top], s1 = head ? nbs_pad : sc[SH_LINK0 + top + 1];
+  if (!head && top < lo && !(last && top == 0)) s0 = s1 = 0;
   for (;;) {
     if (s0 >= s1) {
       if (phase == 0) {
         phase = 1;
         s0 = sc[SH_LINK0 + l]; s1 = sc[SH_LINK0 + l + 1];
-        if (l <= m) s0 = s1 = 0;  // an arm of at most one link: the tail has it
+        if (l < lo) s0 = s1 = 0;  // the head has no link of its own
       } else if (phase == 1) {
         // joint l: T_{l-1} = T_l Rx(-alpha) Tx(-a) Tz(-d) Rz(-theta); it turns the
         // links >= l about z_{l-1} through o_{l-1}: dJ/dq_l = z.M + (o x z).F
@@ -572,8 +582,8 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
         --l;
         if (l == 0) phase = 2;
         s0 = sc[SH_LINK0 + l]; s1 = sc[SH_LINK0 + l + 1];
-        if (head && l <= m) s0 = s1 = 0;  // the tail's links (and the base): torques only
-      } else if (phase == 2 && cp_count > 0 && !head) {
+        if (l < lo && !(last && l == 0)) s0 = s1 = 0;  // other pieces' links: torques only
+      } else if (phase == 2 && cp_count > 0 && last) {
         phase = 3;
         s0 = cp_first; s1 = cp_first + (cp_count + NB - 1) / NB * NB;
         float sp, cp;
@@ -702,6 +712,7 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   if (sub != 0) return;
   atomicAdd(&Tm[cf[CF_T_CF] * PT + pl], J_hold);
   if (!head) {
+    if (!last) return;
     if (cp_count > 0) {
       atomicAdd(&Tm[cf[CF_CP_T] * PT + pl], J_place);
 #pragma unroll
@@ -884,7 +895,7 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
   // configurations first (their environments hold more placed boxes), then the
   // goal cost; warps pull them from a counter so that they finish together
   __shared__ int s_next;
-  const int n_work = 2 * K + (s_pb[PH_GOAL_T] != 0xffffffffu ? 1 : 0);
+  const int n_work = NPIECE * K + (s_pb[PH_GOAL_T] != 0xffffffffu ? 1 : 0);
   double b1t = pow(static_cast<double>(d.beta1), t0), b2t = pow(static_cast<double>(d.beta2), t0);
   unsigned n_obb = 0, n_box = 0;  // broad-phase candidates resolved exactly (work accounting)
 
@@ -904,8 +915,8 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
       if (lane == 0) item = atomicAdd(&s_next, 1);
       item = __shfl_sync(0xffffffffu, item, 0);
       if (item >= n_work) break;
-      if (item < 2 * K)
-        eval_config<L>(s_sc, s_pb, K - 1 - (item >> 1), item & 1, sx, sg, st, slots, splace, ws, n_obb, n_box,
+      if (item < NPIECE * K)
+        eval_config<L>(s_sc, s_pb, K - 1 - item / NPIECE, item % NPIECE, sx, sg, st, slots, splace, ws, n_obb, n_box,
                        lane, pl, sub);
       else if (sub == 0)
         eval_goal<L>(s_sc, s_pb, sx, sg, st, pl);
