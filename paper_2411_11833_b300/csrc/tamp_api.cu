@@ -617,10 +617,11 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
 // the kernel's static shared variables
 constexpr size_t kMaxDynSmem = 227 * 1024 - 256;
 
-// Threads per (particle, configuration).  More lanes split each configuration's
-// environment (shorter critical path, more CTAs for small batches) but repeat
-// its kinematics; one lane keeps 32 particles per CTA.  Measured on the
-// 4096-particle packing problem: 1 lane 41M, 2 lanes 25M particle-iterations/s.
+// Threads per (particle, configuration) when neither the options nor a tuned
+// shape say otherwise.  More lanes split each configuration's environment
+// (shorter critical path, more CTAs for small batches) but repeat its
+// kinematics; one lane keeps 32 particles per CTA, which is fastest as soon as
+// the batch gives every SM a tile or more (tamp_autotune measures it).
 int preferred_lanes(int requested, long total_particles) {
   if (requested == 1 || requested == 2 || requested == 4 || requested == 8) return requested;
   return total_particles >= 148L * 16 ? 1 : (total_particles >= 148L * 8 ? 2 : 4);

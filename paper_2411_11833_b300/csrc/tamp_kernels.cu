@@ -4,10 +4,11 @@
 // optimisation: the particles' values, Adam moments and gradient live in
 // shared memory, every iteration (cost, hand-written adjoint, Adam, Eq. 3 flags)
 // runs inside the CTA, and HBM is touched only to load the tile and to write it
-// back.  Warp w evaluates arm configuration k = w, w + W, ... of the skeleton
-// for all PT particles; the L lanes of one (particle, configuration) pair split
-// the collision environment (obstacles and environment-box spheres) between
-// them and meet in a shuffle reduction.
+// back.  Each configuration of the skeleton is evaluated in independent pieces
+// (ranges of its links, with the held or placed box) that the warps pull from
+// a per-pass counter for all PT particles; the L lanes of one (particle,
+// configuration) pair split the collision environment (obstacles and
+// environment-box spheres) between them and meet in a shuffle reduction.
 //
 // Per configuration (arXiv 2411.11833, Sec. V-A/V-B and the appendix):
 //   forward kinematics of the serial arm (standard DH) into registers;
