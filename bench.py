@@ -29,6 +29,8 @@ P_PARTICLES = 4096
 N_ITERS = 500
 SCENE_SEED = 2001
 METRIC = "particle-iters/s (cost+grad+update)"
+PACKING_WORKLOAD = ("packing: 7-DOF arm (35 spheres), 6 boxes, 8 cuboids, 0.3x0.3 m region, "
+                    "6 pick-place pairs + goal, D=126, uniform init")
 L2_FLUSH_BYTES = 512 << 20
 
 # DRAM traffic of one optimize_kernel launch on this workload, from an ncu
@@ -166,8 +168,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": val, "unit": "particle-iters/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "packing: 6 boxes, 8 cuboids, D=126, uniform init", "particles": Ps,
-                   "iters_per_step": its_per_step},
+        "config": {"workload": PACKING_WORKLOAD, "particles": Ps, "iters_per_step": its_per_step},
         "cpu_baseline": {"value": val, "unit": "particle-iters/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "particle-iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -322,8 +323,7 @@ def main():
                     "12 pick-place pairs + goal, D=252, uniform init")
     else:
         sc, acts = sg.packing_problem(SCENE_SEED)
-        workload = ("packing: 7-DOF arm (35 spheres), 6 boxes, 8 cuboids, 0.3x0.3 m region, "
-                    "6 pick-place pairs + goal, D=126, uniform init")
+        workload = PACKING_WORKLOAD
     with torch.cuda.stream(stream):
         scene = pkg.Scene(sc, device=local, stream=stream.cuda_stream)
         pid = scene.set_skeleton(acts, pkg.default_options(lanes=args.lanes))
