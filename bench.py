@@ -219,10 +219,11 @@ def measure_ttfs(pkg, sg, seeds=range(3001, 3009), budget_iters=1000):
             be.sample = lambda pid, n, sd, s=sampler: scene.sample(pid, n, sd, s)
             torch.cuda.synchronize()
             t1 = time.perf_counter()
+            # both forms check for a satisfying particle every 10 iterations
             if batched:
-                r = search.batched_search(be, skels, sizes, steps_per_chunk=25, max_iterations=budget_iters, seed=seed)
+                r = search.batched_search(be, skels, sizes, steps_per_chunk=10, max_iterations=budget_iters, seed=seed)
             else:
-                r = search.sequential_search(be, skels, sizes, steps_per_chunk=25, chunks_per_visit=2,
+                r = search.sequential_search(be, skels, sizes, steps_per_chunk=10, chunks_per_visit=5,
                                              max_iterations=budget_iters, seed=seed)
             res[name].append({"seed": seed, "solved": bool(r["solved"]), "s": round(time.perf_counter() - t1, 4),
                               "first_iter": int(r["first_iter"])})
