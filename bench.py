@@ -334,8 +334,8 @@ def main():
     if not args.no_autotune and args.lanes == 0:
         with torch.cuda.stream(stream):
             scene.sample(pid, P, 999)
-            L, W, ms = scene.autotune(pid, trial_steps=10)
-        tuned = {"lanes": L, "warps": W, "trial_ms_10_iters": round(ms, 3)}
+            L, W, ms = scene.autotune(pid, trial_steps=50)
+        tuned = {"lanes": L, "warps": W, "trial_ms_50_iters": round(ms, 3)}
 
     def one_step(seed):
         scene.sample(pid, P, seed)

@@ -271,11 +271,11 @@ tamp_status tamp_work_counters(tamp_scene *scene, int problem_id, uint64_t out[2
  * current batches, times every launch shape that fits -- lanes L in {1, 2, 4,
  * 8} per (particle, configuration) (32 / L particles per CTA) and W <= 16 warps
  * per CTA (1..8 work items per warp; a configuration is two items) -- with
- * trial_steps fused iterations on
- * scratch copies of the batches (the problems' state is left untouched), and
- * keeps the fastest for later launches of exactly these problems at these batch
- * sizes whose options have lanes = 0.  Outputs (host, each may be NULL): the
- * chosen L, W and its trial time in ms.  Synchronises. */
+ * trial_steps fused iterations on scratch copies of the batches (the problems'
+ * state is left untouched), three times each in interleaved rounds, and keeps
+ * the shape with the best time for later launches of exactly these problems at
+ * these batch sizes whose options have lanes = 0.  Outputs (host, each may be
+ * NULL): the chosen L, W and its best trial time in ms.  Synchronises. */
 tamp_status tamp_autotune(tamp_scene *scene, const int *problem_ids, int n_problems, int trial_steps,
                           int *lanes, int *warps, float *ms);
 /* Install a known launch shape for the listed problems at their current batch

@@ -22,7 +22,7 @@ cudaError_t launch_optimize(const LaunchArgs& a, int L, int warps, int grid, siz
 cudaError_t optimize_set_smem(int L, size_t smem);
 cudaError_t launch_chunk_control(int* t_dev, const int* const* first_iters, int n_problems, int steps,
                                  int stop_on_first, int* stop, int* chunks_run, cudaStream_t st);
-size_t optimize_tile_bytes(int prob_words, int D, int NT, int NSLOT, int L, bool mv_global);
+size_t optimize_tile_bytes(int prob_words, int D, int NT, int NSLOT, int NANG, int L, bool mv_global);
 size_t optimize_scratch_bytes(int warps);
 int optimize_blocks_per_sm(int L, int warps, size_t smem);
 cudaError_t launch_sample(const uint32_t* pb, const uint32_t* sc, float* x, float* m, float* v, int stride, int P,
@@ -45,7 +45,9 @@ namespace {
 struct Problem {
   int id = -1;
   int D = 0, K = 0, NT = 0, NCON = 0, NSLOT = 0;
+  int NANG = 0;       // entries of the kernel's per-iteration (cos, sin) table per particle
   std::vector<uint32_t> blob;
+  int opt_words = 0;  // leading words of the blob that the optimisation kernel stages
   uint32_t* d_blob = nullptr;
   std::vector<int> term_kinds;
   tamp_options opt{};
@@ -317,6 +319,7 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
   int off = 0;
   struct Cfg {
     int kind, box, qo, go, tsrc, surf, ai;
+    int t_slot = -1, cp_slot = -1;  // placement slots of the Kin target and of the CFreePlace box
     std::vector<std::pair<int, PoseSrc>> env;
     int t_kp, t_kr, t_x, t_cf, t_cp, t_jl;
     float tx, ty, tz, tyaw, pz;
@@ -359,6 +362,7 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
         if (j != b) c.env.push_back({j, pose[j]});
       if (pose[b].kind == 1) {
         c.tsrc = pose[b].off;
+        c.t_slot = pose[b].slot;
         c.tz = static_cast<float>(s->surf[6 * pose[b].surf + 5] + s->box_half[3 * b + 2]);
       } else {
         c.tsrc = -1;
@@ -388,6 +392,7 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
       for (int j = 0; j < B; ++j)
         if (j != b) c.env.push_back({j, pose[j]});
       c.tsrc = po;
+      c.t_slot = static_cast<int>(slots.size());
       c.tz = static_cast<float>(s->surf[6 * sf + 5] + s->box_half[3 * b + 2]);
       c.pz = c.tz;
       c.t_kp = add_term(TK_KIN_POS); c.t_kr = add_term(TK_KIN_ROT); c.t_x = add_term(TK_STABLE);
@@ -422,9 +427,11 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
     if (c.kind != 1) continue;
     const int half = (i > 0 && cfgs[i - 1].kind == 0 && cfgs[i - 1].box == c.box) ? s->NBS / 2 : 0;
     c.cp_src = c.tsrc; c.cp_z = c.pz; c.cp_t = c.t_cp; c.cp_first = half; c.cp_count = s->NBS - half;
+    c.cp_slot = c.t_slot;
     if (half > 0) {
       Cfg& pk = cfgs[i - 1];
       pk.cp_src = c.tsrc; pk.cp_z = c.pz; pk.cp_t = c.t_cp; pk.cp_first = 0; pk.cp_count = half;
+      pk.cp_slot = c.t_slot;
     }
   }
   if (static_cast<int>(cfgs.size()) > MAX_CFG) return fail(s, TAMP_ERR_INVALID_ARG, "too many configurations");
@@ -525,6 +532,10 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
     rec[CF_CP_FIRST] = static_cast<uint32_t>(c.cp_first);
     rec[CF_CP_COUNT] = static_cast<uint32_t>(c.cp_count);
     rec[CF_CP_T] = static_cast<uint32_t>(c.cp_t);
+    rec[CF_T_SLOT] = static_cast<uint32_t>(c.t_slot);
+    rec[CF_CP_SLOT] = static_cast<uint32_t>(c.cp_slot);
+    rec[CF_TCOS] = fbits(static_cast<float>(std::cos(static_cast<double>(c.tyaw))));
+    rec[CF_TSIN] = fbits(static_cast<float>(std::sin(static_cast<double>(c.tyaw))));
     v.insert(v.end(), rec, rec + CFG_W);
     env_count += static_cast<int>(c.env.size());
   }
@@ -581,7 +592,19 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
     v.push_back(fbits(lr));
   }
   align4(v);
+  v[PH_OFF_SLOT] = static_cast<uint32_t>(v.size());
+  for (const Slot& sl : slots) {
+    v.push_back(static_cast<uint32_t>(sl.box));
+    v.push_back(static_cast<uint32_t>(sl.off));
+    v.push_back(fbits(sl.z));
+    v.push_back(0);
+  }
+  if (slots.empty())
+    for (int i = 0; i < SLOT_W; ++i) v.push_back(0);
+  align4(v);
+  // the sampler's records last: the optimisation kernel stages the words before them
   v[PH_OFF_SAMP] = static_cast<uint32_t>(v.size());
+  pr.opt_words = static_cast<int>(v.size());
   for (const Cfg& c : cfgs)
     for (int j = 0; j < nj; ++j) {
       // q ~ U[q_lo, q_hi]: bounds from the scene blob's joint records
@@ -595,16 +618,7 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
     v.push_back(static_cast<uint32_t>(sp.surf));
   }
   align4(v);
-  v[PH_OFF_SLOT] = static_cast<uint32_t>(v.size());
-  for (const Slot& sl : slots) {
-    v.push_back(static_cast<uint32_t>(sl.box));
-    v.push_back(static_cast<uint32_t>(sl.off));
-    v.push_back(fbits(sl.z));
-    v.push_back(0);
-  }
-  if (slots.empty())
-    for (int i = 0; i < SLOT_W; ++i) v.push_back(0);
-  align4(v);
+  pr.NANG = pr.K * (nj + 1);
   pr.NSLOT = static_cast<int>(slots.size());
   v[PH_NSLOT] = static_cast<uint32_t>(pr.NSLOT);
   v[PH_D] = pr.D; v[PH_K] = pr.K; v[PH_NT] = pr.NT; v[PH_NCON] = pr.NCON;
@@ -713,8 +727,8 @@ tamp_status plan_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lanes
     for (int g = 0; g < 2; ++g) {
       size_t tile = 0;
       for (const Job& j : jobs)
-        tile = std::max(tile, optimize_tile_bytes(static_cast<int>(j.pr->blob.size()), j.pr->D, j.pr->NT,
-                                                  j.pr->NSLOT, L, g == 1));
+        tile = std::max(tile, optimize_tile_bytes(j.pr->opt_words, j.pr->D, j.pr->NT, j.pr->NSLOT, j.pr->NANG, L,
+                                                  g == 1));
       smem = 4 * ((s->blob.size() + 3) & ~static_cast<size_t>(3)) + tile + optimize_scratch_bytes(warps);
       mvg = g == 1;
       if (smem <= kMaxDynSmem) break;
@@ -792,7 +806,7 @@ tamp_status launch_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lan
 ProbDesc state_desc(Problem& pr, int n_steps) {
   ProbDesc d{};
   d.prob = pr.d_blob;
-  d.prob_words = static_cast<int>(pr.blob.size());
+  d.prob_words = pr.opt_words;
   d.x_in = pr.d_x; d.x_out = pr.d_x; d.m = pr.d_m; d.v = pr.d_v; d.load_mv = 1;
   d.stride = pr.P; d.P = pr.P;
   d.out_cost = pr.d_cost; d.out_flags = pr.d_flags; d.out_counts = pr.d_counts;
@@ -1135,7 +1149,7 @@ tamp_status tamp_eval(tamp_scene* s, int id, int n, const float* x, float* cost,
   DeviceGuard g(s->device);
   ProbDesc d{};
   d.prob = pr->d_blob;
-  d.prob_words = static_cast<int>(pr->blob.size());
+  d.prob_words = pr->opt_words;
   d.x_in = x; d.stride = n; d.P = n;
   d.out_cost = cost; d.out_terms = terms; d.out_flags = flags; d.out_grad = grad;
   d.n_steps = 0;
@@ -1216,16 +1230,24 @@ tamp_status tamp_autotune(tamp_scene* s, const int* ids, int n, int trial_steps,
     const int w = std::min(max_w, (2 * kmax + per - 1) / per);
     if (std::find(wc.begin(), wc.end(), w) == wc.end()) wc.push_back(w);
   }
-  float best = -1.f;
-  int bL = 0, bW = 0;
+  // the shapes that fit, each timed in kTuneRounds interleaved rounds (its best
+  // time counts), so that clock drift during the tuning treats them alike
+  constexpr int kTuneRounds = 3;
   const std::string saved = s->err;
-  for (int L = 1; L <= 8; L *= 2) {
+  std::vector<std::pair<int, int>> shapes;
+  for (int L = 1; L <= 8; L *= 2)
     for (int W : wc) {
       Plan probe;
-      if (plan_jobs(s, jobs, 0, &probe, L, W) != TAMP_OK) continue;  // does not fit: not a candidate
+      if (plan_jobs(s, jobs, 0, &probe, L, W) == TAMP_OK) shapes.push_back({L, W});  // else: does not fit
+    }
+  std::vector<float> best_ms(shapes.size(), -1.f);
+  for (int round = 0; round < kTuneRounds; ++round)
+    for (size_t c = 0; c < shapes.size(); ++c) {
+      const int L = shapes[c].first, W = shapes[c].second;
       e = restore();
-      if (e == cudaSuccess && launch_jobs(s, jobs, 0, L, W) != TAMP_OK) e = cudaErrorLaunchFailure;  // warm-up
-      if (e == cudaSuccess) e = restore();
+      if (round == 0 && e == cudaSuccess && launch_jobs(s, jobs, 0, L, W) != TAMP_OK)  // warm-up
+        e = cudaErrorLaunchFailure;
+      if (round == 0 && e == cudaSuccess) e = restore();
       if (e == cudaSuccess) e = cudaEventRecord(e0, s->stream);
       if (e == cudaSuccess && launch_jobs(s, jobs, 0, L, W) != TAMP_OK) e = cudaErrorLaunchFailure;
       if (e == cudaSuccess) e = cudaEventRecord(e1, s->stream);
@@ -1236,11 +1258,14 @@ tamp_status tamp_autotune(tamp_scene* s, const int* ids, int n, int trial_steps,
         release();
         return fail(s, TAMP_ERR_CUDA, "autotune trial L=%d W=%d: %s", L, W, cudaGetErrorString(e));
       }
-      if (best < 0.f || ms < best) {
-        best = ms; bL = L; bW = W;
-      }
+      if (best_ms[c] < 0.f || ms < best_ms[c]) best_ms[c] = ms;
     }
-  }
+  float best = -1.f;
+  int bL = 0, bW = 0;
+  for (size_t c = 0; c < shapes.size(); ++c)
+    if (best < 0.f || best_ms[c] < best) {
+      best = best_ms[c]; bL = shapes[c].first; bW = shapes[c].second;
+    }
   s->err = saved;
   release();
   if (best < 0.f) return fail(s, TAMP_ERR_INVALID_ARG, "no launch shape fits these problems");
@@ -1510,7 +1535,7 @@ extern "C" tamp_status tamp_eval_static_scratch(tamp_scene* s, int id, int n, co
   size_t smem = 0;
   for (; L <= 8; L *= 2) {
     smem = 4 * ((s->blob.size() + 3) & ~static_cast<size_t>(3)) +
-           optimize_tile_bytes(static_cast<int>(pr->blob.size()), pr->D, pr->NT, pr->NSLOT, L, false) +
+           optimize_tile_bytes(pr->opt_words, pr->D, pr->NT, pr->NSLOT, pr->NANG, L, false) +
            optimize_scratch_bytes(warps);
     if (smem <= kMaxDynSmem) break;
   }
@@ -1523,7 +1548,7 @@ extern "C" tamp_status tamp_eval_static_scratch(tamp_scene* s, int id, int n, co
                 kStaticTiles, kStaticTiles * PT, L);
   ProbDesc d{};
   d.prob = pr->d_blob;
-  d.prob_words = static_cast<int>(pr->blob.size());
+  d.prob_words = pr->opt_words;
   d.x_in = x; d.stride = n; d.P = n;
   d.out_cost = cost; d.out_terms = terms; d.out_flags = flags; d.out_grad = grad;
   d.n_steps = 0;

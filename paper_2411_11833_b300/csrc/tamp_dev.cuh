@@ -47,7 +47,7 @@ enum ProbHdr {
   PH_D = 0, PH_K, PH_NT, PH_NCON, PH_GOAL_T, PH_NGOAL, PH_OFF_CFG, PH_OFF_ENV, PH_OFF_TERMS,
   PH_OFF_GOAL, PH_OFF_LR, PH_OFF_SAMP, PH_WORDS, PH_NSLOT, PH_OFF_SLOT, PH_HDR_WORDS = 16
 };
-constexpr int CFG_W = 24;
+constexpr int CFG_W = 28;
 enum CfgField {
   CF_KIND = 0, CF_BOX, CF_QOFF, CF_GOFF, CF_TSRC, CF_SURF, CF_NENV, CF_ENVOFF,
   CF_T_KP, CF_T_KR, CF_T_X, CF_T_CF, CF_T_CP, CF_T_JL, CF_PSRC,
@@ -55,8 +55,17 @@ enum CfgField {
   CF_TX, CF_TY, CF_TZ, CF_TYAW,  // floats: target pose if CF_TSRC < 0, else CF_TZ = surface z + h_z
   CF_PZ,                        // float: z of that placed box
   CF_CP_FIRST, CF_CP_COUNT,     // its spheres [first, first + count)
-  CF_CP_T                       // CFreePlace term index
+  CF_CP_T,                      // CFreePlace term index
+  CF_T_SLOT,                    // placement slot of the Kin target if CF_TSRC >= 0, else -1
+  CF_CP_SLOT,                   // placement slot of CF_CP_SRC (-1: none)
+  CF_TCOS, CF_TSIN              // floats: cos, sin of CF_TYAW
 };
+// Per iteration the optimisation kernel tabulates, for every particle of its
+// tile, (cos, sin) of each configuration's joint angles (plus the joint
+// offsets) followed by its grasp yaw: K x (n_joints + 1) entries, so that the
+// kinematics, the reverse sweep and Kin read them instead of evaluating them.
+// The problem blob ends with the sampler's per-component records; the
+// optimisation kernel stages only the words before them (PH_OFF_SAMP).
 // A Place's CFreePlace spheres are split between the Place and the Pick right
 // before it (same box, same environment), which evens the work of their warps.
 constexpr int ENV_W = 4;        // box, src (-1 = initial pose, else placement offset), slot, pad

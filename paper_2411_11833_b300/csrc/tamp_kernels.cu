@@ -81,10 +81,15 @@ constexpr int QUEUE_CHUNK = 16;
 // pieces a configuration's evaluation is split into (work items of a pass)
 constexpr int NPIECE = 2;
 constexpr int QUEUE_CAP = 32 * QUEUE_CHUNK;
-// shared memory of one warp's WarpScratch: queue, counters (padded), accumulators
-// accumulators, queue, counters (padded), then every lane's published batch:
-// its NB spheres and their bounding sphere
-constexpr int WARP_SCRATCH_BYTES = 32 * NB * 16 + QUEUE_CAP * 4 + 16 + 32 * (NB + 1) * 16;
+// A queue entry is 16 bits: owner lane << QUEUE_ITEM_BITS | item (items are
+// the scene's cuboids, then the other boxes: fewer than MAX_OBS + MAX_BOX).
+constexpr int QUEUE_ITEM_BITS = 11;
+static_assert(MAX_OBS + MAX_BOX <= (1 << QUEUE_ITEM_BITS), "queue entry item field");
+// shared memory of one warp's WarpScratch: accumulators, queue, counters
+// (padded), then every lane's published batch: its NB spheres and their
+// bounding sphere
+constexpr int WARP_SCRATCH_BYTES = 32 * NB * 16 + QUEUE_CAP * 2 + 16 + 32 * (NB + 1) * 16;
+static_assert(WARP_SCRATCH_BYTES % 16 == 0, "warp scratch alignment");
 
 // ------------------------------------------------------------------ frame helpers
 // A frame is R (row-major 3x3) and t.  Right-multiplications used by DH:
@@ -177,7 +182,7 @@ __device__ __forceinline__ float obb_pen(const Obb& b, float x, float y, float z
 // (cuboid entries from the front, box entries from the back) and per-owner
 // accumulators (gradient and penetration of each of its NB spheres).
 struct WarpScratch {
-  uint32_t* queue;   // QUEUE_CAP entries: owner lane << 16 | item
+  uint16_t* queue;   // QUEUE_CAP entries: owner lane << QUEUE_ITEM_BITS | item
   int* count;        // [2]: cuboid entries, box entries
   float4* acc;       // [32][NB]: (dpen/dc x, y, z; pen)
   float4* sph;       // [32][NB + 1]: each lane's batch (x, y, z, r) and its bounding sphere
@@ -220,7 +225,7 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
       if (i < O) {
         if (obb_gap(load_obb(obs, i, O), cbx, cby, cbz) < Rb) {
           const int q = atomicAdd(&ws.count[0], 1);
-          ws.queue[q] = static_cast<uint32_t>(lane) << 16 | static_cast<uint32_t>(i);
+          ws.queue[q] = static_cast<uint16_t>(lane << QUEUE_ITEM_BITS | i);
         }
       } else {
         // the batch bound against the other box's bounding sphere and against the
@@ -242,7 +247,7 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
         const float qz = fmaxf(fabsf(dz) - br[12], 0.f);
         if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R * R && fmaf(qx, qx, fmaf(qy, qy, qz * qz)) < Rb * Rb) {
           const int q = atomicAdd(&ws.count[1], 1);
-          ws.queue[QUEUE_CAP - 1 - q] = static_cast<uint32_t>(lane) << 16 | static_cast<uint32_t>(i);
+          ws.queue[QUEUE_CAP - 1 - q] = static_cast<uint16_t>(lane << QUEUE_ITEM_BITS | i);
         }
       }
     }
@@ -265,12 +270,12 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
       const int t = t0 + lane;
       if (t < Tc) {
         const int ci = t / NB, s = t - ci * NB;
-        const uint32_t ent = ws.queue[ci];
-        const int owner = static_cast<int>(ent >> 16);
+        const int ent = ws.queue[ci];
+        const int owner = ent >> QUEUE_ITEM_BITS;
         if (s == 0) ++n_obb;
         const float4 sp = ws.sph[owner * (NB + 1) + s];
         if (sp.w > 0.f) {
-          const Obb b = load_obb(obs, static_cast<int>(ent & 0xffffu), O);
+          const Obb b = load_obb(obs, ent & ((1 << QUEUE_ITEM_BITS) - 1), O);
           float px_, py_, pz_;
           const float pen = obb_pen(b, sp.x, sp.y, sp.z, sp.w, px_, py_, pz_);
           if (pen > 0.f) {
@@ -294,12 +299,12 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
       const int t = t0 + lane;
       if (t < Tb) {
         const int bi = t / NB, s = t - bi * NB;
-        const uint32_t ent = ws.queue[QUEUE_CAP - 1 - bi];
-        const int owner = static_cast<int>(ent >> 16);
+        const int ent = ws.queue[QUEUE_CAP - 1 - bi];
+        const int owner = ent >> QUEUE_ITEM_BITS;
         if (s == 0) ++n_box;
         const float4 sp = ws.sph[owner * (NB + 1) + s];
         const int opl = owner / L;  // the owner's particle in the tile
-        const int* er = env + (static_cast<int>(ent & 0xffffu) - O) * ENV_W;
+        const int* er = env + ((ent & ((1 << QUEUE_ITEM_BITS) - 1)) - O) * ENV_W;
         const int j = er[0], src = er[1];
         const float* br = boxr + j * BOX_W;
         float bx, by, bz, cy_, sy_;
@@ -418,8 +423,8 @@ __device__ __forceinline__ float bound_dist(const float (&v)[N], const float (&l
 template <int L>
 __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __restrict__ pb, int k, int piece,
                             const float* __restrict__ X, float* G, float* Tm, const int* __restrict__ slots,
-                            const float4* __restrict__ place, const WarpScratch& ws, unsigned& n_obb,
-                            unsigned& n_box, int lane, int pl, int sub) {
+                            const float4* __restrict__ place, const float2* __restrict__ trig,
+                            const WarpScratch& ws, unsigned& n_obb, unsigned& n_box, int lane, int pl, int sub) {
   constexpr int PT = 32 / L;
   const int nj = sc[SH_NJ];
   const float* arm = reinterpret_cast<const float*>(sc + sc[SH_OFF_ARM]);
@@ -454,6 +459,9 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   // terms computed redundantly count on lane 0 only; Kin belongs to the head
   const float k0 = (sub == 0 && head) ? 1.f : 0.f;
 #define XV(c) X[(c) * PT + pl]
+  // (cos, sin) of this configuration's joint angles, then of its grasp yaw
+  const float2* tg = trig + k * (nj + 1) * PT + pl;
+#define TG(j) tg[(j) * PT]
 
   // ---------------- forward kinematics T_0 .. T_n (the tail stops at T_m)
   float R[9], t[3];
@@ -463,9 +471,8 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   const int jtop = top;
   for (int j = 0; j < jtop; ++j) {
     const float* Jp = arm + 24 + j * ARM_JW;
-    float sj, cj;
-    sincosf(XV(qo + j) + Jp[4], &sj, &cj);
-    rz_right(R, cj, sj);
+    const float2 cs = TG(j);
+    rz_right(R, cs.x, cs.y);
     const float a = Jp[0], d = Jp[1];
     t[0] = fmaf(d, R[2], fmaf(a, R[0], t[0]));
     t[1] = fmaf(d, R[5], fmaf(a, R[3], t[1]));
@@ -483,22 +490,27 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
     te[i] = fmaf(R[3 * i], tl[9], fmaf(R[3 * i + 1], tl[10], fmaf(R[3 * i + 2], tl[11], t[i])));
   }
 
-  // ---------------- Kin: target P(p) G(g)
-  float px, py, pz, pyaw;
-  if (tsrc < 0) {
-    px = cff[CF_TX]; py = cff[CF_TY]; pz = cff[CF_TZ]; pyaw = cff[CF_TYAW];
-  } else {
-    px = XV(tsrc); py = XV(tsrc + 1); pz = cff[CF_TZ]; pyaw = XV(tsrc + 2);
-  }
-  const float gxv = XV(go), gyv = XV(go + 1), gzv = XV(go + 2), gyaw = XV(go + 3);
-  float sy, cy;
-  sincosf(pyaw, &sy, &cy);
-  const float rgx = fmaf(cy, gxv, -sy * gyv), rgy = fmaf(sy, gxv, cy * gyv);
-  float s2, c2;
-  sincosf(pyaw + gyaw, &s2, &c2);
+  // ---------------- Kin: target P(p) G(g) (head only)
+  float px = 0.f, py = 0.f, cy = 1.f, sy = 0.f;  // target placement: position, yaw
+  float gxv = 0.f, gyv = 0.f, gzv = 0.f;          // grasp position
+  float sgr = 0.f, cgr = 1.f;  // grasp yaw: R_G = Rz(yaw) Rx(pi) = [[c, s, 0], [s, -c, 0], [0, 0, -1]] (symmetric)
   float F[3] = {0.f, 0.f, 0.f}, Mw[3] = {0.f, 0.f, 0.f}, gg[4] = {0.f, 0.f, 0.f, 0.f}, gp[3] = {0.f, 0.f, 0.f};
   float e_pos = 0.f, e_rot = 0.f;
+  float rgx = 0.f, rgy = 0.f;
   if (head) {
+    const float pz = cff[CF_TZ];
+    if (tsrc < 0) {
+      px = cff[CF_TX]; py = cff[CF_TY]; cy = cff[CF_TCOS]; sy = cff[CF_TSIN];
+    } else {
+      const float4 pp = place[cf[CF_T_SLOT] * PT + pl];
+      px = pp.x; py = pp.y; cy = pp.z; sy = pp.w;
+    }
+    gxv = XV(go); gyv = XV(go + 1); gzv = XV(go + 2);
+    const float2 gcs = TG(nj);
+    cgr = gcs.x; sgr = gcs.y;
+    rgx = fmaf(cy, gxv, -sy * gyv); rgy = fmaf(sy, gxv, cy * gyv);
+    // yaw of the target frame: placement yaw + grasp yaw
+    const float c2 = fmaf(cy, cgr, -sy * sgr), s2 = fmaf(sy, cgr, cy * sgr);
     const float ttx = px + rgx, tty = py + rgy, ttz = pz + gzv;
     // M = Re^T R_tgt, R_tgt = [[c2, s2, 0], [s2, -c2, 0], [0, 0, -1]]
     float Mr[9];
@@ -544,8 +556,6 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   float J_hold = 0.f, J_place = 0.f;
   float gpc[3] = {0.f, 0.f, 0.f};  // Kin target / containment -> this configuration's placement
   float gcp[3] = {0.f, 0.f, 0.f};  // CFreePlace part -> placement cp_src
-  float sgr, cgr;  // grasp yaw: R_G = Rz(yaw) Rx(pi) = [[c, s, 0], [s, -c, 0], [0, 0, -1]] (symmetric)
-  sincosf(gyaw, &sgr, &cgr);
 
   // ---------------- batches: held box, links n..1, base, placed box
   // Every batch is c = R l' + t with (R, t) the current link frame, except the
@@ -577,9 +587,8 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
         const float tq =
             fmaf(zx, Mw[0], fmaf(zy, Mw[1], fmaf(zz, Mw[2], fmaf(ox, F[0], fmaf(oy, F[1], oz * F[2])))));
         atomicAdd(&G[(qo + l - 1) * PT + pl], tq);
-        float sl, cl;
-        sincosf(XV(qo + l - 1) + Jp[4], &sl, &cl);
-        rz_right(R, cl, -sl);
+        const float2 cs = TG(l - 1);
+        rz_right(R, cs.x, -cs.y);
         --l;
         if (l == 0) phase = 2;
         s0 = sc[SH_LINK0 + l]; s1 = sc[SH_LINK0 + l + 1];
@@ -587,12 +596,11 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
       } else if (phase == 2 && cp_count > 0 && last) {
         phase = 3;
         s0 = cp_first; s1 = cp_first + (cp_count + NB - 1) / NB * NB;
-        float sp, cp;
-        sincosf(XV(cp_src + 2), &sp, &cp);
-        R[0] = cp; R[1] = -sp; R[2] = 0.f;
-        R[3] = sp; R[4] = cp; R[5] = 0.f;
+        const float4 pp = place[cf[CF_CP_SLOT] * PT + pl];  // (x, y, cos yaw, sin yaw)
+        R[0] = pp.z; R[1] = -pp.w; R[2] = 0.f;
+        R[3] = pp.w; R[4] = pp.z; R[5] = 0.f;
         R[6] = 0.f; R[7] = 0.f; R[8] = 1.f;
-        t[0] = XV(cp_src); t[1] = XV(cp_src + 1); t[2] = cff[CF_PZ];
+        t[0] = pp.x; t[1] = pp.y; t[2] = cff[CF_PZ];
       } else {
         break;
       }
@@ -797,6 +805,7 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
     for (int i = 0; i < 3; ++i) atomicAdd(&G[(psrc + i) * PT + pl], gpc[i]);
   }
 #undef XV
+#undef TG
 }
 
 // Goal MinimizeObjDist: sum over pairs of moved boxes of ||pos_i - pos_j||.
@@ -862,6 +871,11 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
   // cos yaw, sin yaw), refreshed at the start of each iteration
   float4* splace = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(sflag) + ((PT * 4 + 15) & ~15));
   const int NSLOT = s_pb[PH_NSLOT];
+  // (cos, sin) of every configuration's joint angles and grasp yaw at the current iterate
+  float2* strig = reinterpret_cast<float2*>(splace + NSLOT * PT);
+  const int nj = s_sc[SH_NJ], NA = K * (nj + 1);
+  const float* arm = reinterpret_cast<const float*>(s_sc + s_sc[SH_OFF_ARM]);
+  const uint32_t* cfg0 = s_pb + s_pb[PH_OFF_CFG];
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int w = tid >> 5, lane = tid & 31;
   const int pl = lane / L, sub = lane % L;
@@ -910,6 +924,16 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
       sincosf(sx[(off + 2) * PT + p], &sn, &cs);
       splace[i] = make_float4(sx[off * PT + p], sx[(off + 1) * PT + p], cs, sn);
     }
+    for (int i = tid; i < NA * PT; i += nthr) {
+      const int a = i / PT, p = i - a * PT;
+      const int k = a / (nj + 1), j = a - k * (nj + 1);
+      const int* cf = reinterpret_cast<const int*>(cfg0 + k * CFG_W);
+      const float ang = j < nj ? sx[(cf[CF_QOFF] + j) * PT + p] + arm[24 + j * ARM_JW + 4]
+                               : sx[(cf[CF_GOFF] + 3) * PT + p];
+      float sn, cs;
+      sincosf(ang, &sn, &cs);
+      strig[i] = make_float2(cs, sn);
+    }
     __syncthreads();
     for (;;) {
       int item = 0;
@@ -917,8 +941,8 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
       item = __shfl_sync(0xffffffffu, item, 0);
       if (item >= n_work) break;
       if (item < NPIECE * K)
-        eval_config<L>(s_sc, s_pb, K - 1 - item / NPIECE, item % NPIECE, sx, sg, st, slots, splace, ws, n_obb, n_box,
-                       lane, pl, sub);
+        eval_config<L>(s_sc, s_pb, K - 1 - item / NPIECE, item % NPIECE, sx, sg, st, slots, splace, strig, ws, n_obb,
+                       n_box, lane, pl, sub);
       else if (sub == 0)
         eval_goal<L>(s_sc, s_pb, sx, sg, st, pl);
     }
@@ -1061,9 +1085,9 @@ __global__ void __launch_bounds__(512, 1) optimize_kernel(LaunchArgs a) {
   {
     unsigned char* base = smem_raw + a.scratch_offset + static_cast<size_t>(w) * WARP_SCRATCH_BYTES;
     ws.acc = reinterpret_cast<float4*>(base);
-    ws.queue = reinterpret_cast<uint32_t*>(base + 32 * NB * 16);
-    ws.count = reinterpret_cast<int*>(base + 32 * NB * 16 + QUEUE_CAP * 4);
-    ws.sph = reinterpret_cast<float4*>(base + 32 * NB * 16 + QUEUE_CAP * 4 + 16);
+    ws.queue = reinterpret_cast<uint16_t*>(base + 32 * NB * 16);
+    ws.count = reinterpret_cast<int*>(base + 32 * NB * 16 + QUEUE_CAP * 2);
+    ws.sph = reinterpret_cast<float4*>(base + 32 * NB * 16 + QUEUE_CAP * 2 + 16);
     for (int i = lane; i < 32 * NB; i += 32) ws.acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (lane == 0) { ws.count[0] = 0; ws.count[1] = 0; }
   }
@@ -1506,12 +1530,12 @@ cudaError_t launch_sample_proposal(const uint32_t* rows, int R, const float* out
 
 // Dynamic shared memory: scene tables, the largest problem's tables and tile
 // (x, m, v, gradient, terms, flags), then the warps' exact-phase scratch.
-size_t optimize_tile_bytes(int prob_words, int D, int NT, int NSLOT, int L, bool mv_global) {
+size_t optimize_tile_bytes(int prob_words, int D, int NT, int NSLOT, int NANG, int L, bool mv_global) {
   const int PT = 32 / L;
   const size_t pw = (prob_words + 3) & ~3;
   const size_t arrays = mv_global ? 2 : 4;  // x, g (and m, v unless they stay in global memory)
   return 4 * pw + 4 * (arrays * static_cast<size_t>(D) * PT + static_cast<size_t>(NT) * PT) +
-         ((PT * 4 + 15) & ~15) + 16 * static_cast<size_t>(NSLOT) * PT;
+         ((PT * 4 + 15) & ~15) + 16 * static_cast<size_t>(NSLOT) * PT + 8 * static_cast<size_t>(NANG) * PT;
 }
 size_t optimize_scratch_bytes(int warps) { return static_cast<size_t>(WARP_SCRATCH_BYTES) * warps; }
 

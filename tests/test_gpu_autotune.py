@@ -109,7 +109,7 @@ def test_every_launch_shape_takes_the_oracle_adam_step(pkg, lanes, warps):
 
 def test_adam_moments_in_global_memory_take_the_oracle_step(pkg):
     """A tile too large for shared memory at one lane with its Adam moments
-    (the stress skeleton, D = 252, 12 warps) runs with the moments used in
+    (the stress skeleton, D = 252, 8 warps) runs with the moments used in
     place in global memory; one fused iteration from non-zero moments still
     equals the oracle's step, and the moments it leaves are the oracle's."""
     from oracle.problem import Problem
@@ -121,7 +121,7 @@ def test_adam_moments_in_global_memory_take_the_oracle_step(pkg):
     scene = pkg.Scene(sc)
     pid = scene.set_skeleton(acts)
     scene.set_particles(pid, X.T.astype(np.float32), m0.T.astype(np.float32), v0.T.astype(np.float32), 5)
-    scene.set_tuning(pid, 1, 12)
+    scene.set_tuning(pid, 1, 8)
     scene.optimize(pid, 1)
     x1, m1, v1, t1 = scene.get_particles(pid)
     scene.close()
