@@ -123,3 +123,8 @@ struct LaunchArgs {
 constexpr int ITEM_TILE_BITS = 20;
 
 }  // namespace tamp
+
+namespace tamp {
+// the kernels read box records, environment entries and joint records as float4 / int4
+static_assert(BOX_W % 4 == 0 && ENV_W == 4 && ARM_JW % 4 == 0, "16-byte records");
+}  // namespace tamp

@@ -231,20 +231,22 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
         // the batch bound against the other box's bounding sphere and against the
         // oriented box holding its spheres (centre, yaw, sphere hull); a contact
         // needs both: |d| < Rb + r_box and ||max(|u| - hull, 0)|| < Rb
-        const int* er = env + (i - O) * ENV_W;
-        const int src = er[1];
-        const float* br = boxr + er[0] * BOX_W;
+        const int4 er = *reinterpret_cast<const int4*>(env + (i - O) * ENV_W);  // box, src, slot
+        const float4* br = reinterpret_cast<const float4*>(boxr + er.x * BOX_W);
+        const float4 b0 = br[0], b2 = br[2];  // (half extents, bound radius), (cos, sin, hull x, y)
+        const float hull_z = br[3].x;
         float x, y, z, cy_, sy_;
-        if (src < 0) {
-          x = br[4]; y = br[5]; z = br[6]; cy_ = br[8]; sy_ = br[9];
+        if (er.y < 0) {
+          const float4 b1 = br[1];
+          x = b1.x; y = b1.y; z = b1.z; cy_ = b2.x; sy_ = b2.y;
         } else {
-          const float4 pp = place[er[2] * PT + pl];
-          x = pp.x; y = pp.y; z = __int_as_float(slots[er[2] * SLOT_W + 2]); cy_ = pp.z; sy_ = pp.w;
+          const float4 pp = place[er.z * PT + pl];
+          x = pp.x; y = pp.y; z = __int_as_float(slots[er.z * SLOT_W + 2]); cy_ = pp.z; sy_ = pp.w;
         }
-        const float dx = cbx - x, dy = cby - y, dz = cbz - z, R = Rb + br[3];
+        const float dx = cbx - x, dy = cby - y, dz = cbz - z, R = Rb + b0.w;
         const float ux = fmaf(cy_, dx, sy_ * dy), uy = fmaf(-sy_, dx, cy_ * dy);
-        const float qx = fmaxf(fabsf(ux) - br[10], 0.f), qy = fmaxf(fabsf(uy) - br[11], 0.f);
-        const float qz = fmaxf(fabsf(dz) - br[12], 0.f);
+        const float qx = fmaxf(fabsf(ux) - b2.z, 0.f), qy = fmaxf(fabsf(uy) - b2.w, 0.f);
+        const float qz = fmaxf(fabsf(dz) - hull_z, 0.f);
         if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R * R && fmaf(qx, qx, fmaf(qy, qy, qz * qz)) < Rb * Rb) {
           const int q = atomicAdd(&ws.count[1], 1);
           ws.queue[QUEUE_CAP - 1 - q] = static_cast<uint16_t>(lane << QUEUE_ITEM_BITS | i);
@@ -304,20 +306,23 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
         if (s == 0) ++n_box;
         const float4 sp = ws.sph[owner * (NB + 1) + s];
         const int opl = owner / L;  // the owner's particle in the tile
-        const int* er = env + ((ent & ((1 << QUEUE_ITEM_BITS) - 1)) - O) * ENV_W;
-        const int j = er[0], src = er[1];
-        const float* br = boxr + j * BOX_W;
+        const int4 er = *reinterpret_cast<const int4*>(env + ((ent & ((1 << QUEUE_ITEM_BITS) - 1)) - O) * ENV_W);
+        const int j = er.x, src = er.y;
+        const float4* br = reinterpret_cast<const float4*>(boxr + j * BOX_W);
+        const float4 b2 = br[2];  // cos, sin, hull x, y
+        const float hull_z = br[3].x;
         float bx, by, bz, cy_, sy_;
         if (src < 0) {
-          bx = br[4]; by = br[5]; bz = br[6]; cy_ = br[8]; sy_ = br[9];
+          const float4 b1 = br[1];
+          bx = b1.x; by = b1.y; bz = b1.z; cy_ = b2.x; sy_ = b2.y;
         } else {
-          const float4 pp = place[er[2] * PT + opl];
-          bx = pp.x; by = pp.y; bz = __int_as_float(slots[er[2] * SLOT_W + 2]); cy_ = pp.z; sy_ = pp.w;
+          const float4 pp = place[er.z * PT + opl];
+          bx = pp.x; by = pp.y; bz = __int_as_float(slots[er.z * SLOT_W + 2]); cy_ = pp.z; sy_ = pp.w;
         }
         const float dx0 = sp.x - bx, dy0 = sp.y - by, dz0 = sp.z - bz;
         const float ux = fmaf(cy_, dx0, sy_ * dy0), uy = fmaf(-sy_, dx0, cy_ * dy0);
-        const float qx = fmaxf(fabsf(ux) - br[10], 0.f), qy = fmaxf(fabsf(uy) - br[11], 0.f);
-        const float qz = fmaxf(fabsf(dz0) - br[12], 0.f);
+        const float qx = fmaxf(fabsf(ux) - b2.z, 0.f), qy = fmaxf(fabsf(uy) - b2.w, 0.f);
+        const float qz = fmaxf(fabsf(dz0) - hull_z, 0.f);
         if (sp.w > 0.f && fmaf(qx, qx, fmaf(qy, qy, qz * qz)) < sp.w * sp.w) {
           float ax = 0.f, ay = 0.f, az = 0.f, pen = 0.f;
           float fx = 0.f, fy = 0.f, tq = 0.f;  // push on a moving box: force, torque about its centre
@@ -470,14 +475,13 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   t[0] = arm[9]; t[1] = arm[10]; t[2] = arm[11];
   const int jtop = top;
   for (int j = 0; j < jtop; ++j) {
-    const float* Jp = arm + 24 + j * ARM_JW;
+    const float4 Jp = *reinterpret_cast<const float4*>(arm + 24 + j * ARM_JW);  // a, d, cos alpha, sin alpha
     const float2 cs = TG(j);
     rz_right(R, cs.x, cs.y);
-    const float a = Jp[0], d = Jp[1];
-    t[0] = fmaf(d, R[2], fmaf(a, R[0], t[0]));
-    t[1] = fmaf(d, R[5], fmaf(a, R[3], t[1]));
-    t[2] = fmaf(d, R[8], fmaf(a, R[6], t[2]));
-    rx_right(R, Jp[2], Jp[3]);
+    t[0] = fmaf(Jp.y, R[2], fmaf(Jp.x, R[0], t[0]));
+    t[1] = fmaf(Jp.y, R[5], fmaf(Jp.x, R[3], t[1]));
+    t[2] = fmaf(Jp.y, R[8], fmaf(Jp.x, R[6], t[2]));
+    rx_right(R, Jp.z, Jp.w);
   }
   const float* tl = arm + 12;  // tool frame (R row-major, t)
   // end effector = T_n * tool
@@ -576,12 +580,11 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
       } else if (phase == 1) {
         // joint l: T_{l-1} = T_l Rx(-alpha) Tx(-a) Tz(-d) Rz(-theta); it turns the
         // links >= l about z_{l-1} through o_{l-1}: dJ/dq_l = z.M + (o x z).F
-        const float* Jp = arm + 24 + (l - 1) * ARM_JW;
-        rx_right(R, Jp[2], -Jp[3]);
-        const float a = Jp[0], d = Jp[1];
-        t[0] -= fmaf(a, R[0], d * R[2]);
-        t[1] -= fmaf(a, R[3], d * R[5]);
-        t[2] -= fmaf(a, R[6], d * R[8]);
+        const float4 Jp = *reinterpret_cast<const float4*>(arm + 24 + (l - 1) * ARM_JW);  // a, d, cos, sin alpha
+        rx_right(R, Jp.z, -Jp.w);
+        t[0] -= fmaf(Jp.x, R[0], Jp.y * R[2]);
+        t[1] -= fmaf(Jp.x, R[3], Jp.y * R[5]);
+        t[2] -= fmaf(Jp.x, R[6], Jp.y * R[8]);
         const float zx = R[2], zy = R[5], zz = R[8];
         const float ox = t[1] * zz - t[2] * zy, oy = t[2] * zx - t[0] * zz, oz = t[0] * zy - t[1] * zx;
         const float tq =
