@@ -186,6 +186,27 @@ enum {
 tamp_status tamp_sample_particles(tamp_scene *scene, int problem_id, int n_particles,
                                   uint64_t seed, int sampler);
 
+/* Subgraph caching (Sec. VI, reusing samples across skeletons): as
+ * tamp_sample_particles, except that the particle components of the longest
+ * action prefix that problem_id shares with src_problem_id (the same actions
+ * in the same order: the same variables, constraints and environment, at the
+ * same components) are copied from src_problem_id's current batch -- the
+ * sampler's output as long as that batch has not been optimised -- instead of
+ * being drawn, and TAMP_SAMPLE_IK solves only the configurations after the
+ * prefix (they read the copied grasps and placements).  With no shared prefix
+ * this is tamp_sample_particles.  src_problem_id must hold a batch of exactly
+ * n_particles when a prefix is shared (else TAMP_ERR_STATE) and differ from
+ * problem_id.  *shared_components (host, may be NULL) receives the number of
+ * components copied. */
+tamp_status tamp_sample_particles_from(tamp_scene *scene, int problem_id, int n_particles, uint64_t seed,
+                                       int sampler, int src_problem_id, int *shared_components);
+
+/* For every term of a compiled skeleton (term order, as tamp_problem_info),
+ * the index of the action of the skeleton that introduced it (host array of
+ * n_terms entries).  Constraint c of the per-constraint counts is the c-th
+ * term whose kind is not TAMP_TERM_OBJ_DIST. */
+tamp_status tamp_term_actions(const tamp_scene *scene, int problem_id, int *action_index);
+
 /* Load a batch [D][n_particles] (host or device pointer, is_device says which)
  * with optional Adam moments m, v (NULL = zeros) and step count t0. */
 tamp_status tamp_set_particles(tamp_scene *scene, int problem_id, int n_particles,

@@ -109,14 +109,22 @@ def _target_fn(pr: Problem, cfg, x: torch.Tensor):
     return target, po + 2
 
 
-def ik_configurations(pr: Problem, X: np.ndarray, iters: int = ITERS, lam: float = LAM, dmax: float = DMAX):
+def ik_configurations(pr: Problem, X: np.ndarray, iters: int = ITERS, lam: float = LAM, dmax: float = DMAX,
+                      keep: int = 0):
     """The configuration sampler on particles X [P, D]: returns a copy with
-    every configuration's q and free yaw replaced by the IK result."""
+    every configuration's q and free yaw replaced by the IK result.
+
+    ``keep``: components below it are a prefix reused from another skeleton's
+    samples (Sec. VI, reusing samples across skeletons that share a constraint
+    subgraph); configurations whose joints lie there keep their values and the
+    later ones read them."""
     x = torch.as_tensor(np.array(X, dtype=np.float64))
     n = pr.n
     for cfg in pr.configs:
-        target, yo = _target_fn(pr, cfg, x)
         qo = cfg["q_off"]
+        if qo < keep:
+            continue
+        target, yo = _target_fn(pr, cfg, x)
         q, y = x[:, qo:qo + n].clone(), x[:, yo].clone()
         for _ in range(iters):
             q, y, _ = dls_step(pr.arm, q, y, target, lam, dmax, pr.sc.q_lo, pr.sc.q_hi)

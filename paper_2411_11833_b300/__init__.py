@@ -116,9 +116,26 @@ class Scene:
         self._check(self._lib.tamp_problem_info(self._h, pid, ctypes.byref(D), ctypes.byref(nt), kinds))
         return D.value, nt.value, list(kinds)
 
-    def sample(self, pid: int, n: int, seed: int, sampler: int = 0):
-        self._check(self._lib.tamp_sample_particles(self._h, pid, int(n), ctypes.c_uint64(seed), int(sampler)))
+    def sample(self, pid: int, n: int, seed: int, sampler: int = 0, cache_from: int | None = None):
+        """tamp_sample_particles; with ``cache_from`` (another problem id)
+        tamp_sample_particles_from, copying the components of the action prefix
+        the two skeletons share from that problem's batch.  Returns the number
+        of components copied (0 without ``cache_from``)."""
+        shared = ctypes.c_int(0)
+        if cache_from is None:
+            self._check(self._lib.tamp_sample_particles(self._h, pid, int(n), ctypes.c_uint64(seed), int(sampler)))
+        else:
+            self._check(self._lib.tamp_sample_particles_from(self._h, pid, int(n), ctypes.c_uint64(seed),
+                                                             int(sampler), int(cache_from), ctypes.byref(shared)))
         self._sizes[pid] = int(n)
+        return shared.value
+
+    def term_actions(self, pid: int):
+        """tamp_term_actions: the skeleton action that introduced each term."""
+        _, nt, _ = self.problem_info(pid)
+        out = (ctypes.c_int * nt)()
+        self._check(self._lib.tamp_term_actions(self._h, pid, out))
+        return list(out)
 
     def set_particles(self, pid: int, x, m=None, v=None, t0: int = 0):
         """x, m, v: [D][P] float32, numpy (host) or torch CUDA tensors (device)."""

@@ -52,6 +52,9 @@ SIGNATURES = {
     "tamp_problem_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int_p, c_int_p, c_int_p]),
     "tamp_sample_particles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                              ctypes.c_int]),
+    "tamp_sample_particles_from": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                                  ctypes.c_int, ctypes.c_int, c_int_p]),
+    "tamp_term_actions": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int_p]),
     "tamp_set_particles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "tamp_get_particles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,

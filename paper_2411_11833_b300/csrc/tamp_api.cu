@@ -31,7 +31,7 @@ int optimize_warps(int K);
 cudaError_t launch_sample_proposal(const uint32_t* rows, int R, const float* out, float* x, int stride, int P,
                                    uint64_t seed, cudaStream_t st);
 cudaError_t launch_ik(const uint32_t* pb, const uint32_t* sc, float* x, int stride, int P, int iters, float lam,
-                      float dmax, const int* chains, int n_chains, int chain_w, cudaStream_t st);
+                      float dmax, const int* chains, int n_chains, int chain_w, int keep, cudaStream_t st);
 cudaError_t launch_ffma_probe(float* out, int blocks, int iters, cudaStream_t st);
 }  // namespace tamp
 
@@ -50,6 +50,9 @@ struct Problem {
   int opt_words = 0;  // leading words of the blob that the optimisation kernel stages
   uint32_t* d_blob = nullptr;
   std::vector<int> term_kinds;
+  std::vector<int> term_actions;          // the action that introduced each term
+  std::vector<tamp_action> acts;          // the skeleton as given
+  std::vector<int> act_off;               // first particle component of each action; [n] = D
   tamp_options opt{};
   // batch state
   int P = 0, cap = 0, t = 0;
@@ -327,8 +330,9 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
     float cp_z = 0.f;
   };
   std::vector<Cfg> cfgs;
-  struct Term { int kind; };
+  struct Term { int kind, ai; };
   std::vector<Term> terms;
+  int cur_ai = 0;
   std::vector<int> comp_kind;  // 0 q, 1 grasp pos, 2 grasp yaw, 3 place pos, 4 place yaw
   struct Samp { int kind; float a, b; int surf; };
   std::vector<Samp> samp;
@@ -337,10 +341,13 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
   struct Slot { int box, off; float z; };
   std::vector<Slot> slots;
   auto add_term = [&](int kind) {
-    terms.push_back({kind});
+    terms.push_back({kind, cur_ai});
     return static_cast<int>(terms.size()) - 1;
   };
+  pr.act_off.assign(static_cast<size_t>(n) + 1, 0);
   for (int ai = 0; ai < n; ++ai) {
+    cur_ai = ai;
+    pr.act_off[ai] = off;
     const int kind = acts[ai].kind, b = acts[ai].box, sf = acts[ai].surface;
     if (kind == TAMP_PICK || kind == TAMP_PLACE) {
       if (b < 0 || b >= B) return fail(s, TAMP_ERR_INVALID_ARG, "action %d: box %d out of range", ai, b);
@@ -438,6 +445,8 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
   if (off > MAX_D) return fail(s, TAMP_ERR_INVALID_ARG, "particle dimension %d exceeds %d", off, MAX_D);
   if (static_cast<int>(slots.size()) > MAX_SLOT) return fail(s, TAMP_ERR_INVALID_ARG, "too many Place actions");
   pr.D = off;
+  pr.act_off[n] = off;
+  pr.acts.assign(acts, acts + n);
   pr.K = static_cast<int>(cfgs.size());
   // learned-proposal rows: features of what each Pick/Place acts on, and the
   // record the sampler decodes with (Sec. V-A; the layouts are in tamp.h)
@@ -560,7 +569,9 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
   v[PH_OFF_TERMS] = static_cast<uint32_t>(v.size());
   int ncon = 0;
   pr.term_kinds.clear();
+  pr.term_actions.clear();
   for (const Term& t : terms) {
+    pr.term_actions.push_back(t.ai);
     v.push_back(static_cast<uint32_t>(t.kind));
     v.push_back(fbits(opt.w[t.kind]));
     v.push_back(fbits(opt.tol[t.kind]));
@@ -975,9 +986,54 @@ tamp_status tamp_problem_info(const tamp_scene* sc, int id, int* D, int* n_terms
   return TAMP_OK;
 }
 
+tamp_status tamp_term_actions(const tamp_scene* sc, int id, int* action_index) {
+  tamp_scene* s = const_cast<tamp_scene*>(sc);
+  Problem* pr = get_problem(s, id);
+  if (!pr) return fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", id);
+  if (!action_index) return fail(s, TAMP_ERR_INVALID_ARG, "null output");
+  std::copy(pr->term_actions.begin(), pr->term_actions.end(), action_index);
+  return TAMP_OK;
+}
+
+namespace {
+// Components of the longest action prefix two skeletons share: the same
+// actions in the same order give the same sub-CSP (same variables, same
+// constraints, same environment), laid out at the same particle components.
+int shared_prefix_components(const Problem& a, const Problem& b) {
+  size_t k = 0;
+  while (k < a.acts.size() && k < b.acts.size() && a.acts[k].kind == b.acts[k].kind &&
+         a.acts[k].box == b.acts[k].box && a.acts[k].surface == b.acts[k].surface)
+    ++k;
+  return a.act_off[k];
+}
+}  // namespace
+
+static tamp_status sample_batch(tamp_scene* s, Problem* pr, int P, uint64_t seed, int sampler, const Problem* src,
+                                int keep);
+
 tamp_status tamp_sample_particles(tamp_scene* s, int id, int P, uint64_t seed, int sampler) {
   Problem* pr = get_problem(s, id);
   if (!pr) return fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", id);
+  return sample_batch(s, pr, P, seed, sampler, nullptr, 0);
+}
+
+tamp_status tamp_sample_particles_from(tamp_scene* s, int id, int P, uint64_t seed, int sampler, int src_id,
+                                       int* shared) {
+  Problem* pr = get_problem(s, id);
+  if (!pr) return fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", id);
+  Problem* src = get_problem(s, src_id);
+  if (!src) return fail(s, TAMP_ERR_INVALID_ARG, "unknown source problem %d", src_id);
+  if (src == pr) return fail(s, TAMP_ERR_INVALID_ARG, "a problem cannot be its own source");
+  const int keep = shared_prefix_components(*pr, *src);
+  if (keep > 0 && (!src->has_batch || src->P != P))
+    return fail(s, TAMP_ERR_STATE, "source problem %d holds no batch of %d particles", src_id, P);
+  tamp_status st = sample_batch(s, pr, P, seed, sampler, keep > 0 ? src : nullptr, keep);
+  if (st == TAMP_OK && shared) *shared = keep;
+  return st;
+}
+
+static tamp_status sample_batch(tamp_scene* s, Problem* pr, int P, uint64_t seed, int sampler, const Problem* src,
+                                int keep) {
   if (P <= 0 || P > (1 << 24)) return fail(s, TAMP_ERR_INVALID_ARG, "n_particles %d out of range", P);
   if (sampler < 0 || sampler > 3) return fail(s, TAMP_ERR_INVALID_ARG, "sampler %d not available", sampler);
   if ((sampler & TAMP_SAMPLE_LEARNED) && !s->proposal)
@@ -999,6 +1055,10 @@ tamp_status tamp_sample_particles(tamp_scene* s, int id, int P, uint64_t seed, i
     if (st != TAMP_OK) return fail(s, st, "proposal network forward: %s", tamp_mlp_last_error(s->proposal));
     CUDA_TRY(s, launch_sample_proposal(pr->d_prow, pr->R, pr->d_pout, pr->d_x, P, P, seed, s->stream));
   }
+  // the shared prefix: the source's components (rows of the [D][P] layout) as they stand
+  if (src && keep > 0)
+    CUDA_TRY(s, cudaMemcpyAsync(pr->d_x, src->d_x, static_cast<size_t>(keep) * P * 4, cudaMemcpyDeviceToDevice,
+                                s->stream));
   if (sampler & TAMP_SAMPLE_IK) {
     if (!pr->d_chains) {
       CUDA_TRY(s, cudaMalloc(&pr->d_chains, pr->chains.size() * 4));
@@ -1006,7 +1066,7 @@ tamp_status tamp_sample_particles(tamp_scene* s, int id, int P, uint64_t seed, i
                                   s->stream));
     }
     CUDA_TRY(s, launch_ik(pr->d_blob, s->d_blob, pr->d_x, P, P, TAMP_IK_ITERS, TAMP_IK_DAMPING, TAMP_IK_MAX_STEP,
-                          pr->d_chains, pr->n_chain, 1 + pr->K, s->stream));
+                          pr->d_chains, pr->n_chain, 1 + pr->K, keep, s->stream));
   }
   return TAMP_OK;
 }

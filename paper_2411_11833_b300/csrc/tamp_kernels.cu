@@ -1243,12 +1243,14 @@ __device__ __forceinline__ void rot_log(const float (&E)[9], float (&w)[3]) {
 // a chain: a Place reads the grasp yaw its Pick chose, a later Pick the yaw its
 // Place chose, and nothing reads another box's variables.  One thread per
 // (particle, chain); chains[c * chain_w] is a chain's length, then its
-// configuration indices.
+// configuration indices.  Configurations whose joints lie below component
+// `keep` belong to a prefix copied from another skeleton's batch (subgraph
+// caching, Sec. VI) and keep their values; later ones read its grasps and yaws.
 __global__ void __launch_bounds__(128) ik_configs_kernel(const uint32_t* __restrict__ pb,
                                                          const uint32_t* __restrict__ sc, float* __restrict__ x,
                                                          int stride, int P, int iters, float lam, float dmax,
                                                          const int* __restrict__ chains, int n_chains,
-                                                         int chain_w) {
+                                                         int chain_w, int keep) {
   const long g = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (g >= static_cast<long>(P) * n_chains) return;
   const int i = static_cast<int>(g % P), chain = static_cast<int>(g / P);
@@ -1263,6 +1265,7 @@ __global__ void __launch_bounds__(128) ik_configs_kernel(const uint32_t* __restr
     const int* cf = reinterpret_cast<const int*>(pb + pb[PH_OFF_CFG] + k * CFG_W);
     const float* cff = reinterpret_cast<const float*>(cf);
     const int kind = cf[CF_KIND], qo = cf[CF_QOFF], go = cf[CF_GOFF], tsrc = cf[CF_TSRC];
+    if (qo < keep) continue;  // a configuration of a kept prefix: its values stay as they are
     const bool place = kind == 1;
     float bx, by, bz, byaw;
     if (tsrc < 0) {
@@ -1398,11 +1401,11 @@ __global__ void __launch_bounds__(128) ik_configs_kernel(const uint32_t* __restr
 }
 
 cudaError_t launch_ik(const uint32_t* pb, const uint32_t* sc, float* x, int stride, int P, int iters, float lam,
-                      float dmax, const int* chains, int n_chains, int chain_w, cudaStream_t st) {
+                      float dmax, const int* chains, int n_chains, int chain_w, int keep, cudaStream_t st) {
   if (P == 0 || iters <= 0 || n_chains == 0) return cudaSuccess;
   const long threads = static_cast<long>(P) * n_chains;
   ik_configs_kernel<<<static_cast<unsigned>((threads + 127) / 128), 128, 0, st>>>(pb, sc, x, stride, P, iters, lam,
-                                                                                dmax, chains, n_chains, chain_w);
+                                                                                dmax, chains, n_chains, chain_w, keep);
   return cudaGetLastError();
 }
 

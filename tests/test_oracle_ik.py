@@ -133,3 +133,30 @@ def test_converged_particles_satisfy_the_kin_terms():
     assert set(kinds[moved]) <= {"q", "gyaw", "pyaw"}
     q = kinds == "q"
     assert (X[:, q] >= -2.8 - 1e-12).all() and (X[:, q] <= 2.8 + 1e-12).all()
+
+
+def test_kept_prefix_stays_and_later_configurations_are_solved():
+    # subgraph caching (Sec. VI): the components of a prefix reused from another
+    # skeleton's samples stay as they are; the configurations after it are
+    # solved against their own targets, reading the prefix's grasps and yaws
+    sc, acts = sg.robot_packing_problem(21002, n_boxes=2)
+    pr = Problem(sc, acts)
+    k = pr.configs[1]["q_off"] + pr.n            # components of (Pick 0, Place 0)
+    src = ik.ik_configurations(pr, philox.sample_uniform(pr, 64, 5), iters=120, lam=0.02)
+    X0 = philox.sample_uniform(pr, 64, 6)
+    X0[:, :k] = src[:, :k]
+    X = ik.ik_configurations(pr, X0, iters=120, lam=0.02, keep=k)
+    assert np.array_equal(X[:, :k], X0[:, :k])
+    tv = pr.term_values(torch.tensor(X)).numpy()
+    later = [j for j, t in enumerate(pr.terms) if t.kind in (KIN_POS, KIN_ROT) and t.action >= 2]
+    earlier = [j for j, t in enumerate(pr.terms) if t.kind in (KIN_POS, KIN_ROT) and t.action < 2]
+    rate = (tv[:, later] < 1e-6).all(axis=1).mean()
+    # as often as when the whole particle is solved from the same draws
+    plain = pr.term_values(torch.tensor(ik.ik_configurations(pr, X0, iters=120, lam=0.02))).numpy()
+    assert rate > 0.15 and rate >= 0.8 * (plain[:, later] < 1e-6).all(axis=1).mean(), rate
+    # the kept prefix still satisfies Kin where the source's IK did
+    tv_src = pr.term_values(torch.tensor(src)).numpy()
+    assert np.array_equal(tv[:, earlier] < 1e-6, tv_src[:, earlier] < 1e-6)
+    # keep = 0 is the plain sampler, keep = D leaves everything
+    assert np.array_equal(ik.ik_configurations(pr, X0, iters=3, keep=0), ik.ik_configurations(pr, X0, iters=3))
+    assert np.array_equal(ik.ik_configurations(pr, X0, iters=3, keep=pr.D), X0)
