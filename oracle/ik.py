@@ -31,7 +31,7 @@ import numpy as np
 import torch
 
 from . import geometry as G
-from .problem import DT, PICK, Problem
+from .problem import DT, KNOT, PICK, Problem
 
 ITERS, LAM, DMAX = 64, 0.05, 0.4
 
@@ -122,7 +122,7 @@ def ik_configurations(pr: Problem, X: np.ndarray, iters: int = ITERS, lam: float
     n = pr.n
     for cfg in pr.configs:
         qo = cfg["q_off"]
-        if qo < keep:
+        if qo < keep or cfg["kind"] == KNOT:   # knots are interpolated, not solved
             continue
         target, yo = _target_fn(pr, cfg, x)
         q, y = x[:, qo:qo + n].clone(), x[:, yo].clone()

@@ -67,6 +67,8 @@ def sample_uniform(problem, n_particles: int, seed: int) -> np.ndarray:
         for j in range(n):
             X[:, qo + j] = sc.q_lo[j] + (sc.q_hi[j] - sc.q_lo[j]) * U[qo + j]
         b = cfg["box"]
+        if cfg["kind"] == 2:      # a trajectory knot has only its configuration
+            continue
         if cfg["kind"] == 0:      # Pick introduces the grasp variable
             go = cfg["g_off"]
             h = sc.box_half[b]

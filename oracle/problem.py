@@ -13,6 +13,16 @@ Sec. V-A:
                         CFreeHold(o, g, q), CFreePlace(o, p) (+ joint limits)
   MinimizeObjDist       cost: sum of pairwise distances of the moved boxes
 
+With n_knots > 0 the motion between consecutive Pick/Place configurations is
+a trajectory of n_knots knot configurations (Listing 1 MoveFree / MoveHold;
+Sec. VIII, real-robot stacking: knot points, initialised by linear
+interpolation between the start and end configurations):
+
+  MoveFree(q1, q2, tau)        con: Motion(q1, tau, q2) (joint limits of every
+                               knot), CFreeTraj(tau)  cost: TrajLength(tau)
+  MoveHold(o, g, q1, q2, tau)  con: Motion, CFreeTrajHold(o, g, tau)
+                               cost: TrajLength(tau)
+
 The particle layout (Pick: grasp x,y,z,yaw then q; Place: placement x,y,yaw
 then q) is the interface documented in include/tamp.h.
 
@@ -28,7 +38,15 @@ Readings of points the paper leaves open (each one is listed in the design doc):
     scored with the bound distance to the surface rectangle, summed; z is
     fixed by the surface (placements are x, y, yaw);
   * Grasp(o, g): bound distance of g_xyz to [-h_x, h_x] x [-h_y, h_y] x
-    [h_z - 0.02, h_z], yaw free.
+    [h_z - 0.02, h_z], yaw free;
+  * knots: the knots of the motion into an action sit in the particle just
+    before that action's own variables; CFreeTraj(Hold) is CFreeHold's
+    penetration depth at each knot -- the arm, plus the held box on a MoveHold,
+    against the static cuboids and every box not in the hand (on a MoveFree
+    also the box about to be picked) -- checked at the knots only; TrajLength
+    is the joint-space length sum_i ||w_{i+1} - w_i|| of the polyline q1,
+    knots, q2; there is no motion before the first action (the scene has no
+    initial configuration).
 """
 from __future__ import annotations
 
@@ -42,11 +60,14 @@ from . import geometry as G
 
 DT = torch.float64
 PICK, PLACE, GOAL = 0, 1, 2
+KNOT = 2                                     # configuration kind of a trajectory knot
 
 # term kinds (include/tamp.h: tamp_term_kind)
-KIN_POS, KIN_ROT, GRASP, STABLE_PLACE, CFREE_HOLD, CFREE_PLACE, JOINT_LIMIT, OBJ_DIST = range(8)
+(KIN_POS, KIN_ROT, GRASP, STABLE_PLACE, CFREE_HOLD, CFREE_PLACE, JOINT_LIMIT, OBJ_DIST, CFREE_TRAJ,
+ TRAJ_LEN) = range(10)
 TERM_NAMES = ["kin_pos", "kin_rot", "grasp", "stable_place", "cfree_hold", "cfree_place",
-              "joint_limit", "obj_dist"]
+              "joint_limit", "obj_dist", "cfree_traj", "traj_len"]
+COST_KINDS = (OBJ_DIST, TRAJ_LEN)            # costs, never constraints (Eq. 3)
 
 
 @dataclass
@@ -57,11 +78,14 @@ class Options:
     stable placement (2.0) (appendix "Cost Weights"); the goal weight 0.25 is
     the appendix's lambda for the object-distance cost.  Tolerances (appendix
     "Constraint Tolerances"): world collisions 1 mm, kinematics 5 mm / 0.05 rad,
-    joint limits 0, containment 1 mm; grasp bounds 1 mm (reading).
+    joint limits 0, containment 1 mm; grasp bounds 1 mm (reading).  Knots:
+    CFreeTraj as the other collisions (1.0, 1 mm); TrajLength 0.01 per radian
+    of joint-space path (reading: the paper gives no weight).
     """
 
-    w: list = field(default_factory=lambda: [1.0, 5.0, 1.0, 2.0, 1.0, 1.0, 1.0, 0.25])
-    tol: list = field(default_factory=lambda: [5e-3, 0.05, 1e-3, 1e-3, 1e-3, 1e-3, 0.0, math.inf])
+    w: list = field(default_factory=lambda: [1.0, 5.0, 1.0, 2.0, 1.0, 1.0, 1.0, 0.25, 1.0, 0.01])
+    tol: list = field(default_factory=lambda: [5e-3, 0.05, 1e-3, 1e-3, 1e-3, 1e-3, 0.0, math.inf, 1e-3, math.inf])
+    n_knots: int = 0                        # knot configurations per motion between actions
     lr_joint: float = 1e-2
     lr_pos: float = 3e-3
     lr_yaw: float = 1e-2
@@ -103,7 +127,27 @@ class Problem:
         self.configs = []                        # per configuration: dict
         self.terms: list[Term] = []
         self.goal_boxes = None
+        self.segments = []                       # per motion: (first config, knot configs, last config, term)
+        m = self.opts.n_knots
         for ai, (kind, b, s) in enumerate(self.actions):
+            if kind in (PICK, PLACE) and m > 0 and self.configs:
+                # the motion from the previous configuration into this action's
+                hb = held[0] if held is not None else -1
+                env = [(j, pose[j]) for j in range(B) if j != hb]
+                knots = []
+                for _ in range(m):
+                    q_off = off
+                    self.kinds += ["q"] * self.n
+                    off += self.n
+                    self.configs.append(dict(action=ai, kind=KNOT, box=hb, q_off=q_off,
+                                             g_off=held[1] if held is not None else -1, env=env))
+                    ci = len(self.configs) - 1
+                    knots.append(ci)
+                    for k in (CFREE_TRAJ, JOINT_LIMIT):
+                        self.terms.append(Term(k, ai, hb, ci))
+                prev = max(c for c, cf in enumerate(self.configs) if cf["kind"] != KNOT)
+                self.terms.append(Term(TRAJ_LEN, ai, -1, len(self.segments)))
+                self.segments.append(dict(start=prev, knots=knots, end=len(self.configs)))
             if kind == PICK:
                 if held is not None:
                     raise ValueError(f"action {ai}: Pick while holding a box (HandEmpty fails)")
@@ -198,6 +242,19 @@ class Problem:
             q = x[:, cfg["q_off"]:cfg["q_off"] + self.n]
             frames = G.forward_kinematics(self.arm, q)                   # [P,n+1,4,4]
             ee = G.end_effector(self.arm, frames)
+            jl = G.dist_from_bounds(q, torch.as_tensor(sc.q_lo, dtype=DT), torch.as_tensor(sc.q_hi, dtype=DT))
+            if cfg["kind"] == KNOT:
+                # CFreeTraj / CFreeTrajHold at this knot, and its joint limits (Motion)
+                c_all = G.apply(frames[:, links], arm_c)
+                r_all = arm_r
+                if cfg["box"] >= 0:
+                    g = x[:, cfg["g_off"]:cfg["g_off"] + 4]
+                    Gp = G.grasp_pose(g[:, 0], g[:, 1], g[:, 2], g[:, 3])
+                    held_c, held_r = self._box_spheres(cfg["box"], ee @ G.rigid_inverse(Gp))
+                    c_all = torch.cat([c_all, held_c], dim=1)
+                    r_all = torch.cat([arm_r, held_r])
+                per_cfg[ci] = {CFREE_TRAJ: self._env_penetration(c_all, r_all, cfg["env"], x), JOINT_LIMIT: jl}
+                continue
             g = x[:, cfg["g_off"]:cfg["g_off"] + 4]
             Gp = G.grasp_pose(g[:, 0], g[:, 1], g[:, 2], g[:, 3])
             b = cfg["box"]
@@ -209,7 +266,6 @@ class Problem:
             c_all = torch.cat([arm_world, held_c], dim=1)
             r_all = torch.cat([arm_r, held_r])
             cfree_hold = self._env_penetration(c_all, r_all, cfg["env"], x)
-            jl = G.dist_from_bounds(q, torch.as_tensor(sc.q_lo, dtype=DT), torch.as_tensor(sc.q_hi, dtype=DT))
             vals = {KIN_POS: e_pos, KIN_ROT: e_rot, CFREE_HOLD: cfree_hold, JOINT_LIMIT: jl}
             if cfg["kind"] == PICK:
                 h = torch.as_tensor(sc.box_half[b], dtype=DT)
@@ -223,13 +279,39 @@ class Problem:
                 vals[CFREE_PLACE] = self._env_penetration(pc, pr, cfg["env"], x)
             per_cfg[ci] = vals
         for ti, t in enumerate(self.terms):
-            if t.kind == OBJ_DIST:
+            if t.kind == TRAJ_LEN:
+                out[ti] = self._traj_length(self.segments[t.cfg], x)
+            elif t.kind == OBJ_DIST:
                 pos = torch.stack([self._box_pose(src, j, x)[:, :3, 3] for j, src in self.goal_boxes], dim=1) \
                     if self.goal_boxes else torch.zeros(P, 0, 3, dtype=DT)
                 out[ti] = G.obj_dist(pos)
             else:
                 out[ti] = per_cfg[t.cfg][t.kind]
         return torch.stack(out, dim=1) if out else torch.zeros(P, 0, dtype=DT)
+
+    def _waypoints(self, seg, x):
+        cs = [seg["start"]] + seg["knots"] + [seg["end"]]
+        return [x[:, self.configs[c]["q_off"]:self.configs[c]["q_off"] + self.n] for c in cs]
+
+    def _traj_length(self, seg, x):
+        """TrajLength: joint-space length of the polyline start, knots, end."""
+        w = self._waypoints(seg, x)
+        return sum(G.norm(w[i + 1] - w[i]) for i in range(len(w) - 1))
+
+    def interpolate_knots(self, X):
+        """Knot initialisation (Sec. VIII): each motion's knots evenly spaced on
+        the straight joint-space line between its start and end
+        configurations.  Returns a copy of X [P, D]."""
+        x = np.array(X, dtype=np.float64)
+        for seg in self.segments:
+            qa = x[:, self.configs[seg["start"]]["q_off"]:self.configs[seg["start"]]["q_off"] + self.n]
+            qb = x[:, self.configs[seg["end"]]["q_off"]:self.configs[seg["end"]]["q_off"] + self.n]
+            m = len(seg["knots"])
+            for j, c in enumerate(seg["knots"]):
+                f = (j + 1) / (m + 1)
+                o = self.configs[c]["q_off"]
+                x[:, o:o + self.n] = qa + f * (qb - qa)
+        return x
 
     def _containment(self, b, s, p):
         """StablePlace containment: sum over the footprint's 4 corners of the
@@ -258,7 +340,7 @@ class Problem:
         return torch.tensor([self.opts.tol[t.kind] for t in self.terms], dtype=DT)
 
     def constraint_mask(self):
-        return torch.tensor([t.kind != OBJ_DIST for t in self.terms])
+        return torch.tensor([t.kind not in COST_KINDS for t in self.terms])
 
     def total_cost(self, x: torch.Tensor) -> torch.Tensor:
         """Eq. 2: J(x) = sum_c lambda_c J_c + sum_c' lambda_c' c'."""
@@ -372,10 +454,23 @@ class Problem:
         def bound_margins(v, lo, hi):
             return [(v - lo).abs().amin(-1), (v - hi).abs().amin(-1)]
 
+        for seg in self.segments:
+            w = self._waypoints(seg, x)
+            ms += [G.norm(w[i + 1] - w[i]) for i in range(len(w) - 1)]
         for cfg in self.configs:
             q = x[:, cfg["q_off"]:cfg["q_off"] + self.n]
             frames = G.forward_kinematics(self.arm, q)
             ee = G.end_effector(self.arm, frames)
+            if cfg["kind"] == KNOT:
+                c_all, r_all = G.apply(frames[:, links], arm_c), arm_r
+                if cfg["box"] >= 0:
+                    g = x[:, cfg["g_off"]:cfg["g_off"] + 4]
+                    Gp = G.grasp_pose(g[:, 0], g[:, 1], g[:, 2], g[:, 3])
+                    held_c, held_r = self._box_spheres(cfg["box"], ee @ G.rigid_inverse(Gp))
+                    c_all, r_all = torch.cat([c_all, held_c], 1), torch.cat([arm_r, held_r])
+                ms += env_margins(c_all, r_all, cfg["env"])
+                ms += bound_margins(q, lo_q, hi_q)
+                continue
             g = x[:, cfg["g_off"]:cfg["g_off"] + 4]
             Gp = G.grasp_pose(g[:, 0], g[:, 1], g[:, 2], g[:, 3])
             b = cfg["box"]

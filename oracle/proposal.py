@@ -39,7 +39,7 @@ import math
 import numpy as np
 
 from . import philox
-from .problem import PICK, PLACE, GOAL, Problem
+from .problem import GOAL, KNOT, PICK, PLACE, Problem
 
 NF, NT = 48, 16
 LS_MIN, LS_MAX = -8.0, 3.0
@@ -51,6 +51,8 @@ def action_rows(sc, actions):
     pr = Problem(sc, actions)
     rows = []
     for cfg in pr.configs:
+        if cfg["kind"] == KNOT:
+            continue
         ai = cfg["action"]
         kind, b, s = actions[ai]
         if kind == PICK:
