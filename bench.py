@@ -63,6 +63,8 @@ def parse():
                     help="optimize: the headline line; mlp: the proposal network's tensor-core kernels alone")
     ap.add_argument("--workload", default="packing", choices=["packing", "stress"],
                     help="packing (the headline line) or the stress scene (12 boxes, 64 cuboids, 100 spheres)")
+    ap.add_argument("--knots", type=int, default=0,
+                    help="trajectory knots per motion between actions (0: configurations only, the headline)")
     return ap.parse_args()
 
 
@@ -325,9 +327,12 @@ def main():
     else:
         sc, acts = sg.packing_problem(SCENE_SEED)
         workload = PACKING_WORKLOAD
+    if args.knots:
+        workload += (f"; trajectories of {args.knots} knots per motion (MoveFree / MoveHold: CFreeTraj, joint "
+                     "limits, TrajLength)")
     with torch.cuda.stream(stream):
         scene = pkg.Scene(sc, device=local, stream=stream.cuda_stream)
-        pid = scene.set_skeleton(acts, pkg.default_options(lanes=args.lanes))
+        pid = scene.set_skeleton(acts, pkg.default_options(lanes=args.lanes, n_knots=args.knots))
     D, NT, _ = scene.problem_info(pid)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     tuned = None
@@ -396,8 +401,8 @@ def main():
         return
     # roofline numerator: the method's all-pairs work (per-unit
     # figures, flops.algorithmic_flops) x particle-iterations of one launch
-    launch_flops = P * T * flops.algorithmic_flops(sc, acts)
-    executed = (P * ((T + 1) * flops.eval_flops(sc, acts) + T * flops.adam_flops(D))
+    launch_flops = P * T * flops.algorithmic_flops(sc, acts, args.knots)
+    executed = (P * ((T + 1) * flops.eval_flops(sc, acts, args.knots) + T * flops.adam_flops(D))
                 + flops.exact_flops(work[0], work[1], sc.box_spheres.shape[1]))
     kern_s = sum(kern_ms) / len(kern_ms) / 1e3
     props = torch.cuda.get_device_properties(dev)
@@ -409,7 +414,8 @@ def main():
         probe = round(probe_tf.value, 2)
     achieved = launch_flops / kern_s / 1e12
     sha = kernel_source_sha()
-    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["source_sha"] == sha and args.workload == "packing" else None
+    headline = args.workload == "packing" and args.knots == 0
+    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["source_sha"] == sha and headline else None
     out = {
         "metric": METRIC, "value": value, "unit": "particle-iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
@@ -430,9 +436,9 @@ def main():
         "kernel_ms": sum(kern_ms) / len(kern_ms),
         "satisfied_last_step": int(q["n_satisfied"]), "first_satisfying_iter_last_step": int(q["first_iter"]),
     }
-    if not args.no_ttfs and world == 1 and args.workload == "packing":
+    if not args.no_ttfs and world == 1 and headline:
         out["ttfs"] = measure_ttfs(pkg, sg)
-    if not args.no_cpu_baseline and world == 1 and args.workload == "packing":
+    if not args.no_cpu_baseline and world == 1 and headline:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out))
     scene.close()

@@ -66,7 +66,9 @@ enum {
   TAMP_TERM_CFREE_PLACE = 5,  /* CFreePlace: placed box penetration depth, m          */
   TAMP_TERM_JOINT_LIMIT = 6,  /* Motion (limits part): bound distance of q            */
   TAMP_TERM_OBJ_DIST = 7,     /* MinimizeObjDist goal cost: sum of pairwise distances */
-  TAMP_N_TERM_KINDS = 8
+  TAMP_TERM_CFREE_TRAJ = 8,   /* CFreeTraj(Hold): penetration depth at a knot, m       */
+  TAMP_TERM_TRAJ_LEN = 9,     /* TrajLength cost: joint-space length of a motion, rad  */
+  TAMP_N_TERM_KINDS = 10
 };
 
 typedef struct tamp_scene tamp_scene;   /* opaque, library-owned */
@@ -110,7 +112,18 @@ typedef struct {
  * V-B).  tamp_default_options fills the appendix's values: weights 1 except
  * kinematic rotation 5 and stable placement 2, goal 0.25; tolerances 5 mm /
  * 0.05 rad (Kin), 1 mm (collisions, containment, grasp bounds), 0 (joint
- * limits); beta1 0.9, beta2 0.999, eps 1e-8; lr 1e-2 (joints, yaws), 3e-3 (m). */
+ * limits); beta1 0.9, beta2 0.999, eps 1e-8; lr 1e-2 (joints, yaws), 3e-3 (m);
+ * no knots.  Knots (Listing 1 MoveFree / MoveHold; Sec. VIII: trajectories as
+ * knot points): with n_knots > 0 the motion between two consecutive Pick /
+ * Place configurations is a trajectory of n_knots knot configurations whose
+ * joint positions sit in the particle just before the variables of the action
+ * the motion leads to (there is no motion before the first action).  Each
+ * knot carries CFreeTraj -- the CFreeHold penetration depth of the arm, plus
+ * the held box on a MoveHold (between a Pick and its Place), against the
+ * static cuboids and every box not in the hand -- (weight 1, tolerance 1 mm)
+ * and its joint limits (Motion); each motion carries the TrajLength cost, the
+ * joint-space length of the polyline start, knots, end (weight 0.01: the paper
+ * gives none; never a constraint). */
 typedef struct {
   float w[TAMP_N_TERM_KINDS];
   float tol[TAMP_N_TERM_KINDS];
@@ -119,7 +132,8 @@ typedef struct {
   int optimize_grasp;           /* 0: grasps keep their sampled values (lr 0)            */
   int scale_by_batch;           /* 1: gradient of the batch mean (Eq. 4), i.e. / N_b      */
   int lanes;                    /* threads per (particle, configuration): 0 = tuned, 1,2,4,8 */
-  int reserved[3];
+  int n_knots;                  /* knot configurations per motion between actions (0: none) */
+  int reserved[2];
 } tamp_options;
 
 void tamp_default_options(tamp_options *opt);
@@ -154,7 +168,9 @@ enum {
 #define TAMP_IK_DAMPING 0.05f
 #define TAMP_IK_MAX_STEP 0.4f
 
-/* Initialise a batch of n_particles (InitializeParticles, Alg. 1).  sampler 0:
+/* Initialise a batch of n_particles (InitializeParticles, Alg. 1).  Knots,
+ * whatever the sampler, are then placed evenly on the joint-space line between
+ * their motion's start and end configurations (Sec. VIII).  sampler 0:
  * uniform within bounds (the paper's "Optimization" initialisation, Sec. VIII):
  * component c of particle i takes u = (w >> 8) * 2^-24 where w is the first
  * output word of Philox4x32-10 (Salmon et al., SC'11) with counter (i, c, 0, 0)

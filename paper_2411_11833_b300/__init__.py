@@ -13,6 +13,9 @@ import numpy as np
 from . import _native
 from ._native import Action, Options, SceneDesc, TampError
 
+# term kinds that are costs, never constraints (Eq. 3): MinimizeObjDist, TrajLength
+COST_TERM_KINDS = (7, 9)
+
 PICK, PLACE, GOAL = 0, 1, 2
 TERM_NAMES = ["kin_pos", "kin_rot", "grasp", "stable_place", "cfree_hold", "cfree_place", "joint_limit",
               "obj_dist"]
@@ -181,7 +184,7 @@ class Scene:
 
     def query(self, pid: int, n: int, want_particles: bool = False):
         D, nt, kinds = self.problem_info(pid)
-        ncon = sum(1 for k in kinds if k != 7)
+        ncon = sum(1 for k in kinds if k not in COST_TERM_KINDS)
         mask = np.zeros(n, np.uint8)
         cost = np.zeros(n, np.float32)
         counts = np.zeros(max(ncon, 1), np.int32)

@@ -33,6 +33,8 @@ cudaError_t launch_sample_proposal(const uint32_t* rows, int R, const float* out
 cudaError_t launch_ik(const uint32_t* pb, const uint32_t* sc, float* x, int stride, int P, int iters, float lam,
                       float dmax, const int* chains, int n_chains, int chain_w, int keep, cudaStream_t st);
 cudaError_t launch_ffma_probe(float* out, int blocks, int iters, cudaStream_t st);
+cudaError_t launch_knots(const uint32_t* pb, float* x, int stride, int P, int n_seg, int nj, int keep,
+                         cudaStream_t st);
 }  // namespace tamp
 
 tamp_status mlp_forward_on_stream(tamp_mlp* n, const float* x_dev, int B, float* out_dev, cudaStream_t st,
@@ -46,6 +48,7 @@ struct Problem {
   int id = -1;
   int D = 0, K = 0, NT = 0, NCON = 0, NSLOT = 0;
   int NANG = 0;       // entries of the kernel's per-iteration (cos, sin) table per particle
+  int n_seg = 0;      // motions with knots
   std::vector<uint32_t> blob;
   int opt_words = 0;  // leading words of the blob that the optimisation kernel stages
   uint32_t* d_blob = nullptr;
@@ -322,6 +325,7 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
   int off = 0;
   struct Cfg {
     int kind, box, qo, go, tsrc, surf, ai;
+    int hold = 1;                   // the hand holds `box` with the grasp at `go`
     int t_slot = -1, cp_slot = -1;  // placement slots of the Kin target and of the CFreePlace box
     std::vector<std::pair<int, PoseSrc>> env;
     int t_kp, t_kr, t_x, t_cf, t_cp, t_jl;
@@ -330,6 +334,8 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
     float cp_z = 0.f;
   };
   std::vector<Cfg> cfgs;
+  struct Seg { int qa, qb, qk, m, t; };   // motion: start / end q offsets, first knot q offset, knots, term
+  std::vector<Seg> segs;
   struct Term { int kind, ai; };
   std::vector<Term> terms;
   int cur_ai = 0;
@@ -351,6 +357,32 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
     const int kind = acts[ai].kind, b = acts[ai].box, sf = acts[ai].surface;
     if (kind == TAMP_PICK || kind == TAMP_PLACE) {
       if (b < 0 || b >= B) return fail(s, TAMP_ERR_INVALID_ARG, "action %d: box %d out of range", ai, b);
+      // the motion from the previous configuration into this action's (Listing 1
+      // MoveFree / MoveHold): n_knots knots, their q before this action's variables
+      if (opt.n_knots > 0 && !cfgs.empty()) {
+        int prev = static_cast<int>(cfgs.size()) - 1;
+        while (cfgs[prev].kind == CK_KNOT) --prev;
+        Seg sg{cfgs[prev].qo, -1, off, opt.n_knots, -1};
+        for (int j = 0; j < opt.n_knots; ++j) {
+          Cfg c{};
+          c.kind = CK_KNOT; c.box = held; c.hold = held >= 0 ? 1 : 0; c.go = held >= 0 ? held_g : 0; c.ai = ai;
+          c.qo = off;
+          off += nj;
+          for (int d = 0; d < nj; ++d) {
+            samp.push_back({SK_LINEAR, 0.f, 0.f, 0});
+            comp_kind.push_back(0);
+          }
+          for (int jb = 0; jb < B; ++jb)
+            if (jb != held) c.env.push_back({jb, pose[jb]});
+          c.tsrc = -1; c.surf = -1;
+          c.t_cf = add_term(TK_CFREE_TRAJ); c.t_jl = add_term(TK_JOINT_LIMIT);
+          c.t_kp = c.t_kr = c.t_x = c.t_cf;  // never read for a knot
+          c.t_cp = -1;
+          cfgs.push_back(c);
+        }
+        sg.t = add_term(TK_TRAJ_LEN);
+        segs.push_back(sg);
+      }
     }
     if (kind == TAMP_PICK) {
       if (held >= 0) return fail(s, TAMP_ERR_INVALID_ARG, "action %d: Pick while holding box %d", ai, held);
@@ -426,6 +458,13 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
     }
   }
   if (cfgs.empty()) return fail(s, TAMP_ERR_INVALID_ARG, "skeleton has no Pick/Place action");
+  // each motion ends at the configuration right after its knots
+  for (Seg& sg : segs)
+    for (size_t k = 0; k < cfgs.size(); ++k)
+      if (cfgs[k].kind != CK_KNOT && cfgs[k].qo > sg.qk) {
+        sg.qb = cfgs[k].qo;
+        break;
+      }
   // CFreePlace of a Place: first half of the box's spheres on the preceding Pick
   // (the hand holds one box, so that Pick is the configuration right before),
   // second half on the Place itself
@@ -457,6 +496,7 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
     std::vector<int> box_chain(B, -1);
     std::vector<std::vector<int>> ch;
     for (int k = 0; k < static_cast<int>(cfgs.size()); ++k) {
+      if (cfgs[k].kind == CK_KNOT) continue;  // knots are interpolated, not solved
       const int b = cfgs[k].box;
       if (box_chain[b] < 0) {
         box_chain[b] = static_cast<int>(ch.size());
@@ -472,12 +512,15 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
       for (size_t e = 0; e < ch[c].size(); ++e) pr.chains[static_cast<size_t>(c) * w + 1 + e] = ch[c][e];
     }
   }
-  pr.R = static_cast<int>(cfgs.size());
+  std::vector<int> acfg;  // the Pick / Place configurations (one proposal row each)
+  for (size_t k = 0; k < cfgs.size(); ++k)
+    if (cfgs[k].kind != CK_KNOT) acfg.push_back(static_cast<int>(k));
+  pr.R = static_cast<int>(acfg.size());
   pr.pfeat.assign(static_cast<size_t>(pr.R) * PROP_NF, 0.f);
   pr.prow.assign(static_cast<size_t>(pr.R) * PROW_W, 0u);
   pr.prow_box.clear(); pr.prow_kind.clear(); pr.prow_off.clear(); pr.prow_surf.clear();
   for (int r = 0; r < pr.R; ++r) {
-    const Cfg& c = cfgs[r];
+    const Cfg& c = cfgs[acfg[r]];
     int sf = c.surf;
     if (c.kind == 0) {
       sf = -1;
@@ -545,6 +588,7 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
     rec[CF_CP_SLOT] = static_cast<uint32_t>(c.cp_slot);
     rec[CF_TCOS] = fbits(static_cast<float>(std::cos(static_cast<double>(c.tyaw))));
     rec[CF_TSIN] = fbits(static_cast<float>(std::sin(static_cast<double>(c.tyaw))));
+    rec[CF_HOLD] = static_cast<uint32_t>(c.hold);
     v.insert(v.end(), rec, rec + CFG_W);
     env_count += static_cast<int>(c.env.size());
   }
@@ -575,7 +619,8 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
     v.push_back(static_cast<uint32_t>(t.kind));
     v.push_back(fbits(opt.w[t.kind]));
     v.push_back(fbits(opt.tol[t.kind]));
-    v.push_back(t.kind == TK_OBJ_DIST ? static_cast<uint32_t>(-1) : static_cast<uint32_t>(ncon++));
+    const bool cost = t.kind == TK_OBJ_DIST || t.kind == TK_TRAJ_LEN;  // costs never constrain (Eq. 3)
+    v.push_back(cost ? static_cast<uint32_t>(-1) : static_cast<uint32_t>(ncon++));
     pr.term_kinds.push_back(t.kind);
   }
   pr.NCON = ncon;
@@ -612,6 +657,16 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
   }
   if (slots.empty())
     for (int i = 0; i < SLOT_W; ++i) v.push_back(0);
+  align4(v);
+  v[PH_OFF_SEG] = static_cast<uint32_t>(v.size());
+  v[PH_NSEG] = static_cast<uint32_t>(segs.size());
+  pr.n_seg = static_cast<int>(segs.size());
+  for (const Seg& sg : segs) {
+    const uint32_t rec[SEG_W] = {static_cast<uint32_t>(sg.qa), static_cast<uint32_t>(sg.qb),
+                                 static_cast<uint32_t>(sg.qk), static_cast<uint32_t>(sg.m),
+                                 static_cast<uint32_t>(sg.t), 0, 0, 0};
+    v.insert(v.end(), rec, rec + SEG_W);
+  }
   align4(v);
   // the sampler's records last: the optimisation kernel stages the words before them
   v[PH_OFF_SAMP] = static_cast<uint32_t>(v.size());
@@ -696,6 +751,7 @@ struct Job {
 struct Plan {
   int L = 1, warps = 1, grid = 0;
   bool mv_global = false;  // Adam moments in global memory: the tile fits shared memory only that way
+  bool knots = false;      // some problem has trajectory knots
   size_t smem = 0;
   std::vector<ProbDesc> descs;
   std::vector<uint32_t> items;
@@ -765,6 +821,8 @@ tamp_status plan_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lanes
   plan->warps = warps;
   plan->smem = smem;
   plan->mv_global = mvg;
+  plan->knots = false;
+  for (const Job& j : jobs) plan->knots = plan->knots || j.pr->n_seg > 0;
   const int per_sm = std::max(1, optimize_blocks_per_sm(L, warps, smem));
   plan->grid = std::min(static_cast<int>(plan->items.size()), s->sm_count * per_sm);
   return TAMP_OK;
@@ -781,6 +839,7 @@ LaunchArgs plan_args(const tamp_scene* s, const Plan& plan, ProbDesc* d_descs, u
   a.err = s->d_err;
   a.scratch_offset = static_cast<int>(plan.smem - optimize_scratch_bytes(plan.warps));
   a.mv_global = plan.mv_global ? 1 : 0;
+  a.knots = plan.knots ? 1 : 0;
   return a;
 }
 
@@ -868,8 +927,8 @@ extern "C" {
 void tamp_default_options(tamp_options* o) {
   if (!o) return;
   std::memset(o, 0, sizeof *o);
-  const float w[TAMP_N_TERM_KINDS] = {1.f, 5.f, 1.f, 2.f, 1.f, 1.f, 1.f, 0.25f};
-  const float tol[TAMP_N_TERM_KINDS] = {5e-3f, 0.05f, 1e-3f, 1e-3f, 1e-3f, 1e-3f, 0.f, INFINITY};
+  const float w[TAMP_N_TERM_KINDS] = {1.f, 5.f, 1.f, 2.f, 1.f, 1.f, 1.f, 0.25f, 1.f, 0.01f};
+  const float tol[TAMP_N_TERM_KINDS] = {5e-3f, 0.05f, 1e-3f, 1e-3f, 1e-3f, 1e-3f, 0.f, INFINITY, 1e-3f, INFINITY};
   for (int i = 0; i < TAMP_N_TERM_KINDS; ++i) {
     o->w[i] = w[i];
     o->tol[i] = tol[i];
@@ -1068,6 +1127,8 @@ static tamp_status sample_batch(tamp_scene* s, Problem* pr, int P, uint64_t seed
     CUDA_TRY(s, launch_ik(pr->d_blob, s->d_blob, pr->d_x, P, P, TAMP_IK_ITERS, TAMP_IK_DAMPING, TAMP_IK_MAX_STEP,
                           pr->d_chains, pr->n_chain, 1 + pr->K, keep, s->stream));
   }
+  // knots on the joint-space line between their motion's ends (Sec. VIII)
+  CUDA_TRY(s, launch_knots(pr->d_blob, pr->d_x, P, P, pr->n_seg, s->nj, keep, s->stream));
   return TAMP_OK;
 }
 
@@ -1624,6 +1685,7 @@ extern "C" tamp_status tamp_eval_static_scratch(tamp_scene* s, int id, int n, co
   a.item_counter = reinterpret_cast<int*>(scratch + kStaticCounterOff);
   a.err = s->d_err;
   a.scratch_offset = static_cast<int>(smem - optimize_scratch_bytes(warps));
+  a.knots = pr->n_seg > 0 ? 1 : 0;
   const int per_sm = std::max(1, optimize_blocks_per_sm(L, warps, smem));
   CUDA_TRY(s, launch_optimize(a, L, warps, std::min(tiles, s->sm_count * per_sm), smem, s->stream));
   return TAMP_OK;

@@ -13,7 +13,7 @@ constexpr int MAX_NBS = 8;     // spheres per box model
 constexpr int MAX_BOX = 32;
 constexpr int MAX_OBS = 256;
 constexpr int MAX_SPH = 512;   // padded arm sphere table
-constexpr int MAX_CFG = 32;    // arm configurations per skeleton
+constexpr int MAX_CFG = 128;   // arm configurations per skeleton (knots included)
 constexpr int MAX_D = 1024;
 
 // ---- scene blob (32-bit words) ----------------------------------------------
@@ -45,9 +45,13 @@ constexpr int SURF_W = 8;
 // ---- problem blob ------------------------------------------------------------
 enum ProbHdr {
   PH_D = 0, PH_K, PH_NT, PH_NCON, PH_GOAL_T, PH_NGOAL, PH_OFF_CFG, PH_OFF_ENV, PH_OFF_TERMS,
-  PH_OFF_GOAL, PH_OFF_LR, PH_OFF_SAMP, PH_WORDS, PH_NSLOT, PH_OFF_SLOT, PH_HDR_WORDS = 16
+  PH_OFF_GOAL, PH_OFF_LR, PH_OFF_SAMP, PH_WORDS, PH_NSLOT, PH_OFF_SLOT, PH_NSEG, PH_OFF_SEG,
+  PH_HDR_WORDS = 20
 };
-constexpr int CFG_W = 28;
+// Configuration kinds: a Pick's, a Place's, or a knot of the trajectory
+// between two of them (MoveFree / MoveHold).
+enum CfgKind { CK_PICK = 0, CK_PLACE = 1, CK_KNOT = 2 };
+constexpr int CFG_W = 32;
 enum CfgField {
   CF_KIND = 0, CF_BOX, CF_QOFF, CF_GOFF, CF_TSRC, CF_SURF, CF_NENV, CF_ENVOFF,
   CF_T_KP, CF_T_KR, CF_T_X, CF_T_CF, CF_T_CP, CF_T_JL, CF_PSRC,
@@ -58,8 +62,14 @@ enum CfgField {
   CF_CP_T,                      // CFreePlace term index
   CF_T_SLOT,                    // placement slot of the Kin target if CF_TSRC >= 0, else -1
   CF_CP_SLOT,                   // placement slot of CF_CP_SRC (-1: none)
-  CF_TCOS, CF_TSIN              // floats: cos, sin of CF_TYAW
+  CF_TCOS, CF_TSIN,             // floats: cos, sin of CF_TYAW
+  CF_HOLD                       // 1: the hand holds box CF_BOX with the grasp at CF_GOFF (Pick, Place, MoveHold knot)
 };
+// Motion segments between consecutive Pick/Place configurations (only with
+// knots): q offsets of the start and end configurations, of the first knot
+// (the knots' q are consecutive), the number of knots, the TrajLength term.
+constexpr int SEG_W = 8;
+enum SegField { SG_QA = 0, SG_QB, SG_QK, SG_M, SG_T };
 // Per iteration the optimisation kernel tabulates, for every particle of its
 // tile, (cos, sin) of each configuration's joint angles (plus the joint
 // offsets) followed by its grasp yaw: K x (n_joints + 1) entries, so that the
@@ -84,7 +94,7 @@ constexpr int PROP_NF = 48, PROP_NT = 16;   // network inputs, target slots (out
 
 enum TermKind {
   TK_KIN_POS = 0, TK_KIN_ROT, TK_GRASP, TK_STABLE, TK_CFREE_HOLD, TK_CFREE_PLACE, TK_JOINT_LIMIT,
-  TK_OBJ_DIST, TK_N
+  TK_OBJ_DIST, TK_CFREE_TRAJ, TK_TRAJ_LEN, TK_N
 };
 
 // device error word bits
@@ -119,6 +129,7 @@ struct LaunchArgs {
   int scratch_offset;                 // bytes from the start of dynamic shared memory to the warp scratch
   const int* stop;                    // optional: a non-zero value makes the launch return at once
   int mv_global;                      // 1: Adam moments used in place in global memory (not staged)
+  int knots;                          // 1: some problem has trajectory knots (the kernel built for them runs)
 };
 constexpr int ITEM_TILE_BITS = 20;
 

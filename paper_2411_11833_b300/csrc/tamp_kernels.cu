@@ -425,7 +425,7 @@ __device__ __forceinline__ float bound_dist(const float (&v)[N], const float (&l
 //   phase 1  links (tip to base); the frame steps back to T_{l-1} after each
 //   phase 2  spheres fixed to the base (tail, cost only)
 //   phase 3  the placed box at P(p) (tail of a Place: CFreePlace)
-template <int L>
+template <int L, bool KN>
 __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __restrict__ pb, int k, int piece,
                             const float* __restrict__ X, float* G, float* Tm, const int* __restrict__ slots,
                             const float4* __restrict__ place, const float2* __restrict__ trig,
@@ -455,6 +455,9 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   const int cp_src = cf[CF_CP_SRC], cp_first = cf[CF_CP_FIRST], cp_count = cp_src >= 0 ? cf[CF_CP_COUNT] : 0;
   const float w_cp = cp_count > 0 ? tw(terms, cf[CF_CP_T]) : 0.f;
   const bool head = piece == 0, last = piece == NPIECE - 1;
+  // a trajectory knot: no Kin, no grasp / containment term; the held box only on a MoveHold
+  // (KN: the kernel is built for problems with knots; otherwise these are constants)
+  const bool knot = KN && kind == CK_KNOT, hold = !KN || cf[CF_HOLD] != 0;
   // links of each piece, so that sphere batches spread evenly: the head also
   // has the held box (2 batches), the tail the placed box (1)
   const int n_head = NPIECE == 2 ? nj / 2 : max(0, (nj + 3) / 3 - 2);       // links of the head
@@ -462,7 +465,7 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   const int top = head ? nj : (last ? n_tail : nj - n_head);                  // this piece's top link
   const int lo = head ? nj - n_head + 1 : (last ? 1 : n_tail + 1);            // ... and bottom link
   // terms computed redundantly count on lane 0 only; Kin belongs to the head
-  const float k0 = (sub == 0 && head) ? 1.f : 0.f;
+  const float k0 = (sub == 0 && head && !knot) ? 1.f : 0.f;
 #define XV(c) X[(c) * PT + pl]
   // (cos, sin) of this configuration's joint angles, then of its grasp yaw
   const float2* tg = trig + k * (nj + 1) * PT + pl;
@@ -501,7 +504,7 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   float F[3] = {0.f, 0.f, 0.f}, Mw[3] = {0.f, 0.f, 0.f}, gg[4] = {0.f, 0.f, 0.f, 0.f}, gp[3] = {0.f, 0.f, 0.f};
   float e_pos = 0.f, e_rot = 0.f;
   float rgx = 0.f, rgy = 0.f;
-  if (head) {
+  if (head && !knot) {
     const float pz = cff[CF_TZ];
     if (tsrc < 0) {
       px = cff[CF_TX]; py = cff[CF_TY]; cy = cff[CF_TCOS]; sy = cff[CF_TSIN];
@@ -556,6 +559,10 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
     gp[0] = k0 * (-fkx);
     gp[1] = k0 * (-fky);
     gp[2] = k0 * (fkx * rgy - fky * rgx + ubz);
+  } else if (head && hold) {  // a MoveHold knot: the held box's grasp
+    gxv = XV(go); gyv = XV(go + 1); gzv = XV(go + 2);
+    const float2 gcs = TG(nj);
+    cgr = gcs.x; sgr = gcs.y;
   }
   float J_hold = 0.f, J_place = 0.f;
   float gpc[3] = {0.f, 0.f, 0.f};  // Kin target / containment -> this configuration's placement
@@ -569,7 +576,7 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   // a piece without links of its own below the end effector (the tail of a
   // very short arm) starts at the base spheres
   int phase = head ? 0 : (top >= 1 ? 1 : 2), l = top;
-  int s0 = head ? 0 : sc[SH_LINK0 + top], s1 = head ? nbs_pad : sc[SH_LINK0 + top + 1];
+  int s0 = head ? 0 : sc[SH_LINK0 + top], s1 = head ? (hold ? nbs_pad : 0) : sc[SH_LINK0 + top + 1];
   if (!head && top < lo && !(last && top == 0)) s0 = s1 = 0;
   for (;;) {
     if (s0 >= s1) {
@@ -760,11 +767,18 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
       }
     }
   }
+  Tm[cf[CF_T_JL] * PT + pl] = jl;
+  if (knot) {
+    // a MoveHold knot's held-box collisions move the grasp
+    if (hold)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) atomicAdd(&G[(go + i) * PT + pl], gg[i]);
+    return;
+  }
   Tm[cf[CF_T_KP] * PT + pl] = e_pos;
   Tm[cf[CF_T_KR] * PT + pl] = e_rot;
-  Tm[cf[CF_T_JL] * PT + pl] = jl;
   const float* br = boxr + b * BOX_W;
-  if (kind == 0) {
+  if (kind == CK_PICK) {
     // Grasp(o, g): bound distance of g_xyz to [-hx, hx] x [-hy, hy] x [hz - 0.02, hz]
     const float v[3] = {gxv, gyv, gzv};
     const float lo[3] = {-br[0], -br[1], br[2] - 0.02f};
@@ -852,11 +866,51 @@ __device__ void eval_goal(const uint32_t* __restrict__ sc, const uint32_t* __res
   Tm[gt * PT + pl] = J;
 }
 
+// TrajLength of every motion (Listing 1 MoveFree / MoveHold cost): the
+// joint-space length sum_e ||w_{e+1} - w_e|| of the polyline start, knots, end,
+// for one particle, with its gradient.
+template <int L>
+__device__ void eval_traj(const uint32_t* __restrict__ pb, const float* __restrict__ X, float* G, float* Tm, int nj,
+                          int pl) {
+  constexpr int PT = 32 / L;
+  const int ns = pb[PH_NSEG];
+  const uint32_t* seg = pb + pb[PH_OFF_SEG];
+  const uint32_t* terms = pb + pb[PH_OFF_TERMS];
+  for (int si = 0; si < ns; ++si) {
+    const uint32_t* r = seg + si * SEG_W;
+    const int qa = r[SG_QA], qb = r[SG_QB], qk = r[SG_QK], m = r[SG_M], t = r[SG_T];
+    const float wt = tw(terms, t);
+    float J = 0.f;
+    for (int e = 0; e <= m; ++e) {
+      const int o0 = e == 0 ? qa : qk + (e - 1) * nj;
+      const int o1 = e == m ? qb : qk + e * nj;
+      float d[MAXJ], d2 = 0.f;
+#pragma unroll
+      for (int j = 0; j < MAXJ; ++j) {
+        d[j] = j < nj ? X[(o1 + j) * PT + pl] - X[(o0 + j) * PT + pl] : 0.f;
+        d2 = fmaf(d[j], d[j], d2);
+      }
+      const float len = sqrtf(d2);
+      J += len;
+      if (len > 0.f) {
+        const float inv = wt / len;
+#pragma unroll
+        for (int j = 0; j < MAXJ; ++j)
+          if (j < nj) {
+            atomicAdd(&G[(o1 + j) * PT + pl], inv * d[j]);
+            atomicAdd(&G[(o0 + j) * PT + pl], -inv * d[j]);
+          }
+      }
+    }
+    Tm[t * PT + pl] = J;
+  }
+}
+
 // ------------------------------------------------------------------ fused optimisation kernel
 // One tile of PT particles of one problem: load it, run n_steps fused
 // iterations (evaluation + adjoint, Eq. 3 check, Adam) and one final check,
 // write it back.  All threads of the CTA call this together.
-template <int L>
+template <int L, bool KN>
 __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, const uint32_t* s_pb, float* tile_mem,
                          const WarpScratch& ws, bool mv_global) {
   constexpr int PT = 32 / L;
@@ -913,7 +967,8 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
   // configurations first (their environments hold more placed boxes), then the
   // goal cost; warps pull them from a counter so that they finish together
   __shared__ int s_next;
-  const int n_work = NPIECE * K + (s_pb[PH_GOAL_T] != 0xffffffffu ? 1 : 0);
+  const bool has_goal = s_pb[PH_GOAL_T] != 0xffffffffu, has_traj = KN && s_pb[PH_NSEG] != 0;
+  const int n_work = NPIECE * K + (has_goal ? 1 : 0) + (has_traj ? 1 : 0);
   double b1t = pow(static_cast<double>(d.beta1), t0), b2t = pow(static_cast<double>(d.beta2), t0);
   unsigned n_obb = 0, n_box = 0;  // broad-phase candidates resolved exactly (work accounting)
 
@@ -944,10 +999,14 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
       item = __shfl_sync(0xffffffffu, item, 0);
       if (item >= n_work) break;
       if (item < NPIECE * K)
-        eval_config<L>(s_sc, s_pb, K - 1 - item / NPIECE, item % NPIECE, sx, sg, st, slots, splace, strig, ws, n_obb,
+        eval_config<L, KN>(s_sc, s_pb, K - 1 - item / NPIECE, item % NPIECE, sx, sg, st, slots, splace, strig, ws, n_obb,
                        n_box, lane, pl, sub);
-      else if (sub == 0)
-        eval_goal<L>(s_sc, s_pb, sx, sg, st, pl);
+      else if (sub == 0) {
+        if (has_goal && item == NPIECE * K)
+          eval_goal<L>(s_sc, s_pb, sx, sg, st, pl);
+        else if constexpr (KN)
+          eval_traj<L>(s_pb, sx, sg, st, nj, pl);
+      }
     }
     __syncthreads();
     // Eq. 3 at x_t
@@ -1054,7 +1113,7 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
 // skeletons first, as the host orders them -- staging a problem's tables
 // whenever it moves to a new problem.  Many skeletons of uneven length and
 // particle count thus share one launch and balance across the SMs.
-template <int L>
+template <int L, bool KN>
 __global__ void __launch_bounds__(512, 1) optimize_kernel(LaunchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
@@ -1122,7 +1181,7 @@ __global__ void __launch_bounds__(512, 1) optimize_kernel(LaunchArgs a) {
       __syncthreads();
       if (abort_flag) return;
     }
-    run_tile<L>(d, tile, s_sc, s_pb, reinterpret_cast<float*>(s_pb + pw), ws, a.mv_global != 0);
+    run_tile<L, KN>(d, tile, s_sc, s_pb, reinterpret_cast<float*>(s_pb + pw), ws, a.mv_global != 0);
     __syncthreads();  // everyone has read s_item and the tables before they change
   }
 }
@@ -1409,6 +1468,33 @@ cudaError_t launch_ik(const uint32_t* pb, const uint32_t* sc, float* x, int stri
   return cudaGetLastError();
 }
 
+// Knot initialisation (Sec. VIII: linear interpolation between a motion's start
+// and end configurations): one thread per (particle, motion); knots of a
+// motion inside a kept prefix (components below `keep`) stay as they are.
+__global__ void knots_kernel(const uint32_t* __restrict__ pb, float* __restrict__ x, int stride, int P, int nj,
+                             int keep) {
+  const long g = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int ns = pb[PH_NSEG];
+  if (g >= static_cast<long>(P) * ns) return;
+  const int i = static_cast<int>(g % P);
+  const uint32_t* r = pb + pb[PH_OFF_SEG] + static_cast<int>(g / P) * SEG_W;
+  const int qa = r[SG_QA], qb = r[SG_QB], qk = r[SG_QK], m = r[SG_M];
+  if (qk < keep) return;
+  for (int j = 0; j < nj; ++j) {
+    const float a = x[static_cast<long>(qa + j) * stride + i], b = x[static_cast<long>(qb + j) * stride + i];
+    for (int k = 0; k < m; ++k)
+      x[static_cast<long>(qk + k * nj + j) * stride + i] = fmaf(static_cast<float>(k + 1) / (m + 1), b - a, a);
+  }
+}
+
+cudaError_t launch_knots(const uint32_t* pb, float* x, int stride, int P, int n_seg, int nj, int keep,
+                         cudaStream_t st) {
+  if (P == 0 || n_seg == 0) return cudaSuccess;
+  const long threads = static_cast<long>(P) * n_seg;
+  knots_kernel<<<static_cast<unsigned>((threads + 127) / 128), 128, 0, st>>>(pb, x, stride, P, nj, keep);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ FP32 peak probe
 // Measurement utility (not part of the method): independent FFMA chains, 8 per
 // thread, enough warps to fill every SM, so the FP32 pipes are the only limit.
@@ -1459,20 +1545,29 @@ cudaError_t launch_chunk_control(int* t_dev, const int* const* first_iters, int 
 
 // ------------------------------------------------------------------ launchers
 // largest dynamic shared-memory size enabled so far for optimize_kernel<1,2,4,8>
-static size_t g_smem_enabled[4] = {0, 0, 0, 0};
+// without and with knot support
+static size_t g_smem_enabled[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
 static int lane_slot(int L) { return L == 1 ? 0 : (L == 2 ? 1 : (L == 4 ? 2 : 3)); }
+
+template <int L, bool KN>
+static cudaError_t set_smem(size_t smem) {
+  size_t& enabled = g_smem_enabled[KN ? 1 : 0][lane_slot(L)];
+  if (smem <= 48 * 1024 || smem <= enabled) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(optimize_kernel<L, KN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e == cudaSuccess) enabled = smem;
+  return e;
+}
 
 template <int L>
 static cudaError_t launch_opt(const LaunchArgs& a, int warps, int grid, size_t smem, cudaStream_t st) {
-  size_t& enabled = g_smem_enabled[lane_slot(L)];
-  if (smem > 48 * 1024 && smem > enabled) {
-    cudaError_t e = cudaFuncSetAttribute(optimize_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    enabled = smem;
-  }
+  cudaError_t e = a.knots ? set_smem<L, true>(smem) : set_smem<L, false>(smem);
+  if (e != cudaSuccess) return e;
   if (grid <= 0) return cudaSuccess;
-  optimize_kernel<L><<<grid, warps * 32, smem, st>>>(a);
+  if (a.knots)
+    optimize_kernel<L, true><<<grid, warps * 32, smem, st>>>(a);
+  else
+    optimize_kernel<L, false><<<grid, warps * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1480,30 +1575,36 @@ int optimize_blocks_per_sm(int L, int warps, size_t smem) {
   int n = 0;
   cudaError_t e = cudaSuccess;
   switch (L) {
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<1>, warps * 32, smem); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<2>, warps * 32, smem); break;
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<4>, warps * 32, smem); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<8>, warps * 32, smem); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<1, false>, warps * 32, smem); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<2, false>, warps * 32, smem); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<4, false>, warps * 32, smem); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<8, false>, warps * 32, smem); break;
   }
   return e == cudaSuccess ? n : 1;
 }
 
-// Allow `smem` bytes of dynamic shared memory for optimize_kernel<L> (outside
+// Allow `smem` bytes of dynamic shared memory for optimize_kernel<L, *> (outside
 // any stream capture).
 cudaError_t optimize_set_smem(int L, size_t smem) {
-  size_t& enabled = g_smem_enabled[lane_slot(L)];
-  if (smem <= 48 * 1024 || smem <= enabled) return cudaSuccess;
-  const int v = static_cast<int>(smem);
-  cudaError_t e = cudaErrorInvalidValue;
   switch (L) {
-    case 1: e = cudaFuncSetAttribute(optimize_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, v); break;
-    case 2: e = cudaFuncSetAttribute(optimize_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, v); break;
-    case 4: e = cudaFuncSetAttribute(optimize_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, v); break;
-    case 8: e = cudaFuncSetAttribute(optimize_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, v); break;
-    default: break;
+    case 1: {
+      cudaError_t e = set_smem<1, false>(smem);
+      return e != cudaSuccess ? e : set_smem<1, true>(smem);
+    }
+    case 2: {
+      cudaError_t e = set_smem<2, false>(smem);
+      return e != cudaSuccess ? e : set_smem<2, true>(smem);
+    }
+    case 4: {
+      cudaError_t e = set_smem<4, false>(smem);
+      return e != cudaSuccess ? e : set_smem<4, true>(smem);
+    }
+    case 8: {
+      cudaError_t e = set_smem<8, false>(smem);
+      return e != cudaSuccess ? e : set_smem<8, true>(smem);
+    }
+    default: return cudaErrorInvalidValue;
   }
-  if (e == cudaSuccess) enabled = smem;
-  return e;
 }
 
 cudaError_t launch_optimize(const LaunchArgs& a, int L, int warps, int grid, size_t smem, cudaStream_t st) {

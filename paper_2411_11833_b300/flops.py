@@ -28,6 +28,12 @@ Data-dependent work (counted by the kernel, tamp_work_counters):
   exact sphere pair             11 FLOP per (batch sphere, box sphere) of a candidate
 Per iteration and particle: 12 FLOP per sphere of every box on a placement
 variable (its world centre), 12 FLOP per Adam component.
+
+Trajectory knots (n_knots per motion between consecutive Pick/Place
+configurations) are configurations without Kin: the arm, plus the held box on
+a MoveHold, against the cuboids and every box not in the hand; each motion
+adds TrajLength, 3n + 1 FLOP per polyline edge (difference, square sum, add)
+and 2n per edge for its gradient.
 """
 from __future__ import annotations
 
@@ -49,18 +55,28 @@ ADAM = 12
 NB = 5
 
 
-def _walk(scene, actions):
-    """(kind, box, n_env) per configuration; a Place's CFreePlace spheres are
-    split with the Pick before it."""
+def _walk(scene, actions, n_knots: int = 0):
+    """(kind, box, n_env, held) per configuration (kind 2: a knot; held: it
+    carries a held box's spheres).  A Place's CFreePlace spheres are split with
+    the Pick right before it."""
     B = scene.box_half.shape[0]
     out = []
+    holding = False
     for kind, b, _s in actions:
-        if kind in (0, 1):
-            out.append((kind, b, B - 1))
+        if kind not in (0, 1):
+            continue
+        if n_knots and out:
+            out += [(2, -1, B - 1 if holding else B, holding)] * n_knots
+        out.append((kind, b, B - 1, True))
+        holding = kind == 0
     return out
 
 
-def eval_flops(scene, actions) -> int:
+def _motions(actions, n_knots: int) -> int:
+    return max(0, sum(1 for a in actions if a[0] in (0, 1)) - 1) if n_knots else 0
+
+
+def eval_flops(scene, actions, n_knots: int = 0) -> int:
     """Fixed FLOP of one evaluation (cost + gradient) of one particle."""
     n = scene.dh_a.shape[0]
     links = list(scene.sphere_link)
@@ -68,12 +84,14 @@ def eval_flops(scene, actions) -> int:
     arm_batches = sum(int(math.ceil(links.count(l) / NB)) for l in range(n + 1))
     nbs = scene.box_spheres.shape[1]
     O = scene.obs_center.shape[0]
-    cfgs = _walk(scene, actions)
+    cfgs = _walk(scene, actions, n_knots)
     total = 0
     n_place = 0
-    for i, (kind, b, n_env) in enumerate(cfgs):
-        held_batches = int(math.ceil(nbs / NB))
-        if kind == 1:
+    for i, (kind, b, n_env, held) in enumerate(cfgs):
+        held_batches = int(math.ceil(nbs / NB)) if held else 0
+        if kind == 2:
+            cp = 0
+        elif kind == 1:
             half = nbs // 2 if i > 0 and cfgs[i - 1][0] == 0 and cfgs[i - 1][1] == b else 0
             cp = nbs - half
             n_place += 1
@@ -82,12 +100,13 @@ def eval_flops(scene, actions) -> int:
             cp = nbs // 2 if nxt is not None and nxt[0] == 1 and nxt[1] == b else 0
         place_batches = int(math.ceil(cp / NB))
         batches = arm_batches + held_batches + place_batches
-        sph = S + nbs + cp
+        sph = S + (nbs if held else 0) + cp
         total += n * (FK_JOINT + SWEEP_JOINT)
-        total += sph * (SPHERE_XFORM + SPHERE_WRENCH) + nbs * HELD_SPHERE
+        total += sph * (SPHERE_XFORM + SPHERE_WRENCH) + (nbs * HELD_SPHERE if held else 0)
         total += arm_batches * ARM_BOUND + (held_batches + place_batches) * BOX_BOUND
         total += batches * (O * BROAD_OBB + n_env * BROAD_BOX)
     total += n_place * nbs * ENV_SPHERE
+    total += _motions(actions, n_knots) * (n_knots + 1) * 5 * n
     return total
 
 
@@ -96,22 +115,20 @@ def exact_flops(n_obb: int, n_box: int, nbs: int) -> int:
     return n_obb * NB * EXACT_OBB_SPHERE + n_box * NB * nbs * EXACT_PAIR
 
 
-def algorithmic_flops(scene, actions) -> int:
+def algorithmic_flops(scene, actions, n_knots: int = 0) -> int:
     """All-pairs FLOP of one particle-iteration (evaluation, adjoint sweep, Adam)."""
     n = scene.dh_a.shape[0]
     S = len(scene.sphere_link)
     nbs = scene.box_spheres.shape[1]
     O = scene.obs_center.shape[0]
-    B = scene.box_half.shape[0]
     total, D = 0, 0
-    for kind, _b, _s in actions:
-        if kind not in (0, 1):
-            continue
-        D += (4 if kind == 0 else 3) + n
-        own = S + nbs                                  # arm + held box
-        total += n * 60 + own * 18 + own * O * 32 + own * nbs * (B - 1) * 10 + n * 80
+    for kind, _b, n_env, held in _walk(scene, actions, n_knots):
+        D += (4 if kind == 0 else (3 if kind == 1 else 0)) + n
+        own = S + (nbs if held else 0)                 # arm (+ held box)
+        total += n * 60 + own * 18 + own * O * 32 + own * nbs * n_env * 10 + n * 80
         if kind == 1:                                  # CFreePlace: the placed box
-            total += nbs * 18 + nbs * O * 32 + nbs * nbs * (B - 1) * 10
+            total += nbs * 18 + nbs * O * 32 + nbs * nbs * n_env * 10
+    total += _motions(actions, n_knots) * (n_knots + 1) * 5 * n
     return total + 12 * D
 
 

@@ -48,12 +48,12 @@ def plan_heuristic(counts, lambda_penalty: float) -> float:
 
 
 PICK, PLACE, GOAL = 0, 1, 2
-_OBJ_DIST = 7                                 # the goal term kind: never a constraint
-_COLLISION_KINDS = (4, 5)                     # CFreeHold, CFreePlace
+_COSTS = (7, 9)                               # MinimizeObjDist, TrajLength: never constraints
+_COLLISION_KINDS = (4, 5, 8)                  # CFreeHold, CFreePlace, CFreeTraj
 
 
 def constraint_signatures(actions, term_kinds, term_actions):
-    """For every constraint of a skeleton (its terms other than the goal cost,
+    """For every constraint of a skeleton (its terms other than the costs,
     in constraint order), a hashable name of its constraint subgraph (Sec.
     VII): the term kind, the action (kind, box, surface), where the acted-on
     box stands before the action (initial pose, or on the surface an earlier
@@ -70,7 +70,7 @@ def constraint_signatures(actions, term_kinds, term_actions):
             state[box] = ("on", surface)
     sigs = []
     for k, a in zip(term_kinds, term_actions):
-        if k == _OBJ_DIST:
+        if k in _COSTS:
             continue
         kind, box, surface = acts[a]
         st = before[a]
@@ -145,7 +145,7 @@ class _Candidates:
     def _compile(self, actions):
         pid = self.be.compile(actions, self.options)
         kinds, acts = self.be.terms(pid)
-        return pid, constraint_signatures(actions, kinds, acts), [a for k, a in zip(kinds, acts) if k != _OBJ_DIST]
+        return pid, constraint_signatures(actions, kinds, acts), [a for k, a in zip(kinds, acts) if k not in _COSTS]
 
     def initialise(self, i):
         """Compile and sample skeleton i and check its particles; None if a
