@@ -23,6 +23,11 @@ interpolation between the start and end configurations):
   MoveHold(o, g, q1, q2, tau)  con: Motion, CFreeTrajHold(o, g, tau)
                                cost: TrajLength(tau)
 
+With self_collision on, every configuration (knots included) also carries
+SelfCollision: the CFree constraints' "does not cause robot self-collisions"
+(appendix constraint definitions), tolerance 0 penetration (appendix
+constraint tolerances).
+
 The particle layout (Pick: grasp x,y,z,yaw then q; Place: placement x,y,yaw
 then q) is the interface documented in include/tamp.h.
 
@@ -46,7 +51,12 @@ Readings of points the paper leaves open (each one is listed in the design doc):
     also the box about to be picked) -- checked at the knots only; TrajLength
     is the joint-space length sum_i ||w_{i+1} - w_i|| of the polyline q1,
     knots, q2; there is no motion before the first action (the scene has no
-    initial configuration).
+    initial configuration);
+  * SelfCollision: the summed penetration max(0, r_a + r_b - ||c_a - c_b||)
+    over the arm's sphere pairs of links i > j + 1 whose spheres do not
+    already overlap at q = 0 (links that always touch are not a collision,
+    like a robot's self-collision ignore list), plus the held box's spheres
+    against links 0..n-2 (not the wrist and gripper that hold it).
 """
 from __future__ import annotations
 
@@ -64,9 +74,9 @@ KNOT = 2                                     # configuration kind of a trajector
 
 # term kinds (include/tamp.h: tamp_term_kind)
 (KIN_POS, KIN_ROT, GRASP, STABLE_PLACE, CFREE_HOLD, CFREE_PLACE, JOINT_LIMIT, OBJ_DIST, CFREE_TRAJ,
- TRAJ_LEN) = range(10)
+ TRAJ_LEN, SELF_COLLISION) = range(11)
 TERM_NAMES = ["kin_pos", "kin_rot", "grasp", "stable_place", "cfree_hold", "cfree_place",
-              "joint_limit", "obj_dist", "cfree_traj", "traj_len"]
+              "joint_limit", "obj_dist", "cfree_traj", "traj_len", "self_collision"]
 COST_KINDS = (OBJ_DIST, TRAJ_LEN)            # costs, never constraints (Eq. 3)
 
 
@@ -80,12 +90,15 @@ class Options:
     "Constraint Tolerances"): world collisions 1 mm, kinematics 5 mm / 0.05 rad,
     joint limits 0, containment 1 mm; grasp bounds 1 mm (reading).  Knots:
     CFreeTraj as the other collisions (1.0, 1 mm); TrajLength 0.01 per radian
-    of joint-space path (reading: the paper gives no weight).
+    of joint-space path (reading: the paper gives no weight).  Self-collision:
+    weight 1.0, tolerance 0 (appendix "Constraint Tolerances").
     """
 
-    w: list = field(default_factory=lambda: [1.0, 5.0, 1.0, 2.0, 1.0, 1.0, 1.0, 0.25, 1.0, 0.01])
-    tol: list = field(default_factory=lambda: [5e-3, 0.05, 1e-3, 1e-3, 1e-3, 1e-3, 0.0, math.inf, 1e-3, math.inf])
+    w: list = field(default_factory=lambda: [1.0, 5.0, 1.0, 2.0, 1.0, 1.0, 1.0, 0.25, 1.0, 0.01, 1.0])
+    tol: list = field(default_factory=lambda: [5e-3, 0.05, 1e-3, 1e-3, 1e-3, 1e-3, 0.0, math.inf, 1e-3, math.inf,
+                                               0.0])
     n_knots: int = 0                        # knot configurations per motion between actions
+    self_collision: bool = False            # SelfCollision term on every configuration
     lr_joint: float = 1e-2
     lr_pos: float = 3e-3
     lr_yaw: float = 1e-2
@@ -114,7 +127,32 @@ class Problem:
         self.actions = [tuple(int(v) for v in a) for a in actions]
         self.arm = dict(base=scene.base, tool=scene.tool, dh_a=scene.dh_a, dh_d=scene.dh_d,
                         dh_alpha=scene.dh_alpha, dh_offset=scene.dh_offset)
+        self._self_pairs()
         self._walk()
+
+    def _self_pairs(self):
+        """Which link pairs SelfCollision tests: links i > j + 1 whose spheres
+        do not overlap at q = 0; and the arm spheres the held box is tested
+        against (links 0..n-2).  ``self.self_mask`` [S, S] marks the sphere
+        pairs (a on the higher link), ``self.held_mask`` [S] the arm spheres."""
+        sc, n = self.sc, self.n
+        links = np.asarray(sc.sphere_link)
+        S = links.size
+        frames = G.forward_kinematics(self.arm, torch.zeros(1, n, dtype=DT))
+        c0 = G.apply(frames[:, torch.as_tensor(links, dtype=torch.long)],
+                     torch.as_tensor(sc.sphere_xyzr[:, :3], dtype=DT))[0].numpy()
+        r = np.asarray(sc.sphere_xyzr[:, 3], dtype=np.float64)
+        touch = np.linalg.norm(c0[:, None, :] - c0[None, :, :], axis=-1) < r[:, None] + r[None, :]
+        self.self_links = set()
+        for i in range(n + 1):
+            for j in range(i - 1):
+                if (links == i).any() and (links == j).any() and not touch[np.ix_(links == i, links == j)].any():
+                    self.self_links.add((i, j))
+        self.self_mask = np.zeros((S, S), dtype=bool)
+        for a in range(S):
+            for b in range(S):
+                self.self_mask[a, b] = (int(links[a]), int(links[b])) in self.self_links
+        self.held_mask = links <= n - 2
 
     # -------------------------------------------------------------- skeleton walk
     def _walk(self):
@@ -143,7 +181,7 @@ class Problem:
                                              g_off=held[1] if held is not None else -1, env=env))
                     ci = len(self.configs) - 1
                     knots.append(ci)
-                    for k in (CFREE_TRAJ, JOINT_LIMIT):
+                    for k in (CFREE_TRAJ, JOINT_LIMIT) + ((SELF_COLLISION,) if self.opts.self_collision else ()):
                         self.terms.append(Term(k, ai, hb, ci))
                 prev = max(c for c, cf in enumerate(self.configs) if cf["kind"] != KNOT)
                 self.terms.append(Term(TRAJ_LEN, ai, -1, len(self.segments)))
@@ -164,7 +202,8 @@ class Problem:
                            target=pose[b], env=env)
                 self.configs.append(cfg)
                 ci = len(self.configs) - 1
-                for k in (KIN_POS, KIN_ROT, GRASP, CFREE_HOLD, JOINT_LIMIT):
+                for k in (KIN_POS, KIN_ROT, GRASP, CFREE_HOLD, JOINT_LIMIT) + \
+                        ((SELF_COLLISION,) if self.opts.self_collision else ()):
                     self.terms.append(Term(k, ai, b, ci))
                 held = (b, g_off)
                 pose[b] = ("held",)
@@ -184,7 +223,8 @@ class Problem:
                            target=("var", p_off, s), env=env)
                 self.configs.append(cfg)
                 ci = len(self.configs) - 1
-                for k in (KIN_POS, KIN_ROT, STABLE_PLACE, CFREE_HOLD, CFREE_PLACE, JOINT_LIMIT):
+                for k in (KIN_POS, KIN_ROT, STABLE_PLACE, CFREE_HOLD, CFREE_PLACE, JOINT_LIMIT) + \
+                        ((SELF_COLLISION,) if self.opts.self_collision else ()):
                     self.terms.append(Term(k, ai, b, ci))
                 pose[b] = ("var", p_off, s)
                 held = None
@@ -253,7 +293,8 @@ class Problem:
                     held_c, held_r = self._box_spheres(cfg["box"], ee @ G.rigid_inverse(Gp))
                     c_all = torch.cat([c_all, held_c], dim=1)
                     r_all = torch.cat([arm_r, held_r])
-                per_cfg[ci] = {CFREE_TRAJ: self._env_penetration(c_all, r_all, cfg["env"], x), JOINT_LIMIT: jl}
+                per_cfg[ci] = {CFREE_TRAJ: self._env_penetration(c_all, r_all, cfg["env"], x), JOINT_LIMIT: jl,
+                               SELF_COLLISION: self._self_penetration(c_all, r_all)}
                 continue
             g = x[:, cfg["g_off"]:cfg["g_off"] + 4]
             Gp = G.grasp_pose(g[:, 0], g[:, 1], g[:, 2], g[:, 3])
@@ -266,7 +307,8 @@ class Problem:
             c_all = torch.cat([arm_world, held_c], dim=1)
             r_all = torch.cat([arm_r, held_r])
             cfree_hold = self._env_penetration(c_all, r_all, cfg["env"], x)
-            vals = {KIN_POS: e_pos, KIN_ROT: e_rot, CFREE_HOLD: cfree_hold, JOINT_LIMIT: jl}
+            vals = {KIN_POS: e_pos, KIN_ROT: e_rot, CFREE_HOLD: cfree_hold, JOINT_LIMIT: jl,
+                    SELF_COLLISION: self._self_penetration(c_all, r_all)}
             if cfg["kind"] == PICK:
                 h = torch.as_tensor(sc.box_half[b], dtype=DT)
                 lo = torch.stack([-h[0], -h[1], h[2] - 0.02])
@@ -288,6 +330,18 @@ class Problem:
             else:
                 out[ti] = per_cfg[t.cfg][t.kind]
         return torch.stack(out, dim=1) if out else torch.zeros(P, 0, dtype=DT)
+
+    def _self_penetration(self, c, r):
+        """SelfCollision of arm spheres c[:, :S] (then the held box's, if any)."""
+        S = self.self_mask.shape[0]
+        ca, ra = c[:, :S], r[:S]
+        pen = G.sphere_sphere_penetration(ca.unsqueeze(-2), ra.view(-1, 1), ca.unsqueeze(-3), ra.view(1, -1))
+        total = (pen * torch.as_tensor(self.self_mask, dtype=DT)).sum((-1, -2))
+        if c.shape[1] > S:
+            hc, hr = c[:, S:], r[S:]
+            pen = G.sphere_sphere_penetration(hc.unsqueeze(-2), hr.view(-1, 1), ca.unsqueeze(-3), ra.view(1, -1))
+            total = total + (pen * torch.as_tensor(self.held_mask, dtype=DT)).sum((-1, -2))
+        return total
 
     def _waypoints(self, seg, x):
         cs = [seg["start"]] + seg["knots"] + [seg["end"]]
@@ -454,6 +508,23 @@ class Problem:
         def bound_margins(v, lo, hi):
             return [(v - lo).abs().amin(-1), (v - hi).abs().amin(-1)]
 
+        def self_margins(c, r):
+            if not self.opts.self_collision:
+                return []
+            S = self.self_mask.shape[0]
+            out = []
+            for cb, rb, mask in ((c[:, :S], r[:S], self.self_mask),
+                                 (c[:, S:], r[S:], np.broadcast_to(self.held_mask, (c.shape[1] - S, S)))):
+                if cb.shape[1] == 0:
+                    continue
+                d = G.norm(cb.unsqueeze(-2) - c[:, :S].unsqueeze(-3))
+                gap = rb.view(-1, 1) + r[:S].view(1, -1) - d
+                m = torch.as_tensor(np.ascontiguousarray(mask))
+                inf = torch.full_like(d, math.inf)
+                out.append(torch.where(m, gap.abs(), inf).amin((-1, -2)))
+                out.append(torch.where(m & (gap > -1e-3), d, inf).amin((-1, -2)))
+            return out
+
         for seg in self.segments:
             w = self._waypoints(seg, x)
             ms += [G.norm(w[i + 1] - w[i]) for i in range(len(w) - 1)]
@@ -469,6 +540,7 @@ class Problem:
                     held_c, held_r = self._box_spheres(cfg["box"], ee @ G.rigid_inverse(Gp))
                     c_all, r_all = torch.cat([c_all, held_c], 1), torch.cat([arm_r, held_r])
                 ms += env_margins(c_all, r_all, cfg["env"])
+                ms += self_margins(c_all, r_all)
                 ms += bound_margins(q, lo_q, hi_q)
                 continue
             g = x[:, cfg["g_off"]:cfg["g_off"] + 4]
@@ -480,6 +552,7 @@ class Problem:
             arm_world = G.apply(frames[:, links], arm_c)
             held_c, held_r = self._box_spheres(b, ee @ G.rigid_inverse(Gp))
             ms += env_margins(torch.cat([arm_world, held_c], 1), torch.cat([arm_r, held_r]), cfg["env"])
+            ms += self_margins(torch.cat([arm_world, held_c], 1), torch.cat([arm_r, held_r]))
             ms += bound_margins(q, lo_q, hi_q)
             if cfg["kind"] == PICK:
                 h = self.sc.box_half[b]
