@@ -65,6 +65,8 @@ def parse():
                     help="packing (the headline line) or the stress scene (12 boxes, 64 cuboids, 100 spheres)")
     ap.add_argument("--knots", type=int, default=0,
                     help="trajectory knots per motion between actions (0: configurations only, the headline)")
+    ap.add_argument("--self-collision", action="store_true",
+                    help="every configuration also carries SelfCollision (not in the headline)")
     return ap.parse_args()
 
 
@@ -330,9 +332,12 @@ def main():
     if args.knots:
         workload += (f"; trajectories of {args.knots} knots per motion (MoveFree / MoveHold: CFreeTraj, joint "
                      "limits, TrajLength)")
+    if args.self_collision:
+        workload += "; SelfCollision on every configuration"
     with torch.cuda.stream(stream):
         scene = pkg.Scene(sc, device=local, stream=stream.cuda_stream)
-        pid = scene.set_skeleton(acts, pkg.default_options(lanes=args.lanes, n_knots=args.knots))
+        pid = scene.set_skeleton(acts, pkg.default_options(lanes=args.lanes, n_knots=args.knots,
+                                                           self_collision=int(args.self_collision)))
     D, NT, _ = scene.problem_info(pid)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     tuned = None
@@ -401,7 +406,8 @@ def main():
         return
     # roofline numerator: the method's all-pairs work (per-unit
     # figures, flops.algorithmic_flops) x particle-iterations of one launch
-    launch_flops = P * T * flops.algorithmic_flops(sc, acts, args.knots)
+    launch_flops = P * T * (flops.algorithmic_flops(sc, acts, args.knots)
+                            + (flops.self_collision_flops(sc, acts, args.knots) if args.self_collision else 0))
     executed = (P * ((T + 1) * flops.eval_flops(sc, acts, args.knots) + T * flops.adam_flops(D))
                 + flops.exact_flops(work[0], work[1], sc.box_spheres.shape[1]))
     kern_s = sum(kern_ms) / len(kern_ms) / 1e3
@@ -414,7 +420,7 @@ def main():
         probe = round(probe_tf.value, 2)
     achieved = launch_flops / kern_s / 1e12
     sha = kernel_source_sha()
-    headline = args.workload == "packing" and args.knots == 0
+    headline = args.workload == "packing" and args.knots == 0 and not args.self_collision
     traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["source_sha"] == sha and headline else None
     out = {
         "metric": METRIC, "value": value, "unit": "particle-iters/s", "n_gpus": world, "steps": args.steps,

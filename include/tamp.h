@@ -68,7 +68,8 @@ enum {
   TAMP_TERM_OBJ_DIST = 7,     /* MinimizeObjDist goal cost: sum of pairwise distances */
   TAMP_TERM_CFREE_TRAJ = 8,   /* CFreeTraj(Hold): penetration depth at a knot, m       */
   TAMP_TERM_TRAJ_LEN = 9,     /* TrajLength cost: joint-space length of a motion, rad  */
-  TAMP_N_TERM_KINDS = 10
+  TAMP_TERM_SELF_COLLISION = 10, /* robot self-collision penetration depth, m          */
+  TAMP_N_TERM_KINDS = 11
 };
 
 typedef struct tamp_scene tamp_scene;   /* opaque, library-owned */
@@ -123,7 +124,14 @@ typedef struct {
  * static cuboids and every box not in the hand -- (weight 1, tolerance 1 mm)
  * and its joint limits (Motion); each motion carries the TrajLength cost, the
  * joint-space length of the polyline start, knots, end (weight 0.01: the paper
- * gives none; never a constraint). */
+ * gives none; never a constraint).  Self-collision (the CFree constraints'
+ * "does not cause robot self-collisions"; appendix tolerance 0 penetration):
+ * with self_collision = 1 every configuration, knots included, carries
+ * SelfCollision = sum of max(0, r_a + r_b - ||c_a - c_b||) over the arm's
+ * sphere pairs on links i > j + 1 whose spheres do not already overlap at q = 0
+ * (such links always touch: the scene's ignore list), plus the held box's
+ * spheres against the spheres of links 0..n-2 (not the wrist and the gripper
+ * that hold it); weight 1, tolerance 0. */
 typedef struct {
   float w[TAMP_N_TERM_KINDS];
   float tol[TAMP_N_TERM_KINDS];
@@ -133,7 +141,8 @@ typedef struct {
   int scale_by_batch;           /* 1: gradient of the batch mean (Eq. 4), i.e. / N_b      */
   int lanes;                    /* threads per (particle, configuration): 0 = tuned, 1,2,4,8 */
   int n_knots;                  /* knot configurations per motion between actions (0: none) */
-  int reserved[2];
+  int self_collision;           /* 1: every configuration carries SelfCollision             */
+  int reserved[1];
 } tamp_options;
 
 void tamp_default_options(tamp_options *opt);

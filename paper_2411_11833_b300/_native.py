@@ -7,7 +7,7 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libtamp.so")
 
-N_TERM_KINDS = 10
+N_TERM_KINDS = 11
 c_double_p = ctypes.POINTER(ctypes.c_double)
 c_float_p = ctypes.POINTER(ctypes.c_float)
 c_int_p = ctypes.POINTER(ctypes.c_int)
@@ -37,7 +37,7 @@ class Options(ctypes.Structure):
         ("lr_joint", ctypes.c_float), ("lr_pos", ctypes.c_float), ("lr_yaw", ctypes.c_float),
         ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
         ("optimize_grasp", ctypes.c_int), ("scale_by_batch", ctypes.c_int), ("lanes", ctypes.c_int),
-        ("n_knots", ctypes.c_int), ("reserved", ctypes.c_int * 2),
+        ("n_knots", ctypes.c_int), ("self_collision", ctypes.c_int), ("reserved", ctypes.c_int * 1),
     ]
 
 

@@ -49,6 +49,7 @@ struct Problem {
   int D = 0, K = 0, NT = 0, NCON = 0, NSLOT = 0;
   int NANG = 0;       // entries of the kernel's per-iteration (cos, sin) table per particle
   int n_seg = 0;      // motions with knots
+  bool self = false;  // configurations carry SelfCollision
   std::vector<uint32_t> blob;
   int opt_words = 0;  // leading words of the blob that the optimisation kernel stages
   uint32_t* d_blob = nullptr;
@@ -302,6 +303,57 @@ tamp_status build_scene_blob(tamp_scene* s, const tamp_scene_desc* d) {
   if (d->n_surf == 0)
     for (int c = 0; c < SURF_W; ++c) v.push_back(0);
   align4(v);
+  // self-collision masks: link pairs i > j + 1 whose spheres do not overlap at
+  // q = 0 (FP64 kinematics: T_{j+1} = T_j Rz(offset) Tz(d) Tx(a) Rx(alpha)),
+  // and the links 0..n-2 for the held box
+  {
+    auto mul = [](const double* A, const double* B, double* C) {
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+          double acc = 0.0;
+          for (int k = 0; k < 4; ++k) acc += A[4 * i + k] * B[4 * k + j];
+          C[4 * i + j] = acc;
+        }
+    };
+    std::vector<double> T(static_cast<size_t>(nj + 1) * 16);
+    std::copy(d->base, d->base + 16, T.begin());
+    for (int j = 0; j < nj; ++j) {
+      const double th = d->dh_offset[j], ct = std::cos(th), st = std::sin(th);
+      const double ca = std::cos(d->dh_alpha[j]), sa = std::sin(d->dh_alpha[j]);
+      const double A[16] = {ct, -st * ca, st * sa, d->dh_a[j] * ct,
+                            st, ct * ca, -ct * sa, d->dh_a[j] * st,
+                            0.0, sa, ca, d->dh_d[j],
+                            0.0, 0.0, 0.0, 1.0};
+      mul(&T[16 * j], A, &T[16 * (j + 1)]);
+    }
+    std::vector<double> c(3 * static_cast<size_t>(d->n_spheres));
+    for (int i = 0; i < d->n_spheres; ++i) {
+      const double* M = &T[16 * d->sphere_link[i]];
+      const double* l = d->sphere_xyzr + 4 * i;
+      for (int r = 0; r < 3; ++r) c[3 * i + r] = M[4 * r] * l[0] + M[4 * r + 1] * l[1] + M[4 * r + 2] * l[2] + M[4 * r + 3];
+    }
+    uint32_t mask[MAXJ + 2] = {0};
+    for (int li = 0; li <= nj; ++li)
+      for (int lj = 0; lj + 1 < li; ++lj) {
+        bool any_i = false, any_j = false, touch = false;
+        for (int a = 0; a < d->n_spheres; ++a) {
+          if (d->sphere_link[a] != li) continue;
+          any_i = true;
+          for (int b = 0; b < d->n_spheres; ++b) {
+            if (d->sphere_link[b] != lj) continue;
+            any_j = true;
+            const double dx = c[3 * a] - c[3 * b], dy = c[3 * a + 1] - c[3 * b + 1], dz = c[3 * a + 2] - c[3 * b + 2];
+            if (std::sqrt(dx * dx + dy * dy + dz * dz) < d->sphere_xyzr[4 * a + 3] + d->sphere_xyzr[4 * b + 3])
+              touch = true;
+          }
+        }
+        if (any_i && any_j && !touch) mask[li] |= 1u << lj;
+      }
+    for (int lj = 0; lj <= nj - 2; ++lj) mask[MAXJ + 1] |= 1u << lj;
+    v[SH_OFF_SELF] = static_cast<uint32_t>(v.size());
+    v.insert(v.end(), mask, mask + MAXJ + 2);
+  }
+  align4(v);
   v[SH_NJ] = static_cast<uint32_t>(nj);
   v[SH_B] = static_cast<uint32_t>(B);
   v[SH_NBS] = static_cast<uint32_t>(NBS);
@@ -326,6 +378,7 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
   struct Cfg {
     int kind, box, qo, go, tsrc, surf, ai;
     int hold = 1;                   // the hand holds `box` with the grasp at `go`
+    int t_self = -1;                // SelfCollision term
     int t_slot = -1, cp_slot = -1;  // placement slots of the Kin target and of the CFreePlace box
     std::vector<std::pair<int, PoseSrc>> env;
     int t_kp, t_kr, t_x, t_cf, t_cp, t_jl;
@@ -376,6 +429,7 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
             if (jb != held) c.env.push_back({jb, pose[jb]});
           c.tsrc = -1; c.surf = -1;
           c.t_cf = add_term(TK_CFREE_TRAJ); c.t_jl = add_term(TK_JOINT_LIMIT);
+          c.t_self = opt.self_collision ? add_term(TK_SELF) : -1;
           c.t_kp = c.t_kr = c.t_x = c.t_cf;  // never read for a knot
           c.t_cp = -1;
           cfgs.push_back(c);
@@ -412,6 +466,7 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
       c.surf = -1;
       c.t_kp = add_term(TK_KIN_POS); c.t_kr = add_term(TK_KIN_ROT); c.t_x = add_term(TK_GRASP);
       c.t_cf = add_term(TK_CFREE_HOLD); c.t_cp = -1; c.t_jl = add_term(TK_JOINT_LIMIT);
+      c.t_self = opt.self_collision ? add_term(TK_SELF) : -1;
       cfgs.push_back(c);
       held = b; held_g = c.go;
       pose[b].kind = 2;
@@ -436,6 +491,7 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
       c.pz = c.tz;
       c.t_kp = add_term(TK_KIN_POS); c.t_kr = add_term(TK_KIN_ROT); c.t_x = add_term(TK_STABLE);
       c.t_cf = add_term(TK_CFREE_HOLD); c.t_cp = add_term(TK_CFREE_PLACE); c.t_jl = add_term(TK_JOINT_LIMIT);
+      c.t_self = opt.self_collision ? add_term(TK_SELF) : -1;
       cfgs.push_back(c);
       pose[b].kind = 1; pose[b].off = po; pose[b].surf = sf;
       pose[b].slot = static_cast<int>(slots.size());
@@ -589,6 +645,7 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
     rec[CF_TCOS] = fbits(static_cast<float>(std::cos(static_cast<double>(c.tyaw))));
     rec[CF_TSIN] = fbits(static_cast<float>(std::sin(static_cast<double>(c.tyaw))));
     rec[CF_HOLD] = static_cast<uint32_t>(c.hold);
+    rec[CF_T_SELF] = static_cast<uint32_t>(c.t_self);
     v.insert(v.end(), rec, rec + CFG_W);
     env_count += static_cast<int>(c.env.size());
   }
@@ -661,6 +718,7 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
   v[PH_OFF_SEG] = static_cast<uint32_t>(v.size());
   v[PH_NSEG] = static_cast<uint32_t>(segs.size());
   pr.n_seg = static_cast<int>(segs.size());
+  pr.self = opt.self_collision != 0;
   for (const Seg& sg : segs) {
     const uint32_t rec[SEG_W] = {static_cast<uint32_t>(sg.qa), static_cast<uint32_t>(sg.qb),
                                  static_cast<uint32_t>(sg.qk), static_cast<uint32_t>(sg.m),
@@ -822,7 +880,7 @@ tamp_status plan_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lanes
   plan->smem = smem;
   plan->mv_global = mvg;
   plan->knots = false;
-  for (const Job& j : jobs) plan->knots = plan->knots || j.pr->n_seg > 0;
+  for (const Job& j : jobs) plan->knots = plan->knots || j.pr->n_seg > 0 || j.pr->self;
   const int per_sm = std::max(1, optimize_blocks_per_sm(L, warps, smem));
   plan->grid = std::min(static_cast<int>(plan->items.size()), s->sm_count * per_sm);
   return TAMP_OK;
@@ -927,8 +985,8 @@ extern "C" {
 void tamp_default_options(tamp_options* o) {
   if (!o) return;
   std::memset(o, 0, sizeof *o);
-  const float w[TAMP_N_TERM_KINDS] = {1.f, 5.f, 1.f, 2.f, 1.f, 1.f, 1.f, 0.25f, 1.f, 0.01f};
-  const float tol[TAMP_N_TERM_KINDS] = {5e-3f, 0.05f, 1e-3f, 1e-3f, 1e-3f, 1e-3f, 0.f, INFINITY, 1e-3f, INFINITY};
+  const float w[TAMP_N_TERM_KINDS] = {1.f, 5.f, 1.f, 2.f, 1.f, 1.f, 1.f, 0.25f, 1.f, 0.01f, 1.f};
+  const float tol[TAMP_N_TERM_KINDS] = {5e-3f, 0.05f, 1e-3f, 1e-3f, 1e-3f, 1e-3f, 0.f, INFINITY, 1e-3f, INFINITY, 0.f};
   for (int i = 0; i < TAMP_N_TERM_KINDS; ++i) {
     o->w[i] = w[i];
     o->tol[i] = tol[i];
@@ -1685,7 +1743,7 @@ extern "C" tamp_status tamp_eval_static_scratch(tamp_scene* s, int id, int n, co
   a.item_counter = reinterpret_cast<int*>(scratch + kStaticCounterOff);
   a.err = s->d_err;
   a.scratch_offset = static_cast<int>(smem - optimize_scratch_bytes(warps));
-  a.knots = pr->n_seg > 0 ? 1 : 0;
+  a.knots = (pr->n_seg > 0 || pr->self) ? 1 : 0;
   const int per_sm = std::max(1, optimize_blocks_per_sm(L, warps, smem));
   CUDA_TRY(s, launch_optimize(a, L, warps, std::min(tiles, s->sm_count * per_sm), smem, s->stream));
   return TAMP_OK;

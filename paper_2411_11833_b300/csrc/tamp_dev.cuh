@@ -21,7 +21,10 @@ enum SceneHdr {
   SH_NJ = 0, SH_NSPH, SH_O, SH_OPAD, SH_B, SH_NBS, SH_NSURF, SH_WORDS,
   SH_LINK0 = 8,                 // link_start[0..MAXJ+1]: 10 entries (words 8..17)
   SH_OFF_ARM = 18, SH_OFF_SPH, SH_OFF_OBS, SH_OFF_BOX, SH_OFF_BLOC, SH_OFF_BINIT, SH_OFF_SPHB,
-  SH_OFF_SURF, SH_HDR_WORDS = 32
+  SH_OFF_SURF,
+  SH_OFF_SELF,                  // self-collision masks: word l (l = 0..MAXJ) = the lower links j tested against
+                                // link l (bit j); word MAXJ + 1 = the links the held box is tested against
+  SH_HDR_WORDS = 32
 };
 // arm section: base frame (12), tool frame (12), then per joint ARM_JW words
 // frame = R row-major (9) + t (3)
@@ -63,7 +66,8 @@ enum CfgField {
   CF_T_SLOT,                    // placement slot of the Kin target if CF_TSRC >= 0, else -1
   CF_CP_SLOT,                   // placement slot of CF_CP_SRC (-1: none)
   CF_TCOS, CF_TSIN,             // floats: cos, sin of CF_TYAW
-  CF_HOLD                       // 1: the hand holds box CF_BOX with the grasp at CF_GOFF (Pick, Place, MoveHold knot)
+  CF_HOLD,                      // 1: the hand holds box CF_BOX with the grasp at CF_GOFF (Pick, Place, MoveHold knot)
+  CF_T_SELF                     // SelfCollision term index (-1: none)
 };
 // Motion segments between consecutive Pick/Place configurations (only with
 // knots): q offsets of the start and end configurations, of the first knot
@@ -94,7 +98,7 @@ constexpr int PROP_NF = 48, PROP_NT = 16;   // network inputs, target slots (out
 
 enum TermKind {
   TK_KIN_POS = 0, TK_KIN_ROT, TK_GRASP, TK_STABLE, TK_CFREE_HOLD, TK_CFREE_PLACE, TK_JOINT_LIMIT,
-  TK_OBJ_DIST, TK_CFREE_TRAJ, TK_TRAJ_LEN, TK_N
+  TK_OBJ_DIST, TK_CFREE_TRAJ, TK_TRAJ_LEN, TK_SELF, TK_N
 };
 
 // device error word bits
@@ -129,7 +133,7 @@ struct LaunchArgs {
   int scratch_offset;                 // bytes from the start of dynamic shared memory to the warp scratch
   const int* stop;                    // optional: a non-zero value makes the launch return at once
   int mv_global;                      // 1: Adam moments used in place in global memory (not staged)
-  int knots;                          // 1: some problem has trajectory knots (the kernel built for them runs)
+  int knots;                          // 1: some problem has knots or self-collision (the kernel built for them runs)
 };
 constexpr int ITEM_TILE_BITS = 20;
 

@@ -870,7 +870,7 @@ __device__ void eval_goal(const uint32_t* __restrict__ sc, const uint32_t* __res
 // joint-space length sum_e ||w_{e+1} - w_e|| of the polyline start, knots, end,
 // for one particle, with its gradient.
 template <int L>
-__device__ void eval_traj(const uint32_t* __restrict__ pb, const float* __restrict__ X, float* G, float* Tm, int nj,
+__device__ __noinline__ void eval_traj(const uint32_t* __restrict__ pb, const float* __restrict__ X, float* G, float* Tm, int nj,
                           int pl) {
   constexpr int PT = 32 / L;
   const int ns = pb[PH_NSEG];
@@ -904,6 +904,218 @@ __device__ void eval_traj(const uint32_t* __restrict__ pb, const float* __restri
     }
     Tm[t * PT + pl] = J;
   }
+}
+
+// One kinematic step: T <- T Rz(q_j + offset_j) Tz(d_j) Tx(a_j) Rx(alpha_j), with
+// (cos, sin) of the joint angle from the per-iteration table.
+__device__ __forceinline__ void fk_step(float (&R)[9], float (&t)[3], const float* arm, int j, float2 cs) {
+  const float4 Jp = *reinterpret_cast<const float4*>(arm + 24 + j * ARM_JW);  // a, d, cos alpha, sin alpha
+  rz_right(R, cs.x, cs.y);
+  t[0] = fmaf(Jp.y, R[2], fmaf(Jp.x, R[0], t[0]));
+  t[1] = fmaf(Jp.y, R[5], fmaf(Jp.x, R[3], t[1]));
+  t[2] = fmaf(Jp.y, R[8], fmaf(Jp.x, R[6], t[2]));
+  rx_right(R, Jp.z, Jp.w);
+}
+
+// SelfCollision of configuration k (the CFree constraints' "does not cause
+// robot self-collisions"): for each lower link j, the kinematics walk up from
+// T_j and test j's spheres against every higher link i of j's mask (link
+// bounding spheres first), and against the held box once the walk reaches
+// T_n.  A pair adds max(0, r_a + r_b - d) to the term; its gradient w.r.t. each
+// sphere centre goes into that sphere's link wrench (force, moment about the
+// origin) -- kept per lane in the warp's exact-phase scratch, idle during this
+// item -- and the held box's also into the grasp.  A sweep from T_n down then
+// turns the wrenches into joint torques: the two forces of a pair cancel below
+// both links.  All lanes call this; lanes with sub != 0 only help restore the
+// scratch.
+template <int L>
+__device__ __noinline__ void eval_self(const uint32_t* __restrict__ sc, const uint32_t* __restrict__ pb, int k,
+                                       const float* __restrict__ X, float* G, float* Tm,
+                                       const float2* __restrict__ trig, const WarpScratch& ws, int lane, int pl,
+                                       int sub) {
+  constexpr int PT = 32 / L;
+  const int nj = sc[SH_NJ];
+  float* acc = reinterpret_cast<float*>(ws.acc);  // [6 nj][32]: per link 1..nj force, moment
+  __syncwarp();
+  if (sub == 0) {
+    const float* arm = reinterpret_cast<const float*>(sc + sc[SH_OFF_ARM]);
+    const float* tl = arm + 12;
+    const float4* sph = reinterpret_cast<const float4*>(sc + sc[SH_OFF_SPH]);
+    const float4* sphb = reinterpret_cast<const float4*>(sc + sc[SH_OFF_SPHB]);
+    const float4* bloc = reinterpret_cast<const float4*>(sc + sc[SH_OFF_BLOC]);
+    const uint32_t* smask = sc + sc[SH_OFF_SELF];
+    const int NBS = sc[SH_NBS];
+    const int* cf = reinterpret_cast<const int*>(pb + pb[PH_OFF_CFG] + k * CFG_W);
+    const int t_self = cf[CF_T_SELF], qo = cf[CF_QOFF], go = cf[CF_GOFF], box = cf[CF_BOX];
+    const bool hold = cf[CF_HOLD] != 0;
+    const float w = tw(pb + pb[PH_OFF_TERMS], t_self);
+    const float2* tg = trig + k * (nj + 1) * PT + pl;
+    for (int i = 0; i < 6 * nj; ++i) acc[i * 32 + lane] = 0.f;
+    float gxv = 0.f, gyv = 0.f, gzv = 0.f, cgr = 1.f, sgr = 0.f;
+    if (hold) {
+      gxv = X[go * PT + pl]; gyv = X[(go + 1) * PT + pl]; gzv = X[(go + 2) * PT + pl];
+      const float2 c = tg[nj * PT];
+      cgr = c.x; sgr = c.y;
+    }
+    float J = 0.f, gg[4] = {0.f, 0.f, 0.f, 0.f};
+    // adds w * dpen/dc (g) at centre c to the wrench of link l (l = 0: the base, no torque)
+    auto add = [&](int l, float cx, float cy, float cz, float gx, float gy, float gz) {
+      if (l == 0) return;
+      float* a = acc + (l - 1) * 6 * 32 + lane;
+      a[0] += gx; a[32] += gy; a[64] += gz;
+      a[96] += cy * gz - cz * gy; a[128] += cz * gx - cx * gz; a[160] += cx * gy - cy * gx;
+    };
+    float Rj[9], tj[3];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Rj[i] = arm[i];
+    tj[0] = arm[9]; tj[1] = arm[10]; tj[2] = arm[11];
+    for (int j = 0; j <= nj; ++j) {
+      if (j > 0) fk_step(Rj, tj, arm, j - 1, tg[(j - 1) * PT]);
+      uint32_t m = 0;
+      for (int i = j + 2; i <= nj; ++i)
+        if ((smask[i] >> j) & 1u) m |= 1u << i;
+      const bool hj = hold && ((smask[MAXJ + 1] >> j) & 1u);
+      if (!m && !hj) continue;
+      for (int s0 = sc[SH_LINK0 + j]; s0 < static_cast<int>(sc[SH_LINK0 + j + 1]); s0 += NB) {
+        float cx[NB], cy[NB], cz[NB], cr[NB];
+#pragma unroll
+        for (int s = 0; s < NB; ++s) {
+          const float4 p = sph[s0 + s];
+          cx[s] = fmaf(Rj[0], p.x, fmaf(Rj[1], p.y, fmaf(Rj[2], p.z, tj[0])));
+          cy[s] = fmaf(Rj[3], p.x, fmaf(Rj[4], p.y, fmaf(Rj[5], p.z, tj[1])));
+          cz[s] = fmaf(Rj[6], p.x, fmaf(Rj[7], p.y, fmaf(Rj[8], p.z, tj[2])));
+          cr[s] = p.w;
+        }
+        const float4 bj = sphb[s0 / NB];
+        const float bjx = fmaf(Rj[0], bj.x, fmaf(Rj[1], bj.y, fmaf(Rj[2], bj.z, tj[0])));
+        const float bjy = fmaf(Rj[3], bj.x, fmaf(Rj[4], bj.y, fmaf(Rj[5], bj.z, tj[1])));
+        const float bjz = fmaf(Rj[6], bj.x, fmaf(Rj[7], bj.y, fmaf(Rj[8], bj.z, tj[2])));
+        // one sphere (x, y, z, r) on link li against the batch of link j
+        auto pair = [&](int li, float x, float y, float z, float r, float (&gh)[3]) {
+          gh[0] = gh[1] = gh[2] = 0.f;
+          if (!(r >= 0.f)) return;
+          {  // the sphere against the bounding sphere of link j's batch first
+            const float dx = x - bjx, dy = y - bjy, dz = z - bjz, R = r + bj.w;
+            if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= R * R) return;
+          }
+#pragma unroll
+          for (int t = 0; t < NB; ++t) {
+            const float dx = x - cx[t], dy = y - cy[t], dz = z - cz[t];
+            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float R = r + cr[t];
+            if (cr[t] >= 0.f && d2 < R * R) {
+              const float d = sqrtf(d2);
+              J += R - d;
+              if (d > 0.f) {
+                const float s = w / d;  // w dpen/dc_i = -w u, w dpen/dc_j = +w u, u = (c_i - c_j) / d
+                const float ux = s * dx, uy = s * dy, uz = s * dz;
+                gh[0] -= ux; gh[1] -= uy; gh[2] -= uz;
+                add(j, cx[t], cy[t], cz[t], ux, uy, uz);
+              }
+            }
+          }
+          if (gh[0] != 0.f || gh[1] != 0.f || gh[2] != 0.f) add(li, x, y, z, gh[0], gh[1], gh[2]);
+        };
+        float Ri[9], ti[3];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Ri[i] = Rj[i];
+        ti[0] = tj[0]; ti[1] = tj[1]; ti[2] = tj[2];
+        for (int i = j + 1; i <= nj; ++i) {
+          fk_step(Ri, ti, arm, i - 1, tg[(i - 1) * PT]);
+          if ((m >> i) & 1u) {
+            for (int s1 = sc[SH_LINK0 + i]; s1 < static_cast<int>(sc[SH_LINK0 + i + 1]); s1 += NB) {
+              const float4 bi = sphb[s1 / NB];
+              const float bx = fmaf(Ri[0], bi.x, fmaf(Ri[1], bi.y, fmaf(Ri[2], bi.z, ti[0]))) - bjx;
+              const float by = fmaf(Ri[3], bi.x, fmaf(Ri[4], bi.y, fmaf(Ri[5], bi.z, ti[1]))) - bjy;
+              const float bz = fmaf(Ri[6], bi.x, fmaf(Ri[7], bi.y, fmaf(Ri[8], bi.z, ti[2]))) - bjz;
+              const float Rb = bi.w + bj.w;
+              if (fmaf(bx, bx, fmaf(by, by, bz * bz)) >= Rb * Rb) continue;  // the batches cannot touch
+              for (int s = 0; s < NB; ++s) {
+                const float4 p = sph[s1 + s];
+                float gh[3];
+                pair(i, fmaf(Ri[0], p.x, fmaf(Ri[1], p.y, fmaf(Ri[2], p.z, ti[0]))),
+                     fmaf(Ri[3], p.x, fmaf(Ri[4], p.y, fmaf(Ri[5], p.z, ti[1]))),
+                     fmaf(Ri[6], p.x, fmaf(Ri[7], p.y, fmaf(Ri[8], p.z, ti[2]))), p.w, gh);
+              }
+            }
+          }
+          if (i == nj && hj) {
+            // the held box's spheres, rigid with frame n: c = T_n tool G(g)^-1 l; first its
+            // bounding sphere (radius about the box centre) against link j's batch
+            {
+              const float vx = -gxv, vy = -gyv, vz = -gzv;
+              const float wx = fmaf(cgr, vx, sgr * vy), wy = fmaf(sgr, vx, -cgr * vy), wz = -vz;
+              const float px = fmaf(tl[0], wx, fmaf(tl[1], wy, fmaf(tl[2], wz, tl[9])));
+              const float py = fmaf(tl[3], wx, fmaf(tl[4], wy, fmaf(tl[5], wz, tl[10])));
+              const float pz = fmaf(tl[6], wx, fmaf(tl[7], wy, fmaf(tl[8], wz, tl[11])));
+              const float dx = fmaf(Ri[0], px, fmaf(Ri[1], py, fmaf(Ri[2], pz, ti[0]))) - bjx;
+              const float dy = fmaf(Ri[3], px, fmaf(Ri[4], py, fmaf(Ri[5], pz, ti[1]))) - bjy;
+              const float dz = fmaf(Ri[6], px, fmaf(Ri[7], py, fmaf(Ri[8], pz, ti[2]))) - bjz;
+              const float Rh = reinterpret_cast<const float*>(sc + sc[SH_OFF_BOX])[box * BOX_W + 3] + bj.w;
+              if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= Rh * Rh) continue;  // i == nj: the walk ends here
+            }
+            for (int e = 0; e < NBS; ++e) {
+              const float4 l = bloc[box * NBS + e];
+              const float vx = l.x - gxv, vy = l.y - gyv, vz = l.z - gzv;
+              const float wx = fmaf(cgr, vx, sgr * vy), wy = fmaf(sgr, vx, -cgr * vy), wz = -vz;
+              const float px = fmaf(tl[0], wx, fmaf(tl[1], wy, fmaf(tl[2], wz, tl[9])));
+              const float py = fmaf(tl[3], wx, fmaf(tl[4], wy, fmaf(tl[5], wz, tl[10])));
+              const float pz = fmaf(tl[6], wx, fmaf(tl[7], wy, fmaf(tl[8], wz, tl[11])));
+              float gh[3];
+              pair(nj, fmaf(Ri[0], px, fmaf(Ri[1], py, fmaf(Ri[2], pz, ti[0]))),
+                   fmaf(Ri[3], px, fmaf(Ri[4], py, fmaf(Ri[5], pz, ti[1]))),
+                   fmaf(Ri[6], px, fmaf(Ri[7], py, fmaf(Ri[8], pz, ti[2]))), l.w, gh);
+              // the grasp moves the sphere by -R_obj: g by -R_obj^T f, its yaw by -(R_obj^T f x (l - g))_z
+              const float ax = fmaf(Ri[0], gh[0], fmaf(Ri[3], gh[1], Ri[6] * gh[2]));
+              const float ay = fmaf(Ri[1], gh[0], fmaf(Ri[4], gh[1], Ri[7] * gh[2]));
+              const float az = fmaf(Ri[2], gh[0], fmaf(Ri[5], gh[1], Ri[8] * gh[2]));
+              const float bx = fmaf(tl[0], ax, fmaf(tl[3], ay, tl[6] * az));
+              const float by = fmaf(tl[1], ax, fmaf(tl[4], ay, tl[7] * az));
+              const float bz = fmaf(tl[2], ax, fmaf(tl[5], ay, tl[8] * az));
+              const float Gx = fmaf(cgr, bx, sgr * by), Gy = fmaf(sgr, bx, -cgr * by), Gz = -bz;
+              gg[0] -= Gx; gg[1] -= Gy; gg[2] -= Gz;
+              gg[3] -= Gy * vx - Gx * vy;
+            }
+          }
+        }
+      }
+    }
+    Tm[t_self * PT + pl] = J;
+    if (hold)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) atomicAdd(&G[(go + i) * PT + pl], gg[i]);
+    // torques: from T_n down, the wrench of links >= l at joint l
+    float R[9], t[3];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) R[i] = arm[i];
+    t[0] = arm[9]; t[1] = arm[10]; t[2] = arm[11];
+    for (int j = 0; j < nj; ++j) fk_step(R, t, arm, j, tg[j * PT]);
+    float F[3] = {0.f, 0.f, 0.f}, M[3] = {0.f, 0.f, 0.f};
+    for (int l = nj; l >= 1; --l) {
+      const float* a = acc + (l - 1) * 6 * 32 + lane;
+      F[0] += a[0]; F[1] += a[32]; F[2] += a[64];
+      M[0] += a[96]; M[1] += a[128]; M[2] += a[160];
+      const float4 Jp = *reinterpret_cast<const float4*>(arm + 24 + (l - 1) * ARM_JW);
+      rx_right(R, Jp.z, -Jp.w);
+      t[0] -= fmaf(Jp.x, R[0], Jp.y * R[2]);
+      t[1] -= fmaf(Jp.x, R[3], Jp.y * R[5]);
+      t[2] -= fmaf(Jp.x, R[6], Jp.y * R[8]);
+      const float zx = R[2], zy = R[5], zz = R[8];
+      const float ox = t[1] * zz - t[2] * zy, oy = t[2] * zx - t[0] * zz, oz = t[0] * zy - t[1] * zx;
+      atomicAdd(&G[(qo + l - 1) * PT + pl],
+                fmaf(zx, M[0], fmaf(zy, M[1], fmaf(zz, M[2], fmaf(ox, F[0], fmaf(oy, F[1], oz * F[2]))))));
+      const float2 cs = tg[(l - 1) * PT];
+      rz_right(R, cs.x, -cs.y);
+    }
+  }
+  // restore the scratch the exact phase expects: zero accumulators and counters
+  __syncwarp();
+  for (int i = lane; i < 32 * NB * 4; i += 32) acc[i] = 0.f;
+  if (lane == 0) {
+    ws.count[0] = 0;
+    ws.count[1] = 0;
+  }
+  __syncwarp();
 }
 
 // ------------------------------------------------------------------ fused optimisation kernel
@@ -968,7 +1180,9 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
   // goal cost; warps pull them from a counter so that they finish together
   __shared__ int s_next;
   const bool has_goal = s_pb[PH_GOAL_T] != 0xffffffffu, has_traj = KN && s_pb[PH_NSEG] != 0;
-  const int n_work = NPIECE * K + (has_goal ? 1 : 0) + (has_traj ? 1 : 0);
+  // SelfCollision: one more item per configuration (after the pieces)
+  const int n_self = (KN && static_cast<int>(s_pb[s_pb[PH_OFF_CFG] + CF_T_SELF]) >= 0) ? K : 0;
+  const int n_work = NPIECE * K + n_self + (has_goal ? 1 : 0) + (has_traj ? 1 : 0);
   double b1t = pow(static_cast<double>(d.beta1), t0), b2t = pow(static_cast<double>(d.beta2), t0);
   unsigned n_obb = 0, n_box = 0;  // broad-phase candidates resolved exactly (work accounting)
 
@@ -998,11 +1212,14 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
       if (lane == 0) item = atomicAdd(&s_next, 1);
       item = __shfl_sync(0xffffffffu, item, 0);
       if (item >= n_work) break;
-      if (item < NPIECE * K)
+      if (item < NPIECE * K) {
         eval_config<L, KN>(s_sc, s_pb, K - 1 - item / NPIECE, item % NPIECE, sx, sg, st, slots, splace, strig, ws, n_obb,
                        n_box, lane, pl, sub);
-      else if (sub == 0) {
-        if (has_goal && item == NPIECE * K)
+      } else if (KN && item < NPIECE * K + n_self) {
+        if constexpr (KN)
+          eval_self<L>(s_sc, s_pb, K - 1 - (item - NPIECE * K), sx, sg, st, strig, ws, lane, pl, sub);
+      } else if (sub == 0) {
+        if (has_goal && item == NPIECE * K + n_self)
           eval_goal<L>(s_sc, s_pb, sx, sg, st, pl);
         else if constexpr (KN)
           eval_traj<L>(s_pb, sx, sg, st, nj, pl);

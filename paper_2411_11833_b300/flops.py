@@ -34,6 +34,11 @@ configurations) are configurations without Kin: the arm, plus the held box on
 a MoveHold, against the cuboids and every box not in the hand; each motion
 adds TrajLength, 3n + 1 FLOP per polyline edge (difference, square sum, add)
 and 2n per edge for its gradient.
+
+SelfCollision (optional) per configuration: sphere vs sphere 10 FLOP per
+tested pair (the arm's pairs on links i > j + 1 that do not touch at q = 0,
+and the held box's spheres against links 0..n-2), plus one kinematic walk up
+from every lower link (60 per joint step) and a reverse sweep (80 per joint).
 """
 from __future__ import annotations
 
@@ -70,6 +75,44 @@ def _walk(scene, actions, n_knots: int = 0):
         out.append((kind, b, B - 1, True))
         holding = kind == 0
     return out
+
+
+def self_pairs(scene):
+    """(arm sphere pairs, held-box sphere pairs) that SelfCollision tests:
+    links i > j + 1 whose spheres do not overlap at q = 0 (standard DH at the
+    joint offsets), and the box's spheres against the spheres of links 0..n-2."""
+    import numpy as np
+    n = scene.dh_a.shape[0]
+    T = [np.asarray(scene.base, dtype=np.float64)]
+    for j in range(n):
+        th, al = scene.dh_offset[j], scene.dh_alpha[j]
+        ct, st, ca, sa = math.cos(th), math.sin(th), math.cos(al), math.sin(al)
+        A = np.array([[ct, -st * ca, st * sa, scene.dh_a[j] * ct], [st, ct * ca, -ct * sa, scene.dh_a[j] * st],
+                      [0.0, sa, ca, scene.dh_d[j]], [0.0, 0.0, 0.0, 1.0]])
+        T.append(T[-1] @ A)
+    links = np.asarray(scene.sphere_link)
+    xyz = np.asarray(scene.sphere_xyzr)[:, :3]
+    r = np.asarray(scene.sphere_xyzr)[:, 3]
+    c = np.stack([T[l][:3, :3] @ p + T[l][:3, 3] for l, p in zip(links, xyz)])
+    touch = np.linalg.norm(c[:, None] - c[None], axis=-1) < r[:, None] + r[None]
+    arm = 0
+    for i in range(n + 1):
+        for j in range(i - 1):
+            a, b = links == i, links == j
+            if a.any() and b.any() and not touch[np.ix_(a, b)].any():
+                arm += int(a.sum()) * int(b.sum())
+    held = int((links <= n - 2).sum()) * scene.box_spheres.shape[1]
+    return arm, held
+
+
+def self_collision_flops(scene, actions, n_knots: int = 0) -> int:
+    """All-pairs FLOP of SelfCollision over one particle's configurations."""
+    n = scene.dh_a.shape[0]
+    arm, held = self_pairs(scene)
+    total = 0
+    for _kind, _b, _env, is_held in _walk(scene, actions, n_knots):
+        total += (arm + (held if is_held else 0)) * 10 + (n * (n + 1) // 2) * 60 + n * 80
+    return total
 
 
 def _motions(actions, n_knots: int) -> int:
