@@ -765,6 +765,10 @@ int preferred_lanes(int requested, long total_particles) {
   return total_particles >= 148L * 16 ? 1 : (total_particles >= 148L * 8 ? 2 : 4);
 }
 
+// The kernel instantiation a problem needs: knots (with or without
+// self-collision), self-collision only, or neither.
+int problem_feat(const Problem& pr) { return pr.n_seg > 0 ? FEAT_KNOTS : (pr.self ? FEAT_SELF : 0); }
+
 void free_batch(Problem& pr) {
   cudaFree(pr.d_x); cudaFree(pr.d_m); cudaFree(pr.d_v); cudaFree(pr.d_cost);
   cudaFree(pr.d_flags); cudaFree(pr.d_counts); cudaFree(pr.d_first); cudaFree(pr.d_work);
@@ -809,7 +813,7 @@ struct Job {
 struct Plan {
   int L = 1, warps = 1, grid = 0;
   bool mv_global = false;  // Adam moments in global memory: the tile fits shared memory only that way
-  bool knots = false;      // some problem has trajectory knots
+  int feat = 0;            // optional terms of the problems: 0, FEAT_SELF, FEAT_KNOTS
   size_t smem = 0;
   std::vector<ProbDesc> descs;
   std::vector<uint32_t> items;
@@ -879,8 +883,8 @@ tamp_status plan_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lanes
   plan->warps = warps;
   plan->smem = smem;
   plan->mv_global = mvg;
-  plan->knots = false;
-  for (const Job& j : jobs) plan->knots = plan->knots || j.pr->n_seg > 0 || j.pr->self;
+  plan->feat = 0;
+  for (const Job& j : jobs) plan->feat = std::max(plan->feat, problem_feat(*j.pr));
   const int per_sm = std::max(1, optimize_blocks_per_sm(L, warps, smem));
   plan->grid = std::min(static_cast<int>(plan->items.size()), s->sm_count * per_sm);
   return TAMP_OK;
@@ -897,7 +901,7 @@ LaunchArgs plan_args(const tamp_scene* s, const Plan& plan, ProbDesc* d_descs, u
   a.err = s->d_err;
   a.scratch_offset = static_cast<int>(plan.smem - optimize_scratch_bytes(plan.warps));
   a.mv_global = plan.mv_global ? 1 : 0;
-  a.knots = plan.knots ? 1 : 0;
+  a.feat = plan.feat;
   return a;
 }
 
@@ -1743,7 +1747,7 @@ extern "C" tamp_status tamp_eval_static_scratch(tamp_scene* s, int id, int n, co
   a.item_counter = reinterpret_cast<int*>(scratch + kStaticCounterOff);
   a.err = s->d_err;
   a.scratch_offset = static_cast<int>(smem - optimize_scratch_bytes(warps));
-  a.knots = (pr->n_seg > 0 || pr->self) ? 1 : 0;
+  a.feat = problem_feat(*pr);
   const int per_sm = std::max(1, optimize_blocks_per_sm(L, warps, smem));
   CUDA_TRY(s, launch_optimize(a, L, warps, std::min(tiles, s->sm_count * per_sm), smem, s->stream));
   return TAMP_OK;

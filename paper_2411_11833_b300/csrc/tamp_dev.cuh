@@ -133,8 +133,10 @@ struct LaunchArgs {
   int scratch_offset;                 // bytes from the start of dynamic shared memory to the warp scratch
   const int* stop;                    // optional: a non-zero value makes the launch return at once
   int mv_global;                      // 1: Adam moments used in place in global memory (not staged)
-  int knots;                          // 1: some problem has knots or self-collision (the kernel built for them runs)
+  int feat;                           // the optional terms of the launch's problems: 0, FEAT_SELF, FEAT_KNOTS
 };
+// Feature sets of the optimisation kernel's instantiations.
+enum KernelFeat { FEAT_SELF = 1, FEAT_KNOTS = 2 };
 constexpr int ITEM_TILE_BITS = 20;
 
 }  // namespace tamp

@@ -1122,7 +1122,10 @@ __device__ __noinline__ void eval_self(const uint32_t* __restrict__ sc, const ui
 // One tile of PT particles of one problem: load it, run n_steps fused
 // iterations (evaluation + adjoint, Eq. 3 check, Adam) and one final check,
 // write it back.  All threads of the CTA call this together.
-template <int L, bool KN>
+// FEAT: the optional terms the kernel is built for -- FEAT_KNOTS (knot
+// configurations and TrajLength, with self-collision), FEAT_SELF (SelfCollision
+// only), 0 (neither: the configuration code of every other skeleton).
+template <int L, int FEAT>
 __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, const uint32_t* s_pb, float* tile_mem,
                          const WarpScratch& ws, bool mv_global) {
   constexpr int PT = 32 / L;
@@ -1179,9 +1182,10 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
   // configurations first (their environments hold more placed boxes), then the
   // goal cost; warps pull them from a counter so that they finish together
   __shared__ int s_next;
+  constexpr bool KN = FEAT == FEAT_KNOTS, SC = FEAT != 0;
   const bool has_goal = s_pb[PH_GOAL_T] != 0xffffffffu, has_traj = KN && s_pb[PH_NSEG] != 0;
   // SelfCollision: one more item per configuration (after the pieces)
-  const int n_self = (KN && static_cast<int>(s_pb[s_pb[PH_OFF_CFG] + CF_T_SELF]) >= 0) ? K : 0;
+  const int n_self = (SC && static_cast<int>(s_pb[s_pb[PH_OFF_CFG] + CF_T_SELF]) >= 0) ? K : 0;
   const int n_work = NPIECE * K + n_self + (has_goal ? 1 : 0) + (has_traj ? 1 : 0);
   double b1t = pow(static_cast<double>(d.beta1), t0), b2t = pow(static_cast<double>(d.beta2), t0);
   unsigned n_obb = 0, n_box = 0;  // broad-phase candidates resolved exactly (work accounting)
@@ -1215,8 +1219,8 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
       if (item < NPIECE * K) {
         eval_config<L, KN>(s_sc, s_pb, K - 1 - item / NPIECE, item % NPIECE, sx, sg, st, slots, splace, strig, ws, n_obb,
                        n_box, lane, pl, sub);
-      } else if (KN && item < NPIECE * K + n_self) {
-        if constexpr (KN)
+      } else if (SC && item < NPIECE * K + n_self) {
+        if constexpr (SC)
           eval_self<L>(s_sc, s_pb, K - 1 - (item - NPIECE * K), sx, sg, st, strig, ws, lane, pl, sub);
       } else if (sub == 0) {
         if (has_goal && item == NPIECE * K + n_self)
@@ -1330,7 +1334,7 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
 // skeletons first, as the host orders them -- staging a problem's tables
 // whenever it moves to a new problem.  Many skeletons of uneven length and
 // particle count thus share one launch and balance across the SMs.
-template <int L, bool KN>
+template <int L, int FEAT>
 __global__ void __launch_bounds__(512, 1) optimize_kernel(LaunchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
@@ -1398,7 +1402,7 @@ __global__ void __launch_bounds__(512, 1) optimize_kernel(LaunchArgs a) {
       __syncthreads();
       if (abort_flag) return;
     }
-    run_tile<L, KN>(d, tile, s_sc, s_pb, reinterpret_cast<float*>(s_pb + pw), ws, a.mv_global != 0);
+    run_tile<L, FEAT>(d, tile, s_sc, s_pb, reinterpret_cast<float*>(s_pb + pw), ws, a.mv_global != 0);
     __syncthreads();  // everyone has read s_item and the tables before they change
   }
 }
@@ -1762,64 +1766,67 @@ cudaError_t launch_chunk_control(int* t_dev, const int* const* first_iters, int 
 
 // ------------------------------------------------------------------ launchers
 // largest dynamic shared-memory size enabled so far for optimize_kernel<1,2,4,8>
-// without and with knot support
-static size_t g_smem_enabled[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+// per feature set (0, FEAT_SELF, FEAT_KNOTS)
+static size_t g_smem_enabled[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
 static int lane_slot(int L) { return L == 1 ? 0 : (L == 2 ? 1 : (L == 4 ? 2 : 3)); }
 
-template <int L, bool KN>
+template <int L, int FEAT>
 static cudaError_t set_smem(size_t smem) {
-  size_t& enabled = g_smem_enabled[KN ? 1 : 0][lane_slot(L)];
+  size_t& enabled = g_smem_enabled[FEAT][lane_slot(L)];
   if (smem <= 48 * 1024 || smem <= enabled) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(optimize_kernel<L, KN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(optimize_kernel<L, FEAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e == cudaSuccess) enabled = smem;
   return e;
 }
 
-template <int L>
-static cudaError_t launch_opt(const LaunchArgs& a, int warps, int grid, size_t smem, cudaStream_t st) {
-  cudaError_t e = a.knots ? set_smem<L, true>(smem) : set_smem<L, false>(smem);
+template <int L, int FEAT>
+static cudaError_t launch_feat(const LaunchArgs& a, int warps, int grid, size_t smem, cudaStream_t st) {
+  cudaError_t e = set_smem<L, FEAT>(smem);
   if (e != cudaSuccess) return e;
   if (grid <= 0) return cudaSuccess;
-  if (a.knots)
-    optimize_kernel<L, true><<<grid, warps * 32, smem, st>>>(a);
-  else
-    optimize_kernel<L, false><<<grid, warps * 32, smem, st>>>(a);
+  optimize_kernel<L, FEAT><<<grid, warps * 32, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int L>
+static cudaError_t launch_opt(const LaunchArgs& a, int warps, int grid, size_t smem, cudaStream_t st) {
+  switch (a.feat) {
+    case 0: return launch_feat<L, 0>(a, warps, grid, smem, st);
+    case FEAT_SELF: return launch_feat<L, FEAT_SELF>(a, warps, grid, smem, st);
+    case FEAT_KNOTS: return launch_feat<L, FEAT_KNOTS>(a, warps, grid, smem, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 int optimize_blocks_per_sm(int L, int warps, size_t smem) {
   int n = 0;
   cudaError_t e = cudaSuccess;
   switch (L) {
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<1, false>, warps * 32, smem); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<2, false>, warps * 32, smem); break;
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<4, false>, warps * 32, smem); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<8, false>, warps * 32, smem); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<1, 0>, warps * 32, smem); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<2, 0>, warps * 32, smem); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<4, 0>, warps * 32, smem); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<8, 0>, warps * 32, smem); break;
   }
   return e == cudaSuccess ? n : 1;
+}
+
+template <int L>
+static cudaError_t set_smem_all(size_t smem) {
+  cudaError_t e = set_smem<L, 0>(smem);
+  if (e == cudaSuccess) e = set_smem<L, FEAT_SELF>(smem);
+  if (e == cudaSuccess) e = set_smem<L, FEAT_KNOTS>(smem);
+  return e;
 }
 
 // Allow `smem` bytes of dynamic shared memory for optimize_kernel<L, *> (outside
 // any stream capture).
 cudaError_t optimize_set_smem(int L, size_t smem) {
   switch (L) {
-    case 1: {
-      cudaError_t e = set_smem<1, false>(smem);
-      return e != cudaSuccess ? e : set_smem<1, true>(smem);
-    }
-    case 2: {
-      cudaError_t e = set_smem<2, false>(smem);
-      return e != cudaSuccess ? e : set_smem<2, true>(smem);
-    }
-    case 4: {
-      cudaError_t e = set_smem<4, false>(smem);
-      return e != cudaSuccess ? e : set_smem<4, true>(smem);
-    }
-    case 8: {
-      cudaError_t e = set_smem<8, false>(smem);
-      return e != cudaSuccess ? e : set_smem<8, true>(smem);
-    }
+    case 1: return set_smem_all<1>(smem);
+    case 2: return set_smem_all<2>(smem);
+    case 4: return set_smem_all<4>(smem);
+    case 8: return set_smem_all<8>(smem);
     default: return cudaErrorInvalidValue;
   }
 }
