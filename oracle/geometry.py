@@ -48,6 +48,17 @@ def rot_z(th) -> torch.Tensor:
     return T
 
 
+def rot_y(be) -> torch.Tensor:
+    be = torch.as_tensor(be, dtype=DT)
+    c, s = torch.cos(be), torch.sin(be)
+    T = eye4(be.shape)
+    T[..., 0, 0] = c
+    T[..., 0, 2] = s
+    T[..., 2, 0] = -s
+    T[..., 2, 2] = c
+    return T
+
+
 def rot_x(al) -> torch.Tensor:
     al = torch.as_tensor(al, dtype=DT)
     c, s = torch.cos(al), torch.sin(al)
@@ -115,6 +126,13 @@ def grasp_pose(gx, gy, gz, gyaw) -> torch.Tensor:
     """Top-down 4-DOF grasp: end-effector pose in the object frame,
     Trans(g) Rz(yaw) Rx(pi) (the gripper's z axis points down)."""
     return translation(gx, gy, gz) @ rot_z(gyaw) @ rot_x(torch.full_like(torch.as_tensor(gx, dtype=DT), math.pi))
+
+
+def grasp_pose6(gx, gy, gz, gyaw, groll, gpitch) -> torch.Tensor:
+    """6-DOF grasp: Trans(g) Rz(yaw) Ry(pitch) Rx(roll) Rx(pi); zero roll and
+    pitch give the top-down grasp."""
+    return (translation(gx, gy, gz) @ rot_z(gyaw) @ rot_y(gpitch) @ rot_x(groll)
+            @ rot_x(torch.full_like(torch.as_tensor(gx, dtype=DT), math.pi)))
 
 
 # ------------------------------------------------------------------ distances

@@ -94,11 +94,11 @@ def _target_fn(pr: Problem, cfg, x: torch.Tensor):
         Pb = pr._box_pose(cfg["target"], b, x)
 
         def target(y):
-            Gp = G.grasp_pose(x[:, go], x[:, go + 1], x[:, go + 2], y)
+            Gp = pr._grasp(x, go, yaw=y)
             return Pb @ Gp, torch.zeros(x.shape[0], 3, dtype=DT)
         return target, go + 3
     _, po, s = cfg["target"]
-    Gp = G.grasp_pose(x[:, go], x[:, go + 1], x[:, go + 2], x[:, go + 3])
+    Gp = pr._grasp(x, go)
     z = float(pr.sc.surf[s, 5] + pr.sc.box_half[b, 2])
 
     def target(y):

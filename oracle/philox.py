@@ -77,6 +77,13 @@ def sample_uniform(problem, n_particles: int, seed: int) -> np.ndarray:
             for j in range(3):
                 X[:, go + j] = lo[j] + (hi[j] - lo[j]) * U[go + j]
             X[:, go + 3] = -math.pi + 2.0 * math.pi * U[go + 3]
+            if problem.opts.grasp_dof == 6:
+                # roll and pitch in [-pi/2, pi/2): from above to the side, never from below
+                for j in (4, 5):
+                    X[:, go + j] = -0.5 * math.pi + math.pi * U[go + j]
+                lo = [-h[0], -h[1], -h[2]]
+                for j in range(3):
+                    X[:, go + j] = lo[j] + (hi[j] - lo[j]) * U[go + j]
         else:
             _, po, s = cfg["target"]
             cx, cy, syaw, hx, hy, _z = sc.surf[s]

@@ -43,7 +43,10 @@ Readings of points the paper leaves open (each one is listed in the design doc):
     scored with the bound distance to the surface rectangle, summed; z is
     fixed by the surface (placements are x, y, yaw);
   * Grasp(o, g): bound distance of g_xyz to [-h_x, h_x] x [-h_y, h_y] x
-    [h_z - 0.02, h_z], yaw free;
+    [h_z - 0.02, h_z], yaw free; with 6-DOF grasps (Sec. VIII setup: "top-down
+    4-DOF or 6-DOF poses") g = (x, y, z, yaw, roll, pitch), G(g) =
+    Trans(g) Rz(yaw) Ry(pitch) Rx(roll) Rx(pi), the position bounded by the
+    whole box [-h, h] (the gripper may hold any side), the angles free;
   * knots: the knots of the motion into an action sit in the particle just
     before that action's own variables; CFreeTraj(Hold) is CFreeHold's
     penetration depth at each knot -- the arm, plus the held box on a MoveHold,
@@ -98,6 +101,7 @@ class Options:
     tol: list = field(default_factory=lambda: [5e-3, 0.05, 1e-3, 1e-3, 1e-3, 1e-3, 0.0, math.inf, 1e-3, math.inf,
                                                0.0])
     n_knots: int = 0                        # knot configurations per motion between actions
+    grasp_dof: int = 4                      # 4: top-down (x, y, z, yaw); 6: + roll, pitch
     self_collision: bool = False            # SelfCollision term on every configuration
     lr_joint: float = 1e-2
     lr_pos: float = 3e-3
@@ -192,8 +196,8 @@ class Problem:
                 if not (0 <= b < B) or pose[b][0] == "held":
                     raise ValueError(f"action {ai}: invalid box {b}")
                 g_off = off
-                self.kinds += ["gpos"] * 3 + ["gyaw"]
-                off += 4
+                self.kinds += ["gpos"] * 3 + ["gyaw"] + (["gyaw"] * 2 if self.opts.grasp_dof == 6 else [])
+                off += self.opts.grasp_dof
                 q_off = off
                 self.kinds += ["q"] * self.n
                 off += self.n
@@ -237,6 +241,19 @@ class Problem:
         self.D = off
 
     # -------------------------------------------------------------- helpers
+    def _grasp(self, x, go, yaw=None):
+        """G(g) of the grasp at component go (yaw replaced if given)."""
+        y = x[:, go + 3] if yaw is None else yaw
+        if self.opts.grasp_dof == 6:
+            return G.grasp_pose6(x[:, go], x[:, go + 1], x[:, go + 2], y, x[:, go + 4], x[:, go + 5])
+        return G.grasp_pose(x[:, go], x[:, go + 1], x[:, go + 2], y)
+
+    def _grasp_bounds(self, b):
+        h = self.sc.box_half[b]
+        if self.opts.grasp_dof == 6:
+            return (torch.tensor([-h[0], -h[1], -h[2]], dtype=DT), torch.tensor([h[0], h[1], h[2]], dtype=DT))
+        return (torch.tensor([-h[0], -h[1], h[2] - 0.02], dtype=DT), torch.tensor([h[0], h[1], h[2]], dtype=DT))
+
     def _box_pose(self, src, b, x):
         """Pose of box b from its source: the scene's initial pose or a placement."""
         if src[0] == "init":
@@ -288,8 +305,7 @@ class Problem:
                 c_all = G.apply(frames[:, links], arm_c)
                 r_all = arm_r
                 if cfg["box"] >= 0:
-                    g = x[:, cfg["g_off"]:cfg["g_off"] + 4]
-                    Gp = G.grasp_pose(g[:, 0], g[:, 1], g[:, 2], g[:, 3])
+                    Gp = self._grasp(x, cfg["g_off"])
                     held_c, held_r = self._box_spheres(cfg["box"], ee @ G.rigid_inverse(Gp))
                     c_all = torch.cat([c_all, held_c], dim=1)
                     r_all = torch.cat([arm_r, held_r])
@@ -297,7 +313,7 @@ class Problem:
                                SELF_COLLISION: self._self_penetration(c_all, r_all)}
                 continue
             g = x[:, cfg["g_off"]:cfg["g_off"] + 4]
-            Gp = G.grasp_pose(g[:, 0], g[:, 1], g[:, 2], g[:, 3])
+            Gp = self._grasp(x, cfg["g_off"])
             b = cfg["box"]
             Tobj_target = self._box_pose(cfg["target"], b, x)
             e_pos, e_rot = G.pose_error(ee, Tobj_target @ Gp)
@@ -310,9 +326,7 @@ class Problem:
             vals = {KIN_POS: e_pos, KIN_ROT: e_rot, CFREE_HOLD: cfree_hold, JOINT_LIMIT: jl,
                     SELF_COLLISION: self._self_penetration(c_all, r_all)}
             if cfg["kind"] == PICK:
-                h = torch.as_tensor(sc.box_half[b], dtype=DT)
-                lo = torch.stack([-h[0], -h[1], h[2] - 0.02])
-                hi = torch.stack([h[0], h[1], h[2]])
+                lo, hi = self._grasp_bounds(b)
                 vals[GRASP] = G.dist_from_bounds(g[:, :3], lo, hi)
             else:
                 _, p_off, s = cfg["target"]
@@ -535,8 +549,7 @@ class Problem:
             if cfg["kind"] == KNOT:
                 c_all, r_all = G.apply(frames[:, links], arm_c), arm_r
                 if cfg["box"] >= 0:
-                    g = x[:, cfg["g_off"]:cfg["g_off"] + 4]
-                    Gp = G.grasp_pose(g[:, 0], g[:, 1], g[:, 2], g[:, 3])
+                    Gp = self._grasp(x, cfg["g_off"])
                     held_c, held_r = self._box_spheres(cfg["box"], ee @ G.rigid_inverse(Gp))
                     c_all, r_all = torch.cat([c_all, held_c], 1), torch.cat([arm_r, held_r])
                 ms += env_margins(c_all, r_all, cfg["env"])
@@ -544,7 +557,7 @@ class Problem:
                 ms += bound_margins(q, lo_q, hi_q)
                 continue
             g = x[:, cfg["g_off"]:cfg["g_off"] + 4]
-            Gp = G.grasp_pose(g[:, 0], g[:, 1], g[:, 2], g[:, 3])
+            Gp = self._grasp(x, cfg["g_off"])
             b = cfg["box"]
             Tt = self._box_pose(cfg["target"], b, x)
             e_pos, e_rot = G.pose_error(ee, Tt @ Gp)
@@ -555,9 +568,7 @@ class Problem:
             ms += self_margins(torch.cat([arm_world, held_c], 1), torch.cat([arm_r, held_r]))
             ms += bound_margins(q, lo_q, hi_q)
             if cfg["kind"] == PICK:
-                h = self.sc.box_half[b]
-                ms += bound_margins(g[:, :3], torch.tensor([-h[0], -h[1], h[2] - 0.02], dtype=DT),
-                                    torch.tensor([h[0], h[1], h[2]], dtype=DT))
+                ms += bound_margins(g[:, :3], *self._grasp_bounds(b))
             else:
                 _, p_off, s = cfg["target"]
                 pc, pr = self._box_spheres(b, Tt)
