@@ -67,6 +67,8 @@ def parse():
                     help="trajectory knots per motion between actions (0: configurations only, the headline)")
     ap.add_argument("--self-collision", action="store_true",
                     help="every configuration also carries SelfCollision (not in the headline)")
+    ap.add_argument("--grasp-dof", type=int, default=4, choices=[4, 6],
+                    help="4: top-down grasps (the headline); 6: 6-DOF grasps")
     return ap.parse_args()
 
 
@@ -334,10 +336,13 @@ def main():
                      "limits, TrajLength)")
     if args.self_collision:
         workload += "; SelfCollision on every configuration"
+    if args.grasp_dof == 6:
+        workload += "; 6-DOF grasps"
     with torch.cuda.stream(stream):
         scene = pkg.Scene(sc, device=local, stream=stream.cuda_stream)
         pid = scene.set_skeleton(acts, pkg.default_options(lanes=args.lanes, n_knots=args.knots,
-                                                           self_collision=int(args.self_collision)))
+                                                           self_collision=int(args.self_collision),
+                                                           grasp_dof=args.grasp_dof))
     D, NT, _ = scene.problem_info(pid)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     tuned = None
@@ -420,7 +425,7 @@ def main():
         probe = round(probe_tf.value, 2)
     achieved = launch_flops / kern_s / 1e12
     sha = kernel_source_sha()
-    headline = args.workload == "packing" and args.knots == 0 and not args.self_collision
+    headline = args.workload == "packing" and args.knots == 0 and not args.self_collision and args.grasp_dof == 4
     traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["source_sha"] == sha and headline else None
     out = {
         "metric": METRIC, "value": value, "unit": "particle-iters/s", "n_gpus": world, "steps": args.steps,

@@ -131,7 +131,12 @@ typedef struct {
  * sphere pairs on links i > j + 1 whose spheres do not already overlap at q = 0
  * (such links always touch: the scene's ignore list), plus the held box's
  * spheres against the spheres of links 0..n-2 (not the wrist and the gripper
- * that hold it); weight 1, tolerance 0. */
+ * that hold it); weight 1, tolerance 0.  6-DOF grasps (Sec. VIII setup: grasps
+ * are "top-down 4-DOF or 6-DOF poses"): with grasp_dof = 6 a grasp is (x, y, z,
+ * yaw, roll, pitch) in the box frame, G(g) = Trans(x, y, z) Rz(yaw) Ry(pitch)
+ * Rx(roll) Rx(pi) (roll = pitch = 0 is the top-down grasp), Grasp bounds the
+ * position by the whole box [-h, h] (any side may be held), and the uniform
+ * sampler draws roll and pitch in [-pi/2, pi/2). */
 typedef struct {
   float w[TAMP_N_TERM_KINDS];
   float tol[TAMP_N_TERM_KINDS];
@@ -142,7 +147,7 @@ typedef struct {
   int lanes;                    /* threads per (particle, configuration): 0 = tuned, 1,2,4,8 */
   int n_knots;                  /* knot configurations per motion between actions (0: none) */
   int self_collision;           /* 1: every configuration carries SelfCollision             */
-  int reserved[1];
+  int grasp_dof;                /* 4 (0 reads as 4): top-down grasps; 6: 6-DOF grasps         */
 } tamp_options;
 
 void tamp_default_options(tamp_options *opt);

@@ -37,7 +37,7 @@ class Options(ctypes.Structure):
         ("lr_joint", ctypes.c_float), ("lr_pos", ctypes.c_float), ("lr_yaw", ctypes.c_float),
         ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
         ("optimize_grasp", ctypes.c_int), ("scale_by_batch", ctypes.c_int), ("lanes", ctypes.c_int),
-        ("n_knots", ctypes.c_int), ("self_collision", ctypes.c_int), ("reserved", ctypes.c_int * 1),
+        ("n_knots", ctypes.c_int), ("self_collision", ctypes.c_int), ("grasp_dof", ctypes.c_int),
     ]
 
 

@@ -50,6 +50,7 @@ struct Problem {
   int NANG = 0;       // entries of the kernel's per-iteration (cos, sin) table per particle
   int n_seg = 0;      // motions with knots
   bool self = false;  // configurations carry SelfCollision
+  bool grasp6 = false;  // 6-DOF grasps
   std::vector<uint32_t> blob;
   int opt_words = 0;  // leading words of the blob that the optimisation kernel stages
   uint32_t* d_blob = nullptr;
@@ -372,6 +373,9 @@ struct PoseSrc {
 // Walk the skeleton (Listing 1 preconditions / effects) and pack the problem blob.
 tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const tamp_options& opt, Problem& pr) {
   const int nj = s->nj, B = s->B;
+  if (opt.grasp_dof != 0 && opt.grasp_dof != 4 && opt.grasp_dof != 6)
+    return fail(s, TAMP_ERR_INVALID_ARG, "grasp_dof %d (4 or 6)", opt.grasp_dof);
+  const bool g6 = opt.grasp_dof == 6;
   std::vector<PoseSrc> pose(B);
   int held = -1, held_g = -1;
   int off = 0;
@@ -445,10 +449,18 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
       const double* h = &s->box_half[3 * b];
       samp.push_back({SK_LINEAR, static_cast<float>(-h[0]), static_cast<float>(h[0]), 0});
       samp.push_back({SK_LINEAR, static_cast<float>(-h[1]), static_cast<float>(h[1]), 0});
-      samp.push_back({SK_LINEAR, static_cast<float>(h[2] - 0.02), static_cast<float>(h[2]), 0});
+      if (g6)  // a 6-DOF grasp may hold any side: the whole box
+        samp.push_back({SK_LINEAR, static_cast<float>(-h[2]), static_cast<float>(h[2]), 0});
+      else
+        samp.push_back({SK_LINEAR, static_cast<float>(h[2] - 0.02), static_cast<float>(h[2]), 0});
       samp.push_back({SK_LINEAR, static_cast<float>(-M_PI), static_cast<float>(M_PI), 0});
       comp_kind.insert(comp_kind.end(), {1, 1, 1, 2});
-      off += 4;
+      if (g6) {  // roll, pitch in [-pi/2, pi/2): from above to the side
+        samp.push_back({SK_LINEAR, static_cast<float>(-M_PI / 2), static_cast<float>(M_PI / 2), 0});
+        samp.push_back({SK_LINEAR, static_cast<float>(-M_PI / 2), static_cast<float>(M_PI / 2), 0});
+        comp_kind.insert(comp_kind.end(), {2, 2});
+      }
+      off += g6 ? 6 : 4;
       c.qo = off;
       off += nj;
       for (int j = 0; j < B; ++j)
@@ -742,11 +754,13 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
     v.push_back(static_cast<uint32_t>(sp.surf));
   }
   align4(v);
-  pr.NANG = pr.K * (nj + 1);
+  pr.NANG = pr.K * (nj + 1 + (g6 ? 2 : 0));
+  pr.grasp6 = g6;
   pr.NSLOT = static_cast<int>(slots.size());
   v[PH_NSLOT] = static_cast<uint32_t>(pr.NSLOT);
   v[PH_D] = pr.D; v[PH_K] = pr.K; v[PH_NT] = pr.NT; v[PH_NCON] = pr.NCON;
   v[PH_GOAL_T] = static_cast<uint32_t>(goal_t); v[PH_NGOAL] = static_cast<uint32_t>(goal.size());
+  v[PH_GRASP6] = g6 ? 1u : 0u;
   v[PH_WORDS] = static_cast<uint32_t>(v.size());
   return TAMP_OK;
 }
@@ -765,9 +779,11 @@ int preferred_lanes(int requested, long total_particles) {
   return total_particles >= 148L * 16 ? 1 : (total_particles >= 148L * 8 ? 2 : 4);
 }
 
-// The kernel instantiation a problem needs: knots (with or without
-// self-collision), self-collision only, or neither.
-int problem_feat(const Problem& pr) { return pr.n_seg > 0 ? FEAT_KNOTS : (pr.self ? FEAT_SELF : 0); }
+// The kernel instantiation a problem needs: knots or 6-DOF grasps (with or
+// without self-collision), self-collision only, or neither.
+int problem_feat(const Problem& pr) {
+  return (pr.n_seg > 0 || pr.grasp6) ? FEAT_EXT : (pr.self ? FEAT_SELF : 0);
+}
 
 void free_batch(Problem& pr) {
   cudaFree(pr.d_x); cudaFree(pr.d_m); cudaFree(pr.d_v); cudaFree(pr.d_cost);
@@ -813,7 +829,7 @@ struct Job {
 struct Plan {
   int L = 1, warps = 1, grid = 0;
   bool mv_global = false;  // Adam moments in global memory: the tile fits shared memory only that way
-  int feat = 0;            // optional terms of the problems: 0, FEAT_SELF, FEAT_KNOTS
+  int feat = 0;            // optional terms of the problems: 0, FEAT_SELF, FEAT_EXT
   size_t smem = 0;
   std::vector<ProbDesc> descs;
   std::vector<uint32_t> items;
@@ -998,6 +1014,7 @@ void tamp_default_options(tamp_options* o) {
   o->lr_joint = 1e-2f; o->lr_pos = 3e-3f; o->lr_yaw = 1e-2f;
   o->beta1 = 0.9f; o->beta2 = 0.999f; o->eps = 1e-8f;
   o->optimize_grasp = 1; o->scale_by_batch = 1; o->lanes = 0;
+  o->grasp_dof = 4;
 }
 
 tamp_status tamp_create_scene(const tamp_scene_desc* d, int device, void* stream, tamp_scene** out) {

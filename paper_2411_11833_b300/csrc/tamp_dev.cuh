@@ -49,6 +49,7 @@ constexpr int SURF_W = 8;
 enum ProbHdr {
   PH_D = 0, PH_K, PH_NT, PH_NCON, PH_GOAL_T, PH_NGOAL, PH_OFF_CFG, PH_OFF_ENV, PH_OFF_TERMS,
   PH_OFF_GOAL, PH_OFF_LR, PH_OFF_SAMP, PH_WORDS, PH_NSLOT, PH_OFF_SLOT, PH_NSEG, PH_OFF_SEG,
+  PH_GRASP6,                    // 1: grasps are (x, y, z, yaw, roll, pitch)
   PH_HDR_WORDS = 20
 };
 // Configuration kinds: a Pick's, a Place's, or a knot of the trajectory
@@ -76,8 +77,9 @@ constexpr int SEG_W = 8;
 enum SegField { SG_QA = 0, SG_QB, SG_QK, SG_M, SG_T };
 // Per iteration the optimisation kernel tabulates, for every particle of its
 // tile, (cos, sin) of each configuration's joint angles (plus the joint
-// offsets) followed by its grasp yaw: K x (n_joints + 1) entries, so that the
-// kinematics, the reverse sweep and Kin read them instead of evaluating them.
+// offsets) followed by its grasp yaw (and, with 6-DOF grasps, roll and pitch):
+// K x (n_joints + 1 (+ 2)) entries, so that the kinematics, the reverse sweep
+// and Kin read them instead of evaluating them.
 // The problem blob ends with the sampler's per-component records; the
 // optimisation kernel stages only the words before them (PH_OFF_SAMP).
 // A Place's CFreePlace spheres are split between the Place and the Pick right
@@ -133,10 +135,11 @@ struct LaunchArgs {
   int scratch_offset;                 // bytes from the start of dynamic shared memory to the warp scratch
   const int* stop;                    // optional: a non-zero value makes the launch return at once
   int mv_global;                      // 1: Adam moments used in place in global memory (not staged)
-  int feat;                           // the optional terms of the launch's problems: 0, FEAT_SELF, FEAT_KNOTS
+  int feat;                           // the optional terms of the launch's problems: 0, FEAT_SELF, FEAT_EXT
 };
-// Feature sets of the optimisation kernel's instantiations.
-enum KernelFeat { FEAT_SELF = 1, FEAT_KNOTS = 2 };
+// Feature sets of the optimisation kernel's instantiations: SelfCollision
+// alone, or knots / 6-DOF grasps (with or without SelfCollision).
+enum KernelFeat { FEAT_SELF = 1, FEAT_EXT = 2 };
 constexpr int ITEM_TILE_BITS = 20;
 
 }  // namespace tamp

@@ -458,6 +458,9 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   // a trajectory knot: no Kin, no grasp / containment term; the held box only on a MoveHold
   // (KN: the kernel is built for problems with knots; otherwise these are constants)
   const bool knot = KN && kind == CK_KNOT, hold = !KN || cf[CF_HOLD] != 0;
+  // 6-DOF grasps (extended instantiation only): G(g) = Trans Rz(yaw) Ry(pitch) Rx(roll) Rx(pi)
+  const bool g6 = KN && pb[PH_GRASP6] != 0;
+  const int ntg = nj + 1 + (g6 ? 2 : 0);
   // links of each piece, so that sphere batches spread evenly: the head also
   // has the held box (2 batches), the tail the placed box (1)
   const int n_head = NPIECE == 2 ? nj / 2 : max(0, (nj + 3) / 3 - 2);       // links of the head
@@ -468,7 +471,7 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   const float k0 = (sub == 0 && head && !knot) ? 1.f : 0.f;
 #define XV(c) X[(c) * PT + pl]
   // (cos, sin) of this configuration's joint angles, then of its grasp yaw
-  const float2* tg = trig + k * (nj + 1) * PT + pl;
+  const float2* tg = trig + k * ntg * PT + pl;
 #define TG(j) tg[(j) * PT]
 
   // ---------------- forward kinematics T_0 .. T_n (the tail stops at T_m)
@@ -504,6 +507,17 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   float F[3] = {0.f, 0.f, 0.f}, Mw[3] = {0.f, 0.f, 0.f}, gg[4] = {0.f, 0.f, 0.f, 0.f}, gp[3] = {0.f, 0.f, 0.f};
   float e_pos = 0.f, e_rot = 0.f;
   float rgx = 0.f, rgy = 0.f;
+  float rg[9];                       // R_G with 6-DOF grasps (top-down: from cgr, sgr)
+  float cth = 1.f, sth = 0.f;        // cos, sin of the grasp pitch
+  float g_roll = 0.f, g_pitch = 0.f; // gradients of the grasp roll and pitch
+  auto make_rg = [&]() {
+    const float2 r = TG(nj + 1), t = TG(nj + 2);
+    const float cph = r.x, sph = r.y;
+    cth = t.x; sth = t.y;
+    rg[0] = cgr * cth; rg[1] = fmaf(-cgr * sth, sph, sgr * cph); rg[2] = fmaf(-cgr * sth, cph, -sgr * sph);
+    rg[3] = sgr * cth; rg[4] = fmaf(-sgr * sth, sph, -cgr * cph); rg[5] = fmaf(-sgr * sth, cph, cgr * sph);
+    rg[6] = -sth; rg[7] = -cth * sph; rg[8] = -cth * cph;
+  };
   if (head && !knot) {
     const float pz = cff[CF_TZ];
     if (tsrc < 0) {
@@ -519,14 +533,26 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
     // yaw of the target frame: placement yaw + grasp yaw
     const float c2 = fmaf(cy, cgr, -sy * sgr), s2 = fmaf(sy, cgr, cy * sgr);
     const float ttx = px + rgx, tty = py + rgy, ttz = pz + gzv;
-    // M = Re^T R_tgt, R_tgt = [[c2, s2, 0], [s2, -c2, 0], [0, 0, -1]]
     float Mr[9];
+    if (g6) {
+      // M = Re^T R_tgt, R_tgt = Rz(placement yaw) R_G
+      make_rg();
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const float e0 = Re[i], e1 = Re[3 + i], e2 = Re[6 + i];
-      Mr[3 * i] = fmaf(e0, c2, e1 * s2);
-      Mr[3 * i + 1] = fmaf(e0, s2, -e1 * c2);
-      Mr[3 * i + 2] = -e2;
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const float t0 = fmaf(cy, rg[j], -sy * rg[3 + j]), t1 = fmaf(sy, rg[j], cy * rg[3 + j]);
+          Mr[3 * i + j] = fmaf(Re[i], t0, fmaf(Re[3 + i], t1, Re[6 + i] * rg[6 + j]));
+        }
+    } else {
+      // M = Re^T R_tgt, R_tgt = [[c2, s2, 0], [s2, -c2, 0], [0, 0, -1]]
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const float e0 = Re[i], e1 = Re[3 + i], e2 = Re[6 + i];
+        Mr[3 * i] = fmaf(e0, c2, e1 * s2);
+        Mr[3 * i + 1] = fmaf(e0, s2, -e1 * c2);
+        Mr[3 * i + 2] = -e2;
+      }
     }
     const float wx = Mr[7] - Mr[5], wy = Mr[2] - Mr[6], wz = Mr[3] - Mr[1];
     const float wn = sqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz)));
@@ -556,6 +582,11 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
     gg[1] = k0 * (-(-sy * fkx + cy * fky));
     gg[2] = k0 * (-fkz);
     gg[3] = k0 * ubz;
+    if (g6) {
+      // the target turns about R_P Rz(yaw) y (pitch) and R_P Rz(yaw) Ry(pitch) x (roll)
+      g_pitch = k0 * fmaf(-s2, ubx, c2 * uby);
+      g_roll = k0 * fmaf(c2 * cth, ubx, fmaf(s2 * cth, uby, -sth * ubz));
+    }
     gp[0] = k0 * (-fkx);
     gp[1] = k0 * (-fky);
     gp[2] = k0 * (fkx * rgy - fky * rgx + ubz);
@@ -563,6 +594,7 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
     gxv = XV(go); gyv = XV(go + 1); gzv = XV(go + 2);
     const float2 gcs = TG(nj);
     cgr = gcs.x; sgr = gcs.y;
+    if (g6) make_rg();
   }
   float J_hold = 0.f, J_place = 0.f;
   float gpc[3] = {0.f, 0.f, 0.f};  // Kin target / containment -> this configuration's placement
@@ -625,7 +657,13 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
         p = (s0 + s < lim) ? bloc[b * NBS + s0 + s] : make_float4(DUMMY_FAR, DUMMY_FAR, DUMMY_FAR, -1.f);
         if (phase == 0 && s0 + s < NBS) {
           const float vx = p.x - gxv, vy = p.y - gyv, vz = p.z - gzv;
-          const float wx = fmaf(cgr, vx, sgr * vy), wy = fmaf(sgr, vx, -cgr * vy), wz = -vz;
+          // R_G^T (l - g) (top-down R_G is symmetric)
+          float wx = fmaf(cgr, vx, sgr * vy), wy = fmaf(sgr, vx, -cgr * vy), wz = -vz;
+          if (g6) {
+            wx = fmaf(rg[0], vx, fmaf(rg[3], vy, rg[6] * vz));
+            wy = fmaf(rg[1], vx, fmaf(rg[4], vy, rg[7] * vz));
+            wz = fmaf(rg[2], vx, fmaf(rg[5], vy, rg[8] * vz));
+          }
           p.x = fmaf(tl[0], wx, fmaf(tl[1], wy, fmaf(tl[2], wz, tl[9])));
           p.y = fmaf(tl[3], wx, fmaf(tl[4], wy, fmaf(tl[5], wz, tl[10])));
           p.z = fmaf(tl[6], wx, fmaf(tl[7], wy, fmaf(tl[8], wz, tl[11])));
@@ -705,10 +743,24 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
             const float bx = fmaf(tl[0], ax, fmaf(tl[3], ay, tl[6] * az));
             const float by = fmaf(tl[1], ax, fmaf(tl[4], ay, tl[7] * az));
             const float bz = fmaf(tl[2], ax, fmaf(tl[5], ay, tl[8] * az));
-            const float Gx = fmaf(cgr, bx, sgr * by), Gy = fmaf(sgr, bx, -cgr * by), Gz = -bz;
+            float Gx = fmaf(cgr, bx, sgr * by), Gy = fmaf(sgr, bx, -cgr * by), Gz = -bz;
+            if (g6) {
+              Gx = fmaf(rg[0], bx, fmaf(rg[1], by, rg[2] * bz));
+              Gy = fmaf(rg[3], bx, fmaf(rg[4], by, rg[5] * bz));
+              Gz = fmaf(rg[6], bx, fmaf(rg[7], by, rg[8] * bz));
+            }
             const float4 lp = bloc[b * NBS + s0 + s];
+            const float vx = lp.x - gxv, vy = lp.y - gyv, vz = lp.z - gzv;
             gg[0] -= Gx; gg[1] -= Gy; gg[2] -= Gz;
-            gg[3] -= Gy * (lp.x - gxv) - Gx * (lp.y - gyv);
+            gg[3] -= Gy * vx - Gx * vy;
+            if (g6) {
+              // -(a x (l - g)) . G for the pitch axis a = Rz(yaw) y and the roll axis Rz(yaw) Ry(pitch) x
+              const float ptx = cgr * vz, pty = sgr * vz, ptz = fmaf(-sgr, vy, -cgr * vx);  // (-s, c, 0) x v
+              g_pitch -= fmaf(ptx, Gx, fmaf(pty, Gy, ptz * Gz));
+              const float ax_ = cgr * cth, ay_ = sgr * cth, az_ = -sth;
+              const float rx = fmaf(ay_, vz, -az_ * vy), ry = fmaf(az_, vx, -ax_ * vz), rz = fmaf(ax_, vy, -ay_ * vx);
+              g_roll -= fmaf(rx, Gx, fmaf(ry, Gy, rz * Gz));
+            }
           }
         }
       }
@@ -723,6 +775,10 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
     J_place += __shfl_xor_sync(0xffffffffu, J_place, m);
 #pragma unroll
     for (int i = 0; i < 4; ++i) gg[i] += __shfl_xor_sync(0xffffffffu, gg[i], m);
+    if (g6) {
+      g_roll += __shfl_xor_sync(0xffffffffu, g_roll, m);
+      g_pitch += __shfl_xor_sync(0xffffffffu, g_pitch, m);
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i) gpc[i] += __shfl_xor_sync(0xffffffffu, gpc[i], m);
 #pragma unroll
@@ -770,9 +826,14 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   Tm[cf[CF_T_JL] * PT + pl] = jl;
   if (knot) {
     // a MoveHold knot's held-box collisions move the grasp
-    if (hold)
+    if (hold) {
 #pragma unroll
       for (int i = 0; i < 4; ++i) atomicAdd(&G[(go + i) * PT + pl], gg[i]);
+      if (g6) {
+        atomicAdd(&G[(go + 4) * PT + pl], g_roll);
+        atomicAdd(&G[(go + 5) * PT + pl], g_pitch);
+      }
+    }
     return;
   }
   Tm[cf[CF_T_KP] * PT + pl] = e_pos;
@@ -781,7 +842,7 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   if (kind == CK_PICK) {
     // Grasp(o, g): bound distance of g_xyz to [-hx, hx] x [-hy, hy] x [hz - 0.02, hz]
     const float v[3] = {gxv, gyv, gzv};
-    const float lo[3] = {-br[0], -br[1], br[2] - 0.02f};
+    const float lo[3] = {-br[0], -br[1], g6 ? -br[2] : br[2] - 0.02f};  // 6-DOF: the whole box
     const float hi[3] = {br[0], br[1], br[2]};
     float gr[3];
     const float d = bound_dist<3>(v, lo, hi, gr);
@@ -812,6 +873,10 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   // grasp gradient (shared by the Pick and the Place that hold the same grasp)
 #pragma unroll
   for (int i = 0; i < 4; ++i) atomicAdd(&G[(go + i) * PT + pl], gg[i]);
+  if (g6) {
+    atomicAdd(&G[(go + 4) * PT + pl], g_roll);
+    atomicAdd(&G[(go + 5) * PT + pl], g_pitch);
+  }
   // placement gradient: Kin target if the target is a variable, plus CFreePlace/containment
   const int psrc = cf[CF_PSRC];
   if (tsrc >= 0) {
@@ -949,15 +1014,26 @@ __device__ __noinline__ void eval_self(const uint32_t* __restrict__ sc, const ui
     const int t_self = cf[CF_T_SELF], qo = cf[CF_QOFF], go = cf[CF_GOFF], box = cf[CF_BOX];
     const bool hold = cf[CF_HOLD] != 0;
     const float w = tw(pb + pb[PH_OFF_TERMS], t_self);
-    const float2* tg = trig + k * (nj + 1) * PT + pl;
+    const bool g6 = pb[PH_GRASP6] != 0;
+    const float2* tg = trig + k * (nj + 1 + (g6 ? 2 : 0)) * PT + pl;
     for (int i = 0; i < 6 * nj; ++i) acc[i * 32 + lane] = 0.f;
     float gxv = 0.f, gyv = 0.f, gzv = 0.f, cgr = 1.f, sgr = 0.f;
+    // R_G (object frame -> gripper target), top-down unless 6-DOF; the pitch and roll axes
+    float rg[9] = {1.f, 0.f, 0.f, 0.f, -1.f, 0.f, 0.f, 0.f, -1.f}, cth = 1.f, sth = 0.f;
     if (hold) {
       gxv = X[go * PT + pl]; gyv = X[(go + 1) * PT + pl]; gzv = X[(go + 2) * PT + pl];
       const float2 c = tg[nj * PT];
       cgr = c.x; sgr = c.y;
+      float cph = 1.f, sph = 0.f;
+      if (g6) {
+        const float2 r = tg[(nj + 1) * PT], t = tg[(nj + 2) * PT];
+        cph = r.x; sph = r.y; cth = t.x; sth = t.y;
+      }
+      rg[0] = cgr * cth; rg[1] = fmaf(-cgr * sth, sph, sgr * cph); rg[2] = fmaf(-cgr * sth, cph, -sgr * sph);
+      rg[3] = sgr * cth; rg[4] = fmaf(-sgr * sth, sph, -cgr * cph); rg[5] = fmaf(-sgr * sth, cph, cgr * sph);
+      rg[6] = -sth; rg[7] = -cth * sph; rg[8] = -cth * cph;
     }
-    float J = 0.f, gg[4] = {0.f, 0.f, 0.f, 0.f};
+    float J = 0.f, gg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     // adds w * dpen/dc (g) at centre c to the wrench of link l (l = 0: the base, no torque)
     auto add = [&](int l, float cx, float cy, float cz, float gx, float gy, float gz) {
       if (l == 0) return;
@@ -1044,7 +1120,9 @@ __device__ __noinline__ void eval_self(const uint32_t* __restrict__ sc, const ui
             // bounding sphere (radius about the box centre) against link j's batch
             {
               const float vx = -gxv, vy = -gyv, vz = -gzv;
-              const float wx = fmaf(cgr, vx, sgr * vy), wy = fmaf(sgr, vx, -cgr * vy), wz = -vz;
+              const float wx = fmaf(rg[0], vx, fmaf(rg[3], vy, rg[6] * vz));
+              const float wy = fmaf(rg[1], vx, fmaf(rg[4], vy, rg[7] * vz));
+              const float wz = fmaf(rg[2], vx, fmaf(rg[5], vy, rg[8] * vz));
               const float px = fmaf(tl[0], wx, fmaf(tl[1], wy, fmaf(tl[2], wz, tl[9])));
               const float py = fmaf(tl[3], wx, fmaf(tl[4], wy, fmaf(tl[5], wz, tl[10])));
               const float pz = fmaf(tl[6], wx, fmaf(tl[7], wy, fmaf(tl[8], wz, tl[11])));
@@ -1057,7 +1135,9 @@ __device__ __noinline__ void eval_self(const uint32_t* __restrict__ sc, const ui
             for (int e = 0; e < NBS; ++e) {
               const float4 l = bloc[box * NBS + e];
               const float vx = l.x - gxv, vy = l.y - gyv, vz = l.z - gzv;
-              const float wx = fmaf(cgr, vx, sgr * vy), wy = fmaf(sgr, vx, -cgr * vy), wz = -vz;
+              const float wx = fmaf(rg[0], vx, fmaf(rg[3], vy, rg[6] * vz));
+              const float wy = fmaf(rg[1], vx, fmaf(rg[4], vy, rg[7] * vz));
+              const float wz = fmaf(rg[2], vx, fmaf(rg[5], vy, rg[8] * vz));
               const float px = fmaf(tl[0], wx, fmaf(tl[1], wy, fmaf(tl[2], wz, tl[9])));
               const float py = fmaf(tl[3], wx, fmaf(tl[4], wy, fmaf(tl[5], wz, tl[10])));
               const float pz = fmaf(tl[6], wx, fmaf(tl[7], wy, fmaf(tl[8], wz, tl[11])));
@@ -1072,9 +1152,17 @@ __device__ __noinline__ void eval_self(const uint32_t* __restrict__ sc, const ui
               const float bx = fmaf(tl[0], ax, fmaf(tl[3], ay, tl[6] * az));
               const float by = fmaf(tl[1], ax, fmaf(tl[4], ay, tl[7] * az));
               const float bz = fmaf(tl[2], ax, fmaf(tl[5], ay, tl[8] * az));
-              const float Gx = fmaf(cgr, bx, sgr * by), Gy = fmaf(sgr, bx, -cgr * by), Gz = -bz;
+              const float Gx = fmaf(rg[0], bx, fmaf(rg[1], by, rg[2] * bz));
+              const float Gy = fmaf(rg[3], bx, fmaf(rg[4], by, rg[5] * bz));
+              const float Gz = fmaf(rg[6], bx, fmaf(rg[7], by, rg[8] * bz));
               gg[0] -= Gx; gg[1] -= Gy; gg[2] -= Gz;
               gg[3] -= Gy * vx - Gx * vy;
+              if (g6) {  // -(a x (l - g)) . G for the pitch and roll axes
+                gg[5] -= fmaf(cgr * vz, Gx, fmaf(sgr * vz, Gy, fmaf(-sgr, vy, -cgr * vx) * Gz));
+                const float ax_ = cgr * cth, ay_ = sgr * cth, az_ = -sth;
+                gg[4] -= fmaf(fmaf(ay_, vz, -az_ * vy), Gx, fmaf(fmaf(az_, vx, -ax_ * vz), Gy,
+                                                                 fmaf(ax_, vy, -ay_ * vx) * Gz));
+              }
             }
           }
         }
@@ -1082,8 +1170,7 @@ __device__ __noinline__ void eval_self(const uint32_t* __restrict__ sc, const ui
     }
     Tm[t_self * PT + pl] = J;
     if (hold)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) atomicAdd(&G[(go + i) * PT + pl], gg[i]);
+      for (int i = 0; i < (g6 ? 6 : 4); ++i) atomicAdd(&G[(go + i) * PT + pl], gg[i]);
     // torques: from T_n down, the wrench of links >= l at joint l
     float R[9], t[3];
 #pragma unroll
@@ -1122,7 +1209,7 @@ __device__ __noinline__ void eval_self(const uint32_t* __restrict__ sc, const ui
 // One tile of PT particles of one problem: load it, run n_steps fused
 // iterations (evaluation + adjoint, Eq. 3 check, Adam) and one final check,
 // write it back.  All threads of the CTA call this together.
-// FEAT: the optional terms the kernel is built for -- FEAT_KNOTS (knot
+// FEAT: the optional terms the kernel is built for -- FEAT_EXT (knot
 // configurations and TrajLength, with self-collision), FEAT_SELF (SelfCollision
 // only), 0 (neither: the configuration code of every other skeleton).
 template <int L, int FEAT>
@@ -1145,7 +1232,7 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
   const int NSLOT = s_pb[PH_NSLOT];
   // (cos, sin) of every configuration's joint angles and grasp yaw at the current iterate
   float2* strig = reinterpret_cast<float2*>(splace + NSLOT * PT);
-  const int nj = s_sc[SH_NJ], NA = K * (nj + 1);
+  const int nj = s_sc[SH_NJ], ntg = nj + 1 + ((FEAT == FEAT_EXT && s_pb[PH_GRASP6] != 0) ? 2 : 0), NA = K * ntg;
   const float* arm = reinterpret_cast<const float*>(s_sc + s_sc[SH_OFF_ARM]);
   const uint32_t* cfg0 = s_pb + s_pb[PH_OFF_CFG];
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -1182,7 +1269,7 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
   // configurations first (their environments hold more placed boxes), then the
   // goal cost; warps pull them from a counter so that they finish together
   __shared__ int s_next;
-  constexpr bool KN = FEAT == FEAT_KNOTS, SC = FEAT != 0;
+  constexpr bool KN = FEAT == FEAT_EXT, SC = FEAT != 0;
   const bool has_goal = s_pb[PH_GOAL_T] != 0xffffffffu, has_traj = KN && s_pb[PH_NSEG] != 0;
   // SelfCollision: one more item per configuration (after the pieces)
   const int n_self = (SC && static_cast<int>(s_pb[s_pb[PH_OFF_CFG] + CF_T_SELF]) >= 0) ? K : 0;
@@ -1202,10 +1289,11 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
     }
     for (int i = tid; i < NA * PT; i += nthr) {
       const int a = i / PT, p = i - a * PT;
-      const int k = a / (nj + 1), j = a - k * (nj + 1);
+      const int k = a / ntg, j = a - k * ntg;
       const int* cf = reinterpret_cast<const int*>(cfg0 + k * CFG_W);
+      // joints, then the grasp yaw (and roll, pitch): components go + 3 (+ 4, 5)
       const float ang = j < nj ? sx[(cf[CF_QOFF] + j) * PT + p] + arm[24 + j * ARM_JW + 4]
-                               : sx[(cf[CF_GOFF] + 3) * PT + p];
+                               : sx[(cf[CF_GOFF] + 3 + (j - nj)) * PT + p];
       float sn, cs;
       sincosf(ang, &sn, &cs);
       strig[i] = make_float2(cs, sn);
@@ -1554,6 +1642,13 @@ __global__ void __launch_bounds__(128) ik_configs_kernel(const uint32_t* __restr
       bx = XG(tsrc); by = XG(tsrc + 1); bz = cff[CF_TZ]; byaw = XG(tsrc + 2);
     }
     const float gx = XG(go), gy = XG(go + 1), gz = XG(go + 2);
+    // 6-DOF grasps: roll and pitch stay as sampled
+    const bool g6 = pb[PH_GRASP6] != 0;
+    float cph = 1.f, sph = 0.f, cth = 1.f, sth = 0.f;
+    if (g6) {
+      sincosf(XG(go + 4), &sph, &cph);
+      sincosf(XG(go + 5), &sth, &cth);
+    }
     const int yo = place ? tsrc + 2 : go + 3;
     float y = XG(yo);
     float q[MAXJ];
@@ -1567,7 +1662,21 @@ __global__ void __launch_bounds__(128) ik_configs_kernel(const uint32_t* __restr
       sincosf(pyaw, &sp, &cp);
       sincosf(phi, &sf, &cfv);
       const float tx = bx + fmaf(cp, gx, -sp * gy), ty = by + fmaf(sp, gx, cp * gy), tz = bz + gz;
-      const float Rt[9] = {cfv, sf, 0.f, sf, -cfv, 0.f, 0.f, 0.f, -1.f};
+      float Rt[9] = {cfv, sf, 0.f, sf, -cfv, 0.f, 0.f, 0.f, -1.f};
+      if (g6) {
+        // R* = Rz(box yaw) R_G, R_G = Rz(grasp yaw) Ry(pitch) Rx(roll) Rx(pi)
+        float sgy, cgy;
+        sincosf(place ? XG(go + 3) : y, &sgy, &cgy);
+        const float rg[9] = {cgy * cth, fmaf(-cgy * sth, sph, sgy * cph), fmaf(-cgy * sth, cph, -sgy * sph),
+                             sgy * cth, fmaf(-sgy * sth, sph, -cgy * cph), fmaf(-sgy * sth, cph, cgy * sph),
+                             -sth, -cth * sph, -cth * cph};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          Rt[j] = fmaf(cp, rg[j], -sp * rg[3 + j]);
+          Rt[3 + j] = fmaf(sp, rg[j], cp * rg[3 + j]);
+          Rt[6 + j] = rg[6 + j];
+        }
+      }
       // forward kinematics, keeping each joint's axis and origin
       float R[9], t[3], oz[MAXJ][6];
 #pragma unroll
@@ -1766,7 +1875,7 @@ cudaError_t launch_chunk_control(int* t_dev, const int* const* first_iters, int 
 
 // ------------------------------------------------------------------ launchers
 // largest dynamic shared-memory size enabled so far for optimize_kernel<1,2,4,8>
-// per feature set (0, FEAT_SELF, FEAT_KNOTS)
+// per feature set (0, FEAT_SELF, FEAT_EXT)
 static size_t g_smem_enabled[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
 static int lane_slot(int L) { return L == 1 ? 0 : (L == 2 ? 1 : (L == 4 ? 2 : 3)); }
 
@@ -1794,7 +1903,7 @@ static cudaError_t launch_opt(const LaunchArgs& a, int warps, int grid, size_t s
   switch (a.feat) {
     case 0: return launch_feat<L, 0>(a, warps, grid, smem, st);
     case FEAT_SELF: return launch_feat<L, FEAT_SELF>(a, warps, grid, smem, st);
-    case FEAT_KNOTS: return launch_feat<L, FEAT_KNOTS>(a, warps, grid, smem, st);
+    case FEAT_EXT: return launch_feat<L, FEAT_EXT>(a, warps, grid, smem, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1815,7 +1924,7 @@ template <int L>
 static cudaError_t set_smem_all(size_t smem) {
   cudaError_t e = set_smem<L, 0>(smem);
   if (e == cudaSuccess) e = set_smem<L, FEAT_SELF>(smem);
-  if (e == cudaSuccess) e = set_smem<L, FEAT_KNOTS>(smem);
+  if (e == cudaSuccess) e = set_smem<L, FEAT_EXT>(smem);
   return e;
 }
 

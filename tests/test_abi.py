@@ -50,7 +50,7 @@ def test_default_options_are_the_papers(lib):
     assert list(o.w) == pytest.approx([1.0, 5.0, 1.0, 2.0, 1.0, 1.0, 1.0, 0.25, 1.0, 0.01, 1.0])
     assert list(o.tol)[:7] == pytest.approx([5e-3, 0.05, 1e-3, 1e-3, 1e-3, 1e-3, 0.0])
     assert o.tol[8] == pytest.approx(1e-3) and o.tol[10] == 0.0
-    assert o.n_knots == 0 and o.self_collision == 0
+    assert o.n_knots == 0 and o.self_collision == 0 and o.grasp_dof == 4
     assert o.beta1 == pytest.approx(0.9) and o.beta2 == pytest.approx(0.999)
 
 

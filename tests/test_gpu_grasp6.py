@@ -1,0 +1,79 @@
+"""6-DOF grasps through the C ABI (options grasp_dof = 6; Sec. VIII setup:
+grasps are top-down 4-DOF or 6-DOF poses) against the FP64 oracle, with the
+tolerances of tests/parity.py and the IK-sampler bar of tests/test_gpu_ik.py."""
+import numpy as np
+import pytest
+import torch
+
+import scenegen as sg
+from oracle import ik, philox
+from oracle.problem import Options, Problem
+from tests.parity import compare_eval
+
+from test_gpu_ik import _compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2411_11833_b300.build import build_library
+    build_library()
+    import paper_2411_11833_b300 as p
+    torch.cuda.set_device(0)
+    return p
+
+
+@pytest.mark.parametrize("lanes,m,selfc", [(1, 0, 0), (2, 0, 0), (1, 1, 1)])
+def test_eval_parity_with_six_dof_grasps(pkg, lanes, m, selfc):
+    sc, acts = sg.robot_packing_problem(21002, n_boxes=2)
+    pr = Problem(sc, acts, Options(grasp_dof=6, n_knots=m, self_collision=bool(selfc)))
+    X = pr.interpolate_knots(philox.sample_uniform(pr, 70, 61))
+    scene = pkg.Scene(sc)
+    pid = scene.set_skeleton(acts, pkg.default_options(lanes=lanes, grasp_dof=6, n_knots=m, self_collision=selfc))
+    D, _, kinds = scene.problem_info(pid)
+    assert D == pr.D and kinds == [t.kind for t in pr.terms]
+    out = scene.eval(pid, torch.tensor(np.ascontiguousarray(X.T), dtype=torch.float32, device="cuda"))
+    torch.cuda.synchronize()
+    scene.close()
+    print(compare_eval(pr, X, *out, label=f"grasp6 L={lanes} knots={m} self={selfc}"))
+
+
+def test_samplers_with_six_dof_grasps(pkg):
+    sc, acts = sg.robot_packing_problem(21002, n_boxes=2)
+    pr = Problem(sc, acts, Options(grasp_dof=6))
+    scene = pkg.Scene(sc)
+    pid = scene.set_skeleton(acts, pkg.default_options(grasp_dof=6))
+    n, seed = 384, 23
+    scene.sample(pid, n, seed)
+    x = scene.get_particles(pid)[0].T.astype(np.float64)
+    assert np.abs(x - philox.sample_uniform(pr, n, seed)).max() < 2e-6
+    scene.sample(pid, n, seed, sampler=2)
+    x = scene.get_particles(pid)[0].T.astype(np.float64)
+    _compare(pr, x, ik.ik_configurations(pr, philox.sample_uniform(pr, n, seed)))
+    scene.close()
+
+
+def test_adam_step_with_six_dof_grasps_matches_oracle(pkg):
+    sc, acts = sg.robot_packing_problem(21003, n_boxes=2)
+    pr = Problem(sc, acts, Options(grasp_dof=6))
+    P = 80
+    X = philox.sample_uniform(pr, P, 63)
+    m0, v0 = sg.random_adam_state(P, pr.D, seed=64)
+    scene = pkg.Scene(sc)
+    pid = scene.set_skeleton(acts, pkg.default_options(grasp_dof=6))
+    scene.set_particles(pid, X.T.astype(np.float32), m0.T.astype(np.float32), v0.T.astype(np.float32), 2)
+    scene.optimize(pid, 1)
+    x1, m1, _, t1 = scene.get_particles(pid)
+    scene.close()
+    assert t1 == 3
+    Xt = torch.tensor(X.astype(np.float32).astype(np.float64))
+    _, g = pr.gradient(Xt)
+    xr, mr, _ = pr.adam_step(Xt, torch.tensor(m0.astype(np.float32).astype(np.float64)),
+                             torch.tensor(v0.astype(np.float32).astype(np.float64)), 3, g, P)
+    keep = pr.kink_margin(Xt).numpy() > 1e-4
+    assert keep.mean() > 0.5
+    assert np.abs(m1.T - mr.numpy())[keep].max() <= 1e-3 * np.abs(mr.numpy()[keep]).max() + 1e-9
+    step_g = (x1.T - X.astype(np.float32))[keep]
+    step_r = (xr.numpy() - Xt.numpy())[keep]
+    assert np.abs(step_g - step_r).max() <= 1e-3 * np.abs(step_r).max() + 2e-6
