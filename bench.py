@@ -36,7 +36,7 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM traffic of one optimize_kernel launch on this workload, from an ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the
 # kernel source whose hash is recorded with it.
-TRAFFIC = {"source_sha": "8d40033a78366cf8", "bytes_per_launch": 6350336}
+TRAFFIC = {"source_sha": "2ca639bb3eacc44e", "bytes_per_launch": 6319360}
 
 
 def kernel_source_sha() -> str:
@@ -194,7 +194,7 @@ def job_throughput(step_ms, world: int, units_per_rank_step: int, device=None):
     return world * units_per_rank_step * len(step_ms) / total_s, total_s
 
 
-def measure_ttfs(pkg, sg, seeds=range(3001, 3009), budget_iters=1000):
+def measure_ttfs(pkg, sg, seeds=range(3001, 3009), budget_iters=1000, harvest_scenes=128, train_steps=1500):
     """Time to the first satisfying particle on obstructed stacking (one fixed
     7-DOF arm; 2-4 blockers cover B's top; 16 candidate skeletons of 2-8
     actions with batches of 1024-8192): the plain form -- Algorithm 1 one
@@ -209,9 +209,9 @@ def measure_ttfs(pkg, sg, seeds=range(3001, 3009), budget_iters=1000):
 
     from paper_2411_11833_b300 import proposal, search
     t0 = time.perf_counter()
-    F, Y, M, st = proposal.harvest([sg.robot_plain_problem(10000 + k) for k in range(128)], n_particles=4096,
-                                   iters=200, chunk=50, sampler=2, max_rows_per_problem=256)
-    net, losses = proposal.train(F, Y, M, steps=1500, batch=4096, lr=1e-3, log_every=1499)
+    F, Y, M, st = proposal.harvest([sg.robot_plain_problem(10000 + k) for k in range(harvest_scenes)],
+                                   n_particles=4096, iters=200, chunk=50, sampler=2, max_rows_per_problem=256)
+    net, losses = proposal.train(F, Y, M, steps=train_steps, batch=4096, lr=1e-3, log_every=max(1, train_steps - 1))
     train_s = time.perf_counter() - t0
     forms = {"plain_sequential_uniform": (0, False), "batched_ik": (2, True), "batched_learned_ik": (3, True)}
     res = {k: [] for k in forms}
@@ -221,8 +221,7 @@ def measure_ttfs(pkg, sg, seeds=range(3001, 3009), budget_iters=1000):
             scene = pkg.Scene(sc)
             if sampler & 1:
                 scene.set_proposal(net)
-            be = search._Backend(scene)
-            be.sample = lambda pid, n, sd, s=sampler: scene.sample(pid, n, sd, s)
+            be = search._Backend(scene, sampler=sampler)
             torch.cuda.synchronize()
             t1 = time.perf_counter()
             # both forms check for a satisfying particle every 10 iterations
@@ -238,7 +237,7 @@ def measure_ttfs(pkg, sg, seeds=range(3001, 3009), budget_iters=1000):
     out = {"workload": "obstructed stacking: fixed 7-DOF arm, A on B under 2-4 blockers, 16 candidate skeletons "
                        "of 2-8 actions, batches of 1024-8192, 16 cuboids",
            "seeds": list(seeds), "budget_iters_per_skeleton": budget_iters, "unit": "s",
-           "network": {"harvest_particles": st["particles"], "harvest_scenes": st["problems"], "train_steps": 1500,
+           "network": {"harvest_particles": st["particles"], "harvest_scenes": st["problems"], "train_steps": train_steps,
                        "final_nll": round(losses[-1][1], 4), "harvest_and_train_s": round(train_s, 2)},
            "forms": {}}
     for name, rows in res.items():
