@@ -73,3 +73,27 @@ def test_gradient_with_six_dof_grasps_matches_central_differences():
     x = x[pr.kink_margin(x) > 1e-4][:4]
     assert x.shape[0] >= 2
     assert _fd_error(pr, x) < 1e-6
+
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    """Plausible slips in the 6-DOF grasp make one of the pins above fail."""
+    import pytest
+    orig = G.grasp_pose6
+
+    # 1. Euler factors in the other order (roll before pitch)
+    def swapped(gx, gy, gz, gyaw, groll, gpitch):
+        return (G.translation(gx, gy, gz) @ G.rot_z(gyaw) @ G.rot_x(groll) @ G.rot_y(gpitch)
+                @ G.rot_x(torch.full_like(torch.as_tensor(gx, dtype=DT), math.pi)))
+    monkeypatch.setattr(G, "grasp_pose6", swapped)
+    with pytest.raises(AssertionError):
+        test_pose_is_the_euler_composition_and_reduces_to_top_down()
+    with pytest.raises(AssertionError):
+        test_grasp_read_from_the_end_effector_satisfies_kin()
+
+    # 2. the gripper not flipped to point down
+    def unflipped(gx, gy, gz, gyaw, groll, gpitch):
+        return G.translation(gx, gy, gz) @ G.rot_z(gyaw) @ G.rot_y(gpitch) @ G.rot_x(groll)
+    monkeypatch.setattr(G, "grasp_pose6", unflipped)
+    with pytest.raises(AssertionError):
+        test_grasp_read_from_the_end_effector_satisfies_kin()
+    monkeypatch.setattr(G, "grasp_pose6", orig)

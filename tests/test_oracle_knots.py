@@ -99,3 +99,30 @@ def test_gradient_with_knots_matches_central_differences():
     x = x[pr.kink_margin(x) > 1e-4][:4]
     assert x.shape[0] >= 2
     assert _fd_error(pr, x) < 1e-6
+
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    """Plausible slips in the knot terms make one of the pins above fail."""
+    import pytest
+    from oracle import problem as PM
+    orig_len, orig_walk = PM.Problem._traj_length, PM.Problem._walk
+
+    # 1. TrajLength without its last edge (the knots' end configuration dropped)
+    def len_short(self, seg, x):
+        w = self._waypoints(seg, x)[:-1]
+        return sum(PM.G.norm(w[i + 1] - w[i]) for i in range(len(w) - 1))
+    monkeypatch.setattr(PM.Problem, "_traj_length", len_short)
+    with pytest.raises(AssertionError):
+        test_straight_knots_give_the_straight_line_length()
+    monkeypatch.setattr(PM.Problem, "_traj_length", orig_len)
+
+    # 2. a MoveFree knot that does not see the box just placed
+    def walk_blind(self):
+        orig_walk(self)
+        for c in self.configs:
+            if c["kind"] == KNOT and c["box"] < 0:
+                c["env"] = [(j, src) for j, src in c["env"] if src[0] == "init"]
+    monkeypatch.setattr(PM.Problem, "_walk", walk_blind)
+    with pytest.raises(AssertionError):
+        test_knots_sit_before_the_action_they_lead_to()
+    monkeypatch.setattr(PM.Problem, "_walk", orig_walk)

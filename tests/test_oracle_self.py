@@ -83,3 +83,28 @@ def test_gradient_with_self_collision_matches_central_differences():
     x = x[torch.as_tensor(active) & (pr.kink_margin(x) > 1e-4)][:4]
     assert x.shape[0] >= 2
     assert _fd_error(pr, x) < 1e-6
+
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    """Plausible slips in SelfCollision make one of the pins above fail."""
+    import pytest
+    from oracle import problem as PM
+    orig_pairs, orig_pen = PM.Problem._self_pairs, PM.Problem._self_penetration
+
+    # 1. adjacent links counted, and links that touch at q = 0 not ignored
+    def pairs_all(self):
+        orig_pairs(self)
+        links = np.asarray(self.sc.sphere_link)
+        self.self_mask = links[:, None] > links[None, :]
+    monkeypatch.setattr(PM.Problem, "_self_pairs", pairs_all)
+    with pytest.raises(AssertionError):
+        test_no_self_collision_at_the_reference_configuration()
+    monkeypatch.setattr(PM.Problem, "_self_pairs", orig_pairs)
+
+    # 2. one radius instead of the sum of the pair's radii
+    def pen_one_radius(self, c, r):
+        return orig_pen(self, c, r * 0.5) * 2.0
+    monkeypatch.setattr(PM.Problem, "_self_penetration", pen_one_radius)
+    with pytest.raises(AssertionError):
+        test_folded_planar_arm_penetration_is_the_closed_form()
+    monkeypatch.setattr(PM.Problem, "_self_penetration", orig_pen)
