@@ -637,9 +637,12 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
   std::vector<uint32_t>& v = pr.blob;
   v.assign(PH_HDR_WORDS, 0);
   v[PH_OFF_CFG] = static_cast<uint32_t>(v.size());
-  int env_count = 0;
+  int env_count = 0, n_tab = 0;
   for (const Cfg& c : cfgs) {
     uint32_t rec[CFG_W] = {0};
+    // knots have no row in the kernel's table: with several knots per motion
+    // the table would crowd the particle tile out of shared memory
+    rec[CF_TG] = c.kind == CK_KNOT ? static_cast<uint32_t>(-1) : static_cast<uint32_t>(n_tab++);
     rec[CF_KIND] = c.kind; rec[CF_BOX] = c.box; rec[CF_QOFF] = c.qo; rec[CF_GOFF] = c.go;
     rec[CF_TSRC] = static_cast<uint32_t>(c.tsrc); rec[CF_SURF] = static_cast<uint32_t>(c.surf);
     rec[CF_NENV] = static_cast<uint32_t>(c.env.size()); rec[CF_ENVOFF] = static_cast<uint32_t>(env_count);
@@ -738,6 +741,11 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
     v.insert(v.end(), rec, rec + SEG_W);
   }
   align4(v);
+  v[PH_OFF_TAB] = static_cast<uint32_t>(v.size());
+  v[PH_NTAB] = static_cast<uint32_t>(n_tab);
+  for (int k = 0; k < pr.K; ++k)
+    if (cfgs[k].kind != CK_KNOT) v.push_back(static_cast<uint32_t>(k));
+  align4(v);
   // the sampler's records last: the optimisation kernel stages the words before them
   v[PH_OFF_SAMP] = static_cast<uint32_t>(v.size());
   pr.opt_words = static_cast<int>(v.size());
@@ -754,7 +762,7 @@ tamp_status compile_problem(tamp_scene* s, const tamp_action* acts, int n, const
     v.push_back(static_cast<uint32_t>(sp.surf));
   }
   align4(v);
-  pr.NANG = pr.K * (nj + 1 + (g6 ? 2 : 0));
+  pr.NANG = n_tab * (nj + 1 + (g6 ? 2 : 0));
   pr.grasp6 = g6;
   pr.NSLOT = static_cast<int>(slots.size());
   v[PH_NSLOT] = static_cast<uint32_t>(pr.NSLOT);
@@ -779,10 +787,11 @@ int preferred_lanes(int requested, long total_particles) {
   return total_particles >= 148L * 16 ? 1 : (total_particles >= 148L * 8 ? 2 : 4);
 }
 
-// The kernel instantiation a problem needs: knots or 6-DOF grasps (with or
-// without self-collision), self-collision only, or neither.
+// The kernel instantiation a problem needs: knots (with or without 6-DOF
+// grasps and self-collision), 6-DOF grasps (with or without self-collision),
+// self-collision only, or none of them.
 int problem_feat(const Problem& pr) {
-  return (pr.n_seg > 0 || pr.grasp6) ? FEAT_EXT : (pr.self ? FEAT_SELF : 0);
+  return pr.n_seg > 0 ? FEAT_KNOT : (pr.grasp6 ? FEAT_EXT : (pr.self ? FEAT_SELF : 0));
 }
 
 void free_batch(Problem& pr) {
@@ -829,7 +838,7 @@ struct Job {
 struct Plan {
   int L = 1, warps = 1, grid = 0;
   bool mv_global = false;  // Adam moments in global memory: the tile fits shared memory only that way
-  int feat = 0;            // optional terms of the problems: 0, FEAT_SELF, FEAT_EXT
+  int feat = 0;            // optional terms of the problems: 0 or a KernelFeat (the largest set a problem needs)
   size_t smem = 0;
   std::vector<ProbDesc> descs;
   std::vector<uint32_t> items;

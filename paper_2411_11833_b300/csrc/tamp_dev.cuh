@@ -50,6 +50,7 @@ enum ProbHdr {
   PH_D = 0, PH_K, PH_NT, PH_NCON, PH_GOAL_T, PH_NGOAL, PH_OFF_CFG, PH_OFF_ENV, PH_OFF_TERMS,
   PH_OFF_GOAL, PH_OFF_LR, PH_OFF_SAMP, PH_WORDS, PH_NSLOT, PH_OFF_SLOT, PH_NSEG, PH_OFF_SEG,
   PH_GRASP6,                    // 1: grasps are (x, y, z, yaw, roll, pitch)
+  PH_NTAB, PH_OFF_TAB,          // configurations with rows in the per-iteration (cos, sin) table: count, list
   PH_HDR_WORDS = 20
 };
 // Configuration kinds: a Pick's, a Place's, or a knot of the trajectory
@@ -68,7 +69,9 @@ enum CfgField {
   CF_CP_SLOT,                   // placement slot of CF_CP_SRC (-1: none)
   CF_TCOS, CF_TSIN,             // floats: cos, sin of CF_TYAW
   CF_HOLD,                      // 1: the hand holds box CF_BOX with the grasp at CF_GOFF (Pick, Place, MoveHold knot)
-  CF_T_SELF                     // SelfCollision term index (-1: none)
+  CF_T_SELF,                    // SelfCollision term index (-1: none)
+  CF_TG                         // row of the per-iteration (cos, sin) table (-1: a knot, whose angles
+                                // the kernel computes where it needs them)
 };
 // Motion segments between consecutive Pick/Place configurations (only with
 // knots): q offsets of the start and end configurations, of the first knot
@@ -135,11 +138,12 @@ struct LaunchArgs {
   int scratch_offset;                 // bytes from the start of dynamic shared memory to the warp scratch
   const int* stop;                    // optional: a non-zero value makes the launch return at once
   int mv_global;                      // 1: Adam moments used in place in global memory (not staged)
-  int feat;                           // the optional terms of the launch's problems: 0, FEAT_SELF, FEAT_EXT
+  int feat;                           // the optional terms of the launch's problems: 0 or a KernelFeat
 };
 // Feature sets of the optimisation kernel's instantiations: SelfCollision
-// alone, or knots / 6-DOF grasps (with or without SelfCollision).
-enum KernelFeat { FEAT_SELF = 1, FEAT_EXT = 2 };
+// alone; 6-DOF grasps (with or without SelfCollision); knots (with or without
+// 6-DOF grasps and SelfCollision).  Each set includes the ones before it.
+enum KernelFeat { FEAT_SELF = 1, FEAT_EXT = 2, FEAT_KNOT = 3 };
 constexpr int ITEM_TILE_BITS = 20;
 
 }  // namespace tamp

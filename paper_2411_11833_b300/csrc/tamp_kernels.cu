@@ -425,7 +425,7 @@ __device__ __forceinline__ float bound_dist(const float (&v)[N], const float (&l
 //   phase 1  links (tip to base); the frame steps back to T_{l-1} after each
 //   phase 2  spheres fixed to the base (tail, cost only)
 //   phase 3  the placed box at P(p) (tail of a Place: CFreePlace)
-template <int L, bool KN>
+template <int L, bool EX, bool KT>
 __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __restrict__ pb, int k, int piece,
                             const float* __restrict__ X, float* G, float* Tm, const int* __restrict__ slots,
                             const float4* __restrict__ place, const float2* __restrict__ trig,
@@ -456,10 +456,10 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   const float w_cp = cp_count > 0 ? tw(terms, cf[CF_CP_T]) : 0.f;
   const bool head = piece == 0, last = piece == NPIECE - 1;
   // a trajectory knot: no Kin, no grasp / containment term; the held box only on a MoveHold
-  // (KN: the kernel is built for problems with knots; otherwise these are constants)
-  const bool knot = KN && kind == CK_KNOT, hold = !KN || cf[CF_HOLD] != 0;
+  // (KT: the kernel is built for problems with knots; otherwise these are constants)
+  const bool knot = KT && kind == CK_KNOT, hold = !KT || cf[CF_HOLD] != 0;
   // 6-DOF grasps (extended instantiation only): G(g) = Trans Rz(yaw) Ry(pitch) Rx(roll) Rx(pi)
-  const bool g6 = KN && pb[PH_GRASP6] != 0;
+  const bool g6 = EX && pb[PH_GRASP6] != 0;
   const int ntg = nj + 1 + (g6 ? 2 : 0);
   // links of each piece, so that sphere batches spread evenly: the head also
   // has the held box (2 batches), the tail the placed box (1)
@@ -471,8 +471,24 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   const float k0 = (sub == 0 && head && !knot) ? 1.f : 0.f;
 #define XV(c) X[(c) * PT + pl]
   // (cos, sin) of this configuration's joint angles, then of its grasp yaw
-  const float2* tg = trig + k * ntg * PT + pl;
-#define TG(j) tg[(j) * PT]
+  // (and roll, pitch): its table row, or for a knot, computed here for the
+  // joints below this piece's top link and, on a MoveHold, the grasp angles
+  const float2* tg = trig + (KT ? max(cf[CF_TG], 0) : k) * ntg * PT + pl;
+  float2 kt[MAXJ + 3];
+  if (knot) {
+    for (int j = 0; j < top; ++j) {
+      float sn, cs;
+      sincosf(XV(qo + j) + arm[24 + j * ARM_JW + 4], &sn, &cs);
+      kt[j] = make_float2(cs, sn);
+    }
+    if (head && hold)
+      for (int j = 0; j < (g6 ? 3 : 1); ++j) {
+        float sn, cs;
+        sincosf(XV(go + 3 + j), &sn, &cs);
+        kt[nj + j] = make_float2(cs, sn);
+      }
+  }
+#define TG(j) (knot ? kt[j] : tg[(j) * PT])
 
   // ---------------- forward kinematics T_0 .. T_n (the tail stops at T_m)
   float R[9], t[3];
@@ -993,7 +1009,7 @@ __device__ __forceinline__ void fk_step(float (&R)[9], float (&t)[3], const floa
 // turns the wrenches into joint torques: the two forces of a pair cancel below
 // both links.  All lanes call this; lanes with sub != 0 only help restore the
 // scratch.
-template <int L>
+template <int L, bool KT>
 __device__ __noinline__ void eval_self(const uint32_t* __restrict__ sc, const uint32_t* __restrict__ pb, int k,
                                        const float* __restrict__ X, float* G, float* Tm,
                                        const float2* __restrict__ trig, const WarpScratch& ws, int lane, int pl,
@@ -1015,18 +1031,36 @@ __device__ __noinline__ void eval_self(const uint32_t* __restrict__ sc, const ui
     const bool hold = cf[CF_HOLD] != 0;
     const float w = tw(pb + pb[PH_OFF_TERMS], t_self);
     const bool g6 = pb[PH_GRASP6] != 0;
-    const float2* tg = trig + k * (nj + 1 + (g6 ? 2 : 0)) * PT + pl;
+    const float2* tg = trig + (KT ? max(cf[CF_TG], 0) : k) * (nj + 1 + (g6 ? 2 : 0)) * PT + pl;
+    // a knot has no table row: its angles are computed once here
+    const bool knot = KT && cf[CF_KIND] == CK_KNOT;
+    float2 kt[MAXJ + 3];
+    if (knot) {
+      const float* jr = arm + 24;
+      for (int j = 0; j < nj; ++j) {
+        float sn, cs;
+        sincosf(X[(qo + j) * PT + pl] + jr[j * ARM_JW + 4], &sn, &cs);
+        kt[j] = make_float2(cs, sn);
+      }
+      if (hold)
+        for (int j = 0; j < (g6 ? 3 : 1); ++j) {
+          float sn, cs;
+          sincosf(X[(go + 3 + j) * PT + pl], &sn, &cs);
+          kt[nj + j] = make_float2(cs, sn);
+        }
+    }
+    auto TS = [&](int j) { return knot ? kt[j] : tg[j * PT]; };
     for (int i = 0; i < 6 * nj; ++i) acc[i * 32 + lane] = 0.f;
     float gxv = 0.f, gyv = 0.f, gzv = 0.f, cgr = 1.f, sgr = 0.f;
     // R_G (object frame -> gripper target), top-down unless 6-DOF; the pitch and roll axes
     float rg[9] = {1.f, 0.f, 0.f, 0.f, -1.f, 0.f, 0.f, 0.f, -1.f}, cth = 1.f, sth = 0.f;
     if (hold) {
       gxv = X[go * PT + pl]; gyv = X[(go + 1) * PT + pl]; gzv = X[(go + 2) * PT + pl];
-      const float2 c = tg[nj * PT];
+      const float2 c = TS(nj);
       cgr = c.x; sgr = c.y;
       float cph = 1.f, sph = 0.f;
       if (g6) {
-        const float2 r = tg[(nj + 1) * PT], t = tg[(nj + 2) * PT];
+        const float2 r = TS(nj + 1), t = TS(nj + 2);
         cph = r.x; sph = r.y; cth = t.x; sth = t.y;
       }
       rg[0] = cgr * cth; rg[1] = fmaf(-cgr * sth, sph, sgr * cph); rg[2] = fmaf(-cgr * sth, cph, -sgr * sph);
@@ -1046,7 +1080,7 @@ __device__ __noinline__ void eval_self(const uint32_t* __restrict__ sc, const ui
     for (int i = 0; i < 9; ++i) Rj[i] = arm[i];
     tj[0] = arm[9]; tj[1] = arm[10]; tj[2] = arm[11];
     for (int j = 0; j <= nj; ++j) {
-      if (j > 0) fk_step(Rj, tj, arm, j - 1, tg[(j - 1) * PT]);
+      if (j > 0) fk_step(Rj, tj, arm, j - 1, TS(j - 1));
       uint32_t m = 0;
       for (int i = j + 2; i <= nj; ++i)
         if ((smask[i] >> j) & 1u) m |= 1u << i;
@@ -1097,7 +1131,7 @@ __device__ __noinline__ void eval_self(const uint32_t* __restrict__ sc, const ui
         for (int i = 0; i < 9; ++i) Ri[i] = Rj[i];
         ti[0] = tj[0]; ti[1] = tj[1]; ti[2] = tj[2];
         for (int i = j + 1; i <= nj; ++i) {
-          fk_step(Ri, ti, arm, i - 1, tg[(i - 1) * PT]);
+          fk_step(Ri, ti, arm, i - 1, TS(i - 1));
           if ((m >> i) & 1u) {
             for (int s1 = sc[SH_LINK0 + i]; s1 < static_cast<int>(sc[SH_LINK0 + i + 1]); s1 += NB) {
               const float4 bi = sphb[s1 / NB];
@@ -1176,7 +1210,7 @@ __device__ __noinline__ void eval_self(const uint32_t* __restrict__ sc, const ui
 #pragma unroll
     for (int i = 0; i < 9; ++i) R[i] = arm[i];
     t[0] = arm[9]; t[1] = arm[10]; t[2] = arm[11];
-    for (int j = 0; j < nj; ++j) fk_step(R, t, arm, j, tg[j * PT]);
+    for (int j = 0; j < nj; ++j) fk_step(R, t, arm, j, TS(j));
     float F[3] = {0.f, 0.f, 0.f}, M[3] = {0.f, 0.f, 0.f};
     for (int l = nj; l >= 1; --l) {
       const float* a = acc + (l - 1) * 6 * 32 + lane;
@@ -1191,7 +1225,7 @@ __device__ __noinline__ void eval_self(const uint32_t* __restrict__ sc, const ui
       const float ox = t[1] * zz - t[2] * zy, oy = t[2] * zx - t[0] * zz, oz = t[0] * zy - t[1] * zx;
       atomicAdd(&G[(qo + l - 1) * PT + pl],
                 fmaf(zx, M[0], fmaf(zy, M[1], fmaf(zz, M[2], fmaf(ox, F[0], fmaf(oy, F[1], oz * F[2]))))));
-      const float2 cs = tg[(l - 1) * PT];
+      const float2 cs = TS(l - 1);
       rz_right(R, cs.x, -cs.y);
     }
   }
@@ -1230,9 +1264,12 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
   // cos yaw, sin yaw), refreshed at the start of each iteration
   float4* splace = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(sflag) + ((PT * 4 + 15) & ~15));
   const int NSLOT = s_pb[PH_NSLOT];
-  // (cos, sin) of every configuration's joint angles and grasp yaw at the current iterate
+  // (cos, sin) of the joint angles and grasp angles of every Pick / Place
+  // configuration at the current iterate (knots compute theirs where they use them)
   float2* strig = reinterpret_cast<float2*>(splace + NSLOT * PT);
-  const int nj = s_sc[SH_NJ], ntg = nj + 1 + ((FEAT == FEAT_EXT && s_pb[PH_GRASP6] != 0) ? 2 : 0), NA = K * ntg;
+  const int ntab = FEAT == FEAT_KNOT ? static_cast<int>(s_pb[PH_NTAB]) : K;
+  const int* tab = reinterpret_cast<const int*>(s_pb + s_pb[PH_OFF_TAB]);
+  const int nj = s_sc[SH_NJ], ntg = nj + 1 + ((FEAT >= FEAT_EXT && s_pb[PH_GRASP6] != 0) ? 2 : 0), NA = ntab * ntg;
   const float* arm = reinterpret_cast<const float*>(s_sc + s_sc[SH_OFF_ARM]);
   const uint32_t* cfg0 = s_pb + s_pb[PH_OFF_CFG];
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -1269,8 +1306,8 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
   // configurations first (their environments hold more placed boxes), then the
   // goal cost; warps pull them from a counter so that they finish together
   __shared__ int s_next;
-  constexpr bool KN = FEAT == FEAT_EXT, SC = FEAT != 0;
-  const bool has_goal = s_pb[PH_GOAL_T] != 0xffffffffu, has_traj = KN && s_pb[PH_NSEG] != 0;
+  constexpr bool EX = FEAT >= FEAT_EXT, KT = FEAT == FEAT_KNOT, SC = FEAT != 0;
+  const bool has_goal = s_pb[PH_GOAL_T] != 0xffffffffu, has_traj = KT && s_pb[PH_NSEG] != 0;
   // SelfCollision: one more item per configuration (after the pieces)
   const int n_self = (SC && static_cast<int>(s_pb[s_pb[PH_OFF_CFG] + CF_T_SELF]) >= 0) ? K : 0;
   const int n_work = NPIECE * K + n_self + (has_goal ? 1 : 0) + (has_traj ? 1 : 0);
@@ -1289,7 +1326,8 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
     }
     for (int i = tid; i < NA * PT; i += nthr) {
       const int a = i / PT, p = i - a * PT;
-      const int k = a / ntg, j = a - k * ntg;
+      const int r = a / ntg, j = a - r * ntg;
+      const int k = KT ? tab[r] : r;  // without knots every configuration has a row
       const int* cf = reinterpret_cast<const int*>(cfg0 + k * CFG_W);
       // joints, then the grasp yaw (and roll, pitch): components go + 3 (+ 4, 5)
       const float ang = j < nj ? sx[(cf[CF_QOFF] + j) * PT + p] + arm[24 + j * ARM_JW + 4]
@@ -1305,15 +1343,15 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
       item = __shfl_sync(0xffffffffu, item, 0);
       if (item >= n_work) break;
       if (item < NPIECE * K) {
-        eval_config<L, KN>(s_sc, s_pb, K - 1 - item / NPIECE, item % NPIECE, sx, sg, st, slots, splace, strig, ws, n_obb,
+        eval_config<L, EX, KT>(s_sc, s_pb, K - 1 - item / NPIECE, item % NPIECE, sx, sg, st, slots, splace, strig, ws, n_obb,
                        n_box, lane, pl, sub);
       } else if (SC && item < NPIECE * K + n_self) {
         if constexpr (SC)
-          eval_self<L>(s_sc, s_pb, K - 1 - (item - NPIECE * K), sx, sg, st, strig, ws, lane, pl, sub);
+          eval_self<L, KT>(s_sc, s_pb, K - 1 - (item - NPIECE * K), sx, sg, st, strig, ws, lane, pl, sub);
       } else if (sub == 0) {
         if (has_goal && item == NPIECE * K + n_self)
           eval_goal<L>(s_sc, s_pb, sx, sg, st, pl);
-        else if constexpr (KN)
+        else if constexpr (KT)
           eval_traj<L>(s_pb, sx, sg, st, nj, pl);
       }
     }
@@ -1904,6 +1942,7 @@ static cudaError_t launch_opt(const LaunchArgs& a, int warps, int grid, size_t s
     case 0: return launch_feat<L, 0>(a, warps, grid, smem, st);
     case FEAT_SELF: return launch_feat<L, FEAT_SELF>(a, warps, grid, smem, st);
     case FEAT_EXT: return launch_feat<L, FEAT_EXT>(a, warps, grid, smem, st);
+    case FEAT_KNOT: return launch_feat<L, FEAT_KNOT>(a, warps, grid, smem, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1925,6 +1964,7 @@ static cudaError_t set_smem_all(size_t smem) {
   cudaError_t e = set_smem<L, 0>(smem);
   if (e == cudaSuccess) e = set_smem<L, FEAT_SELF>(smem);
   if (e == cudaSuccess) e = set_smem<L, FEAT_EXT>(smem);
+  if (e == cudaSuccess) e = set_smem<L, FEAT_KNOT>(smem);
   return e;
 }
 
