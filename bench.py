@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttfs", action="store_true", help="skip the time-to-first-satisfying measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's heuristic launch shape")
+    ap.add_argument("--shape", default="", help="pin the launch shape LANES,WARPS (no tuning), e.g. 1,12")
     ap.add_argument("--mode", default="optimize", choices=["optimize", "mlp"],
                     help="optimize: the headline line; mlp: the proposal network's tensor-core kernels alone")
     ap.add_argument("--workload", default="packing", choices=["packing", "stress"],
@@ -345,7 +346,13 @@ def main():
     D, NT, _ = scene.problem_info(pid)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     tuned = None
-    if not args.no_autotune and args.lanes == 0:
+    if args.shape:
+        L, W = (int(v) for v in args.shape.split(","))
+        with torch.cuda.stream(stream):
+            scene.sample(pid, P, 999)
+            scene.set_tuning(pid, L, W)
+        tuned = {"lanes": L, "warps": W, "pinned": True}
+    elif not args.no_autotune and args.lanes == 0:
         with torch.cuda.stream(stream):
             scene.sample(pid, P, 999)
             L, W, ms = scene.autotune(pid, trial_steps=50)
