@@ -31,7 +31,7 @@ constraint tolerances).
 The particle layout (Pick: grasp x,y,z,yaw then q; Place: placement x,y,yaw
 then q) is the interface documented in include/tamp.h.
 
-Readings of points the paper leaves open (each one is listed in the design doc):
+Readings of points the paper leaves open:
   * Kin is two constraints, translation (m) and rotation (geodesic angle, rad);
   * CFreeHold(o, g, q): arm spheres at q plus o's spheres held at FK(q) G(g)^-1,
     against the static cuboids and every other box at its current pose; the
