@@ -1311,11 +1311,24 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
   // SelfCollision: one more item per configuration (after the pieces)
   const int n_self = (SC && static_cast<int>(s_pb[s_pb[PH_OFF_CFG] + CF_T_SELF]) >= 0) ? K : 0;
   const int n_work = NPIECE * K + n_self + (has_goal ? 1 : 0) + (has_traj ? 1 : 0);
-  double b1t = pow(static_cast<double>(d.beta1), t0), b2t = pow(static_cast<double>(d.beta2), t0);
+  // Adam's bias corrections in FP64 by one thread (FP64 is slow on this part),
+  // handed to the others through shared memory: beta^t, then 1 / (1 - beta^(t + 1))
+  __shared__ float s_ib[2];
+  double b1t = 0.0, b2t = 0.0;
+  if (tid == 0) {
+    b1t = pow(static_cast<double>(d.beta1), t0);
+    b2t = pow(static_cast<double>(d.beta2), t0);
+  }
   unsigned n_obb = 0, n_box = 0;  // broad-phase candidates resolved exactly (work accounting)
 
   for (int it = 0;; ++it) {
-    if (tid == 0) s_next = 0;
+    if (tid == 0) {
+      s_next = 0;
+      b1t *= static_cast<double>(d.beta1);  // beta^(t0 + it + 1), for this iteration's step
+      b2t *= static_cast<double>(d.beta2);
+      s_ib[0] = static_cast<float>(1.0 / (1.0 - b1t));
+      s_ib[1] = static_cast<float>(1.0 / (1.0 - b2t));
+    }
     for (int i = tid; i < NT * PT; i += nthr) st[i] = 0.f;  // collision terms are sums over pieces
     for (int i = tid; i < NSLOT * PT; i += nthr) {
       const int si = i / PT, p = i - si * PT;
@@ -1372,9 +1385,7 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
     }
     if (it == d.n_steps) break;
     // Adam (Kingma & Ba) on the Eq. 4 gradient; the gradient buffer is cleared for the next pass
-    b1t *= static_cast<double>(d.beta1);  // beta^(t0 + it + 1)
-    b2t *= static_cast<double>(d.beta2);
-    const float ib1 = static_cast<float>(1.0 / (1.0 - b1t)), ib2 = static_cast<float>(1.0 / (1.0 - b2t));
+    const float ib1 = s_ib[0], ib2 = s_ib[1];
     for (int i = tid; i < D * PT; i += nthr) {
       const float g = sg[i] * d.gscale;
       float m0, v0;
