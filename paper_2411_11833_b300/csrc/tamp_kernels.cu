@@ -1320,6 +1320,11 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
     b2t = pow(static_cast<double>(d.beta2), t0);
   }
   unsigned n_obb = 0, n_box = 0;  // broad-phase candidates resolved exactly (work accounting)
+  // this thread's entries of the angle table: a = tid / PT + m (nthr / PT) (nthr is a multiple of PT),
+  // particle tid % PT, row a / ntg, angle a % ntg
+  const int tg_p = tid % PT, tg_a0 = tid / PT, tg_astep = nthr / PT;
+  const int tg_r0 = tg_a0 / ntg, tg_j0 = tg_a0 - tg_r0 * ntg;
+  const int tg_rstep = tg_astep / ntg, tg_jstep = tg_astep - tg_rstep * ntg;
 
   for (int it = 0;; ++it) {
     if (tid == 0) {
@@ -1337,17 +1342,22 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
       sincosf(sx[(off + 2) * PT + p], &sn, &cs);
       splace[i] = make_float4(sx[off * PT + p], sx[(off + 1) * PT + p], cs, sn);
     }
-    for (int i = tid; i < NA * PT; i += nthr) {
-      const int a = i / PT, p = i - a * PT;
-      const int r = a / ntg, j = a - r * ntg;
+    // entry (row r, angle j) of particle tg_p; the row and angle step without a division
+    for (int a = tg_a0, r = tg_r0, j = tg_j0; a < NA; a += tg_astep) {
       const int k = KT ? tab[r] : r;  // without knots every configuration has a row
       const int* cf = reinterpret_cast<const int*>(cfg0 + k * CFG_W);
       // joints, then the grasp yaw (and roll, pitch): components go + 3 (+ 4, 5)
-      const float ang = j < nj ? sx[(cf[CF_QOFF] + j) * PT + p] + arm[24 + j * ARM_JW + 4]
-                               : sx[(cf[CF_GOFF] + 3 + (j - nj)) * PT + p];
+      const float ang = j < nj ? sx[(cf[CF_QOFF] + j) * PT + tg_p] + arm[24 + j * ARM_JW + 4]
+                               : sx[(cf[CF_GOFF] + 3 + (j - nj)) * PT + tg_p];
       float sn, cs;
       sincosf(ang, &sn, &cs);
-      strig[i] = make_float2(cs, sn);
+      strig[a * PT + tg_p] = make_float2(cs, sn);
+      r += tg_rstep;
+      j += tg_jstep;
+      if (j >= ntg) {
+        j -= ntg;
+        ++r;
+      }
     }
     __syncthreads();
     for (;;) {
