@@ -368,3 +368,45 @@ def test_stress_full_batch_adam_step_sampled(pkg):
     step_r = (xr.numpy() - Xs.numpy())[keep]
     # first Adam step: -lr * g / (|g| + eps), so compare the steps' signs and sizes
     assert np.abs(step_g - step_r).max() <= 1e-3 * np.abs(step_r).max() + 2e-6
+
+
+def test_packing_full_batch_two_launches_sampled(pkg):
+    """The packing workload at the benchmark's batch (4096 particles) in its
+    launch shape (1 lane, 16 warps): two launches of one fused iteration each,
+    the second starting at Adam step 1 (bias corrections 1 / (1 - beta^2) from
+    the step count carried over).  32 sampled particles are checked one by one:
+    the first step against the oracle's gradient + Adam step from the initial
+    batch, the second against the oracle's step from the GPU's own state after
+    the first (particles within 1e-4 of a kink are left out)."""
+    sc, acts = sg.packing_problem(2001)
+    pr = Problem(sc, acts)
+    P = 4096
+    X = sg.random_particles(sc, acts, P, seed=82).astype(np.float32)
+    scene = pkg.Scene(sc)
+    pid = scene.set_skeleton(acts)
+    scene.set_particles(pid, np.ascontiguousarray(X.T))
+    scene.set_tuning(pid, 1, 16)
+    scene.optimize(pid, 1)
+    x1, m1, v1, t1 = scene.get_particles(pid)
+    scene.optimize(pid, 1)
+    x2, m2, v2, t2 = scene.get_particles(pid)
+    scene.close()
+    assert (t1, t2) == (1, 2)
+    idx = np.random.default_rng(4).choice(P, 32, replace=False)
+
+    def check(x0, m0, v0, t, x_gpu, m_gpu):
+        xs = torch.tensor(x0[idx].astype(np.float64))
+        keep = pr.kink_margin(xs).numpy() > 1e-4
+        assert keep.sum() >= 8, keep.sum()
+        _, g = pr.gradient(xs)
+        xr, mr, _ = pr.adam_step(xs, torch.tensor(m0[idx].astype(np.float64)),
+                                 torch.tensor(v0[idx].astype(np.float64)), t, g, P)
+        dm = np.abs(m_gpu[idx] - mr.numpy())[keep]
+        assert dm.max() <= 1e-3 * np.abs(mr.numpy()[keep]).max() + 1e-12
+        step_g = (x_gpu[idx] - x0[idx])[keep]
+        step_r = (xr.numpy() - xs.numpy())[keep]
+        assert np.abs(step_g - step_r).max() <= 1e-3 * np.abs(step_r).max() + 2e-6
+
+    zeros = np.zeros_like(X)
+    check(X, zeros, zeros, 1, x1.T, m1.T)
+    check(x1.T, m1.T, v1.T, 2, x2.T, m2.T)
