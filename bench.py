@@ -47,6 +47,19 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
+def _shape(text: str):
+    """LANES,WARPS for --shape: lanes 1, 2, 4 or 8, warps 1-16."""
+    if not text:
+        return ""
+    try:
+        lanes, warps = (int(v) for v in text.split(","))
+    except ValueError:
+        raise argparse.ArgumentTypeError(f"expected LANES,WARPS, got {text!r}")
+    if lanes not in (1, 2, 4, 8) or not 1 <= warps <= 16:
+        raise argparse.ArgumentTypeError(f"lanes must be 1, 2, 4 or 8 and warps 1-16, got {text!r}")
+    return (lanes, warps)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -59,7 +72,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttfs", action="store_true", help="skip the time-to-first-satisfying measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's heuristic launch shape")
-    ap.add_argument("--shape", default="", help="pin the launch shape LANES,WARPS (no tuning), e.g. 1,12")
+    ap.add_argument("--shape", default="", type=_shape,
+                    help="pin the launch shape LANES,WARPS (no tuning), e.g. 1,12")
     ap.add_argument("--mode", default="optimize", choices=["optimize", "mlp"],
                     help="optimize: the headline line; mlp: the proposal network's tensor-core kernels alone")
     ap.add_argument("--workload", default="packing", choices=["packing", "stress"],
@@ -347,7 +361,7 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     tuned = None
     if args.shape:
-        L, W = (int(v) for v in args.shape.split(","))
+        L, W = args.shape
         with torch.cuda.stream(stream):
             scene.sample(pid, P, 999)
             scene.set_tuning(pid, L, W)
