@@ -787,12 +787,14 @@ int preferred_lanes(int requested, long total_particles) {
   return total_particles >= 148L * 16 ? 1 : (total_particles >= 148L * 8 ? 2 : 4);
 }
 
-// The kernel instantiation a problem needs: knots (with or without 6-DOF
-// grasps and self-collision), 6-DOF grasps (with or without self-collision),
-// self-collision only, or none of them.
-int problem_feat(const Problem& pr) {
-  return pr.n_seg > 0 ? FEAT_KNOT : (pr.grasp6 ? FEAT_EXT : (pr.self ? FEAT_SELF : 0));
+// The kernel instantiation for problems that need knots, 6-DOF grasps and
+// self-collision (any of them): the smallest feature set that holds them.
+int feat_of(bool knots, bool g6, bool self) {
+  if (knots) return g6 ? FEAT_KNOT6 : FEAT_KNOT;
+  if (g6) return FEAT_EXT;
+  return self ? FEAT_SELF : 0;
 }
+int problem_feat(const Problem& pr) { return feat_of(pr.n_seg > 0, pr.grasp6, pr.self); }
 
 void free_batch(Problem& pr) {
   cudaFree(pr.d_x); cudaFree(pr.d_m); cudaFree(pr.d_v); cudaFree(pr.d_cost);
@@ -838,7 +840,7 @@ struct Job {
 struct Plan {
   int L = 1, warps = 1, grid = 0;
   bool mv_global = false;  // Adam moments in global memory: the tile fits shared memory only that way
-  int feat = 0;            // optional terms of the problems: 0 or a KernelFeat (the largest set a problem needs)
+  int feat = 0;            // optional terms of the problems: 0 or the KernelFeat that holds all of them
   size_t smem = 0;
   std::vector<ProbDesc> descs;
   std::vector<uint32_t> items;
@@ -908,8 +910,13 @@ tamp_status plan_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lanes
   plan->warps = warps;
   plan->smem = smem;
   plan->mv_global = mvg;
-  plan->feat = 0;
-  for (const Job& j : jobs) plan->feat = std::max(plan->feat, problem_feat(*j.pr));
+  bool knots = false, g6 = false, self = false;
+  for (const Job& j : jobs) {
+    knots = knots || j.pr->n_seg > 0;
+    g6 = g6 || j.pr->grasp6;
+    self = self || j.pr->self;
+  }
+  plan->feat = feat_of(knots, g6, self);
   const int per_sm = std::max(1, optimize_blocks_per_sm(L, warps, smem));
   plan->grid = std::min(static_cast<int>(plan->items.size()), s->sm_count * per_sm);
   return TAMP_OK;

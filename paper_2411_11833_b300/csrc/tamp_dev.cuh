@@ -140,10 +140,10 @@ struct LaunchArgs {
   int mv_global;                      // 1: Adam moments used in place in global memory (not staged)
   int feat;                           // the optional terms of the launch's problems: 0 or a KernelFeat
 };
-// Feature sets of the optimisation kernel's instantiations: SelfCollision
-// alone; 6-DOF grasps (with or without SelfCollision); knots (with or without
-// 6-DOF grasps and SelfCollision).  Each set includes the ones before it.
-enum KernelFeat { FEAT_SELF = 1, FEAT_EXT = 2, FEAT_KNOT = 3 };
+// Feature sets of the optimisation kernel's instantiations (0: none of the
+// optional terms): SelfCollision alone; 6-DOF grasps; knots with 4-DOF grasps;
+// knots with 6-DOF grasps -- each with or without SelfCollision.
+enum KernelFeat { FEAT_SELF = 1, FEAT_EXT = 2, FEAT_KNOT = 3, FEAT_KNOT6 = 4, N_FEAT = 5 };
 constexpr int ITEM_TILE_BITS = 20;
 
 }  // namespace tamp

@@ -1243,13 +1243,15 @@ __device__ __noinline__ void eval_self(const uint32_t* __restrict__ sc, const ui
 // One tile of PT particles of one problem: load it, run n_steps fused
 // iterations (evaluation + adjoint, Eq. 3 check, Adam) and one final check,
 // write it back.  All threads of the CTA call this together.
-// FEAT: the optional terms the kernel is built for -- FEAT_EXT (knot
-// configurations and TrajLength, with self-collision), FEAT_SELF (SelfCollision
-// only), 0 (neither: the configuration code of every other skeleton).
+// FEAT: the optional terms the kernel is built for (a KernelFeat; 0: none,
+// the configuration code of every skeleton without them).
 template <int L, int FEAT>
 __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, const uint32_t* s_pb, float* tile_mem,
                          const WarpScratch& ws, bool mv_global) {
   constexpr int PT = 32 / L;
+  // EX: 6-DOF grasps; KT: knots (configurations of kind 2, TrajLength); SC: SelfCollision
+  constexpr bool EX = FEAT == FEAT_EXT || FEAT == FEAT_KNOT6, KT = FEAT == FEAT_KNOT || FEAT == FEAT_KNOT6;
+  constexpr bool SC = FEAT != 0;
   const int D = s_pb[PH_D], K = s_pb[PH_K], NT = s_pb[PH_NT];
   // the tile in shared memory: x, the Adam moments m and v (unless they are
   // used in place in global memory, for problems whose tile would not fit
@@ -1267,9 +1269,9 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
   // (cos, sin) of the joint angles and grasp angles of every Pick / Place
   // configuration at the current iterate (knots compute theirs where they use them)
   float2* strig = reinterpret_cast<float2*>(splace + NSLOT * PT);
-  const int ntab = FEAT == FEAT_KNOT ? static_cast<int>(s_pb[PH_NTAB]) : K;
+  const int ntab = KT ? static_cast<int>(s_pb[PH_NTAB]) : K;
   const int* tab = reinterpret_cast<const int*>(s_pb + s_pb[PH_OFF_TAB]);
-  const int nj = s_sc[SH_NJ], ntg = nj + 1 + ((FEAT >= FEAT_EXT && s_pb[PH_GRASP6] != 0) ? 2 : 0), NA = ntab * ntg;
+  const int nj = s_sc[SH_NJ], ntg = nj + 1 + ((EX && s_pb[PH_GRASP6] != 0) ? 2 : 0), NA = ntab * ntg;
   const float* arm = reinterpret_cast<const float*>(s_sc + s_sc[SH_OFF_ARM]);
   const uint32_t* cfg0 = s_pb + s_pb[PH_OFF_CFG];
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -1306,7 +1308,6 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
   // configurations first (their environments hold more placed boxes), then the
   // goal cost; warps pull them from a counter so that they finish together
   __shared__ int s_next;
-  constexpr bool EX = FEAT >= FEAT_EXT, KT = FEAT == FEAT_KNOT, SC = FEAT != 0;
   const bool has_goal = s_pb[PH_GOAL_T] != 0xffffffffu, has_traj = KT && s_pb[PH_NSEG] != 0;
   // SelfCollision: one more item per configuration (after the pieces)
   const int n_self = (SC && static_cast<int>(s_pb[s_pb[PH_OFF_CFG] + CF_T_SELF]) >= 0) ? K : 0;
@@ -1934,8 +1935,8 @@ cudaError_t launch_chunk_control(int* t_dev, const int* const* first_iters, int 
 
 // ------------------------------------------------------------------ launchers
 // largest dynamic shared-memory size enabled so far for optimize_kernel<1,2,4,8>
-// per feature set (0, FEAT_SELF, FEAT_EXT)
-static size_t g_smem_enabled[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+// per feature set (0 .. N_FEAT - 1)
+static size_t g_smem_enabled[N_FEAT][4] = {};
 static int lane_slot(int L) { return L == 1 ? 0 : (L == 2 ? 1 : (L == 4 ? 2 : 3)); }
 
 template <int L, int FEAT>
@@ -1964,6 +1965,7 @@ static cudaError_t launch_opt(const LaunchArgs& a, int warps, int grid, size_t s
     case FEAT_SELF: return launch_feat<L, FEAT_SELF>(a, warps, grid, smem, st);
     case FEAT_EXT: return launch_feat<L, FEAT_EXT>(a, warps, grid, smem, st);
     case FEAT_KNOT: return launch_feat<L, FEAT_KNOT>(a, warps, grid, smem, st);
+    case FEAT_KNOT6: return launch_feat<L, FEAT_KNOT6>(a, warps, grid, smem, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1986,6 +1988,7 @@ static cudaError_t set_smem_all(size_t smem) {
   if (e == cudaSuccess) e = set_smem<L, FEAT_SELF>(smem);
   if (e == cudaSuccess) e = set_smem<L, FEAT_EXT>(smem);
   if (e == cudaSuccess) e = set_smem<L, FEAT_KNOT>(smem);
+  if (e == cudaSuccess) e = set_smem<L, FEAT_KNOT6>(smem);
   return e;
 }
 
