@@ -77,3 +77,31 @@ def test_adam_step_with_six_dof_grasps_matches_oracle(pkg):
     step_g = (x1.T - X.astype(np.float32))[keep]
     step_r = (xr.numpy() - Xt.numpy())[keep]
     assert np.abs(step_g - step_r).max() <= 1e-3 * np.abs(step_r).max() + 2e-6
+
+
+@pytest.mark.parametrize("with_g6", [True, False])
+def test_one_launch_over_problems_with_different_optional_terms(pkg, with_g6):
+    """Problems that need different kernel feature sets in one persistent
+    launch (the launch takes the set that holds all of them: knots with 6-DOF
+    grasps, or knots with 4-DOF grasps when no problem has 6-DOF grasps): each
+    problem's costs still match the oracle, particle by particle."""
+    from tests.parity import cost_ok
+    sc, acts = sg.robot_packing_problem(21002, n_boxes=2)
+    specs = [dict(n_knots=2), dict(), dict(self_collision=1)]
+    if with_g6:
+        specs.append(dict(grasp_dof=6))
+    scene = pkg.Scene(sc)
+    probs = []
+    for i, o in enumerate(specs):
+        pr = Problem(sc, acts, Options(n_knots=o.get("n_knots", 0), grasp_dof=o.get("grasp_dof", 4),
+                                       self_collision=bool(o.get("self_collision", 0))))
+        pid = scene.set_skeleton(acts, pkg.default_options(**o))
+        X = pr.interpolate_knots(philox.sample_uniform(pr, 40 + 7 * i, 90 + i))
+        scene.set_particles(pid, np.ascontiguousarray(X.T).astype(np.float32))
+        probs.append((pid, pr, X))
+    scene.optimize([p for p, _, _ in probs], 0)       # evaluation only, one launch
+    for pid, pr, X in probs:
+        q = scene.query(pid, X.shape[0])
+        J = pr.total_cost(torch.tensor(X.astype(np.float32).astype(np.float64))).numpy()
+        assert cost_ok(q["cost"].astype(np.float64), J).all(), (pid, np.abs(q["cost"] - J).max())
+    scene.close()
