@@ -40,10 +40,15 @@ TRAFFIC = {"source_sha": "1770fe590b28233d", "bytes_per_launch": 6326528}
 
 
 def kernel_source_sha() -> str:
+    """Hash of the optimisation kernel's sources and the code-generation flags
+    they are compiled with (the traffic figure below belongs to one build)."""
+    from paper_2411_11833_b300 import build
+
     h = hashlib.sha256()
     for f in ("tamp_kernels.cu", "tamp_dev.cuh"):
         with open(os.path.join(ROOT, "paper_2411_11833_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
+    h.update(" ".join(build.ARCH + build.MATH).encode())
     return h.hexdigest()[:16]
 
 
