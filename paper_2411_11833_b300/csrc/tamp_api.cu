@@ -252,6 +252,30 @@ tamp_status build_scene_blob(tamp_scene* s, const tamp_scene_desc* d) {
     for (int k = 0; k < OBS_W; ++k) v.push_back(0);
   v[SH_O] = static_cast<uint32_t>(O);
   align4(v);
+  // the same obstacles in pairs (broad phase): the values of the records above
+  v[SH_OFF_OBS2] = static_cast<uint32_t>(v.size());
+  {
+    const size_t rec0 = v[SH_OFF_OBS];
+    auto word = [&](int o, int k) -> uint32_t {  // word k of obstacle o's record; o == O: far away
+      if (o < O) return v[rec0 + static_cast<size_t>(o) * OBS_W + k];
+      if (k < 3) return fbits(DUMMY_FAR);
+      if (k < 12) return fbits((k - 3) % 4 == 0 ? 1.f : 0.f);  // identity rotation
+      return 0;
+    };
+    auto neg = [](uint32_t w) { return w ^ 0x80000000u; };
+    for (int p = 0; 2 * p < std::max(O, 1); ++p) {
+      const int a = 2 * p, b = 2 * p + 1;
+      for (int ax = 0; ax < 3; ++ax) {
+        // R[ax], R[3 + ax], R[6 + ax] (record words 3 + ...), then -t'[ax]
+        const uint32_t r[8] = {word(a, 3 + ax), word(b, 3 + ax), word(a, 6 + ax),  word(b, 6 + ax),
+                               word(a, 9 + ax), word(b, 9 + ax), neg(word(a, ax)), neg(word(b, ax))};
+        v.insert(v.end(), r, r + 8);
+      }
+      const uint32_t h[8] = {word(a, 12), word(b, 12), word(a, 13), word(b, 13), word(a, 14), word(b, 14), 0, 0};
+      v.insert(v.end(), h, h + 8);
+    }
+  }
+  align4(v);
   // boxes
   const int B = d->n_boxes, NBS = d->spheres_per_box;
   v[SH_OFF_BOX] = static_cast<uint32_t>(v.size());

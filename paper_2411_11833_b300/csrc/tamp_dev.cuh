@@ -24,6 +24,7 @@ enum SceneHdr {
   SH_OFF_SURF,
   SH_OFF_SELF,                  // self-collision masks: word l (l = 0..MAXJ) = the lower links j tested against
                                 // link l (bit j); word MAXJ + 1 = the links the held box is tested against
+  SH_OFF_OBS2,                  // the obstacles again, two per OBS2_W-word record (broad phase)
   SH_HDR_WORDS = 32
 };
 // arm section: base frame (12), tool frame (12), then per joint ARM_JW words
@@ -37,6 +38,11 @@ constexpr float DUMMY_FAR = 1.0e4f;
 // pad; the 80-byte stride puts the records of 8 consecutive obstacles in
 // disjoint shared-memory banks when the lanes of a warp read different ones
 constexpr int OBS_W = 20;
+// obstacles 2i and 2i + 1 interleaved for the broad phase's paired FP32 math:
+// per axis k the R column (R[0k] pair, R[3+k] pair, R[6+k] pair) and -t'_k pair,
+// then the half extents (hx, hx', hy, hy', hz, hz', pad, pad); an odd count is
+// padded with an obstacle far away that nothing touches
+constexpr int OBS2_W = 32;
 // box record: half x,y,z, bounding radius of its spheres about its centre,
 // init x,y,z,yaw, cos(yaw), sin(yaw), then the half extents (box frame, about
 // the centre) of a box that holds every sphere of the model, pad

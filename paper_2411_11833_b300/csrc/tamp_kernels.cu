@@ -209,7 +209,8 @@ template <int L>
 __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy)[NB], const float (&cz)[NB],
                                          const float (&cr)[NB], float (&gx)[NB], float (&gy)[NB],
                                          float (&gz)[NB], float cbx, float cby, float cbz, float Rb,
-                                         const float4* __restrict__ obs, int O, const int* __restrict__ env,
+                                         const float4* __restrict__ obs, const float4* __restrict__ obs2, int O,
+                                         const int* __restrict__ env,
                                          int n_env, const float* __restrict__ boxr, const int* __restrict__ slots,
                                          const float4* __restrict__ bloc, const float4* __restrict__ binit,
                                          int NBS, const float4* __restrict__ place, float* G, int pl, int sub,
@@ -218,16 +219,36 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
   constexpr int PT = 32 / L;
   const int n_items = O + n_env;  // cuboids, then the other boxes
   bool published = false;
+  // the batch centre in both halves of a packed pair (two cuboids per test)
+  const float2 cx2 = make_float2(cbx, cbx), cy2 = make_float2(cby, cby), cz2 = make_float2(cbz, cbz);
   for (int base = 0; base < n_items; base += QUEUE_CHUNK * L) {
-    // ---- broad phase over this chunk of items
-    const int end = min(base + QUEUE_CHUNK * L, n_items);
-    for (int i = base + sub; i < end; i += L) {
-      if (i < O) {
-        if (obb_gap(load_obb(obs, i, O), cbx, cby, cbz) < Rb) {
-          const int q = atomicAdd(&ws.count[0], 1);
-          ws.queue[q] = static_cast<uint16_t>(lane << QUEUE_ITEM_BITS | i);
-        }
-      } else {
+    // ---- broad phase over this chunk of items: cuboids two at a time (packed
+    // FP32 pairs, the same roundings as one at a time), then the other boxes
+    const int end = min(base + QUEUE_CHUNK * L, n_items), cend = min(end, O);
+    for (int i = base + 2 * sub; i < cend; i += 2 * L) {
+      const float4* q = obs2 + (i >> 1) * (OBS2_W / 4);
+      const float4 q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3], q4 = q[4], q5 = q[5], q6 = q[6], q7 = q[7];
+      const float2 ux = __ffma2_rn(make_float2(q0.x, q0.y), cx2,
+                                   __ffma2_rn(make_float2(q0.z, q0.w), cy2,
+                                              __ffma2_rn(make_float2(q1.x, q1.y), cz2, make_float2(q1.z, q1.w))));
+      const float2 uy = __ffma2_rn(make_float2(q2.x, q2.y), cx2,
+                                   __ffma2_rn(make_float2(q2.z, q2.w), cy2,
+                                              __ffma2_rn(make_float2(q3.x, q3.y), cz2, make_float2(q3.z, q3.w))));
+      const float2 uz = __ffma2_rn(make_float2(q4.x, q4.y), cx2,
+                                   __ffma2_rn(make_float2(q4.z, q4.w), cy2,
+                                              __ffma2_rn(make_float2(q5.x, q5.y), cz2, make_float2(q5.z, q5.w))));
+      // max_i(|u_i| - h_i) < Rb for each of the two (i + 1 = O: the far pad)
+      if (fmaxf(fabsf(ux.x) - q6.x, fmaxf(fabsf(uy.x) - q6.z, fabsf(uz.x) - q7.x)) < Rb) {
+        const int e = atomicAdd(&ws.count[0], 1);
+        ws.queue[e] = static_cast<uint16_t>(lane << QUEUE_ITEM_BITS | i);
+      }
+      if (fmaxf(fabsf(ux.y) - q6.y, fmaxf(fabsf(uy.y) - q6.w, fabsf(uz.y) - q7.y)) < Rb) {
+        const int e = atomicAdd(&ws.count[0], 1);
+        ws.queue[e] = static_cast<uint16_t>(lane << QUEUE_ITEM_BITS | (i + 1));
+      }
+    }
+    for (int i = max(base, O) + sub; i < end; i += L) {
+      {
         // the batch bound against the other box's bounding sphere and against the
         // oriented box holding its spheres (centre, yaw, sphere hull); a contact
         // needs both: |d| < Rb + r_box and ||max(|u| - hull, 0)|| < Rb
@@ -436,6 +457,7 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
   const float4* sph = reinterpret_cast<const float4*>(sc + sc[SH_OFF_SPH]);
   const int O = sc[SH_O];
   const float4* obs = reinterpret_cast<const float4*>(sc + sc[SH_OFF_OBS]);
+  const float4* obs2 = reinterpret_cast<const float4*>(sc + sc[SH_OFF_OBS2]);
   const float* boxr = reinterpret_cast<const float*>(sc + sc[SH_OFF_BOX]);
   const float4* bloc = reinterpret_cast<const float4*>(sc + sc[SH_OFF_BLOC]);
   const float4* binit = reinterpret_cast<const float4*>(sc + sc[SH_OFF_BINIT]);
@@ -724,7 +746,7 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
       }
     }
     const float wenv = phase == 3 ? w_cp : w_cf;
-    const float Jb = collide<L>(cx, cyy, cz, cr, gx, gyy, gz, cbx, cby, cbz, Rb, obs, O, env, n_env, boxr, slots,
+    const float Jb = collide<L>(cx, cyy, cz, cr, gx, gyy, gz, cbx, cby, cbz, Rb, obs, obs2, O, env, n_env, boxr, slots,
                                 bloc, binit, NBS, place, G, pl, sub, lane, wenv, ws, n_obb, n_box);
     if (phase == 3) {
       J_place += Jb;
