@@ -205,7 +205,7 @@ struct WarpScratch {
 // owners.  Pairs the broad phase skips have zero penetration and gradient, so
 // the result equals the all-pairs sum.  Lane `sub` of the L lanes of a
 // (particle, configuration) takes items sub, sub + L, ...
-template <int L>
+template <int L, bool PR>
 __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy)[NB], const float (&cz)[NB],
                                          const float (&cr)[NB], float (&gx)[NB], float (&gy)[NB],
                                          float (&gz)[NB], float cbx, float cby, float cbz, float Rb,
@@ -222,55 +222,69 @@ __device__ __forceinline__ float collide(const float (&cx)[NB], const float (&cy
   // the batch centre in both halves of a packed pair (two cuboids per test)
   const float2 cx2 = make_float2(cbx, cbx), cy2 = make_float2(cby, cby), cz2 = make_float2(cbz, cbz);
   for (int base = 0; base < n_items; base += QUEUE_CHUNK * L) {
-    // ---- broad phase over this chunk of items: cuboids two at a time (packed
-    // FP32 pairs, the same roundings as one at a time), then the other boxes
+    // ---- broad phase over this chunk of items: cuboids (PR: two at a time in
+    // packed FP32 pairs, the same roundings as one at a time), then the other
+    // boxes.  PR is the plain instantiation's choice: in the instantiations
+    // with optional terms the pairs measured slower (more register pressure).
     const int end = min(base + QUEUE_CHUNK * L, n_items), cend = min(end, O);
-    for (int i = base + 2 * sub; i < cend; i += 2 * L) {
-      const float4* q = obs2 + (i >> 1) * (OBS2_W / 4);
-      const float4 q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3], q4 = q[4], q5 = q[5], q6 = q[6], q7 = q[7];
-      const float2 ux = __ffma2_rn(make_float2(q0.x, q0.y), cx2,
-                                   __ffma2_rn(make_float2(q0.z, q0.w), cy2,
-                                              __ffma2_rn(make_float2(q1.x, q1.y), cz2, make_float2(q1.z, q1.w))));
-      const float2 uy = __ffma2_rn(make_float2(q2.x, q2.y), cx2,
-                                   __ffma2_rn(make_float2(q2.z, q2.w), cy2,
-                                              __ffma2_rn(make_float2(q3.x, q3.y), cz2, make_float2(q3.z, q3.w))));
-      const float2 uz = __ffma2_rn(make_float2(q4.x, q4.y), cx2,
-                                   __ffma2_rn(make_float2(q4.z, q4.w), cy2,
-                                              __ffma2_rn(make_float2(q5.x, q5.y), cz2, make_float2(q5.z, q5.w))));
-      // max_i(|u_i| - h_i) < Rb for each of the two (i + 1 = O: the far pad)
-      if (fmaxf(fabsf(ux.x) - q6.x, fmaxf(fabsf(uy.x) - q6.z, fabsf(uz.x) - q7.x)) < Rb) {
-        const int e = atomicAdd(&ws.count[0], 1);
-        ws.queue[e] = static_cast<uint16_t>(lane << QUEUE_ITEM_BITS | i);
+    // the batch bound against the other box's bounding sphere and against the
+    // oriented box holding its spheres (centre, yaw, sphere hull); a contact
+    // needs both: |d| < Rb + r_box and ||max(|u| - hull, 0)|| < Rb
+    auto box_test = [&](int i) {
+      const int4 er = *reinterpret_cast<const int4*>(env + (i - O) * ENV_W);  // box, src, slot
+      const float4* br = reinterpret_cast<const float4*>(boxr + er.x * BOX_W);
+      const float4 b0 = br[0], b2 = br[2];  // (half extents, bound radius), (cos, sin, hull x, y)
+      const float hull_z = br[3].x;
+      float x, y, z, cy_, sy_;
+      if (er.y < 0) {
+        const float4 b1 = br[1];
+        x = b1.x; y = b1.y; z = b1.z; cy_ = b2.x; sy_ = b2.y;
+      } else {
+        const float4 pp = place[er.z * PT + pl];
+        x = pp.x; y = pp.y; z = __int_as_float(slots[er.z * SLOT_W + 2]); cy_ = pp.z; sy_ = pp.w;
       }
-      if (fmaxf(fabsf(ux.y) - q6.y, fmaxf(fabsf(uy.y) - q6.w, fabsf(uz.y) - q7.y)) < Rb) {
-        const int e = atomicAdd(&ws.count[0], 1);
-        ws.queue[e] = static_cast<uint16_t>(lane << QUEUE_ITEM_BITS | (i + 1));
+      const float dx = cbx - x, dy = cby - y, dz = cbz - z, R = Rb + b0.w;
+      const float ux = fmaf(cy_, dx, sy_ * dy), uy = fmaf(-sy_, dx, cy_ * dy);
+      const float qx = fmaxf(fabsf(ux) - b2.z, 0.f), qy = fmaxf(fabsf(uy) - b2.w, 0.f);
+      const float qz = fmaxf(fabsf(dz) - hull_z, 0.f);
+      if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R * R && fmaf(qx, qx, fmaf(qy, qy, qz * qz)) < Rb * Rb) {
+        const int q = atomicAdd(&ws.count[1], 1);
+        ws.queue[QUEUE_CAP - 1 - q] = static_cast<uint16_t>(lane << QUEUE_ITEM_BITS | i);
       }
-    }
-    for (int i = max(base, O) + sub; i < end; i += L) {
-      {
-        // the batch bound against the other box's bounding sphere and against the
-        // oriented box holding its spheres (centre, yaw, sphere hull); a contact
-        // needs both: |d| < Rb + r_box and ||max(|u| - hull, 0)|| < Rb
-        const int4 er = *reinterpret_cast<const int4*>(env + (i - O) * ENV_W);  // box, src, slot
-        const float4* br = reinterpret_cast<const float4*>(boxr + er.x * BOX_W);
-        const float4 b0 = br[0], b2 = br[2];  // (half extents, bound radius), (cos, sin, hull x, y)
-        const float hull_z = br[3].x;
-        float x, y, z, cy_, sy_;
-        if (er.y < 0) {
-          const float4 b1 = br[1];
-          x = b1.x; y = b1.y; z = b1.z; cy_ = b2.x; sy_ = b2.y;
-        } else {
-          const float4 pp = place[er.z * PT + pl];
-          x = pp.x; y = pp.y; z = __int_as_float(slots[er.z * SLOT_W + 2]); cy_ = pp.z; sy_ = pp.w;
+    };
+    if constexpr (PR) {
+      for (int i = base + 2 * sub; i < cend; i += 2 * L) {
+        const float4* q = obs2 + (i >> 1) * (OBS2_W / 4);
+        const float4 q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3], q4 = q[4], q5 = q[5], q6 = q[6], q7 = q[7];
+        const float2 ux = __ffma2_rn(make_float2(q0.x, q0.y), cx2,
+                                     __ffma2_rn(make_float2(q0.z, q0.w), cy2,
+                                                __ffma2_rn(make_float2(q1.x, q1.y), cz2, make_float2(q1.z, q1.w))));
+        const float2 uy = __ffma2_rn(make_float2(q2.x, q2.y), cx2,
+                                     __ffma2_rn(make_float2(q2.z, q2.w), cy2,
+                                                __ffma2_rn(make_float2(q3.x, q3.y), cz2, make_float2(q3.z, q3.w))));
+        const float2 uz = __ffma2_rn(make_float2(q4.x, q4.y), cx2,
+                                     __ffma2_rn(make_float2(q4.z, q4.w), cy2,
+                                                __ffma2_rn(make_float2(q5.x, q5.y), cz2, make_float2(q5.z, q5.w))));
+        // max_i(|u_i| - h_i) < Rb for each of the two (i + 1 = O: the far pad)
+        if (fmaxf(fabsf(ux.x) - q6.x, fmaxf(fabsf(uy.x) - q6.z, fabsf(uz.x) - q7.x)) < Rb) {
+          const int e = atomicAdd(&ws.count[0], 1);
+          ws.queue[e] = static_cast<uint16_t>(lane << QUEUE_ITEM_BITS | i);
         }
-        const float dx = cbx - x, dy = cby - y, dz = cbz - z, R = Rb + b0.w;
-        const float ux = fmaf(cy_, dx, sy_ * dy), uy = fmaf(-sy_, dx, cy_ * dy);
-        const float qx = fmaxf(fabsf(ux) - b2.z, 0.f), qy = fmaxf(fabsf(uy) - b2.w, 0.f);
-        const float qz = fmaxf(fabsf(dz) - hull_z, 0.f);
-        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R * R && fmaf(qx, qx, fmaf(qy, qy, qz * qz)) < Rb * Rb) {
-          const int q = atomicAdd(&ws.count[1], 1);
-          ws.queue[QUEUE_CAP - 1 - q] = static_cast<uint16_t>(lane << QUEUE_ITEM_BITS | i);
+        if (fmaxf(fabsf(ux.y) - q6.y, fmaxf(fabsf(uy.y) - q6.w, fabsf(uz.y) - q7.y)) < Rb) {
+          const int e = atomicAdd(&ws.count[0], 1);
+          ws.queue[e] = static_cast<uint16_t>(lane << QUEUE_ITEM_BITS | (i + 1));
+        }
+      }
+      for (int i = max(base, O) + sub; i < end; i += L) box_test(i);
+    } else {
+      for (int i = base + sub; i < end; i += L) {
+        if (i < O) {
+          if (obb_gap(load_obb(obs, i, O), cbx, cby, cbz) < Rb) {
+            const int e = atomicAdd(&ws.count[0], 1);
+            ws.queue[e] = static_cast<uint16_t>(lane << QUEUE_ITEM_BITS | i);
+          }
+        } else {
+          box_test(i);
         }
       }
     }
@@ -446,7 +460,7 @@ __device__ __forceinline__ float bound_dist(const float (&v)[N], const float (&l
 //   phase 1  links (tip to base); the frame steps back to T_{l-1} after each
 //   phase 2  spheres fixed to the base (tail, cost only)
 //   phase 3  the placed box at P(p) (tail of a Place: CFreePlace)
-template <int L, bool EX, bool KT>
+template <int L, bool EX, bool KT, bool PR>
 __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __restrict__ pb, int k, int piece,
                             const float* __restrict__ X, float* G, float* Tm, const int* __restrict__ slots,
                             const float4* __restrict__ place, const float2* __restrict__ trig,
@@ -746,7 +760,7 @@ __device__ void eval_config(const uint32_t* __restrict__ sc, const uint32_t* __r
       }
     }
     const float wenv = phase == 3 ? w_cp : w_cf;
-    const float Jb = collide<L>(cx, cyy, cz, cr, gx, gyy, gz, cbx, cby, cbz, Rb, obs, obs2, O, env, n_env, boxr, slots,
+    const float Jb = collide<L, PR>(cx, cyy, cz, cr, gx, gyy, gz, cbx, cby, cbz, Rb, obs, obs2, O, env, n_env, boxr, slots,
                                 bloc, binit, NBS, place, G, pl, sub, lane, wenv, ws, n_obb, n_box);
     if (phase == 3) {
       J_place += Jb;
@@ -1389,7 +1403,7 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
       item = __shfl_sync(0xffffffffu, item, 0);
       if (item >= n_work) break;
       if (item < NPIECE * K) {
-        eval_config<L, EX, KT>(s_sc, s_pb, K - 1 - item / NPIECE, item % NPIECE, sx, sg, st, slots, splace, strig, ws, n_obb,
+        eval_config<L, EX, KT, FEAT == 0>(s_sc, s_pb, K - 1 - item / NPIECE, item % NPIECE, sx, sg, st, slots, splace, strig, ws, n_obb,
                        n_box, lane, pl, sub);
       } else if (SC && item < NPIECE * K + n_self) {
         if constexpr (SC)
