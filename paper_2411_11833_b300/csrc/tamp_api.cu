@@ -1734,26 +1734,29 @@ static_assert(sizeof(ProbDesc) <= kStaticItemsOff - kStaticDescOff, "descriptor 
 __device__ __align__(256) unsigned char g_eval_scratch[kStaticBytes];
 
 constexpr int kMaxDevices = 64;
-std::once_flag g_scratch_once[kMaxDevices];
-unsigned char* g_scratch_dev[kMaxDevices];
-cudaError_t g_scratch_err[kMaxDevices];
+std::mutex g_scratch_mu;
+unsigned char* g_scratch_dev[kMaxDevices];   // non-null once the device's set-up has succeeded
 
 // With `device` current: resolve the array's device address and write the
-// work-item list (tile i of problem 0), which never changes afterwards.
+// work-item list (tile i of problem 0), which never changes afterwards.  The
+// copy is finished on the device before the address is published, so a first
+// call whose kernel runs on any stream reads the complete list.  Only a set-up
+// that succeeded is kept: after a failure the next call tries again.
 cudaError_t static_scratch(int device, unsigned char** out) {
-  std::call_once(g_scratch_once[device], [device]() {
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_dev[device]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_eval_scratch);
-    if (e == cudaSuccess) {
-      uint32_t items[kStaticTiles];
-      for (int i = 0; i < kStaticTiles; ++i) items[i] = static_cast<uint32_t>(i);
-      e = cudaMemcpy(static_cast<unsigned char*>(p) + kStaticItemsOff, items, sizeof items, cudaMemcpyHostToDevice);
-    }
+    if (e != cudaSuccess) return e;
+    static uint32_t items[kStaticTiles];
+    for (int i = 0; i < kStaticTiles; ++i) items[i] = static_cast<uint32_t>(i);
+    e = cudaMemcpy(static_cast<unsigned char*>(p) + kStaticItemsOff, items, sizeof items, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return e;
     g_scratch_dev[device] = static_cast<unsigned char*>(p);
-    g_scratch_err[device] = e;
-  });
+  }
   *out = g_scratch_dev[device];
-  return g_scratch_err[device];
+  return cudaSuccess;
 }
 
 }  // namespace

@@ -59,3 +59,49 @@ def test_static_scratch_eval_matches_eval_on_two_calls_in_a_row():
     st = lib.tamp_eval_static_scratch(scene._h, pid, big, _p(x), _p(cost), _p(terms), _p(flags), _p(grad))
     assert st == 1 and b"static scratch limit" in lib.tamp_last_error(scene._h)
     scene.close()
+
+
+_FIRST_CALL_ON_A_SIDE_STREAM = r"""
+import ctypes, sys
+import numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+import scenegen as sg
+import paper_2411_11833_b300 as pkg
+from paper_2411_11833_b300 import _native
+from tests.parity import COST_FLOOR, COST_REL
+lib = _native.load()
+torch.cuda.set_device(0)
+side = torch.cuda.Stream()
+with torch.cuda.stream(side):                     # the scene's stream is this non-blocking side stream
+    sc, acts = sg.packing_problem(2001)
+    scene = pkg.Scene(sc)
+    pid = scene.set_skeleton(acts)
+    D, nt, _ = scene.problem_info(pid)
+    n = 2000                                       # 63 tiles: a stale work-item list would show
+    X = sg.random_particles(sc, acts, n, seed=3)
+    x = torch.tensor(np.ascontiguousarray(X.T), dtype=torch.float32, device="cuda")
+    cost = torch.full((n,), float("nan"), device="cuda")
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    st = lib.tamp_eval_static_scratch(scene._h, pid, n, p(x), p(cost), None, None, None)
+    assert st == 0, lib.tamp_last_error(scene._h).decode()
+    cost_r = scene.eval(pid, x)[0]
+side.synchronize()
+c, cr = cost.cpu().double().numpy(), cost_r.cpu().double().numpy()
+assert np.isfinite(c).all(), "some tiles were never evaluated"
+assert (np.abs(c - cr) <= COST_REL * np.maximum(np.abs(cr), COST_FLOOR)).all()
+scene.close()
+print("first call on a side stream ok")
+"""
+
+
+def test_static_scratch_first_call_on_a_side_stream():
+    # The array is set up by the first call in a process, so this runs in a
+    # fresh one whose first call is issued on a non-default stream.
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = subprocess.run([sys.executable, "-c", _FIRST_CALL_ON_A_SIDE_STREAM, root], capture_output=True,
+                         text=True, timeout=600, cwd=root)
+    assert res.returncode == 0, res.stdout + res.stderr
+    assert "first call on a side stream ok" in res.stdout
