@@ -161,14 +161,16 @@ def sphere_sphere_penetration(ca, ra, cb, rb) -> torch.Tensor:
 
 
 def dist_from_bounds(v: torch.Tensor, lo: torch.Tensor, hi: torch.Tensor) -> torch.Tensor:
-    """Euclidean distance of v[..., d] from the box [lo, hi] (0 inside).
+    """Euclidean distance from the point v[..., d] to the axis-aligned box [lo, hi].
 
-    Per coordinate the excess is the larger of (lo - v) and (v - hi), floored
-    at zero; the result is the L2 norm of the excess vector (appendix listing,
-    used for joint limits, containment and grasp bounds).
+    The nearest point of the box is v with each coordinate clamped into its
+    interval, so the distance is the norm of v minus that point (0 inside).
+    The appendix scores joint limits (Motion), placement containment
+    (StablePlace) and, in the library's reading, grasp bounds (Grasp) by this
+    distance.
     """
-    excess = torch.maximum(lo - v, v - hi).clamp(min=0.0)
-    return norm(excess)
+    nearest = torch.minimum(torch.maximum(v, lo), hi)
+    return norm(v - nearest)
 
 
 def obj_dist(pos: torch.Tensor) -> torch.Tensor:

@@ -199,6 +199,45 @@ def test_pose_error_pure_offsets():
     assert float(e_pos) < 1e-15 and float(e_rot) == pytest.approx(0.7, abs=1e-14)
 
 
+# ------------------------------------------------------------------ containment and grasp bounds
+
+def _bounds_case_errors():
+    """Largest error of the StablePlace and Grasp terms against the hand-worked
+    cases, each case evaluated through the problem's own term list (the
+    witness skeleton Pick(0)-Place(0) with box 0 and surface 0 replaced)."""
+    gold = _gold("bounds_hand_values.json")
+    sc0, acts, x0 = _scara_witness_scene()
+    worst_c = 0.0
+    for case in gold["containment"]:
+        sc = dataclasses.replace(sc0, box_half=sc0.box_half.copy(), surf=sc0.surf.copy())
+        sc.box_half[0, :2] = case["box_half"]
+        sc.surf[0, :5] = case["surface"]
+        pr = Problem(sc, acts)
+        x = x0.clone()
+        p_off = pr.configs[1]["target"][1]
+        x[0, p_off:p_off + 3] = torch.tensor(case["placement"], dtype=DT)
+        ti = [t.kind for t in pr.terms].index(STABLE_PLACE)
+        got = float(pr.term_values(x)[0, ti])
+        worst_c = max(worst_c, abs(got - case["value"]))
+    worst_g = 0.0
+    for case in gold["grasp"]:
+        sc = dataclasses.replace(sc0, box_half=sc0.box_half.copy())
+        sc.box_half[0] = case["box_half"]
+        pr = Problem(sc, acts, Options(grasp_dof=case["dof"]))
+        x = torch.zeros(1, pr.D, dtype=DT)
+        x[0, 0:3] = torch.tensor(case["g"], dtype=DT)
+        ti = [t.kind for t in pr.terms].index(GRASP)
+        got = float(pr.term_values(x)[0, ti])
+        worst_g = max(worst_g, abs(got - case["value"]))
+    return worst_c, worst_g
+
+
+def test_containment_and_grasp_bounds_hand_values():
+    worst_c, worst_g = _bounds_case_errors()
+    assert worst_c < 1e-12
+    assert worst_g < 1e-12
+
+
 # ------------------------------------------------------------------ constructed witness
 
 def _scara_witness_scene(seed=5):
@@ -501,3 +540,40 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(PM.Problem, "_containment", cont_world)
     assert _invariance_error()[0] > 1e-6
     monkeypatch.setattr(PM.Problem, "_containment", orig_cont)
+
+    # 6.-7. containment with the box's half extents swapped, or with a corner left out
+    def cont_variant(swap, corners):
+        def cont(self, b, s, p):
+            cx, cy, syaw, hx, hy, _z = (float(v) for v in self.sc.surf[s])
+            h = self.sc.box_half[b][[1, 0]] if swap else self.sc.box_half[b]
+            cs, ss = math.cos(syaw), math.sin(syaw)
+            c, si = torch.cos(p[:, 2]), torch.sin(p[:, 2])
+            total = torch.zeros(p.shape[0], dtype=DT)
+            for sx, sy in corners:
+                wx = p[:, 0] + c * (sx * h[0]) - si * (sy * h[1]) - cx
+                wy = p[:, 1] + si * (sx * h[0]) + c * (sy * h[1]) - cy
+                u = torch.stack([cs * wx + ss * wy, -ss * wx + cs * wy], dim=-1)
+                total = total + G.dist_from_bounds(u, torch.tensor([-hx, -hy], dtype=DT),
+                                                   torch.tensor([hx, hy], dtype=DT))
+            return total
+        return cont
+    four = [(-1.0, -1.0), (-1.0, 1.0), (1.0, -1.0), (1.0, 1.0)]
+    assert _bounds_case_errors()[0] < 1e-12           # the rewritten form itself agrees
+    monkeypatch.setattr(PM.Problem, "_containment", cont_variant(False, four))
+    assert _bounds_case_errors()[0] < 1e-12
+    monkeypatch.setattr(PM.Problem, "_containment", cont_variant(True, four))
+    assert _bounds_case_errors()[0] > 1e-3
+    for dropped in range(4):
+        monkeypatch.setattr(PM.Problem, "_containment", cont_variant(False, four[:dropped] + four[dropped + 1:]))
+        assert _bounds_case_errors()[0] > 1e-3
+    monkeypatch.setattr(PM.Problem, "_containment", orig_cont)
+
+    # 8. the top-down grasp's lower z bound taken as -h_z (the whole box) instead of h_z - 0.02
+    orig_gb = PM.Problem._grasp_bounds
+
+    def gb_whole_box(self, b):
+        h = self.sc.box_half[b]
+        return torch.tensor([-h[0], -h[1], -h[2]], dtype=DT), torch.tensor([h[0], h[1], h[2]], dtype=DT)
+    monkeypatch.setattr(PM.Problem, "_grasp_bounds", gb_whole_box)
+    assert _bounds_case_errors()[1] > 1e-3
+    monkeypatch.setattr(PM.Problem, "_grasp_bounds", orig_gb)
