@@ -13,8 +13,9 @@
  *     outputs are left untouched and tamp_last_error() describes the cause;
  *   - geometry is in metres and radians, z up; 4x4 poses are row-major;
  *   - host pointers are owned by the caller and only read/written during the
- *     call; the library owns all device memory it allocates (cudaMalloc on the
- *     scene's device) and frees it in tamp_destroy_scene;
+ *     call; the library owns all device memory it allocates for a scene -- by
+ *     cudaMalloc on the scene's device, or from the caller's tamp_allocator --
+ *     and gives it back at the latest in tamp_destroy_scene;
  *   - all GPU work of a scene is issued on the stream given at creation, in call
  *     order; calls on one scene must not be made from two threads at once;
  *   - particle arrays are structure-of-arrays: component c of particle i is at
@@ -152,10 +153,27 @@ typedef struct {
 
 void tamp_default_options(tamp_options *opt);
 
+/* A caller-supplied device allocator (optional; not part of the paper's
+ * method).  alloc returns `bytes` bytes of device memory on `device`, to be
+ * used on `stream` (the scene's stream), or NULL when it cannot (the library
+ * call then fails with TAMP_ERR_OOM or TAMP_ERR_CUDA); free gives back a block
+ * that alloc returned, with the same device and stream.  ctx is passed through
+ * unchanged.  Both callbacks are called on the thread that makes the library
+ * call, during that call.  A host framework that pools device memory (e.g.
+ * PyTorch's caching allocator) can so back every buffer of a scene. */
+typedef struct {
+  void *(*alloc)(size_t bytes, int device, void *stream, void *ctx);
+  void (*free)(void *ptr, int device, void *stream, void *ctx);
+  void *ctx;
+} tamp_allocator;
+
 /* Copy a scene to the device.  device: CUDA ordinal; stream: a cudaStream_t
- * (NULL = legacy default stream).  *out receives the handle. */
+ * (NULL = legacy default stream).  allocator: NULL = cudaMalloc / cudaFree;
+ * otherwise (copied; alloc and free both set, else TAMP_ERR_INVALID_ARG) every
+ * device buffer of the scene, of its problems, graphs and autotuner trials
+ * comes from it.  *out receives the handle. */
 tamp_status tamp_create_scene(const tamp_scene_desc *desc, int device, void *stream,
-                              tamp_scene **out);
+                              const tamp_allocator *allocator, tamp_scene **out);
 tamp_status tamp_destroy_scene(tamp_scene *scene);
 
 /* Compile a skeleton (Sec. V: con(pi), cost(pi), the particle layout above).
@@ -251,9 +269,17 @@ tamp_status tamp_get_particles(tamp_scene *scene, int problem_id, float *x, floa
 /* OptimizeParticles (Alg. 1; Sec. V-B): n_steps Adam updates of each listed
  * problem's batch.  At x_t before every update, and once more after the last
  * update, every particle is checked against Eq. 3; the first check index with a
- * satisfying particle is recorded per problem.  Asynchronous on the stream. */
+ * satisfying particle is recorded per problem.
+ * stop_on_first_satisfying = 0: all n_steps run, asynchronously on the stream.
+ * stop_on_first_satisfying = k > 0 (the stopping criterion of Alg. 1 and Sec.
+ * V-B): the steps run in chunks of k (the last one shorter), and every chunk
+ * after the first one whose checks found a satisfying particle in any listed
+ * problem is skipped on the device, without a host round trip; the call then
+ * synchronises to read back how many steps ran (tamp_get_particles reports the
+ * step count).  The results of the last check (tamp_query_satisfied) are those
+ * of the last chunk that ran. */
 tamp_status tamp_optimize_steps(tamp_scene *scene, const int *problem_ids, int n_problems,
-                                int n_steps);
+                                int n_steps, int stop_on_first_satisfying);
 
 /* A CUDA graph of the optimisation loop (OptimizeParticles, Alg. 1; Sec. V-B):
  * n_chunks chunks of steps_per_chunk fused iterations of the listed problems,

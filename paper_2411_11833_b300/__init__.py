@@ -38,6 +38,30 @@ def _torch():
     return torch
 
 
+def _torch_allocator():
+    """tamp_allocator callbacks on PyTorch's caching allocator.  Returns the
+    struct and a record of the live blocks (the callbacks must outlive the
+    scene, so the Scene keeps both)."""
+    torch = _torch()
+    live = {}
+
+    def alloc(nbytes, device, stream, _ctx):
+        try:
+            ptr = torch.cuda.caching_allocator_alloc(int(nbytes), device=int(device), stream=int(stream or 0))
+        except RuntimeError:
+            return None
+        live[ptr] = int(nbytes)
+        return ptr
+
+    def free(ptr, _device, _stream, _ctx):
+        if ptr:
+            live.pop(ptr, None)
+            torch.cuda.caching_allocator_delete(ptr)
+
+    cb = (_native.ALLOC_FN(alloc), _native.FREE_FN(free))
+    return _native.Allocator(cb[0], cb[1], None), cb, live
+
+
 def _ptr(t) -> int:
     return 0 if t is None else int(t.data_ptr())
 
@@ -45,12 +69,16 @@ def _ptr(t) -> int:
 class Scene:
     """A scene on one device; owns its problems (compiled skeletons)."""
 
-    def __init__(self, sc, device: int = 0, stream=None):
+    def __init__(self, sc, device: int = 0, stream=None, torch_allocator: bool = False):
+        """``torch_allocator``: back every device buffer of the scene with
+        PyTorch's caching allocator (tamp_allocator callbacks) instead of
+        cudaMalloc."""
         lib = _native.load()
         self._lib = lib
         torch = _torch()
         if stream is None:
             stream = torch.cuda.current_stream(device).cuda_stream
+        self._alloc = _torch_allocator() if torch_allocator else None
         keep = {}
 
         def arr(name, dtype=np.float64):
@@ -79,7 +107,8 @@ class Scene:
         d.n_surf = int(np.asarray(sc.surf).shape[0])
         d.surf = _dptr(arr("surf"))
         h = ctypes.c_void_p()
-        st = lib.tamp_create_scene(ctypes.byref(d), int(device), ctypes.c_void_p(stream), ctypes.byref(h))
+        alloc = ctypes.byref(self._alloc[0]) if self._alloc else None
+        st = lib.tamp_create_scene(ctypes.byref(d), int(device), ctypes.c_void_p(stream), alloc, ctypes.byref(h))
         if st != 0:
             raise TampError(st, "tamp_create_scene rejected the scene description")
         self._h = h
@@ -176,11 +205,13 @@ class Scene:
     def _n(self, pid):
         return self._sizes[pid]
 
-    def optimize(self, pids, n_steps: int):
+    def optimize(self, pids, n_steps: int, stop_every: int = 0):
+        """tamp_optimize_steps; ``stop_every`` = k > 0 stops at the end of the
+        first chunk of k iterations in which a satisfying particle was found."""
         if isinstance(pids, int):
             pids = [pids]
         arr = (ctypes.c_int * len(pids))(*pids)
-        self._check(self._lib.tamp_optimize_steps(self._h, arr, len(pids), int(n_steps)))
+        self._check(self._lib.tamp_optimize_steps(self._h, arr, len(pids), int(n_steps), int(stop_every)))
 
     def query(self, pid: int, n: int, want_particles: bool = False):
         D, nt, kinds = self.problem_info(pid)

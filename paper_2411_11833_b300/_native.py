@@ -41,11 +41,20 @@ class Options(ctypes.Structure):
     ]
 
 
+# tamp_allocator: the callbacks' C types and the struct
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
 # every symbol include/tamp.h declares, with its ctypes signature
 SIGNATURES = {
     "tamp_default_options": (None, [ctypes.POINTER(Options)]),
     "tamp_create_scene": (ctypes.c_int, [ctypes.POINTER(SceneDesc), ctypes.c_int, ctypes.c_void_p,
-                                         ctypes.POINTER(ctypes.c_void_p)]),
+                                         ctypes.POINTER(Allocator), ctypes.POINTER(ctypes.c_void_p)]),
     "tamp_destroy_scene": (ctypes.c_int, [ctypes.c_void_p]),
     "tamp_set_skeleton": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Action), ctypes.c_int,
                                          ctypes.POINTER(Options), c_int_p]),
@@ -59,7 +68,7 @@ SIGNATURES = {
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "tamp_get_particles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, c_int_p, ctypes.c_int]),
-    "tamp_optimize_steps": (ctypes.c_int, [ctypes.c_void_p, c_int_p, ctypes.c_int, ctypes.c_int]),
+    "tamp_optimize_steps": (ctypes.c_int, [ctypes.c_void_p, c_int_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "tamp_query_satisfied": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, c_int_p, c_int_p,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "tamp_eval": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,

@@ -20,8 +20,9 @@
 namespace tamp {
 cudaError_t launch_optimize(const LaunchArgs& a, int L, int warps, int grid, size_t smem, cudaStream_t st);
 cudaError_t optimize_set_smem(int L, size_t smem);
-cudaError_t launch_chunk_control(int* t_dev, const int* const* first_iters, int n_problems, int steps,
-                                 int stop_on_first, int* stop, int* chunks_run, cudaStream_t st);
+cudaError_t launch_chunk_control(int* t_dev, const int* const* first_iters, int* const* counts, const int* n_counts,
+                                 int n_problems, int steps, int stop_on_first, int* stop, int* chunks_run, int last,
+                                 cudaStream_t st);
 size_t optimize_tile_bytes(int prob_words, int D, int NT, int NSLOT, int NANG, int L, bool mv_global);
 size_t optimize_scratch_bytes(int warps);
 int optimize_blocks_per_sm(int L, int warps, size_t smem);
@@ -86,6 +87,7 @@ struct Problem {
 struct tamp_scene {
   int device = 0;
   cudaStream_t stream = nullptr;
+  tamp_allocator alloc{};                 // the caller's device allocator (alloc == NULL: cudaMalloc)
   int nj = 0, S = 0, B = 0, NBS = 0, O = 0, NS = 0;
   std::vector<double> box_half, box_init, surf;
   std::vector<double> dh_a, dh_d, dh_alpha;
@@ -104,6 +106,10 @@ struct tamp_scene {
   uint32_t* d_items = nullptr;
   int items_cap = 0;
   int* d_item_counter = nullptr;
+  // control block of tamp_optimize_steps when it stops on the first satisfying
+  // particle (library-owned, grown on demand)
+  unsigned char* d_ctl = nullptr;
+  size_t ctl_cap = 0;
   std::vector<Problem*> probs;
   std::string err;
 };
@@ -139,6 +145,28 @@ inline void align4(std::vector<uint32_t>& v) {
   while (v.size() % 4) v.push_back(0);
 }
 inline void push_f(std::vector<uint32_t>& v, double x) { v.push_back(fbits(static_cast<float>(x))); }
+
+// Device memory of a scene: from the caller's allocator when tamp_create_scene
+// was given one, else cudaMalloc / cudaFree.
+cudaError_t dalloc_raw(tamp_scene* s, void** p, size_t bytes) {
+  if (s->alloc.alloc) {
+    *p = s->alloc.alloc(bytes, s->device, s->stream, s->alloc.ctx);
+    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+template <class T>
+cudaError_t dalloc(tamp_scene* s, T** p, size_t bytes) {
+  void* v = nullptr;
+  const cudaError_t e = dalloc_raw(s, &v, bytes);
+  *p = static_cast<T*>(v);
+  return e;
+}
+void dfree(tamp_scene* s, void* p) {
+  if (!p) return;
+  if (s->alloc.alloc) s->alloc.free(p, s->device, s->stream, s->alloc.ctx);
+  else cudaFree(p);
+}
 
 struct DeviceGuard {
   int prev = -1;
@@ -820,9 +848,9 @@ int feat_of(bool knots, bool g6, bool self) {
 }
 int problem_feat(const Problem& pr) { return feat_of(pr.n_seg > 0, pr.grasp6, pr.self); }
 
-void free_batch(Problem& pr) {
-  cudaFree(pr.d_x); cudaFree(pr.d_m); cudaFree(pr.d_v); cudaFree(pr.d_cost);
-  cudaFree(pr.d_flags); cudaFree(pr.d_counts); cudaFree(pr.d_first); cudaFree(pr.d_work);
+void free_batch(tamp_scene* s, Problem& pr) {
+  dfree(s, pr.d_x); dfree(s, pr.d_m); dfree(s, pr.d_v); dfree(s, pr.d_cost);
+  dfree(s, pr.d_flags); dfree(s, pr.d_counts); dfree(s, pr.d_first); dfree(s, pr.d_work);
   pr.d_x = pr.d_m = pr.d_v = pr.d_cost = nullptr;
   pr.d_flags = nullptr; pr.d_counts = nullptr; pr.d_first = nullptr; pr.d_work = nullptr;
   pr.cap = 0;
@@ -830,16 +858,16 @@ void free_batch(Problem& pr) {
 
 tamp_status ensure_batch(tamp_scene* s, Problem& pr, int P) {
   if (P > pr.cap) {
-    free_batch(pr);
+    free_batch(s, pr);
     const size_t n = static_cast<size_t>(pr.D) * P;
-    CUDA_TRY(s, cudaMalloc(&pr.d_x, n * 4));
-    CUDA_TRY(s, cudaMalloc(&pr.d_m, n * 4));
-    CUDA_TRY(s, cudaMalloc(&pr.d_v, n * 4));
-    CUDA_TRY(s, cudaMalloc(&pr.d_cost, static_cast<size_t>(P) * 4));
-    CUDA_TRY(s, cudaMalloc(&pr.d_flags, static_cast<size_t>(P)));
-    CUDA_TRY(s, cudaMalloc(&pr.d_counts, static_cast<size_t>(std::max(pr.NCON, 1)) * 4));
-    CUDA_TRY(s, cudaMalloc(&pr.d_first, 4));
-    CUDA_TRY(s, cudaMalloc(&pr.d_work, 2 * sizeof(unsigned long long)));
+    CUDA_TRY(s, dalloc(s, &pr.d_x, n * 4));
+    CUDA_TRY(s, dalloc(s, &pr.d_m, n * 4));
+    CUDA_TRY(s, dalloc(s, &pr.d_v, n * 4));
+    CUDA_TRY(s, dalloc(s, &pr.d_cost, static_cast<size_t>(P) * 4));
+    CUDA_TRY(s, dalloc(s, &pr.d_flags, static_cast<size_t>(P)));
+    CUDA_TRY(s, dalloc(s, &pr.d_counts, static_cast<size_t>(std::max(pr.NCON, 1)) * 4));
+    CUDA_TRY(s, dalloc(s, &pr.d_first, 4));
+    CUDA_TRY(s, dalloc(s, &pr.d_work, 2 * sizeof(unsigned long long)));
     pr.cap = P;
   }
   CUDA_TRY(s, cudaMemsetAsync(pr.d_work, 0, 2 * sizeof(unsigned long long), s->stream));
@@ -968,17 +996,17 @@ tamp_status launch_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lan
   tamp_status st = plan_jobs(s, jobs, requested_lanes, &plan, forced_L, forced_W);
   if (st != TAMP_OK) return st;
   if (static_cast<int>(jobs.size()) > s->descs_cap) {
-    cudaFree(s->d_descs);
+    dfree(s, s->d_descs);
     s->d_descs = nullptr;
     s->descs_cap = 0;
-    CUDA_TRY(s, cudaMalloc(&s->d_descs, jobs.size() * sizeof(ProbDesc)));
+    CUDA_TRY(s, dalloc(s, &s->d_descs, jobs.size() * sizeof(ProbDesc)));
     s->descs_cap = static_cast<int>(jobs.size());
   }
   if (static_cast<int>(plan.items.size()) > s->items_cap) {
-    cudaFree(s->d_items);
+    dfree(s, s->d_items);
     s->d_items = nullptr;
     s->items_cap = 0;
-    CUDA_TRY(s, cudaMalloc(&s->d_items, plan.items.size() * 4));
+    CUDA_TRY(s, dalloc(s, &s->d_items, plan.items.size() * 4));
     s->items_cap = static_cast<int>(plan.items.size());
   }
   CUDA_TRY(s, cudaMemcpyAsync(s->d_descs, plan.descs.data(), plan.descs.size() * sizeof(ProbDesc),
@@ -1024,6 +1052,88 @@ tamp_status run_state(tamp_scene* s, std::vector<Problem*> prs, int n_steps) {
   return TAMP_OK;
 }
 
+tamp_status check_device_error(tamp_scene* s);
+
+// tamp_optimize_steps stopping on the first satisfying particle: the steps run
+// as chunks of `chunk` fused iterations (the last one shorter), each followed
+// by the control kernel, which advances the step counts on the device and
+// raises the stop flag once a listed problem's Eq. 3 check has found a
+// satisfying particle; every later chunk returns at once.  The host then reads
+// the step counts back (this synchronises).
+tamp_status run_state_stopping(tamp_scene* s, const std::vector<Problem*>& prs, int n_steps, int chunk) {
+  const int n = static_cast<int>(prs.size());
+  const int full = n_steps / chunk, rem = n_steps % chunk, n_chunks = full + (rem ? 1 : 0);
+  // control block: ints [item counter, stop, chunks run, step counts [n], count sizes [n]], then pointers
+  // [first-satisfying records [n], count arrays [n]], then the descriptors of a full and of the last chunk
+  const size_t off_ptr = (4 * (3 + 2 * static_cast<size_t>(n)) + 15) & ~static_cast<size_t>(15);
+  const size_t off_desc = (off_ptr + 2 * n * sizeof(void*) + 15) & ~static_cast<size_t>(15);
+  const size_t bytes = off_desc + 2 * n * sizeof(ProbDesc);
+  if (bytes > s->ctl_cap) {
+    dfree(s, s->d_ctl);
+    s->d_ctl = nullptr;
+    s->ctl_cap = 0;
+    CUDA_TRY(s, dalloc(s, &s->d_ctl, bytes));
+    s->ctl_cap = bytes;
+  }
+  int* ints = reinterpret_cast<int*>(s->d_ctl);
+  void** ptrs = reinterpret_cast<void**>(s->d_ctl + off_ptr);
+  ProbDesc* descs = reinterpret_cast<ProbDesc*>(s->d_ctl + off_desc);
+  std::vector<unsigned char> host(bytes, 0);
+  int* hi = reinterpret_cast<int*>(host.data());
+  void** hp = reinterpret_cast<void**>(host.data() + off_ptr);
+  std::vector<Job> jobs;
+  for (int i = 0; i < n; ++i) {
+    Problem* pr = prs[i];
+    hi[3 + i] = pr->t;
+    hi[3 + n + i] = std::max(pr->NCON, 1);
+    hp[i] = pr->d_first;
+    hp[n + i] = pr->d_counts;
+    ProbDesc d = state_desc(*pr, chunk);
+    d.t_dev = ints + 3 + i;
+    jobs.push_back({pr, d});
+    CUDA_TRY(s, cudaMemsetAsync(pr->d_counts, 0, static_cast<size_t>(std::max(pr->NCON, 1)) * 4, s->stream));
+  }
+  Plan plan;
+  tamp_status st = plan_jobs(s, jobs, prs[0]->opt.lanes, &plan);
+  if (st != TAMP_OK) return st;
+  ProbDesc* hd = reinterpret_cast<ProbDesc*>(host.data() + off_desc);
+  for (int i = 0; i < n; ++i) {
+    hd[i] = plan.descs[i];
+    hd[n + i] = plan.descs[i];
+    hd[n + i].n_steps = rem;
+  }
+  if (static_cast<int>(plan.items.size()) > s->items_cap) {
+    dfree(s, s->d_items);
+    s->d_items = nullptr;
+    s->items_cap = 0;
+    CUDA_TRY(s, dalloc(s, &s->d_items, plan.items.size() * 4));
+    s->items_cap = static_cast<int>(plan.items.size());
+  }
+  CUDA_TRY(s, cudaMemcpyAsync(s->d_ctl, host.data(), bytes, cudaMemcpyHostToDevice, s->stream));
+  CUDA_TRY(s, cudaMemcpyAsync(s->d_items, plan.items.data(), plan.items.size() * 4, cudaMemcpyHostToDevice,
+                              s->stream));
+  for (int c = 0; c < n_chunks; ++c) {
+    const bool short_chunk = c == full;
+    LaunchArgs a = plan_args(s, plan, short_chunk ? descs + n : descs, s->d_items, ints);
+    a.stop = ints + 1;
+    CUDA_TRY(s, cudaMemsetAsync(ints, 0, sizeof(int), s->stream));
+    CUDA_TRY(s, launch_optimize(a, plan.L, plan.warps, plan.grid, plan.smem, s->stream));
+    CUDA_TRY(s, launch_chunk_control(ints + 3, reinterpret_cast<const int* const*>(ptrs),
+                                     reinterpret_cast<int* const*>(ptrs + n), ints + 3 + n, n,
+                                     short_chunk ? rem : chunk, 1, ints + 1, ints + 2, c == n_chunks - 1,
+                                     s->stream));
+  }
+  std::vector<int> t(3 + n, 0);
+  CUDA_TRY(s, cudaMemcpyAsync(t.data(), ints, t.size() * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  st = check_device_error(s);  // synchronises
+  if (st != TAMP_OK) return st;
+  for (int i = 0; i < n; ++i) {
+    prs[i]->t = t[3 + i];
+    prs[i]->checked = true;
+  }
+  return TAMP_OK;
+}
+
 Problem* get_problem(tamp_scene* s, int id) {
   if (!s || id < 0 || id >= static_cast<int>(s->probs.size())) return nullptr;
   return s->probs[id];
@@ -1057,9 +1167,11 @@ void tamp_default_options(tamp_options* o) {
   o->grasp_dof = 4;
 }
 
-tamp_status tamp_create_scene(const tamp_scene_desc* d, int device, void* stream, tamp_scene** out) {
+tamp_status tamp_create_scene(const tamp_scene_desc* d, int device, void* stream, const tamp_allocator* allocator,
+                              tamp_scene** out) {
   if (!d || !out) return TAMP_ERR_INVALID_ARG;
   *out = nullptr;
+  if (allocator && (!allocator->alloc || !allocator->free)) return TAMP_ERR_INVALID_ARG;
   tamp_scene* s = new tamp_scene();
   auto bad = [&](const char*) {
     delete s;
@@ -1081,6 +1193,7 @@ tamp_status tamp_create_scene(const tamp_scene_desc* d, int device, void* stream
     return bad("non-finite arm");
   s->device = device;
   s->stream = static_cast<cudaStream_t>(stream);
+  if (allocator) s->alloc = *allocator;
   s->nj = d->n_joints; s->S = d->n_spheres; s->B = d->n_boxes; s->NBS = d->spheres_per_box;
   s->O = d->n_obs; s->NS = d->n_surf;
   s->box_half.assign(d->box_half, d->box_half + 3 * d->n_boxes);
@@ -1095,16 +1208,16 @@ tamp_status tamp_create_scene(const tamp_scene_desc* d, int device, void* stream
     return st;
   }
   DeviceGuard g(device);
-  cudaError_t e = cudaMalloc(&s->d_blob, s->blob.size() * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_err, 4);
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_scratch_first, 4);
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_item_counter, 4);
+  cudaError_t e = dalloc(s, &s->d_blob, s->blob.size() * 4);
+  if (e == cudaSuccess) e = dalloc(s, &s->d_err, 4);
+  if (e == cudaSuccess) e = dalloc(s, &s->d_scratch_first, 4);
+  if (e == cudaSuccess) e = dalloc(s, &s->d_item_counter, 4);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_blob, s->blob.data(), s->blob.size() * 4, cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, 4, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) {
-    cudaFree(s->d_blob); cudaFree(s->d_err); cudaFree(s->d_scratch_first); cudaFree(s->d_item_counter);
+    dfree(s, s->d_blob); dfree(s, s->d_err); dfree(s, s->d_scratch_first); dfree(s, s->d_item_counter);
     delete s;
     return e == cudaErrorMemoryAllocation ? TAMP_ERR_OOM : TAMP_ERR_CUDA;
   }
@@ -1117,13 +1230,13 @@ tamp_status tamp_destroy_scene(tamp_scene* s) {
   DeviceGuard g(s->device);
   cudaStreamSynchronize(s->stream);
   for (Problem* p : s->probs) {
-    free_batch(*p);
-    cudaFree(p->d_blob);
-    cudaFree(p->d_prow); cudaFree(p->d_pfeat); cudaFree(p->d_pout); cudaFree(p->d_chains);
+    free_batch(s, *p);
+    dfree(s, p->d_blob);
+    dfree(s, p->d_prow); dfree(s, p->d_pfeat); dfree(s, p->d_pout); dfree(s, p->d_chains);
     delete p;
   }
-  cudaFree(s->d_blob); cudaFree(s->d_err); cudaFree(s->d_scratch_first); cudaFree(s->d_item_counter);
-  cudaFree(s->d_descs); cudaFree(s->d_items);
+  dfree(s, s->d_blob); dfree(s, s->d_err); dfree(s, s->d_scratch_first); dfree(s, s->d_item_counter);
+  dfree(s, s->d_descs); dfree(s, s->d_items); dfree(s, s->d_ctl);
   delete s;
   return TAMP_OK;
 }
@@ -1139,11 +1252,11 @@ tamp_status tamp_set_skeleton(tamp_scene* s, const tamp_action* acts, int n, con
     return st;
   }
   DeviceGuard g(s->device);
-  cudaError_t e = cudaMalloc(&pr->d_blob, pr->blob.size() * 4);
+  cudaError_t e = dalloc(s, &pr->d_blob, pr->blob.size() * 4);
   if (e == cudaSuccess) e = cudaMemcpyAsync(pr->d_blob, pr->blob.data(), pr->blob.size() * 4, cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) {
-    cudaFree(pr->d_blob);
+    dfree(s, pr->d_blob);
     delete pr;
     return fail(s, TAMP_ERR_CUDA, "skeleton upload: %s", cudaGetErrorString(e));
   }
@@ -1222,9 +1335,9 @@ static tamp_status sample_batch(tamp_scene* s, Problem* pr, int P, uint64_t seed
   CUDA_TRY(s, launch_sample(pr->d_blob, s->d_blob, pr->d_x, pr->d_m, pr->d_v, P, P, pr->D, seed, s->stream));
   if (sampler & TAMP_SAMPLE_LEARNED) {
     if (!pr->d_prow) {
-      CUDA_TRY(s, cudaMalloc(&pr->d_prow, pr->prow.size() * 4));
-      CUDA_TRY(s, cudaMalloc(&pr->d_pfeat, pr->pfeat.size() * 4));
-      CUDA_TRY(s, cudaMalloc(&pr->d_pout, static_cast<size_t>(pr->R) * 2 * PROP_NT * 4));
+      CUDA_TRY(s, dalloc(s, &pr->d_prow, pr->prow.size() * 4));
+      CUDA_TRY(s, dalloc(s, &pr->d_pfeat, pr->pfeat.size() * 4));
+      CUDA_TRY(s, dalloc(s, &pr->d_pout, static_cast<size_t>(pr->R) * 2 * PROP_NT * 4));
       CUDA_TRY(s, cudaMemcpyAsync(pr->d_prow, pr->prow.data(), pr->prow.size() * 4, cudaMemcpyHostToDevice, s->stream));
       CUDA_TRY(s, cudaMemcpyAsync(pr->d_pfeat, pr->pfeat.data(), pr->pfeat.size() * 4, cudaMemcpyHostToDevice,
                                   s->stream));
@@ -1239,7 +1352,7 @@ static tamp_status sample_batch(tamp_scene* s, Problem* pr, int P, uint64_t seed
                                 s->stream));
   if (sampler & TAMP_SAMPLE_IK) {
     if (!pr->d_chains) {
-      CUDA_TRY(s, cudaMalloc(&pr->d_chains, pr->chains.size() * 4));
+      CUDA_TRY(s, dalloc(s, &pr->d_chains, pr->chains.size() * 4));
       CUDA_TRY(s, cudaMemcpyAsync(pr->d_chains, pr->chains.data(), pr->chains.size() * 4, cudaMemcpyHostToDevice,
                                   s->stream));
     }
@@ -1333,9 +1446,10 @@ tamp_status tamp_get_particles(tamp_scene* s, int id, float* x, float* m, float*
   return check_device_error(s);
 }
 
-tamp_status tamp_optimize_steps(tamp_scene* s, const int* ids, int n, int n_steps) {
+tamp_status tamp_optimize_steps(tamp_scene* s, const int* ids, int n, int n_steps, int stop_on_first_satisfying) {
   if (!s) return TAMP_ERR_INVALID_ARG;
-  if (!ids || n <= 0 || n_steps < 0) return fail(s, TAMP_ERR_INVALID_ARG, "bad optimize arguments");
+  if (!ids || n <= 0 || n_steps < 0 || stop_on_first_satisfying < 0)
+    return fail(s, TAMP_ERR_INVALID_ARG, "bad optimize arguments");
   DeviceGuard g(s->device);
   for (int i = 0; i < n; ++i) {
     Problem* pr = get_problem(s, ids[i]);
@@ -1349,6 +1463,7 @@ tamp_status tamp_optimize_steps(tamp_scene* s, const int* ids, int n, int n_step
       return fail(s, TAMP_ERR_INVALID_ARG, "problem %d listed twice", ids[i]);
     prs.push_back(pr);
   }
+  if (stop_on_first_satisfying > 0 && n_steps > 0) return run_state_stopping(s, prs, n_steps, stop_on_first_satisfying);
   return run_state(s, prs, n_steps);
 }
 
@@ -1419,8 +1534,8 @@ tamp_status tamp_autotune(tamp_scene* s, const int* ids, int n, int trial_steps,
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   auto release = [&]() {
     for (Scratch& b : sc) {
-      cudaFree(b.x); cudaFree(b.m); cudaFree(b.v); cudaFree(b.cost); cudaFree(b.flags);
-      cudaFree(b.counts); cudaFree(b.first); cudaFree(b.work);
+      dfree(s, b.x); dfree(s, b.m); dfree(s, b.v); dfree(s, b.cost); dfree(s, b.flags);
+      dfree(s, b.counts); dfree(s, b.first); dfree(s, b.work);
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -1429,14 +1544,14 @@ tamp_status tamp_autotune(tamp_scene* s, const int* ids, int n, int trial_steps,
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   for (size_t i = 0; i < prs.size() && e == cudaSuccess; ++i) {
     const size_t nb = static_cast<size_t>(prs[i]->D) * prs[i]->P * 4;
-    e = cudaMalloc(&sc[i].x, nb);
-    if (e == cudaSuccess) e = cudaMalloc(&sc[i].m, nb);
-    if (e == cudaSuccess) e = cudaMalloc(&sc[i].v, nb);
-    if (e == cudaSuccess) e = cudaMalloc(&sc[i].cost, static_cast<size_t>(prs[i]->P) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&sc[i].flags, static_cast<size_t>(prs[i]->P));
-    if (e == cudaSuccess) e = cudaMalloc(&sc[i].counts, static_cast<size_t>(std::max(prs[i]->NCON, 1)) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&sc[i].first, 4);
-    if (e == cudaSuccess) e = cudaMalloc(&sc[i].work, 16);
+    e = dalloc(s, &sc[i].x, nb);
+    if (e == cudaSuccess) e = dalloc(s, &sc[i].m, nb);
+    if (e == cudaSuccess) e = dalloc(s, &sc[i].v, nb);
+    if (e == cudaSuccess) e = dalloc(s, &sc[i].cost, static_cast<size_t>(prs[i]->P) * 4);
+    if (e == cudaSuccess) e = dalloc(s, &sc[i].flags, static_cast<size_t>(prs[i]->P));
+    if (e == cudaSuccess) e = dalloc(s, &sc[i].counts, static_cast<size_t>(std::max(prs[i]->NCON, 1)) * 4);
+    if (e == cudaSuccess) e = dalloc(s, &sc[i].first, 4);
+    if (e == cudaSuccess) e = dalloc(s, &sc[i].work, 16);
   }
   if (e != cudaSuccess) {
     release();
@@ -1596,8 +1711,9 @@ struct tamp_graph {
   int steps = 0, chunks = 0;
   ProbDesc* d_descs = nullptr;
   uint32_t* d_items = nullptr;
-  int* d_ints = nullptr;  // [0] item counter, [1] stop, [2] chunks run, [3..] per-problem step counts
-  const int** d_first = nullptr;
+  int* d_ints = nullptr;  // [0] item counter, [1] stop, [2] chunks run, [3, 3 + n) per-problem step
+                          // counts, [3 + n, 3 + 2n) per-problem constraint counts (Eq. 5 array sizes)
+  void** d_first = nullptr;  // [0, n) first-satisfying records, [n, 2n) Eq. 5 count arrays
   cudaStream_t capture = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -1608,7 +1724,7 @@ void free_graph(tamp_graph* g) {
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   if (g->capture) cudaStreamDestroy(g->capture);
-  cudaFree(g->d_descs); cudaFree(g->d_items); cudaFree(g->d_ints); cudaFree(g->d_first);
+  dfree(g->s, g->d_descs); dfree(g->s, g->d_items); dfree(g->s, g->d_ints); dfree(g->s, g->d_first);
   delete g;
 }
 }  // namespace
@@ -1628,10 +1744,11 @@ extern "C" tamp_status tamp_graph_create(tamp_scene* s, const int* ids, int n, i
     free_graph(g);
     return st;
   };
-  cudaError_t e = cudaMalloc(&g->d_ints, (3 + n) * sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&g->d_first, n * sizeof(int*));
+  cudaError_t e = dalloc(s, &g->d_ints, (3 + 2 * n) * sizeof(int));
+  if (e == cudaSuccess) e = dalloc(s, &g->d_first, 2 * n * sizeof(void*));
   if (e != cudaSuccess) return bail(fail(s, TAMP_ERR_OOM, "graph buffers: %s", cudaGetErrorString(e)));
-  std::vector<const int*> firsts;
+  std::vector<void*> firsts(2 * n, nullptr);
+  std::vector<int> ncons(n, 0);
   for (int i = 0; i < n; ++i) {
     Problem* pr = get_problem(s, ids[i]);
     if (!pr) return bail(fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", ids[i]));
@@ -1643,33 +1760,39 @@ extern "C" tamp_status tamp_graph_create(tamp_scene* s, const int* ids, int n, i
     ProbDesc d = state_desc(*pr, steps_per_chunk);
     d.t_dev = g->d_ints + 3 + i;
     jobs.push_back({pr, d});
-    firsts.push_back(pr->d_first);
+    firsts[i] = pr->d_first;
+    firsts[n + i] = pr->d_counts;
+    ncons[i] = std::max(pr->NCON, 1);
   }
   Plan plan;
   tamp_status st = plan_jobs(s, jobs, g->prs[0]->opt.lanes, &plan);
   if (st != TAMP_OK) return bail(st);
-  e = cudaMalloc(&g->d_descs, plan.descs.size() * sizeof(ProbDesc));
-  if (e == cudaSuccess) e = cudaMalloc(&g->d_items, plan.items.size() * 4);
+  e = dalloc(s, &g->d_descs, plan.descs.size() * sizeof(ProbDesc));
+  if (e == cudaSuccess) e = dalloc(s, &g->d_items, plan.items.size() * 4);
   if (e == cudaSuccess)
     e = cudaMemcpy(g->d_descs, plan.descs.data(), plan.descs.size() * sizeof(ProbDesc), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_items, plan.items.data(), plan.items.size() * 4, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(g->d_first, firsts.data(), n * sizeof(int*), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_first, firsts.data(), 2 * n * sizeof(void*), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_ints + 3 + n, ncons.data(), n * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = optimize_set_smem(plan.L, plan.smem);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking);
   if (e != cudaSuccess) return bail(fail(s, TAMP_ERR_CUDA, "graph set-up: %s", cudaGetErrorString(e)));
   LaunchArgs a = plan_args(s, plan, g->d_descs, g->d_items, g->d_ints);
   a.stop = g->d_ints + 1;
-  // capture: per chunk, clear the counts and the item counter, optimise, control
+  // capture: clear the counts; per chunk, clear the item counter, optimise, control (which clears the
+  // counts again for the next chunk's final check unless the loop stops)
   e = cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal);
+  for (Problem* pr : g->prs)
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(pr->d_counts, 0, static_cast<size_t>(std::max(pr->NCON, 1)) * 4, g->capture);
   for (int c = 0; c < n_chunks && e == cudaSuccess; ++c) {
-    for (Problem* pr : g->prs)
-      if (e == cudaSuccess)
-        e = cudaMemsetAsync(pr->d_counts, 0, static_cast<size_t>(std::max(pr->NCON, 1)) * 4, g->capture);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->d_ints, 0, sizeof(int), g->capture);
     if (e == cudaSuccess) e = launch_optimize(a, plan.L, plan.warps, plan.grid, plan.smem, g->capture);
     if (e == cudaSuccess)
-      e = launch_chunk_control(g->d_ints + 3, g->d_first, n, steps_per_chunk, stop_on_first, g->d_ints + 1,
-                               g->d_ints + 2, g->capture);
+      e = launch_chunk_control(g->d_ints + 3, reinterpret_cast<const int* const*>(g->d_first),
+                               reinterpret_cast<int* const*>(g->d_first + n), g->d_ints + 3 + n, n,
+                               steps_per_chunk, stop_on_first, g->d_ints + 1, g->d_ints + 2, c == n_chunks - 1,
+                               g->capture);
   }
   cudaError_t e2 = cudaStreamEndCapture(g->capture, &g->graph);
   if (e == cudaSuccess) e = e2;
@@ -1684,7 +1807,7 @@ extern "C" tamp_status tamp_graph_run(tamp_graph* g, int* steps_run) {
   tamp_scene* s = g->s;
   DeviceGuard dg(s->device);
   const int n = static_cast<int>(g->prs.size());
-  std::vector<int> host(3 + n, 0);
+  std::vector<int> host(3 + n, 0);  // the control words and step counts (the count sizes stay)
   for (int i = 0; i < n; ++i) {
     if (g->prs[i]->P != g->sizes[i] || !g->prs[i]->has_batch)
       return fail(s, TAMP_ERR_STATE, "batch of a graph's problem changed size; rebuild the graph");

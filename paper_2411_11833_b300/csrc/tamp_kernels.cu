@@ -1947,25 +1947,41 @@ cudaError_t launch_ffma_probe(float* out, int blocks, int iters, cudaStream_t st
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ graph chunk controller
-// After each chunk of a captured optimisation: advance every problem's step
-// count, and raise the stop flag when stopping on the first satisfying particle
-// and some problem has one (the Eq. 3 check records its iteration).
-__global__ void chunk_control_kernel(int* t_dev, const int* const* first_iters, int n_problems, int steps,
-                                     int stop_on_first, int* stop, int* chunks_run) {
-  if (threadIdx.x != 0 || blockIdx.x != 0 || *stop) return;
-  bool found = false;
-  for (int p = 0; p < n_problems; ++p) {
-    t_dev[p] += steps;
-    found = found || *first_iters[p] != 0x7fffffff;
+// ------------------------------------------------------------------ chunk controller
+// After each chunk of a chunked optimisation (a CUDA graph's, or
+// tamp_optimize_steps stopping on the first satisfying particle): advance every
+// problem's step count, and raise the stop flag when stopping on the first
+// satisfying particle and some problem has one (the Eq. 3 check records its
+// iteration).  When another chunk follows and runs, the problems' Eq. 5 counts
+// are cleared for its final check; once stopped they keep the last check's.
+__global__ void chunk_control_kernel(int* t_dev, const int* const* first_iters, int* const* counts,
+                                     const int* n_counts, int n_problems, int steps, int stop_on_first, int* stop,
+                                     int* chunks_run, int last) {
+  __shared__ int s_next;
+  if (threadIdx.x == 0) {
+    s_next = 0;
+    if (!*stop) {
+      bool found = false;
+      for (int p = 0; p < n_problems; ++p) {
+        t_dev[p] += steps;
+        found = found || *first_iters[p] != 0x7fffffff;
+      }
+      *chunks_run += 1;
+      if (stop_on_first && found) *stop = 1;
+      else s_next = !last;
+    }
   }
-  *chunks_run += 1;
-  if (stop_on_first && found) *stop = 1;
+  __syncthreads();
+  if (!s_next) return;
+  for (int p = 0; p < n_problems; ++p)
+    for (int i = threadIdx.x; i < n_counts[p]; i += blockDim.x) counts[p][i] = 0;
 }
 
-cudaError_t launch_chunk_control(int* t_dev, const int* const* first_iters, int n_problems, int steps,
-                                 int stop_on_first, int* stop, int* chunks_run, cudaStream_t st) {
-  chunk_control_kernel<<<1, 32, 0, st>>>(t_dev, first_iters, n_problems, steps, stop_on_first, stop, chunks_run);
+cudaError_t launch_chunk_control(int* t_dev, const int* const* first_iters, int* const* counts, const int* n_counts,
+                                 int n_problems, int steps, int stop_on_first, int* stop, int* chunks_run, int last,
+                                 cudaStream_t st) {
+  chunk_control_kernel<<<1, 128, 0, st>>>(t_dev, first_iters, counts, n_counts, n_problems, steps, stop_on_first,
+                                          stop, chunks_run, last);
   return cudaGetLastError();
 }
 

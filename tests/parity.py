@@ -1,25 +1,38 @@
 """Comparison rules of the CUDA path against the FP64 oracle.
 
 Tolerances (FP32 kernel vs FP64 oracle):
-  * term values and Eq. 2 totals: |gpu - ora| <= 1e-4 * max(|ora|, 0.1).  The
-    floor 0.1 (m or rad) gives an absolute 1e-5: FP32 unit roundoff (6e-8) times
-    the workspace scale (~1 m) times the depth of the kinematic chain and the
-    sums over sphere pairs (~100 roundings) is ~6e-6.
+  * term values and Eq. 2 totals: |gpu - ora| <= 1e-4 * max(|ora|, 1e-2).  The
+    floor 1e-2 (m or rad) gives an absolute 1e-6 near zero; measured over the
+    plain, packing, stress, stacking, knot, self-collision and 6-DOF workloads
+    the largest error is 0.22 of this bound (a collision sum, 3.2e-6 absolute
+    at 0.15 m), every other term kind at most 0.07 of it.
   * gradients, per particle: ||g_gpu - g_ora|| <= 1e-3 * max(||g_ora||, 1e-2),
     for particles whose kink margin (oracle ``kink_margin``) is above
     KINK_MARGIN; the others are counted and reported.
   * Eq. 3 flags: identical, except particles with some constraint within 1e-5
     of its tolerance (counted).
+  * multi-step trajectories: FP32 and FP64 iterates can part ways only where a
+    particle comes within the FP32 rounding band of a point at which a cost's
+    derivative jumps (a penetration switching on, a bound crossed, a norm at
+    zero: the oracle's ``kink_margin``).  A particle whose margin stays above
+    TRAJ_MARGIN at every iterate of the oracle's run must end within TRAJ_TOL
+    of the oracle's iterate (measured: at most 5.4e-6 after 20 Adam steps,
+    from FP32 rounding of x, about 1e-7 per step); the others are counted.
+  * the gradient comparison must keep at least MIN_KEPT of a batch of 16 or more
+    particles (a caller may lower it for scenes dense in contacts, with more
+    particles), so that it never rests on a handful of them.
 """
 from __future__ import annotations
 
 import numpy as np
 import torch
 
-COST_REL, COST_FLOOR = 1e-4, 0.1
+COST_REL, COST_FLOOR = 1e-4, 1e-2
 GRAD_REL, GRAD_FLOOR = 1e-3, 1e-2
 KINK_MARGIN = 1e-4
 FLAG_BAND = 1e-5
+MIN_KEPT = 0.6
+TRAJ_MARGIN, TRAJ_TOL = 1e-6, 5e-5
 
 
 def cost_ok(gpu: np.ndarray, ora: np.ndarray) -> np.ndarray:
@@ -39,7 +52,7 @@ def near_threshold(problem, terms_ora: np.ndarray) -> np.ndarray:
     return (np.abs(terms_ora[:, cm] - tol[cm]) <= FLAG_BAND).any(axis=1)
 
 
-def compare_eval(problem, X: np.ndarray, cost, terms, flags, grad, label=""):
+def compare_eval(problem, X: np.ndarray, cost, terms, flags, grad, label="", min_kept=MIN_KEPT):
     """Full comparison of a tamp_eval result with the oracle on the same X [P, D].
 
     Returns a dict of counts; raises AssertionError with details on a violation."""
@@ -64,6 +77,9 @@ def compare_eval(problem, X: np.ndarray, cost, terms, flags, grad, label=""):
 
     err, bound = grad_errors(grad, g_ora)
     keep = margin > KINK_MARGIN
+    if len(X) >= 16:
+        assert keep.mean() >= min_kept, (f"{label}: the gradient comparison keeps only {int(keep.sum())} of "
+                                         f"{len(X)} particles")
     bad_g = (err > bound) & keep
     if bad_g.any():
         p = int(np.argmax(np.where(keep, err / bound, 0)))
@@ -77,5 +93,63 @@ def compare_eval(problem, X: np.ndarray, cost, terms, flags, grad, label=""):
     band = near_threshold(problem, T_ora)
     bad_f = (flags != ora_flags) & ~band
     assert not bad_f.any(), f"{label}: Eq. 3 flags differ for particles {np.nonzero(bad_f)[0][:8]}"
-    return dict(n=len(X), kink_excluded=int((~keep).sum()), flag_band=int(band.sum()),
+    return dict(n=len(X), kept=int(keep.sum()), kink_excluded=int((~keep).sum()), flag_band=int(band.sum()),
                 satisfied=int(ora_flags.sum()), max_rel_grad=float(np.max(np.where(keep, err / bound, 0))) * GRAD_REL)
+
+
+def oracle_run(problem, X: np.ndarray, n_steps: int):
+    """The oracle's n-step run (Problem.optimize from zero moments) and, per
+    particle, the smallest kink margin met at its iterates x_0 .. x_n."""
+    out = problem.optimize(torch.tensor(X), n_steps)
+    x = torch.tensor(X)
+    m, v = torch.zeros_like(x), torch.zeros_like(x)
+    margin = problem.kink_margin(x).numpy()
+    for t in range(n_steps):
+        _, g = problem.gradient(x)
+        x, m, v = problem.adam_step(x, m, v, t + 1, g, x.shape[0])
+        margin = np.minimum(margin, problem.kink_margin(x).numpy())
+    assert torch.equal(x, out["x"])            # the same steps as Problem.optimize
+    return out, margin
+
+
+def check_trajectory(problem, x_gpu: np.ndarray, cost_gpu: np.ndarray, out, margin, min_smooth=0.5):
+    """x_gpu [P, D] and cost_gpu [P] after the run against oracle_run's result."""
+    smooth = margin > TRAJ_MARGIN
+    d = np.abs(x_gpu - out["x"].numpy()).max(axis=1)
+    assert smooth.mean() >= min_smooth, f"only {int(smooth.sum())} of {len(smooth)} trajectories stay off kinks"
+    bad = smooth & (d > TRAJ_TOL)
+    assert not bad.any(), f"{int(bad.sum())} smooth trajectories left the oracle's (worst {d[smooth].max():.2e})"
+    assert cost_ok(cost_gpu.astype(np.float64), out["cost"].numpy())[smooth].all()
+    return dict(smooth=int(smooth.sum()), of=len(smooth), worst=float(d[smooth].max()) if smooth.any() else 0.0,
+                parted=int((d > TRAJ_TOL).sum()))
+
+
+def check_adam_step(problem, X, m0, v0, t0: int, x1, m1, n_batch: int, keep):
+    """One fused Adam step from (X, m0, v0) at step count t0 (all [P, D],
+    FP32-representable) against the oracle's.  The kernel's gradient is read
+    back from the first moment (m1 = b1 m0 + (1 - b1) g / N_b) and must match
+    the oracle's per particle; each component's step must match within what
+    that gradient bound implies for it: a gradient error dg moves the step by
+    lr (1 - b1) dg / N_b / (1 - b1^t) / (sqrt(v_hat) + eps), plus the FP32
+    rounding of x (the step is read as x1 - x0).  Particles near a kink
+    (keep False) are left out.  Returns the largest error/bound ratios."""
+    Xt = torch.tensor(X)
+    _, g = problem.gradient(Xt)
+    g = g.numpy()
+    o = problem.opts
+    b1, t = o.beta1, t0 + 1
+    gsc = n_batch if o.scale_by_batch else 1.0
+    g_gpu = (m1.astype(np.float64) - b1 * m0) / (1.0 - b1) * gsc
+    err, bound = grad_errors(g_gpu, g)
+    # m1 is FP32: its rounding, scaled back to a gradient, widens the bound
+    bound = bound + 2.0 ** -23 * (np.abs(m1) + b1 * np.abs(m0)).max(axis=1) / (1.0 - b1) * gsc * np.sqrt(X.shape[1])
+    assert (err <= bound)[keep].all(), f"gradient err {np.max(err[keep] / bound[keep]):.2f} x its bound"
+    xr, mr, vr = problem.adam_step(Xt, torch.tensor(m0), torch.tensor(v0), t, torch.tensor(g), n_batch)
+    lr = problem.learning_rates().numpy()
+    vhat = vr.numpy() / (1.0 - o.beta2 ** t)
+    dstep = lr * (1.0 - b1) * bound[:, None] / gsc / (1.0 - b1 ** t) / (np.sqrt(vhat) + o.eps)
+    step_r = xr.numpy() - X
+    lim = 2.0 * dstep + 1e-4 * np.abs(step_r) + 4.0 * 2.0 ** -24 * np.maximum(np.abs(X), 1.0)
+    dx = np.abs((x1.astype(np.float64) - X) - step_r)
+    assert (dx <= lim)[keep].all(), f"step err {np.max((dx / lim)[keep]):.2f} x its bound"
+    return dict(grad=float(np.max(err[keep] / bound[keep])), step=float(np.max((dx / lim)[keep])))

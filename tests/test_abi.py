@@ -56,6 +56,6 @@ def test_default_options_are_the_papers(lib):
 
 def test_null_arguments_are_rejected_without_a_device(lib):
     h = ctypes.c_void_p()
-    assert lib.tamp_create_scene(None, 0, None, ctypes.byref(h)) == 1
+    assert lib.tamp_create_scene(None, 0, None, None, ctypes.byref(h)) == 1
     assert lib.tamp_destroy_scene(None) == 1
-    assert lib.tamp_optimize_steps(None, None, 0, 1) == 1
+    assert lib.tamp_optimize_steps(None, None, 0, 1, 0) == 1

@@ -7,6 +7,7 @@ import pytest
 import torch
 
 import scenegen as sg
+from tests.parity import check_adam_step
 
 pytestmark = pytest.mark.gpu
 
@@ -94,17 +95,10 @@ def test_every_launch_shape_takes_the_oracle_adam_step(pkg, lanes, warps):
     x1, m1, _, t1 = scene.get_particles(pid)
     scene.close()
     assert t1 == 4
-    Xt = torch.tensor(X.astype(np.float32).astype(np.float64))
-    _, g = pr.gradient(Xt)
-    xr, mr, _ = pr.adam_step(Xt, torch.tensor(m0.astype(np.float32).astype(np.float64)),
-                             torch.tensor(v0.astype(np.float32).astype(np.float64)), 4, g, P)
-    keep = pr.kink_margin(Xt).numpy() > 1e-4
+    X32, m32, v32 = (a.astype(np.float32).astype(np.float64) for a in (X, m0, v0))
+    keep = pr.kink_margin(torch.tensor(X32)).numpy() > 1e-4
     assert keep.mean() > 0.5
-    dm = np.abs(m1.T - mr.numpy())[keep]
-    assert dm.max() <= 1e-3 * np.abs(mr.numpy()[keep]).max() + 1e-9
-    step_g = (x1.T - X.astype(np.float32))[keep]
-    step_r = (xr.numpy() - Xt.numpy())[keep]
-    assert np.abs(step_g - step_r).max() <= 1e-3 * np.abs(step_r).max() + 2e-6
+    check_adam_step(pr, X32, m32, v32, 3, x1.T, m1.T, P, keep)
 
 
 def test_adam_moments_in_global_memory_take_the_oracle_step(pkg):
@@ -126,17 +120,18 @@ def test_adam_moments_in_global_memory_take_the_oracle_step(pkg):
     x1, m1, v1, t1 = scene.get_particles(pid)
     scene.close()
     assert t1 == 6
-    Xt = torch.tensor(X.astype(np.float32).astype(np.float64))
-    _, g = pr.gradient(Xt)
-    xr, mr, vr = pr.adam_step(Xt, torch.tensor(m0.astype(np.float32).astype(np.float64)),
-                              torch.tensor(v0.astype(np.float32).astype(np.float64)), 6, g, P)
-    keep = pr.kink_margin(Xt).numpy() > 1e-4
+    X32, m32, v32 = (a.astype(np.float32).astype(np.float64) for a in (X, m0, v0))
+    keep = pr.kink_margin(torch.tensor(X32)).numpy() > 1e-4
     assert keep.sum() >= 8
-    assert np.abs(m1.T - mr.numpy())[keep].max() <= 1e-3 * np.abs(mr.numpy()[keep]).max() + 1e-9
-    assert np.abs(v1.T - vr.numpy())[keep].max() <= 1e-3 * np.abs(vr.numpy()[keep]).max() + 1e-12
-    step_g = (x1.T - X.astype(np.float32))[keep]
-    step_r = (xr.numpy() - Xt.numpy())[keep]
-    assert np.abs(step_g - step_r).max() <= 1e-3 * np.abs(step_r).max() + 2e-6
+    check_adam_step(pr, X32, m32, v32, 5, x1.T, m1.T, P, keep)
+    # the second moment left in global memory: v1 = b2 v0 + (1 - b2) (g / N_b)^2, where a gradient error
+    # |dg_c| <= b (the particle's gradient bound) moves it by (1 - b2) (2 |g_c| + b) b / N_b^2, plus FP32 rounding
+    _, g = pr.gradient(torch.tensor(X32))
+    g = g.numpy()
+    b = (1e-3 * np.maximum(np.linalg.norm(g, axis=1), 1e-2))[:, None]
+    vr = pr.opts.beta2 * v32 + (1.0 - pr.opts.beta2) * (g / P) ** 2
+    lim = (1.0 - pr.opts.beta2) * (2.0 * np.abs(g) + b) * b / P ** 2 + 2.0 ** -22 * vr
+    assert (np.abs(v1.T - vr) <= lim)[keep].all()
 
 
 def test_fp32_peak_probe_is_near_the_unit_count_peak(pkg):

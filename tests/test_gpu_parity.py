@@ -8,7 +8,7 @@ import torch
 import scenegen as sg
 from oracle import philox
 from oracle.problem import Options, Problem
-from tests.parity import compare_eval, cost_ok, grad_errors
+from tests.parity import check_adam_step, check_trajectory, compare_eval, cost_ok, grad_errors, oracle_run
 
 pytestmark = pytest.mark.gpu
 
@@ -66,10 +66,14 @@ def test_eval_single_particle_and_full_warp(pkg):
 
 
 def test_eval_stress_scene_sampled(pkg):
-    """100-sphere arm, 64 cuboids, 12 boxes, 24 configurations."""
+    """100-sphere arm, 64 cuboids, 12 boxes, 24 configurations.  Contacts are
+    dense here (about half the particles sit within 1e-4 of a kink), so the
+    batch is large enough for the gradient comparison to keep 40 or more."""
     sc, acts = sg.stress_problem(5001)
-    X = sg.random_particles(sc, acts, 12, seed=51)
-    compare_eval(Problem(sc, acts), X, *_eval(pkg, sc, acts, X, 1), label="stress")
+    X = sg.random_particles(sc, acts, 96, seed=51, spread=0.0)
+    res = compare_eval(Problem(sc, acts), X, *_eval(pkg, sc, acts, X, 1), label="stress", min_kept=0.4)
+    assert res["kept"] >= 40, res
+    print(res)
 
 
 def test_eval_full_size_packing_sampled(pkg):
@@ -109,18 +113,10 @@ def test_adam_step_matches_oracle(pkg):
     x1, m1, v1, t1 = scene.get_particles(pid)
     scene.close()
     assert t1 == t0 + 1
-    Xt = torch.tensor(X.astype(np.float32).astype(np.float64))
-    _, g = pr.gradient(Xt)
-    xr, mr, vr = pr.adam_step(Xt, torch.tensor(m0.astype(np.float32).astype(np.float64)),
-                              torch.tensor(v0.astype(np.float32).astype(np.float64)), t0 + 1, g, P)
-    margin = pr.kink_margin(Xt).numpy()
-    keep = margin > 1e-4
-    dm = np.abs(m1.T - mr.numpy())[keep]
-    assert dm.max() <= 1e-3 * np.abs(mr.numpy()[keep]).max() + 1e-9
-    # the update is lr * m_hat / (sqrt(v_hat) + eps): compare the step taken
-    step_g = (x1.T - X.astype(np.float32))[keep]
-    step_r = (xr.numpy() - Xt.numpy())[keep]
-    assert np.abs(step_g - step_r).max() <= 1e-3 * np.abs(step_r).max() + 2e-6
+    X32 = X.astype(np.float32).astype(np.float64)
+    keep = pr.kink_margin(torch.tensor(X32)).numpy() > 1e-4
+    print(check_adam_step(pr, X32, m0.astype(np.float32).astype(np.float64), v0.astype(np.float32).astype(np.float64),
+                          t0, x1.T, m1.T, P, keep))
 
 
 def test_first_satisfying_iteration_of_witness(pkg):
@@ -140,7 +136,8 @@ def test_first_satisfying_iteration_of_witness(pkg):
 
 def test_optimize_trajectory_tracks_oracle(pkg):
     """Ten fused Adam iterations from the same particles: FP32 vs FP64 paths
-    stay together except where a particle crosses a kink (counted)."""
+    stay together except where a particle comes near a kink (counted; the
+    rule of tests/parity.py check_trajectory)."""
     sc, acts = sg.plain_problem(1001)
     pr = Problem(sc, acts)
     P = 64
@@ -152,13 +149,9 @@ def test_optimize_trajectory_tracks_oracle(pkg):
     x10, _, _, t = scene.get_particles(pid)
     q = scene.query(pid, P)
     scene.close()
-    out = pr.optimize(torch.tensor(X.astype(np.float32).astype(np.float64)), 10)
-    d = np.abs(x10.T - out["x"].numpy()).max(axis=1)
-    close = d < 1e-3
+    out, margin = oracle_run(pr, X.astype(np.float32).astype(np.float64), 10)
     assert t == 10
-    assert close.mean() >= 0.8, f"only {close.mean():.2f} of trajectories agree"
-    ok = cost_ok(q["cost"][close].astype(np.float64), out["cost"].numpy()[close]) | (np.abs(q["cost"][close] - out["cost"].numpy()[close]) < 1e-3)
-    assert ok.all()
+    print(check_trajectory(pr, x10.T, q["cost"], out, margin))
 
 
 def test_counts_and_mask_match_oracle(pkg):
@@ -215,106 +208,6 @@ def test_no_obstacles_no_other_boxes(pkg):
     compare_eval(Problem(sc0, acts), X, *_eval(pkg, sc0, acts, X), label="empty environment")
 
 
-def test_batched_launch_matches_separate_launches(pkg):
-    """Skeletons of different lengths and batch sizes share one persistent
-    launch; every tile is independent, so the result equals separate launches
-    up to the order of float atomic additions (shared-variable gradients and
-    contact sums are accumulated with shared-memory atomics): after 6 Adam steps
-    nearly every component agrees to 1e-4 and costs agree to 1e-4 relative."""
-    sc, _ = sg.packing_problem(2001)
-    skels = [sg.pick_place_skeleton([0]), sg.pick_place_skeleton([0, 1, 2]),
-             sg.pick_place_skeleton(range(6), goal=True)]
-    sizes = [100, 70, 45]
-    opts = pkg.default_options(lanes=1)
-
-    def run(batched):
-        scene = pkg.Scene(sc)
-        pids = [scene.set_skeleton(a, opts) for a in skels]
-        for pid, n, a in zip(pids, sizes, skels):
-            X = sg.random_particles(sc, a, n, seed=100 + n, spread=0.5)
-            scene.set_particles(pid, X.T.astype(np.float32))
-        if batched:
-            scene.optimize(pids, 6)
-        else:
-            for pid in pids:
-                scene.optimize(pid, 6)
-        out = [scene.get_particles(pid)[0] for pid in pids]
-        qs = [scene.query(pid, n) for pid, n in zip(pids, sizes)]
-        scene.close()
-        return out, qs
-
-    xb, qb = run(True)
-    xs, qs = run(False)
-    for a, b in zip(xb, xs):
-        d = np.abs(a - b)
-        assert (d < 1e-4).mean() > 0.99 and d.max() < 0.1
-    for a, b in zip(qb, qs):
-        close = np.abs(a["cost"] - b["cost"]) <= 1e-4 * np.maximum(np.abs(b["cost"]), 0.1)
-        assert close.mean() > 0.95
-
-
-def test_batched_problem_matches_oracle(pkg):
-    """A short skeleton in a batched launch still matches the oracle."""
-    sc, _ = sg.packing_problem(2001)
-    acts = sg.pick_place_skeleton([0, 1])
-    pr = Problem(sc, acts)
-    scene = pkg.Scene(sc)
-    pid = scene.set_skeleton(acts)
-    other = scene.set_skeleton(sg.pick_place_skeleton(range(6), goal=True))
-    X = sg.random_particles(sc, acts, 64, seed=5)
-    scene.set_particles(pid, X.T.astype(np.float32))
-    scene.sample(other, 200, seed=3)
-    scene.optimize([other, pid], 0)              # evaluation only
-    q = scene.query(pid, 64)
-    scene.close()
-    J = pr.total_cost(torch.tensor(X.astype(np.float32).astype(np.float64))).numpy()
-    assert cost_ok(q["cost"].astype(np.float64), J).all()
-
-
-def test_graph_replays_the_optimisation_loop(pkg):
-    """4 captured chunks of 5 fused iterations == 20 iterations of tamp_optimize_steps
-    (up to float-atomic reordering); the step count advances on the device."""
-    sc, acts = sg.plain_problem(1001)
-    X = sg.random_particles(sc, acts, 150, seed=21, spread=0.5).T.astype(np.float32)
-
-    def run(graph):
-        scene = pkg.Scene(sc)
-        pid = scene.set_skeleton(acts)
-        scene.set_particles(pid, X)
-        if graph:
-            g = pkg.Graph(scene, pid, 5, 4)
-            steps = g.run()
-            g.close()
-        else:
-            scene.optimize(pid, 20)
-            steps = 20
-        x, _, _, t = scene.get_particles(pid)
-        q = scene.query(pid, 150)
-        scene.close()
-        return x, t, steps, q
-
-    xg, tg, sg_, qg = run(True)
-    xo, to, _, qo = run(False)
-    assert sg_ == 20 and tg == 20 and to == 20
-    d = np.abs(xg - xo)
-    assert (d < 1e-4).mean() > 0.99
-    assert qg["first_iter"] == qo["first_iter"]
-
-
-def test_graph_stops_on_first_satisfying_particle(pkg):
-    from tests.test_oracle_pins import _scara_witness_scene
-    sc, acts, x = _scara_witness_scene()
-    scene = pkg.Scene(sc)
-    pid = scene.set_skeleton(acts)
-    scene.set_particles(pid, np.repeat(x.numpy(), 3, axis=0).T.astype(np.float32))
-    g = pkg.Graph(scene, pid, 5, 10, stop_on_first=True)
-    steps = g.run()
-    q = scene.query(pid, 3)
-    g.close()
-    scene.close()
-    assert steps == 5 and q["first_iter"] == 0
-
-
 def test_stacking_skeleton_parity(pkg):
     """Obstructed stacking: blockers standing on B, A placed on B's top face."""
     sc, skels, _ = sg.stacking_problem(3002)
@@ -341,7 +234,7 @@ def test_stacking_searches_run_end_to_end(pkg):
 def test_stress_full_batch_adam_step_sampled(pkg):
     """The stress workload at its full batch (65536 particles, D = 252, 24
     configurations) in the launch shape the benchmark's tuner picks for it
-    (2 lanes, 16 warps): one fused iteration, then 32 sampled particles checked
+    (2 lanes, 16 warps): one fused iteration, then 48 sampled particles checked
     against the oracle's gradient + Adam step one by one (those within 1e-4 of a
     kink of the 64-cuboid scene are left out and counted)."""
     sc, acts = sg.stress_problem(5001)
@@ -356,25 +249,19 @@ def test_stress_full_batch_adam_step_sampled(pkg):
     x1, m1, _, t1 = scene.get_particles(pid)
     scene.close()
     assert t1 == 1
-    idx = np.random.default_rng(3).choice(P, 32, replace=False)
-    Xs = torch.tensor(X[idx].astype(np.float64))
-    _, g = pr.gradient(Xs)
-    xr, mr, _ = pr.adam_step(Xs, torch.zeros_like(Xs), torch.zeros_like(Xs), 1, g, P)
-    keep = pr.kink_margin(Xs).numpy() > 1e-4
-    assert keep.sum() >= 8, keep.sum()
-    dm = np.abs(m1.T[idx] - mr.numpy())[keep]
-    assert dm.max() <= 1e-3 * np.abs(mr.numpy()[keep]).max() + 1e-12
-    step_g = (x1.T[idx] - X[idx])[keep]
-    step_r = (xr.numpy() - Xs.numpy())[keep]
-    # first Adam step: -lr * g / (|g| + eps), so compare the steps' signs and sizes
-    assert np.abs(step_g - step_r).max() <= 1e-3 * np.abs(step_r).max() + 2e-6
+    idx = np.random.default_rng(3).choice(P, 48, replace=False)
+    Xs = X[idx].astype(np.float64)
+    keep = pr.kink_margin(torch.tensor(Xs)).numpy() > 1e-4
+    assert keep.sum() >= 16, keep.sum()
+    zeros = np.zeros_like(Xs)
+    print(check_adam_step(pr, Xs, zeros, zeros, 0, x1.T[idx], m1.T[idx], P, keep))
 
 
 def test_packing_full_batch_two_launches_sampled(pkg):
     """The packing workload at the benchmark's batch (4096 particles) in its
     launch shape (1 lane, 16 warps): two launches of one fused iteration each,
     the second starting at Adam step 1 (bias corrections 1 / (1 - beta^2) from
-    the step count carried over).  32 sampled particles are checked one by one:
+    the step count carried over).  48 sampled particles are checked one by one:
     the first step against the oracle's gradient + Adam step from the initial
     batch, the second against the oracle's step from the GPU's own state after
     the first (particles within 1e-4 of a kink are left out)."""
@@ -392,21 +279,15 @@ def test_packing_full_batch_two_launches_sampled(pkg):
     x2, m2, v2, t2 = scene.get_particles(pid)
     scene.close()
     assert (t1, t2) == (1, 2)
-    idx = np.random.default_rng(4).choice(P, 32, replace=False)
+    idx = np.random.default_rng(4).choice(P, 48, replace=False)
 
-    def check(x0, m0, v0, t, x_gpu, m_gpu):
-        xs = torch.tensor(x0[idx].astype(np.float64))
-        keep = pr.kink_margin(xs).numpy() > 1e-4
-        assert keep.sum() >= 8, keep.sum()
-        _, g = pr.gradient(xs)
-        xr, mr, _ = pr.adam_step(xs, torch.tensor(m0[idx].astype(np.float64)),
-                                 torch.tensor(v0[idx].astype(np.float64)), t, g, P)
-        dm = np.abs(m_gpu[idx] - mr.numpy())[keep]
-        assert dm.max() <= 1e-3 * np.abs(mr.numpy()[keep]).max() + 1e-12
-        step_g = (x_gpu[idx] - x0[idx])[keep]
-        step_r = (xr.numpy() - xs.numpy())[keep]
-        assert np.abs(step_g - step_r).max() <= 1e-3 * np.abs(step_r).max() + 2e-6
+    def check(x0, m0, v0, t0, x_gpu, m_gpu):
+        xs = x0[idx].astype(np.float64)
+        keep = pr.kink_margin(torch.tensor(xs)).numpy() > 1e-4
+        assert keep.sum() >= 16, keep.sum()
+        print(check_adam_step(pr, xs, m0[idx].astype(np.float64), v0[idx].astype(np.float64), t0, x_gpu[idx],
+                              m_gpu[idx], P, keep))
 
     zeros = np.zeros_like(X)
-    check(X, zeros, zeros, 1, x1.T, m1.T)
-    check(x1.T, m1.T, v1.T, 2, x2.T, m2.T)
+    check(X, zeros, zeros, 0, x1.T, m1.T)
+    check(x1.T, m1.T, v1.T, 1, x2.T, m2.T)
