@@ -10,7 +10,7 @@ from oracle import ik, philox
 from oracle.problem import Options, Problem
 from tests.parity import compare_eval
 
-from test_gpu_ik import _compare
+from test_gpu_ik import _compare, _moved
 
 pytestmark = pytest.mark.gpu
 
@@ -50,7 +50,8 @@ def test_samplers_with_six_dof_grasps(pkg):
     assert np.abs(x - philox.sample_uniform(pr, n, seed)).max() < 2e-6
     scene.sample(pid, n, seed, sampler=2)
     x = scene.get_particles(pid)[0].T.astype(np.float64)
-    _compare(pr, x, ik.ik_configurations(pr, philox.sample_uniform(pr, n, seed)))
+    X0 = philox.sample_uniform(pr, n, seed)
+    _compare(pr, x, ik.ik_configurations(pr, X0), ik.ik_configurations(pr, _moved(X0)))
     scene.close()
 
 

@@ -1,12 +1,17 @@
 """The IK configuration sampler (TAMP_SAMPLE_IK) through the C ABI vs the FP64
 oracle (oracle/ik.py) on the same uniform draws.
 
-The sampler is an iteration of 64 damped-least-squares steps: FP32 and FP64
-runs of it agree step by step while it contracts, and may part where a step is
-clipped or a joint limit is hit at slightly different values.  The bar: at
-least 90% of particles end within 1e-3 rad / 1e-4 m of the oracle on every
-component the sampler writes, and the share of particles whose Kin terms the
-sampler satisfied (judged by the oracle's Kin terms) agrees within 5 points.
+The sampler is an iteration of 64 damped-least-squares steps with a clipped
+step and joint limits.  Near a clip or a limit it is sensitive to its inputs
+in any precision: the FP64 oracle itself, rerun from inputs moved by one FP32
+rounding (a relative 2^-24), ends more than 1e-6 away on 16-44% of particles
+and more than 1e-3 away on up to 1.2%.  The bar therefore has two parts:
+among the particles whose FP64 run is stable under that perturbation (it moves
+by at most 1e-6), at least 99% end within 1e-3 rad / m of the oracle on every
+component the sampler writes (measured: 99.7-100%); over all particles at
+least 97% do (measured: 97.5-99.8%), the rest being counted; and the share of
+particles whose Kin terms the sampler satisfied (judged by the oracle's Kin
+terms) agrees within 3 points.
 """
 import numpy as np
 import pytest
@@ -40,16 +45,32 @@ def _kin_ok(pr, X):
     return (tv[:, kin] <= np.array([5e-3 if pr.terms[j].kind == KIN_POS else 0.05 for j in kin])).all(axis=1)
 
 
-def _compare(pr, x, ref):
+def _max_diff(pr, a, b):
     kinds = np.array(pr.kinds)
-    d = np.abs(x - ref)
+    d = np.abs(a - b)
     yaw = np.isin(kinds, ["gyaw", "pyaw"])
-    d[:, yaw] = np.abs(_wrap(x[:, yaw] - ref[:, yaw]))
-    close = (d <= 1e-3).all(axis=1)
-    assert close.mean() >= 0.9, close.mean()
+    d[:, yaw] = np.abs(_wrap(a[:, yaw] - b[:, yaw]))
+    return d.max(axis=1)
+
+
+def _compare(pr, x, ref, ref_moved):
+    """x: the kernel's configurations; ref: the oracle's from the same draws;
+    ref_moved: the oracle's from the draws moved by one FP32 rounding."""
+    d = _max_diff(pr, x, ref)
+    stable = _max_diff(pr, ref_moved, ref) <= 1e-6
+    assert stable.mean() >= 0.5, stable.mean()
+    assert (d[stable] <= 1e-3).mean() >= 0.99, (d[stable] <= 1e-3).mean()
+    assert (d <= 1e-3).mean() >= 0.97, (d <= 1e-3).mean()
     ok_g, ok_o = _kin_ok(pr, x), _kin_ok(pr, ref)
-    assert abs(ok_g.mean() - ok_o.mean()) <= 0.05, (ok_g.mean(), ok_o.mean())
+    assert abs(ok_g.mean() - ok_o.mean()) <= 0.03, (ok_g.mean(), ok_o.mean())
+    print(f"\nIK: {int((d > 1e-3).sum())} of {len(d)} particles beyond 1e-3, "
+          f"{int((d[stable] > 1e-3).sum())} of {int(stable.sum())} stable ones")
     return ok_g.mean()
+
+
+def _moved(X, seed=0):
+    """The draws moved by one FP32 rounding (relative 2^-24, random sign)."""
+    return X * (1.0 + np.random.default_rng(seed).choice([-1.0, 1.0], X.shape) * 2.0 ** -24)
 
 
 @pytest.mark.parametrize("maker,n", [(lambda: sg.robot_plain_problem(20001), 512),
@@ -63,8 +84,8 @@ def test_ik_sampler_matches_oracle(pkg, maker, n):
     seed = 0x5EED_0001
     scene.sample(pid, n, seed, sampler=2)
     x = scene.get_particles(pid)[0].T.astype(np.float64)
-    ref = ik.ik_configurations(pr, philox.sample_uniform(pr, n, seed))
-    rate = _compare(pr, x, ref)
+    X0 = philox.sample_uniform(pr, n, seed)
+    rate = _compare(pr, x, ik.ik_configurations(pr, X0), ik.ik_configurations(pr, _moved(X0)))
     print(f"\nIK sampler: {sc.name} Kin satisfied after sampling {rate:.3f}")
     scene.close()
 
@@ -82,7 +103,7 @@ def test_learned_then_ik_matches_oracle(pkg):
     scene.sample(pid, n, seed, sampler=3)
     x = scene.get_particles(pid)[0].T.astype(np.float64)
     out = om.forward(torch.from_numpy(th).double(), torch.from_numpy(op.features(sc, acts))).numpy()
-    ref = ik.ik_configurations(pr, op.sample(sc, acts, out, n, seed))
-    _compare(pr, x, ref)
+    X0 = op.sample(sc, acts, out, n, seed)
+    _compare(pr, x, ik.ik_configurations(pr, X0), ik.ik_configurations(pr, _moved(X0)))
     scene.close()
     net.close()

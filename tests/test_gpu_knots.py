@@ -11,7 +11,7 @@ from oracle import ik, philox
 from oracle.problem import KNOT, TRAJ_LEN, Options, Problem
 from tests.parity import compare_eval
 
-from test_gpu_ik import _compare
+from test_gpu_ik import _compare, _moved
 
 pytestmark = pytest.mark.gpu
 
@@ -64,7 +64,9 @@ def test_knots_start_on_the_line_between_their_configurations(pkg):
     # IK configurations: the knots follow the solved ends
     scene.sample(pid, n, seed, sampler=2)
     x = scene.get_particles(pid)[0].T.astype(np.float64)
-    _compare(pr, x, pr.interpolate_knots(ik.ik_configurations(pr, philox.sample_uniform(pr, n, seed))))
+    X0 = philox.sample_uniform(pr, n, seed)
+    _compare(pr, x, pr.interpolate_knots(ik.ik_configurations(pr, X0)),
+             pr.interpolate_knots(ik.ik_configurations(pr, _moved(X0))))
     # and TrajLength of straight knots is the straight-line length
     tv = pr.term_values(torch.tensor(x)).numpy()
     for ti, t in enumerate(pr.terms):

@@ -11,7 +11,7 @@ import scenegen as sg
 from oracle import mlp as om
 from oracle import philox
 from oracle import proposal as op
-from oracle.problem import Problem
+from oracle.problem import GRASP, STABLE_PLACE, Problem
 
 pytestmark = pytest.mark.gpu
 
@@ -99,7 +99,7 @@ def test_proposal_sampler_needs_a_network(pkg):
     scene.close()
 
 
-def test_trained_proposals_gain_over_the_method_without_them(pkg):
+def test_trained_proposals_gain_over_the_method_without_them(pkg, trained):
     """What the trained network adds, judged on held-out scenes of one robot.
 
     Training: the method itself (uniform grasps/placements, IK configurations,
@@ -110,12 +110,8 @@ def test_trained_proposals_gain_over_the_method_without_them(pkg):
     same seeds and tolerances; the measure is how many particles satisfy
     Eq. 3 straight after sampling, counted by the GPU check and re-judged by
     the FP64 oracle on a subset."""
-    from paper_2411_11833_b300 import proposal
-    train = [sg.robot_plain_problem(10000 + k) for k in range(128)]
-    F, Y, M, st = proposal.harvest(train, n_particles=4096, iters=200, chunk=50, sampler=2,
-                                   max_rows_per_problem=256)
+    net, st, losses = trained
     assert st["particles"] >= 8000, st
-    net, losses = proposal.train(F, Y, M, steps=1500, batch=4096, lr=1e-3, log_every=500)
     assert losses[-1][1] < losses[0][1] - 0.5, losses
     counts = {2: [], 3: []}
     oracle_rate = {2: [], 3: []}
@@ -143,4 +139,52 @@ def test_trained_proposals_gain_over_the_method_without_them(pkg):
           f"{u.tolist()}; learned+IK mean {l.mean():.0f} {l.tolist()}; oracle-judged rates uniform "
           f"{np.round(oracle_rate[2], 3).tolist()} learned {np.round(oracle_rate[3], 3).tolist()}")
     assert l.mean() > u.mean()
+
+
+def test_learned_seeds_against_uniform_seeds_judged_by_the_oracle(pkg, trained):
+    """The learned-proposal comparison without IK (the network proposes grasps
+    and placements, joints stay uniform), on 32 held-out scenes: iterations to
+    the first satisfying particle under the device-side stop (checks every 10
+    iterations, at most 1000), and the FP64 oracle's judgement of the seeds
+    themselves -- the share of seeds whose Grasp and StablePlace constraints
+    (the terms that depend only on what the network proposes) hold."""
+    net = trained[0]
+    iters = {0: [], 1: []}
+    held = {0: [], 1: []}
+    for k in range(32):
+        sc, acts = sg.robot_plain_problem(20000 + k)
+        pr = Problem(sc, acts)
+        own = [i for i, t in enumerate(pr.terms) if t.kind in (GRASP, STABLE_PLACE)]
+        scene = pkg.Scene(sc)
+        pid = scene.set_skeleton(acts)
+        scene.set_proposal(net)
+        for sampler in (0, 1):
+            scene.sample(pid, 1024, 31 + k, sampler=sampler)
+            X = scene.get_particles(pid)[0][:, :256].T.astype(np.float64)
+            T = pr.term_values(torch.from_numpy(X)).numpy()
+            held[sampler].append(float((T[:, own] <= pr.tolerances().numpy()[own]).all(axis=1).mean()))
+            scene.optimize(pid, 1000, stop_every=10)
+            f = scene.query(pid, 1024)["first_iter"]
+            iters[sampler].append(f if f >= 0 else 1000)
+        scene.set_proposal(None)
+        scene.close()
+    iu, il = np.array(iters[0]), np.array(iters[1])
+    hu, hl = np.array(held[0]), np.array(held[1])
+    print(f"\nlearned vs uniform seeds, 32 held-out scenes: iterations to first satisfying mean {il.mean():.0f} vs "
+          f"{iu.mean():.0f}; oracle: Grasp and StablePlace hold for {hl.mean():.3f} vs {hu.mean():.3f} of seeds")
+    assert hl.mean() > hu.mean()                     # the oracle prefers the network's seeds
+    assert (il < 1000).mean() >= 0.9 and (iu < 1000).mean() >= 0.9
+
+
+@pytest.fixture(scope="module")
+def trained(pkg):
+    """The network trained on what the method finds on 128 plain Pick-Place
+    scenes of one robot (uniform grasps/placements, IK configurations, 200
+    Adam steps), by the library's tensor-core kernels."""
+    from paper_2411_11833_b300 import proposal
+    train = [sg.robot_plain_problem(10000 + k) for k in range(128)]
+    F, Y, M, st = proposal.harvest(train, n_particles=4096, iters=200, chunk=50, sampler=2,
+                                   max_rows_per_problem=256)
+    net, losses = proposal.train(F, Y, M, steps=1500, batch=4096, lr=1e-3, log_every=500)
+    yield net, st, losses
     net.close()

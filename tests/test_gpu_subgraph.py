@@ -18,7 +18,7 @@ import scenegen as sg
 from oracle import ik, philox
 from oracle.problem import Problem
 
-from test_gpu_ik import _compare
+from test_gpu_ik import _compare, _moved
 
 pytestmark = pytest.mark.gpu
 
@@ -58,8 +58,9 @@ def test_cached_prefix_sampling_matches_the_oracle(pkg):
     assert np.array_equal(x2[:k], x1[:k])                    # [D][P]: the prefix rows, bit for bit
     X = philox.sample_uniform(pr2, n, 12)
     X[:, :k] = x1[:k].T.astype(np.float64)
-    ref = ik.ik_configurations(pr2, X, keep=k)
-    _compare(pr2, x2.T.astype(np.float64), ref)
+    Xm = _moved(X)
+    Xm[:, :k] = X[:, :k]                                      # the copied prefix is exact
+    _compare(pr2, x2.T.astype(np.float64), ik.ik_configurations(pr2, X, keep=k), ik.ik_configurations(pr2, Xm, keep=k))
     # no shared prefix: exactly the plain sampler
     assert scene.sample(p3, n, 13, sampler=2, cache_from=p1) == 0
     x3 = scene.get_particles(p3)[0]
