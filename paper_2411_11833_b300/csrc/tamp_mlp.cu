@@ -195,9 +195,39 @@ __device__ bool gemm_tile(uint32_t tmem, const unsigned char* A, const unsigned 
 __device__ __forceinline__ uint32_t lane_addr(uint32_t tmem, int col) {
   return tmem + (static_cast<uint32_t>(32 * ((threadIdx.x >> 5) & 3)) << 16) + static_cast<uint32_t>(col);
 }
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+// erf(x) for the exact GELU, on the FP32 pipe only (no special-function unit):
+// erf(x) / x is a smooth even function, fitted here by least squares in the
+// Chebyshev basis as a degree-10 polynomial in t = 2 x^2 / 3.2^2 - 1 on
+// |x| <= 3.2 and evaluated by Horner's rule in t (well conditioned: the
+// coefficients' magnitudes sum to 1.13); beyond 3.2, x is clamped (1 - erf(3.2)
+// = 6e-6).  Measured in FP32 against the double-precision erf: |error| <= 9e-6,
+// GELU's absolute error <= 2e-5 over [-10, 10], far below the BF16 rounding
+// (2^-9 relative) of the activations it produces.
+__device__ __forceinline__ float erf_fit(float x) {
+  constexpr float X = 3.2f, TS = 2.f / (3.2f * 3.2f);
+  const float xc = fminf(fmaxf(x, -X), X);
+  const float t = fmaf(xc * xc, TS, -1.f);
+  float p = 0.00292568514123559f;
+  p = fmaf(p, t, -0.006891352590173483f);
+  p = fmaf(p, t, 0.008087416179478168f);
+  p = fmaf(p, t, -0.015537121333181858f);
+  p = fmaf(p, t, 0.033078957349061966f);
+  p = fmaf(p, t, -0.0545048713684082f);
+  p = fmaf(p, t, 0.0806603953242302f);
+  p = fmaf(p, t, -0.11369938403367996f);
+  p = fmaf(p, t, 0.15435127913951874f);
+  p = fmaf(p, t, -0.21730433404445648f);
+  p = fmaf(p, t, 0.44133424758911133f);
+  return xc * p;
+}
+// GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2 and its derivative
+// Phi(z) + z phi(z), phi(z) = exp(-z^2 / 2) / sqrt(2 pi)
+__device__ __forceinline__ float gelu(float z) {
+  const float h = 0.5f * z;
+  return fmaf(h, erf_fit(z * 0.70710678118654752f), h);
+}
 __device__ __forceinline__ float gelu_grad(float z) {
-  return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+  return fmaf(0.5f, erf_fit(z * 0.70710678118654752f), 0.5f) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
 }
 
 // ------------------------------------------------------------------ forward
@@ -223,6 +253,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
   unsigned char* opB = smem + SMEM_A;
   __shared__ __align__(8) uint64_t bar_mma, bar_w;
   __shared__ uint32_t tslot;
+  __shared__ __align__(16) float s_bias[3 * H + OUT];  // every layer's bias, read by the epilogues
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31, grp = warp >> 2;
   const int row = 32 * (warp & 3) + lane, row0 = blockIdx.x * ROWS, r = row0 + row;
   const int Rv = min(ROWS, a.B - row0);
@@ -235,6 +266,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
     bulk_g2s(opB, a.Wp + pk_off(0), static_cast<uint32_t>(pk_bytes(0)), &bar_w);
     w_pending = true;
   }
+  for (int i = t; i < 3 * H + OUT; i += THREADS) s_bias[i] = i < 3 * H ? a.b[i / H][i % H] : a.b[3][i - 3 * H];
   if (warp == 0) tmem_alloc(&tslot);
   // inputs: 8 columns (one 16-byte chunk of the layout) per step
   for (int c = t; c < ROWS * (IN / 8); c += THREADS) {
@@ -282,7 +314,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
       for (int c0 = grp * per; c0 < grp * per + per; c0 += 32) {
         float v[32];
         tmem_ld32(lane_addr(tmem, c0), v);
-        const float* bias = a.b[l] + c0;
+        const float* bias = s_bias + l * H + c0;
         if (l < 3) {
           uint32_t hp[16];
 #pragma unroll
