@@ -14,6 +14,7 @@
 // an mbarrier, and every thread reads back its own row with tcgen05.ld.  A
 // transposed operand is just staged transposed, so the backward pass (dA = dZ W,
 // dW = dZ^T A) uses the same instruction forms as the forward pass.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -506,34 +507,38 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_backward_dz_kernel(DzArgs a) {
   if (warp == 0) tmem_dealloc(tmem);
 }
 
-constexpr int DW_THREADS = 256;        // 8 warps: TMEM lane quarter (w % 4), column half (w / 4)
-constexpr int DW_CHUNK = 64;           // rows per staged chunk (4 MMAs of K = 16)
-constexpr size_t DW_BUF_A = 128 * DW_CHUNK * 2, DW_BUF_B = 256 * DW_CHUNK * 2;
-constexpr size_t DW_SMEM = 2 * (DW_BUF_A + DW_BUF_B);
-
+// The weight gradients dW_l = dZ_l^T A_{l-1} (and db_l = column sums of dZ_l):
+// per CTA one layer, 128 of its outputs and a split of the batch rows, which
+// are the GEMM's K.  Both operands are feature-major in global memory
+// ([features][ldT]); TMA tensor copies (cp.async.bulk.tensor) bring each
+// 64-row chunk into a ring of DW_STAGES shared-memory stages in the canonical
+// K-major layout without swizzle -- one copy of a box of 8 batch rows (16
+// bytes) by R features per 8-row group, so that every 8 x 16-byte core matrix
+// is contiguous (core matrices 128 B apart along M/N, R x 16 B apart along K)
+// -- while one thread issues the MMAs of the chunks that have landed.  The
+// 128 threads of the epilogue warps add each of their row's chunk values for
+// db before releasing a stage.  Batch rows past B are filled with zeros by
+// the copies.
+constexpr int DW_STAGES = 4;
+constexpr int DW_CHUNK = 64;                              // batch rows per stage (4 MMAs of K = 16)
+constexpr int DW_THREADS = 160;                           // 4 epilogue warps (TMEM lane quarters) + 1 issuing warp
+constexpr size_t DW_STAGE_A = 128 * DW_CHUNK * 2, DW_STAGE_B = 256 * DW_CHUNK * 2;
+constexpr size_t DW_STAGE = DW_STAGE_A + DW_STAGE_B;
+constexpr size_t DW_SMEM = DW_STAGES * DW_STAGE;
 constexpr int DW_MAX_SPLITS = 32;
 
+// tensor maps: A operands (128-feature boxes) dZ_0^T, dZ_1^T, dZ_2^T, A_2^T;
+// B operands (every feature) x^T, A_0^T, A_1^T, dZ_3^T
+struct DwMaps {
+  CUtensorMap map[8];
+};
 struct DwArgs {
-  int B, ldT, rows_per_split;
-  const __nv_bfloat16* XT;            // [IN][ldT]
-  const __nv_bfloat16* AT[3];         // [H][ldT]
-  const __nv_bfloat16* dZT[4];        // [H][ldT] (l < 3), [OUT][ldT] (l = 3)
+  int B, rows_per_split;
   float* part;                        // [split][N_PARAMS]: this split's share of dW and db
   int* err;
 };
 
-// 16 bytes (8 BF16) of a feature-major row starting at column r (zero past B)
-__device__ __forceinline__ uint4 load8(const __nv_bfloat16* p, int r, int B) {
-  if (r + 8 <= B) return *reinterpret_cast<const uint4*>(p);
-  uint32_t w[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const unsigned short lo = r + 2 * q < B ? __bfloat16_as_ushort(p[2 * q]) : 0;
-    const unsigned short hi = r + 2 * q + 1 < B ? __bfloat16_as_ushort(p[2 * q + 1]) : 0;
-    w[q] = static_cast<uint32_t>(lo) | static_cast<uint32_t>(hi) << 16;
-  }
-  return make_uint4(w[0], w[1], w[2], w[3]);
-}
+// sum of 8 BF16 values
 __device__ __forceinline__ float sum8(const uint4& u) {
   const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
   float s = 0.f;
@@ -541,151 +546,161 @@ __device__ __forceinline__ float sum8(const uint4& u) {
   for (int q = 0; q < 4; ++q) s += __low2float(h[q]) + __high2float(h[q]);
   return s;
 }
-
-// One chunk of both operands: A = 128 rows, B = NBR rows, 64 columns each.
-template <int NBR>
-__device__ __forceinline__ void dw_stage(unsigned char* bufA, unsigned char* bufB, const __nv_bfloat16* srcA,
-                                         const __nv_bfloat16* srcB, int ldT, int r0, int r_end, int ra, int kc,
-                                         bool sum_a, bool sum_b, float (&csA)[4], float (&csB)[8]) {
-  constexpr int KB = (NBR + 31) / 32;
-  uint4 ua[4], ub[KB];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) ua[k] = load8(srcA + static_cast<long>(ra + 32 * k) * ldT + r0 + kc, r0 + kc, r_end);
-#pragma unroll
-  for (int k = 0; k < KB; ++k)
-    ub[k] = (NBR % 32 == 0 || ra + 32 * k < NBR)
-                ? load8(srcB + static_cast<long>(ra + 32 * k) * ldT + r0 + kc, r0 + kc, r_end)
-                : make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    *reinterpret_cast<uint4*>(bufA + blk_off(ra + 32 * k, kc, 128)) = ua[k];
-    if (sum_a) csA[k] += sum8(ua[k]);
-  }
-#pragma unroll
-  for (int k = 0; k < KB; ++k)
-    if (NBR % 32 == 0 || ra + 32 * k < NBR) {
-      *reinterpret_cast<uint4*>(bufB + blk_off(ra + 32 * k, kc, NBR)) = ub[k];
-      if (sum_b) csB[k] += sum8(ub[k]);
-    }
+__device__ __forceinline__ void mbar_init_n(uint64_t* bar, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// 2-D tensor copy global -> shared, completion counted on the mbarrier
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+// K-major, no swizzle, with explicit core-matrix strides: lbo along K, sbo along M/N
+__device__ __forceinline__ uint64_t smem_desc_strided(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-__global__ void __launch_bounds__(DW_THREADS, 2) mlp_backward_dw_kernel(DwArgs a) {
+__global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __grid_constant__ DwMaps tm, DwArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  // two buffers, each an A and a B operand chunk; mbarrier phases and pending
-  // commits of the two kept as bit masks (no dynamically indexed arrays)
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t full[DW_STAGES], empty[DW_STAGES];
   __shared__ uint32_t tslot;
-  __shared__ float colsum[256];
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31, grp = warp >> 2;
+  __shared__ int abort_flag;
+  const int t = threadIdx.x, warp = t >> 5;
   const int l = blockIdx.x >> 1, half = blockIdx.x & 1;
   const bool swapped = l == 3;  // 32 outputs: M runs over the inputs, D = dW^T
   const int K = kdim(l), N = ndim(l);
-  // A operand: 128 rows of dZ_l^T (outputs), or of A_2^T (inputs) when swapped;
-  // B operand: the N' rows of the other factor
-  const __nv_bfloat16* srcA = swapped ? a.AT[2] + static_cast<long>(half * 128) * a.ldT
-                                      : a.dZT[l] + static_cast<long>(half * 128) * a.ldT;
-  const __nv_bfloat16* srcB = swapped ? a.dZT[3] : (l == 0 ? a.XT : a.AT[l - 1]);
-  const int NB_ = swapped ? N : K;  // the GEMM's N'
+  const int NB_ = swapped ? N : K;  // the GEMM's N' (rows of the B operand)
+  const CUtensorMap* mA = &tm.map[swapped ? 3 : l];
+  const CUtensorMap* mB = &tm.map[4 + l];
   const bool sum_a = !swapped, sum_b = swapped && half == 0;  // db: each output's column once
   const int r_begin = blockIdx.y * a.rows_per_split, r_end = min(a.B, r_begin + a.rows_per_split);
+  const int n_chunks = r_end > r_begin ? (r_end - r_begin + DW_CHUNK - 1) / DW_CHUNK : 0;
+  const uint32_t stage_tx = static_cast<uint32_t>((128 + NB_) * DW_CHUNK * 2);
   if (t == 0) {
-    mbar_init(&bar[0]);
-    mbar_init(&bar[1]);
+    abort_flag = 0;
+    for (int st = 0; st < DW_STAGES; ++st) {
+      mbar_init_n(&full[st], 1);
+      mbar_init_n(&empty[st], 1 + 128);  // the MMAs' commit and the 128 db threads
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int i = t; i < 256; i += DW_THREADS) colsum[i] = 0.f;
   if (warp == 0) tmem_alloc(&tslot);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tslot;
-  uint32_t ph = 0u, pend = 0u;
-  bool ok = true;
-  int ci = 0;
-  const int ra = t >> 3, kc = (t & 7) * 8;  // this thread's staging rows (ra + 32 k) and column piece
-  float csA[4] = {0.f, 0.f, 0.f, 0.f}, csB[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int r0 = r_begin; r0 < r_end; r0 += DW_CHUNK, ++ci) {
-    const int b = ci & 1;
-    unsigned char* bA = smem + b * DW_BUF_A;
-    unsigned char* bB = smem + 2 * DW_BUF_A + b * DW_BUF_B;
-    if (pend >> b & 1u) {  // the MMAs of two chunks ago read this buffer
-      const bool okb = mbar_wait_bounded(&bar[b], ph >> b & 1u);
-      ph ^= 1u << b;
-      pend &= ~(1u << b);
-      if (!okb) atomicOr(a.err, ERR_WAIT);
-      ok = __syncthreads_and(okb) != 0;
-      if (!ok) break;
-    }
-    // every piece of this thread's share first (independent 16-byte loads),
-    // then the stores: thread t stages rows t / 8 + 32 k, columns 8 (t % 8) ..
-    if (NB_ == 256)
-      dw_stage<256>(bA, bB, srcA, srcB, a.ldT, r0, r_end, ra, kc, sum_a, sum_b, csA, csB);
-    else if (NB_ == 48)
-      dw_stage<48>(bA, bB, srcA, srcB, a.ldT, r0, r_end, ra, kc, sum_a, sum_b, csA, csB);
-    else
-      dw_stage<32>(bA, bB, srcA, srcB, a.ldT, r0, r_end, ra, kc, sum_a, sum_b, csA, csB);
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
-    if (t == 0) {
-      tc_fence_after();
-      const uint32_t a0 = smem_u32(bA), b0 = smem_u32(bB), id = instr_desc(ROWS, NB_);
-      for (int c = 0; c < DW_CHUNK / 16; ++c)
-        umma_bf16(tmem, smem_desc(a0 + c * ROWS * 32), smem_desc(b0 + c * NB_ * 32), id, (ci > 0 || c > 0) ? 1u : 0u);
-      umma_commit(&bar[b]);
-    }
-    pend |= 1u << b;
-  }
-  // drain: the last commit covers every MMA issued before it
-  for (int b = 0; b < 2; ++b)
-    if (pend >> b & 1u) {
-      if (!mbar_wait_bounded(&bar[b], ph >> b & 1u)) {
-        atomicOr(a.err, ERR_WAIT);
-        ok = false;
+  auto stage_a = [&](int st) { return smem + st * DW_STAGE; };
+  auto stage_b = [&](int st) { return smem + st * DW_STAGE + DW_STAGE_A; };
+
+  if (t == 128) {
+    // copies and MMAs: chunk c lives in stage c % DW_STAGES; its stage is refilled
+    // with chunk c + DW_STAGES once the MMAs of c and its db sums are done
+    auto load = [&](int c) {
+      const int st = c % DW_STAGES, x0 = r_begin + c * DW_CHUNK;
+      mbar_expect_tx(&full[st], stage_tx);
+      for (int j = 0; j < DW_CHUNK / 8; ++j) {
+        tma_load_2d(stage_a(st) + j * 128 * 16, mA, x0 + 8 * j, half * 128, &full[st]);
+        tma_load_2d(stage_b(st) + j * NB_ * 16, mB, x0 + 8 * j, 0, &full[st]);
       }
-      ph ^= 1u << b;
+    };
+    const uint32_t id = instr_desc(ROWS, NB_);
+    int issued = 0;
+    for (; issued < n_chunks && issued < DW_STAGES; ++issued) load(issued);
+    for (int c = 0; c < n_chunks; ++c) {
+      const int st = c % DW_STAGES;
+      const uint32_t par = static_cast<uint32_t>(c / DW_STAGES) & 1u;
+      if (!mbar_wait_bounded(&full[st], par)) {
+        atomicOr(a.err, ERR_WAIT);
+        abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(stage_a(st)), b0 = smem_u32(stage_b(st));
+      for (int kk = 0; kk < DW_CHUNK / 16; ++kk)
+        umma_bf16(tmem, smem_desc_strided(a0 + kk * 2 * 128 * 16, 128 * 16, 128),
+                  smem_desc_strided(b0 + kk * 2 * NB_ * 16, NB_ * 16, 128), id, (c > 0 || kk > 0) ? 1u : 0u);
+      umma_commit(&empty[st]);
+      if (issued < n_chunks) {
+        if (!mbar_wait_bounded(&empty[st], par)) {
+          atomicOr(a.err, ERR_WAIT);
+          abort_flag = 1;
+          break;
+        }
+        load(issued++);
+      }
     }
+    // no copy may land after the CTA ends: wait for every chunk issued
+    for (int c = max(0, issued - DW_STAGES); c < issued; ++c)
+      mbar_wait_bounded(&full[c % DW_STAGES], static_cast<uint32_t>(c / DW_STAGES) & 1u);
+  } else if (t < 128) {
+    // db: this thread's row of the chunk (outputs of the layer), then release the stage
+    const int row = t;
+    const bool mine = sum_a || (sum_b && row < NB_);
+    float cs = 0.f;
+    for (int c = 0; c < n_chunks; ++c) {
+      const int st = c % DW_STAGES;
+      const uint32_t par = static_cast<uint32_t>(c / DW_STAGES) & 1u;
+      if (!mbar_wait_bounded(&full[st], par)) {
+        atomicOr(a.err, ERR_WAIT);
+        abort_flag = 1;
+        break;
+      }
+      if (mine) {
+        const unsigned char* base = sum_a ? stage_a(st) : stage_b(st);
+        const int R = sum_a ? 128 : NB_;
+#pragma unroll
+        for (int j = 0; j < DW_CHUNK / 8; ++j)
+          cs += sum8(*reinterpret_cast<const uint4*>(base + j * R * 16 + (row >> 3) * 128 + (row & 7) * 16));
+      }
+      mbar_arrive(&empty[st]);
+    }
+    if (mine) {
+      float* gb = a.part + static_cast<long>(blockIdx.y) * N_PARAMS + b_off(l);
+      gb[sum_a ? half * 128 + row : row] = cs;
+    }
+  }
+  __syncthreads();
+  // every MMA has completed once the last chunk's stage was released
+  bool ok = abort_flag == 0;
+  if (ok && n_chunks > 0 && t < 128) {
+    const int c = n_chunks - 1;
+    if (!mbar_wait_bounded(&empty[c % DW_STAGES], static_cast<uint32_t>(c / DW_STAGES) & 1u)) {
+      atomicOr(a.err, ERR_WAIT);
+      ok = false;
+    }
+  }
   tc_fence_after();
   ok = __syncthreads_and(ok) != 0;
   // this split's partial dW, written whole (zeros for a split past the last row)
-  float* part = a.part + static_cast<long>(blockIdx.y) * N_PARAMS;
-  if (ok) {
-    float* gW = part + w_off(l);
-    const int row = 32 * (warp & 3) + lane;
-    const int per = NB_ >= 128 ? NB_ / 2 : NB_;
-    if (NB_ >= 128 || grp == 0) {
-      for (int c0 = grp * per; c0 < grp * per + per; c0 += 32) {
-        float v[32];
-        tmem_ld32(lane_addr(tmem, c0), v);
-        if (ci == 0)
+  if (ok && t < 128) {
+    float* gW = a.part + static_cast<long>(blockIdx.y) * N_PARAMS + w_off(l);
+    const int row = t;
+    for (int c0 = 0; c0 < NB_; c0 += 32) {
+      float v[32];
+      tmem_ld32(lane_addr(tmem, c0), v);
+      if (n_chunks == 0)
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] = 0.f;
-        if (swapped) {
+        for (int j = 0; j < 32; ++j) v[j] = 0.f;
+      if (swapped) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (c0 + j < NB_) gW[static_cast<long>(c0 + j) * K + half * 128 + row] = v[j];
-        } else {
-          float4* dst = reinterpret_cast<float4*>(gW + static_cast<long>(half * 128 + row) * K + c0);
+        for (int j = 0; j < 32; ++j)
+          if (c0 + j < NB_) gW[static_cast<long>(c0 + j) * K + half * 128 + row] = v[j];
+      } else {
+        float4* dst = reinterpret_cast<float4*>(gW + static_cast<long>(half * 128 + row) * K + c0);
 #pragma unroll
-          for (int q = 0; q < 8; ++q)
-            if (c0 + 4 * q < NB_) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        }
+        for (int q = 0; q < 8; ++q)
+          if (c0 + 4 * q < NB_) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       }
     }
   }
-  // the bias: each row's sum over the split, from the registers of its 8 threads
-  if (sum_a)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) atomicAdd(&colsum[ra + 32 * k], csA[k]);
-  if (sum_b)
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (ra + 32 * k < NB_) atomicAdd(&colsum[ra + 32 * k], csB[k]);
+  tc_fence_before();
   __syncthreads();
-  if (sum_a || sum_b) {
-    float* gb = part + b_off(l);
-    const int nb = sum_a ? 128 : N;
-    for (int i = t; i < nb; i += DW_THREADS) gb[(sum_a ? half * 128 : 0) + i] = colsum[i];
-  }
   if (warp == 0) tmem_dealloc(tmem);
 }
 
@@ -755,6 +770,8 @@ struct tamp_mlp {
   float* out = nullptr;        // [max_batch][OUT]
   float* dout = nullptr;       // [max_batch][OUT]
   float* part = nullptr;       // [DW_MAX_SPLITS][N_PARAMS]: per row split partial gradients
+  mlpk::DwMaps dw_maps;        // tensor maps of the weight-gradient operands for batches of dw_maps_B rows
+  int dw_maps_B = -1;
   float* loss = nullptr;
   int* err = nullptr;
   long step = 0;
@@ -817,6 +834,50 @@ FwdArgs fwd_args(tamp_mlp* n, const float* x, int B, float* out, bool train) {
   return a;
 }
 
+// cuTensorMapEncodeTiled from the driver, through the runtime (no link-time
+// dependency on the driver library)
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encode_tiled() {
+  static EncodeTiled fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  }
+  return fn;
+}
+
+// The weight-gradient operands as 2-D tensors [features][batch rows] (row
+// length ldT, B valid rows: the copies fill rows past B with zeros), with
+// boxes of 8 batch rows by 128 features (A operands) or by every feature (B
+// operands).
+tamp_status make_dw_maps(tamp_mlp* n, int B) {
+  if (n->dw_maps_B == B) return TAMP_OK;
+  EncodeTiled enc = encode_tiled();
+  if (!enc) return mfail(n, TAMP_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const size_t lt = static_cast<size_t>(n->ldT);
+  struct Spec { const void* base; int rows, box; };
+  const Spec spec[8] = {
+      {n->dZT, H, 128}, {n->dZT + H * lt, H, 128}, {n->dZT + 2 * H * lt, H, 128}, {n->AT + 2 * H * lt, H, 128},
+      {n->XT, IN, IN}, {n->AT, H, H}, {n->AT + H * lt, H, H}, {n->dZT + 3 * H * lt, OUT, OUT}};
+  for (int i = 0; i < 8; ++i) {
+    const cuuint64_t dims[2] = {static_cast<cuuint64_t>(B), static_cast<cuuint64_t>(spec[i].rows)};
+    const cuuint64_t strides[1] = {static_cast<cuuint64_t>(lt * 2)};
+    const cuuint32_t box[2] = {8, static_cast<cuuint32_t>(spec[i].box)};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = enc(&n->dw_maps.map[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(spec[i].base),
+                           dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return mfail(n, TAMP_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
+  }
+  n->dw_maps_B = B;
+  return TAMP_OK;
+}
+
 tamp_status check_err(tamp_mlp* n) {
   int e = 0;
   MLP_TRY(n, cudaMemcpyAsync(&e, n->err, 4, cudaMemcpyDeviceToHost, n->stream));
@@ -844,13 +905,16 @@ tamp_status gradient(tamp_mlp* n, const float* x, const float* y, const float* m
   z.dZT[3] = n->dZT + static_cast<size_t>(3) * H * n->ldT;
   mlp_backward_dz_kernel<<<tiles, THREADS, SMEM_BYTES, n->stream>>>(z);
   MLP_TRY(n, cudaGetLastError());
+  // weight gradients: 8 (layer, 128 outputs) blocks x row splits, about one CTA per SM
+  const tamp_status ms = make_dw_maps(n, B);
+  if (ms != TAMP_OK) return ms;
   DwArgs w{};
-  const int splits = std::max(1, std::min(DW_MAX_SPLITS, (B + 511) / 512));
-  w.B = B; w.ldT = n->ldT; w.part = n->part; w.err = n->err; w.XT = n->XT;
+  int sm = 148;
+  cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, n->device);
+  const int splits = std::max(1, std::min({DW_MAX_SPLITS, sm / 8, (B + DW_CHUNK - 1) / DW_CHUNK}));
+  w.B = B; w.part = n->part; w.err = n->err;
   w.rows_per_split = ((B + splits - 1) / splits + DW_CHUNK - 1) / DW_CHUNK * DW_CHUNK;
-  for (int l = 0; l < 3; ++l) w.AT[l] = n->AT + static_cast<size_t>(l) * H * n->ldT;
-  for (int l = 0; l < 4; ++l) w.dZT[l] = z.dZT[l];
-  mlp_backward_dw_kernel<<<dim3(8, splits), DW_THREADS, DW_SMEM, n->stream>>>(w);
+  mlp_backward_dw_kernel<<<dim3(8, splits), DW_THREADS, DW_SMEM, n->stream>>>(n->dw_maps, w);
   MLP_TRY(n, cudaGetLastError());
   mlp_reduce_kernel<<<static_cast<int>((N_PARAMS + 255) / 256), 256, 0, n->stream>>>(n->part, splits, n->grad,
                                                                                    static_cast<int>(N_PARAMS));

@@ -71,11 +71,13 @@ def test_forward_matches_oracle(pkg, B):
     net.close()
 
 
-@pytest.mark.parametrize("B", [128, 300])
+@pytest.mark.parametrize("B", [128, 300, 3000, 16384])
 def test_gradient_matches_oracle(pkg, B):
+    # 3000 rows: weight-gradient row splits of three chunks and splits with no
+    # rows at all; 16384 (the benchmark's training batch): 15 chunks per split
     th = _params(5)
     x, y, mask = _batch(B, 20 + B)
-    net = pkg.Mlp(max_batch=512)
+    net = pkg.Mlp(max_batch=max(512, B))
     net.set_params(th)
     loss, g = net.gradient(_cuda(x), _cuda(y), _cuda(mask))
     g = g.cpu().double().numpy()
@@ -128,7 +130,10 @@ def test_training_fits_a_conditional_gaussian_and_stays_consistent(pkg):
         x = g.normal(0.0, 1.0, (B, om.IN)).astype(np.float32)
         y = np.zeros((B, 16), np.float32)
         y[:, :9] = x @ A.T + g.normal(0.0, 1.0, (B, 9)) * sig
-        losses.append(net.train_step(_cuda(x), _cuda(y), _cuda(mask), 2e-3))
+        # at 2e-3 throughout, the loss keeps bouncing by ~1 over the last 150 steps (the
+        # smallest noise's log sigma sits in a steep valley) and where the run stops
+        # depends on the last bits of the gradients; the lower rate settles it
+        losses.append(net.train_step(_cuda(x), _cuda(y), _cuda(mask), 2e-3 if it < 200 else 4e-4))
     assert losses[-1] < losses[0] - 3.0, (losses[0], losses[-1])
     # the trained parameters read back drive the oracle to the kernel's outputs
     th1 = net.get_params()
