@@ -511,20 +511,19 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_backward_dz_kernel(DzArgs a) {
 // per CTA one layer, 128 of its outputs and a split of the batch rows, which
 // are the GEMM's K.  Both operands are feature-major in global memory
 // ([features][ldT]); TMA tensor copies (cp.async.bulk.tensor) bring each
-// 64-row chunk into a ring of DW_STAGES shared-memory stages in the canonical
-// K-major layout without swizzle -- one copy of a box of 8 batch rows (16
-// bytes) by R features per 8-row group, so that every 8 x 16-byte core matrix
-// is contiguous (core matrices 128 B apart along M/N, R x 16 B apart along K)
-// -- while one thread issues the MMAs of the chunks that have landed.  The
-// 128 threads of the epilogue warps add each of their row's chunk values for
-// db before releasing a stage.  Batch rows past B are filled with zeros by
-// the copies.
+// 64-row chunk -- one box of 64 batch rows (128 bytes) by R features per
+// operand -- into a ring of DW_STAGES shared-memory stages in the 128-byte
+// swizzled K-major layout the tensor core reads (8-row atoms of 1 KB, the
+// 16-byte pieces of row r at positions permuted by r mod 8), while one thread
+// issues the MMAs of the chunks that have landed.  The 128 threads of the
+// epilogue warps add each of their row's chunk values for db before releasing
+// a stage.  Batch rows past B are filled with zeros by the copies.
 constexpr int DW_STAGES = 4;
 constexpr int DW_CHUNK = 64;                              // batch rows per stage (4 MMAs of K = 16)
 constexpr int DW_THREADS = 160;                           // 4 epilogue warps (TMEM lane quarters) + 1 issuing warp
 constexpr size_t DW_STAGE_A = 128 * DW_CHUNK * 2, DW_STAGE_B = 256 * DW_CHUNK * 2;
 constexpr size_t DW_STAGE = DW_STAGE_A + DW_STAGE_B;
-constexpr size_t DW_SMEM = DW_STAGES * DW_STAGE;
+constexpr size_t DW_SMEM = DW_STAGES * DW_STAGE + 1024;  // + alignment of the ring to the 1 KB swizzle atom
 constexpr int DW_MAX_SPLITS = 32;
 
 // tensor maps: A operands (128-feature boxes) dZ_0^T, dZ_1^T, dZ_2^T, A_2^T;
@@ -560,10 +559,12 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
-// K-major, no swizzle, with explicit core-matrix strides: lbo along K, sbo along M/N
-__device__ __forceinline__ uint64_t smem_desc_strided(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
-         (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+// K-major with the 128-byte swizzle: 8-row atoms 1024 B apart (stride offset),
+// leading offset unused (16 B), descriptor version 1, layout type 2 (128-byte
+// swizzle); a K step of 16 BF16 inside the 128-byte row advances the start by 32 B
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) | (1ull << 16) | (static_cast<uint64_t>(1024 >> 4) << 32) |
+         (1ull << 46) | (2ull << 61);
 }
 
 __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __grid_constant__ DwMaps tm, DwArgs a) {
@@ -595,8 +596,9 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tslot;
-  auto stage_a = [&](int st) { return smem + st * DW_STAGE; };
-  auto stage_b = [&](int st) { return smem + st * DW_STAGE + DW_STAGE_A; };
+  unsigned char* ring = smem + ((1024u - (smem_u32(smem) & 1023u)) & 1023u);  // 1 KB aligned
+  auto stage_a = [&](int st) { return ring + st * DW_STAGE; };
+  auto stage_b = [&](int st) { return ring + st * DW_STAGE + DW_STAGE_A; };
 
   if (t == 128) {
     // copies and MMAs: chunk c lives in stage c % DW_STAGES; its stage is refilled
@@ -604,10 +606,8 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __
     auto load = [&](int c) {
       const int st = c % DW_STAGES, x0 = r_begin + c * DW_CHUNK;
       mbar_expect_tx(&full[st], stage_tx);
-      for (int j = 0; j < DW_CHUNK / 8; ++j) {
-        tma_load_2d(stage_a(st) + j * 128 * 16, mA, x0 + 8 * j, half * 128, &full[st]);
-        tma_load_2d(stage_b(st) + j * NB_ * 16, mB, x0 + 8 * j, 0, &full[st]);
-      }
+      tma_load_2d(stage_a(st), mA, x0, half * 128, &full[st]);
+      tma_load_2d(stage_b(st), mB, x0, 0, &full[st]);
     };
     const uint32_t id = instr_desc(ROWS, NB_);
     int issued = 0;
@@ -623,8 +623,8 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __
       tc_fence_after();
       const uint32_t a0 = smem_u32(stage_a(st)), b0 = smem_u32(stage_b(st));
       for (int kk = 0; kk < DW_CHUNK / 16; ++kk)
-        umma_bf16(tmem, smem_desc_strided(a0 + kk * 2 * 128 * 16, 128 * 16, 128),
-                  smem_desc_strided(b0 + kk * 2 * NB_ * 16, NB_ * 16, 128), id, (c > 0 || kk > 0) ? 1u : 0u);
+        umma_bf16(tmem, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), id,
+                  (c > 0 || kk > 0) ? 1u : 0u);
       umma_commit(&empty[st]);
       if (issued < n_chunks) {
         if (!mbar_wait_bounded(&empty[st], par)) {
@@ -652,11 +652,10 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __
         break;
       }
       if (mine) {
-        const unsigned char* base = sum_a ? stage_a(st) : stage_b(st);
-        const int R = sum_a ? 128 : NB_;
+        // the row's 128 bytes, its 16-byte pieces in swizzled order (the sum does not mind)
+        const unsigned char* base = (sum_a ? stage_a(st) : stage_b(st)) + row * 128;
 #pragma unroll
-        for (int j = 0; j < DW_CHUNK / 8; ++j)
-          cs += sum8(*reinterpret_cast<const uint4*>(base + j * R * 16 + (row >> 3) * 128 + (row & 7) * 16));
+        for (int j = 0; j < DW_CHUNK / 8; ++j) cs += sum8(*reinterpret_cast<const uint4*>(base + j * 16));
       }
       mbar_arrive(&empty[st]);
     }
@@ -853,8 +852,8 @@ EncodeTiled encode_tiled() {
 
 // The weight-gradient operands as 2-D tensors [features][batch rows] (row
 // length ldT, B valid rows: the copies fill rows past B with zeros), with
-// boxes of 8 batch rows by 128 features (A operands) or by every feature (B
-// operands).
+// boxes of 64 batch rows by 128 features (A operands) or by every feature (B
+// operands), written into shared memory with the 128-byte swizzle.
 tamp_status make_dw_maps(tamp_mlp* n, int B) {
   if (n->dw_maps_B == B) return TAMP_OK;
   EncodeTiled enc = encode_tiled();
@@ -867,10 +866,10 @@ tamp_status make_dw_maps(tamp_mlp* n, int B) {
   for (int i = 0; i < 8; ++i) {
     const cuuint64_t dims[2] = {static_cast<cuuint64_t>(B), static_cast<cuuint64_t>(spec[i].rows)};
     const cuuint64_t strides[1] = {static_cast<cuuint64_t>(lt * 2)};
-    const cuuint32_t box[2] = {8, static_cast<cuuint32_t>(spec[i].box)};
+    const cuuint32_t box[2] = {DW_CHUNK, static_cast<cuuint32_t>(spec[i].box)};
     const cuuint32_t es[2] = {1, 1};
     const CUresult r = enc(&n->dw_maps.map[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(spec[i].base),
-                           dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return mfail(n, TAMP_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
   }
