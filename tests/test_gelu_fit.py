@@ -1,5 +1,5 @@
 """The GELU of the network kernels evaluates erf by a polynomial fit (the
-coefficients in tamp_mlp.cu's erf_fit).  Evaluated here the way the kernel
+coefficients kErfFit in tamp_mlp.cu).  Evaluated here the way the kernel
 does -- FP32 clamp, FP32 Horner in t = 2 x^2 / 3.2^2 - 1 -- it must stay
 within 1e-5 of the double-precision erf everywhere, and the GELU built on it
 within 2.5e-5 (absolute) of the exact GELU, far below the BF16 rounding of
@@ -16,11 +16,9 @@ SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), 
 
 def _coefficients():
     body = open(SRC).read()
-    body = body[body.index("float erf_fit(float x)"):]
-    body = body[:body.index("return xc * p;")]
-    first = re.search(r"float p = (-?[0-9.e-]+)f;", body).group(1)
-    rest = re.findall(r"p = fmaf\(p, t, (-?[0-9.e-]+)f\);", body)
-    return [np.float32(v) for v in [first] + rest]          # highest degree first
+    body = body[body.index("kErfFit[11] = {"):]
+    body = body[body.index("{") + 1:body.index("}")]
+    return [np.float32(v.strip().rstrip("f")) for v in body.split(",") if v.strip()]   # highest degree first
 
 
 def _erf_fit(x):
