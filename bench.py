@@ -36,7 +36,11 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM traffic of one optimize_kernel launch on this workload, from an ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the
 # kernel source whose hash is recorded with it.
-TRAFFIC = {"source_sha": "5f7b06a84441ce6b", "bytes_per_launch": 6313472}
+TRAFFIC = {"source_sha": "2dcb940e8d11cfdc", "bytes_per_launch": 6312960}
+# ... and of one launch of the stress configuration (65536 particles, 2 lanes,
+# 16 warps; the particle state is read and written once per launch whatever
+# the iteration count), from a 20-iteration capture of the same source
+STRESS_TRAFFIC = {"source_sha": "2dcb940e8d11cfdc", "bytes_per_launch": 206102016 + 152663296}
 
 
 def kernel_source_sha() -> str:
@@ -384,8 +388,10 @@ def measure_stress(pkg, sg, flops, net, dev, steps=2, warmup=1, T=1000, P=65536)
             "value": P * T / (step_ms / 1e3), "unit": "particle-iters/s", "ms_per_step": step_ms, "kernel_ms": kern_ms,
             "launch_shape": {"lanes": L, "warps": W, "trial_ms_10_iters": round(tms, 3)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "optimize_kernel",
-                         "flop_per_launch": launch_flops},
+                         "frac": achieved / peak,
+                         "traffic": (STRESS_TRAFFIC["bytes_per_launch"]
+                                     if STRESS_TRAFFIC["source_sha"] == kernel_source_sha() else None),
+                         "kernel": "optimize_kernel", "flop_per_launch": launch_flops},
             "satisfied_last_step": int(q["n_satisfied"]), "first_satisfying_iter_last_step": int(q["first_iter"]),
             "clocks": clk.summary(), "gpu_launches": 3 * steps}
 
