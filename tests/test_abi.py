@@ -57,5 +57,11 @@ def test_default_options_are_the_papers(lib):
 def test_null_arguments_are_rejected_without_a_device(lib):
     h = ctypes.c_void_p()
     assert lib.tamp_create_scene(None, 0, None, None, ctypes.byref(h)) == 1
+    # an allocator must give both callbacks: refused before the description is read or a device touched
+    from paper_2411_11833_b300 import _native
+    half = _native.Allocator(_native.ALLOC_FN(lambda n, d, s, c: None), _native.FREE_FN(), None)
+    desc = _native.SceneDesc()
+    assert lib.tamp_create_scene(ctypes.byref(desc), 0, None, ctypes.byref(half), ctypes.byref(h)) == 1
+    assert not h.value
     assert lib.tamp_destroy_scene(None) == 1
     assert lib.tamp_optimize_steps(None, None, 0, 1, 0) == 1
