@@ -364,6 +364,229 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
   if (warp == 0) tmem_dealloc(tmem);
 }
 
+// ------------------------------------------------------------------ forward, two tiles in turn
+// Inference forward over many rows: each CTA takes pairs of 128-row tiles and
+// runs them half a layer apart, so that the tensor core computes one tile's
+// layer while the 16 epilogue warps turn the other tile's accumulator into
+// its next activations:
+//   MMA(t0, L0) | epi(t0, L0) + MMA(t1, L0) | epi(t1, L0) + MMA(t0, L1) | ...
+// Each tile keeps its activations in its own 64 KB operand buffer and its
+// accumulator in its own 256 tensor-memory columns.  The weights stream in
+// K-chunks of 64 (at most 32 KB, one bulk copy each) through a 2-stage ring,
+// once per (tile, layer), in the order the MMAs use them.  Roles: warps 0-15
+// epilogue (warp w: TMEM lane quarter w % 4, column group w / 4), warp 16 the
+// copies, warp 17 the MMAs.  Every wait is bounded; a wait that gives up sets
+// the error word and every role stops at its next wait.
+constexpr int PP_EPI_WARPS = 16;
+constexpr int PP_THREADS = (PP_EPI_WARPS + 2) * 32;
+constexpr int PP_KCHUNK = 64;                               // K per weight chunk (4 MMAs of K = 16)
+constexpr size_t PP_STAGE = 256 * PP_KCHUNK * 2;            // largest chunk: N = 256
+constexpr size_t PP_SMEM = 2 * SMEM_A + 2 * PP_STAGE;       // two activation tiles + the weight ring
+// chunks of layer l: 48 inputs -> one chunk of 3 K-blocks, 256 -> four of 4
+__host__ __device__ constexpr int pp_chunks(int l) { return (kdim(l) + PP_KCHUNK - 1) / PP_KCHUNK; }
+__host__ __device__ constexpr int pp_kblocks(int l, int c) {
+  return (kdim(l) - c * PP_KCHUNK) >= PP_KCHUNK ? PP_KCHUNK / 16 : (kdim(l) - c * PP_KCHUNK) / 16;
+}
+
+__device__ __forceinline__ void tmem_alloc512(uint32_t* slot) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(slot)) : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc512(uint32_t taddr) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(taddr) : "memory");
+}
+__device__ __forceinline__ void mbar_init_cnt(uint64_t* bar, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_one(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+struct PpArgs {
+  const float* x; int B;              // inputs [B][IN]
+  const unsigned char* Wp;            // packed BF16 forward operands (pk_off)
+  const float* b[4];
+  float* out;                         // [B][OUT]
+  int* err;
+};
+
+// Stage the inputs of rows row0 .. row0 + 127 as a BF16 operand (zeros past B).
+__device__ __forceinline__ void pp_stage_input(unsigned char* A, const float* x, int B, int row0, int t) {
+  for (int c = t; c < ROWS * (IN / 8); c += PP_EPI_WARPS * 32) {
+    const int rr = c / (IN / 8), kk = (c % (IN / 8)) * 8;
+    float v[8];
+    const bool in = row0 + rr < B;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = in ? x[static_cast<long>(row0 + rr) * IN + kk + e] : 0.f;
+    *reinterpret_cast<uint4*>(A + blk_off(rr, kk, ROWS)) =
+        make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+  }
+}
+
+__global__ void __launch_bounds__(PP_THREADS, 1) mlp_forward_pp_kernel(PpArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* ring = smem + 2 * SMEM_A;
+  __shared__ __align__(8) uint64_t w_full[2], w_empty[2], acc_full[2], a_ready[2];
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+  __shared__ __align__(16) float s_bias[3 * H + OUT];
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int n_tiles = (a.B + ROWS - 1) / ROWS, n_pairs = (n_tiles + 1) / 2;
+  if (t == 0) {
+    abort_flag = 0;
+    for (int i = 0; i < 2; ++i) {
+      mbar_init_cnt(&w_full[i], 1);
+      mbar_init_cnt(&w_empty[i], 1);
+      mbar_init_cnt(&acc_full[i], 1);
+      mbar_init_cnt(&a_ready[i], PP_EPI_WARPS);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = t; i < 3 * H + OUT; i += PP_THREADS) s_bias[i] = i < 3 * H ? a.b[i / H][i % H] : a.b[3][i - 3 * H];
+  if (warp == 0) tmem_alloc512(&tslot);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tslot;
+  int my_pairs = 0;
+  for (int p = blockIdx.x; p < n_pairs; p += gridDim.x) ++my_pairs;
+  auto give_up = [&]() {
+    atomicOr(a.err, ERR_WAIT);
+    abort_flag = 1;
+  };
+
+  if (warp == PP_EPI_WARPS) {
+    // ---- copies: every (pair, layer, tile) job's weight chunks, in MMA order
+    if (lane == 0) {
+      int q = 0;
+      for (int i = 0; i < my_pairs; ++i)
+        for (int l = 0; l < 4; ++l)
+          for (int tt = 0; tt < 2; ++tt)
+            for (int c = 0; c < pp_chunks(l); ++c) {
+              const int s = q & 1;
+              if (q >= 2 && (abort_flag || !mbar_wait_bounded(&w_empty[s], static_cast<uint32_t>((q >> 1) - 1) & 1u))) {
+                give_up();
+                goto copies_done;
+              }
+              const uint32_t bytes = static_cast<uint32_t>(pp_kblocks(l, c) * ndim(l) * 32);
+              mbar_expect_tx(&w_full[s], bytes);
+              bulk_g2s(ring + s * PP_STAGE, a.Wp + pk_off(l) + static_cast<size_t>(c) * (PP_KCHUNK / 16) * ndim(l) * 32,
+                       bytes, &w_full[s]);
+              ++q;
+            }
+    copies_done:
+      // no copy may land after the CTA ends
+      for (int qq = max(0, q - 2); qq < q; ++qq) mbar_wait_bounded(&w_full[qq & 1], static_cast<uint32_t>(qq >> 1) & 1u);
+    }
+  } else if (warp == PP_EPI_WARPS + 1) {
+    // ---- MMAs: job (tile tt, layer l) once tile tt's activations for layer l are staged
+    if (lane == 0) {
+      int q = 0, j0 = 0, j1 = 0;
+      for (int i = 0; i < my_pairs; ++i)
+        for (int l = 0; l < 4; ++l)
+          for (int tt = 0; tt < 2; ++tt) {
+            const int j = tt ? j1 : j0;
+            if (abort_flag || !mbar_wait_bounded(&a_ready[tt], static_cast<uint32_t>(j) & 1u)) {
+              give_up();
+              goto mma_done;
+            }
+            tc_fence_after();
+            const uint32_t acc = tmem + static_cast<uint32_t>(tt * 256);
+            const uint32_t id = instr_desc(ROWS, ndim(l));
+            const uint32_t A0 = smem_u32(smem + tt * SMEM_A);
+            for (int c = 0; c < pp_chunks(l); ++c) {
+              const int s = q & 1;
+              if (!mbar_wait_bounded(&w_full[s], static_cast<uint32_t>(q >> 1) & 1u)) {
+                give_up();
+                goto mma_done;
+              }
+              const uint32_t b0 = smem_u32(ring + s * PP_STAGE);
+              for (int kb = 0; kb < pp_kblocks(l, c); ++kb)
+                umma_bf16(acc, smem_desc(A0 + (c * (PP_KCHUNK / 16) + kb) * ROWS * 32),
+                          smem_desc(b0 + kb * ndim(l) * 32), id, (c > 0 || kb > 0) ? 1u : 0u);
+              umma_commit(&w_empty[s]);
+              ++q;
+            }
+            umma_commit(&acc_full[tt]);
+            if (tt) ++j1; else ++j0;
+          }
+    mma_done:;
+    }
+  } else {
+    // ---- epilogues: warp w reads TMEM lanes 32 (w % 4) .. + 31, column group w / 4
+    const int grp = warp >> 2, row = 32 * (warp & 3) + lane;
+    int j0 = 0, j1 = 0;
+    if (my_pairs > 0) {
+      pp_stage_input(smem, a.x, a.B, 2 * blockIdx.x * ROWS, t);
+      pp_stage_input(smem + SMEM_A, a.x, a.B, (2 * blockIdx.x + 1) * ROWS, t);
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive_one(&a_ready[0]);
+      mbar_arrive_one(&a_ready[1]);
+    }
+    for (int i = 0; i < my_pairs; ++i) {
+      const int pair = blockIdx.x + i * gridDim.x;
+      for (int l = 0; l < 4; ++l)
+        for (int tt = 0; tt < 2; ++tt) {
+          const int j = tt ? j1 : j0;
+          if (abort_flag || !mbar_wait_bounded(&acc_full[tt], static_cast<uint32_t>(j) & 1u)) {
+            give_up();
+            goto epi_done;
+          }
+          tc_fence_after();
+          unsigned char* A = smem + tt * SMEM_A;
+          const uint32_t acc = tmem + static_cast<uint32_t>(tt * 256);
+          const int r = (2 * pair + tt) * ROWS + row;
+          if (l < 3) {
+            for (int c0 = grp * (H / 4); c0 < (grp + 1) * (H / 4); c0 += 32) {
+              float v[32];
+              tmem_ld32(lane_addr(acc, c0), v);
+              const float* bias = s_bias + l * H + c0;
+              uint32_t hp[16];
+#pragma unroll
+              for (int e = 0; e < 32; e += 2) {
+                const float2 g = gelu2(__fadd2_rn(make_float2(v[e], v[e + 1]), make_float2(bias[e], bias[e + 1])));
+                hp[e / 2] = pack_bf16x2(g.x, g.y);
+              }
+#pragma unroll
+              for (int qd = 0; qd < 4; ++qd)
+                *reinterpret_cast<uint4*>(A + blk_off(row, c0 + 8 * qd, ROWS)) =
+                    make_uint4(hp[4 * qd], hp[4 * qd + 1], hp[4 * qd + 2], hp[4 * qd + 3]);
+            }
+          } else {
+            if (grp == 0) {
+              float v[32];
+              tmem_ld32(lane_addr(acc, 0), v);
+              if (r < a.B) {
+                const float* bias = s_bias + 3 * H;
+                float4* od = reinterpret_cast<float4*>(a.out + static_cast<long>(r) * OUT);
+#pragma unroll
+                for (int qd = 0; qd < 8; ++qd)
+                  od[qd] = make_float4(v[4 * qd] + bias[4 * qd], v[4 * qd + 1] + bias[4 * qd + 1],
+                                       v[4 * qd + 2] + bias[4 * qd + 2], v[4 * qd + 3] + bias[4 * qd + 3]);
+              }
+            }
+            // this tile's buffer takes the next pair's inputs
+            if (i + 1 < my_pairs) pp_stage_input(A, a.x, a.B, (2 * (pair + gridDim.x) + tt) * ROWS, t);
+          }
+          fence_proxy_async();  // the activations, written by every thread, to the tensor core
+          tc_fence_before();    // ... after this warp's reads of the accumulator
+          __syncwarp();
+          if (lane == 0) mbar_arrive_one(&a_ready[tt]);
+          if (tt) ++j1; else ++j0;
+        }
+    }
+  epi_done:;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc512(tmem);
+}
+
 // ------------------------------------------------------------------ loss
 // Gaussian NLL per row: sum over masked k of (y - mu)^2 exp(-2 s) / 2 + s,
 // mean over rows; dOut = d(mean)/d(out).
@@ -820,6 +1043,9 @@ cudaError_t enable_smem(int device) {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mlp_backward_dw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(DW_SMEM));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mlp_forward_pp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(PP_SMEM));
   if (e == cudaSuccess) done |= bit;
   return e;
 }
@@ -880,6 +1106,19 @@ tamp_status make_dw_maps(tamp_mlp* n, int B) {
   }
   n->dw_maps_B = B;
   return TAMP_OK;
+}
+
+// Inference forward: pairs of 128-row tiles, about one CTA per SM, each taking
+// pairs until none is left.
+cudaError_t launch_forward_pp(tamp_mlp* n, const float* x, int B, float* out, cudaStream_t st) {
+  PpArgs a{};
+  a.x = x; a.B = B; a.out = out; a.err = n->err; a.Wp = n->wp;
+  for (int l = 0; l < 4; ++l) a.b[l] = n->params + b_off(l);
+  int sm = 148;
+  cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, n->device);
+  const int pairs = ((B + ROWS - 1) / ROWS + 1) / 2;
+  mlp_forward_pp_kernel<<<std::min(pairs, sm), PP_THREADS, PP_SMEM, st>>>(a);
+  return cudaGetLastError();
 }
 
 tamp_status check_err(tamp_mlp* n) {
@@ -1012,8 +1251,7 @@ tamp_status tamp_mlp_forward(tamp_mlp* n, const float* x_dev, int B, float* out_
   if (!x_dev || !out_dev || B <= 0) return mfail(n, TAMP_ERR_INVALID_ARG, "bad forward arguments");
   Dev g(n->device);
   MLP_TRY(n, enable_smem(n->device));
-  mlp_forward_kernel<<<(B + ROWS - 1) / ROWS, THREADS, SMEM_BYTES, n->stream>>>(fwd_args(n, x_dev, B, out_dev, false));
-  MLP_TRY(n, cudaGetLastError());
+  MLP_TRY(n, launch_forward_pp(n, x_dev, B, out_dev, n->stream));
   return TAMP_OK;
 }
 
@@ -1063,7 +1301,6 @@ tamp_status mlp_forward_on_stream(tamp_mlp* n, const float* x_dev, int B, float*
   if (n->device != device) return mfail(n, TAMP_ERR_INVALID_ARG, "network and scene are on different devices");
   MLP_TRY(n, cudaStreamSynchronize(n->stream));
   MLP_TRY(n, enable_smem(n->device));
-  mlp_forward_kernel<<<(B + ROWS - 1) / ROWS, THREADS, SMEM_BYTES, st>>>(fwd_args(n, x_dev, B, out_dev, false));
-  MLP_TRY(n, cudaGetLastError());
+  MLP_TRY(n, launch_forward_pp(n, x_dev, B, out_dev, st));
   return TAMP_OK;
 }
