@@ -243,9 +243,6 @@ struct FwdArgs {
   // BF16 operands of the weight gradients, feature-major: x^T [IN][ldT],
   // A_l^T [H][ldT]
   float* Z[3]; __nv_bfloat16* XT; __nv_bfloat16* AT[3]; int ldT;
-  // training only (else null): the Gaussian NLL of the outputs against y
-  // [B][16] under mask [B][16], its gradient dout [B][OUT] and the loss sum
-  const float* y; const float* mask; float* dout; float* loss;
   int* err;
 };
 
@@ -348,36 +345,12 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
               at[static_cast<long>(2 * j + 1) * a.ldT] = h2.y;
             }
           }
-        } else {
-          float lsum = 0.f;
-          if (r < a.B) {
+        } else if (r < a.B) {
+          float4* od = reinterpret_cast<float4*>(a.out + static_cast<long>(r) * OUT + c0);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] += bias[j];
-            float4* od = reinterpret_cast<float4*>(a.out + static_cast<long>(r) * OUT + c0);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) od[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-            if (a.dout) {
-              // the loss, fused: sum over masked k of (y - mu)^2 exp(-2 s) / 2 + s, and its
-              // gradient with respect to mu and s divided by B (the mean over rows)
-              const float inv = 1.f / static_cast<float>(a.B);
-              const float* yr = a.y + static_cast<long>(r) * NTGT;
-              const float* mr = a.mask + static_cast<long>(r) * NTGT;
-              float* dr = a.dout + static_cast<long>(r) * OUT;
-#pragma unroll
-              for (int k = 0; k < NTGT; ++k) {
-                const float mu = v[k], sd = v[NTGT + k], m = mr[k], d = yr[k] - mu;
-                const float e = expf(-2.f * sd);
-                lsum += m * (0.5f * d * d * e + sd);
-                dr[k] = m * (-d * e) * inv;
-                dr[NTGT + k] = m * (1.f - d * d * e) * inv;
-              }
-            }
-          }
-          if (a.dout) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-            if (lane == 0 && lsum != 0.f) atomicAdd(a.loss, lsum / static_cast<float>(a.B));
-          }
+          for (int q = 0; q < 8; ++q)
+            od[q] = make_float4(v[4 * q] + bias[4 * q], v[4 * q + 1] + bias[4 * q + 1], v[4 * q + 2] + bias[4 * q + 2],
+                                v[4 * q + 3] + bias[4 * q + 3]);
         }
       }
     }
@@ -612,6 +585,36 @@ __global__ void __launch_bounds__(PP_THREADS, 1) mlp_forward_pp_kernel(PpArgs a)
   __syncthreads();
   tc_fence_after();
   if (warp == 0) tmem_dealloc512(tmem);
+}
+
+// ------------------------------------------------------------------ loss
+// Gaussian NLL per row: sum over masked k of (y - mu)^2 exp(-2 s) / 2 + s,
+// mean over rows; dOut = d(mean)/d(out).
+__global__ void mlp_loss_kernel(const float* out, const float* y, const float* mask, int B, float* dout,
+                                float* loss_sum) {
+  // one thread per (row, target): consecutive threads read consecutive targets
+  const long i = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  float l = 0.f;
+  if (i < static_cast<long>(B) * NTGT) {
+    const long r = i / NTGT;
+    const int k = static_cast<int>(i - r * NTGT);
+    const float inv = 1.f / static_cast<float>(B);
+    const float mu = out[r * OUT + k], s = out[r * OUT + NTGT + k];
+    const float m = mask[i], d = y[i] - mu;
+    const float e = expf(-2.f * s);
+    l = m * (0.5f * d * d * e + s);
+    dout[r * OUT + k] = m * (-d * e) * inv;
+    dout[r * OUT + NTGT + k] = m * (1.f - d * d * e) * inv;
+  }
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  __shared__ float part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = l;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float sum = 0.f;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) sum += part[w];
+    if (sum != 0.f) atomicAdd(loss_sum, sum / static_cast<float>(B));
+  }
 }
 
 // ------------------------------------------------------------------ backward
@@ -1136,9 +1139,10 @@ tamp_status gradient(tamp_mlp* n, const float* x, const float* y, const float* m
   MLP_TRY(n, enable_smem(n->device));
   const int tiles = (B + ROWS - 1) / ROWS;
   MLP_TRY(n, cudaMemsetAsync(n->loss, 0, 4, n->stream));
-  FwdArgs fa = fwd_args(n, x, B, n->out, true);
-  fa.y = y; fa.mask = mask; fa.dout = n->dout; fa.loss = n->loss;   // the loss in the output layer's epilogue
-  mlp_forward_kernel<<<tiles, THREADS, SMEM_BYTES, n->stream>>>(fa);
+  mlp_forward_kernel<<<tiles, THREADS, SMEM_BYTES, n->stream>>>(fwd_args(n, x, B, n->out, true));
+  MLP_TRY(n, cudaGetLastError());
+  mlp_loss_kernel<<<static_cast<int>((static_cast<long>(B) * NTGT + 255) / 256), 256, 0, n->stream>>>(
+      n->out, y, mask, B, n->dout, n->loss);
   MLP_TRY(n, cudaGetLastError());
   DzArgs z{};
   z.B = B; z.ldT = n->ldT; z.dout = n->dout; z.WpT = n->wpt; z.err = n->err;
