@@ -149,6 +149,8 @@ typedef struct {
   int n_knots;                  /* knot configurations per motion between actions (0: none) */
   int self_collision;           /* 1: every configuration carries SelfCollision             */
   int grasp_dof;                /* 4 (0 reads as 4): top-down grasps; 6: 6-DOF grasps         */
+  int keep_best;                /* 1: every optimisation launch keeps the best-satisfying
+                                   record (tamp_query_best); the stop modes keep it anyway */
 } tamp_options;
 
 void tamp_default_options(tamp_options *opt);
@@ -305,6 +307,31 @@ tamp_status tamp_graph_destroy(tamp_graph *graph);
 tamp_status tamp_query_satisfied(tamp_scene *scene, int problem_id, uint8_t *mask,
                                  int *n_satisfied, int *first_iter, float *particles,
                                  float *cost, int *counts);
+
+/* Best satisfying state of each particle (Alg. 1 returns a particle that
+ * satisfies Eq. 3; the soft-cost experiments of Sec. VIII and the appendix
+ * keep the lowest-cost one).  Every Eq. 3 check of an optimisation launch that
+ * keeps the record -- at x_t before each update and after the last -- compares
+ * each satisfying particle's Eq. 2 cost with its record and keeps the state if
+ * the cost is lower, so a satisfying particle is not lost when later updates
+ * move it out of the feasible set (the state tamp_query_satisfied reports
+ * after a stop on the first satisfying particle is the one after the chunk's
+ * last update).  Launches that keep it: tamp_optimize_steps with
+ * stop_on_first_satisfying > 0, graphs created with stop_on_first, and every
+ * launch that includes a problem whose options set keep_best (the other
+ * problems of such a launch keep theirs too); other launches skip this work
+ * (about 1.5% of an iteration).  The record starts empty with each batch
+ * (tamp_sample_particles*, tamp_set_particles) and runs across calls and graph
+ * replays; tamp_autotune's trial launches leave it alone.  Host pointers, each
+ * may be NULL: found[P] (1: the particle satisfied some check), particles[D][P]
+ * (the recorded state; unspecified where found is 0), cost[P] (its Eq. 2 cost,
+ * +inf where found is 0), iter[P] (the check index, the Adam step count at that
+ * check, as first_iter counts; -1 where found is 0); *n_found = number of found
+ * particles.  A batch not checked yet is checked once first.  Synchronises.
+ * Errors: TAMP_ERR_INVALID_ARG for an unknown problem, TAMP_ERR_STATE without a
+ * batch. */
+tamp_status tamp_query_best(tamp_scene *scene, int problem_id, uint8_t *found, int *n_found,
+                            float *particles, float *cost, int *iter);
 
 /* Evaluate a caller batch on the device without touching the problem's state:
  * x_dev [D][n] (stride n), outputs (device, each may be NULL) cost[n] (Eq. 2),

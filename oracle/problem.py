@@ -456,25 +456,47 @@ class Problem:
         """OptimizeParticles: Adam on Eq. 4 for n_steps.  Satisfaction (Eq. 3) is
         checked at x_t before each update and once more after the last one; the
         index of the first check with a satisfying particle is returned (-1 if
-        none)."""
+        none).
+
+        Best satisfying record (Alg. 1 returns a satisfying particle; the
+        soft-cost experiments keep the lowest-cost one): for each particle, among
+        the checks k = 0..n_steps at which it satisfies Eq. 3, the state x_k of
+        lowest Eq. 2 cost (the earliest of equal ones), with that cost and its
+        check index t0 + k; best_iter -1 and best_cost +inf where it never
+        satisfies."""
         x = torch.as_tensor(x0, dtype=DT).clone()
         P = x.shape[0]
         m = torch.zeros_like(x) if m0 is None else torch.as_tensor(m0, dtype=DT).clone()
         v = torch.zeros_like(x) if v0 is None else torch.as_tensor(v0, dtype=DT).clone()
         first = -1
+        best_x = torch.zeros_like(x)
+        best_cost = torch.full((P,), math.inf, dtype=DT)
+        best_iter = torch.full((P,), -1, dtype=torch.long)
+
+        def record(terms, k):
+            sat = self.satisfied(terms)
+            cost = (terms * self.weights()).sum(1)
+            better = sat & (cost < best_cost)
+            best_x[better] = x[better]
+            best_cost[better] = cost[better]
+            best_iter[better] = t0 + k
+
         for it in range(n_steps):
             with torch.no_grad():
                 terms = self.term_values(x)
             if first < 0 and bool(self.satisfied(terms).any()):
                 first = it
+            record(terms, it)
             _, g = self.gradient(x)
             x, m, v = self.adam_step(x, m, v, t0 + it + 1, g, P)
         with torch.no_grad():
             terms = self.term_values(x)
         if first < 0 and bool(self.satisfied(terms).any()):
             first = n_steps
+        record(terms, n_steps)
         return dict(x=x, m=m, v=v, terms=terms, first_iter=first,
-                    satisfied=self.satisfied(terms), cost=(terms * self.weights()).sum(1))
+                    satisfied=self.satisfied(terms), cost=(terms * self.weights()).sum(1),
+                    best_x=best_x, best_cost=best_cost, best_iter=best_iter)
 
     # -------------------------------------------------------------- kink margins
     def kink_margin(self, x: torch.Tensor) -> torch.Tensor:

@@ -228,6 +228,21 @@ class Scene:
         return dict(mask=mask.astype(bool), n_satisfied=ns.value, first_iter=first.value, cost=cost,
                     counts=counts[:ncon], particles=parts)
 
+    def query_best(self, pid: int, n: int, want_particles: bool = True):
+        """tamp_query_best: each particle's lowest-cost state among the Eq. 3
+        checks it satisfied since the batch was set."""
+        D, _, _ = self.problem_info(pid)
+        found = np.zeros(n, np.uint8)
+        cost = np.zeros(n, np.float32)
+        it = np.zeros(n, np.int32)
+        parts = np.zeros((D, n), np.float32) if want_particles else None
+        nf = ctypes.c_int()
+        self._check(self._lib.tamp_query_best(
+            self._h, pid, ctypes.c_void_p(found.ctypes.data), ctypes.byref(nf),
+            None if parts is None else ctypes.c_void_p(parts.ctypes.data), ctypes.c_void_p(cost.ctypes.data),
+            ctypes.c_void_p(it.ctypes.data)))
+        return dict(found=found.astype(bool), n_found=nf.value, cost=cost, iter=it, particles=parts)
+
     def set_proposal(self, net):
         """Attach a proposal network (``Mlp``) for ``sample(..., sampler=1)``; None detaches."""
         self._proposal = net                      # keep it alive while attached

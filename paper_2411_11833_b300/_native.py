@@ -38,6 +38,7 @@ class Options(ctypes.Structure):
         ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
         ("optimize_grasp", ctypes.c_int), ("scale_by_batch", ctypes.c_int), ("lanes", ctypes.c_int),
         ("n_knots", ctypes.c_int), ("self_collision", ctypes.c_int), ("grasp_dof", ctypes.c_int),
+        ("keep_best", ctypes.c_int),
     ]
 
 
@@ -71,6 +72,8 @@ SIGNATURES = {
     "tamp_optimize_steps": (ctypes.c_int, [ctypes.c_void_p, c_int_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "tamp_query_satisfied": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, c_int_p, c_int_p,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "tamp_query_best": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, c_int_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
     "tamp_eval": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "tamp_eval_static_scratch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,

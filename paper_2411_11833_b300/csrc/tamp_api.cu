@@ -67,6 +67,9 @@ struct Problem {
   int* d_counts = nullptr;
   int* d_first = nullptr;
   unsigned long long* d_work = nullptr;  // [2] broad-phase candidates resolved exactly
+  // best-satisfying record of the batch (tamp_query_best) and the kernel's staging of x_t
+  float *d_best_x = nullptr, *d_best_cost = nullptr, *d_stage = nullptr;
+  int* d_best_iter = nullptr;
   bool has_batch = false, checked = false;
   // learned proposals: one row per Pick/Place action (features, decode record)
   int R = 0;
@@ -851,8 +854,10 @@ int problem_feat(const Problem& pr) { return feat_of(pr.n_seg > 0, pr.grasp6, pr
 void free_batch(tamp_scene* s, Problem& pr) {
   dfree(s, pr.d_x); dfree(s, pr.d_m); dfree(s, pr.d_v); dfree(s, pr.d_cost);
   dfree(s, pr.d_flags); dfree(s, pr.d_counts); dfree(s, pr.d_first); dfree(s, pr.d_work);
+  dfree(s, pr.d_best_x); dfree(s, pr.d_best_cost); dfree(s, pr.d_stage); dfree(s, pr.d_best_iter);
   pr.d_x = pr.d_m = pr.d_v = pr.d_cost = nullptr;
   pr.d_flags = nullptr; pr.d_counts = nullptr; pr.d_first = nullptr; pr.d_work = nullptr;
+  pr.d_best_x = pr.d_best_cost = pr.d_stage = nullptr; pr.d_best_iter = nullptr;
   pr.cap = 0;
 }
 
@@ -868,9 +873,16 @@ tamp_status ensure_batch(tamp_scene* s, Problem& pr, int P) {
     CUDA_TRY(s, dalloc(s, &pr.d_counts, static_cast<size_t>(std::max(pr.NCON, 1)) * 4));
     CUDA_TRY(s, dalloc(s, &pr.d_first, 4));
     CUDA_TRY(s, dalloc(s, &pr.d_work, 2 * sizeof(unsigned long long)));
+    CUDA_TRY(s, dalloc(s, &pr.d_best_x, n * 4));
+    CUDA_TRY(s, dalloc(s, &pr.d_stage, 2 * static_cast<size_t>(pr.D) * ((P + 31) & ~31) * 4));
+    CUDA_TRY(s, dalloc(s, &pr.d_best_cost, static_cast<size_t>(P) * 4));
+    CUDA_TRY(s, dalloc(s, &pr.d_best_iter, static_cast<size_t>(P) * 4));
     pr.cap = P;
   }
   CUDA_TRY(s, cudaMemsetAsync(pr.d_work, 0, 2 * sizeof(unsigned long long), s->stream));
+  // a new batch starts with no best-satisfying record: cost kNoBestCostBits, check index -1
+  CUDA_TRY(s, cudaMemsetAsync(pr.d_best_cost, kNoBestCostBits & 0xff, static_cast<size_t>(P) * 4, s->stream));
+  CUDA_TRY(s, cudaMemsetAsync(pr.d_best_iter, 0xff, static_cast<size_t>(P) * 4, s->stream));
   pr.P = P;
   const int big = INT_MAX;
   CUDA_TRY(s, cudaMemcpyAsync(pr.d_first, &big, 4, cudaMemcpyHostToDevice, s->stream));
@@ -986,6 +998,7 @@ LaunchArgs plan_args(const tamp_scene* s, const Plan& plan, ProbDesc* d_descs, u
   a.scratch_offset = static_cast<int>(plan.smem - optimize_scratch_bytes(plan.warps));
   a.mv_global = plan.mv_global ? 1 : 0;
   a.feat = plan.feat;
+  a.rec = plan.descs.empty() || plan.descs[0].best_x == nullptr ? 0 : 1;
   return a;
 }
 
@@ -1019,6 +1032,20 @@ tamp_status launch_jobs(tamp_scene* s, std::vector<Job>& jobs, int requested_lan
   return TAMP_OK;
 }
 
+// The launch keeps this problem's best-satisfying record (tamp_query_best).
+void keep_record(ProbDesc& d, Problem& pr) {
+  d.best_x = pr.d_best_x; d.best_cost = pr.d_best_cost; d.best_iter = pr.d_best_iter; d.stage_x = pr.d_stage;
+}
+
+// Whether a launch of these problems keeps the records: always in the stop
+// modes, otherwise if one of them asks for it (tamp_options.keep_best).
+bool wants_record(const std::vector<Problem*>& prs, bool stop_mode) {
+  if (stop_mode) return true;
+  for (const Problem* pr : prs)
+    if (pr->opt.keep_best) return true;
+  return false;
+}
+
 ProbDesc state_desc(Problem& pr, int n_steps) {
   ProbDesc d{};
   d.prob = pr.d_blob;
@@ -1038,9 +1065,11 @@ ProbDesc state_desc(Problem& pr, int n_steps) {
 tamp_status run_state(tamp_scene* s, std::vector<Problem*> prs, int n_steps) {
   std::vector<Job> jobs;
   int lanes = 0;
+  const bool rec = wants_record(prs, false);
   for (Problem* pr : prs) {
     CUDA_TRY(s, cudaMemsetAsync(pr->d_counts, 0, static_cast<size_t>(std::max(pr->NCON, 1)) * 4, s->stream));
     jobs.push_back({pr, state_desc(*pr, n_steps)});
+    if (rec) keep_record(jobs.back().d, *pr);
     lanes = pr->opt.lanes;
   }
   tamp_status st = launch_jobs(s, jobs, lanes);
@@ -1090,6 +1119,7 @@ tamp_status run_state_stopping(tamp_scene* s, const std::vector<Problem*>& prs, 
     hp[n + i] = pr->d_counts;
     ProbDesc d = state_desc(*pr, chunk);
     d.t_dev = ints + 3 + i;
+    keep_record(d, *pr);  // a stop must not lose the satisfying particle it stopped on
     jobs.push_back({pr, d});
     CUDA_TRY(s, cudaMemsetAsync(pr->d_counts, 0, static_cast<size_t>(std::max(pr->NCON, 1)) * 4, s->stream));
   }
@@ -1496,6 +1526,39 @@ tamp_status tamp_query_satisfied(tamp_scene* s, int id, uint8_t* mask, int* n_sa
   return TAMP_OK;
 }
 
+tamp_status tamp_query_best(tamp_scene* s, int id, uint8_t* found, int* n_found, float* particles, float* cost,
+                            int* iter) {
+  Problem* pr = get_problem(s, id);
+  if (!pr) return fail(s, TAMP_ERR_INVALID_ARG, "unknown problem %d", id);
+  if (!pr->has_batch) return fail(s, TAMP_ERR_STATE, "problem %d has no particles", id);
+  DeviceGuard g(s->device);
+  if (!pr->checked) {  // the batch as set has not been checked yet: check it once
+    tamp_status st = run_state(s, {pr}, 0);
+    if (st != TAMP_OK) return st;
+  }
+  std::vector<int> it(pr->P);
+  CUDA_TRY(s, cudaMemcpyAsync(it.data(), pr->d_best_iter, static_cast<size_t>(pr->P) * 4, cudaMemcpyDeviceToHost,
+                              s->stream));
+  if (particles)
+    CUDA_TRY(s, cudaMemcpyAsync(particles, pr->d_best_x, static_cast<size_t>(pr->D) * pr->P * 4,
+                                cudaMemcpyDeviceToHost, s->stream));
+  if (cost)
+    CUDA_TRY(s, cudaMemcpyAsync(cost, pr->d_best_cost, static_cast<size_t>(pr->P) * 4, cudaMemcpyDeviceToHost,
+                                s->stream));
+  tamp_status st = check_device_error(s);
+  if (st != TAMP_OK) return st;
+  int nf = 0;
+  for (int i = 0; i < pr->P; ++i) {
+    const bool f = it[i] >= 0;
+    nf += f ? 1 : 0;
+    if (found) found[i] = f ? 1 : 0;
+    if (cost && !f) cost[i] = INFINITY;
+  }
+  if (iter) std::copy(it.begin(), it.end(), iter);
+  if (n_found) *n_found = nf;
+  return TAMP_OK;
+}
+
 tamp_status tamp_eval(tamp_scene* s, int id, int n, const float* x, float* cost, float* terms, uint8_t* flags,
                       float* grad) {
   Problem* pr = get_problem(s, id);
@@ -1564,6 +1627,7 @@ tamp_status tamp_autotune(tamp_scene* s, const int* ids, int n, int trial_steps,
     d.x_in = d.x_out = sc[i].x; d.m = sc[i].m; d.v = sc[i].v;
     d.out_cost = sc[i].cost; d.out_flags = sc[i].flags; d.out_counts = sc[i].counts;
     d.first_iter = sc[i].first; d.work = sc[i].work;
+    // trial launches run on copies and keep no best-satisfying record
     jobs.push_back({prs[i], d});
   }
   auto restore = [&]() {
@@ -1764,6 +1828,8 @@ extern "C" tamp_status tamp_graph_create(tamp_scene* s, const int* ids, int n, i
     firsts[n + i] = pr->d_counts;
     ncons[i] = std::max(pr->NCON, 1);
   }
+  if (wants_record(g->prs, stop_on_first != 0))
+    for (Job& j : jobs) keep_record(j.d, *j.pr);
   Plan plan;
   tamp_status st = plan_jobs(s, jobs, g->prs[0]->opt.lanes, &plan);
   if (st != TAMP_OK) return bail(st);

@@ -131,7 +131,16 @@ struct ProbDesc {
   float beta1, beta2, eps;
   int load_mv;                        // read m, v from memory (else zeros)
   int pad;
+  // optional best-satisfying record (all four set or all null): per particle the
+  // state with the lowest Eq. 2 cost among the Eq. 3 checks it satisfied
+  float* best_x;                      // [D][stride]
+  float* best_cost;                   // [stride]; kNoBestCost: none yet
+  int* best_iter;                     // [stride]; the check index of best_x, -1: none
+  float* stage_x;                     // 2 x [tiles][D][PT] (2 * D * ceil(P / 32) * 32 floats, 16-byte
+                                      // aligned): x_t of each tile, by iteration parity
 };
+// byte-uniform sentinel of best_cost (so that a memset clears it): 0x7f7f7f7f = 3.39e38
+constexpr unsigned kNoBestCostBits = 0x7f7f7f7fu;
 
 // One launch of the persistent optimisation kernel: CTAs take work items
 // (problem << 20 | tile) from a shared counter until the list is exhausted.
@@ -145,6 +154,7 @@ struct LaunchArgs {
   const int* stop;                    // optional: a non-zero value makes the launch return at once
   int mv_global;                      // 1: Adam moments used in place in global memory (not staged)
   int feat;                           // the optional terms of the launch's problems: 0 or a KernelFeat
+  int rec;                            // 1: every problem's best-satisfying record is kept (ProbDesc best_*)
 };
 // Feature sets of the optimisation kernel's instantiations (0: none of the
 // optional terms): SelfCollision alone; 6-DOF grasps; knots with 4-DOF grasps;

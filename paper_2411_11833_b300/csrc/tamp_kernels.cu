@@ -1280,8 +1280,10 @@ __device__ __noinline__ void eval_self(const uint32_t* __restrict__ sc, const ui
 // iterations (evaluation + adjoint, Eq. 3 check, Adam) and one final check,
 // write it back.  All threads of the CTA call this together.
 // FEAT: the optional terms the kernel is built for (a KernelFeat; 0: none,
-// the configuration code of every skeleton without them).
-template <int L, int FEAT>
+// the configuration code of every skeleton without them).  REC: the launch
+// keeps the problems' best-satisfying records (tamp_query_best); launches
+// without them run none of that code.
+template <int L, int FEAT, bool REC>
 __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, const uint32_t* s_pb, float* tile_mem,
                          const WarpScratch& ws, bool mv_global) {
   constexpr int PT = 32 / L;
@@ -1315,6 +1317,9 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
   const int pl = lane / L, sub = lane % L;
   const int tile0 = tile * PT;
   const int t0 = d.t_dev ? *d.t_dev : d.t0;
+  // best-satisfying record: the particles (bits) whose x_t beat their record at
+  // the last check; warp 0 copies their staged x_t at the top of the next iteration
+  __shared__ unsigned s_snap;
 
   for (int i = tid; i < D * PT; i += nthr) {
     const int c = i / PT, p = i % PT, gp = tile0 + p;
@@ -1370,6 +1375,27 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
       b2t *= static_cast<double>(d.beta2);
       s_ib[0] = static_cast<float>(1.0 / (1.0 - b1t));
       s_ib[1] = static_cast<float>(1.0 / (1.0 - b2t));
+    }
+    if constexpr (REC) {
+      // x_t is staged, as the tile's contiguous [D][PT] block, in the block of
+      // this iteration's parity while the pass only reads it; warp 0 first copies
+      // the last check's new records out of the other parity's block (staged at
+      // the top of the last iteration, so complete and visible here).  The two
+      // blocks of the problem are [ceil(P / 32) * 32 / PT tiles][D][PT] each.
+      const long half = static_cast<long>(D) * ((d.P + 31) & ~31), toff = static_cast<long>(tile) * D * PT;
+      if (w == 0 && it > 0) {
+        const unsigned snap = s_snap;
+        if (snap) {
+          const float* prev = d.stage_x + ((it - 1) & 1) * half + toff;
+          for (int i = lane; i < D * PT; i += 32) {
+            const int c = i / PT, p = i - c * PT;
+            if ((snap >> p) & 1u) d.best_x[static_cast<long>(c) * d.stride + tile0 + p] = prev[i];
+          }
+        }
+      }
+      const float4* src = reinterpret_cast<const float4*>(sx);
+      float4* dst = reinterpret_cast<float4*>(d.stage_x + (it & 1) * half + toff);
+      for (int j = tid; j < D * PT / 4; j += nthr) dst[j] = src[j];
     }
     for (int i = tid; i < NT * PT; i += nthr) st[i] = 0.f;  // collision terms are sums over pieces
     for (int i = tid; i < NSLOT * PT; i += nthr) {
@@ -1429,6 +1455,33 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
         if (tile0 + lane >= d.P) sat = 0;
       }
       if (__any_sync(0xffffffffu, sat) && lane == 0 && d.first_iter) atomicMin(d.first_iter, t0 + it);
+      if constexpr (REC) {
+        // a satisfying particle whose Eq. 2 cost (summed as the query's cost) is
+        // below its record takes the check's index and cost; its state is copied
+        // straight from the tile at the launch's last check, otherwise from the
+        // staging block at the top of the next iteration
+        bool better = false;
+        if (sat) {
+          float c = 0.f;
+          for (int tt = 0; tt < NT; ++tt) c = fmaf(__uint_as_float(terms[tt * TERM_W + 1]), st[tt * PT + lane], c);
+          const int gp = tile0 + lane;
+          if (c < d.best_cost[gp]) {
+            d.best_cost[gp] = c;
+            d.best_iter[gp] = t0 + it;
+            better = true;
+          }
+        }
+        const unsigned snap = __ballot_sync(0xffffffffu, better);
+        if (it == d.n_steps) {
+          if (snap)
+            for (int i = lane; i < D * PT; i += 32) {
+              const int c = i / PT, p = i - c * PT;
+              if ((snap >> p) & 1u) d.best_x[static_cast<long>(c) * d.stride + tile0 + p] = sx[i];
+            }
+        } else if (lane == 0) {
+          s_snap = snap;
+        }
+      }
     }
     if (it == d.n_steps) break;
     // Adam (Kingma & Ba) on the Eq. 4 gradient; the gradient buffer is cleared for the next pass
@@ -1518,7 +1571,7 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
 // skeletons first, as the host orders them -- staging a problem's tables
 // whenever it moves to a new problem.  Many skeletons of uneven length and
 // particle count thus share one launch and balance across the SMs.
-template <int L, int FEAT>
+template <int L, int FEAT, bool REC>
 __global__ void __launch_bounds__(512, 1) optimize_kernel(LaunchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
@@ -1586,7 +1639,7 @@ __global__ void __launch_bounds__(512, 1) optimize_kernel(LaunchArgs a) {
       __syncthreads();
       if (abort_flag) return;
     }
-    run_tile<L, FEAT>(d, tile, s_sc, s_pb, reinterpret_cast<float*>(s_pb + pw), ws, a.mv_global != 0);
+    run_tile<L, FEAT, REC>(d, tile, s_sc, s_pb, reinterpret_cast<float*>(s_pb + pw), ws, a.mv_global != 0);
     __syncthreads();  // everyone has read s_item and the tables before they change
   }
 }
@@ -1987,15 +2040,15 @@ cudaError_t launch_chunk_control(int* t_dev, const int* const* first_iters, int*
 
 // ------------------------------------------------------------------ launchers
 // largest dynamic shared-memory size enabled so far for optimize_kernel<1,2,4,8>
-// per feature set (0 .. N_FEAT - 1)
-static size_t g_smem_enabled[N_FEAT][4] = {};
+// per feature set (0 .. N_FEAT - 1) and record flag
+static size_t g_smem_enabled[2][N_FEAT][4] = {};
 static int lane_slot(int L) { return L == 1 ? 0 : (L == 2 ? 1 : (L == 4 ? 2 : 3)); }
 
-template <int L, int FEAT>
+template <int L, int FEAT, bool REC>
 static cudaError_t set_smem(size_t smem) {
-  size_t& enabled = g_smem_enabled[FEAT][lane_slot(L)];
+  size_t& enabled = g_smem_enabled[REC ? 1 : 0][FEAT][lane_slot(L)];
   if (smem <= 48 * 1024 || smem <= enabled) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(optimize_kernel<L, FEAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(optimize_kernel<L, FEAT, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e == cudaSuccess) enabled = smem;
   return e;
@@ -2003,10 +2056,13 @@ static cudaError_t set_smem(size_t smem) {
 
 template <int L, int FEAT>
 static cudaError_t launch_feat(const LaunchArgs& a, int warps, int grid, size_t smem, cudaStream_t st) {
-  cudaError_t e = set_smem<L, FEAT>(smem);
+  cudaError_t e = a.rec ? set_smem<L, FEAT, true>(smem) : set_smem<L, FEAT, false>(smem);
   if (e != cudaSuccess) return e;
   if (grid <= 0) return cudaSuccess;
-  optimize_kernel<L, FEAT><<<grid, warps * 32, smem, st>>>(a);
+  if (a.rec)
+    optimize_kernel<L, FEAT, true><<<grid, warps * 32, smem, st>>>(a);
+  else
+    optimize_kernel<L, FEAT, false><<<grid, warps * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -2026,21 +2082,27 @@ int optimize_blocks_per_sm(int L, int warps, size_t smem) {
   int n = 0;
   cudaError_t e = cudaSuccess;
   switch (L) {
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<1, 0>, warps * 32, smem); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<2, 0>, warps * 32, smem); break;
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<4, 0>, warps * 32, smem); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<8, 0>, warps * 32, smem); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<1, 0, false>, warps * 32, smem); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<2, 0, false>, warps * 32, smem); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<4, 0, false>, warps * 32, smem); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, optimize_kernel<8, 0, false>, warps * 32, smem); break;
   }
   return e == cudaSuccess ? n : 1;
 }
 
+template <int L, bool REC>
+static cudaError_t set_smem_feats(size_t smem) {
+  cudaError_t e = set_smem<L, 0, REC>(smem);
+  if (e == cudaSuccess) e = set_smem<L, FEAT_SELF, REC>(smem);
+  if (e == cudaSuccess) e = set_smem<L, FEAT_EXT, REC>(smem);
+  if (e == cudaSuccess) e = set_smem<L, FEAT_KNOT, REC>(smem);
+  if (e == cudaSuccess) e = set_smem<L, FEAT_KNOT6, REC>(smem);
+  return e;
+}
 template <int L>
 static cudaError_t set_smem_all(size_t smem) {
-  cudaError_t e = set_smem<L, 0>(smem);
-  if (e == cudaSuccess) e = set_smem<L, FEAT_SELF>(smem);
-  if (e == cudaSuccess) e = set_smem<L, FEAT_EXT>(smem);
-  if (e == cudaSuccess) e = set_smem<L, FEAT_KNOT>(smem);
-  if (e == cudaSuccess) e = set_smem<L, FEAT_KNOT6>(smem);
+  cudaError_t e = set_smem_feats<L, false>(smem);
+  if (e == cudaSuccess) e = set_smem_feats<L, true>(smem);
   return e;
 }
 

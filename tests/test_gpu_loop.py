@@ -1,7 +1,8 @@
 """The optimisation loop through the C ABI against the FP64 oracle: CUDA-graph
 replay, the device-side stop on the first satisfying particle (graph and
 tamp_optimize_steps), several problems in one persistent launch, odd cuboid
-counts in the paired broad phase, and a caller-supplied allocator.
+counts in the paired broad phase, a caller-supplied allocator, and the
+best-satisfying record (tamp_query_best).
 
 Multi-step trajectories follow the rule of tests/parity.py (check_trajectory).
 """
@@ -14,8 +15,8 @@ import torch
 import scenegen as sg
 from oracle import philox
 from oracle.problem import Problem
-from tests.parity import (KINK_MARGIN, TRAJ_MARGIN, check_adam_step, check_trajectory, cost_ok, near_threshold,
-                          oracle_run)
+from tests.parity import (FLAG_BAND, KINK_MARGIN, TRAJ_MARGIN, check_adam_step, check_trajectory, cost_ok,
+                          cost_sum_bound, near_threshold, oracle_run)
 
 pytestmark = pytest.mark.gpu
 
@@ -100,6 +101,160 @@ def test_optimize_steps_stops_on_the_first_satisfying_particle(pkg):
     out, margin = oracle_run(pr, X, 10)
     print(check_trajectory(pr, xs.T, q["cost"], out, margin, min_smooth=0.0))
     _counts_match(pr, xs.T, q["counts"])
+
+
+def _near(pr, T: np.ndarray) -> np.ndarray:
+    """Particles with a constraint term within 1e-5 of its tolerance, a term that
+    is exactly 0 left out: a 0 tolerance (joint limits) is met exactly inside
+    the bounds in either precision, so such a term cannot fall either side."""
+    tol = pr.tolerances().numpy()
+    cm = pr.constraint_mask().numpy()
+    t = T[:, cm]
+    return ((np.abs(t - tol[cm]) <= FLAG_BAND) & (t != 0.0)).any(axis=1)
+
+
+def _check_best_valid(pr, best):
+    """Every recorded state satisfies Eq. 3 in the oracle (a particle within 1e-5
+    of a tolerance may fall either side) at the cost the record gives."""
+    f = best["found"]
+    if not f.any():
+        return 0
+    xb = best["particles"].T[f].astype(np.float64)
+    T = pr.term_values(torch.tensor(xb))
+    ok = pr.satisfied(T).numpy() | _near(pr, T.numpy())
+    assert ok.all(), f"{int((~ok).sum())} recorded states do not satisfy Eq. 3"
+    cost = (T * pr.weights()).sum(1).numpy()
+    bad = np.abs(best["cost"][f].astype(np.float64) - cost) > cost_sum_bound(pr, T.numpy())
+    if bad.any():
+        idx = np.nonzero(f)[0][bad]
+        marg = pr.kink_margin(torch.tensor(xb[bad])).numpy()
+        raise AssertionError(f"record costs differ from the oracle's at the recorded state: particles {idx[:6]}, "
+                             f"gpu {best['cost'][idx[:6]]}, oracle {cost[bad][:6]}, checks {best['iter'][idx[:6]]}, "
+                             f"kink margins {marg[:6]}, terms {T.numpy()[bad][:2]}")
+    assert np.isinf(best["cost"][~f]).all() and (best["iter"][~f] == -1).all()
+    return int(f.sum())
+
+
+def test_best_record_is_the_lowest_cost_satisfying_check(pkg):
+    """tamp_query_best against its definition on the run's own checks, each
+    check pinned to the oracle.  200 particles (7 tiles, a ragged tail of 8)
+    around the SCARA witness, whose satisfying checks come and go as Adam moves
+    them, run 30 single-iteration calls (the record runs across calls); after
+    each call the state x_k, the Eq. 3 mask and Eq. 2 costs of its last check
+    are read back.  Every check must agree with the oracle evaluated at the same
+    FP32 state (flags, except within 1e-5 of a tolerance; costs within the
+    bound the per-term rule implies), and the record must be the state of the
+    lowest-cost satisfying check (bit for bit), with its cost and index.
+
+    Near satisfaction the FP32 and FP64 trajectories themselves part ways: a
+    Kin error norm passing near zero turns a rounding difference d into a
+    gradient direction change d/|e|, which the next step (about the learning
+    rate) multiplies by lr/|e| (60 at |e| = 1.6e-4; measured: smooth-margin
+    particles 1.4e-2 apart after 30 steps), so the record is checked on the
+    run's own iterates rather than against the oracle's trajectory."""
+    from tests.test_oracle_pins import _scara_witness_scene
+    sc, acts, x = _scara_witness_scene()
+    pr = Problem(sc, acts)
+    P, n = 200, 30
+    rng = np.random.default_rng(3)
+    X = np.repeat(x.numpy(), P, axis=0)
+    X[1:] += rng.normal(0.0, 0.002, (P - 1, X.shape[1]))
+    X[-5:, 4:11] += 0.3                                # far off: never satisfy
+    X = X.astype(np.float32).astype(np.float64)
+    scene = pkg.Scene(sc)
+    pid = scene.set_skeleton(acts, pkg.default_options(keep_best=1))
+    scene.set_particles(pid, X.T.astype(np.float32))
+    xs, masks, costs = [], [], []
+    for k in range(n + 1):
+        if k:
+            scene.optimize(pid, 1)
+        q = scene.query(pid, P)                        # k = 0: the check of the batch as set
+        xs.append(scene.get_particles(pid)[0].T.copy())
+        masks.append(q["mask"])
+        costs.append(q["cost"].astype(np.float64))
+    best = scene.query_best(pid, P)
+    scene.close()
+    S, C = np.array(masks).T, np.array(costs).T       # [P, n + 1]
+    near = np.zeros_like(S)
+    for k in range(n + 1):
+        T = pr.term_values(torch.tensor(xs[k].astype(np.float64)))
+        near[:, k] = _near(pr, T.numpy())
+        ok = (pr.satisfied(T).numpy() == S[:, k]) | near[:, k]
+        assert ok.all(), f"check {k}: Eq. 3 flags differ for particles {np.nonzero(~ok)[0][:8]}"
+        c_ora = (T * pr.weights()).sum(1).numpy()
+        assert (np.abs(C[:, k] - c_ora) <= cost_sum_bound(pr, T.numpy())).all(), f"check {k}: costs"
+    assert _check_best_valid(pr, best) == best["n_found"]
+    # a particle re-checked at the start of a call (same state as the last check
+    # of the call before) may take the recheck's cost, equal up to the order of
+    # its summed collision contributions; particles with a flag within 1e-5 of a
+    # tolerance at some check are only checked for validity (above)
+    strict = ~near.any(axis=1)
+    assert np.array_equal(S.any(axis=1)[strict], best["found"][strict])
+    n_sat_checks = 0
+    for p in np.nonzero(strict & best["found"])[0]:
+        ks = np.nonzero(S[p])[0]
+        kg = int(best["iter"][p])
+        assert kg in set(ks.tolist()), (p, kg, ks)
+        tie = 1e-5 * max(abs(C[p, ks].min()), 1e-2)
+        assert C[p, kg] <= C[p, ks].min() + tie, (p, kg, C[p, ks])
+        assert abs(np.float64(best["cost"][p]) - C[p, kg]) <= tie
+        assert np.array_equal(best["particles"][:, p], xs[kg][p].astype(np.float32)), p
+        n_sat_checks += len(ks)
+    print(dict(found=best["n_found"], strict=int(strict.sum()), satisfying_checks=n_sat_checks))
+    assert strict.sum() >= P // 2 and best["n_found"] >= 100
+
+
+def test_best_record_is_kept_only_where_asked(pkg):
+    """Plain optimisation launches skip the record unless the problem's options
+    ask for it (keep_best); the stop mode keeps it.  The same witness batch,
+    which satisfies at its first check, in three problems of one scene."""
+    from tests.test_oracle_pins import _scara_witness_scene
+    sc, acts, x = _scara_witness_scene()
+    X = np.repeat(x.numpy(), 8, axis=0).T.astype(np.float32)
+    scene = pkg.Scene(sc)
+    plain = scene.set_skeleton(acts)
+    kept = scene.set_skeleton(acts, pkg.default_options(keep_best=1))
+    stop = scene.set_skeleton(acts)
+    for pid in (plain, kept, stop):
+        scene.set_particles(pid, X)
+    scene.optimize(plain, 5)
+    scene.optimize(kept, 5)
+    scene.optimize(stop, 5, stop_every=5)
+    found = [scene.query_best(pid, 8, want_particles=False)["n_found"] for pid in (plain, kept, stop)]
+    firsts = [scene.query(pid, 8)["first_iter"] for pid in (plain, kept, stop)]
+    scene.close()
+    assert firsts == [0, 0, 0]
+    assert found[0] == 0 and found[1] == 8 and found[2] == 8
+
+
+def test_stop_on_first_satisfying_keeps_the_satisfying_state(pkg):
+    """After tamp_optimize_steps stops on the first satisfying particle, the
+    particle that satisfied is in the record, even where the updates after its
+    check moved it out of the feasible set (the witness does so after one
+    update: Kin's gradient has unit size at zero error).  The record's earliest
+    check is the first satisfying iteration, and each recorded state satisfies
+    Eq. 3 in the oracle."""
+    from tests.test_oracle_pins import _scara_witness_scene
+    sc, acts, x = _scara_witness_scene()
+    pr = Problem(sc, acts)
+    X = np.repeat(x.numpy(), 40, axis=0)
+    X[1:] += np.random.default_rng(4).normal(0.0, 0.002, (39, X.shape[1]))
+    X = X.astype(np.float32).astype(np.float64)
+    scene = pkg.Scene(sc)
+    pid = scene.set_skeleton(acts)
+    scene.set_particles(pid, X.T.astype(np.float32))
+    scene.optimize(pid, 100, stop_every=10)
+    t = scene.get_particles(pid)[3]
+    q = scene.query(pid, 40)
+    best = scene.query_best(pid, 40)
+    scene.close()
+    assert t == 10 and q["first_iter"] == 0
+    assert best["n_found"] >= 1 and best["found"][0] and best["iter"][0] == 0
+    assert best["iter"][best["found"]].min() == q["first_iter"]
+    assert (best["iter"][best["found"]] <= t).all()
+    # the witness, recorded at x_0, is the state that was set
+    assert np.array_equal(best["particles"][:, 0], X[0].astype(np.float32))
+    _check_best_valid(pr, best)
 
 
 def test_optimize_steps_stop_mode_without_a_solution_runs_every_chunk(pkg):

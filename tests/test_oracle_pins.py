@@ -450,6 +450,66 @@ def test_optimize_reports_satisfied_at_iteration_zero_for_witness():
     assert out["first_iter"] == 0
 
 
+def _replayed_checks(pr, X, n):
+    """The optimiser's checks k = 0..n replayed one update at a time: states
+    x_k, Eq. 3 flags and Eq. 2 costs."""
+    xk, m, v = X.clone(), torch.zeros_like(X), torch.zeros_like(X)
+    xs, S, C = [], [], []
+    for k in range(n + 1):
+        t = pr.term_values(xk)
+        xs.append(xk.clone())
+        S.append(pr.satisfied(t).numpy())
+        C.append((t * pr.weights()).sum(1).numpy())
+        if k < n:
+            o = pr.optimize(xk, 1, m, v, t0=k)
+            xk, m, v = o["x"], o["m"], o["v"]
+    return xs, np.array(S).T, np.array(C).T
+
+
+def test_best_record_is_the_lowest_cost_satisfying_check():
+    """The best satisfying record of OptimizeParticles against its definition
+    over a trajectory replayed update by update: the lowest-cost state among
+    the checks where the particle satisfies Eq. 3 (the earliest of equal ones),
+    none where it never does.  The batch (witness and small perturbations of
+    it, one particle far off) has particles whose lowest check is neither their
+    first nor their last satisfying one, and one that satisfies only at the
+    check after the last update, so recording the first, the latest or
+    skipping the final check each fails."""
+    sc, acts, x = _scara_witness_scene()
+    pr = Problem(sc, acts)
+    rng = np.random.default_rng(0)
+    X = x.repeat(25, 1).clone()
+    X[1:24] += torch.tensor(rng.normal(0.0, 0.002, (23, X.shape[1])))
+    X[24, 4:11] += 0.3                                # never satisfies
+    n = 30
+    out = pr.optimize(X, n)
+    xs, S, C = _replayed_checks(pr, X, n)
+    not_first = not_latest = only_final = never = 0
+    for p in range(X.shape[0]):
+        ks = np.nonzero(S[p])[0]
+        if len(ks) == 0:
+            never += 1
+            assert int(out["best_iter"][p]) == -1 and math.isinf(float(out["best_cost"][p]))
+            continue
+        k = int(ks[np.argmin(C[p, ks])])
+        not_first += k != ks[0]
+        not_latest += k != ks[-1]
+        only_final += len(ks) == 1 and ks[0] == n
+        assert int(out["best_iter"][p]) == k, p
+        assert float(out["best_cost"][p]) == C[p, k]
+        assert torch.equal(out["best_x"][p], xs[k][p])
+    assert not_first >= 3 and not_latest >= 3 and only_final >= 1 and never >= 1
+
+
+def test_best_record_counts_checks_from_the_step_count():
+    """Check indices of the record are the Adam step count at the check (t0 +
+    k), as the first satisfying iteration of a continued run."""
+    sc, acts, x = _scara_witness_scene()
+    pr = Problem(sc, acts)
+    out = pr.optimize(x, 2, t0=7)
+    assert int(out["best_iter"][0]) == 7
+
+
 def test_optimize_lowers_mean_cost():
     sc, acts = sg.plain_problem()
     pr = Problem(sc, acts)
