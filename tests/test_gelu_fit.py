@@ -1,47 +1,69 @@
-"""The GELU of the network kernels evaluates erf by a polynomial fit (the
-coefficients kErfFit in tamp_mlp.cu).  Evaluated here the way the kernel
-does -- FP32 clamp, FP32 Horner in t = 2 x^2 / 3.2^2 - 1 -- it must stay
-within 1e-5 of the double-precision erf everywhere, and the GELU built on it
-within 2.5e-5 (absolute) of the exact GELU, far below the BF16 rounding of
-the activations (2^-9 relative)."""
+"""The GELU of the network kernels evaluates the normal CDF Phi by a
+polynomial fit (the coefficients kPhiFit in tamp_mlp.cu): Phi(z) = 1/2 + z_c
+p(z_c^2), z_c = z clamped to +-Zc, Zc = 2.9 sqrt 2.  Evaluated here the way
+the kernel does -- FP32 clamp, FP32 Horner in s = z_c^2 -- it must stay within
+2e-5 of the double-precision Phi everywhere, the GELU built on it (z Phi(z))
+within 1e-5 of the exact GELU on |z| <= 2 (where most pre-activations lie),
+4.5e-5 on |z| <= 4 and 8e-5 on |z| <= 12, and its derivative (Phi(z) + z
+phi(z)) within 2e-5.  What sets the bar is the BF16
+rounding (2^-9 relative: 1e-3 at an activation of 0.5) of the activations the
+kernels store: the fit's errors stay an order below it."""
 import os
-import re
 
 import numpy as np
 from scipy.special import erf
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2411_11833_b300", "csrc",
                    "tamp_mlp.cu")
+ZC = np.float32(4.101219)
 
 
 def _coefficients():
     body = open(SRC).read()
-    body = body[body.index("kErfFit[11] = {"):]
+    body = body[body.index("kPhiFit[9] = {"):]
     body = body[body.index("{") + 1:body.index("}")]
     return [np.float32(v.strip().rstrip("f")) for v in body.split(",") if v.strip()]   # highest degree first
 
 
-def _erf_fit(x):
+def _phi_fit(z):
     c = _coefficients()
-    x = np.asarray(x, dtype=np.float32)
-    xc = np.minimum(np.maximum(x, np.float32(-3.2)), np.float32(3.2))
-    t = (xc * xc * np.float32(2.0 / (3.2 * 3.2)) - np.float32(1.0)).astype(np.float32)
+    z = np.asarray(z, dtype=np.float32)
+    zc = np.minimum(np.maximum(z, -ZC), ZC)
+    s = (zc * zc).astype(np.float32)
     p = c[0]
     for ck in c[1:]:
-        p = (p * t + ck).astype(np.float32)
-    return (xc * p).astype(np.float32)
+        p = (p * s + ck).astype(np.float32)
+    return (zc * p + np.float32(0.5)).astype(np.float32)
 
 
-def test_erf_fit_against_double_precision_erf():
-    assert len(_coefficients()) == 11
-    x = np.linspace(-8.0, 8.0, 400001).astype(np.float32)
-    assert np.abs(_erf_fit(x).astype(np.float64) - erf(x.astype(np.float64))).max() <= 1e-5
+def _phi(zd):
+    return 0.5 * (1.0 + erf(zd / np.sqrt(2.0)))
+
+
+def test_the_kernel_clamp():
+    assert "kPhiClamp = 4.101219f;" in open(SRC).read()
+    assert abs(float(ZC) - 2.9 * np.sqrt(2.0)) < 1e-6
+
+
+def test_phi_fit_against_double_precision_phi():
+    assert len(_coefficients()) == 9
+    z = np.linspace(-12.0, 12.0, 600001).astype(np.float32)
+    assert np.abs(_phi_fit(z).astype(np.float64) - _phi(z.astype(np.float64))).max() <= 2e-5
 
 
 def test_gelu_on_the_fit_against_exact_gelu():
     z = np.linspace(-12.0, 12.0, 600001).astype(np.float32)
-    h = np.float32(0.5) * z
-    g = h + h * _erf_fit(z * np.float32(0.70710678118654752))
+    g = (z * _phi_fit(z)).astype(np.float64)
     zd = z.astype(np.float64)
-    exact = 0.5 * zd * (1.0 + erf(zd / np.sqrt(2.0)))
-    assert np.abs(g.astype(np.float64) - exact).max() <= 2.5e-5
+    err = np.abs(g - zd * _phi(zd))
+    assert err[np.abs(zd) <= 2.0].max() <= 1e-5
+    assert err[np.abs(zd) <= 4.0].max() <= 4.5e-5
+    assert err.max() <= 8e-5
+
+
+def test_gelu_derivative_on_the_fit():
+    z = np.linspace(-12.0, 12.0, 600001).astype(np.float32)
+    zd = z.astype(np.float64)
+    pdf = np.exp(-0.5 * zd * zd) / np.sqrt(2.0 * np.pi)
+    d = _phi_fit(z).astype(np.float64) + zd * pdf
+    assert np.abs(d - (_phi(zd) + zd * pdf)).max() <= 2e-5
