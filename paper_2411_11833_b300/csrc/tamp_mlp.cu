@@ -141,6 +141,14 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(u[i]);
 }
 
+// the same load without the wait: several may be in flight before one tcgen05.wait::ld
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&u)[32]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+               : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]), "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]), "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
+               : "r"(taddr)
+               : "memory");
+}
+
 // ------------------------------------------------------------------ tile GEMM
 // byte offset of element (r, k) of an R-row operand in the staged layout
 __host__ __device__ __forceinline__ uint32_t blk_off(int r, int k, int R) {
@@ -378,6 +386,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
 // copies, warp 17 the MMAs.  Every wait is bounded; a wait that gives up sets
 // the error word and every role stops at its next wait.
 constexpr int PP_EPI_WARPS = 16;
+static_assert(H / 4 == 64, "an epilogue warp's column group is two 32-column accumulator loads");
 constexpr int PP_THREADS = (PP_EPI_WARPS + 2) * 32;
 constexpr int PP_KCHUNK = 64;                               // K per weight chunk (4 MMAs of K = 16)
 constexpr size_t PP_STAGE = 256 * PP_KCHUNK * 2;            // largest chunk: N = 256
@@ -541,14 +550,21 @@ __global__ void __launch_bounds__(PP_THREADS, 1) mlp_forward_pp_kernel(PpArgs a)
           const uint32_t acc = tmem + static_cast<uint32_t>(tt * 256);
           const int r = (2 * pair + tt) * ROWS + row;
           if (l < 3) {
-            for (int c0 = grp * (H / 4); c0 < (grp + 1) * (H / 4); c0 += 32) {
-              float v[32];
-              tmem_ld32(lane_addr(acc, c0), v);
+            // the warp's 64 columns: both accumulator loads in flight before one wait
+            uint32_t u0[32], u1[32];
+            const int cb = grp * (H / 4);
+            tmem_ld32_nowait(lane_addr(acc, cb), u0);
+            tmem_ld32_nowait(lane_addr(acc, cb + 32), u1);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+              const int c0 = cb + 32 * h2;
               const float* bias = s_bias + l * H + c0;
               uint32_t hp[16];
 #pragma unroll
               for (int e = 0; e < 32; e += 2) {
-                const float2 g = gelu2(__fadd2_rn(make_float2(v[e], v[e + 1]), make_float2(bias[e], bias[e + 1])));
+                const float vx = __uint_as_float(h2 ? u1[e] : u0[e]), vy = __uint_as_float(h2 ? u1[e + 1] : u0[e + 1]);
+                const float2 g = gelu2(__fadd2_rn(make_float2(vx, vy), make_float2(bias[e], bias[e + 1])));
                 hp[e / 2] = pack_bf16x2(g.x, g.y);
               }
 #pragma unroll
