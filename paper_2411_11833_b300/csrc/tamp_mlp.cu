@@ -210,28 +210,35 @@ __device__ __forceinline__ uint32_t lane_addr(uint32_t tmem, int col) {
 // smooth even function -- is a degree-8 polynomial, fitted to Phi by least
 // squares in the Chebyshev basis of t = z^2 / Zc^2 - 1 on |z| <= Zc = 2.9
 // sqrt 2 (4.1012; 1 - Phi(Zc) = 2.1e-5), rewritten in powers of s = z^2 (its
-// terms stay below 10 in magnitude on the clamped range, so FP32 Horner keeps
-// the fit's error) and evaluated by Horner's rule in s; z is clamped to +-Zc.
-// Measured in FP32 against the double-precision Phi: |error| <= 1.8e-5; GELU's
-// absolute error <= 8e-6 on |z| <= 2, 4.2e-5 on |z| <= 4, 7.2e-5 on |z| <= 12,
-// its derivative's <= 1.8e-5 -- against a BF16 rounding of 2^-9 relative (1e-3
-// at an activation of 0.5) in the activations the kernels store.  With z as
-// the variable the 1 / sqrt 2 of erf(z / sqrt 2) and GELU's 1/2 fold into the
-// coefficients: a pair of values takes 4 clamps and 11 paired instructions.
+// terms stay below 10 in magnitude on |z| <= Zc, so FP32 Horner keeps the
+// fit's error) and evaluated by Horner's rule in s.  Beyond Zc the polynomial
+// keeps growing (1/2 + z p(z^2) passes 1 at z = 4.15 and never comes back; it
+// is odd in z), so the last step, 1/2 + z p, saturates to [0, 1] instead of
+// clamping z: Phi = 1 or 0 there, also where p overflows to infinity.
+// Measured in FP32 against the double-precision Phi: |error| <= 2.1e-5; GELU's
+// absolute error <= 8e-6 on |z| <= 2, 4.2e-5 on |z| <= 4, 9e-5 everywhere, its
+// derivative's <= 2.1e-5 -- against a BF16 rounding of 2^-9 relative (1e-3 at
+// an activation of 0.5) in the activations the kernels store.  With z as the
+// variable the 1 / sqrt 2 of erf(z / sqrt 2) and GELU's 1/2 fold into the
+// coefficients: a pair of values takes 9 paired instructions and 2 saturating
+// FMAs.
 // coefficients of s^8 .. s^0
 __device__ constexpr float kPhiFit[9] = {
     7.3491581e-11f, -6.5462733e-09f, 2.5961910e-07f, -6.1287783e-06f, 9.7603224e-05f,
     -1.1281440e-03f, 9.8639885e-03f, -6.6396549e-02f, 3.9891848e-01f};
-constexpr float kPhiClamp = 4.101219f;   // Zc
-// two at a time on the paired FP32 instructions (FFMA2 / FMUL2): the same
-// roundings as one at a time, half the instructions
+__device__ __forceinline__ float fma_sat(float a, float b, float c) {  // a b + c, saturated to [0, 1]
+  float d;
+  asm("fma.rn.ftz.sat.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+// two at a time: the polynomial on the paired FP32 instructions (FFMA2 / FMUL2;
+// the same roundings as one at a time, half the instructions)
 __device__ __forceinline__ float2 phi_fit2(float2 z) {
-  const float2 zc = make_float2(fminf(fmaxf(z.x, -kPhiClamp), kPhiClamp), fminf(fmaxf(z.y, -kPhiClamp), kPhiClamp));
-  const float2 s = __fmul2_rn(zc, zc);
+  const float2 s = __fmul2_rn(z, z);
   float2 p = make_float2(kPhiFit[0], kPhiFit[0]);
 #pragma unroll
   for (int k = 1; k < 9; ++k) p = __ffma2_rn(p, s, make_float2(kPhiFit[k], kPhiFit[k]));
-  return __ffma2_rn(zc, p, make_float2(0.5f, 0.5f));
+  return make_float2(fma_sat(z.x, p.x, 0.5f), fma_sat(z.y, p.y, 0.5f));
 }
 // GELU(z) = z Phi(z) and its derivative Phi(z) + z phi(z), phi(z) = exp(-z^2 / 2) / sqrt(2 pi), for two values
 __device__ __forceinline__ float2 gelu2(float2 z) { return __fmul2_rn(z, phi_fit2(z)); }
@@ -381,16 +388,24 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
 // Each tile keeps its activations in its own 64 KB operand buffer and its
 // accumulator in its own 256 tensor-memory columns.  The weights stream in
 // K-chunks of 64 (at most 32 KB, one bulk copy each) through a 2-stage ring,
-// once per (tile, layer), in the order the MMAs use them.  Roles: warps 0-15
-// epilogue (warp w: TMEM lane quarter w % 4, column group w / 4), warp 16 the
-// copies, warp 17 the MMAs.  Every wait is bounded; a wait that gives up sets
-// the error word and every role stops at its next wait.
+// once per (tile, layer), in the order the MMAs use them.  A tile's inputs,
+// the first layer's operand, sit in a 12 KB buffer of their own, which a
+// staging warp fills with the tile's inputs of the next pair once the first
+// layer's MMA of this pair has read it: the global loads' latency stays off
+// the path between the output layer and the next pair's first layer.  Roles:
+// warps 0-15 epilogue (warp w: TMEM lane quarter w % 4, column group w / 4),
+// warp 16 the copies, warp 17 the MMAs, warp 18 the input staging (the first
+// pair's inputs are staged by the epilogue warps at the start).  Every wait is
+// bounded; a wait that gives up sets the error word and every role stops at
+// its next wait.
 constexpr int PP_EPI_WARPS = 16;
 static_assert(H / 4 == 64, "an epilogue warp's column group is two 32-column accumulator loads");
-constexpr int PP_THREADS = (PP_EPI_WARPS + 2) * 32;
+constexpr int PP_THREADS = (PP_EPI_WARPS + 3) * 32;
 constexpr int PP_KCHUNK = 64;                               // K per weight chunk (4 MMAs of K = 16)
 constexpr size_t PP_STAGE = 256 * PP_KCHUNK * 2;            // largest chunk: N = 256
-constexpr size_t PP_SMEM = 2 * SMEM_A + 2 * PP_STAGE;       // two activation tiles + the weight ring
+constexpr size_t PP_SMEM_IN = ROWS * IN * 2;                // a tile's inputs as the first layer's operand
+// two activation tiles, the weight ring, two input tiles
+constexpr size_t PP_SMEM = 2 * SMEM_A + 2 * PP_STAGE + 2 * PP_SMEM_IN;
 // chunks of layer l: 48 inputs -> one chunk of 3 K-blocks, 256 -> four of 4
 __host__ __device__ constexpr int pp_chunks(int l) { return (kdim(l) + PP_KCHUNK - 1) / PP_KCHUNK; }
 __host__ __device__ constexpr int pp_kblocks(int l, int c) {
@@ -419,23 +434,39 @@ struct PpArgs {
   int* err;
 };
 
-// Stage the inputs of rows row0 .. row0 + 127 as a BF16 operand (zeros past B).
-__device__ __forceinline__ void pp_stage_input(unsigned char* A, const float* x, int B, int row0, int t) {
-  for (int c = t; c < ROWS * (IN / 8); c += PP_EPI_WARPS * 32) {
-    const int rr = c / (IN / 8), kk = (c % (IN / 8)) * 8;
-    float v[8];
-    const bool in = row0 + rr < B;
+// Stage the inputs of rows row0 .. row0 + 127 as a BF16 operand (zeros past B):
+// 768 groups of 8, group c at row c / 6, columns 8 (c % 6) .. + 7, taken by
+// `n` threads (thread t: groups t, t + n, ...) `G` groups at a time, so that
+// 8 G loads are in flight per thread.
+constexpr int PP_IN_GROUPS = ROWS * (IN / 8);
+template <int G>
+__device__ __forceinline__ void pp_stage_input(unsigned char* S, const float* x, int B, int row0, int t, int n) {
+  for (int c0 = t; c0 < PP_IN_GROUPS; c0 += G * n) {
+    float v[G][8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = in ? x[static_cast<long>(row0 + rr) * IN + kk + e] : 0.f;
-    *reinterpret_cast<uint4*>(A + blk_off(rr, kk, ROWS)) =
-        make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+    for (int g = 0; g < G; ++g) {
+      const int c = c0 + g * n, rr = c / (IN / 8), kk = (c % (IN / 8)) * 8;
+      const bool in = c < PP_IN_GROUPS && row0 + rr < B;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[g][e] = in ? x[static_cast<long>(row0 + rr) * IN + kk + e] : 0.f;
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int c = c0 + g * n, rr = c / (IN / 8), kk = (c % (IN / 8)) * 8;
+      if (c < PP_IN_GROUPS)
+        *reinterpret_cast<uint4*>(S + blk_off(rr, kk, ROWS)) =
+            make_uint4(pack_bf16x2(v[g][0], v[g][1]), pack_bf16x2(v[g][2], v[g][3]), pack_bf16x2(v[g][4], v[g][5]),
+                       pack_bf16x2(v[g][6], v[g][7]));
+    }
   }
 }
 
 __global__ void __launch_bounds__(PP_THREADS, 1) mlp_forward_pp_kernel(PpArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* ring = smem + 2 * SMEM_A;
-  __shared__ __align__(8) uint64_t w_full[2], w_empty[2], acc_full[2], a_ready[2];
+  unsigned char* sin = ring + 2 * PP_STAGE;  // the two tiles' inputs: the first layer's A operands
+  // in_ready: a tile's inputs of the next pair staged; l0_done: its first-layer MMA has read them
+  __shared__ __align__(8) uint64_t w_full[2], w_empty[2], acc_full[2], a_ready[2], in_ready[2], l0_done[2];
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
   __shared__ __align__(16) float s_bias[3 * H + OUT];
@@ -448,6 +479,8 @@ __global__ void __launch_bounds__(PP_THREADS, 1) mlp_forward_pp_kernel(PpArgs a)
       mbar_init_cnt(&w_empty[i], 1);
       mbar_init_cnt(&acc_full[i], 1);
       mbar_init_cnt(&a_ready[i], PP_EPI_WARPS);
+      mbar_init_cnt(&in_ready[i], 1);
+      mbar_init_cnt(&l0_done[i], 1);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -495,14 +528,15 @@ __global__ void __launch_bounds__(PP_THREADS, 1) mlp_forward_pp_kernel(PpArgs a)
         for (int l = 0; l < 4; ++l)
           for (int tt = 0; tt < 2; ++tt) {
             const int j = tt ? j1 : j0;
-            if (abort_flag || !mbar_wait_bounded(&a_ready[tt], static_cast<uint32_t>(j) & 1u)) {
+            if (abort_flag || !mbar_wait_bounded(&a_ready[tt], static_cast<uint32_t>(j) & 1u) ||
+                (l == 0 && i > 0 && !mbar_wait_bounded(&in_ready[tt], static_cast<uint32_t>(i - 1) & 1u))) {
               give_up();
               goto mma_done;
             }
             tc_fence_after();
             const uint32_t acc = tmem + static_cast<uint32_t>(tt * 256);
             const uint32_t id = instr_desc(ROWS, ndim(l));
-            const uint32_t A0 = smem_u32(smem + tt * SMEM_A);
+            const uint32_t A0 = smem_u32(l == 0 ? sin + tt * PP_SMEM_IN : smem + tt * SMEM_A);
             for (int c = 0; c < pp_chunks(l); ++c) {
               const int s = q & 1;
               if (!mbar_wait_bounded(&w_full[s], static_cast<uint32_t>(q >> 1) & 1u)) {
@@ -517,17 +551,35 @@ __global__ void __launch_bounds__(PP_THREADS, 1) mlp_forward_pp_kernel(PpArgs a)
               ++q;
             }
             umma_commit(&acc_full[tt]);
+            if (l == 0) umma_commit(&l0_done[tt]);  // the tile's input buffer may take the next pair's
             if (tt) ++j1; else ++j0;
           }
     mma_done:;
     }
+  } else if (warp == PP_EPI_WARPS + 2) {
+    // ---- input staging: each later pair's inputs, tile by tile, once the tile's
+    // first-layer MMA of the pair before has read its buffer
+    for (int i = 1; i < my_pairs; ++i) {
+      const int pair = blockIdx.x + i * gridDim.x;
+      for (int tt = 0; tt < 2; ++tt) {
+        if (abort_flag || !mbar_wait_bounded(&l0_done[tt], static_cast<uint32_t>(i - 1) & 1u)) {
+          give_up();
+          goto staging_done;
+        }
+        pp_stage_input<4>(sin + tt * PP_SMEM_IN, a.x, a.B, (2 * pair + tt) * ROWS, lane, 32);
+        fence_proxy_async();  // the operand, written by this warp, to the tensor core
+        __syncwarp();
+        if (lane == 0) mbar_arrive_one(&in_ready[tt]);
+      }
+    }
+  staging_done:;
   } else {
     // ---- epilogues: warp w reads TMEM lanes 32 (w % 4) .. + 31, column group w / 4
     const int grp = warp >> 2, row = 32 * (warp & 3) + lane;
     int j0 = 0, j1 = 0;
-    if (my_pairs > 0) {
-      pp_stage_input(smem, a.x, a.B, 2 * blockIdx.x * ROWS, t);
-      pp_stage_input(smem + SMEM_A, a.x, a.B, (2 * blockIdx.x + 1) * ROWS, t);
+    if (my_pairs > 0) {  // the first pair's inputs (the staging warp takes the later pairs')
+      pp_stage_input<1>(sin, a.x, a.B, 2 * blockIdx.x * ROWS, t, PP_EPI_WARPS * 32);
+      pp_stage_input<1>(sin + PP_SMEM_IN, a.x, a.B, (2 * blockIdx.x + 1) * ROWS, t, PP_EPI_WARPS * 32);
     }
     fence_proxy_async();
     tc_fence_before();
@@ -585,8 +637,6 @@ __global__ void __launch_bounds__(PP_THREADS, 1) mlp_forward_pp_kernel(PpArgs a)
                                        v[4 * qd + 2] + bias[4 * qd + 2], v[4 * qd + 3] + bias[4 * qd + 3]);
               }
             }
-            // this tile's buffer takes the next pair's inputs
-            if (i + 1 < my_pairs) pp_stage_input(A, a.x, a.B, (2 * (pair + gridDim.x) + tt) * ROWS, t);
           }
           fence_proxy_async();  // the activations, written by every thread, to the tensor core
           tc_fence_before();    // ... after this warp's reads of the accumulator
