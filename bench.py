@@ -461,19 +461,24 @@ def run_mlp(args):
     m = torch.ones(16384, 16, device="cuda")
     flop_row = 2 * (48 * 256 + 2 * 256 * 256 + 256 * 32)
 
+    # at least 2000 calls per timed region (0.1-0.2 s), so that the clocks are
+    # sampled while the kernels run
+    calls = max(args.steps, 2000)
+
     def timed(fn):
         for _ in range(args.warmup):
             fn()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        for _ in range(args.steps):
+        for _ in range(calls):
             fn()
         b.record()
         torch.cuda.synchronize()
-        return a.elapsed_time(b) / args.steps
-    fwd_ms = timed(lambda: net.forward(x))
-    trn_ms = timed(lambda: net.train_step(xt, y, m, 1e-4, want_loss=False))
+        return a.elapsed_time(b) / calls
+    with ClockSampler(0) as clk:
+        fwd_ms = timed(lambda: net.forward(x))
+        trn_ms = timed(lambda: net.train_step(xt, y, m, 1e-4, want_loss=False))
     peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1800.0
     fwd = flop_row * 65536 / fwd_ms / 1e9
@@ -482,7 +487,7 @@ def run_mlp(args):
                       "forward": {"rows": 65536, "ms": fwd_ms, "tflops": fwd, "frac": fwd / peak},
                       "train_step": {"rows": 16384, "ms": trn_ms, "tflops": trn, "frac": trn / peak},
                       "peak": peak, "peak_basis": "MEASURED_PEAKS.json bf16 burst",
-                      "steps": args.steps, "warmup": args.warmup}))
+                      "calls_timed": calls, "warmup": args.warmup, "clocks": clk.summary()}))
     net.close()
 
 
