@@ -350,9 +350,8 @@ tamp_status tamp_eval(tamp_scene *scene, int problem_id, int n, const float *x_d
  * library keeps its copy until the process exits).
  *   - The first call on a device sets the array up (resolves its address,
  *     writes the work-item list and waits for the device to finish that copy,
- *     so the kernel may then run on any stream); make that first call before
- *     any stream capture.  A set-up that fails returns TAMP_ERR_CUDA and the
- *     next call tries it again.
+ *     so the kernel may then run on any stream).  A set-up that fails returns
+ *     TAMP_ERR_CUDA and the next call tries it again.
  *   - Batches are limited to 4096 tiles of 32/L particles (131072 particles at
  *     one lane per particle-configuration); a larger n returns
  *     TAMP_ERR_INVALID_ARG with the limit in tamp_last_error.
