@@ -16,6 +16,7 @@
 // dW = dZ^T A) uses the same instruction forms as the forward pass.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -174,6 +175,14 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&h);
 }
+__device__ __forceinline__ uint32_t pack_f16x2(float a, float b) {
+  const __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+// the two FP16 halves of a word as floats (exact): low half first
+__device__ __forceinline__ float2 unpack_f16x2(uint32_t w) {
+  return __half22float2(*reinterpret_cast<const __half2*>(&w));
+}
 
 // Issue D[128 x N] = A[128 x K] . B[N x K]^T (one thread) and commit it.
 __device__ __forceinline__ void issue_gemm(uint32_t tmem, const unsigned char* A, const unsigned char* B, int N, int K,
@@ -254,10 +263,11 @@ struct FwdArgs {
   const unsigned char* Wp;            // packed BF16 forward operands (pk_off)
   const float* b[4];
   float* out;                         // [B][OUT]
-  // training only (else null): pre-activations Z_l [B][H] (FP32), and the
-  // BF16 operands of the weight gradients, feature-major: x^T [IN][ldT],
-  // A_l^T [H][ldT]
-  float* Z[3]; __nv_bfloat16* XT; __nv_bfloat16* AT[3]; int ldT;
+  // training only (else null): GELU'(Z_l) [B][H] (FP16: GELU' lies in
+  // [-0.17, 1.13], where FP16 rounds 8 times finer than BF16) -- the backward
+  // pass uses the pre-activations only through it -- and the BF16 operands of
+  // the weight gradients, feature-major: x^T [IN][ldT], A_l^T [H][ldT]
+  __half* G[3]; __nv_bfloat16* XT; __nv_bfloat16* AT[3]; int ldT;
   int* err;
 };
 
@@ -334,23 +344,25 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
         tmem_ld32(lane_addr(tmem, c0), v);
         const float* bias = s_bias + l * H + c0;
         if (l < 3) {
-          uint32_t hp[16];
+          uint32_t hp[16], gp[16];
 #pragma unroll
           for (int j = 0; j < 32; j += 2) {
             const float2 z = __fadd2_rn(make_float2(v[j], v[j + 1]), make_float2(bias[j], bias[j + 1]));
-            v[j] = z.x;
-            v[j + 1] = z.y;
             const float2 g = gelu2(z);
             hp[j / 2] = pack_bf16x2(g.x, g.y);
+            if (a.G[l]) {  // GELU'(z) for the backward pass, sharing gelu2's Phi(z)
+              const float2 d = gelu_grad2(z);
+              gp[j / 2] = pack_f16x2(d.x, d.y);
+            }
           }
 #pragma unroll
           for (int q = 0; q < 4; ++q)
             *reinterpret_cast<uint4*>(opA + blk_off(row, c0 + 8 * q, ROWS)) =
                 make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
-          if (a.Z[l] && r < a.B) {
-            float4* zd = reinterpret_cast<float4*>(a.Z[l] + static_cast<long>(r) * H + c0);
+          if (a.G[l] && r < a.B) {
+            uint4* gd = reinterpret_cast<uint4*>(a.G[l] + static_cast<long>(r) * H + c0);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) zd[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            for (int q = 0; q < 4; ++q) gd[q] = make_uint4(gp[4 * q], gp[4 * q + 1], gp[4 * q + 2], gp[4 * q + 3]);
             // feature-major: for each column the 32 rows of a warp are 64 contiguous bytes
             __nv_bfloat16* at = a.AT[l] + static_cast<long>(c0) * a.ldT + r;
 #pragma unroll
@@ -696,7 +708,7 @@ __global__ void mlp_loss_kernel(const float* out, const float* y, const float* m
 struct DzArgs {
   int B, ldT;
   const float* dout;                  // [B][OUT]: dL/d(outputs) = dZ_3
-  const float* Z[3];                  // [B][H]
+  const __half* G[3];                 // GELU'(Z_l) [B][H] (FP16)
   const unsigned char* WpT;           // packed W^T operands (pk_off)
   __nv_bfloat16* dZT[4];              // feature-major dZ_l: [H][ldT] (l < 3), [OUT][ldT] (l = 3)
   int* err;
@@ -764,14 +776,16 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_backward_dz_kernel(DzArgs a) {
       tmem_ld32(lane_addr(tmem, c0), v);
       uint32_t hp[16];
       if (r < a.B) {
-        const float4* zs = reinterpret_cast<const float4*>(a.Z[l - 1] + static_cast<long>(r) * H + c0);
+        const uint4* gs = reinterpret_cast<const uint4*>(a.G[l - 1] + static_cast<long>(r) * H + c0);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float4 z = zs[q];
-          const float2 d0 = __fmul2_rn(make_float2(v[4 * q], v[4 * q + 1]), gelu_grad2(make_float2(z.x, z.y)));
-          const float2 d1 = __fmul2_rn(make_float2(v[4 * q + 2], v[4 * q + 3]), gelu_grad2(make_float2(z.z, z.w)));
-          hp[2 * q] = pack_bf16x2(d0.x, d0.y);
-          hp[2 * q + 1] = pack_bf16x2(d1.x, d1.y);
+        for (int q = 0; q < 4; ++q) {
+          const uint4 g = gs[q];
+          const uint32_t gw[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const float2 d = __fmul2_rn(make_float2(v[8 * q + 2 * h], v[8 * q + 2 * h + 1]), unpack_f16x2(gw[h]));
+            hp[4 * q + h] = pack_bf16x2(d.x, d.y);
+          }
         }
       } else {
 #pragma unroll
@@ -1059,7 +1073,7 @@ struct tamp_mlp {
   float* m = nullptr;
   float* v = nullptr;
   int ldT = 0;                   // row length of the feature-major arrays: max_batch rounded up to 64
-  float* Z = nullptr;            // [3][max_batch][H]
+  __half* G = nullptr;           // [3][max_batch][H]: GELU'(Z_l) of the last training forward (FP16)
   __nv_bfloat16* XT = nullptr;   // [IN][ldT]
   __nv_bfloat16* AT = nullptr;   // [3][H][ldT]
   __nv_bfloat16* dZT = nullptr;  // [3][H][ldT] then [OUT][ldT]
@@ -1127,7 +1141,7 @@ FwdArgs fwd_args(tamp_mlp* n, const float* x, int B, float* out, bool train) {
   a.ldT = n->ldT;
   a.XT = train ? n->XT : nullptr;
   for (int l = 0; l < 3; ++l) {
-    a.Z[l] = train ? n->Z + static_cast<size_t>(l) * n->max_batch * H : nullptr;
+    a.G[l] = train ? n->G + static_cast<size_t>(l) * n->max_batch * H : nullptr;
     a.AT[l] = train ? n->AT + static_cast<size_t>(l) * H * n->ldT : nullptr;
   }
   return a;
@@ -1213,7 +1227,7 @@ tamp_status gradient(tamp_mlp* n, const float* x, const float* y, const float* m
   DzArgs z{};
   z.B = B; z.ldT = n->ldT; z.dout = n->dout; z.WpT = n->wpt; z.err = n->err;
   for (int l = 0; l < 3; ++l) {
-    z.Z[l] = n->Z + static_cast<size_t>(l) * n->max_batch * H;
+    z.G[l] = n->G + static_cast<size_t>(l) * n->max_batch * H;
     z.dZT[l] = n->dZT + static_cast<size_t>(l) * H * n->ldT;
   }
   z.dZT[3] = n->dZT + static_cast<size_t>(3) * H * n->ldT;
@@ -1259,7 +1273,7 @@ tamp_status tamp_mlp_create(int device, void* stream, int max_batch, tamp_mlp** 
   if (e == cudaSuccess) e = cudaMalloc(&n->v, N_PARAMS * 4);
   n->ldT = static_cast<int>((mb + 63) / 64 * 64);
   const size_t lt = static_cast<size_t>(n->ldT);
-  if (e == cudaSuccess) e = cudaMalloc(&n->Z, 3 * mb * H * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&n->G, 3 * mb * H * 2);
   if (e == cudaSuccess) e = cudaMalloc(&n->XT, IN * lt * 2);
   if (e == cudaSuccess) e = cudaMalloc(&n->AT, 3 * H * lt * 2);
   if (e == cudaSuccess) e = cudaMalloc(&n->dZT, (3 * H + OUT) * lt * 2);
@@ -1288,7 +1302,7 @@ tamp_status tamp_mlp_destroy(tamp_mlp* n) {
   Dev g(n->device);
   cudaStreamSynchronize(n->stream);
   cudaFree(n->params); cudaFree(n->wp); cudaFree(n->wpt); cudaFree(n->grad); cudaFree(n->m); cudaFree(n->v);
-  cudaFree(n->Z); cudaFree(n->XT); cudaFree(n->AT); cudaFree(n->dZT); cudaFree(n->out); cudaFree(n->dout);
+  cudaFree(n->G); cudaFree(n->XT); cudaFree(n->AT); cudaFree(n->dZT); cudaFree(n->out); cudaFree(n->dout);
   cudaFree(n->loss); cudaFree(n->err); cudaFree(n->part);
   delete n;
   return TAMP_OK;

@@ -257,6 +257,40 @@ def test_stop_on_first_satisfying_keeps_the_satisfying_state(pkg):
     _check_best_valid(pr, best)
 
 
+def test_graph_stop_keeps_the_satisfying_states_of_every_problem(pkg):
+    """A CUDA graph stopping on the first satisfying particle, over two
+    problems in one launch: the witness batch (perturbed copies of the SCARA
+    witness, which satisfies at x_0) and the same skeleton from particles far
+    from it (joints moved 0.3 rad: no particle satisfies in the 5 iterations
+    that run).  The first problem's record holds its satisfying states, each
+    satisfying Eq. 3 in the oracle, the witness at x_0 among them; the second's
+    stays empty."""
+    from tests.test_oracle_pins import _scara_witness_scene
+    sc, acts, x = _scara_witness_scene()
+    pr = Problem(sc, acts)
+    X = np.repeat(x.numpy(), 40, axis=0)
+    X[1:] += np.random.default_rng(5).normal(0.0, 0.002, (39, X.shape[1]))
+    X = X.astype(np.float32).astype(np.float64)
+    Y = X.copy()
+    Y[:, 4:11] += 0.3
+    scene = pkg.Scene(sc)
+    p1, p2 = scene.set_skeleton(acts), scene.set_skeleton(acts)
+    scene.set_particles(p1, X.T.astype(np.float32))
+    scene.set_particles(p2, Y.T.astype(np.float32))
+    g = pkg.Graph(scene, [p1, p2], 5, 10, stop_on_first=True)
+    steps = g.run()
+    g.close()
+    b1, b2 = scene.query_best(p1, 40), scene.query_best(p2, 40)
+    q1 = scene.query(p1, 40)
+    scene.close()
+    assert steps == 5 and q1["first_iter"] == 0
+    assert b1["n_found"] >= 1 and b1["found"][0] and b1["iter"][0] == 0
+    assert np.array_equal(b1["particles"][:, 0], X[0].astype(np.float32))
+    assert b1["iter"][b1["found"]].min() == 0 and (b1["iter"][b1["found"]] <= steps).all()
+    _check_best_valid(pr, b1)
+    assert b2["n_found"] == 0
+
+
 def test_optimize_steps_stop_mode_without_a_solution_runs_every_chunk(pkg):
     """No particle satisfies within the budget: 23 steps in chunks 5, 5, 5, 5, 3;
     the trajectory and the last check's Eq. 5 counts are the oracle's."""
