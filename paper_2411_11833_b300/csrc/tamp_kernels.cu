@@ -1354,12 +1354,21 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
   const int n_self = (SC && static_cast<int>(s_pb[s_pb[PH_OFF_CFG] + CF_T_SELF]) >= 0) ? K : 0;
   const int n_work = NPIECE * K + n_self + (has_goal ? 1 : 0) + (has_traj ? 1 : 0);
   // Adam's bias corrections 1 / (1 - beta^t) of each iteration's step t, by one
-  // thread, handed to the others through shared memory: 1 - beta^t =
-  // -expm1(t log1p(beta - 1)) keeps FP32's relative accuracy (1.2e-7 against
-  // the FP64 value for t up to 2e5) also where beta^t is close to 1, with no
-  // FP64 (slow on this part) and no value carried across the pass
+  // thread, handed to the others through shared memory.  At one lane per
+  // (particle, configuration): 1 - beta^t = -expm1(t log1p(beta - 1)), which
+  // keeps FP32's relative accuracy (1.2e-7 against the FP64 value for t up to
+  // 2e5) also where beta^t is close to 1, with no FP64 (slow on this part) and
+  // no double carried across the pass (+0.9% on the packing workload).  With
+  // more lanes the register allocation of the pass came out slower that way
+  // (-1.4% on the stress scene at 2 lanes, A/B on one box), so there beta^t is
+  // kept in FP64 and stepped by one multiplication per iteration.
   __shared__ float s_ib[2];
   const float lb1 = log1pf(d.beta1 - 1.f), lb2 = log1pf(d.beta2 - 1.f);
+  double b1t = 0.0, b2t = 0.0;
+  if (L > 1 && tid == 0) {
+    b1t = pow(static_cast<double>(d.beta1), t0);
+    b2t = pow(static_cast<double>(d.beta2), t0);
+  }
   unsigned n_obb = 0, n_box = 0;  // broad-phase candidates resolved exactly (work accounting)
   // this thread's entries of the angle table: a = tid / PT + m (nthr / PT) (nthr is a multiple of PT),
   // particle tid % PT, row a / ntg, angle a % ntg
@@ -1370,9 +1379,16 @@ __device__ void run_tile(const ProbDesc& d, int tile, const uint32_t* s_sc, cons
   for (int it = 0;; ++it) {
     if (tid == 0) {
       s_next = 0;
-      const float ts = static_cast<float>(t0 + it + 1);  // this iteration's step
-      s_ib[0] = -1.f / expm1f(ts * lb1);
-      s_ib[1] = -1.f / expm1f(ts * lb2);
+      if constexpr (L == 1) {
+        const float ts = static_cast<float>(t0 + it + 1);  // this iteration's step
+        s_ib[0] = -1.f / expm1f(ts * lb1);
+        s_ib[1] = -1.f / expm1f(ts * lb2);
+      } else {
+        b1t *= static_cast<double>(d.beta1);  // beta^(t0 + it + 1), for this iteration's step
+        b2t *= static_cast<double>(d.beta2);
+        s_ib[0] = static_cast<float>(1.0 / (1.0 - b1t));
+        s_ib[1] = static_cast<float>(1.0 / (1.0 - b2t));
+      }
     }
     if constexpr (REC) {
       // x_t is staged, as the tile's contiguous [D][PT] block, in the block of
