@@ -15,8 +15,8 @@ import torch
 import scenegen as sg
 from oracle import philox
 from oracle.problem import Problem
-from tests.parity import (FLAG_BAND, KINK_MARGIN, TRAJ_MARGIN, check_adam_step, check_trajectory, cost_ok,
-                          cost_sum_bound, near_threshold, oracle_run)
+from tests.parity import (KINK_MARGIN, TRAJ_MARGIN, check_adam_step, check_trajectory, cost_ok, cost_sum_bound,
+                          near_threshold, oracle_run)
 
 pytestmark = pytest.mark.gpu
 
@@ -33,9 +33,10 @@ def pkg():
 def _counts_match(pr, x, counts):
     """Eq. 5 counts of the last check against the oracle's at the final iterate
     (a particle within 1e-5 of a tolerance may count either way)."""
-    T = pr.term_values(torch.tensor(x.astype(np.float32).astype(np.float64)))
+    xt = torch.tensor(x.astype(np.float32).astype(np.float64))
+    T = pr.term_values(xt)
     ref = pr.constraint_counts(T).numpy()
-    band = near_threshold(pr, T.numpy())
+    band = near_threshold(pr, T.numpy(), pr.kink_margin(xt).numpy())
     assert np.abs(counts - ref).max() <= band.sum(), (counts, ref)
 
 
@@ -103,16 +104,6 @@ def test_optimize_steps_stops_on_the_first_satisfying_particle(pkg):
     _counts_match(pr, xs.T, q["counts"])
 
 
-def _near(pr, T: np.ndarray) -> np.ndarray:
-    """Particles with a constraint term within 1e-5 of its tolerance, a term that
-    is exactly 0 left out: a 0 tolerance (joint limits) is met exactly inside
-    the bounds in either precision, so such a term cannot fall either side."""
-    tol = pr.tolerances().numpy()
-    cm = pr.constraint_mask().numpy()
-    t = T[:, cm]
-    return ((np.abs(t - tol[cm]) <= FLAG_BAND) & (t != 0.0)).any(axis=1)
-
-
 def _check_best_valid(pr, best):
     """Every recorded state satisfies Eq. 3 in the oracle (a particle within 1e-5
     of a tolerance may fall either side) at the cost the record gives."""
@@ -121,7 +112,7 @@ def _check_best_valid(pr, best):
         return 0
     xb = best["particles"].T[f].astype(np.float64)
     T = pr.term_values(torch.tensor(xb))
-    ok = pr.satisfied(T).numpy() | _near(pr, T.numpy())
+    ok = pr.satisfied(T).numpy() | near_threshold(pr, T.numpy())
     assert ok.all(), f"{int((~ok).sum())} recorded states do not satisfy Eq. 3"
     cost = (T * pr.weights()).sum(1).numpy()
     bad = np.abs(best["cost"][f].astype(np.float64) - cost) > cost_sum_bound(pr, T.numpy())
@@ -178,7 +169,7 @@ def test_best_record_is_the_lowest_cost_satisfying_check(pkg):
     near = np.zeros_like(S)
     for k in range(n + 1):
         T = pr.term_values(torch.tensor(xs[k].astype(np.float64)))
-        near[:, k] = _near(pr, T.numpy())
+        near[:, k] = near_threshold(pr, T.numpy())
         ok = (pr.satisfied(T).numpy() == S[:, k]) | near[:, k]
         assert ok.all(), f"check {k}: Eq. 3 flags differ for particles {np.nonzero(~ok)[0][:8]}"
         c_ora = (T * pr.weights()).sum(1).numpy()

@@ -164,10 +164,12 @@ def test_counts_and_mask_match_oracle(pkg):
     scene.set_particles(pid, X.T.astype(np.float32))
     q = scene.query(pid, P)
     scene.close()
-    T = pr.term_values(torch.tensor(X.astype(np.float32).astype(np.float64)))
+    xt = torch.tensor(X.astype(np.float32).astype(np.float64))
+    T = pr.term_values(xt)
     counts = pr.constraint_counts(T).numpy()
     from tests.parity import near_threshold
-    band = near_threshold(pr, T.numpy())
+    band = near_threshold(pr, T.numpy(), pr.kink_margin(xt).numpy())
+    assert band.sum() < P // 2, f"{int(band.sum())} of {P} particles near a tolerance: the check would be vacuous"
     assert np.abs(q["counts"] - counts).max() <= band.sum()
     assert ((q["mask"] != pr.satisfied(T).numpy()) & ~band).sum() == 0
 
