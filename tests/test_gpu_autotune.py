@@ -36,23 +36,33 @@ def test_autotune_keeps_state_and_matches_other_shapes(pkg):
     for a, b in zip(before[:3], after[:3]):
         assert np.array_equal(a, b)
     assert before[3] == after[3]
-    scene.optimize(pid, 6)                       # the tuned shape (options lanes = 0)
-    xt = scene.get_particles(pid)[0]
-    qt = scene.query(pid, n)
-    # the same work with an explicit lane split and the default warps
+    # the tuned shape (options lanes = 0) against an explicit other lane split with the default warps,
+    # from the same state, one step at a time: each launch orders its float atomic additions differently,
+    # so a particle may part ways only at a step that starts near a kink (oracle margin below TRAJ_MARGIN);
+    # every other particle agrees to 1e-5 after each step, and the ones that parted are counted
+    from oracle.problem import Problem
+    from tests.parity import TRAJ_MARGIN
+    pr = Problem(sc, acts)
     ref = pkg.Scene(sc)
     rid = ref.set_skeleton(acts, pkg.default_options(lanes=1 if L != 1 else 2))
-    ref.set_particles(rid, X)
-    ref.optimize(rid, 3)
-    ref.optimize(rid, 6)
-    xr = ref.get_particles(rid)[0]
-    qr = ref.query(rid, n)
-    d = np.abs(xt - xr)
-    assert (d < 1e-4).mean() > 0.99 and d.max() < 0.1
-    close = np.abs(qt["cost"] - qr["cost"]) <= 1e-4 * np.maximum(np.abs(qr["cost"]), 0.1)
-    assert close.mean() > 0.95
+    ref.set_particles(rid, before[0], before[1], before[2], before[3])
+    alive = np.ones(n, bool)
+    parted = 0
+    for step in range(6):
+        x0 = scene.get_particles(pid)[0].T.astype(np.float64)
+        scene.optimize(pid, 1)
+        ref.optimize(rid, 1)
+        d = np.abs(scene.get_particles(pid)[0] - ref.get_particles(rid)[0]).max(axis=0)
+        off = alive & (d > 1e-5)
+        if off.any():
+            near = pr.kink_margin(torch.tensor(x0[off])).numpy() < TRAJ_MARGIN
+            assert near.all(), f"step {step}: a particle away from kinks parted ({d[off].max():.2e})"
+            parted += int(off.sum())
+            alive &= ~off
     scene.close()
     ref.close()
+    print(f"{parted} of {n} particles parted at a step that started near a kink")
+    assert parted <= 0.25 * n
 
 
 def test_set_tuning_validates_and_clears(pkg):

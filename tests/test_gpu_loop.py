@@ -410,27 +410,40 @@ def test_odd_cuboid_counts(pkg, n_obs, lanes):
 def test_scene_on_a_caller_supplied_allocator(pkg):
     """A scene whose device memory comes from PyTorch's caching allocator
     (tamp_allocator callbacks) computes what a cudaMalloc scene computes, and
-    gives every block back."""
+    gives every block back.  The two run side by side one step at a time; as
+    with any two launches, a particle may part ways only at a step that starts
+    near a kink (oracle margin below TRAJ_MARGIN), every other one agrees to
+    1e-5 after each step, and the costs of those that never parted agree."""
     sc, acts = sg.packing_problem(2001)
-    X = sg.random_particles(sc, acts, 200, seed=9).T.astype(np.float32)
-
-    def run(torch_allocator):
-        scene = pkg.Scene(sc, torch_allocator=torch_allocator)
-        pid = scene.set_skeleton(acts)
-        scene.set_particles(pid, X)
-        scene.optimize(pid, 3)
-        x = scene.get_particles(pid)[0]
-        q = scene.query(pid, 200)
-        g = pkg.Graph(scene, pid, 2, 2)
+    n = 200
+    pr = Problem(sc, acts)
+    X = sg.random_particles(sc, acts, n, seed=9).T.astype(np.float32)
+    scenes = [pkg.Scene(sc), pkg.Scene(sc, torch_allocator=True)]
+    pids = [s.set_skeleton(acts) for s in scenes]
+    for s, pid in zip(scenes, pids):
+        s.set_particles(pid, X)
+    assert len(scenes[1]._alloc[2]) > 0      # the scene's buffers came from the callbacks
+    alive = np.ones(n, bool)
+    parted = 0
+    for step in range(3):
+        x0 = scenes[0].get_particles(pids[0])[0].T.astype(np.float64)
+        for s, pid in zip(scenes, pids):
+            s.optimize(pid, 1)
+        d = np.abs(scenes[0].get_particles(pids[0])[0] - scenes[1].get_particles(pids[1])[0]).max(axis=0)
+        off = alive & (d > 1e-5)
+        if off.any():
+            near = pr.kink_margin(torch.tensor(x0[off])).numpy() < TRAJ_MARGIN
+            assert near.all(), f"step {step}: a particle away from kinks parted ({d[off].max():.2e})"
+            parted += int(off.sum())
+            alive &= ~off
+    q = [s.query(pid, n) for s, pid in zip(scenes, pids)]
+    assert cost_ok(q[1]["cost"].astype(np.float64), q[0]["cost"].astype(np.float64))[alive].all()
+    assert parted <= 0.25 * n
+    for s, pid in zip(scenes, pids):
+        g = pkg.Graph(s, pid, 2, 2)
         g.run()
         g.close()
-        live = dict(scene._alloc[2]) if torch_allocator else {}
-        scene.close()
-        return x, q, live, (scene._alloc[2] if torch_allocator else {})
-
-    x0, q0, _, _ = run(False)
-    x1, q1, live, after = run(True)
-    assert len(live) > 0                     # the scene's buffers came from the callbacks
-    assert len(after) == 0                   # ... and were all given back
-    assert np.abs(x1 - x0).max() < 1e-4
-    assert cost_ok(q1["cost"].astype(np.float64), q0["cost"].astype(np.float64)).mean() > 0.99
+    live = dict(scenes[1]._alloc[2])
+    for s in scenes:
+        s.close()
+    assert len(live) > 0 and len(scenes[1]._alloc[2]) == 0   # ... and were all given back
