@@ -24,6 +24,7 @@
 #include <cstdint>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "tamp.h"
@@ -97,6 +98,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
   return false;
 }
+// Programmatic dependent launch, for the kernels of a training step, which
+// are launched with programmatic stream serialisation: pdl_wait blocks until
+// the grids this one depends on have completed and their writes are visible
+// (a no-op for a grid launched without the attribute); pdl_release lets the
+// next grid in the stream be scheduled, where it runs its own set-up up to
+// its pdl_wait.  No kernel reads another grid's output before its pdl_wait.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 // tensor memory: allocated and freed by one whole warp
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
@@ -268,6 +277,7 @@ struct FwdArgs {
   // pass uses the pre-activations only through it -- and the BF16 operands of
   // the weight gradients, feature-major: x^T [IN][ldT], A_l^T [H][ldT]
   __half* G[3]; __nv_bfloat16* XT; __nv_bfloat16* AT[3]; int ldT;
+  float* loss;                        // training: the NLL accumulator, zeroed here for the backward pass
   int* err;
 };
 
@@ -290,12 +300,17 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
     mbar_init(&bar_mma);
     mbar_init(&bar_w);
     fence_proxy_async();
+  }
+  if (warp == 0) tmem_alloc(&tslot);
+  pdl_wait();  // the weights of the last update, the inputs
+  pdl_release();
+  if (t == 0) {
     mbar_expect_tx(&bar_w, static_cast<uint32_t>(pk_bytes(0)));
     bulk_g2s(opB, a.Wp + pk_off(0), static_cast<uint32_t>(pk_bytes(0)), &bar_w);
     w_pending = true;
+    if (a.loss && blockIdx.x == 0) *a.loss = 0.f;
   }
   for (int i = t; i < 3 * H + OUT; i += THREADS) s_bias[i] = i < 3 * H ? a.b[i / H][i % H] : a.b[3][i - 3 * H];
-  if (warp == 0) tmem_alloc(&tslot);
   // inputs: 8 columns (one 16-byte chunk of the layout) per step
   for (int c = t; c < ROWS * (IN / 8); c += THREADS) {
     const int rr = c / (IN / 8), kk = (c % (IN / 8)) * 8;
@@ -665,36 +680,6 @@ __global__ void __launch_bounds__(PP_THREADS, 1) mlp_forward_pp_kernel(PpArgs a)
   if (warp == 0) tmem_dealloc512(tmem);
 }
 
-// ------------------------------------------------------------------ loss
-// Gaussian NLL per row: sum over masked k of (y - mu)^2 exp(-2 s) / 2 + s,
-// mean over rows; dOut = d(mean)/d(out).
-__global__ void mlp_loss_kernel(const float* out, const float* y, const float* mask, int B, float* dout,
-                                float* loss_sum) {
-  // one thread per (row, target): consecutive threads read consecutive targets
-  const long i = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  float l = 0.f;
-  if (i < static_cast<long>(B) * NTGT) {
-    const long r = i / NTGT;
-    const int k = static_cast<int>(i - r * NTGT);
-    const float inv = 1.f / static_cast<float>(B);
-    const float mu = out[r * OUT + k], s = out[r * OUT + NTGT + k];
-    const float m = mask[i], d = y[i] - mu;
-    const float e = expf(-2.f * s);
-    l = m * (0.5f * d * d * e + s);
-    dout[r * OUT + k] = m * (-d * e) * inv;
-    dout[r * OUT + NTGT + k] = m * (1.f - d * d * e) * inv;
-  }
-  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-  __shared__ float part[32];
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = l;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float sum = 0.f;
-    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) sum += part[w];
-    if (sum != 0.f) atomicAdd(loss_sum, sum / static_cast<float>(B));
-  }
-}
-
 // ------------------------------------------------------------------ backward
 // Two kernels.  (1) Per 128-row tile: dZ_l for l = 3 .. 0 through the layers,
 // dA_{l-1} = dZ_l W_l on the tensor core (W_l^T packed, one bulk copy per
@@ -707,7 +692,10 @@ __global__ void mlp_loss_kernel(const float* out, const float* y, const float* m
 // weight, and db_l with one per output.
 struct DzArgs {
   int B, ldT;
-  const float* dout;                  // [B][OUT]: dL/d(outputs) = dZ_3
+  const float* out;                   // [B][OUT]: the training forward's outputs (mu, log sigma)
+  const float* y;                     // [B][NTGT] targets
+  const float* mask;                  // [B][NTGT]
+  float* loss;                        // the NLL's mean over rows, accumulated (zeroed before the launch)
   const __half* G[3];                 // GELU'(Z_l) [B][H] (FP16)
   const unsigned char* WpT;           // packed W^T operands (pk_off)
   __nv_bfloat16* dZT[4];              // feature-major dZ_l: [H][ldT] (l < 3), [OUT][ldT] (l = 3)
@@ -728,27 +716,61 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_backward_dz_kernel(DzArgs a) {
     mbar_init(&bar_mma);
     mbar_init(&bar_w);
     fence_proxy_async();
+  }
+  if (warp == 0) tmem_alloc(&tslot);
+  pdl_wait();  // the forward's outputs and GELU'(Z)
+  pdl_release();
+  if (t == 0) {
     mbar_expect_tx(&bar_w, static_cast<uint32_t>(pk_bytes(3)));
     bulk_g2s(opB, a.WpT + pk_off(3), static_cast<uint32_t>(pk_bytes(3)), &bar_w);
     w_pending = true;
   }
-  if (warp == 0) tmem_alloc(&tslot);
-  // dZ_3 = dL/d(outputs): the A operand (K = 32) and its feature-major copy
+  // dZ_3 = dL/d(outputs) of the Gaussian NLL, mean over the B rows of
+  // sum over masked k of (y_k - mu_k)^2 exp(-2 s_k) / 2 + s_k (s = log sigma):
+  // dL/dmu_k = -m (y_k - mu_k) exp(-2 s_k) / B, dL/ds_k = m (1 - (y_k - mu_k)^2 exp(-2 s_k)) / B.
+  // The A operand (K = 32) and its feature-major copy; the threads of columns
+  // 0 .. 15 (the means) also sum the rows' NLL terms.
+  __shared__ float s_loss[THREADS / 32];
+  float lsum = 0.f;
+  const float inv = 1.f / static_cast<float>(a.B);
   for (int c = t; c < ROWS * (OUT / 8); c += THREADS) {
-    const int rr = c / (OUT / 8), kk = (c % (OUT / 8)) * 8;
+    const int rr = c / (OUT / 8), kk = (c % (OUT / 8)) * 8, k0 = kk % NTGT;
     float v[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = rr < Rv ? a.dout[static_cast<long>(row0 + rr) * OUT + kk + e] : 0.f;
+    for (int e = 0; e < 8; ++e) {
+      v[e] = 0.f;
+      if (rr < Rv) {
+        const long rw = row0 + rr;
+        const int k = k0 + e;
+        const float mu = a.out[rw * OUT + k], sg = a.out[rw * OUT + NTGT + k];
+        const float m = a.mask[rw * NTGT + k], d = a.y[rw * NTGT + k] - mu;
+        const float ex = expf(-2.f * sg);
+        if (kk < NTGT) {
+          v[e] = m * (-d * ex) * inv;
+          lsum += m * (0.5f * d * d * ex + sg);
+        } else {
+          v[e] = m * (1.f - d * d * ex) * inv;
+        }
+      }
+    }
     *reinterpret_cast<uint4*>(opA + blk_off(rr, kk, ROWS)) =
         make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
     if (rr < Rv)
 #pragma unroll
       for (int e = 0; e < 8; ++e) a.dZT[3][static_cast<long>(kk + e) * a.ldT + row0 + rr] = __float2bfloat16_rn(v[e]);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+  if (lane == 0) s_loss[warp] = lsum;
   fence_proxy_async();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  if (t == 0) {
+    float sum = 0.f;
+    for (int w = 0; w < THREADS / 32; ++w) sum += s_loss[w];
+    if (sum != 0.f) atomicAdd(a.loss, sum * inv);
+  }
   const uint32_t tmem = tslot;
   uint32_t ph_mma = 0, ph_w = 0;
   for (int l = 3; l >= 1; --l) {
@@ -900,6 +922,8 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(&tslot);
+  pdl_wait();  // the feature-major operands of the forward and the dZ chain
+  pdl_release();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -1042,6 +1066,8 @@ __global__ void mlp_adam_kernel(float* p, const float* __restrict__ part, int sp
                                 unsigned char* Wp, unsigned char* WpT, int n, float lr, float b1, float b2, float eps,
                                 float ib1, float ib2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_wait();  // the row splits' partial gradients
+  pdl_release();
   if (i >= n) return;
   float gi = 0.f;
   for (int s = 0; s < splits; ++s) gi += part[static_cast<long>(s) * n + i];
@@ -1078,7 +1104,6 @@ struct tamp_mlp {
   __nv_bfloat16* AT = nullptr;   // [3][H][ldT]
   __nv_bfloat16* dZT = nullptr;  // [3][H][ldT] then [OUT][ldT]
   float* out = nullptr;        // [max_batch][OUT]
-  float* dout = nullptr;       // [max_batch][OUT]
   float* part = nullptr;       // [DW_MAX_SPLITS][N_PARAMS]: per row split partial gradients
   mlpk::DwMaps dw_maps;        // tensor maps of the weight-gradient operands for batches of dw_maps_B rows
   int dw_maps_B = -1;
@@ -1212,27 +1237,41 @@ tamp_status check_err(tamp_mlp* n) {
   return TAMP_OK;
 }
 
+// a kernel of the training step, launched with programmatic stream
+// serialisation: it may be scheduled while the previous kernel of the stream
+// finishes, and waits for it (pdl_wait) before reading its outputs
+template <typename... P, typename... A>
+cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
 // forward (training form) + loss + backward: the row splits' partial gradients
 // in n->part (*splits_out of them), summed into n->grad if `reduce`
 tamp_status gradient(tamp_mlp* n, const float* x, const float* y, const float* mask, int B, bool reduce,
                      int* splits_out) {
   MLP_TRY(n, enable_smem(n->device));
   const int tiles = (B + ROWS - 1) / ROWS;
-  MLP_TRY(n, cudaMemsetAsync(n->loss, 0, 4, n->stream));
-  mlp_forward_kernel<<<tiles, THREADS, SMEM_BYTES, n->stream>>>(fwd_args(n, x, B, n->out, true));
-  MLP_TRY(n, cudaGetLastError());
-  mlp_loss_kernel<<<static_cast<int>((static_cast<long>(B) * NTGT + 255) / 256), 256, 0, n->stream>>>(
-      n->out, y, mask, B, n->dout, n->loss);
-  MLP_TRY(n, cudaGetLastError());
+  FwdArgs fa = fwd_args(n, x, B, n->out, true);
+  fa.loss = n->loss;  // zeroed by the forward, summed by the dZ chain
+  MLP_TRY(n, launch_pdl(mlp_forward_kernel, dim3(tiles), dim3(THREADS), SMEM_BYTES, n->stream, fa));
   DzArgs z{};
-  z.B = B; z.ldT = n->ldT; z.dout = n->dout; z.WpT = n->wpt; z.err = n->err;
+  z.B = B; z.ldT = n->ldT; z.out = n->out; z.y = y; z.mask = mask; z.loss = n->loss; z.WpT = n->wpt; z.err = n->err;
   for (int l = 0; l < 3; ++l) {
     z.G[l] = n->G + static_cast<size_t>(l) * n->max_batch * H;
     z.dZT[l] = n->dZT + static_cast<size_t>(l) * H * n->ldT;
   }
   z.dZT[3] = n->dZT + static_cast<size_t>(3) * H * n->ldT;
-  mlp_backward_dz_kernel<<<tiles, THREADS, SMEM_BYTES, n->stream>>>(z);
-  MLP_TRY(n, cudaGetLastError());
+  MLP_TRY(n, launch_pdl(mlp_backward_dz_kernel, dim3(tiles), dim3(THREADS), SMEM_BYTES, n->stream, z));
   // weight gradients: 8 (layer, 128 outputs) blocks x row splits, about one CTA per SM
   const tamp_status ms = make_dw_maps(n, B);
   if (ms != TAMP_OK) return ms;
@@ -1242,8 +1281,7 @@ tamp_status gradient(tamp_mlp* n, const float* x, const float* y, const float* m
   const int splits = std::max(1, std::min({DW_MAX_SPLITS, sm / 8, (B + DW_CHUNK - 1) / DW_CHUNK}));
   w.B = B; w.part = n->part; w.err = n->err;
   w.rows_per_split = ((B + splits - 1) / splits + DW_CHUNK - 1) / DW_CHUNK * DW_CHUNK;
-  mlp_backward_dw_kernel<<<dim3(8, splits), DW_THREADS, DW_SMEM, n->stream>>>(n->dw_maps, w);
-  MLP_TRY(n, cudaGetLastError());
+  MLP_TRY(n, launch_pdl(mlp_backward_dw_kernel, dim3(8, splits), dim3(DW_THREADS), DW_SMEM, n->stream, n->dw_maps, w));
   *splits_out = splits;
   if (reduce) {
     mlp_reduce_kernel<<<static_cast<int>((N_PARAMS + 255) / 256), 256, 0, n->stream>>>(n->part, splits, n->grad,
@@ -1278,7 +1316,6 @@ tamp_status tamp_mlp_create(int device, void* stream, int max_batch, tamp_mlp** 
   if (e == cudaSuccess) e = cudaMalloc(&n->AT, 3 * H * lt * 2);
   if (e == cudaSuccess) e = cudaMalloc(&n->dZT, (3 * H + OUT) * lt * 2);
   if (e == cudaSuccess) e = cudaMalloc(&n->out, mb * OUT * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&n->dout, mb * OUT * 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->part, static_cast<size_t>(DW_MAX_SPLITS) * N_PARAMS * 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->loss, 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->err, 4);
@@ -1302,7 +1339,7 @@ tamp_status tamp_mlp_destroy(tamp_mlp* n) {
   Dev g(n->device);
   cudaStreamSynchronize(n->stream);
   cudaFree(n->params); cudaFree(n->wp); cudaFree(n->wpt); cudaFree(n->grad); cudaFree(n->m); cudaFree(n->v);
-  cudaFree(n->G); cudaFree(n->XT); cudaFree(n->AT); cudaFree(n->dZT); cudaFree(n->out); cudaFree(n->dout);
+  cudaFree(n->G); cudaFree(n->XT); cudaFree(n->AT); cudaFree(n->dZT); cudaFree(n->out);
   cudaFree(n->loss); cudaFree(n->err); cudaFree(n->part);
   delete n;
   return TAMP_OK;
@@ -1368,10 +1405,9 @@ tamp_status tamp_mlp_train_step(tamp_mlp* n, const float* x, const float* y, con
   const double b1 = 0.9, b2 = 0.999;
   const float ib1 = static_cast<float>(1.0 / (1.0 - std::pow(b1, static_cast<double>(n->step))));
   const float ib2 = static_cast<float>(1.0 / (1.0 - std::pow(b2, static_cast<double>(n->step))));
-  mlp_adam_kernel<<<static_cast<int>((N_PARAMS + 255) / 256), 256, 0, n->stream>>>(
-      n->params, n->part, splits, n->m, n->v, n->wp, n->wpt, static_cast<int>(N_PARAMS), lr, 0.9f, 0.999f, 1e-8f,
-      ib1, ib2);
-  MLP_TRY(n, cudaGetLastError());
+  MLP_TRY(n, launch_pdl(mlp_adam_kernel, dim3(static_cast<int>((N_PARAMS + 255) / 256)), dim3(256), 0, n->stream,
+                        n->params, n->part, splits, n->m, n->v, n->wp, n->wpt, static_cast<int>(N_PARAMS), lr, 0.9f,
+                        0.999f, 1e-8f, ib1, ib2));
   if (loss) {
     MLP_TRY(n, cudaMemcpyAsync(loss, n->loss, 4, cudaMemcpyDeviceToHost, n->stream));
     return check_err(n);
