@@ -184,6 +184,15 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&h);
 }
+// GELU'(Z_l) is written by the training forward and read by the dZ chain,
+// both with thread (warp w, lane i) on row 32 (w % 4) + i of a 128-row tile
+// and the 32-column chunks of column group w / 4.  It is kept in the layout
+// they share: per tile, warp, chunk and 16-byte piece q of a row's chunk, the
+// 32 lanes' pieces side by side -- each store and load of a warp moves 512
+// contiguous bytes (by rows, each would touch 32 rows).  64 KB per tile.
+__device__ __forceinline__ uint4* g_pieces(__half* G, int tile, int warp, int chunk, int lane) {
+  return reinterpret_cast<uint4*>(G) + static_cast<long>(((tile * (THREADS / 32) + warp) * 2 + chunk) * 4) * 32 + lane;
+}
 __device__ __forceinline__ uint32_t pack_f16x2(float a, float b) {
   const __half2 h = __floats2half2_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&h);
@@ -272,10 +281,11 @@ struct FwdArgs {
   const unsigned char* Wp;            // packed BF16 forward operands (pk_off)
   const float* b[4];
   float* out;                         // [B][OUT]
-  // training only (else null): GELU'(Z_l) [B][H] (FP16: GELU' lies in
-  // [-0.17, 1.13], where FP16 rounds 8 times finer than BF16) -- the backward
-  // pass uses the pre-activations only through it -- and the BF16 operands of
-  // the weight gradients, feature-major: x^T [IN][ldT], A_l^T [H][ldT]
+  // training only (else null): GELU'(Z_l) (FP16: GELU' lies in [-0.17,
+  // 1.13], where FP16 rounds 8 times finer than BF16; in the g_pieces layout)
+  // -- the backward pass uses the pre-activations only through it -- and the
+  // BF16 operands of the weight gradients, feature-major: x^T [IN][ldT],
+  // A_l^T [H][ldT]
   __half* G[3]; __nv_bfloat16* XT; __nv_bfloat16* AT[3]; int ldT;
   float* loss;                        // training: the NLL accumulator, zeroed here for the backward pass
   int* err;
@@ -375,9 +385,9 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
             *reinterpret_cast<uint4*>(opA + blk_off(row, c0 + 8 * q, ROWS)) =
                 make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
           if (a.G[l] && r < a.B) {
-            uint4* gd = reinterpret_cast<uint4*>(a.G[l] + static_cast<long>(r) * H + c0);
+            uint4* gd = g_pieces(a.G[l], blockIdx.x, warp, (c0 - grp * per) >> 5, lane);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) gd[q] = make_uint4(gp[4 * q], gp[4 * q + 1], gp[4 * q + 2], gp[4 * q + 3]);
+            for (int q = 0; q < 4; ++q) gd[32 * q] = make_uint4(gp[4 * q], gp[4 * q + 1], gp[4 * q + 2], gp[4 * q + 3]);
             // feature-major: for each column the 32 rows of a warp are 64 contiguous bytes
             __nv_bfloat16* at = a.AT[l] + static_cast<long>(c0) * a.ldT + r;
 #pragma unroll
@@ -696,7 +706,7 @@ struct DzArgs {
   const float* y;                     // [B][NTGT] targets
   const float* mask;                  // [B][NTGT]
   float* loss;                        // the NLL's mean over rows, accumulated (zeroed before the launch)
-  const __half* G[3];                 // GELU'(Z_l) [B][H] (FP16)
+  __half* G[3];                       // GELU'(Z_l) (FP16, the g_pieces layout)
   const unsigned char* WpT;           // packed W^T operands (pk_off)
   __nv_bfloat16* dZT[4];              // feature-major dZ_l: [H][ldT] (l < 3), [OUT][ldT] (l = 3)
   int* err;
@@ -798,10 +808,10 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_backward_dz_kernel(DzArgs a) {
       tmem_ld32(lane_addr(tmem, c0), v);
       uint32_t hp[16];
       if (r < a.B) {
-        const uint4* gs = reinterpret_cast<const uint4*>(a.G[l - 1] + static_cast<long>(r) * H + c0);
+        const uint4* gs = g_pieces(a.G[l - 1], blockIdx.x, warp, (c0 - grp * (K / NGRP)) >> 5, lane);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const uint4 g = gs[q];
+          const uint4 g = gs[32 * q];
           const uint32_t gw[4] = {g.x, g.y, g.z, g.w};
 #pragma unroll
           for (int h = 0; h < 4; ++h) {
@@ -1099,7 +1109,7 @@ struct tamp_mlp {
   float* m = nullptr;
   float* v = nullptr;
   int ldT = 0;                   // row length of the feature-major arrays: max_batch rounded up to 64
-  __half* G = nullptr;           // [3][max_batch][H]: GELU'(Z_l) of the last training forward (FP16)
+  __half* G = nullptr;           // [3][g_rows][H]: GELU'(Z_l) of the last training forward (FP16, g_pieces layout)
   __nv_bfloat16* XT = nullptr;   // [IN][ldT]
   __nv_bfloat16* AT = nullptr;   // [3][H][ldT]
   __nv_bfloat16* dZT = nullptr;  // [3][H][ldT] then [OUT][ldT]
@@ -1114,6 +1124,8 @@ struct tamp_mlp {
 };
 
 namespace {
+// rows of each layer's GELU'(Z) block: whole 128-row tiles
+size_t g_rows(const tamp_mlp* n) { return (static_cast<size_t>(n->max_batch) + ROWS - 1) / ROWS * ROWS; }
 tamp_status mfail(tamp_mlp* n, tamp_status st, const std::string& msg) {
   if (n) n->last_error = msg;
   return st;
@@ -1166,7 +1178,7 @@ FwdArgs fwd_args(tamp_mlp* n, const float* x, int B, float* out, bool train) {
   a.ldT = n->ldT;
   a.XT = train ? n->XT : nullptr;
   for (int l = 0; l < 3; ++l) {
-    a.G[l] = train ? n->G + static_cast<size_t>(l) * n->max_batch * H : nullptr;
+    a.G[l] = train ? n->G + static_cast<size_t>(l) * g_rows(n) * H : nullptr;
     a.AT[l] = train ? n->AT + static_cast<size_t>(l) * H * n->ldT : nullptr;
   }
   return a;
@@ -1267,7 +1279,7 @@ tamp_status gradient(tamp_mlp* n, const float* x, const float* y, const float* m
   DzArgs z{};
   z.B = B; z.ldT = n->ldT; z.out = n->out; z.y = y; z.mask = mask; z.loss = n->loss; z.WpT = n->wpt; z.err = n->err;
   for (int l = 0; l < 3; ++l) {
-    z.G[l] = n->G + static_cast<size_t>(l) * n->max_batch * H;
+    z.G[l] = n->G + static_cast<size_t>(l) * g_rows(n) * H;
     z.dZT[l] = n->dZT + static_cast<size_t>(l) * H * n->ldT;
   }
   z.dZT[3] = n->dZT + static_cast<size_t>(3) * H * n->ldT;
@@ -1311,7 +1323,7 @@ tamp_status tamp_mlp_create(int device, void* stream, int max_batch, tamp_mlp** 
   if (e == cudaSuccess) e = cudaMalloc(&n->v, N_PARAMS * 4);
   n->ldT = static_cast<int>((mb + 63) / 64 * 64);
   const size_t lt = static_cast<size_t>(n->ldT);
-  if (e == cudaSuccess) e = cudaMalloc(&n->G, 3 * mb * H * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&n->G, 3 * g_rows(n) * H * 2);
   if (e == cudaSuccess) e = cudaMalloc(&n->XT, IN * lt * 2);
   if (e == cudaSuccess) e = cudaMalloc(&n->AT, 3 * H * lt * 2);
   if (e == cudaSuccess) e = cudaMalloc(&n->dZT, (3 * H + OUT) * lt * 2);
