@@ -284,9 +284,8 @@ struct FwdArgs {
   // training only (else null): GELU'(Z_l) (FP16: GELU' lies in [-0.17,
   // 1.13], where FP16 rounds 8 times finer than BF16; in the g_pieces layout)
   // -- the backward pass uses the pre-activations only through it -- and the
-  // BF16 operands of the weight gradients, feature-major: x^T [IN][ldT],
-  // A_l^T [H][ldT]
-  __half* G[3]; __nv_bfloat16* XT; __nv_bfloat16* AT[3]; int ldT;
+  // BF16 operands of the weight gradients x and A_l in the f8 layout (ldR rows)
+  __half* G[3]; uint4* X8; uint4* A8[3]; int ldR;
   float* loss;                        // training: the NLL accumulator, zeroed here for the backward pass
   int* err;
 };
@@ -327,11 +326,10 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
     float v[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[e] = rr < Rv ? a.x[static_cast<long>(row0 + rr) * IN + kk + e] : 0.f;
-    *reinterpret_cast<uint4*>(opA + blk_off(rr, kk, ROWS)) =
+    const uint4 pk =
         make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
-    if (a.XT && rr < Rv)
-#pragma unroll
-      for (int e = 0; e < 8; ++e) a.XT[static_cast<long>(kk + e) * a.ldT + row0 + rr] = __float2bfloat16_rn(v[e]);
+    *reinterpret_cast<uint4*>(opA + blk_off(rr, kk, ROWS)) = pk;
+    if (a.X8) a.X8[static_cast<long>(kk >> 3) * a.ldR + row0 + rr] = pk;  // rows past B: zeros
   }
   fence_proxy_async();
   tc_fence_before();
@@ -384,17 +382,15 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
           for (int q = 0; q < 4; ++q)
             *reinterpret_cast<uint4*>(opA + blk_off(row, c0 + 8 * q, ROWS)) =
                 make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
-          if (a.G[l] && r < a.B) {
+          if (a.G[l]) {
             uint4* gd = g_pieces(a.G[l], blockIdx.x, warp, (c0 - grp * per) >> 5, lane);
+            uint4* ad = a.A8[l] + static_cast<long>(c0 >> 3) * a.ldR + r;  // f8: the warp's 32 rows side by side
+            const bool in = r < a.B;  // rows past B: zeros in A8 (the weight-gradient copies read whole chunks)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) gd[32 * q] = make_uint4(gp[4 * q], gp[4 * q + 1], gp[4 * q + 2], gp[4 * q + 3]);
-            // feature-major: for each column the 32 rows of a warp are 64 contiguous bytes
-            __nv_bfloat16* at = a.AT[l] + static_cast<long>(c0) * a.ldT + r;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&hp[j]);
-              at[static_cast<long>(2 * j) * a.ldT] = h2.x;
-              at[static_cast<long>(2 * j + 1) * a.ldT] = h2.y;
+            for (int q = 0; q < 4; ++q) {
+              if (in) gd[32 * q] = make_uint4(gp[4 * q], gp[4 * q + 1], gp[4 * q + 2], gp[4 * q + 3]);
+              ad[static_cast<long>(q) * a.ldR] =
+                  in ? make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]) : make_uint4(0u, 0u, 0u, 0u);
             }
           }
         } else if (r < a.B) {
@@ -701,14 +697,14 @@ __global__ void __launch_bounds__(PP_THREADS, 1) mlp_forward_pp_kernel(PpArgs a)
 // and double-buffered; each split adds its partial dW with one atomic per
 // weight, and db_l with one per output.
 struct DzArgs {
-  int B, ldT;
+  int B, ldR;
   const float* out;                   // [B][OUT]: the training forward's outputs (mu, log sigma)
   const float* y;                     // [B][NTGT] targets
   const float* mask;                  // [B][NTGT]
   float* loss;                        // the NLL's mean over rows, accumulated (zeroed before the launch)
   __half* G[3];                       // GELU'(Z_l) (FP16, the g_pieces layout)
   const unsigned char* WpT;           // packed W^T operands (pk_off)
-  __nv_bfloat16* dZT[4];              // feature-major dZ_l: [H][ldT] (l < 3), [OUT][ldT] (l = 3)
+  uint4* dZ8[4];                      // dZ_l in the f8 layout (ldR rows): H features (l < 3), OUT (l = 3)
   int* err;
 };
 
@@ -763,11 +759,10 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_backward_dz_kernel(DzArgs a) {
         }
       }
     }
-    *reinterpret_cast<uint4*>(opA + blk_off(rr, kk, ROWS)) =
+    const uint4 pk =
         make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
-    if (rr < Rv)
-#pragma unroll
-      for (int e = 0; e < 8; ++e) a.dZT[3][static_cast<long>(kk + e) * a.ldT + row0 + rr] = __float2bfloat16_rn(v[e]);
+    *reinterpret_cast<uint4*>(opA + blk_off(rr, kk, ROWS)) = pk;
+    a.dZ8[3][static_cast<long>(kk >> 3) * a.ldR + row0 + rr] = pk;  // rows past B: zeros
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
@@ -802,7 +797,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_backward_dz_kernel(DzArgs a) {
       bulk_g2s(opB, a.WpT + pk_off(l - 1), static_cast<uint32_t>(pk_bytes(l - 1)), &bar_w);
       w_pending = true;
     }
-    __nv_bfloat16* dzt = a.dZT[l - 1];
+    uint4* dz8 = a.dZ8[l - 1];
     for (int c0 = grp * (K / NGRP); c0 < (grp + 1) * (K / NGRP); c0 += 32) {
       float v[32];
       tmem_ld32(lane_addr(tmem, c0), v);
@@ -827,14 +822,11 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_backward_dz_kernel(DzArgs a) {
       for (int q = 0; q < 4; ++q)
         *reinterpret_cast<uint4*>(opA + blk_off(row, c0 + 8 * q, ROWS)) =
             make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
-      if (r < a.B) {
-        __nv_bfloat16* dt = dzt + static_cast<long>(c0) * a.ldT + r;
+      {
+        uint4* dd = dz8 + static_cast<long>(c0 >> 3) * a.ldR + r;  // f8: the warp's 32 rows side by side (zeros past B)
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&hp[j]);
-          dt[static_cast<long>(2 * j) * a.ldT] = h2.x;
-          dt[static_cast<long>(2 * j + 1) * a.ldT] = h2.y;
-        }
+        for (int q = 0; q < 4; ++q)
+          dd[static_cast<long>(q) * a.ldR] = make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
       }
     }
     fence_proxy_async();
@@ -849,15 +841,20 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_backward_dz_kernel(DzArgs a) {
 
 // The weight gradients dW_l = dZ_l^T A_{l-1} (and db_l = column sums of dZ_l):
 // per CTA one layer, 128 of its outputs and a split of the batch rows, which
-// are the GEMM's K.  Both operands are feature-major in global memory
-// ([features][ldT]); TMA tensor copies (cp.async.bulk.tensor) bring each
-// 64-row chunk -- one box of 64 batch rows (128 bytes) by R features per
-// operand -- into a ring of DW_STAGES shared-memory stages in the 128-byte
-// swizzled K-major layout the tensor core reads (8-row atoms of 1 KB, the
-// 16-byte pieces of row r at positions permuted by r mod 8), while one thread
-// issues the MMAs of the chunks that have landed.  The 128 threads of the
-// epilogue warps add each of their row's chunk values for db before releasing
-// a stage.  Batch rows past B are filled with zeros by the copies.
+// are the GEMM's K.  The operands -- x, A_l, dZ_l -- arrive in the f8 layout
+// the forward and the dZ chain write: per group of 8 features, every row's 8
+// BF16 values (16 bytes) one after the other, so that a chunk's 64 rows of a
+// group are 1 KB in one piece.  TMA tensor copies (cp.async.bulk.tensor, 3-D:
+// 128-byte core matrices x feature groups x 8-row blocks) bring each 64-row
+// chunk of both operands into a ring of DW_STAGES shared-memory stages, a K
+// group's core matrices side by side (so that the tensor core's reads of
+// neighbouring feature groups fall on different banks): the MN-major operand
+// layout without swizzle, core matrices of 8 rows (K) x 16 bytes, the next
+// feature group 128 bytes on, the next 8 rows G x 128 bytes on (G: the
+// operand's feature groups); a K step of 16 rows moves 2 G x 128 bytes.  One thread
+// issues the MMAs of the chunks that have landed; the 128 threads of the
+// epilogue warps add their output's chunk values for db before releasing a
+// stage.  Batch rows past B are zeros, written by the producers.
 constexpr int DW_STAGES = 4;
 constexpr int DW_CHUNK = 64;                              // batch rows per stage (4 MMAs of K = 16)
 constexpr int DW_THREADS = 160;                           // 4 epilogue warps (TMEM lane quarters) + 1 issuing warp
@@ -866,8 +863,8 @@ constexpr size_t DW_STAGE = DW_STAGE_A + DW_STAGE_B;
 constexpr size_t DW_SMEM = DW_STAGES * DW_STAGE + 1024;  // + alignment of the ring to the 1 KB swizzle atom
 constexpr int DW_MAX_SPLITS = 32;
 
-// tensor maps: A operands (128-feature boxes) dZ_0^T, dZ_1^T, dZ_2^T, A_2^T;
-// B operands (every feature) x^T, A_0^T, A_1^T, dZ_3^T
+// tensor maps (f8 layout): A operands (16 feature groups: 128 features) dZ_0,
+// dZ_1, dZ_2, A_2; B operands (every feature group) x, A_0, A_1, dZ_3
 struct DwMaps {
   CUtensorMap map[8];
 };
@@ -877,35 +874,30 @@ struct DwArgs {
   int* err;
 };
 
-// sum of 8 BF16 values
-__device__ __forceinline__ float sum8(const uint4& u) {
-  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
-  float s = 0.f;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) s += __low2float(h[q]) + __high2float(h[q]);
-  return s;
-}
 __device__ __forceinline__ void mbar_init_n(uint64_t* bar, uint32_t n) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(n) : "memory");
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-// 2-D tensor copy global -> shared, completion counted on the mbarrier
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+// 3-D tensor copy global -> shared, completion counted on the mbarrier
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
           smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
-// K-major with the 128-byte swizzle: 8-row atoms 1024 B apart (stride offset),
-// leading offset unused (16 B), descriptor version 1, layout type 2 (128-byte
-// swizzle); a K step of 16 BF16 inside the 128-byte row advances the start by 32 B
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
-  return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) | (1ull << 16) | (static_cast<uint64_t>(1024 >> 4) << 32) |
-         (1ull << 46) | (2ull << 61);
+// MN-major without swizzle, as the stages hold the operands: core matrices of
+// 8 rows (K) x 16 bytes (8 features), the feature groups' core matrices of a
+// K group side by side (128 B apart: stride offset), K groups G x 128 B apart
+// (leading offset; G = the operand's feature groups), descriptor version 1,
+// layout type 0
+__device__ __forceinline__ uint64_t smem_desc_f8(uint32_t saddr, uint32_t kgroup_bytes) {
+  return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) | (static_cast<uint64_t>(kgroup_bytes >> 4) << 16) |
+         (static_cast<uint64_t>(128 >> 4) << 32) | (1ull << 46);
 }
+constexpr uint32_t IDESC_MN = (1u << 15) | (1u << 16);  // kind::f16: both operands MN-major
 
 __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __grid_constant__ DwMaps tm, DwArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -946,12 +938,12 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __
     // copies and MMAs: chunk c lives in stage c % DW_STAGES; its stage is refilled
     // with chunk c + DW_STAGES once the MMAs of c and its db sums are done
     auto load = [&](int c) {
-      const int st = c % DW_STAGES, x0 = r_begin + c * DW_CHUNK;
+      const int st = c % DW_STAGES, y0 = r_begin + c * DW_CHUNK;
       mbar_expect_tx(&full[st], stage_tx);
-      tma_load_2d(stage_a(st), mA, x0, half * 128, &full[st]);
-      tma_load_2d(stage_b(st), mB, x0, 0, &full[st]);
+      tma_load_3d(stage_a(st), mA, 0, half * 16, y0 / 8, &full[st]);
+      tma_load_3d(stage_b(st), mB, 0, 0, y0 / 8, &full[st]);
     };
-    const uint32_t id = instr_desc(ROWS, NB_);
+    const uint32_t id = instr_desc(ROWS, NB_) | IDESC_MN;
     int issued = 0;
     for (; issued < n_chunks && issued < DW_STAGES; ++issued) load(issued);
     for (int c = 0; c < n_chunks; ++c) {
@@ -965,8 +957,8 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __
       tc_fence_after();
       const uint32_t a0 = smem_u32(stage_a(st)), b0 = smem_u32(stage_b(st));
       for (int kk = 0; kk < DW_CHUNK / 16; ++kk)
-        umma_bf16(tmem, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), id,
-                  (c > 0 || kk > 0) ? 1u : 0u);
+        umma_bf16(tmem, smem_desc_f8(a0 + kk * 2 * 16 * 128, 16 * 128),
+                  smem_desc_f8(b0 + kk * 2 * (NB_ / 8) * 128, (NB_ / 8) * 128), id, (c > 0 || kk > 0) ? 1u : 0u);
       umma_commit(&empty[st]);
       if (issued < n_chunks) {
         if (!mbar_wait_bounded(&empty[st], par)) {
@@ -994,10 +986,15 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __
         break;
       }
       if (mine) {
-        // the row's 128 bytes, its 16-byte pieces in swizzled order (the sum does not mind)
-        const unsigned char* base = (sum_a ? stage_a(st) : stage_b(st)) + row * 128;
+        // output `row`: element row % 8 of the 16-byte rows of its feature group's
+        // core matrices, one per K group (G x 128 B apart)
+        const int G = sum_a ? 16 : NB_ / 8;
+        const unsigned char* base = (sum_a ? stage_a(st) : stage_b(st)) + (row >> 3) * 128 + (row & 7) * 2;
 #pragma unroll
-        for (int j = 0; j < DW_CHUNK / 8; ++j) cs += sum8(*reinterpret_cast<const uint4*>(base + j * 16));
+        for (int kg = 0; kg < DW_CHUNK / 8; ++kg)
+#pragma unroll
+          for (int ri = 0; ri < 8; ++ri)
+            cs += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(base + kg * G * 128 + ri * 16));
       }
       mbar_arrive(&empty[st]);
     }
@@ -1108,11 +1105,11 @@ struct tamp_mlp {
   float* grad = nullptr;
   float* m = nullptr;
   float* v = nullptr;
-  int ldT = 0;                   // row length of the feature-major arrays: max_batch rounded up to 64
   __half* G = nullptr;           // [3][g_rows][H]: GELU'(Z_l) of the last training forward (FP16, g_pieces layout)
-  __nv_bfloat16* XT = nullptr;   // [IN][ldT]
-  __nv_bfloat16* AT = nullptr;   // [3][H][ldT]
-  __nv_bfloat16* dZT = nullptr;  // [3][H][ldT] then [OUT][ldT]
+  // weight-gradient operands in the f8 layout ([features / 8][g_rows] x 16 bytes)
+  uint4* X8 = nullptr;           // x: IN / 8 groups
+  uint4* A8 = nullptr;           // A_0 .. A_2: 3 x H / 8 groups
+  uint4* dZ8 = nullptr;          // dZ_0 .. dZ_2 (3 x H / 8 groups), then dZ_3 (OUT / 8)
   float* out = nullptr;        // [max_batch][OUT]
   float* part = nullptr;       // [DW_MAX_SPLITS][N_PARAMS]: per row split partial gradients
   mlpk::DwMaps dw_maps;        // tensor maps of the weight-gradient operands for batches of dw_maps_B rows
@@ -1175,11 +1172,11 @@ FwdArgs fwd_args(tamp_mlp* n, const float* x, int B, float* out, bool train) {
   a.x = x; a.B = B; a.out = out; a.err = n->err;
   a.Wp = n->wp;
   for (int l = 0; l < 4; ++l) a.b[l] = n->params + b_off(l);
-  a.ldT = n->ldT;
-  a.XT = train ? n->XT : nullptr;
+  a.ldR = static_cast<int>(g_rows(n));
+  a.X8 = train ? n->X8 : nullptr;
   for (int l = 0; l < 3; ++l) {
     a.G[l] = train ? n->G + static_cast<size_t>(l) * g_rows(n) * H : nullptr;
-    a.AT[l] = train ? n->AT + static_cast<size_t>(l) * H * n->ldT : nullptr;
+    a.A8[l] = train ? n->A8 + static_cast<size_t>(l) * (H / 8) * g_rows(n) : nullptr;
   }
   return a;
 }
@@ -1201,26 +1198,28 @@ EncodeTiled encode_tiled() {
   return fn;
 }
 
-// The weight-gradient operands as 2-D tensors [features][batch rows] (row
-// length ldT, B valid rows: the copies fill rows past B with zeros), with
-// boxes of 64 batch rows by 128 features (A operands) or by every feature (B
-// operands), written into shared memory with the 128-byte swizzle.
+// The weight-gradient operands in the f8 layout as 3-D tensors: 8 rows of a
+// feature group (one 128-byte core matrix) x feature groups x blocks of 8 rows
+// (g_rows / 8), with boxes of 128 bytes x 16 groups (A operands: 128
+// features) or every group (B operands) x 8 blocks (a 64-row chunk): in shared
+// memory a K group's core matrices lie side by side.  No swizzle.  Rows past
+// B hold zeros, written by the producers for every row of their tiles.
 tamp_status make_dw_maps(tamp_mlp* n, int B) {
   if (n->dw_maps_B == B) return TAMP_OK;
   EncodeTiled enc = encode_tiled();
   if (!enc) return mfail(n, TAMP_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
-  const size_t lt = static_cast<size_t>(n->ldT);
-  struct Spec { const void* base; int rows, box; };
+  const size_t lr = g_rows(n), g = static_cast<size_t>(H / 8) * lr;  // uint4 per 256-feature array
+  struct Spec { const void* base; int groups, box; };
   const Spec spec[8] = {
-      {n->dZT, H, 128}, {n->dZT + H * lt, H, 128}, {n->dZT + 2 * H * lt, H, 128}, {n->AT + 2 * H * lt, H, 128},
-      {n->XT, IN, IN}, {n->AT, H, H}, {n->AT + H * lt, H, H}, {n->dZT + 3 * H * lt, OUT, OUT}};
+      {n->dZ8, H / 8, 16}, {n->dZ8 + g, H / 8, 16}, {n->dZ8 + 2 * g, H / 8, 16}, {n->A8 + 2 * g, H / 8, 16},
+      {n->X8, IN / 8, IN / 8}, {n->A8, H / 8, H / 8}, {n->A8 + g, H / 8, H / 8}, {n->dZ8 + 3 * g, OUT / 8, OUT / 8}};
   for (int i = 0; i < 8; ++i) {
-    const cuuint64_t dims[2] = {static_cast<cuuint64_t>(B), static_cast<cuuint64_t>(spec[i].rows)};
-    const cuuint64_t strides[1] = {static_cast<cuuint64_t>(lt * 2)};
-    const cuuint32_t box[2] = {DW_CHUNK, static_cast<cuuint32_t>(spec[i].box)};
-    const cuuint32_t es[2] = {1, 1};
-    const CUresult r = enc(&n->dw_maps.map[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(spec[i].base),
-                           dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+    const cuuint64_t dims[3] = {64, static_cast<cuuint64_t>(spec[i].groups), static_cast<cuuint64_t>(lr / 8)};
+    const cuuint64_t strides[2] = {static_cast<cuuint64_t>(lr * 16), 128};
+    const cuuint32_t box[3] = {64, static_cast<cuuint32_t>(spec[i].box), static_cast<cuuint32_t>(DW_CHUNK / 8)};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUresult r = enc(&n->dw_maps.map[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(spec[i].base),
+                           dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return mfail(n, TAMP_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
   }
@@ -1277,12 +1276,12 @@ tamp_status gradient(tamp_mlp* n, const float* x, const float* y, const float* m
   fa.loss = n->loss;  // zeroed by the forward, summed by the dZ chain
   MLP_TRY(n, launch_pdl(mlp_forward_kernel, dim3(tiles), dim3(THREADS), SMEM_BYTES, n->stream, fa));
   DzArgs z{};
-  z.B = B; z.ldT = n->ldT; z.out = n->out; z.y = y; z.mask = mask; z.loss = n->loss; z.WpT = n->wpt; z.err = n->err;
+  z.B = B; z.ldR = static_cast<int>(g_rows(n)); z.out = n->out; z.y = y; z.mask = mask; z.loss = n->loss; z.WpT = n->wpt; z.err = n->err;
   for (int l = 0; l < 3; ++l) {
     z.G[l] = n->G + static_cast<size_t>(l) * g_rows(n) * H;
-    z.dZT[l] = n->dZT + static_cast<size_t>(l) * H * n->ldT;
+    z.dZ8[l] = n->dZ8 + static_cast<size_t>(l) * (H / 8) * g_rows(n);
   }
-  z.dZT[3] = n->dZT + static_cast<size_t>(3) * H * n->ldT;
+  z.dZ8[3] = n->dZ8 + static_cast<size_t>(3) * (H / 8) * g_rows(n);
   MLP_TRY(n, launch_pdl(mlp_backward_dz_kernel, dim3(tiles), dim3(THREADS), SMEM_BYTES, n->stream, z));
   // weight gradients: 8 (layer, 128 outputs) blocks x row splits, about one CTA per SM
   const tamp_status ms = make_dw_maps(n, B);
@@ -1321,12 +1320,11 @@ tamp_status tamp_mlp_create(int device, void* stream, int max_batch, tamp_mlp** 
   if (e == cudaSuccess) e = cudaMalloc(&n->grad, N_PARAMS * 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->m, N_PARAMS * 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->v, N_PARAMS * 4);
-  n->ldT = static_cast<int>((mb + 63) / 64 * 64);
-  const size_t lt = static_cast<size_t>(n->ldT);
+  const size_t lr = g_rows(n);
   if (e == cudaSuccess) e = cudaMalloc(&n->G, 3 * g_rows(n) * H * 2);
-  if (e == cudaSuccess) e = cudaMalloc(&n->XT, IN * lt * 2);
-  if (e == cudaSuccess) e = cudaMalloc(&n->AT, 3 * H * lt * 2);
-  if (e == cudaSuccess) e = cudaMalloc(&n->dZT, (3 * H + OUT) * lt * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&n->X8, IN * lr * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&n->A8, 3 * H * lr * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&n->dZ8, (3 * H + OUT) * lr * 2);
   if (e == cudaSuccess) e = cudaMalloc(&n->out, mb * OUT * 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->part, static_cast<size_t>(DW_MAX_SPLITS) * N_PARAMS * 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->loss, 4);
@@ -1351,7 +1349,7 @@ tamp_status tamp_mlp_destroy(tamp_mlp* n) {
   Dev g(n->device);
   cudaStreamSynchronize(n->stream);
   cudaFree(n->params); cudaFree(n->wp); cudaFree(n->wpt); cudaFree(n->grad); cudaFree(n->m); cudaFree(n->v);
-  cudaFree(n->G); cudaFree(n->XT); cudaFree(n->AT); cudaFree(n->dZT); cudaFree(n->out);
+  cudaFree(n->G); cudaFree(n->X8); cudaFree(n->A8); cudaFree(n->dZ8); cudaFree(n->out);
   cudaFree(n->loss); cudaFree(n->err); cudaFree(n->part);
   delete n;
   return TAMP_OK;
