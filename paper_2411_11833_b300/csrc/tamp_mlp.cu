@@ -778,8 +778,20 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_backward_dz_kernel(DzArgs a) {
   }
   const uint32_t tmem = tslot;
   uint32_t ph_mma = 0, ph_w = 0;
+  static_assert(H / NGRP == 64, "a thread's columns of dA: two 32-column chunks");
   for (int l = 3; l >= 1; --l) {
     const int K = kdim(l), N = ndim(l);
+    // this layer's GELU'(Z_{l-1}) pieces, loaded while the product runs (the
+    // global loads' latency off the path from the product to the epilogue)
+    uint4 gpre[2][4];
+    if (r < a.B) {
+#pragma unroll
+      for (int ch = 0; ch < 2; ++ch) {
+        const uint4* gs = g_pieces(a.G[l - 1], blockIdx.x, warp, ch, lane);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) gpre[ch][q] = gs[32 * q];
+      }
+    }
     if (t == 0) {
       const bool okw = mbar_wait_bounded(&bar_w, ph_w);
       w_pending = !okw;
@@ -798,15 +810,16 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_backward_dz_kernel(DzArgs a) {
       w_pending = true;
     }
     uint4* dz8 = a.dZ8[l - 1];
-    for (int c0 = grp * (K / NGRP); c0 < (grp + 1) * (K / NGRP); c0 += 32) {
+#pragma unroll
+    for (int ch = 0; ch < 2; ++ch) {
+      const int c0 = grp * 64 + 32 * ch;
       float v[32];
       tmem_ld32(lane_addr(tmem, c0), v);
       uint32_t hp[16];
       if (r < a.B) {
-        const uint4* gs = g_pieces(a.G[l - 1], blockIdx.x, warp, (c0 - grp * (K / NGRP)) >> 5, lane);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const uint4 g = gs[32 * q];
+          const uint4 g = gpre[ch][q];
           const uint32_t gw[4] = {g.x, g.y, g.z, g.w};
 #pragma unroll
           for (int h = 0; h < 4; ++h) {
