@@ -517,8 +517,10 @@ __global__ void __launch_bounds__(PP_THREADS, 1) mlp_forward_pp_kernel(PpArgs a)
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int i = t; i < 3 * H + OUT; i += PP_THREADS) s_bias[i] = i < 3 * H ? a.b[i / H][i % H] : a.b[3][i - 3 * H];
   if (warp == 0) tmem_alloc512(&tslot);
+  pdl_wait();  // the inputs, the weights of the last update
+  pdl_release();
+  for (int i = t; i < 3 * H + OUT; i += PP_THREADS) s_bias[i] = i < 3 * H ? a.b[i / H][i % H] : a.b[3][i - 3 * H];
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -1240,30 +1242,10 @@ tamp_status make_dw_maps(tamp_mlp* n, int B) {
   return TAMP_OK;
 }
 
-// Inference forward: pairs of 128-row tiles, about one CTA per SM, each taking
-// pairs until none is left.
-cudaError_t launch_forward_pp(tamp_mlp* n, const float* x, int B, float* out, cudaStream_t st) {
-  PpArgs a{};
-  a.x = x; a.B = B; a.out = out; a.err = n->err; a.Wp = n->wp;
-  for (int l = 0; l < 4; ++l) a.b[l] = n->params + b_off(l);
-  int sm = 148;
-  cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, n->device);
-  const int pairs = ((B + ROWS - 1) / ROWS + 1) / 2;
-  mlp_forward_pp_kernel<<<std::min(pairs, sm), PP_THREADS, PP_SMEM, st>>>(a);
-  return cudaGetLastError();
-}
-
-tamp_status check_err(tamp_mlp* n) {
-  int e = 0;
-  MLP_TRY(n, cudaMemcpyAsync(&e, n->err, 4, cudaMemcpyDeviceToHost, n->stream));
-  MLP_TRY(n, cudaStreamSynchronize(n->stream));
-  if (e) return mfail(n, TAMP_ERR_TIMEOUT, "a tensor-core completion wait timed out on the device");
-  return TAMP_OK;
-}
-
-// a kernel of the training step, launched with programmatic stream
-// serialisation: it may be scheduled while the previous kernel of the stream
-// finishes, and waits for it (pdl_wait) before reading its outputs
+// a kernel launched with programmatic stream serialisation (the training
+// step's kernels, the inference forward): it may be scheduled while the
+// previous kernel of the stream finishes, and waits for it (pdl_wait) before
+// reading its outputs
 template <typename... P, typename... A>
 cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args) {
   cudaLaunchConfig_t cfg{};
@@ -1278,6 +1260,27 @@ cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem,
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
 }
+
+// Inference forward: pairs of 128-row tiles, about one CTA per SM, each taking
+// pairs until none is left.
+cudaError_t launch_forward_pp(tamp_mlp* n, const float* x, int B, float* out, cudaStream_t st) {
+  PpArgs a{};
+  a.x = x; a.B = B; a.out = out; a.err = n->err; a.Wp = n->wp;
+  for (int l = 0; l < 4; ++l) a.b[l] = n->params + b_off(l);
+  int sm = 148;
+  cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, n->device);
+  const int pairs = ((B + ROWS - 1) / ROWS + 1) / 2;
+  return launch_pdl(mlp_forward_pp_kernel, dim3(std::min(pairs, sm)), dim3(PP_THREADS), PP_SMEM, st, a);
+}
+
+tamp_status check_err(tamp_mlp* n) {
+  int e = 0;
+  MLP_TRY(n, cudaMemcpyAsync(&e, n->err, 4, cudaMemcpyDeviceToHost, n->stream));
+  MLP_TRY(n, cudaStreamSynchronize(n->stream));
+  if (e) return mfail(n, TAMP_ERR_TIMEOUT, "a tensor-core completion wait timed out on the device");
+  return TAMP_OK;
+}
+
 
 // forward (training form) + loss + backward: the row splits' partial gradients
 // in n->part (*splits_out of them), summed into n->grad if `reduce`
