@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* opA = smem;
   unsigned char* opB = smem + SMEM_A;
-  __shared__ __align__(8) uint64_t bar_mma, bar_w;
+  __shared__ __align__(8) uint64_t bar_mma[2], bar_w;  // the product's two column halves; the weights
   __shared__ uint32_t tslot;
   __shared__ __align__(16) float s_bias[3 * H + OUT];  // every layer's bias, read by the epilogues
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31, grp = warp >> 2;
@@ -306,7 +306,8 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
   const int Rv = min(ROWS, a.B - row0);
   bool w_pending = false;  // thread 0: a weight copy is in flight
   if (t == 0) {
-    mbar_init(&bar_mma);
+    mbar_init(&bar_mma[0]);
+    mbar_init(&bar_mma[1]);
     mbar_init(&bar_w);
     fence_proxy_async();
   }
@@ -337,31 +338,51 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
   tc_fence_after();
   const uint32_t tmem = tslot;
   uint32_t ph_mma = 0, ph_w = 0;
-  bool ok = true;
+  int copy_par = -1;  // thread 256: the barrier phase parity of the last weight copy it issued
   for (int l = 0; l < 4; ++l) {
     const int K = kdim(l), N = ndim(l);
+    bool fail = false;
     if (t == 0) {
       const bool okw = mbar_wait_bounded(&bar_w, ph_w);
       w_pending = !okw;
-      if (okw) issue_gemm(tmem, opA, opB, N, K, &bar_mma);
-      else atomicOr(a.err, ERR_WAIT);
+      if (okw && N == H) {
+        // two column halves, each committed to its own barrier: the epilogue
+        // warps of columns 0 .. 127 start while the tensor core computes 128 .. 255
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(opA), b0 = smem_u32(opB), id = instr_desc(ROWS, H / 2);
+        for (int h = 0; h < 2; ++h) {
+          for (int c = 0; c < K / 16; ++c)
+            umma_bf16(tmem + h * (H / 2), smem_desc(a0 + c * ROWS * 32), smem_desc(b0 + h * (H / 16) * 256 + c * H * 32),
+                      id, c > 0 ? 1u : 0u);
+          umma_commit(&bar_mma[h]);
+        }
+      } else if (okw) {
+        issue_gemm(tmem, opA, opB, N, K, &bar_mma[0]);
+        umma_commit(&bar_mma[1]);
+      } else {
+        atomicOr(a.err, ERR_WAIT);
+        fail = true;
+      }
     }
     ph_w ^= 1u;
-    bool okm = mbar_wait_bounded(&bar_mma, ph_mma);
+    const bool okm = mbar_wait_bounded(&bar_mma[grp >> 1], ph_mma);  // this group's column half
     ph_mma ^= 1u;
-    if (!okm) atomicOr(a.err, ERR_WAIT);
+    if (!okm) {
+      atomicOr(a.err, ERR_WAIT);
+      fail = true;
+    }
     tc_fence_after();
-    ok = __syncthreads_and(okm) != 0;
-    if (!ok) break;
-    if (t == 0 && l < 3) {  // the MMAs are done with opB: fetch the next layer's weights
+    if (t == 256 && l < 3 && okm) {
+      // the second half's commit covers every product of the layer: opB is free
+      // for the next layer's weights
       mbar_expect_tx(&bar_w, static_cast<uint32_t>(pk_bytes(l + 1)));
       bulk_g2s(opB, a.Wp + pk_off(l + 1), static_cast<uint32_t>(pk_bytes(l + 1)), &bar_w);
-      w_pending = true;
+      copy_par = (l + 1) & 1;
     }
     // epilogue: this warp's rows, its group's columns (the 32-wide last layer:
     // group 0 only)
     const int per = N >= 128 ? N / NGRP : N;
-    if (N >= 128 || grp == 0) {
+    if (!fail && (N >= 128 || grp == 0)) {
       for (int c0 = grp * per; c0 < grp * per + per; c0 += 32) {
         float v[32];
         tmem_ld32(lane_addr(tmem, c0), v);
@@ -404,10 +425,13 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
     }
     fence_proxy_async();  // the activations, written by every thread, to the tensor core
     tc_fence_before();
-    __syncthreads();      // every row's activations staged; accumulator free for the next layer
+    const int any_fail = __syncthreads_or(fail);  // every row's activations staged; accumulator free
     tc_fence_after();
+    if (any_fail) break;
   }
-  if (t == 0 && w_pending) mbar_wait_bounded(&bar_w, ph_w);  // no copy may land after the CTA ends
+  // no copy may land after the CTA ends
+  if (t == 0 && w_pending) mbar_wait_bounded(&bar_w, ph_w);
+  if (t == 256 && copy_par >= 0) mbar_wait_bounded(&bar_w, static_cast<uint32_t>(copy_par));
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem);
 }
