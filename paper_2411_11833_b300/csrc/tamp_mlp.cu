@@ -738,14 +738,15 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_backward_dz_kernel(DzArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* opA = smem;
   unsigned char* opB = smem + SMEM_A;
-  __shared__ __align__(8) uint64_t bar_mma, bar_w;
+  __shared__ __align__(8) uint64_t bar_mma[2], bar_w;  // the product's two column halves; the weights
   __shared__ uint32_t tslot;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31, grp = warp >> 2;
   const int row = 32 * (warp & 3) + lane, row0 = blockIdx.x * ROWS, r = row0 + row;
   const int Rv = min(ROWS, a.B - row0);
   bool w_pending = false;
   if (t == 0) {
-    mbar_init(&bar_mma);
+    mbar_init(&bar_mma[0]);
+    mbar_init(&bar_mma[1]);
     mbar_init(&bar_w);
     fence_proxy_async();
   }
@@ -804,6 +805,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_backward_dz_kernel(DzArgs a) {
   }
   const uint32_t tmem = tslot;
   uint32_t ph_mma = 0, ph_w = 0;
+  int copy_par = -1;  // thread 256: the barrier phase parity of the last weight copy it issued
   static_assert(H / NGRP == 64, "a thread's columns of dA: two 32-column chunks");
   for (int l = 3; l >= 1; --l) {
     const int K = kdim(l), N = ndim(l);
@@ -818,26 +820,43 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_backward_dz_kernel(DzArgs a) {
         for (int q = 0; q < 4; ++q) gpre[ch][q] = gs[32 * q];
       }
     }
+    bool fail = false;
     if (t == 0) {
       const bool okw = mbar_wait_bounded(&bar_w, ph_w);
       w_pending = !okw;
-      if (okw) issue_gemm(tmem, opA, opB, K, N, &bar_mma);  // dA_{l-1} [128 x K] = dZ_l [128 x N] . W_l
-      else atomicOr(a.err, ERR_WAIT);
+      if (okw) {
+        // dA_{l-1} [128 x K] = dZ_l [128 x N] . W_l in two column halves, each
+        // committed to its own barrier (the first half's epilogue overlaps the
+        // second half's product)
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(opA), b0 = smem_u32(opB), id = instr_desc(ROWS, K / 2);
+        for (int h = 0; h < 2; ++h) {
+          for (int c = 0; c < N / 16; ++c)
+            umma_bf16(tmem + h * (K / 2), smem_desc(a0 + c * ROWS * 32), smem_desc(b0 + h * (K / 16) * 256 + c * K * 32),
+                      id, c > 0 ? 1u : 0u);
+          umma_commit(&bar_mma[h]);
+        }
+      } else {
+        atomicOr(a.err, ERR_WAIT);
+        fail = true;
+      }
     }
     ph_w ^= 1u;
-    const bool okm = mbar_wait_bounded(&bar_mma, ph_mma);
+    const bool okm = mbar_wait_bounded(&bar_mma[grp >> 1], ph_mma);  // this group's column half
     ph_mma ^= 1u;
-    if (!okm) atomicOr(a.err, ERR_WAIT);
+    if (!okm) {
+      atomicOr(a.err, ERR_WAIT);
+      fail = true;
+    }
     tc_fence_after();
-    if (__syncthreads_and(okm) == 0) break;
-    if (t == 0 && l > 1) {
+    if (t == 256 && l > 1 && okm) {  // every product of the layer is done with opB: the next weights
       mbar_expect_tx(&bar_w, static_cast<uint32_t>(pk_bytes(l - 1)));
       bulk_g2s(opB, a.WpT + pk_off(l - 1), static_cast<uint32_t>(pk_bytes(l - 1)), &bar_w);
-      w_pending = true;
+      copy_par = (4 - l) & 1;
     }
     uint4* dz8 = a.dZ8[l - 1];
 #pragma unroll
-    for (int ch = 0; ch < 2; ++ch) {
+    for (int ch = 0; ch < 2 && !fail; ++ch) {
       const int c0 = grp * 64 + 32 * ch;
       float v[32];
       tmem_ld32(lane_addr(tmem, c0), v);
@@ -870,10 +889,13 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_backward_dz_kernel(DzArgs a) {
     }
     fence_proxy_async();
     tc_fence_before();
-    __syncthreads();
+    const int any_fail = __syncthreads_or(fail);
     tc_fence_after();
+    if (any_fail) break;
   }
+  // no copy may land after the CTA ends
   if (t == 0 && w_pending) mbar_wait_bounded(&bar_w, ph_w);
+  if (t == 256 && copy_par >= 0) mbar_wait_bounded(&bar_w, static_cast<uint32_t>(copy_par));
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem);
 }
