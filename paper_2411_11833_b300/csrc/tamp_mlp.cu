@@ -921,7 +921,9 @@ constexpr int DW_CHUNK = 64;                              // batch rows per stag
 constexpr int DW_THREADS = 160;                           // 4 epilogue warps (TMEM lane quarters) + 1 issuing warp
 constexpr size_t DW_STAGE_A = 128 * DW_CHUNK * 2, DW_STAGE_B = 256 * DW_CHUNK * 2;
 constexpr size_t DW_STAGE = DW_STAGE_A + DW_STAGE_B;
-constexpr size_t DW_SMEM = DW_STAGES * DW_STAGE + 1024;  // + alignment of the ring to the 1 KB swizzle atom
+// + alignment of the ring to 1 KB, + the all-ones operand of the bias gradients (16 x 64 BF16)
+constexpr size_t DW_ONES = 16 * DW_CHUNK * 2;
+constexpr size_t DW_SMEM = DW_STAGES * DW_STAGE + 1024 + DW_ONES;
 constexpr int DW_MAX_SPLITS = 32;
 
 // tensor maps (f8 layout): A operands (16 feature groups: 128 features) dZ_0,
@@ -980,18 +982,25 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __
     abort_flag = 0;
     for (int st = 0; st < DW_STAGES; ++st) {
       mbar_init_n(&full[st], 1);
-      mbar_init_n(&empty[st], 1 + 128);  // the MMAs' commit and the 128 db threads
+      // the MMAs' commit (and, for the 32-output layer, the 128 threads summing db)
+      mbar_init_n(&empty[st], swapped ? 1 + 128 : 1);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(&tslot);
-  pdl_wait();  // the feature-major operands of the forward and the dZ chain
+  if (warp == 0) tmem_alloc512(&tslot);  // dW: columns 0 .. 255; db: 256 .. 271
+  unsigned char* ring = smem + ((1024u - (smem_u32(smem) & 1023u)) & 1023u);  // 1 KB aligned
+  // db_l[n] = sum over rows of dZ_l[row][n] = (dZ_l^T . 1)[n]: a second product of
+  // the same A operand with a 16-column block of ones (the f8 layout of 16
+  // features x 64 rows), accumulated in tensor memory next to dW
+  unsigned char* ones = ring + DW_STAGES * DW_STAGE;
+  if (t < 128) reinterpret_cast<uint4*>(ones)[t] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+  fence_proxy_async();
+  pdl_wait();  // the operands written by the forward and the dZ chain
   pdl_release();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tslot;
-  unsigned char* ring = smem + ((1024u - (smem_u32(smem) & 1023u)) & 1023u);  // 1 KB aligned
   auto stage_a = [&](int st) { return ring + st * DW_STAGE; };
   auto stage_b = [&](int st) { return ring + st * DW_STAGE + DW_STAGE_A; };
 
@@ -1004,7 +1013,8 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __
       tma_load_3d(stage_a(st), mA, 0, half * 16, y0 / 8, &full[st]);
       tma_load_3d(stage_b(st), mB, 0, 0, y0 / 8, &full[st]);
     };
-    const uint32_t id = instr_desc(ROWS, NB_) | IDESC_MN;
+    const uint32_t id = instr_desc(ROWS, NB_) | IDESC_MN, id_db = instr_desc(ROWS, 16) | IDESC_MN;
+    const uint32_t o0 = smem_u32(ones);
     int issued = 0;
     for (; issued < n_chunks && issued < DW_STAGES; ++issued) load(issued);
     for (int c = 0; c < n_chunks; ++c) {
@@ -1020,6 +1030,10 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __
       for (int kk = 0; kk < DW_CHUNK / 16; ++kk)
         umma_bf16(tmem, smem_desc_f8(a0 + kk * 2 * 16 * 128, 16 * 128),
                   smem_desc_f8(b0 + kk * 2 * (NB_ / 8) * 128, (NB_ / 8) * 128), id, (c > 0 || kk > 0) ? 1u : 0u);
+      if (!swapped)
+        for (int kk = 0; kk < DW_CHUNK / 16; ++kk)
+          umma_bf16(tmem + 256, smem_desc_f8(a0 + kk * 2 * 16 * 128, 16 * 128), smem_desc_f8(o0 + kk * 2 * 256, 256),
+                    id_db, (c > 0 || kk > 0) ? 1u : 0u);
       umma_commit(&empty[st]);
       if (issued < n_chunks) {
         if (!mbar_wait_bounded(&empty[st], par)) {
@@ -1033,10 +1047,11 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __
     // no copy may land after the CTA ends: wait for every chunk issued
     for (int c = max(0, issued - DW_STAGES); c < issued; ++c)
       mbar_wait_bounded(&full[c % DW_STAGES], static_cast<uint32_t>(c / DW_STAGES) & 1u);
-  } else if (t < 128) {
-    // db: this thread's row of the chunk (outputs of the layer), then release the stage
+  } else if (t < 128 && swapped) {
+    // db of the 32-output layer (its outputs are the B operand): this thread's
+    // output summed over the chunk's rows, then the stage released
     const int row = t;
-    const bool mine = sum_a || (sum_b && row < NB_);
+    const bool mine = sum_b && row < NB_;
     float cs = 0.f;
     for (int c = 0; c < n_chunks; ++c) {
       const int st = c % DW_STAGES;
@@ -1049,8 +1064,8 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __
       if (mine) {
         // output `row`: element row % 8 of the 16-byte rows of its feature group's
         // core matrices, one per K group (G x 128 B apart)
-        const int G = sum_a ? 16 : NB_ / 8;
-        const unsigned char* base = (sum_a ? stage_a(st) : stage_b(st)) + (row >> 3) * 128 + (row & 7) * 2;
+        const int G = NB_ / 8;
+        const unsigned char* base = stage_b(st) + (row >> 3) * 128 + (row & 7) * 2;
 #pragma unroll
         for (int kg = 0; kg < DW_CHUNK / 8; ++kg)
 #pragma unroll
@@ -1059,10 +1074,7 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __
       }
       mbar_arrive(&empty[st]);
     }
-    if (mine) {
-      float* gb = a.part + static_cast<long>(blockIdx.y) * N_PARAMS + b_off(l);
-      gb[sum_a ? half * 128 + row : row] = cs;
-    }
+    if (mine) a.part[static_cast<long>(blockIdx.y) * N_PARAMS + b_off(l) + row] = cs;
   }
   __syncthreads();
   // every MMA has completed once the last chunk's stage was released
@@ -1097,10 +1109,15 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __
           if (c0 + 4 * q < NB_) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       }
     }
+    if (sum_a) {  // db of this block's outputs, from the ones product
+      float v[32];
+      tmem_ld32(lane_addr(tmem, 256), v);
+      a.part[static_cast<long>(blockIdx.y) * N_PARAMS + b_off(l) + half * 128 + row] = n_chunks ? v[0] : 0.f;
+    }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem);
+  if (warp == 0) tmem_dealloc512(tmem);
 }
 
 // grad = sum over the row splits of their partial gradients
