@@ -916,15 +916,20 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_backward_dz_kernel(DzArgs a) {
 // issues the MMAs of the chunks that have landed; the 128 threads of the
 // epilogue warps add their output's chunk values for db before releasing a
 // stage.  Batch rows past B are zeros, written by the producers.
-constexpr int DW_STAGES = 4;
+constexpr int DW_STAGES = 3;
 constexpr int DW_CHUNK = 64;                              // batch rows per stage (4 MMAs of K = 16)
 constexpr int DW_THREADS = 160;                           // 4 epilogue warps (TMEM lane quarters) + 1 issuing warp
-constexpr size_t DW_STAGE_A = 128 * DW_CHUNK * 2, DW_STAGE_B = 256 * DW_CHUNK * 2;
+constexpr size_t DW_STAGE_A = 128 * DW_CHUNK * 2, DW_STAGE_B = 128 * DW_CHUNK * 2;  // B: at most 128 features
 constexpr size_t DW_STAGE = DW_STAGE_A + DW_STAGE_B;
 // + alignment of the ring to 1 KB, + the all-ones operand of the bias gradients (16 x 64 BF16)
 constexpr size_t DW_ONES = 16 * DW_CHUNK * 2;
 constexpr size_t DW_SMEM = DW_STAGES * DW_STAGE + 1024 + DW_ONES;
 constexpr int DW_MAX_SPLITS = 32;
+// CTAs of one row split: the 256-wide layers 1 and 2 as (128 outputs) x (128
+// inputs) blocks, 4 each; layers 0 (48 inputs) and 3 (32 outputs, swapped) as
+// 128-row blocks of the whole product, 2 each -- blocks of similar work, two
+// CTAs per SM (99 KB of shared memory, 256 tensor-memory columns each)
+constexpr int DW_BLOCKS = 12;
 
 // tensor maps (f8 layout): A operands (16 feature groups: 128 features) dZ_0,
 // dZ_1, dZ_2, A_2; B operands (every feature group) x, A_0, A_1, dZ_3
@@ -962,19 +967,22 @@ __device__ __forceinline__ uint64_t smem_desc_f8(uint32_t saddr, uint32_t kgroup
 }
 constexpr uint32_t IDESC_MN = (1u << 15) | (1u << 16);  // kind::f16: both operands MN-major
 
-__global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __grid_constant__ DwMaps tm, DwArgs a) {
+__global__ void __launch_bounds__(DW_THREADS, 2) mlp_backward_dw_kernel(const __grid_constant__ DwMaps tm, DwArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[DW_STAGES], empty[DW_STAGES];
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
   const int t = threadIdx.x, warp = t >> 5;
-  const int l = blockIdx.x >> 1, half = blockIdx.x & 1;
+  // block: layers 1, 2 -> (layer, output half, input half); layers 0, 3 -> (layer, half)
+  const int bx = blockIdx.x;
+  const int l = bx < 8 ? 1 + (bx >> 2) : (bx < 10 ? 0 : 3);
+  const int half = bx < 8 ? (bx >> 1) & 1 : bx & 1, nh = bx < 8 ? bx & 1 : 0;
   const bool swapped = l == 3;  // 32 outputs: M runs over the inputs, D = dW^T
   const int K = kdim(l), N = ndim(l);
-  const int NB_ = swapped ? N : K;  // the GEMM's N' (rows of the B operand)
+  const int NB_ = swapped ? N : (K == H ? H / 2 : K);  // the GEMM's N' (rows of the B operand)
   const CUtensorMap* mA = &tm.map[swapped ? 3 : l];
   const CUtensorMap* mB = &tm.map[4 + l];
-  const bool sum_a = !swapped, sum_b = swapped && half == 0;  // db: each output's column once
+  const bool sum_a = !swapped && nh == 0, sum_b = swapped && half == 0;  // db: each output's column once
   const int r_begin = blockIdx.y * a.rows_per_split, r_end = min(a.B, r_begin + a.rows_per_split);
   const int n_chunks = r_end > r_begin ? (r_end - r_begin + DW_CHUNK - 1) / DW_CHUNK : 0;
   const uint32_t stage_tx = static_cast<uint32_t>((128 + NB_) * DW_CHUNK * 2);
@@ -987,7 +995,7 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) tmem_alloc512(&tslot);  // dW: columns 0 .. 255; db: 256 .. 271
+  if (warp == 0) tmem_alloc(&tslot);  // dW: columns 0 .. N' - 1 (at most 128); db: 128 .. 143
   unsigned char* ring = smem + ((1024u - (smem_u32(smem) & 1023u)) & 1023u);  // 1 KB aligned
   // db_l[n] = sum over rows of dZ_l[row][n] = (dZ_l^T . 1)[n]: a second product of
   // the same A operand with a 16-column block of ones (the f8 layout of 16
@@ -1011,7 +1019,7 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __
       const int st = c % DW_STAGES, y0 = r_begin + c * DW_CHUNK;
       mbar_expect_tx(&full[st], stage_tx);
       tma_load_3d(stage_a(st), mA, 0, half * 16, y0 / 8, &full[st]);
-      tma_load_3d(stage_b(st), mB, 0, 0, y0 / 8, &full[st]);
+      tma_load_3d(stage_b(st), mB, 0, nh * 16, y0 / 8, &full[st]);
     };
     const uint32_t id = instr_desc(ROWS, NB_) | IDESC_MN, id_db = instr_desc(ROWS, 16) | IDESC_MN;
     const uint32_t o0 = smem_u32(ones);
@@ -1030,9 +1038,9 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __
       for (int kk = 0; kk < DW_CHUNK / 16; ++kk)
         umma_bf16(tmem, smem_desc_f8(a0 + kk * 2 * 16 * 128, 16 * 128),
                   smem_desc_f8(b0 + kk * 2 * (NB_ / 8) * 128, (NB_ / 8) * 128), id, (c > 0 || kk > 0) ? 1u : 0u);
-      if (!swapped)
+      if (sum_a)
         for (int kk = 0; kk < DW_CHUNK / 16; ++kk)
-          umma_bf16(tmem + 256, smem_desc_f8(a0 + kk * 2 * 16 * 128, 16 * 128), smem_desc_f8(o0 + kk * 2 * 256, 256),
+          umma_bf16(tmem + 128, smem_desc_f8(a0 + kk * 2 * 16 * 128, 16 * 128), smem_desc_f8(o0 + kk * 2 * 256, 256),
                     id_db, (c > 0 || kk > 0) ? 1u : 0u);
       umma_commit(&empty[st]);
       if (issued < n_chunks) {
@@ -1103,7 +1111,7 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __
         for (int j = 0; j < 32; ++j)
           if (c0 + j < NB_) gW[static_cast<long>(c0 + j) * K + half * 128 + row] = v[j];
       } else {
-        float4* dst = reinterpret_cast<float4*>(gW + static_cast<long>(half * 128 + row) * K + c0);
+        float4* dst = reinterpret_cast<float4*>(gW + static_cast<long>(half * 128 + row) * K + nh * 128 + c0);
 #pragma unroll
         for (int q = 0; q < 8; ++q)
           if (c0 + 4 * q < NB_) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
@@ -1111,13 +1119,13 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_backward_dw_kernel(const __
     }
     if (sum_a) {  // db of this block's outputs, from the ones product
       float v[32];
-      tmem_ld32(lane_addr(tmem, 256), v);
+      tmem_ld32(lane_addr(tmem, 128), v);
       a.part[static_cast<long>(blockIdx.y) * N_PARAMS + b_off(l) + half * 128 + row] = n_chunks ? v[0] : 0.f;
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc512(tmem);
+  if (warp == 0) tmem_dealloc(tmem);
 }
 
 // grad = sum over the row splits of their partial gradients
@@ -1290,7 +1298,7 @@ tamp_status make_dw_maps(tamp_mlp* n, int B) {
   struct Spec { const void* base; int groups, box; };
   const Spec spec[8] = {
       {n->dZ8, H / 8, 16}, {n->dZ8 + g, H / 8, 16}, {n->dZ8 + 2 * g, H / 8, 16}, {n->A8 + 2 * g, H / 8, 16},
-      {n->X8, IN / 8, IN / 8}, {n->A8, H / 8, H / 8}, {n->A8 + g, H / 8, H / 8}, {n->dZ8 + 3 * g, OUT / 8, OUT / 8}};
+      {n->X8, IN / 8, IN / 8}, {n->A8, H / 8, 16}, {n->A8 + g, H / 8, 16}, {n->dZ8 + 3 * g, OUT / 8, OUT / 8}};
   for (int i = 0; i < 8; ++i) {
     const cuuint64_t dims[3] = {64, static_cast<cuuint64_t>(spec[i].groups), static_cast<cuuint64_t>(lr / 8)};
     const cuuint64_t strides[2] = {static_cast<cuuint64_t>(lr * 16), 128};
@@ -1362,16 +1370,18 @@ tamp_status gradient(tamp_mlp* n, const float* x, const float* y, const float* m
   }
   z.dZ8[3] = n->dZ8 + static_cast<size_t>(3) * (H / 8) * g_rows(n);
   MLP_TRY(n, launch_pdl(mlp_backward_dz_kernel, dim3(tiles), dim3(THREADS), SMEM_BYTES, n->stream, z));
-  // weight gradients: 8 (layer, 128 outputs) blocks x row splits, about one CTA per SM
+  // weight gradients: DW_BLOCKS blocks x row splits
   const tamp_status ms = make_dw_maps(n, B);
   if (ms != TAMP_OK) return ms;
   DwArgs w{};
   int sm = 148;
   cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, n->device);
-  const int splits = std::max(1, std::min({DW_MAX_SPLITS, sm / 8, (B + DW_CHUNK - 1) / DW_CHUNK}));
+  // row splits: about two CTAs per SM over the DW_BLOCKS blocks of each split
+  const int splits = std::max(1, std::min({DW_MAX_SPLITS, 2 * sm / DW_BLOCKS, (B + DW_CHUNK - 1) / DW_CHUNK}));
   w.B = B; w.part = n->part; w.err = n->err;
   w.rows_per_split = ((B + splits - 1) / splits + DW_CHUNK - 1) / DW_CHUNK * DW_CHUNK;
-  MLP_TRY(n, launch_pdl(mlp_backward_dw_kernel, dim3(8, splits), dim3(DW_THREADS), DW_SMEM, n->stream, n->dw_maps, w));
+  MLP_TRY(n, launch_pdl(mlp_backward_dw_kernel, dim3(DW_BLOCKS, splits), dim3(DW_THREADS), DW_SMEM, n->stream,
+                        n->dw_maps, w));
   *splits_out = splits;
   if (reduce) {
     mlp_reduce_kernel<<<static_cast<int>((N_PARAMS + 255) / 256), 256, 0, n->stream>>>(n->part, splits, n->grad,
