@@ -287,6 +287,7 @@ struct FwdArgs {
   // BF16 operands of the weight gradients x and A_l in the f8 layout (ldR rows)
   __half* G[3]; uint4* X8; uint4* A8[3]; int ldR;
   float* loss;                        // training: the NLL accumulator, zeroed here for the backward pass
+  float* grad;                        // training: the gradient accumulator [N_PARAMS], zeroed here for dW
   int* err;
 };
 
@@ -320,6 +321,9 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
     w_pending = true;
     if (a.loss && blockIdx.x == 0) *a.loss = 0.f;
   }
+  if (a.grad)  // the dW kernel adds every split's share into it
+    for (int i = blockIdx.x * THREADS + t; i < static_cast<int>(N_PARAMS / 4); i += gridDim.x * THREADS)
+      reinterpret_cast<float4*>(a.grad)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int i = t; i < 3 * H + OUT; i += THREADS) s_bias[i] = i < 3 * H ? a.b[i / H][i % H] : a.b[3][i - 3 * H];
   // inputs: 8 columns (one 16-byte chunk of the layout) per step
   for (int c = t; c < ROWS * (IN / 8); c += THREADS) {
@@ -938,7 +942,7 @@ struct DwMaps {
 };
 struct DwArgs {
   int B, rows_per_split;
-  float* part;                        // [split][N_PARAMS]: this split's share of dW and db
+  float* grad;                        // [N_PARAMS]: every split adds its share of dW and db (zeroed by the forward)
   int* err;
 };
 
@@ -1082,7 +1086,7 @@ __global__ void __launch_bounds__(DW_THREADS, 2) mlp_backward_dw_kernel(const __
       }
       mbar_arrive(&empty[st]);
     }
-    if (mine) a.part[static_cast<long>(blockIdx.y) * N_PARAMS + b_off(l) + row] = cs;
+    if (mine && n_chunks > 0) atomicAdd(a.grad + b_off(l) + row, cs);
   }
   __syncthreads();
   // every MMA has completed once the last chunk's stage was released
@@ -1096,45 +1100,33 @@ __global__ void __launch_bounds__(DW_THREADS, 2) mlp_backward_dw_kernel(const __
   }
   tc_fence_after();
   ok = __syncthreads_and(ok) != 0;
-  // this split's partial dW, written whole (zeros for a split past the last row)
-  if (ok && t < 128) {
-    float* gW = a.part + static_cast<long>(blockIdx.y) * N_PARAMS + w_off(l);
+  // this split's share of dW (and db), added into the gradient
+  if (ok && t < 128 && n_chunks > 0) {
+    float* gW = a.grad + w_off(l);
     const int row = t;
     for (int c0 = 0; c0 < NB_; c0 += 32) {
       float v[32];
       tmem_ld32(lane_addr(tmem, c0), v);
-      if (n_chunks == 0)
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = 0.f;
       if (swapped) {
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-          if (c0 + j < NB_) gW[static_cast<long>(c0 + j) * K + half * 128 + row] = v[j];
+          if (c0 + j < NB_) atomicAdd(gW + static_cast<long>(c0 + j) * K + half * 128 + row, v[j]);
       } else {
         float4* dst = reinterpret_cast<float4*>(gW + static_cast<long>(half * 128 + row) * K + nh * 128 + c0);
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-          if (c0 + 4 * q < NB_) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          if (c0 + 4 * q < NB_) atomicAdd(dst + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
       }
     }
     if (sum_a) {  // db of this block's outputs, from the ones product
       float v[32];
       tmem_ld32(lane_addr(tmem, 128), v);
-      a.part[static_cast<long>(blockIdx.y) * N_PARAMS + b_off(l) + half * 128 + row] = n_chunks ? v[0] : 0.f;
+      atomicAdd(a.grad + b_off(l) + half * 128 + row, v[0]);
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem);
-}
-
-// grad = sum over the row splits of their partial gradients
-__global__ void mlp_reduce_kernel(const float* __restrict__ part, int splits, float* __restrict__ grad, int n) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  float sum = 0.f;
-  for (int s = 0; s < splits; ++s) sum += part[static_cast<long>(s) * n + i];
-  grad[i] = sum;
 }
 
 // ------------------------------------------------------------------ Adam on the FP32 master weights
@@ -1154,16 +1146,15 @@ __device__ __forceinline__ void store_packed(int i, float w, unsigned char* Wp, 
   }
 }
 
-// the gradient is the sum of the row splits' partials (as mlp_reduce_kernel forms it)
-__global__ void mlp_adam_kernel(float* p, const float* __restrict__ part, int splits, float* m, float* v,
-                                unsigned char* Wp, unsigned char* WpT, int n, float lr, float b1, float b2, float eps,
-                                float ib1, float ib2) {
+// the gradient as the dW kernel has summed it over the row splits
+__global__ void mlp_adam_kernel(float* p, const float* __restrict__ grad, float* m, float* v, unsigned char* Wp,
+                                unsigned char* WpT, int n, float lr, float b1, float b2, float eps, float ib1,
+                                float ib2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  pdl_wait();  // the row splits' partial gradients
+  pdl_wait();  // the gradient
   pdl_release();
   if (i >= n) return;
-  float gi = 0.f;
-  for (int s = 0; s < splits; ++s) gi += part[static_cast<long>(s) * n + i];
+  const float gi = grad[i];
   const float mi = fmaf(b1, m[i], (1.f - b1) * gi), vi = fmaf(b2, v[i], (1.f - b2) * gi * gi);
   m[i] = mi;
   v[i] = vi;
@@ -1197,7 +1188,6 @@ struct tamp_mlp {
   uint4* A8 = nullptr;           // A_0 .. A_2: 3 x H / 8 groups
   uint4* dZ8 = nullptr;          // dZ_0 .. dZ_2 (3 x H / 8 groups), then dZ_3 (OUT / 8)
   float* out = nullptr;        // [max_batch][OUT]
-  float* part = nullptr;       // [DW_MAX_SPLITS][N_PARAMS]: per row split partial gradients
   mlpk::DwMaps dw_maps;        // tensor maps of the weight-gradient operands for batches of dw_maps_B rows
   int dw_maps_B = -1;
   float* loss = nullptr;
@@ -1353,14 +1343,14 @@ tamp_status check_err(tamp_mlp* n) {
 }
 
 
-// forward (training form) + loss + backward: the row splits' partial gradients
-// in n->part (*splits_out of them), summed into n->grad if `reduce`
-tamp_status gradient(tamp_mlp* n, const float* x, const float* y, const float* mask, int B, bool reduce,
-                     int* splits_out) {
+// forward (training form) + loss + backward: the gradient in n->grad (every
+// row split's share added by the dW kernel into the buffer the forward zeroed)
+tamp_status gradient(tamp_mlp* n, const float* x, const float* y, const float* mask, int B) {
   MLP_TRY(n, enable_smem(n->device));
   const int tiles = (B + ROWS - 1) / ROWS;
   FwdArgs fa = fwd_args(n, x, B, n->out, true);
   fa.loss = n->loss;  // zeroed by the forward, summed by the dZ chain
+  fa.grad = n->grad;  // zeroed by the forward, summed by the dW kernel
   MLP_TRY(n, launch_pdl(mlp_forward_kernel, dim3(tiles), dim3(THREADS), SMEM_BYTES, n->stream, fa));
   DzArgs z{};
   z.B = B; z.ldR = static_cast<int>(g_rows(n)); z.out = n->out; z.y = y; z.mask = mask; z.loss = n->loss; z.WpT = n->wpt; z.err = n->err;
@@ -1378,16 +1368,10 @@ tamp_status gradient(tamp_mlp* n, const float* x, const float* y, const float* m
   cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, n->device);
   // row splits: about two CTAs per SM over the DW_BLOCKS blocks of each split
   const int splits = std::max(1, std::min({DW_MAX_SPLITS, 2 * sm / DW_BLOCKS, (B + DW_CHUNK - 1) / DW_CHUNK}));
-  w.B = B; w.part = n->part; w.err = n->err;
+  w.B = B; w.grad = n->grad; w.err = n->err;
   w.rows_per_split = ((B + splits - 1) / splits + DW_CHUNK - 1) / DW_CHUNK * DW_CHUNK;
   MLP_TRY(n, launch_pdl(mlp_backward_dw_kernel, dim3(DW_BLOCKS, splits), dim3(DW_THREADS), DW_SMEM, n->stream,
                         n->dw_maps, w));
-  *splits_out = splits;
-  if (reduce) {
-    mlp_reduce_kernel<<<static_cast<int>((N_PARAMS + 255) / 256), 256, 0, n->stream>>>(n->part, splits, n->grad,
-                                                                                     static_cast<int>(N_PARAMS));
-    MLP_TRY(n, cudaGetLastError());
-  }
   return TAMP_OK;
 }
 }  // namespace
@@ -1415,7 +1399,6 @@ tamp_status tamp_mlp_create(int device, void* stream, int max_batch, tamp_mlp** 
   if (e == cudaSuccess) e = cudaMalloc(&n->A8, 3 * H * lr * 2);
   if (e == cudaSuccess) e = cudaMalloc(&n->dZ8, (3 * H + OUT) * lr * 2);
   if (e == cudaSuccess) e = cudaMalloc(&n->out, mb * OUT * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&n->part, static_cast<size_t>(DW_MAX_SPLITS) * N_PARAMS * 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->loss, 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->err, 4);
   if (e == cudaSuccess) e = cudaMemsetAsync(n->params, 0, N_PARAMS * 4, n->stream);
@@ -1439,7 +1422,7 @@ tamp_status tamp_mlp_destroy(tamp_mlp* n) {
   cudaStreamSynchronize(n->stream);
   cudaFree(n->params); cudaFree(n->wp); cudaFree(n->wpt); cudaFree(n->grad); cudaFree(n->m); cudaFree(n->v);
   cudaFree(n->G); cudaFree(n->X8); cudaFree(n->A8); cudaFree(n->dZ8); cudaFree(n->out);
-  cudaFree(n->loss); cudaFree(n->err); cudaFree(n->part);
+  cudaFree(n->loss); cudaFree(n->err);
   delete n;
   return TAMP_OK;
 }
@@ -1484,8 +1467,7 @@ tamp_status tamp_mlp_gradient(tamp_mlp* n, const float* x, const float* y, const
   if (!n) return TAMP_ERR_INVALID_ARG;
   if (!x || !y || !mask || B <= 0 || B > n->max_batch) return mfail(n, TAMP_ERR_INVALID_ARG, "bad batch");
   Dev g(n->device);
-  int splits = 0;
-  tamp_status st = gradient(n, x, y, mask, B, true, &splits);
+  tamp_status st = gradient(n, x, y, mask, B);
   if (st != TAMP_OK) return st;
   if (grad_dev) MLP_TRY(n, cudaMemcpyAsync(grad_dev, n->grad, N_PARAMS * 4, cudaMemcpyDeviceToDevice, n->stream));
   if (loss) MLP_TRY(n, cudaMemcpyAsync(loss, n->loss, 4, cudaMemcpyDeviceToHost, n->stream));
@@ -1497,16 +1479,15 @@ tamp_status tamp_mlp_train_step(tamp_mlp* n, const float* x, const float* y, con
   if (!n) return TAMP_ERR_INVALID_ARG;
   if (!x || !y || !mask || B <= 0 || B > n->max_batch || !(lr >= 0.f)) return mfail(n, TAMP_ERR_INVALID_ARG, "bad batch");
   Dev g(n->device);
-  int splits = 0;
-  tamp_status st = gradient(n, x, y, mask, B, false, &splits);
+  tamp_status st = gradient(n, x, y, mask, B);
   if (st != TAMP_OK) return st;
   ++n->step;
   const double b1 = 0.9, b2 = 0.999;
   const float ib1 = static_cast<float>(1.0 / (1.0 - std::pow(b1, static_cast<double>(n->step))));
   const float ib2 = static_cast<float>(1.0 / (1.0 - std::pow(b2, static_cast<double>(n->step))));
   MLP_TRY(n, launch_pdl(mlp_adam_kernel, dim3(static_cast<int>((N_PARAMS + 255) / 256)), dim3(256), 0, n->stream,
-                        n->params, n->part, splits, n->m, n->v, n->wp, n->wpt, static_cast<int>(N_PARAMS), lr, 0.9f,
-                        0.999f, 1e-8f, ib1, ib2));
+                        n->params, n->grad, n->m, n->v, n->wp, n->wpt, static_cast<int>(N_PARAMS), lr, 0.9f, 0.999f,
+                        1e-8f, ib1, ib2));
   if (loss) {
     MLP_TRY(n, cudaMemcpyAsync(loss, n->loss, 4, cudaMemcpyDeviceToHost, n->stream));
     return check_err(n);
