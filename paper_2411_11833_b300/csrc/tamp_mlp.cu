@@ -275,33 +275,41 @@ __device__ __forceinline__ float2 gelu_grad2(float2 z) {
   return __ffma2_rn(z, pdf, phi_fit2(z));
 }
 
-// ------------------------------------------------------------------ forward
-struct FwdArgs {
+// ------------------------------------------------------------------ training: forward, NLL, dZ chain
+struct TrainArgs {
   const float* x; int B;              // inputs [B][IN]
+  const float* y;                     // [B][NTGT] targets
+  const float* mask;                  // [B][NTGT]
   const unsigned char* Wp;            // packed BF16 forward operands (pk_off)
+  const unsigned char* WpT;           // packed W^T operands (pk_off)
   const float* b[4];
-  float* out;                         // [B][OUT]
-  // training only (else null): GELU'(Z_l) (FP16: GELU' lies in [-0.17,
-  // 1.13], where FP16 rounds 8 times finer than BF16; in the g_pieces layout)
-  // -- the backward pass uses the pre-activations only through it -- and the
-  // BF16 operands of the weight gradients x and A_l in the f8 layout (ldR rows)
-  __half* G[3]; uint4* X8; uint4* A8[3]; int ldR;
-  float* loss;                        // training: the NLL accumulator, zeroed here for the backward pass
-  float* grad;                        // training: the gradient accumulator [N_PARAMS], zeroed here for dW
+  // GELU'(Z_l) (FP16: GELU' lies in [-0.17, 1.13], where FP16 rounds 8 times
+  // finer than BF16; in the g_pieces layout) -- the backward pass uses the
+  // pre-activations only through it -- and the BF16 operands of the weight
+  // gradients x, A_l and dZ_l in the f8 layout (ldR rows)
+  __half* G[3]; uint4* X8; uint4* A8[3]; uint4* dZ8[4]; int ldR;
+  float* loss;                        // the NLL's mean over rows, zeroed here and accumulated
+  float* grad;                        // the gradient accumulator [N_PARAMS], zeroed here for dW
   int* err;
 };
 
-// One CTA per 128 rows.  Each layer's packed weights arrive by one bulk copy,
-// issued as soon as the previous layer's MMAs have finished reading the operand
-// buffer, so it overlaps that layer's epilogue; activations stay in shared
-// memory as the next layer's A operand.
-__global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
+// One CTA per 128 rows: the forward through the 4 layers, the Gaussian NLL
+// and its gradient dZ_3 at the outputs, then the dZ chain back to dZ_0
+// (dA_{l-1} = dZ_l W_l on the tensor core, dZ_{l-1} = dA_{l-1} * GELU'(Z_{l-1})).
+// Each product's packed weights (W_l forward, W_l^T backward) arrive by one
+// bulk copy, issued as soon as the previous product has finished reading the
+// operand buffer, so it overlaps that layer's epilogue; activations and dZ_l
+// stay in shared memory as the next product's A operand.  A 256-wide product
+// runs in two column halves with their own barriers, so that the epilogue of
+// the first half overlaps the product of the second.
+__global__ void __launch_bounds__(THREADS, 1) mlp_train_kernel(TrainArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* opA = smem;
   unsigned char* opB = smem + SMEM_A;
   __shared__ __align__(8) uint64_t bar_mma[2], bar_w;  // the product's two column halves; the weights
   __shared__ uint32_t tslot;
   __shared__ __align__(16) float s_bias[3 * H + OUT];  // every layer's bias, read by the epilogues
+  __shared__ float s_loss[4];                          // the output layer's warps' NLL sums
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31, grp = warp >> 2;
   const int row = 32 * (warp & 3) + lane, row0 = blockIdx.x * ROWS, r = row0 + row;
   const int Rv = min(ROWS, a.B - row0);
@@ -343,6 +351,8 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
   const uint32_t tmem = tslot;
   uint32_t ph_mma = 0, ph_w = 0;
   int copy_par = -1;  // thread 256: the barrier phase parity of the last weight copy it issued
+  bool alive = true;  // no wait has given up
+  static_assert(H / NGRP == 64, "a thread's columns of dA: two 32-column chunks");
   for (int l = 0; l < 4; ++l) {
     const int K = kdim(l), N = ndim(l);
     bool fail = false;
@@ -376,11 +386,14 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
       fail = true;
     }
     tc_fence_after();
-    if (t == 256 && l < 3 && okm) {
+    if (t == 256 && okm) {
       // the second half's commit covers every product of the layer: opB is free
-      // for the next layer's weights
-      mbar_expect_tx(&bar_w, static_cast<uint32_t>(pk_bytes(l + 1)));
-      bulk_g2s(opB, a.Wp + pk_off(l + 1), static_cast<uint32_t>(pk_bytes(l + 1)), &bar_w);
+      // for the next layer's weights (after the output layer: W_3^T, the first
+      // operand of the backward pass)
+      const unsigned char* src = l < 3 ? a.Wp + pk_off(l + 1) : a.WpT + pk_off(3);
+      const uint32_t bytes = static_cast<uint32_t>(l < 3 ? pk_bytes(l + 1) : pk_bytes(3));
+      mbar_expect_tx(&bar_w, bytes);
+      bulk_g2s(opB, src, bytes, &bar_w);
       copy_par = (l + 1) & 1;
     }
     // epilogue: this warp's rows, its group's columns (the 32-wide last layer:
@@ -418,12 +431,39 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
                   in ? make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]) : make_uint4(0u, 0u, 0u, 0u);
             }
           }
-        } else if (r < a.B) {
-          float4* od = reinterpret_cast<float4*>(a.out + static_cast<long>(r) * OUT + c0);
+        } else {
+          // the outputs (mu_k, s_k = log sigma_k) and from them dZ_3 = dL/d(outputs) of
+          // the Gaussian NLL, the mean over the B rows of sum over masked k of
+          // (y_k - mu_k)^2 exp(-2 s_k) / 2 + s_k:
+          // dL/dmu_k = -m (y_k - mu_k) exp(-2 s_k) / B, dL/ds_k = m (1 - (y_k - mu_k)^2 exp(-2 s_k)) / B.
+          // It is the A operand (K = 32) of the first backward product, and goes to
+          // dZ8[3] for the weight gradients; this warp's rows' NLL terms are summed.
+          const float inv = 1.f / static_cast<float>(a.B);
+          float dz[OUT], lsum = 0.f;
 #pragma unroll
-          for (int q = 0; q < 8; ++q)
-            od[q] = make_float4(v[4 * q] + bias[4 * q], v[4 * q + 1] + bias[4 * q + 1], v[4 * q + 2] + bias[4 * q + 2],
-                                v[4 * q + 3] + bias[4 * q + 3]);
+          for (int k = 0; k < NTGT; ++k) {
+            dz[k] = 0.f;
+            dz[NTGT + k] = 0.f;
+            if (r < a.B) {
+              const float mu = v[k] + bias[k], sg = v[NTGT + k] + bias[NTGT + k];
+              const float m = a.mask[static_cast<long>(r) * NTGT + k], d = a.y[static_cast<long>(r) * NTGT + k] - mu;
+              const float ex = expf(-2.f * sg);
+              dz[k] = m * (-d * ex) * inv;
+              dz[NTGT + k] = m * (1.f - d * d * ex) * inv;
+              lsum += m * (0.5f * d * d * ex + sg);
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < OUT / 8; ++q) {
+            const uint4 pk = make_uint4(pack_bf16x2(dz[8 * q], dz[8 * q + 1]), pack_bf16x2(dz[8 * q + 2], dz[8 * q + 3]),
+                                        pack_bf16x2(dz[8 * q + 4], dz[8 * q + 5]),
+                                        pack_bf16x2(dz[8 * q + 6], dz[8 * q + 7]));
+            *reinterpret_cast<uint4*>(opA + blk_off(row, 8 * q, ROWS)) = pk;
+            a.dZ8[3][static_cast<long>(q) * a.ldR + r] = pk;  // rows past B: zeros
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+          if (lane == 0) s_loss[warp] = lsum;
         }
       }
     }
@@ -431,7 +471,102 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(FwdArgs a) {
     tc_fence_before();
     const int any_fail = __syncthreads_or(fail);  // every row's activations staged; accumulator free
     tc_fence_after();
-    if (any_fail) break;
+    if (any_fail) {
+      alive = false;
+      break;
+    }
+  }
+  // the mean NLL: the output layer's warps' sums (complete after the last forward barrier)
+  if (t == 0 && alive) atomicAdd(a.loss, (s_loss[0] + s_loss[1] + s_loss[2] + s_loss[3]) / static_cast<float>(a.B));
+  // ---- the dZ chain, from dZ_3 in opA and W_3^T arriving in opB
+  for (int l = 3; alive && l >= 1; --l) {
+    const int K = kdim(l), N = ndim(l);
+    // this layer's GELU'(Z_{l-1}) pieces, loaded while the product runs (the
+    // global loads' latency off the path from the product to the epilogue)
+    uint4 gpre[2][4];
+    if (r < a.B) {
+#pragma unroll
+      for (int ch = 0; ch < 2; ++ch) {
+        const uint4* gs = g_pieces(a.G[l - 1], blockIdx.x, warp, ch, lane);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) gpre[ch][q] = gs[32 * q];
+      }
+    }
+    bool fail = false;
+    if (t == 0) {
+      const bool okw = mbar_wait_bounded(&bar_w, ph_w);
+      w_pending = !okw;
+      if (okw) {
+        // dA_{l-1} [128 x K] = dZ_l [128 x N] . W_l in two column halves, each
+        // committed to its own barrier (the first half's epilogue overlaps the
+        // second half's product)
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(opA), b0 = smem_u32(opB), id = instr_desc(ROWS, K / 2);
+        for (int h = 0; h < 2; ++h) {
+          for (int c = 0; c < N / 16; ++c)
+            umma_bf16(tmem + h * (K / 2), smem_desc(a0 + c * ROWS * 32), smem_desc(b0 + h * (K / 16) * 256 + c * K * 32),
+                      id, c > 0 ? 1u : 0u);
+          umma_commit(&bar_mma[h]);
+        }
+      } else {
+        atomicOr(a.err, ERR_WAIT);
+        fail = true;
+      }
+    }
+    ph_w ^= 1u;
+    const bool okm = mbar_wait_bounded(&bar_mma[grp >> 1], ph_mma);  // this group's column half
+    ph_mma ^= 1u;
+    if (!okm) {
+      atomicOr(a.err, ERR_WAIT);
+      fail = true;
+    }
+    tc_fence_after();
+    if (t == 256 && l > 1 && okm) {  // every product of the layer is done with opB: the next weights
+      mbar_expect_tx(&bar_w, static_cast<uint32_t>(pk_bytes(l - 1)));
+      bulk_g2s(opB, a.WpT + pk_off(l - 1), static_cast<uint32_t>(pk_bytes(l - 1)), &bar_w);
+      copy_par = l & 1;  // the copy of W_{l-1}^T completes the barrier's phase 8 - l
+    }
+    uint4* dz8 = a.dZ8[l - 1];
+#pragma unroll
+    for (int ch = 0; ch < 2 && !fail; ++ch) {
+      const int c0 = grp * 64 + 32 * ch;
+      float v[32];
+      tmem_ld32(lane_addr(tmem, c0), v);
+      uint32_t hp[16];
+      if (r < a.B) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint4 g = gpre[ch][q];
+          const uint32_t gw[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const float2 d = __fmul2_rn(make_float2(v[8 * q + 2 * h], v[8 * q + 2 * h + 1]), unpack_f16x2(gw[h]));
+            hp[4 * q + h] = pack_bf16x2(d.x, d.y);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) hp[q] = 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(opA + blk_off(row, c0 + 8 * q, ROWS)) =
+            make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
+      {
+        uint4* dd = dz8 + static_cast<long>(c0 >> 3) * a.ldR + r;  // f8: the warp's 32 rows side by side (zeros past B)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          dd[static_cast<long>(q) * a.ldR] = make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
+      }
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    const int any_fail = __syncthreads_or(fail);
+    tc_fence_after();
+    if (any_fail) {
+      alive = false;
+      break;
+    }
   }
   // no copy may land after the CTA ends
   if (t == 0 && w_pending) mbar_wait_bounded(&bar_w, ph_w);
@@ -716,194 +851,7 @@ __global__ void __launch_bounds__(PP_THREADS, 1) mlp_forward_pp_kernel(PpArgs a)
   if (warp == 0) tmem_dealloc512(tmem);
 }
 
-// ------------------------------------------------------------------ backward
-// Two kernels.  (1) Per 128-row tile: dZ_l for l = 3 .. 0 through the layers,
-// dA_{l-1} = dZ_l W_l on the tensor core (W_l^T packed, one bulk copy per
-// layer, prefetched during the previous epilogue), dZ_{l-1} = dA_{l-1} *
-// gelu'(Z_{l-1}) kept in shared memory as the next product's operand and
-// written feature-major for (2).  (2) Per (layer, 128 outputs, row split):
-// dW_l = dZ_l^T A_{l-1} accumulated over the split's rows in tensor memory
-// (rows are the GEMM's K), both operands read feature-major in 16-byte pieces
-// and double-buffered; each split adds its partial dW with one atomic per
-// weight, and db_l with one per output.
-struct DzArgs {
-  int B, ldR;
-  const float* out;                   // [B][OUT]: the training forward's outputs (mu, log sigma)
-  const float* y;                     // [B][NTGT] targets
-  const float* mask;                  // [B][NTGT]
-  float* loss;                        // the NLL's mean over rows, accumulated (zeroed before the launch)
-  __half* G[3];                       // GELU'(Z_l) (FP16, the g_pieces layout)
-  const unsigned char* WpT;           // packed W^T operands (pk_off)
-  uint4* dZ8[4];                      // dZ_l in the f8 layout (ldR rows): H features (l < 3), OUT (l = 3)
-  int* err;
-};
-
-__global__ void __launch_bounds__(THREADS, 1) mlp_backward_dz_kernel(DzArgs a) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char* opA = smem;
-  unsigned char* opB = smem + SMEM_A;
-  __shared__ __align__(8) uint64_t bar_mma[2], bar_w;  // the product's two column halves; the weights
-  __shared__ uint32_t tslot;
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31, grp = warp >> 2;
-  const int row = 32 * (warp & 3) + lane, row0 = blockIdx.x * ROWS, r = row0 + row;
-  const int Rv = min(ROWS, a.B - row0);
-  bool w_pending = false;
-  if (t == 0) {
-    mbar_init(&bar_mma[0]);
-    mbar_init(&bar_mma[1]);
-    mbar_init(&bar_w);
-    fence_proxy_async();
-  }
-  if (warp == 0) tmem_alloc(&tslot);
-  pdl_wait();  // the forward's outputs and GELU'(Z)
-  pdl_release();
-  if (t == 0) {
-    mbar_expect_tx(&bar_w, static_cast<uint32_t>(pk_bytes(3)));
-    bulk_g2s(opB, a.WpT + pk_off(3), static_cast<uint32_t>(pk_bytes(3)), &bar_w);
-    w_pending = true;
-  }
-  // dZ_3 = dL/d(outputs) of the Gaussian NLL, mean over the B rows of
-  // sum over masked k of (y_k - mu_k)^2 exp(-2 s_k) / 2 + s_k (s = log sigma):
-  // dL/dmu_k = -m (y_k - mu_k) exp(-2 s_k) / B, dL/ds_k = m (1 - (y_k - mu_k)^2 exp(-2 s_k)) / B.
-  // The A operand (K = 32) and its feature-major copy; the threads of columns
-  // 0 .. 15 (the means) also sum the rows' NLL terms.
-  __shared__ float s_loss[THREADS / 32];
-  float lsum = 0.f;
-  const float inv = 1.f / static_cast<float>(a.B);
-  for (int c = t; c < ROWS * (OUT / 8); c += THREADS) {
-    const int rr = c / (OUT / 8), kk = (c % (OUT / 8)) * 8, k0 = kk % NTGT;
-    float v[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      v[e] = 0.f;
-      if (rr < Rv) {
-        const long rw = row0 + rr;
-        const int k = k0 + e;
-        const float mu = a.out[rw * OUT + k], sg = a.out[rw * OUT + NTGT + k];
-        const float m = a.mask[rw * NTGT + k], d = a.y[rw * NTGT + k] - mu;
-        const float ex = expf(-2.f * sg);
-        if (kk < NTGT) {
-          v[e] = m * (-d * ex) * inv;
-          lsum += m * (0.5f * d * d * ex + sg);
-        } else {
-          v[e] = m * (1.f - d * d * ex) * inv;
-        }
-      }
-    }
-    const uint4 pk =
-        make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
-    *reinterpret_cast<uint4*>(opA + blk_off(rr, kk, ROWS)) = pk;
-    a.dZ8[3][static_cast<long>(kk >> 3) * a.ldR + row0 + rr] = pk;  // rows past B: zeros
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-  if (lane == 0) s_loss[warp] = lsum;
-  fence_proxy_async();
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (t == 0) {
-    float sum = 0.f;
-    for (int w = 0; w < THREADS / 32; ++w) sum += s_loss[w];
-    if (sum != 0.f) atomicAdd(a.loss, sum * inv);
-  }
-  const uint32_t tmem = tslot;
-  uint32_t ph_mma = 0, ph_w = 0;
-  int copy_par = -1;  // thread 256: the barrier phase parity of the last weight copy it issued
-  static_assert(H / NGRP == 64, "a thread's columns of dA: two 32-column chunks");
-  for (int l = 3; l >= 1; --l) {
-    const int K = kdim(l), N = ndim(l);
-    // this layer's GELU'(Z_{l-1}) pieces, loaded while the product runs (the
-    // global loads' latency off the path from the product to the epilogue)
-    uint4 gpre[2][4];
-    if (r < a.B) {
-#pragma unroll
-      for (int ch = 0; ch < 2; ++ch) {
-        const uint4* gs = g_pieces(a.G[l - 1], blockIdx.x, warp, ch, lane);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) gpre[ch][q] = gs[32 * q];
-      }
-    }
-    bool fail = false;
-    if (t == 0) {
-      const bool okw = mbar_wait_bounded(&bar_w, ph_w);
-      w_pending = !okw;
-      if (okw) {
-        // dA_{l-1} [128 x K] = dZ_l [128 x N] . W_l in two column halves, each
-        // committed to its own barrier (the first half's epilogue overlaps the
-        // second half's product)
-        tc_fence_after();
-        const uint32_t a0 = smem_u32(opA), b0 = smem_u32(opB), id = instr_desc(ROWS, K / 2);
-        for (int h = 0; h < 2; ++h) {
-          for (int c = 0; c < N / 16; ++c)
-            umma_bf16(tmem + h * (K / 2), smem_desc(a0 + c * ROWS * 32), smem_desc(b0 + h * (K / 16) * 256 + c * K * 32),
-                      id, c > 0 ? 1u : 0u);
-          umma_commit(&bar_mma[h]);
-        }
-      } else {
-        atomicOr(a.err, ERR_WAIT);
-        fail = true;
-      }
-    }
-    ph_w ^= 1u;
-    const bool okm = mbar_wait_bounded(&bar_mma[grp >> 1], ph_mma);  // this group's column half
-    ph_mma ^= 1u;
-    if (!okm) {
-      atomicOr(a.err, ERR_WAIT);
-      fail = true;
-    }
-    tc_fence_after();
-    if (t == 256 && l > 1 && okm) {  // every product of the layer is done with opB: the next weights
-      mbar_expect_tx(&bar_w, static_cast<uint32_t>(pk_bytes(l - 1)));
-      bulk_g2s(opB, a.WpT + pk_off(l - 1), static_cast<uint32_t>(pk_bytes(l - 1)), &bar_w);
-      copy_par = (4 - l) & 1;
-    }
-    uint4* dz8 = a.dZ8[l - 1];
-#pragma unroll
-    for (int ch = 0; ch < 2 && !fail; ++ch) {
-      const int c0 = grp * 64 + 32 * ch;
-      float v[32];
-      tmem_ld32(lane_addr(tmem, c0), v);
-      uint32_t hp[16];
-      if (r < a.B) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const uint4 g = gpre[ch][q];
-          const uint32_t gw[4] = {g.x, g.y, g.z, g.w};
-#pragma unroll
-          for (int h = 0; h < 4; ++h) {
-            const float2 d = __fmul2_rn(make_float2(v[8 * q + 2 * h], v[8 * q + 2 * h + 1]), unpack_f16x2(gw[h]));
-            hp[4 * q + h] = pack_bf16x2(d.x, d.y);
-          }
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) hp[q] = 0u;
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        *reinterpret_cast<uint4*>(opA + blk_off(row, c0 + 8 * q, ROWS)) =
-            make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
-      {
-        uint4* dd = dz8 + static_cast<long>(c0 >> 3) * a.ldR + r;  // f8: the warp's 32 rows side by side (zeros past B)
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          dd[static_cast<long>(q) * a.ldR] = make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
-      }
-    }
-    fence_proxy_async();
-    tc_fence_before();
-    const int any_fail = __syncthreads_or(fail);
-    tc_fence_after();
-    if (any_fail) break;
-  }
-  // no copy may land after the CTA ends
-  if (t == 0 && w_pending) mbar_wait_bounded(&bar_w, ph_w);
-  if (t == 256 && copy_par >= 0) mbar_wait_bounded(&bar_w, static_cast<uint32_t>(copy_par));
-  __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem);
-}
-
+// ------------------------------------------------------------------ backward: weight gradients
 // The weight gradients dW_l = dZ_l^T A_{l-1} (and db_l = column sums of dZ_l):
 // per CTA one layer, 128 of its outputs and a split of the batch rows, which
 // are the GEMM's K.  The operands -- x, A_l, dZ_l -- arrive in the f8 layout
@@ -1228,11 +1176,8 @@ cudaError_t enable_smem(int device) {
   static unsigned long long done = 0;  // one bit per device ordinal < 64
   const unsigned long long bit = device < 64 ? 1ull << device : 0;
   if (done & bit) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(SMEM_BYTES));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(mlp_backward_dz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(SMEM_BYTES));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mlp_backward_dw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(DW_SMEM));
@@ -1243,19 +1188,6 @@ cudaError_t enable_smem(int device) {
   return e;
 }
 
-FwdArgs fwd_args(tamp_mlp* n, const float* x, int B, float* out, bool train) {
-  FwdArgs a{};
-  a.x = x; a.B = B; a.out = out; a.err = n->err;
-  a.Wp = n->wp;
-  for (int l = 0; l < 4; ++l) a.b[l] = n->params + b_off(l);
-  a.ldR = static_cast<int>(g_rows(n));
-  a.X8 = train ? n->X8 : nullptr;
-  for (int l = 0; l < 3; ++l) {
-    a.G[l] = train ? n->G + static_cast<size_t>(l) * g_rows(n) * H : nullptr;
-    a.A8[l] = train ? n->A8 + static_cast<size_t>(l) * (H / 8) * g_rows(n) : nullptr;
-  }
-  return a;
-}
 
 // cuTensorMapEncodeTiled from the driver, through the runtime (no link-time
 // dependency on the driver library)
@@ -1348,18 +1280,20 @@ tamp_status check_err(tamp_mlp* n) {
 tamp_status gradient(tamp_mlp* n, const float* x, const float* y, const float* mask, int B) {
   MLP_TRY(n, enable_smem(n->device));
   const int tiles = (B + ROWS - 1) / ROWS;
-  FwdArgs fa = fwd_args(n, x, B, n->out, true);
-  fa.loss = n->loss;  // zeroed by the forward, summed by the dZ chain
-  fa.grad = n->grad;  // zeroed by the forward, summed by the dW kernel
-  MLP_TRY(n, launch_pdl(mlp_forward_kernel, dim3(tiles), dim3(THREADS), SMEM_BYTES, n->stream, fa));
-  DzArgs z{};
-  z.B = B; z.ldR = static_cast<int>(g_rows(n)); z.out = n->out; z.y = y; z.mask = mask; z.loss = n->loss; z.WpT = n->wpt; z.err = n->err;
+  TrainArgs ta{};
+  ta.x = x; ta.B = B; ta.y = y; ta.mask = mask; ta.err = n->err;
+  ta.Wp = n->wp; ta.WpT = n->wpt;
+  for (int l = 0; l < 4; ++l) ta.b[l] = n->params + b_off(l);
+  ta.ldR = static_cast<int>(g_rows(n));
+  ta.X8 = n->X8;
   for (int l = 0; l < 3; ++l) {
-    z.G[l] = n->G + static_cast<size_t>(l) * g_rows(n) * H;
-    z.dZ8[l] = n->dZ8 + static_cast<size_t>(l) * (H / 8) * g_rows(n);
+    ta.G[l] = n->G + static_cast<size_t>(l) * g_rows(n) * H;
+    ta.A8[l] = n->A8 + static_cast<size_t>(l) * (H / 8) * g_rows(n);
   }
-  z.dZ8[3] = n->dZ8 + static_cast<size_t>(3) * (H / 8) * g_rows(n);
-  MLP_TRY(n, launch_pdl(mlp_backward_dz_kernel, dim3(tiles), dim3(THREADS), SMEM_BYTES, n->stream, z));
+  for (int l = 0; l < 4; ++l) ta.dZ8[l] = n->dZ8 + static_cast<size_t>(l) * (H / 8) * g_rows(n);
+  ta.loss = n->loss;  // zeroed by the kernel, summed over its tiles
+  ta.grad = n->grad;  // zeroed by the kernel, summed by the dW kernel
+  MLP_TRY(n, launch_pdl(mlp_train_kernel, dim3(tiles), dim3(THREADS), SMEM_BYTES, n->stream, ta));
   // weight gradients: DW_BLOCKS blocks x row splits
   const tamp_status ms = make_dw_maps(n, B);
   if (ms != TAMP_OK) return ms;
