@@ -73,23 +73,27 @@ def test_forward_matches_oracle(pkg, B):
 
 @pytest.mark.parametrize("B", [128, 300, 3000, 16384])
 def test_gradient_matches_oracle(pkg, B):
-    # 3000 rows: weight-gradient row splits of three chunks and splits with no
-    # rows at all; 16384 (the benchmark's training batch): 15 chunks per split
+    # 300 rows: a ragged last tile (rows past the batch are zeros in the
+    # weight-gradient operands); 3000 rows: row splits of two chunks and splits
+    # with no rows at all; 16384 (the benchmark's training batch): 11 chunks per
+    # split.  Two calls in a row: the loss and the gradient are accumulators the
+    # training kernel zeroes, so the second call must not add onto the first.
     th = _params(5)
     x, y, mask = _batch(B, 20 + B)
     net = pkg.Mlp(max_batch=max(512, B))
     net.set_params(th)
-    loss, g = net.gradient(_cuda(x), _cuda(y), _cuda(mask))
-    g = g.cpu().double().numpy()
     L, gr = om.loss_and_grad(torch.from_numpy(th).double(), torch.from_numpy(x).double(),
                              torch.from_numpy(y).double(), torch.from_numpy(mask).double())
     gr = gr.numpy()
-    assert abs(loss - float(L)) <= 1e-4 * abs(float(L))
-    for kind, a, b in _blocks():
-        u, v = g[a:b], gr[a:b]
-        cos = float(u @ v / (np.linalg.norm(u) * np.linalg.norm(v)))
-        rel = float(np.linalg.norm(u - v) / np.linalg.norm(v))
-        assert cos >= 0.999 and rel <= 1e-2, (kind, a, cos, rel)
+    for call in range(2):
+        loss, g = net.gradient(_cuda(x), _cuda(y), _cuda(mask))
+        g = g.cpu().double().numpy()
+        assert abs(loss - float(L)) <= 1e-4 * abs(float(L)), (call, loss, float(L))
+        for kind, a, b in _blocks():
+            u, v = g[a:b], gr[a:b]
+            cos = float(u @ v / (np.linalg.norm(u) * np.linalg.norm(v)))
+            rel = float(np.linalg.norm(u - v) / np.linalg.norm(v))
+            assert cos >= 0.999 and rel <= 1e-2, (call, kind, a, cos, rel)
     net.close()
 
 
