@@ -433,11 +433,14 @@ tamp_status tamp_mlp_get_params(tamp_mlp *net, float *host_params, int count);
 tamp_status tamp_mlp_forward(tamp_mlp *net, const float *x_dev, int B, float *out_dev);
 /* Gradient of L at the current parameters (1 <= B <= max_batch): grad_dev
  * (device, param_count floats, may be NULL) and *loss (host, may be NULL).
+ * The sums over rows are accumulated by floating-point atomic additions, so
+ * two calls on the same batch agree to rounding, not bit for bit.
  * Synchronises. */
 tamp_status tamp_mlp_gradient(tamp_mlp *net, const float *x_dev, const float *y_dev, const float *mask_dev,
                               int B, float *grad_dev, float *loss);
-/* One Adam step on L with learning rate lr.  *loss (host, may be NULL) gets the
- * loss before the step; asking for it synchronises. */
+/* One Adam step on L with learning rate lr (the gradient as tamp_mlp_gradient
+ * forms it).  *loss (host, may be NULL) gets the loss before the step; asking
+ * for it synchronises. */
 tamp_status tamp_mlp_train_step(tamp_mlp *net, const float *x_dev, const float *y_dev, const float *mask_dev,
                                 int B, float lr, float *loss);
 const char *tamp_mlp_last_error(const tamp_mlp *net);
